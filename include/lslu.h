@@ -1,0 +1,151 @@
+/*
+ * lslu.h - C ABI of the GB300 (sm_103a) LSLU / Hybrid LSLU library.
+ *
+ * The library solves b = A x + e for a sparse rectangular A (m x n, CSR) with
+ * the inner-product-free LSLU and Hybrid LSLU methods of Brown, Chung, Nagy
+ * and Sabate Landman, "Inner Product Free Krylov Methods for Large-Scale
+ * Inverse Problems" (arXiv 2409.05239):
+ *   - the basis L_k (n-space) and D_{k+1} (m-space) come from the Hessenberg
+ *     process with pivoting for rectangular systems (Algorithm 4), with
+ *     A L_k = D_{k+1} H_{k+1,k} and A^T D_{k+1} = L_{k+1} W_{k+1}
+ *     (Eqs. nhr, nhr2);
+ *   - x_k = x_0 + L_k y_k with y_k = argmin ||beta e1 - H_{k+1,k} y||^2 +
+ *     lambda_k^2 ||y||^2 (Eq. TSP, Algorithm 5); lambda_k = 0 is LSLU
+ *     (Section 2.2), otherwise lambda_k is fixed or chosen by GCV (Eq. gcv2)
+ *     or weighted GCV with omega = (k+1)/m (Eq. wgcv).
+ *
+ * Conventions shared by every entry point:
+ *   - indices are 0-based; dense matrices are column-major;
+ *   - every call returns an lslu_status; the library never aborts or traps;
+ *     lslu_error_string() gives a one-line description of the last failure;
+ *   - pointers marked "host or device" are read or written on the host when
+ *     ptr_location is LSLU_HOST and on the current CUDA device when it is
+ *     LSLU_DEVICE; the caller owns every buffer it passes, the library owns
+ *     the memory behind a handle until lslu_destroy();
+ *   - calls on one handle are not thread-safe; all device work of a handle is
+ *     ordered on the stream given at creation (NULL = the legacy default
+ *     stream); calls that return host data synchronise that stream.
+ */
+#ifndef LSLU_H
+#define LSLU_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lslu_ctx* lslu_handle;
+
+typedef enum {
+  LSLU_OK = 0,
+  LSLU_ERR_INVALID_ARG = 1,  /* a size, pointer, CSR structure or option is invalid */
+  LSLU_ERR_CUDA = 2,         /* a CUDA runtime call failed                         */
+  LSLU_ERR_OOM = 3,          /* device memory allocation failed                    */
+  LSLU_ERR_TIMEOUT = 4,      /* a bounded device-side wait gave up                  */
+  LSLU_BREAKDOWN_BETA = 5,   /* r0 = b - A x0 is zero (Algorithm 4, initialisation) */
+  LSLU_BREAKDOWN_W = 6,      /* q has no non-zero unpivoted entry (Algorithm 4)     */
+  LSLU_BREAKDOWN_H = 7,      /* u has no non-zero unpivoted entry (Algorithm 4)     */
+  LSLU_ERR_NONFINITE = 8     /* a pivot or the data is NaN or infinite             */
+} lslu_status;
+
+/* Storage of A's values.  F64 keeps the basis and all accumulation in FP64.
+ * F32 and BF16 keep the basis vectors in FP32 and accumulate in FP32; the
+ * Hessenberg entries (H, W), the projected solve, lambda and x stay FP64. */
+typedef enum { LSLU_F64 = 0, LSLU_F32 = 1, LSLU_BF16 = 2 } lslu_value_type;
+
+/* Choice of lambda_k in Algorithm 5 (Section 3.3). */
+typedef enum {
+  LSLU_LAMBDA_NONE = 0,  /* LSLU: lambda = 0                                  */
+  LSLU_LAMBDA_FIXED = 1, /* the lambda argument for every k                   */
+  LSLU_LAMBDA_GCV = 2,   /* minimiser of the projected GCV function, Eq. gcv2 */
+  LSLU_LAMBDA_WGCV = 3   /* weighted GCV, omega = (k+1)/m, Eq. wgcv           */
+} lslu_lambda_rule;
+
+enum { LSLU_HOST = 0, LSLU_DEVICE = 1 };
+
+/* Create a solver for the m x n CSR matrix A (row_ptr: m+1 int64 offsets,
+ * col_idx: nnz int32 column indices in [0, n), vals: nnz FP64 values), all
+ * host or device per ptr_location.  The values are rounded to value_type
+ * (FP64 -> FP32 round-to-nearest-even; BF16 rounds that FP32 value to
+ * nearest-even).  The library keeps its own copy of A and of A^T (a
+ * transposed CSR, so A^T u needs no atomics) and allocates the bases for up to
+ * max_iter iterations: (n + m) * (max_iter + 1) basis entries.
+ * Errors: LSLU_ERR_INVALID_ARG for m, n < 1, nnz < 0, nnz >= 2^31,
+ * max_iter < 1 or > 2048, a non-monotone row_ptr, a column out of range or a
+ * non-finite value; LSLU_ERR_OOM; LSLU_ERR_CUDA.  *out is NULL on failure. */
+lslu_status lslu_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row_ptr,
+                        const int32_t* col_idx, const double* vals, int32_t value_type,
+                        int32_t max_iter, int32_t ptr_location, void* cuda_stream,
+                        lslu_handle* out);
+
+/* Run K iterations of Hybrid LSLU (Algorithm 5) on data b (length m, FP64)
+ * from x0 (length n, FP64; NULL means x0 = 0).  rule is an lslu_lambda_rule;
+ * lambda is used by LSLU_LAMBDA_FIXED only.  Outputs (host or device per
+ * ptr_location, any may be NULL except x_out):
+ *   x_out       n      FP64  x_k of the last completed iteration k = *k_done
+ *   col_pivots  K      int32 g: pivot row of l_1..l_k (entries past k_done = -1)
+ *   row_pivots  K+1    int32 t: pivot row of d_1..d_{k+1}
+ *   lambda_hist K      FP64  lambda_j for j = 1..k (needs per-iteration solves)
+ *   resid_hist  K      FP64  ||beta e1 - H_{j+1,j} y_j|| for j = 1..k
+ *   k_done      1      int32 completed iterations (== K unless a breakdown)
+ * When lambda_hist or resid_hist is non-NULL the projected problem is solved
+ * for every j (all at once after the basis loop, since the basis never
+ * depends on lambda); otherwise only for j = k_done.  A breakdown is not a
+ * failure of the call: it returns LSLU_BREAKDOWN_* with x of the last
+ * completed iteration (x0 if none).  K must satisfy 1 <= K <= max_iter. */
+lslu_status lslu_solve(lslu_handle h, const double* b, const double* x0, int32_t K,
+                       int32_t rule, double lambda, int32_t ptr_location, double* x_out,
+                       int32_t* col_pivots, int32_t* row_pivots, double* lambda_hist,
+                       double* resid_hist, int32_t* k_done);
+
+/* Copy the state of the last lslu_solve (host or device per ptr_location;
+ * any pointer may be NULL).  k = *k_done of that solve.
+ *   H  (k+1) x k FP64 column-major, W k x k FP64 column-major, beta 1 FP64,
+ *   L  n x k basis (FP64 for LSLU_F64, FP32 otherwise), column-major,
+ *   D  m x (k+1) basis, column-major.
+ * Errors: LSLU_ERR_INVALID_ARG if no solve has run. */
+lslu_status lslu_get_state(lslu_handle h, int32_t ptr_location, double* H, double* W,
+                           double* beta, void* L, void* D);
+
+/* One sparse product on the device (the first step of each half of an
+ * Algorithm 4 iteration): y = A x (transpose = 0; x length n, y length m) or
+ * y = A^T x (transpose = 1; x length m, y length n).  x and y are device
+ * pointers of the basis type (FP64 for LSLU_F64, FP32 otherwise).  Launched
+ * on the handle's stream without synchronising. */
+lslu_status lslu_spmv(lslu_handle h, int32_t transpose, const void* x, void* y);
+
+/* Solve the projected problem of Eq. (TSP) for one upper Hessenberg
+ * H ((k+1) x k, FP64, column-major with leading dimension ldh >= k+1) and
+ * beta, on the device, with the lambda rule of lslu_solve (m is the row
+ * count used by LSLU_LAMBDA_WGCV for omega = (k+1)/m).  Outputs (any may be
+ * NULL): y (k), sigma (k, descending singular values of H), c (k+1,
+ * beta U^T e1), lambda_out (1), resid_out (1, ||beta e1 - H y||).  Uses the
+ * handle's workspace; 1 <= k <= max_iter of the handle. */
+lslu_status lslu_projected(lslu_handle h, int32_t k, const double* H, int32_t ldh, double beta,
+                           int32_t rule, double lambda, int64_t m, int32_t ptr_location,
+                           double* y, double* sigma, double* c, double* lambda_out,
+                           double* resid_out);
+
+/* Per-kernel CUDA-event timing of later solves: enable != 0 records an
+ * event pair around every sparse product launched by lslu_solve.
+ * lslu_timing returns the number of such launches since the last reset and
+ * their summed duration in milliseconds, then resets the counters. */
+lslu_status lslu_profile(lslu_handle h, int32_t enable);
+lslu_status lslu_timing(lslu_handle h, int32_t* spmv_launches, double* spmv_ms);
+
+/* Number of kernel launches made by the last lslu_solve. */
+int64_t lslu_last_launch_count(lslu_handle h);
+
+/* One-line description of the last failure on h (h may be NULL for a failed
+ * lslu_create on this thread).  The string stays valid until the next call. */
+const char* lslu_error_string(lslu_handle h);
+
+/* Free everything the handle owns.  NULL is allowed. */
+void lslu_destroy(lslu_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LSLU_H */

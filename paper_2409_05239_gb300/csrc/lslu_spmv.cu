@@ -1,0 +1,237 @@
+// Sparse products of Algorithm 4: u = A l_k and q = A^T d_k.
+//
+// Both run on a row-major CSR: A^T is stored as its own (transposed) CSR, so
+// every output entry is one row dot product and no atomics are needed.  One
+// warp owns one row; lane j reads chunks j, j+32, ... of the row with 16-byte
+// vector loads (rows are padded to a multiple of kRowAlign entries), keeps a
+// private partial sum in chunk order and the warp adds the 32 partials with a
+// fixed butterfly, so results are bitwise reproducible run to run.
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "lslu_internal.cuh"
+
+namespace lslu {
+
+namespace {
+
+template <typename VT>
+struct ValTraits;
+template <>
+struct ValTraits<double> {
+  static constexpr int kChunk = 4;  // entries per lane step
+};
+template <>
+struct ValTraits<float> {
+  static constexpr int kChunk = 4;
+};
+template <>
+struct ValTraits<__nv_bfloat16> {
+  static constexpr int kChunk = 8;
+};
+
+template <typename AT>
+__device__ __forceinline__ AT warp_sum(AT v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Loads kChunk values starting at p (16-byte aligned) as the accumulation type.
+template <typename AT>
+__device__ __forceinline__ void load_vals(const double* p, AT (&v)[4]) {
+  const double2 a = __ldg(reinterpret_cast<const double2*>(p));
+  const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+  v[0] = (AT)a.x; v[1] = (AT)a.y; v[2] = (AT)b.x; v[3] = (AT)b.y;
+}
+template <typename AT>
+__device__ __forceinline__ void load_vals(const float* p, AT (&v)[4]) {
+  const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+  v[0] = (AT)a.x; v[1] = (AT)a.y; v[2] = (AT)a.z; v[3] = (AT)a.w;
+}
+template <typename AT>
+__device__ __forceinline__ void load_vals(const __nv_bfloat16* p, AT (&v)[8]) {
+  const uint4 a = __ldg(reinterpret_cast<const uint4*>(p));
+  const uint32_t w[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    v[2 * i] = (AT)__uint_as_float(w[i] << 16);
+    v[2 * i + 1] = (AT)__uint_as_float(w[i] & 0xffff0000u);
+  }
+}
+
+template <typename VT, typename XT, typename YT>
+__global__ void __launch_bounds__(256) k_spmv(int64_t rows, const int32_t* __restrict__ rp,
+                                              const int32_t* __restrict__ rl,
+                                              const int32_t* __restrict__ col,
+                                              const VT* __restrict__ val, const XT* __restrict__ x,
+                                              YT* __restrict__ y) {
+  constexpr int C = ValTraits<VT>::kChunk;
+  const int lane = threadIdx.x & 31;
+  const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (row >= rows) return;
+  const int32_t start = __ldg(rp + row);
+  const int32_t len = __ldg(rl + row);
+  YT acc = 0;
+  for (int32_t e = lane * C; e < len; e += 32 * C) {
+    const int32_t base = start + e;
+    int32_t cidx[C];
+#pragma unroll
+    for (int i = 0; i < C; i += 4) {
+      const int4 c4 = __ldg(reinterpret_cast<const int4*>(col + base + i));
+      cidx[i] = c4.x; cidx[i + 1] = c4.y; cidx[i + 2] = c4.z; cidx[i + 3] = c4.w;
+    }
+    YT v[C];
+    load_vals<YT>(val + base, v);
+#pragma unroll
+    for (int i = 0; i < C; ++i) acc = fma(v[i], (YT)__ldg(x + cidx[i]), acc);
+  }
+  acc = warp_sum(acc);
+  if (lane == 0) y[row] = acc;
+}
+
+template <typename VT, typename XT, typename YT>
+void spmv_typed(const DevCsr& A, const XT* x, YT* y, cudaStream_t s) {
+  if (A.rows == 0) return;
+  const int wpb = 8;
+  const int64_t blocks = (A.rows + wpb - 1) / wpb;
+  k_spmv<VT, XT, YT><<<(unsigned)blocks, wpb * 32, 0, s>>>(
+      A.rows, A.row_ptr, A.row_len, A.col, reinterpret_cast<const VT*>(A.val), x, y);
+}
+
+uint16_t f32_to_bf16_rne(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  const uint32_t lsb = (u >> 16) & 1u;
+  return (uint16_t)((u + 0x7fffu + lsb) >> 16);
+}
+
+// Host-side construction of the padded CSR (values converted to the storage
+// type): rows start on multiples of kRowAlign; pad entries repeat the last
+// column of their row with value 0.
+cudaError_t upload_padded(int64_t rows, int64_t cols, const std::vector<int64_t>& rp,
+                          const std::vector<int32_t>& ci, const std::vector<double>& vv, int vt,
+                          DevCsr* out, cudaStream_t s) {
+  std::vector<int32_t> prp(rows + 1), prl(rows);
+  int64_t tot = 0;
+  for (int64_t r = 0; r < rows; ++r) {
+    const int64_t len = rp[r + 1] - rp[r];
+    const int64_t plen = (len + kRowAlign - 1) / kRowAlign * kRowAlign;
+    prp[r] = (int32_t)tot;
+    prl[r] = (int32_t)plen;
+    tot += plen;
+    if (tot >= (int64_t)INT32_MAX) return cudaErrorInvalidValue;
+  }
+  prp[rows] = (int32_t)tot;
+  std::vector<int32_t> pc((size_t)tot);
+  std::vector<double> pv((size_t)tot);
+  for (int64_t r = 0; r < rows; ++r) {
+    const int64_t a = rp[r], len = rp[r + 1] - rp[r];
+    int32_t* dc = pc.data() + prp[r];
+    double* dv = pv.data() + prp[r];
+    for (int64_t e = 0; e < len; ++e) {
+      dc[e] = ci[a + e];
+      dv[e] = vv[a + e];
+    }
+    for (int64_t e = len; e < prl[r]; ++e) {
+      dc[e] = len ? ci[a + len - 1] : 0;
+      dv[e] = 0.0;
+    }
+  }
+  out->rows = rows;
+  out->cols = cols;
+  out->nnz = rp[rows];
+  out->nnz_padded = tot;
+  size_t vbytes = vt == LSLU_F64 ? 8 : (vt == LSLU_F32 ? 4 : 2);
+  cudaError_t e;
+  if ((e = cudaMalloc(&out->row_ptr, (rows + 1) * sizeof(int32_t))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&out->row_len, std::max<int64_t>(rows, 1) * sizeof(int32_t))) != cudaSuccess)
+    return e;
+  if ((e = cudaMalloc(&out->col, std::max<int64_t>(tot, kRowAlign) * sizeof(int32_t))) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaMalloc(&out->val, std::max<int64_t>(tot, kRowAlign) * vbytes)) != cudaSuccess)
+    return e;
+  if ((e = cudaMemcpyAsync(out->row_ptr, prp.data(), (rows + 1) * sizeof(int32_t),
+                           cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return e;
+  if (rows && (e = cudaMemcpyAsync(out->row_len, prl.data(), rows * sizeof(int32_t),
+                                   cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return e;
+  if (tot && (e = cudaMemcpyAsync(out->col, pc.data(), tot * sizeof(int32_t),
+                                  cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return e;
+  if (tot) {
+    if (vt == LSLU_F64) {
+      e = cudaMemcpyAsync(out->val, pv.data(), tot * 8, cudaMemcpyHostToDevice, s);
+    } else if (vt == LSLU_F32) {
+      std::vector<float> f((size_t)tot);
+      for (int64_t i = 0; i < tot; ++i) f[i] = (float)pv[i];
+      e = cudaMemcpyAsync(out->val, f.data(), tot * 4, cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    } else {
+      std::vector<uint16_t> h((size_t)tot);
+      for (int64_t i = 0; i < tot; ++i) h[i] = f32_to_bf16_rne((float)pv[i]);
+      e = cudaMemcpyAsync(out->val, h.data(), tot * 2, cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
+    if (e != cudaSuccess) return e;
+  }
+  return cudaStreamSynchronize(s);
+}
+
+}  // namespace
+
+cudaError_t build_csr_pair(int64_t m, int64_t n, const int64_t* rp, const int32_t* ci,
+                           const double* vv, int vt, DevCsr* A, DevCsr* AT, cudaStream_t s) {
+  const int64_t nnz = rp[m];
+  std::vector<int64_t> rpa(rp, rp + m + 1);
+  std::vector<int32_t> cia(ci, ci + nnz);
+  std::vector<double> va(vv, vv + nnz);
+  cudaError_t e = upload_padded(m, n, rpa, cia, va, vt, A, s);
+  if (e != cudaSuccess) return e;
+  // stable counting sort by column: rows of A^T list the rows of A in
+  // increasing order (entries of one row of A keep their input order)
+  std::vector<int64_t> rpt(n + 1, 0);
+  for (int64_t i = 0; i < nnz; ++i) rpt[cia[i] + 1]++;
+  for (int64_t c = 0; c < n; ++c) rpt[c + 1] += rpt[c];
+  std::vector<int64_t> cur(rpt.begin(), rpt.end() - 1);
+  std::vector<int32_t> cit((size_t)nnz);
+  std::vector<double> vt_((size_t)nnz);
+  for (int64_t r = 0; r < m; ++r)
+    for (int64_t i = rpa[r]; i < rpa[r + 1]; ++i) {
+      const int64_t pos = cur[cia[i]]++;
+      cit[pos] = (int32_t)r;
+      vt_[pos] = va[i];
+    }
+  return upload_padded(n, m, rpt, cit, vt_, vt, AT, s);
+}
+
+void free_csr(DevCsr* c) {
+  cudaFree(c->row_ptr);
+  cudaFree(c->row_len);
+  cudaFree(c->col);
+  cudaFree(c->val);
+  *c = DevCsr();
+}
+
+template <typename XT, typename YT>
+void launch_spmv(const DevCsr& A, int vt, const XT* x, YT* y, cudaStream_t s, int) {
+  if (vt == LSLU_F64)
+    spmv_typed<double, XT, YT>(A, x, y, s);
+  else if (vt == LSLU_F32)
+    spmv_typed<float, XT, YT>(A, x, y, s);
+  else
+    spmv_typed<__nv_bfloat16, XT, YT>(A, x, y, s);
+}
+
+template void launch_spmv<double, double>(const DevCsr&, int, const double*, double*,
+                                          cudaStream_t, int);
+template void launch_spmv<float, float>(const DevCsr&, int, const float*, float*, cudaStream_t,
+                                        int);
+
+}  // namespace lslu

@@ -1,0 +1,205 @@
+"""ctypes binding of the LSLU C ABI (include/lslu.h).
+
+Argument marshalling only: every step of the solve runs in the CUDA library.
+Importing this module never compiles anything; it raises if the library has
+not been built (paper_2409_05239_gb300.build.build()).  Host arrays are numpy
+arrays; device buffers are torch CUDA tensors (only their data pointers are
+passed to the library).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "liblslu.so")
+
+OK, ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_TIMEOUT = 0, 1, 2, 3, 4
+BREAKDOWN_BETA, BREAKDOWN_W, BREAKDOWN_H, ERR_NONFINITE = 5, 6, 7, 8
+BREAKDOWNS = (BREAKDOWN_BETA, BREAKDOWN_W, BREAKDOWN_H)
+VALUE_TYPES = {"f64": 0, "f32": 1, "bf16": 2}
+RULES = {"none": 0, "fixed": 1, "gcv": 2, "wgcv": 3}
+HOST, DEVICE = 0, 1
+
+EXPORTS = ("lslu_create", "lslu_solve", "lslu_get_state", "lslu_spmv", "lslu_projected",
+           "lslu_profile", "lslu_timing", "lslu_last_launch_count", "lslu_error_string",
+           "lslu_destroy")
+
+_lib = None
+
+
+class LsluError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"lslu status {status}: {msg}")
+        self.status = status
+
+
+def load(path: str | None = None):
+    """Load the shared library (once) and declare the C signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"CUDA library not built: {p} is missing "
+                           "(run paper_2409_05239_gb300.build.build())")
+    lib = ctypes.CDLL(p)
+    vp, i32, i64, f64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    lib.lslu_create.argtypes = [i64, i64, i64, vp, vp, vp, i32, i32, i32, vp, ctypes.POINTER(vp)]
+    lib.lslu_create.restype = i32
+    lib.lslu_solve.argtypes = [vp, vp, vp, i32, i32, f64, i32, vp, vp, vp, vp, vp, vp]
+    lib.lslu_solve.restype = i32
+    lib.lslu_get_state.argtypes = [vp, i32, vp, vp, vp, vp, vp]
+    lib.lslu_get_state.restype = i32
+    lib.lslu_spmv.argtypes = [vp, i32, vp, vp]
+    lib.lslu_spmv.restype = i32
+    lib.lslu_projected.argtypes = [vp, i32, vp, i32, f64, i32, f64, i64, i32, vp, vp, vp, vp, vp]
+    lib.lslu_projected.restype = i32
+    lib.lslu_profile.argtypes = [vp, i32]
+    lib.lslu_profile.restype = i32
+    lib.lslu_timing.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(f64)]
+    lib.lslu_timing.restype = i32
+    lib.lslu_last_launch_count.argtypes = [vp]
+    lib.lslu_last_launch_count.restype = i64
+    lib.lslu_error_string.argtypes = [vp]
+    lib.lslu_error_string.restype = ctypes.c_char_p
+    lib.lslu_destroy.argtypes = [vp]
+    lib.lslu_destroy.restype = None
+    _lib = lib
+    return lib
+
+
+def _ptr(a):
+    """Address of a numpy array or torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"] or a.flags["F_CONTIGUOUS"]
+        return a.ctypes.data
+    return a.data_ptr()  # torch tensor
+
+
+class Solver:
+    """One LSLU handle on the current CUDA device.
+
+    value_type: 'f64' (FP64 basis and accumulation), 'f32' or 'bf16' (A's
+    values stored in that type, FP32 basis and accumulation).
+    """
+
+    def __init__(self, m, n, row_ptr, col_idx, vals, value_type="f32", max_iter=300,
+                 stream=None):
+        self.lib = load()
+        self.m, self.n = int(m), int(n)
+        self.value_type = value_type
+        self.max_iter = int(max_iter)
+        self.basis_dtype = np.float64 if value_type == "f64" else np.float32
+        on_dev = not isinstance(row_ptr, np.ndarray)
+        if not on_dev:
+            row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+            col_idx = np.ascontiguousarray(col_idx, dtype=np.int32)
+            vals = np.ascontiguousarray(vals, dtype=np.float64)
+        nnz = int(row_ptr[-1]) if not on_dev else int(row_ptr[-1].item())
+        h = ctypes.c_void_p()
+        st = self.lib.lslu_create(self.m, self.n, nnz, _ptr(row_ptr), _ptr(col_idx), _ptr(vals),
+                                  VALUE_TYPES[value_type], self.max_iter,
+                                  DEVICE if on_dev else HOST, stream, ctypes.byref(h))
+        if st != OK:
+            raise LsluError(st, self.lib.lslu_error_string(None).decode())
+        self.h = h
+
+    def _check(self, st, allow_breakdown=False):
+        if st == OK or (allow_breakdown and st in BREAKDOWNS):
+            return st
+        raise LsluError(st, self.lib.lslu_error_string(self.h).decode())
+
+    def solve(self, b, K, rule="gcv", lam=0.0, x0=None, histories=False):
+        """Host arrays in and out.  Returns a dict with x, pivots, histories,
+        k_done and status (a breakdown is reported, not raised)."""
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        x0 = None if x0 is None else np.ascontiguousarray(x0, dtype=np.float64)
+        x = np.zeros(self.n)
+        gp = np.zeros(K, dtype=np.int32)
+        tp = np.zeros(K + 1, dtype=np.int32)
+        lh = np.zeros(K) if histories else None
+        rh = np.zeros(K) if histories else None
+        kd = ctypes.c_int32(0)
+        st = self.lib.lslu_solve(self.h, _ptr(b), _ptr(x0), int(K), RULES[rule], float(lam), HOST,
+                                 _ptr(x), _ptr(gp), _ptr(tp), _ptr(lh), _ptr(rh),
+                                 ctypes.addressof(kd))
+        self._check(st, allow_breakdown=True)
+        return dict(x=x, gp=gp, tp=tp, lam_hist=lh, res_hist=rh, k_done=kd.value, status=st)
+
+    def solve_device(self, b, x_out, K, rule="gcv", lam=0.0, x0=None, gp=None, tp=None,
+                     lam_hist=None, res_hist=None, k_done=None):
+        """Device buffers (torch tensors) in and out; returns the status."""
+        st = self.lib.lslu_solve(self.h, _ptr(b), _ptr(x0), int(K), RULES[rule], float(lam),
+                                 DEVICE, _ptr(x_out), _ptr(gp), _ptr(tp), _ptr(lam_hist),
+                                 _ptr(res_hist), _ptr(k_done))
+        return self._check(st, allow_breakdown=True)
+
+    def state(self, k):
+        """H, W, beta, L, D of the last solve (host copies); k = its k_done."""
+        H = np.zeros((k, k + 1)) if k else np.zeros((0, 1))
+        W = np.zeros((k, k))
+        beta = np.zeros(1)
+        L = np.zeros((k, self.n), dtype=self.basis_dtype)
+        D = np.zeros((k + 1, self.m), dtype=self.basis_dtype)
+        st = self.lib.lslu_get_state(self.h, HOST, _ptr(H), _ptr(W), _ptr(beta), _ptr(L), _ptr(D))
+        self._check(st)
+        return dict(H=H.T.copy(), W=W.T.copy(), beta=float(beta[0]), L=L.T.copy(), D=D.T.copy())
+
+    def spmv(self, transpose, x, y):
+        """y = A x or y = A^T x on device tensors of the basis type."""
+        self._check(self.lib.lslu_spmv(self.h, int(transpose), _ptr(x), _ptr(y)))
+
+    def projected(self, H, beta, rule="gcv", lam=0.0, m=None):
+        """Projected solve of Eq. (TSP) on the device for a host H ((k+1) x k)."""
+        H = np.asfortranarray(H, dtype=np.float64)
+        k = H.shape[1]
+        y = np.zeros(k)
+        sig = np.zeros(k)
+        c = np.zeros(k + 1)
+        lo = np.zeros(1)
+        ro = np.zeros(1)
+        st = self.lib.lslu_projected(self.h, k, _ptr(H), k + 1, float(beta), RULES[rule],
+                                     float(lam), int(m or self.m), HOST, _ptr(y), _ptr(sig),
+                                     _ptr(c), _ptr(lo), _ptr(ro))
+        self._check(st)
+        return dict(y=y, sigma=sig, c=c, lam=float(lo[0]), resid=float(ro[0]))
+
+    def profile(self, enable=True):
+        self._check(self.lib.lslu_profile(self.h, int(enable)))
+
+    def timing(self):
+        n = ctypes.c_int32(0)
+        ms = ctypes.c_double(0.0)
+        self._check(self.lib.lslu_timing(self.h, ctypes.byref(n), ctypes.byref(ms)))
+        return n.value, ms.value
+
+    def last_launch_count(self):
+        return int(self.lib.lslu_last_launch_count(self.h))
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.lib.lslu_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def from_problem(P, value_type="f32", max_iter=300):
+    """Solver for a tomography problem (paper_2409_05239_gb300.tomo.TomoProblem)."""
+    return Solver(P.m, P.n, P.row_ptr, P.col_idx, P.vals, value_type=value_type,
+                  max_iter=max_iter)

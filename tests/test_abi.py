@@ -1,0 +1,91 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point
+that include/lslu.h declares (no GPU needed)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_2409_05239_gb300 import build as B
+from paper_2409_05239_gb300 import lslu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    syms = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", f)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            syms |= set(re.findall(r"\b(lslu_[a-z_0-9]+)\s*\(", src))
+    return syms
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return lslu.load()
+
+
+def test_header_declares_entry_points():
+    syms = declared_symbols()
+    assert {"lslu_create", "lslu_solve", "lslu_destroy", "lslu_error_string"} <= syms
+    assert syms == set(lslu.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for s in declared_symbols():
+        assert hasattr(lib, s), f"{s} not exported"
+    out = subprocess.run(["nm", "-D", "--defined-only", B.LIB], capture_output=True, text=True)
+    exported = set(re.findall(r"\bT (lslu_\w+)", out.stdout))
+    assert declared_symbols() <= exported
+
+
+def test_library_is_sm103a(lib):
+    out = subprocess.run(["cuobjdump", "--list-elf", B.LIB], capture_output=True, text=True)
+    assert "sm_103a" in out.stdout
+
+
+def test_create_rejects_bad_arguments_without_gpu(lib):
+    """Argument checks run before any CUDA call."""
+    h = ctypes.c_void_p()
+    import numpy as np
+
+    rp = np.array([0, 1, 2], dtype=np.int64)
+    ci = np.array([0, 5], dtype=np.int32)  # column 5 out of range for n = 2
+    v = np.array([1.0, 2.0])
+    st = lib.lslu_create(2, 2, 2, rp.ctypes.data, ci.ctypes.data, v.ctypes.data, 1, 10, 0, None,
+                         ctypes.byref(h))
+    assert st == lslu.ERR_INVALID_ARG and not h.value
+    assert b"column index" in lib.lslu_error_string(None)
+    ci = np.array([0, 1], dtype=np.int32)
+    rp_bad = np.array([0, 2, 1], dtype=np.int64)
+    st = lib.lslu_create(2, 2, 1, rp_bad.ctypes.data, ci.ctypes.data, v.ctypes.data, 1, 10, 0,
+                         None, ctypes.byref(h))
+    assert st == lslu.ERR_INVALID_ARG
+    st = lib.lslu_create(2, 2, 2, rp.ctypes.data, ci.ctypes.data, v.ctypes.data, 1, 0, 0, None,
+                         ctypes.byref(h))
+    assert st == lslu.ERR_INVALID_ARG
+    vn = np.array([1.0, np.nan])
+    st = lib.lslu_create(2, 2, 2, rp.ctypes.data, ci.ctypes.data, vn.ctypes.data, 1, 10, 0, None,
+                         ctypes.byref(h))
+    assert st == lslu.ERR_INVALID_ARG and b"non-finite" in lib.lslu_error_string(None)
+
+
+def test_null_handle_calls_fail_cleanly(lib):
+    assert lib.lslu_solve(None, None, None, 1, 2, 0.0, 0, None, None, None, None, None,
+                          None) == lslu.ERR_INVALID_ARG
+    assert lib.lslu_last_launch_count(None) == 0
+    lib.lslu_destroy(None)
+
+
+def test_binding_fails_loudly_without_library(tmp_path):
+    with pytest.raises(RuntimeError, match="not built"):
+        saved = lslu._lib
+        lslu._lib = None
+        try:
+            lslu.load(str(tmp_path / "missing.so"))
+        finally:
+            lslu._lib = saved
