@@ -1,0 +1,331 @@
+"""Benchmark: Hybrid LSLU iterations/s on the 512x512 parallel-beam CT workload.
+
+One step = one complete Hybrid LSLU solve (K = 300 iterations of the basis
+loop of Algorithm 5, GCV lambda on the projected problem, x_K = L_K y) on a
+seeded synthetic problem that stands in for a tomography test problem:
+512x512 image (n = 262144), 360 angles x 724 rays (m = 260640), Siddon
+ray-pixel lengths (~120M non-zeros), 20-ellipse phantom, 0.5% noise.
+A's values are stored in FP32 (default) with FP32 accumulation and FP32 basis
+vectors; H, W, the projected solve, lambda and x are FP64.
+
+Contract: `python bench.py --gpus N --steps K --warmup W` prints ONE JSON line.
+Under torchrun (N > 1) every rank runs an independent replica (the solve of
+one problem does not shard); value = all ranks' iterations / max time.
+`--impl reference` times the FP64 CPU oracle instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+os.environ.setdefault("OMP_NUM_THREADS", "1")
+os.environ.setdefault("MKL_NUM_THREADS", "1")
+
+import numpy as np  # noqa: E402
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2409_05239_gb300 import tomo  # noqa: E402
+
+METRIC = "Hybrid LSLU iterations/s, 512x512 parallel-beam CT (K=300, GCV)"
+WORKLOAD = "ct512"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    p.add_argument("--workload", default=WORKLOAD, choices=sorted(tomo.CONFIGS))
+    p.add_argument("--value-type", default="f32", choices=["f32", "bf16", "f64"])
+    p.add_argument("--K", type=int, default=None)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-extras", action="store_true", help="skip the precision study")
+    p.add_argument("--cpu-sample-s", type=float, default=15.0)
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def spmv_bytes(P, value_type):
+    """Algorithmic bytes of one sparse product (either direction, averaged):
+    values + column indices + row pointers + output + input vector."""
+    sv = {"f64": 8, "f32": 4, "bf16": 2}[value_type]
+    sb = 8 if value_type == "f64" else 4
+    a = P.nnz * (sv + 4) + (P.m + 1) * 4 + P.m * sb + P.n * sb
+    at = P.nnz * (sv + 4) + (P.n + 1) * 4 + P.n * sb + P.m * sb
+    return 0.5 * (a + at)
+
+
+def solve_bytes(P, value_type, K):
+    """Algorithmic HBM bytes of one K-iteration solve (basis loop + recombine)."""
+    sb = 8 if value_type == "f64" else 4
+    per_iter_spmv = 2 * spmv_bytes(P, value_type)
+    # elimination reads k (resp. k+1) basis columns, plus the new vector read,
+    # scaled basis column written, and the scale pass (read v, write b)
+    elim = 0
+    for k in range(K):
+        elim += (P.n * k + P.m * (k + 1)) * sb + 4 * (P.n + P.m) * sb
+    recombine = P.n * K * sb + P.n * 8
+    return K * per_iter_spmv + elim + recombine
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(P, K, sample_s):
+    """The FP64 oracle as it stands on a bounded sample of the workload: the
+    first k_s iterations of the same solve, k_s chosen to take ~sample_s."""
+    import oracle.lslu_oracle as O
+
+    A = P.scipy()
+    t0 = time.perf_counter()
+    O.hybrid_lslu(A, P.b, None, 2, "gcv", histories=False)
+    t_probe = time.perf_counter() - t0
+    ks = int(max(2, min(K, 2 * sample_s / max(t_probe, 1e-3))))
+    t0 = time.perf_counter()
+    O.hybrid_lslu(A, P.b, None, ks, "gcv", histories=False)
+    dt = time.perf_counter() - t0
+    return {"value": ks / dt, "unit": "iter/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {ks} of {K} iterations of the same solve (FP64 numpy/scipy, "
+                      f"1 thread), {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    cfg = tomo.CONFIGS[args.workload]
+    K = args.K or cfg["K"]
+    P = tomo.make_config(args.workload)
+    import oracle.lslu_oracle as O
+
+    A = P.scipy()
+    t0 = time.perf_counter()
+    O.hybrid_lslu(A, P.b, None, 2, "gcv", histories=False)
+    t_probe = time.perf_counter() - t0
+    # each step: a bounded sample of the same solve, sized so the whole run
+    # stays within a few minutes
+    ks = int(max(2, min(K, (120.0 / max(1, args.steps + args.warmup)) / max(t_probe / 2, 1e-3))))
+    for _ in range(args.warmup):
+        O.hybrid_lslu(A, P.b, None, ks, "gcv", histories=False)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.hybrid_lslu(A, P.b, None, ks, "gcv", histories=False)
+    dt = time.perf_counter() - t0
+    v = ks * args.steps / dt
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "iter/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"{args.workload} (m={P.m}, n={P.n}, nnz={P.nnz})",
+                   "iterations_per_step": ks},
+        "cpu_baseline": {"value": v, "unit": "iter/s", "cores": 1, "kind": "oracle",
+                         "sample": f"first {ks} of {K} iterations per step"},
+        "e2e": {"value": v, "unit": "iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2409_05239_gb300 import build, lslu
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build.build()
+    cfg = tomo.CONFIGS[args.workload]
+    K = args.K or cfg["K"]
+    P = tomo.make_problem(cfg["N"], cfg["n_ang"], cfg["p"], cfg["n_ellipses"], cfg["etas"][0],
+                          seed=1000 * cfg["config"] + rank)
+    stream = torch.cuda.current_stream(dev)
+    solver = lslu.Solver(P.m, P.n, P.row_ptr, P.col_idx, P.vals, args.value_type, K,
+                         stream=stream.cuda_stream)
+    b_dev = torch.from_numpy(P.b).to(dev)
+    x_dev = torch.empty(P.n, dtype=torch.float64, device=dev)
+    rule = "gcv"
+
+    def step():
+        solver.solve_device(b_dev, x_dev, K, rule)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    solver.profile(True)
+    solver.timing()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    launches = 0
+    for _ in range(args.steps):
+        step()
+        launches += solver.last_launch_count()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    clocks = sampler.stop()
+    n_spmv, spmv_ms = solver.timing()
+    solver.profile(False)
+    ms_t = torch.tensor([ms], device=dev)
+    if world > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    total_iters = K * args.steps * world
+    value = total_iters / (ms_max / 1e3)
+
+    # end to end through the C ABI with host buffers (H2D of b, D2H of x)
+    b_host = torch.from_numpy(P.b).pin_memory()
+    x_host = torch.empty(P.n, dtype=torch.float64).pin_memory()
+
+    def step_host():
+        st = solver.lib.lslu_solve(solver.h, b_host.data_ptr(), None, K, lslu.RULES[rule], 0.0,
+                                   lslu.HOST, x_host.data_ptr(), None, None, None, None, None)
+        solver._check(st, allow_breakdown=True)
+
+    step_host()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step_host()
+    e2e_s = time.perf_counter() - t0
+    e2e_t = torch.tensor([e2e_s], device=dev)
+    if world > 1:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_value = total_iters / float(e2e_t.item())
+
+    out = None
+    if rank == 0:
+        x = x_dev.cpu().numpy()
+        rel_true = float(np.linalg.norm(x - P.x_true) / np.linalg.norm(P.x_true))
+        sbytes = spmv_bytes(P, args.value_type)
+        peaks = {}
+        try:
+            peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        except (OSError, ValueError):
+            pass
+        hbm = peaks.get("hbm_gbs", 6800.0)
+        avg_ms = spmv_ms / max(n_spmv, 1)
+        achieved = sbytes / (avg_ms * 1e-3) / 1e9 if n_spmv else None
+        total_bytes = solve_bytes(P, args.value_type, K)
+        out = {
+            "metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.value_type != "f64" else "f64", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {cfg['N']}x{cfg['N']} image, "
+                                   f"{cfg['n_ang']} angles x {cfg['p']} rays",
+                       "m": P.m, "n": P.n, "nnz": P.nnz, "K": K, "lambda_rule": rule,
+                       "A_values": args.value_type, "basis": "f64" if args.value_type == "f64"
+                       else "f32", "projected_solve": "f64",
+                       "l2": "inputs larger than L2 (CSR of A and A^T ~%.1f GB)" % (
+                           2 * P.nnz * 8 / 1e9)},
+            "roofline": {"bound": "hbm", "kernel": "csr_spmv (A l_k and A^T d_k)",
+                         "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm if achieved else None,
+                         "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
+                         "algorithmic_bytes_per_launch": sbytes, "launches": n_spmv,
+                         "avg_launch_ms": avg_ms, "traffic": None},
+            "hbm_gbs_solve": total_bytes * args.steps * world / (ms_max / 1e3) / 1e9,
+            "rel_err_x_true": rel_true,
+            "e2e": {"value": e2e_value, "unit": "iter/s", "h2d_bytes_per_step": P.m * 8,
+                    "d2h_bytes_per_step": P.n * 8},
+            "gpu_launches": launches,
+            "clocks": clocks,
+        }
+    solver.close()
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        out["cpu_baseline"] = cpu_baseline(P, K, args.cpu_sample_s)
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

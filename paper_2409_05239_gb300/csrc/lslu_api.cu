@@ -4,6 +4,7 @@
 
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -45,19 +46,22 @@ void destroy_ctx(lslu_ctx* c) {
   if (!c) return;
   free_csr(&c->A);
   free_csr(&c->AT);
-  void* ptrs[] = {c->L, c->D, c->H, c->W, c->TL, c->TD, c->gp, c->tp, c->gused, c->tused,
-                  c->q, c->u, c->r0, c->xin, c->coef, c->part_val, c->part_idx, c->st,
-                  c->pw.A, c->pw.Q, c->bw_A, c->bw_Q, c->proj_out, c->y, c->sig, c->cvec,
-                  c->xout};
+  if (c->proj_tstamp) cudaFree(c->proj_tstamp);
+  void* ptrs[] = {c->L, c->D, c->H, c->W, c->gp, c->tp, c->gused, c->tused,
+                  c->q, c->u, c->r0, c->xin, c->coef, c->xp, c->part_val, c->part_idx, c->st,
+                  c->TLi, c->TDi,
+                  c->pw_single, c->pw_batched, c->pw_offsets, c->proj_out, c->y, c->sig,
+                  c->cvec, c->xout};
   for (void* p : ptrs) cudaFree(p);
   if (c->st_host) cudaFreeHost(c->st_host);
+  for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->ev_in) cudaEventDestroy(c->ev_in);
+  if (c->ev_out) cudaEventDestroy(c->ev_out);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   delete c;
 }
 
-// Workspace of the projected kernel: problems of size kk use packed offsets.
-int64_t offA(int kk) { return (int64_t)(kk - 1) * kk * (kk + 1) / 3; }
-int64_t offQ(int kk) { return (int64_t)(kk - 1) * kk * (2 * kk - 1) / 6; }
 
 }  // namespace
 
@@ -139,15 +143,17 @@ extern "C" lslu_status lslu_create(int64_t m, int64_t n, int64_t nnz, const int6
                      c->stream));
   const int K = max_iter;
   const size_t bb = basis_bytes(value_type);
-  c->ldl = round_up(n, 64);
-  c->ldd = round_up(m, 64);
+  c->ldl = round_up(n, 128);  // whole 128-row tiles of the elimination kernel
+  c->ldd = round_up(m, 128);
   c->ldt = K + 1;
   CKC(cudaMalloc(&c->L, (size_t)c->ldl * K * bb));
   CKC(cudaMalloc(&c->D, (size_t)c->ldd * (K + 1) * bb));
+  CKC(cudaMemset(c->L, 0, (size_t)c->ldl * K * bb));
+  CKC(cudaMemset(c->D, 0, (size_t)c->ldd * (K + 1) * bb));
   CKC(dmalloc(&c->H, (size_t)(K + 1) * K));
   CKC(dmalloc(&c->W, (size_t)K * K));
-  CKC(dmalloc(&c->TL, (size_t)(K + 1) * (K + 1)));
-  CKC(dmalloc(&c->TD, (size_t)(K + 1) * (K + 1)));
+  CKC(cudaMalloc(&c->TLi, (size_t)(K + 1) * (K + 1) * bb));
+  CKC(cudaMalloc(&c->TDi, (size_t)(K + 1) * (K + 1) * bb));
   CKC(dmalloc(&c->gp, K));
   CKC(dmalloc(&c->tp, K + 1));
   CKC(dmalloc(&c->gused, n));
@@ -157,7 +163,8 @@ extern "C" lslu_status lslu_create(int64_t m, int64_t n, int64_t nnz, const int6
   CKC(dmalloc(&c->r0, m));
   CKC(dmalloc(&c->xin, m + n));
   CKC(dmalloc(&c->coef, K + 1));
-  c->part_cap = c->num_sms * 8;
+  CKC(cudaMalloc(&c->xp, (size_t)((K + 8) / 8 + 1) * (K + 1) * bb));
+  c->part_cap = c->num_sms * 16;
   CKC(dmalloc(&c->part_val, c->part_cap));
   CKC(dmalloc(&c->part_idx, c->part_cap));
   CKC(dmalloc(&c->st, 1));
@@ -166,14 +173,23 @@ extern "C" lslu_status lslu_create(int64_t m, int64_t n, int64_t nnz, const int6
   CKC(cudaMemset(c->st, 0, sizeof(DevState)));
   // projected workspace for the single final problem (k <= K); the batched
   // workspace for histories is allocated on first use
-  c->pw.nprob = 1;
-  CKC(dmalloc(&c->pw.A, (size_t)(K + 1) * K));
-  CKC(dmalloc(&c->pw.Q, (size_t)K * K));
+  c->pw_cluster = projected_cluster_size();
+  if (std::getenv("LSLU_PROJ_TIMING")) {
+    CKC(cudaMallocManaged(&c->proj_tstamp, 16 * sizeof(unsigned long long)));
+    std::memset(c->proj_tstamp, 0, 16 * sizeof(unsigned long long));
+  }
+  if (std::getenv("LSLU_VERBOSE"))
+    std::fprintf(stderr, "lslu: %d SMs, projected-solve cluster of %d CTAs\n", c->num_sms,
+                 c->pw_cluster);
+  CKC(dmalloc(&c->pw_single, (size_t)projected_slot_doubles(K, c->pw_cluster)));
   CKC(dmalloc(&c->proj_out, 2 * (size_t)K));
   CKC(dmalloc(&c->y, K));
   CKC(dmalloc(&c->sig, K));
   CKC(dmalloc(&c->cvec, K + 1));
   CKC(dmalloc(&c->xout, n));
+  CKC(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+  CKC(cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming));
+  CKC(cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming));
   CKC(cudaStreamSynchronize(c->stream));
 #undef CKC
   *out = c;
@@ -212,10 +228,12 @@ void collect_spmv_times(Ctx* c) {
   c->ev_used = 0;
 }
 
+// Enqueues one whole solve on stream s (no host synchronisation, capturable):
+// state reset, r0 and its pivot, K basis iterations, the projected problems
+// and x = x0 + L y.  Inputs are read from the handle's staging buffers.
 template <typename BT, typename CT>
-lslu_status solve_impl(Ctx* c, const double* db, const double* dx0, int K, int rule, double lam,
-                       bool hist) {
-  cudaStream_t s = c->stream;
+int64_t enqueue_solve(Ctx* c, cudaStream_t s, const double* db, const double* dx0, int K,
+                      int rule, double lam, bool hist) {
   const int64_t m = c->m, n = c->n;
   const int vt = c->value_type;
   BT* L = (BT*)c->L;
@@ -225,16 +243,12 @@ lslu_status solve_impl(Ctx* c, const double* db, const double* dx0, int K, int r
   const int64_t ldh = c->kmax + 1, ldw = c->kmax;
   int64_t launches = 0;
 
-  DevState init;
-  std::memset(&init, 0, sizeof(init));
-  init.status = LSLU_OK;
-  init.k_done = K;
-  *c->st_host = init;
-  CK(cudaMemcpyAsync(c->st, c->st_host, sizeof(DevState), cudaMemcpyHostToDevice, s));
-  CK(cudaMemsetAsync(c->gused, 0, n, s));
-  CK(cudaMemsetAsync(c->tused, 0, m, s));
-  CK(cudaMemsetAsync(c->gp, 0xff, sizeof(int32_t) * c->kmax, s));
-  CK(cudaMemsetAsync(c->tp, 0xff, sizeof(int32_t) * (c->kmax + 1), s));
+  launch_init_state(c->st, K, s);
+  cudaMemsetAsync(c->gused, 0, n, s);
+  cudaMemsetAsync(c->tused, 0, m, s);
+  cudaMemsetAsync(c->gp, 0xff, sizeof(int32_t) * c->kmax, s);
+  cudaMemsetAsync(c->tp, 0xff, sizeof(int32_t) * (c->kmax + 1), s);
+  launches += 1;
 
   // r0 = b - A x0
   if (dx0) {
@@ -247,44 +261,38 @@ lslu_status solve_impl(Ctx* c, const double* db, const double* dx0, int K, int r
   }
   // beta = signed max-abs entry of r0, d_1 = r0 / beta, t(1)
   {
-    PivotArgs pa{c->tp, 0, c->tused, nullptr, c->TD, c->ldt, LSLU_BREAKDOWN_BETA, 0, 1};
+    PivotArgs pa{c->tp, 0, c->tused, nullptr, c->ldt, LSLU_BREAKDOWN_BETA, 0, 1, c->TDi};
     launch_eliminate_argmax<double, BT, double>(c->r0, D, c->ldd, 0, c->coef, m, c->r0, pa,
                                                 c->part_val, c->part_idx, c->part_cap, c->st, s,
                                                 c->num_sms);
     launch_scale<double, BT>(c->r0, D, m, c->st, s, c->num_sms);
     launches += 2;
   }
-  const int xdbl = sizeof(CT) == 8;
   for (int k = 0; k < K; ++k) {
-    // q = A^T d_k; eliminate l_0..l_{k-1}; pivot; l_k
+    // q = A^T d_k (with the coefficients W(0:k, k) from its pivot rows);
+    // eliminate l_0..l_{k-1}; pivot; l_k
     cudaEvent_t e0;
+    PivotCoef pcw{c->gp, k, L, c->ldl, c->coef, c->W + k * ldw, c->xp, c->TLi, c->ldt, c->st, 0};
     record_spmv_start(c, &e0);
-    launch_spmv<BT, CT>(c->AT, vt, D + (int64_t)k * c->ldd, q, s, c->num_sms);
+    launch_spmv_pivots<BT, CT>(c->AT, vt, D + (int64_t)k * c->ldd, q, pcw, s);
     record_spmv_end(c, e0);
-    if (k > 0) {
-      launch_coefficients<BT>(q, xdbl, L, c->gp, k, c->TL, c->ldt, c->coef, c->W + k * ldw,
-                              c->st, s);
-      launches++;
-    }
-    PivotArgs paw{c->gp, k, c->gused, c->W + k + k * ldw, c->TL, c->ldt, LSLU_BREAKDOWN_W, k, 0};
+    PivotArgs paw{c->gp, k, c->gused, c->W + k + k * ldw, c->ldt, LSLU_BREAKDOWN_W, k, 0, c->TLi};
     launch_eliminate_argmax<CT, BT, CT>(q, L, c->ldl, k, c->coef, n, q, paw, c->part_val,
                                         c->part_idx, c->part_cap, c->st, s, c->num_sms);
     launch_scale<CT, BT>(q, L + (int64_t)k * c->ldl, n, c->st, s, c->num_sms);
-    // u = A l_k; eliminate d_0..d_k; pivot; d_{k+1}
+    // u = A l_k (with H(0:k+1, k)); eliminate d_0..d_k; pivot; d_{k+1}
+    PivotCoef pch{c->tp, k + 1, D, c->ldd, c->coef, c->H + k * ldh, c->xp, c->TDi, c->ldt, c->st,
+                  0};
     record_spmv_start(c, &e0);
-    launch_spmv<BT, CT>(c->A, vt, L + (int64_t)k * c->ldl, u, s, c->num_sms);
+    launch_spmv_pivots<BT, CT>(c->A, vt, L + (int64_t)k * c->ldl, u, pch, s);
     record_spmv_end(c, e0);
-    launch_coefficients<BT>(u, xdbl, D, c->tp, k + 1, c->TD, c->ldt, c->coef, c->H + k * ldh,
-                            c->st, s);
-    PivotArgs pah{c->tp, k + 1, c->tused, c->H + (k + 1) + k * ldh, c->TD, c->ldt,
-                  LSLU_BREAKDOWN_H, k, 0};
+    PivotArgs pah{c->tp, k + 1, c->tused, c->H + (k + 1) + k * ldh, c->ldt, LSLU_BREAKDOWN_H, k,
+                  0, c->TDi};
     launch_eliminate_argmax<CT, BT, CT>(u, D, c->ldd, k + 1, c->coef, m, u, pah, c->part_val,
                                         c->part_idx, c->part_cap, c->st, s, c->num_sms);
     launch_scale<CT, BT>(u, D + (int64_t)(k + 1) * c->ldd, m, c->st, s, c->num_sms);
-    launches += 7;
+    launches += 6;
   }
-  CK(cudaGetLastError());
-
   // projected problems: every k (histories) or only k = k_done
   ProjArgs pa;
   std::memset(&pa, 0, sizeof(pa));
@@ -301,32 +309,96 @@ lslu_status solve_impl(Ctx* c, const double* db, const double* dx0, int K, int r
   pa.lam_out = c->proj_out;
   pa.res_out = c->proj_out + c->kmax;
   pa.st = c->st;
+  pa.tstamp = c->proj_tstamp;
   ProjWork w;
+  w.cluster = c->pw_cluster;
   if (hist) {
-    if (c->bw_kmax < c->kmax) {
-      cudaFree(c->bw_A);
-      cudaFree(c->bw_Q);
-      c->bw_A = c->bw_Q = nullptr;
-      CK(dmalloc(&c->bw_A, (size_t)offA(c->kmax + 1)));
-      CK(dmalloc(&c->bw_Q, (size_t)offQ(c->kmax + 1)));
-      c->bw_kmax = c->kmax;
-    }
-    w.A = c->bw_A;
-    w.Q = c->bw_Q;
-    w.nprob = c->kmax;
+    w.base = c->pw_batched;
+    w.offsets = c->pw_offsets;
     w.packed = 1;
   } else {
-    w = c->pw;
+    w.base = c->pw_single;
     w.packed = 0;
   }
-  CK(launch_projected(pa, w, s));
+  launch_projected(pa, w, s);
   launch_recombine<BT>(L, c->ldl, c->y, dx0, c->xout, n, c->st, K, s, c->num_sms);
   launches += 2;
+  return launches;
+}
+
+lslu_status ensure_batched_workspace(Ctx* c) {
+  if (c->pw_batched) return LSLU_OK;
+  std::vector<int64_t> off(c->kmax + 2, 0);
+  for (int kk = 1; kk <= c->kmax; ++kk)
+    off[kk + 1] = off[kk] + projected_slot_doubles(kk, c->pw_cluster);
+  CK(dmalloc(&c->pw_batched, (size_t)off[c->kmax + 1]));
+  CK(dmalloc(&c->pw_offsets, off.size()));
+  CK(cudaMemcpy(c->pw_offsets, off.data(), off.size() * 8, cudaMemcpyHostToDevice));
+  return LSLU_OK;
+}
+
+template <typename BT, typename CT>
+lslu_status solve_impl(Ctx* c, const double* db, const double* dx0, int K, int rule, double lam,
+                       bool hist) {
+  if (hist) {
+    lslu_status st = ensure_batched_workspace(c);
+    if (st != LSLU_OK) return st;
+  }
+  cudaStream_t s = c->stream;
+  if (c->profile || !c->use_graphs) {
+    c->launches = enqueue_solve<BT, CT>(c, s, db, dx0, K, rule, lam, hist);
+    CK(cudaGetLastError());
+  } else {
+    const int has_x0 = dx0 != nullptr;
+    Ctx::GraphEntry* ge = nullptr;
+    for (auto& g : c->graphs)
+      if (g.K == K && g.rule == rule && g.hist == (int)hist && g.has_x0 == has_x0 &&
+          g.lam == lam)
+        ge = &g;
+    if (!ge) {
+      cudaGraph_t graph;
+      CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+      const int64_t nl = enqueue_solve<BT, CT>(c, c->cap_stream, db, dx0, K, rule, lam, hist);
+      cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_err(c, LSLU_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+      }
+      cudaGraphExec_t exec;
+      e = cudaGraphInstantiate(&exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess)
+        return set_err(c, LSLU_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+      if (c->graphs.size() >= 8) {
+        cudaGraphExecDestroy(c->graphs.front().exec);
+        c->graphs.erase(c->graphs.begin());
+      }
+      c->graphs.push_back({K, rule, (int)hist, has_x0, lam, exec, nl});
+      ge = &c->graphs.back();
+    }
+    CK(cudaEventRecord(c->ev_in, s));
+    CK(cudaStreamWaitEvent(c->cap_stream, c->ev_in, 0));
+    CK(cudaGraphLaunch(ge->exec, c->cap_stream));
+    CK(cudaEventRecord(c->ev_out, c->cap_stream));
+    CK(cudaStreamWaitEvent(s, c->ev_out, 0));
+    c->launches = ge->launches;
+  }
   CK(cudaMemcpyAsync(c->st_host, c->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   CK(cudaGetLastError());
-  c->launches = launches;
   if (c->profile) collect_spmv_times(c);
+  if (c->proj_tstamp) {
+    const unsigned long long* t = c->proj_tstamp;
+    std::fprintf(stderr,
+                 "lslu projected k=%d: bidiag %.1f us, sturm grid %.1f us, newton+weights %.1f us, "
+                 "lambda %.1f us, lsqr %.1f us, Q %.1f us\n",
+                 K, (t[1] - t[0]) * 1e-3, (t[2] - t[1]) * 1e-3, (t[3] - t[2]) * 1e-3,
+                 (t[4] - t[3]) * 1e-3, (t[6] - t[5]) * 1e-3, (t[7] - t[6]) * 1e-3);
+    std::fprintf(stderr,
+                 "  bidiag sections: norms %.1f, cluster syncs %.1f, right house+partials %.1f, "
+                 "right update + left house %.1f, left update %.1f us\n",
+                 t[8] * 1e-3, t[9] * 1e-3, t[10] * 1e-3, t[11] * 1e-3, t[12] * 1e-3);
+  }
   return LSLU_OK;
 }
 
@@ -349,17 +421,18 @@ extern "C" lslu_status lslu_solve(lslu_handle h, const double* b, const double* 
   const bool host = ptr_location == LSLU_HOST;
   const int64_t m = c->m, n = c->n;
   cudaStream_t s = c->stream;
-  const double* db = b;
-  const double* dx0 = x0;
-  if (host) {
+  // inputs are staged in the handle's buffers (captured solves read fixed
+  // addresses)
+  if (host)
     for (int64_t i = 0; i < m; ++i)
       if (!std::isfinite(b[i])) return set_err(c, LSLU_ERR_NONFINITE, "b has a non-finite entry");
-    CK(cudaMemcpyAsync(c->xin, b, m * 8, cudaMemcpyHostToDevice, s));
-    db = c->xin;
-    if (x0) {
-      CK(cudaMemcpyAsync(c->xin + m, x0, n * 8, cudaMemcpyHostToDevice, s));
-      dx0 = c->xin + m;
-    }
+  const cudaMemcpyKind h2d = host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  CK(cudaMemcpyAsync(c->xin, b, m * 8, h2d, s));
+  const double* db = c->xin;
+  const double* dx0 = nullptr;
+  if (x0) {
+    CK(cudaMemcpyAsync(c->xin + m, x0, n * 8, h2d, s));
+    dx0 = c->xin + m;
   }
   const bool hist = lambda_hist || resid_hist;
   const double lam = rule == LSLU_LAMBDA_FIXED ? lambda : 0.0;
@@ -508,8 +581,9 @@ extern "C" lslu_status lslu_projected(lslu_handle h, int32_t k, const double* H,
   pa.ldc = c->kmax + 1;
   pa.lam_out = c->proj_out;
   pa.res_out = c->proj_out + c->kmax;
-  ProjWork w = c->pw;
-  w.packed = 0;
+  ProjWork w;
+  w.base = c->pw_single;
+  w.cluster = c->pw_cluster;
   CK(launch_projected(pa, w, s));
   const cudaMemcpyKind kind =
       ptr_location == LSLU_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;

@@ -63,24 +63,46 @@ __device__ void block_argmax(double& v, int& i) {
   __syncthreads();
 }
 
-template <typename XT>
-__global__ void k_coefficients(const XT* __restrict__ x, const int32_t* __restrict__ piv, int cnt,
-                               const double* __restrict__ T, int64_t ldt, double* __restrict__ coef,
-                               double* __restrict__ hess_col, const DevState* st) {
-  extern __shared__ double r[];
-  if (st->status != LSLU_OK) return;
-  for (int i = threadIdx.x; i < cnt; i += blockDim.x) r[i] = (double)x[piv[i]];
-  for (int j = 0; j < cnt; ++j) {
-    __syncthreads();
-    const double cj = r[j];
-    for (int i = j + 1 + threadIdx.x; i < cnt; i += blockDim.x)
-      r[i] = fma(-T[i + j * ldt], cj, r[i]);
+// Tiles of rows x all basis columns: a tile of 32*VEC consecutive rows is read
+// by every warp of the block as 16-byte vectors (VEC rows per lane); warp w
+// takes the columns j = w, w+8, ...  The eight per-warp partial sums of each
+// row are combined in warp order, then subtracted from x.
+template <typename BT>
+struct Vec16;
+template <>
+struct Vec16<float> {
+  static constexpr int N = 4;
+  __device__ static void load(const float* p, float (&o)[4]) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
   }
-  __syncthreads();
-  for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
-    coef[i] = r[i];
-    if (hess_col) hess_col[i] = r[i];
+};
+template <>
+struct Vec16<double> {
+  static constexpr int N = 2;
+  __device__ static void load(const double* p, double (&o)[2]) {
+    const double2 v = __ldg(reinterpret_cast<const double2*>(p));
+    o[0] = v.x; o[1] = v.y;
   }
+};
+
+// Pivot search.  FP32 compute: each candidate becomes the 64-bit key
+// (bits of |v| << 32) | (2^32 - 1 - i), so one unsigned max gives the
+// largest |v| with ties to the lowest index (a NaN has larger bits than any
+// number and wins, so it is reported); blocks combine with one atomicMax.
+// FP64 compute: (|v|, i) pairs are reduced per block and the partials are
+// reduced in block order by the last block.
+__device__ __forceinline__ unsigned long long argkey(float a, int i) {
+  return ((unsigned long long)__float_as_uint(a) << 32) | (unsigned long long)(0xffffffffu - (unsigned)i);
+}
+
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long k) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long ok = __shfl_xor_sync(0xffffffffu, k, o);
+    k = ok > k ? ok : k;
+  }
+  return k;
 }
 
 template <typename XT, typename BT, typename CT>
@@ -89,90 +111,137 @@ __global__ void __launch_bounds__(kThreads)
                        const double* __restrict__ coef, int64_t rows, CT* v, PivotArgs pa,
                        double* __restrict__ part_val, int32_t* __restrict__ part_idx,
                        DevState* st) {
+  constexpr bool kKey = sizeof(CT) == 4;
+  constexpr int VEC = Vec16<BT>::N;
+  constexpr int TILE = 32 * VEC;
+  constexpr int NW = kThreads / 32;
   extern __shared__ unsigned char smem_raw[];
   CT* c = reinterpret_cast<CT*>(smem_raw);
+  __shared__ CT part[NW][TILE];
+  __shared__ unsigned long long kred[NW];
   __shared__ bool is_last;
   if (st->status != LSLU_OK) return;
   for (int j = threadIdx.x; j < cnt; j += blockDim.x) c[j] = (CT)coef[j];
   __syncthreads();
-
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t ntiles = (rows + TILE - 1) / TILE;
   double best = 0.0;
   int besti = -1;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < rows;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    CT acc = 0;
-    if (!pa.used[i]) {
-      acc = (CT)x[i];
-      const BT* bp = B + i;
-      int j = 0;
-      for (; j + 8 <= cnt; j += 8) {
-        BT b[8];
+  unsigned long long bkey = 0;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t r0 = t * TILE;
+    CT acc[VEC];
 #pragma unroll
-        for (int t = 0; t < 8; ++t) b[t] = __ldg(bp + (int64_t)(j + t) * ld);
+    for (int e = 0; e < VEC; ++e) acc[e] = 0;
+    const BT* bp = B + r0 + lane * VEC;
+    int j = warp;
+    for (; j + 7 * NW < cnt; j += 8 * NW) {
+      BT b[8][VEC];
 #pragma unroll
-        for (int t = 0; t < 8; ++t) acc = fma(-c[j + t], (CT)b[t], acc);
-      }
-      for (; j < cnt; ++j) acc = fma(-c[j], (CT)__ldg(bp + (int64_t)j * ld), acc);
-      double a = fabs((double)acc);
-      if (isnan(a)) a = INFINITY;  // a NaN must win so that it is reported
-      if (better(a, (int)i, best, besti)) {
-        best = a;
-        besti = (int)i;
+      for (int u = 0; u < 8; ++u) Vec16<BT>::load(bp + (int64_t)(j + u * NW) * ld, b[u]);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const CT cu = c[j + u * NW];
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) acc[e] = fma(cu, (CT)b[u][e], acc[e]);
       }
     }
-    v[i] = acc;
+    for (; j < cnt; j += NW) {
+      BT b0[VEC];
+      Vec16<BT>::load(bp + (int64_t)j * ld, b0);
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) acc[e] = fma(c[j], (CT)b0[e], acc[e]);
+    }
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) part[warp][lane * VEC + e] = acc[e];
+    __syncthreads();
+    if (threadIdx.x < TILE) {
+      const int64_t i = r0 + threadIdx.x;
+      if (i < rows) {
+        CT s = 0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) s += part[w][threadIdx.x];
+        CT val = 0;
+        if (!pa.used[i]) {
+          val = (CT)x[i] - s;
+          if constexpr (kKey) {
+            const unsigned long long kk = argkey(fabsf((float)val), (int)i);
+            bkey = kk > bkey ? kk : bkey;
+          } else {
+            double a = fabs((double)val);
+            if (isnan(a)) a = INFINITY;  // a NaN must win so that it is reported
+            if (better(a, (int)i, best, besti)) {
+              best = a;
+              besti = (int)i;
+            }
+          }
+        }
+        v[i] = val;
+      }
+    }
+    __syncthreads();
   }
-  block_argmax(best, besti);
-  if (threadIdx.x == 0) {
-    part_val[blockIdx.x] = best;
-    part_idx[blockIdx.x] = besti;
-    __threadfence();
-    const int t = atomicAdd(&st->ticket, 1);
-    is_last = (t == (int)gridDim.x - 1);
+  if constexpr (kKey) {
+    bkey = warp_max_u64(bkey);
+    if (lane == 0) kred[warp] = bkey;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned long long m = 0;
+      for (int w = 0; w < NW; ++w) m = kred[w] > m ? kred[w] : m;
+      if (m) atomicMax(&st->amax, m);
+      __threadfence();
+      is_last = (atomicAdd(&st->ticket, 1) == (int)gridDim.x - 1);
+    }
+  } else {
+    block_argmax(best, besti);
+    if (threadIdx.x == 0) {
+      part_val[blockIdx.x] = best;
+      part_idx[blockIdx.x] = besti;
+      __threadfence();
+      is_last = (atomicAdd(&st->ticket, 1) == (int)gridDim.x - 1);
+    }
   }
   __syncthreads();
   if (!is_last) return;
   __threadfence();
-  best = 0.0;
-  besti = -1;
-  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
-    const double pv = ((volatile double*)part_val)[b];
-    const int pi = ((volatile int32_t*)part_idx)[b];
-    if (better(pv, pi, best, besti)) {
-      best = pv;
-      besti = pi;
+  if constexpr (!kKey) {
+    best = 0.0;
+    besti = -1;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+      const double pv = __ldcg(part_val + b);
+      const int pi = __ldcg(part_idx + b);
+      if (better(pv, pi, best, besti)) {
+        best = pv;
+        besti = pi;
+      }
     }
+    block_argmax(best, besti);
   }
-  block_argmax(best, besti);
-  __shared__ double pval_s;
   if (threadIdx.x == 0) {
     st->ticket = 0;
+    if constexpr (kKey) {
+      const unsigned long long m = atomicExch(&st->amax, 0ull);
+      besti = m ? (int)(0xffffffffu - (unsigned)(m & 0xffffffffull)) : -1;
+      const float a = __uint_as_float((unsigned)(m >> 32));
+      best = (a != a) ? INFINITY : (double)a;
+    }
     if (besti < 0 || best == 0.0) {
       st->status = pa.breakdown_code;
       st->k_done = pa.k_on_breakdown;
-      pval_s = 0.0;
     } else if (!isfinite(best)) {
       st->status = LSLU_ERR_NONFINITE;
       st->k_done = pa.k_on_breakdown;
-      pval_s = 0.0;
     } else {
-      const CT pv = ((volatile CT*)v)[besti];
-      pval_s = (double)pv;
+      const CT pv = __ldcg(v + besti);
       st->pivot = (double)pv;
       st->pivot_f = (float)pv;
       pa.piv_list[pa.piv_slot] = besti;
       pa.used[besti] = 1;
       if (pa.hess_entry) *pa.hess_entry = (double)pv;
       if (pa.is_init) st->beta = (double)pv;
-      pa.T[pa.piv_slot + pa.piv_slot * pa.ldt] = 1.0;
+      reinterpret_cast<BT*>(pa.Tinv)[(int64_t)pa.piv_slot * pa.ldt + pa.piv_slot] = (BT)1;
     }
-    is_last = (pval_s != 0.0);
   }
-  __syncthreads();
-  if (!is_last) return;
-  // new row of T: entries of the earlier basis vectors at the new pivot row
-  for (int j = threadIdx.x; j < cnt; j += blockDim.x)
-    pa.T[pa.piv_slot + j * pa.ldt] = (double)B[besti + (int64_t)j * ld];
 }
 
 template <typename CT, typename BT>
@@ -183,6 +252,17 @@ __global__ void k_scale(const CT* __restrict__ v, BT* __restrict__ out, int64_t 
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < rows;
        i += (int64_t)gridDim.x * blockDim.x)
     out[i] = (BT)(v[i] / p);
+}
+
+__global__ void k_init_state(DevState* st, int K) {
+  st->status = LSLU_OK;
+  st->k_done = K;
+  st->ticket = 0;
+  st->ticket2 = 0;
+  st->beta = 0.0;
+  st->pivot = 0.0;
+  st->pivot_f = 0.0f;
+  st->amax = 0ull;
 }
 
 __global__ void k_residual0(const double* b, const double* Ax0, double* r0, int64_t m) {
@@ -218,30 +298,18 @@ int grid_for(int64_t rows, int num_sms, int per_sm) {
 
 }  // namespace
 
-template <typename BT>
-void launch_coefficients(const void* x, int x_is_double, const BT*, const int32_t* piv, int cnt,
-                         const double* T, int64_t ldt, double* coef, double* hess_col,
-                         DevState* st, cudaStream_t s) {
-  if (cnt == 0) return;
-  const size_t sm = (size_t)cnt * sizeof(double);
-  if (x_is_double)
-    k_coefficients<double><<<1, 256, sm, s>>>((const double*)x, piv, cnt, T, ldt, coef,
-                                               hess_col, st);
-  else
-    k_coefficients<float><<<1, 256, sm, s>>>((const float*)x, piv, cnt, T, ldt, coef, hess_col,
-                                              st);
-}
-
 template <typename XT, typename BT, typename CT>
 void launch_eliminate_argmax(const XT* x, const BT* B, int64_t ld, int cnt, const double* coef,
                              int64_t rows, CT* v, const PivotArgs& pa, double* part_val,
                              int32_t* part_idx, int part_cap, DevState* st, cudaStream_t s,
-                             int num_sms) {
-  int g = grid_for(rows, num_sms, 8);
+                             int) {
+  constexpr int TILE = 32 * Vec16<BT>::N;
+  int64_t g = (rows + TILE - 1) / TILE;
   if (g > part_cap) g = part_cap;
+  if (g < 1) g = 1;
   const size_t sm = (size_t)(cnt > 0 ? cnt : 1) * sizeof(CT);
-  k_eliminate_argmax<XT, BT, CT><<<g, kThreads, sm, s>>>(x, B, ld, cnt, coef, rows, v, pa,
-                                                         part_val, part_idx, st);
+  k_eliminate_argmax<XT, BT, CT><<<(unsigned)g, kThreads, sm, s>>>(x, B, ld, cnt, coef, rows, v,
+                                                                   pa, part_val, part_idx, st);
 }
 
 template <typename CT, typename BT>
@@ -249,6 +317,8 @@ void launch_scale(const CT* v, BT* out, int64_t rows, DevState* st, cudaStream_t
                   int num_sms) {
   k_scale<CT, BT><<<grid_for(rows, num_sms, 8), kThreads, 0, s>>>(v, out, rows, st);
 }
+
+void launch_init_state(DevState* st, int K, cudaStream_t s) { k_init_state<<<1, 1, 0, s>>>(st, K); }
 
 void launch_residual0(const double* b, const double* Ax0, double* r0, int64_t m,
                       cudaStream_t s) {
@@ -263,12 +333,6 @@ void launch_recombine(const BT* L, int64_t ldl, const double* y, const double* x
 }
 
 // explicit instantiations: FP64 mode (basis double) and FP32 mode (basis float)
-template void launch_coefficients<double>(const void*, int, const double*, const int32_t*, int,
-                                          const double*, int64_t, double*, double*, DevState*,
-                                          cudaStream_t);
-template void launch_coefficients<float>(const void*, int, const float*, const int32_t*, int,
-                                         const double*, int64_t, double*, double*, DevState*,
-                                         cudaStream_t);
 template void launch_eliminate_argmax<double, double, double>(
     const double*, const double*, int64_t, int, const double*, int64_t, double*,
     const PivotArgs&, double*, int32_t*, int, DevState*, cudaStream_t, int);

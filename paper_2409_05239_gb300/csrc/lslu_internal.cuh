@@ -35,19 +35,22 @@ struct DevState {
   int32_t status;   // lslu_status of the running solve
   int32_t k_done;   // completed iterations when status != OK
   int32_t ticket;   // block counter of the grid-wide argmax reduction
-  int32_t pad0;
+  int32_t ticket2;  // block counter of the pivot-row products
   double beta;      // signed max-abs entry of r0
   double pivot;     // value of the last pivot (FP64 copy)
   float pivot_f;    // same, FP32 copy for the FP32 scale kernel
   float pad1;
+  unsigned long long amax;  // running argmax key of the FP32 pivot search
 };
 
-// Work space of the projected-problem kernel for up to max_iter columns.
+// Work space of the projected-problem kernel (global memory): one slot per
+// problem; slot of problem size kk at base + offsets[kk] when packed.
 struct ProjWork {
-  double* A = nullptr;      // per problem: (k+1) x k copy of H (bidiagonalised in place)
-  double* Q = nullptr;      // per problem: right reflectors, k x k
-  int nprob = 0;
-  int packed = 0;  // 1: problem of size kk at packed offsets (histories)
+  double* base = nullptr;
+  const int64_t* offsets = nullptr;  // device table, kmax+2 entries (packed only)
+  int packed = 0;
+  int cluster = 1;       // CTAs per cluster
+  int slab_in_smem = 0;  // set by the launcher
 };
 
 struct Ctx {
@@ -65,8 +68,10 @@ struct Ctx {
   int64_t ldl = 0, ldd = 0;
   double* H = nullptr;   // (kmax+1) x kmax, ld = kmax+1
   double* W = nullptr;   // kmax x kmax, ld = kmax
-  double* TL = nullptr;  // pivot rows of L: TL[i + j*ldt] = l_j(g_i), ldt = kmax+1
-  double* TD = nullptr;  // pivot rows of D: TD[i + j*ldt] = d_j(t_i)
+  // inverses of the pivot-row matrices T_L(i,j) = l_j(g_i), T_D(i,j) = d_j(t_i),
+  // column-major, basis type, leading dimension ldt = kmax+1
+  void* TLi = nullptr;
+  void* TDi = nullptr;
   int64_t ldt = 0;
   int32_t* gp = nullptr;  // kmax
   int32_t* tp = nullptr;  // kmax+1
@@ -77,20 +82,35 @@ struct Ctx {
   double* r0 = nullptr;   // m, FP64
   double* xin = nullptr;  // max(m, n) FP64 staging for host inputs
   double* coef = nullptr; // kmax+1 elimination coefficients (FP64)
+  void* xp = nullptr;     // partial coefficient sums: ceil((kmax+1)/8) x ldt
   double* part_val = nullptr;  // argmax partials
   int32_t* part_idx = nullptr;
   int part_cap = 0;
   DevState* st = nullptr;
   DevState* st_host = nullptr;  // pinned mirror
-  ProjWork pw;              // one problem of size <= kmax
-  double* bw_A = nullptr;   // batched workspace (histories), allocated on first use
-  double* bw_Q = nullptr;
-  int bw_kmax = 0;
+  double* pw_single = nullptr;   // projected work space, one problem of size <= kmax
+  double* pw_batched = nullptr;  // all problem sizes 1..kmax (histories), on first use
+  int64_t* pw_offsets = nullptr; // device offset table of pw_batched
+  int pw_cluster = 1;
   double* proj_out = nullptr;  // per problem: lambda, resid (2 doubles)
   double* y = nullptr;         // kmax
   double* sig = nullptr;       // kmax per problem (histories)
   double* cvec = nullptr;      // (kmax+1) per problem
   double* xout = nullptr;      // n, FP64
+
+  // captured solves: one instantiated CUDA graph per (K, rule, lambda,
+  // histories, x0) and the stream they are launched on
+  struct GraphEntry {
+    int K, rule, hist, has_x0;
+    double lam;
+    cudaGraphExec_t exec;
+    int64_t launches;
+  };
+  std::vector<GraphEntry> graphs;
+  cudaStream_t cap_stream = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  bool use_graphs = true;
+  unsigned long long* proj_tstamp = nullptr;  // LSLU_PROJ_TIMING diagnostics
 
   int last_k = -1;  // k_done of the last solve, -1 if none
   int last_K = 0;
@@ -111,6 +131,25 @@ struct Ctx {
 template <typename XT, typename YT>
 void launch_spmv(const DevCsr& A, int vt, const XT* x, YT* y, cudaStream_t s, int num_sms);
 
+// Elimination coefficients computed inside the sparse product (see
+// k_spmv_pivots): cnt pivot rows piv, pivot-row matrix T.
+struct PivotCoef {
+  const int32_t* piv;
+  int cnt;
+  const void* B;     // the basis (basis type), leading dimension ldb: T(i,j) = B(piv_i, j)
+  int64_t ldb;
+  double* coef;      // cnt coefficients (FP64 copy)
+  double* hess_col;  // cnt Hessenberg entries of this column (W(:,k) or H(:,k))
+  void* xp;          // partial sums, npiv_blocks x ldi (accumulation type)
+  void* Tinv;        // column-major inverse of T (basis type = accumulation type), ld ldi
+  int64_t ldi;
+  DevState* st;
+  int npiv_blocks;   // set by the launcher
+};
+template <typename XT, typename YT>
+void launch_spmv_pivots(const DevCsr& A, int vt, const XT* x, YT* y, PivotCoef pc,
+                        cudaStream_t s);
+
 // Build the padded CSR of A and of A^T (host-side layout, then upload).
 cudaError_t build_csr_pair(int64_t m, int64_t n, const int64_t* rp, const int32_t* ci,
                            const double* vv, int vt, DevCsr* A, DevCsr* AT, cudaStream_t s);
@@ -122,17 +161,12 @@ struct PivotArgs {
   int piv_slot;          // index written in piv_list (== number of earlier vectors)
   uint8_t* used;         // pivoted-row mask
   double* hess_entry;    // where the pivot value goes (W(k,k) or H(k+1,k)); may be null
-  double* T;             // pivot-row matrix of this basis
-  int64_t ldt;
+  int64_t ldt;           // leading dimension of Tinv
   int breakdown_code;    // status to set when no non-zero candidate is left
   int k_on_breakdown;    // k_done to record on breakdown
   int is_init;           // 1 for the r0 pivot (records beta)
+  void* Tinv;            // inverse of T (basis type, row-major): its diagonal entry is set
 };
-
-template <typename BT>
-void launch_coefficients(const void* x, int x_is_double, const BT* basis_unused, const int32_t* piv,
-                         int cnt, const double* T, int64_t ldt, double* coef, double* hess_col,
-                         DevState* st, cudaStream_t s);
 
 template <typename XT, typename BT, typename CT>
 void launch_eliminate_argmax(const XT* x, const BT* B, int64_t ld, int cnt, const double* coef,
@@ -144,6 +178,7 @@ template <typename CT, typename BT>
 void launch_scale(const CT* v, BT* out, int64_t rows, DevState* st, cudaStream_t s, int num_sms);
 
 void launch_residual0(const double* b, const double* Ax0, double* r0, int64_t m, cudaStream_t s);
+void launch_init_state(DevState* st, int K, cudaStream_t s);
 
 // Projected problem (lslu_projected.cu).
 struct ProjArgs {
@@ -166,8 +201,11 @@ struct ProjArgs {
   double* res_out;  // per problem (may be null), index k-1
   const DevState* st;  // if non-null, problems with k > k_done are skipped and
                        // the y problem uses k = k_done
+  unsigned long long* tstamp;  // optional phase timestamps (ns) of the last problem
 };
 cudaError_t launch_projected(const ProjArgs& a, ProjWork& w, cudaStream_t s);
+int64_t projected_slot_doubles(int kk, int CL);
+int projected_cluster_size();
 
 template <typename BT>
 void launch_recombine(const BT* L, int64_t ldl, const double* y, const double* x0, double* x,

@@ -64,16 +64,16 @@ __device__ __forceinline__ void load_vals(const __nv_bfloat16* p, AT (&v)[8]) {
   }
 }
 
+// Dot product of one CSR row with x, computed by one warp (result in every
+// lane).  Lane l takes chunks l, l+32, ... in order; the 32 partial sums are
+// combined by a fixed butterfly, so a row always gets the same bits.
 template <typename VT, typename XT, typename YT>
-__global__ void __launch_bounds__(256) k_spmv(int64_t rows, const int32_t* __restrict__ rp,
-                                              const int32_t* __restrict__ rl,
-                                              const int32_t* __restrict__ col,
-                                              const VT* __restrict__ val, const XT* __restrict__ x,
-                                              YT* __restrict__ y) {
+__device__ __forceinline__ YT row_dot(int64_t row, const int32_t* __restrict__ rp,
+                                      const int32_t* __restrict__ rl,
+                                      const int32_t* __restrict__ col,
+                                      const VT* __restrict__ val, const XT* __restrict__ x,
+                                      int lane) {
   constexpr int C = ValTraits<VT>::kChunk;
-  const int lane = threadIdx.x & 31;
-  const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (row >= rows) return;
   const int32_t start = __ldg(rp + row);
   const int32_t len = __ldg(rl + row);
   YT acc = 0;
@@ -90,7 +90,98 @@ __global__ void __launch_bounds__(256) k_spmv(int64_t rows, const int32_t* __res
 #pragma unroll
     for (int i = 0; i < C; ++i) acc = fma(v[i], (YT)__ldg(x + cidx[i]), acc);
   }
-  acc = warp_sum(acc);
+  return warp_sum(acc);
+}
+
+template <typename VT, typename XT, typename YT>
+__global__ void __launch_bounds__(256) k_spmv(int64_t rows, const int32_t* __restrict__ rp,
+                                              const int32_t* __restrict__ rl,
+                                              const int32_t* __restrict__ col,
+                                              const VT* __restrict__ val, const XT* __restrict__ x,
+                                              YT* __restrict__ y) {
+  const int lane = threadIdx.x & 31;
+  const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (row >= rows) return;
+  const YT acc = row_dot<VT, XT, YT>(row, rp, rl, col, val, x, lane);
+  if (lane == 0) y[row] = acc;
+}
+
+// y = A x plus the elimination coefficients of the next Hessenberg step,
+// c = T^-1 y(piv), where T(i,j) = b_j(piv_i) is the unit lower triangular
+// pivot-row matrix of the basis b and T^-1 is kept explicitly (column-major,
+// accumulation type).  |T| <= 1 under max-abs pivoting keeps
+// T^-1 small and well conditioned, so every coefficient becomes a plain
+// dot product instead of a step of a sequential forward substitution.
+//
+// The first npiv blocks own the pivot columns, one warp per column j:
+//   a. completes the newest row of T^-1 in its column,
+//      Tinv(nr, j) = -sum_{l=j}^{nr-1} T(nr, l) Tinv(l, j),  nr = cnt-1;
+//   b. computes y(piv_j) with the same warp reduction as every other row
+//      (so the two agree bit for bit);
+//   c. the block adds Tinv(i, j) y(piv_j) over its 8 columns into a partial
+//      vector; the last pivot block to finish adds the partials in block order.
+// The remaining blocks compute the other rows of y meanwhile.
+template <typename VT, typename XT, typename YT>
+__global__ void __launch_bounds__(256) k_spmv_pivots(int64_t rows, const int32_t* __restrict__ rp,
+                                                     const int32_t* __restrict__ rl,
+                                                     const int32_t* __restrict__ col,
+                                                     const VT* __restrict__ val,
+                                                     const XT* __restrict__ x, YT* __restrict__ y,
+                                                     PivotCoef pc) {
+  __shared__ int last;
+  __shared__ YT xs[8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if ((int)blockIdx.x < pc.npiv_blocks) {
+    if (pc.st->status != LSLU_OK) return;
+    YT* Tinv = reinterpret_cast<YT*>(pc.Tinv);
+    YT* part = reinterpret_cast<YT*>(pc.xp);
+    const int cnt = pc.cnt, nr = cnt - 1;
+    const int j0 = blockIdx.x * 8;
+    const int j = j0 + warp;
+    if (j < cnt) {
+      if (j < nr) {
+        YT a = 0;
+        // T(nr, l) = b_l(piv_nr): the newest pivot row of the earlier basis vectors
+        const YT* brow = reinterpret_cast<const YT*>(pc.B) + pc.piv[nr];
+        const YT* tcol = Tinv + (int64_t)j * pc.ldi;
+        for (int l = j + lane; l < nr; l += 32)
+          a = fma(__ldcg(brow + (int64_t)l * pc.ldb), __ldcg(tcol + l), a);
+        a = warp_sum(a);
+        if (lane == 0) __stcg(Tinv + (int64_t)j * pc.ldi + nr, -a);
+      }
+      const YT yp = row_dot<VT, XT, YT>(pc.piv[j], rp, rl, col, val, x, lane);
+      if (lane == 0) xs[warp] = yp;
+    } else if (lane == 0) {
+      xs[warp] = 0;
+    }
+    __threadfence_block();
+    __syncthreads();
+    const int jn = min(8, cnt - j0);
+    for (int i = j0 + threadIdx.x; i < cnt; i += blockDim.x) {
+      YT acc = 0;
+      for (int w = 0; w < jn; ++w)
+        if (i >= j0 + w) acc = fma(__ldcg(Tinv + (int64_t)(j0 + w) * pc.ldi + i), xs[w], acc);
+      __stcg(part + (int64_t)blockIdx.x * pc.ldi + i, acc);
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = (atomicAdd(&pc.st->ticket2, 1) == pc.npiv_blocks - 1);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (threadIdx.x == 0) pc.st->ticket2 = 0;
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+      YT acc = 0;
+      const int bmax = i / 8;  // blocks whose columns start at or before row i
+      for (int bb = 0; bb <= bmax; ++bb) acc += __ldcg(part + (int64_t)bb * pc.ldi + i);
+      pc.coef[i] = (double)acc;
+      if (pc.hess_col) pc.hess_col[i] = (double)acc;
+    }
+    return;
+  }
+  const int64_t row = (int64_t)(blockIdx.x - pc.npiv_blocks) * 8 + warp;
+  if (row >= rows) return;
+  const YT acc = row_dot<VT, XT, YT>(row, rp, rl, col, val, x, lane);
   if (lane == 0) y[row] = acc;
 }
 
@@ -101,6 +192,13 @@ void spmv_typed(const DevCsr& A, const XT* x, YT* y, cudaStream_t s) {
   const int64_t blocks = (A.rows + wpb - 1) / wpb;
   k_spmv<VT, XT, YT><<<(unsigned)blocks, wpb * 32, 0, s>>>(
       A.rows, A.row_ptr, A.row_len, A.col, reinterpret_cast<const VT*>(A.val), x, y);
+}
+
+template <typename VT, typename XT, typename YT>
+void spmv_pivots_typed(const DevCsr& A, const XT* x, YT* y, const PivotCoef& pc, cudaStream_t s) {
+  const int64_t blocks = pc.npiv_blocks + (A.rows + 7) / 8;
+  k_spmv_pivots<VT, XT, YT><<<(unsigned)blocks, 256, 0, s>>>(
+      A.rows, A.row_ptr, A.row_len, A.col, reinterpret_cast<const VT*>(A.val), x, y, pc);
 }
 
 uint16_t f32_to_bf16_rne(float f) {
@@ -229,9 +327,25 @@ void launch_spmv(const DevCsr& A, int vt, const XT* x, YT* y, cudaStream_t s, in
     spmv_typed<__nv_bfloat16, XT, YT>(A, x, y, s);
 }
 
+template <typename XT, typename YT>
+void launch_spmv_pivots(const DevCsr& A, int vt, const XT* x, YT* y, PivotCoef pc,
+                        cudaStream_t s) {
+  pc.npiv_blocks = (pc.cnt + 7) / 8;
+  if (vt == LSLU_F64)
+    spmv_pivots_typed<double, XT, YT>(A, x, y, pc, s);
+  else if (vt == LSLU_F32)
+    spmv_pivots_typed<float, XT, YT>(A, x, y, pc, s);
+  else
+    spmv_pivots_typed<__nv_bfloat16, XT, YT>(A, x, y, pc, s);
+}
+
 template void launch_spmv<double, double>(const DevCsr&, int, const double*, double*,
                                           cudaStream_t, int);
 template void launch_spmv<float, float>(const DevCsr&, int, const float*, float*, cudaStream_t,
                                         int);
+template void launch_spmv_pivots<double, double>(const DevCsr&, int, const double*, double*,
+                                                 PivotCoef, cudaStream_t);
+template void launch_spmv_pivots<float, float>(const DevCsr&, int, const float*, float*,
+                                               PivotCoef, cudaStream_t);
 
 }  // namespace lslu

@@ -156,3 +156,17 @@ def test_nonfinite_b_rejected(ct32):
     with lslu.from_problem(ct32, "f64", 5) as s:
         with pytest.raises(lslu.LsluError):
             s.solve(b, 5, "gcv")
+
+
+def test_graph_replay_matches_direct_launches(ct32):
+    """Solves replayed from the captured CUDA graph equal direct launches
+    (profiling mode launches kernel by kernel) bit for bit."""
+    with lslu.from_problem(ct32, "f32", 40) as s:
+        a = s.solve(ct32.b, 40, "gcv")
+        b = s.solve(ct32.b, 40, "gcv")  # graph replay
+        s.profile(True)
+        c = s.solve(ct32.b, 40, "gcv")
+        s.profile(False)
+        n, ms = s.timing()
+    assert np.array_equal(a["x"], b["x"]) and np.array_equal(a["x"], c["x"])
+    assert np.array_equal(a["gp"], c["gp"]) and n == 80 and ms > 0
