@@ -174,6 +174,9 @@ extern "C" lslu_status lslu_create(int64_t m, int64_t n, int64_t nnz, const int6
   // projected workspace for the single final problem (k <= K); the batched
   // workspace for histories is allocated on first use
   c->pw_cluster = projected_cluster_size();
+  // LSLU_NO_GRAPHS=1: launch every kernel directly instead of replaying
+  // captured graphs (for kernel-level profilers)
+  if (const char* ng = std::getenv("LSLU_NO_GRAPHS")) c->use_graphs = ng[0] == '0';
   if (std::getenv("LSLU_PROJ_TIMING")) {
     CKC(cudaMallocManaged(&c->proj_tstamp, 16 * sizeof(unsigned long long)));
     std::memset(c->proj_tstamp, 0, 16 * sizeof(unsigned long long));
@@ -198,34 +201,43 @@ extern "C" lslu_status lslu_create(int64_t m, int64_t n, int64_t nnz, const int6
 
 namespace {
 
-void record_spmv_start(Ctx* c, cudaEvent_t* e0) {
+// CUDA-event timing of the sparse products (lslu_profile).  Inside a stream
+// capture the events become external event-record nodes of the graph, so a
+// profiled solve replays the same graph of kernels.
+void ensure_events(Ctx* c, int need) {
+  while ((int)c->ev_pool.size() < need) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    c->ev_pool.push_back(e);
+  }
+}
+void record_event(Ctx* c, cudaStream_t s, bool capturing, cudaEvent_t e) {
+  if (capturing)
+    cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+  else
+    cudaEventRecord(e, s);
+}
+void record_spmv_start(Ctx* c, cudaStream_t s, bool capturing, cudaEvent_t* e0) {
   *e0 = nullptr;
   if (!c->profile) return;
-  if (c->ev_used + 2 > (int)c->ev_pool.size()) {
-    for (int i = 0; i < 64; ++i) {
-      cudaEvent_t e;
-      cudaEventCreate(&e);
-      c->ev_pool.push_back(e);
-    }
-  }
+  ensure_events(c, c->ev_used + 2);
   *e0 = c->ev_pool[c->ev_used];
-  cudaEventRecord(*e0, c->stream);
+  record_event(c, s, capturing, *e0);
 }
-void record_spmv_end(Ctx* c, cudaEvent_t e0) {
+void record_spmv_end(Ctx* c, cudaStream_t s, bool capturing, cudaEvent_t e0) {
   if (!e0) return;
-  cudaEvent_t e1 = c->ev_pool[c->ev_used + 1];
-  cudaEventRecord(e1, c->stream);
+  record_event(c, s, capturing, c->ev_pool[c->ev_used + 1]);
   c->ev_used += 2;
 }
-void collect_spmv_times(Ctx* c) {
-  for (int i = 0; i + 1 < c->ev_used; i += 2) {
+void collect_spmv_times(Ctx* c, int pairs) {
+  for (int i = 0; i < pairs; ++i) {
     float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, c->ev_pool[i], c->ev_pool[i + 1]) == cudaSuccess) {
+    if (cudaEventElapsedTime(&ms, c->ev_pool[2 * i], c->ev_pool[2 * i + 1]) == cudaSuccess) {
       c->prof_ms += ms;
       c->prof_launches += 1;
     }
   }
-  c->ev_used = 0;
+  cudaGetLastError();
 }
 
 // Enqueues one whole solve on stream s (no host synchronisation, capturable):
@@ -233,7 +245,8 @@ void collect_spmv_times(Ctx* c) {
 // and x = x0 + L y.  Inputs are read from the handle's staging buffers.
 template <typename BT, typename CT>
 int64_t enqueue_solve(Ctx* c, cudaStream_t s, const double* db, const double* dx0, int K,
-                      int rule, double lam, bool hist) {
+                      int rule, double lam, bool hist, bool capturing) {
+  c->ev_used = 0;
   const int64_t m = c->m, n = c->n;
   const int vt = c->value_type;
   BT* L = (BT*)c->L;
@@ -273,9 +286,9 @@ int64_t enqueue_solve(Ctx* c, cudaStream_t s, const double* db, const double* dx
     // eliminate l_0..l_{k-1}; pivot; l_k
     cudaEvent_t e0;
     PivotCoef pcw{c->gp, k, L, c->ldl, c->coef, c->W + k * ldw, c->xp, c->TLi, c->ldt, c->st, 0};
-    record_spmv_start(c, &e0);
+    record_spmv_start(c, s, capturing, &e0);
     launch_spmv_pivots<BT, CT>(c->AT, vt, D + (int64_t)k * c->ldd, q, pcw, s);
-    record_spmv_end(c, e0);
+    record_spmv_end(c, s, capturing, e0);
     PivotArgs paw{c->gp, k, c->gused, c->W + k + k * ldw, c->ldt, LSLU_BREAKDOWN_W, k, 0, c->TLi};
     launch_eliminate_argmax<CT, BT, CT>(q, L, c->ldl, k, c->coef, n, q, paw, c->part_val,
                                         c->part_idx, c->part_cap, c->st, s, c->num_sms);
@@ -283,9 +296,9 @@ int64_t enqueue_solve(Ctx* c, cudaStream_t s, const double* db, const double* dx
     // u = A l_k (with H(0:k+1, k)); eliminate d_0..d_k; pivot; d_{k+1}
     PivotCoef pch{c->tp, k + 1, D, c->ldd, c->coef, c->H + k * ldh, c->xp, c->TDi, c->ldt, c->st,
                   0};
-    record_spmv_start(c, &e0);
+    record_spmv_start(c, s, capturing, &e0);
     launch_spmv_pivots<BT, CT>(c->A, vt, L + (int64_t)k * c->ldl, u, pch, s);
-    record_spmv_end(c, e0);
+    record_spmv_end(c, s, capturing, e0);
     PivotArgs pah{c->tp, k + 1, c->tused, c->H + (k + 1) + k * ldh, c->ldt, LSLU_BREAKDOWN_H, k,
                   0, c->TDi};
     launch_eliminate_argmax<CT, BT, CT>(u, D, c->ldd, k + 1, c->coef, m, u, pah, c->part_val,
@@ -345,20 +358,26 @@ lslu_status solve_impl(Ctx* c, const double* db, const double* dx0, int K, int r
     if (st != LSLU_OK) return st;
   }
   cudaStream_t s = c->stream;
-  if (c->profile || !c->use_graphs) {
-    c->launches = enqueue_solve<BT, CT>(c, s, db, dx0, K, rule, lam, hist);
+  int ev_pairs = 0;
+  if (c->profile) ensure_events(c, 4 * K + 8);
+  if (!c->use_graphs) {
+    c->launches = enqueue_solve<BT, CT>(c, s, db, dx0, K, rule, lam, hist, false);
+    ev_pairs = c->ev_used / 2;
     CK(cudaGetLastError());
   } else {
     const int has_x0 = dx0 != nullptr;
+    const int prof = c->profile ? 1 : 0;
     Ctx::GraphEntry* ge = nullptr;
     for (auto& g : c->graphs)
       if (g.K == K && g.rule == rule && g.hist == (int)hist && g.has_x0 == has_x0 &&
-          g.lam == lam)
+          g.lam == lam && g.prof == prof)
         ge = &g;
     if (!ge) {
       cudaGraph_t graph;
       CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
-      const int64_t nl = enqueue_solve<BT, CT>(c, c->cap_stream, db, dx0, K, rule, lam, hist);
+      const int64_t nl =
+          enqueue_solve<BT, CT>(c, c->cap_stream, db, dx0, K, rule, lam, hist, true);
+      const int pairs = c->ev_used / 2;
       cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
       if (e != cudaSuccess) {
         cudaGetLastError();
@@ -373,7 +392,7 @@ lslu_status solve_impl(Ctx* c, const double* db, const double* dx0, int K, int r
         cudaGraphExecDestroy(c->graphs.front().exec);
         c->graphs.erase(c->graphs.begin());
       }
-      c->graphs.push_back({K, rule, (int)hist, has_x0, lam, exec, nl});
+      c->graphs.push_back({K, rule, (int)hist, has_x0, lam, exec, nl, prof, pairs});
       ge = &c->graphs.back();
     }
     CK(cudaEventRecord(c->ev_in, s));
@@ -382,11 +401,12 @@ lslu_status solve_impl(Ctx* c, const double* db, const double* dx0, int K, int r
     CK(cudaEventRecord(c->ev_out, c->cap_stream));
     CK(cudaStreamWaitEvent(s, c->ev_out, 0));
     c->launches = ge->launches;
+    ev_pairs = ge->ev_pairs;
   }
   CK(cudaMemcpyAsync(c->st_host, c->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   CK(cudaGetLastError());
-  if (c->profile) collect_spmv_times(c);
+  if (c->profile) collect_spmv_times(c, ev_pairs);
   if (c->proj_tstamp) {
     const unsigned long long* t = c->proj_tstamp;
     std::fprintf(stderr,

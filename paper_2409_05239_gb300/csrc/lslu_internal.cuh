@@ -105,6 +105,8 @@ struct Ctx {
     double lam;
     cudaGraphExec_t exec;
     int64_t launches;
+    int prof;      // 1: event-record nodes around every sparse product
+    int ev_pairs;  // number of such event pairs
   };
   std::vector<GraphEntry> graphs;
   cudaStream_t cap_stream = nullptr;

@@ -41,22 +41,38 @@ __device__ __forceinline__ AT warp_sum(AT v) {
   return v;
 }
 
-// Loads kChunk values starting at p (16-byte aligned) as the accumulation type.
-template <typename AT>
-__device__ __forceinline__ void load_vals(const double* p, AT (&v)[4]) {
-  const double2 a = __ldg(reinterpret_cast<const double2*>(p));
-  const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
-  v[0] = (AT)a.x; v[1] = (AT)a.y; v[2] = (AT)b.x; v[3] = (AT)b.y;
+// Matrix stream: 16-byte loads through the non-coherent path without L1
+// allocation (ld.global.nc.L1::no_allocate), so L1 keeps the gathered x.
+__device__ __forceinline__ int4 ld_stream(const int32_t* p) {
+  int4 c;
+  asm volatile("ld.global.nc.L1::no_allocate.v4.s32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(c.x), "=r"(c.y), "=r"(c.z), "=r"(c.w)
+               : "l"(p));
+  return c;
 }
 template <typename AT>
-__device__ __forceinline__ void load_vals(const float* p, AT (&v)[4]) {
-  const float4 a = __ldg(reinterpret_cast<const float4*>(p));
-  v[0] = (AT)a.x; v[1] = (AT)a.y; v[2] = (AT)a.z; v[3] = (AT)a.w;
+__device__ __forceinline__ void load_vals_cs(const double* p, AT (&v)[4]) {
+  double a0, a1, a2, a3;
+  asm volatile("ld.global.nc.L1::no_allocate.v2.f64 {%0,%1}, [%2];" : "=d"(a0), "=d"(a1) : "l"(p));
+  asm volatile("ld.global.nc.L1::no_allocate.v2.f64 {%0,%1}, [%2];"
+               : "=d"(a2), "=d"(a3)
+               : "l"(p + 2));
+  v[0] = (AT)a0; v[1] = (AT)a1; v[2] = (AT)a2; v[3] = (AT)a3;
 }
 template <typename AT>
-__device__ __forceinline__ void load_vals(const __nv_bfloat16* p, AT (&v)[8]) {
-  const uint4 a = __ldg(reinterpret_cast<const uint4*>(p));
-  const uint32_t w[4] = {a.x, a.y, a.z, a.w};
+__device__ __forceinline__ void load_vals_cs(const float* p, AT (&v)[4]) {
+  float a0, a1, a2, a3;
+  asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
+               : "=f"(a0), "=f"(a1), "=f"(a2), "=f"(a3)
+               : "l"(p));
+  v[0] = (AT)a0; v[1] = (AT)a1; v[2] = (AT)a2; v[3] = (AT)a3;
+}
+template <typename AT>
+__device__ __forceinline__ void load_vals_cs(const __nv_bfloat16* p, AT (&v)[8]) {
+  uint32_t w[4];
+  asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3])
+               : "l"(p));
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     v[2 * i] = (AT)__uint_as_float(w[i] << 16);
@@ -82,11 +98,11 @@ __device__ __forceinline__ YT row_dot(int64_t row, const int32_t* __restrict__ r
     int32_t cidx[C];
 #pragma unroll
     for (int i = 0; i < C; i += 4) {
-      const int4 c4 = __ldg(reinterpret_cast<const int4*>(col + base + i));
+      const int4 c4 = ld_stream(col + base + i);
       cidx[i] = c4.x; cidx[i + 1] = c4.y; cidx[i + 2] = c4.z; cidx[i + 3] = c4.w;
     }
     YT v[C];
-    load_vals<YT>(val + base, v);
+    load_vals_cs<YT>(val + base, v);
 #pragma unroll
     for (int i = 0; i < C; ++i) acc = fma(v[i], (YT)__ldg(x + cidx[i]), acc);
   }

@@ -158,9 +158,9 @@ def test_nonfinite_b_rejected(ct32):
             s.solve(b, 5, "gcv")
 
 
-def test_graph_replay_matches_direct_launches(ct32):
-    """Solves replayed from the captured CUDA graph equal direct launches
-    (profiling mode launches kernel by kernel) bit for bit."""
+def test_graph_replay_matches_direct_launches(ct32, monkeypatch):
+    """Solves replayed from the captured CUDA graph (with and without timing
+    events) equal kernel-by-kernel launches bit for bit."""
     with lslu.from_problem(ct32, "f32", 40) as s:
         a = s.solve(ct32.b, 40, "gcv")
         b = s.solve(ct32.b, 40, "gcv")  # graph replay
@@ -168,5 +168,9 @@ def test_graph_replay_matches_direct_launches(ct32):
         c = s.solve(ct32.b, 40, "gcv")
         s.profile(False)
         n, ms = s.timing()
+    monkeypatch.setenv("LSLU_NO_GRAPHS", "1")
+    with lslu.from_problem(ct32, "f32", 40) as s2:
+        d = s2.solve(ct32.b, 40, "gcv")
     assert np.array_equal(a["x"], b["x"]) and np.array_equal(a["x"], c["x"])
-    assert np.array_equal(a["gp"], c["gp"]) and n == 80 and ms > 0
+    assert np.array_equal(a["x"], d["x"]) and np.array_equal(a["gp"], d["gp"])
+    assert n == 80 and ms > 0
