@@ -127,6 +127,34 @@ lslu_status lslu_projected(lslu_handle h, int32_t k, const double* H, int32_t ld
                            double* y, double* sigma, double* c, double* lambda_out,
                            double* resid_out);
 
+/* Allocation-free variant of lslu_projected, for callers that cannot call
+ * cudaMalloc (for example code that runs under a framework whose memory pool
+ * must own every device allocation, or a time-critical loop that cannot
+ * afford an allocation's implicit synchronisation).  The paper has no
+ * counterpart: this is a deployment interface.
+ *   - Same problem and outputs as lslu_projected, but every pointer (H, y,
+ *     sigma, c, lambda_out, resid_out) is a device pointer, no handle is
+ *     needed, and the work runs asynchronously on cuda_stream (NULL = the
+ *     legacy default stream): the outputs are ready once that stream reaches
+ *     this point.  Any output pointer may be NULL.  c holds |beta U^T e1|.
+ *   - Work space: a fixed array of 1.12 MB of device memory that the library
+ *     reserves when it is loaded, on every GPU that loads it, until the
+ *     process exits.  It serves 1 <= k <= 256; larger k is rejected with
+ *     LSLU_ERR_INVALID_ARG and a message naming the limit.  Nothing else is
+ *     allocated.
+ *   - The first call on a device looks up the array's device address and
+ *     sets kernel attributes for that device; make it before any stream
+ *     capture.
+ *   - Every call shares the one array: calls whose work may overlap on the
+ *     GPU (other streams, other host threads) race and must be serialised by
+ *     the caller.  No part of the array needs to start at zero.
+ * Errors: LSLU_ERR_INVALID_ARG, LSLU_ERR_CUDA; lslu_error_string(NULL) has
+ * the message. */
+lslu_status lslu_projected_noalloc(int32_t k, const double* H, int32_t ldh, double beta,
+                                   int32_t rule, double lambda, int64_t m, double* y,
+                                   double* sigma, double* c, double* lambda_out,
+                                   double* resid_out, void* cuda_stream);
+
 /* Per-kernel CUDA-event timing of later solves: enable != 0 records an
  * event pair around every sparse product launched by lslu_solve.
  * lslu_timing returns the number of such launches since the last reset and

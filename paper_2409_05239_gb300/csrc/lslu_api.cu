@@ -14,14 +14,23 @@
 using namespace lslu;
 
 namespace {
+thread_local std::string g_create_err_store;
+}
 
-thread_local std::string g_create_err;
+namespace lslu {
+// Last failure of a call that has no handle (lslu_create, allocation-free
+// entry points); read by lslu_error_string(NULL).
+std::string& thread_error() { return g_create_err_store; }
+}  // namespace lslu
+
+namespace {
+
 
 lslu_status set_err(Ctx* c, lslu_status st, const std::string& msg) {
   if (c)
     c->err = msg;
   else
-    g_create_err = msg;
+    lslu::thread_error() = msg;
   return st;
 }
 
@@ -124,7 +133,7 @@ extern "C" lslu_status lslu_create(int64_t m, int64_t n, int64_t nnz, const int6
   c->stream = (cudaStream_t)cuda_stream;
   lslu_status st = LSLU_OK;
   auto fail = [&](lslu_status s2) {
-    g_create_err = c->err;
+    lslu::thread_error() = c->err;
     destroy_ctx(c);
     return s2;
   };
@@ -635,7 +644,7 @@ extern "C" lslu_status lslu_timing(lslu_handle h, int32_t* spmv_launches, double
 extern "C" int64_t lslu_last_launch_count(lslu_handle h) { return h ? h->launches : 0; }
 
 extern "C" const char* lslu_error_string(lslu_handle h) {
-  return h ? h->err.c_str() : g_create_err.c_str();
+  return h ? h->err.c_str() : lslu::thread_error().c_str();
 }
 
 extern "C" void lslu_destroy(lslu_handle h) {

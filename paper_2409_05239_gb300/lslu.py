@@ -24,8 +24,8 @@ RULES = {"none": 0, "fixed": 1, "gcv": 2, "wgcv": 3}
 HOST, DEVICE = 0, 1
 
 EXPORTS = ("lslu_create", "lslu_solve", "lslu_get_state", "lslu_spmv", "lslu_projected",
-           "lslu_profile", "lslu_timing", "lslu_last_launch_count", "lslu_error_string",
-           "lslu_destroy")
+           "lslu_projected_noalloc", "lslu_profile", "lslu_timing", "lslu_last_launch_count",
+           "lslu_error_string", "lslu_destroy")
 
 _lib = None
 
@@ -57,6 +57,9 @@ def load(path: str | None = None):
     lib.lslu_spmv.restype = i32
     lib.lslu_projected.argtypes = [vp, i32, vp, i32, f64, i32, f64, i64, i32, vp, vp, vp, vp, vp]
     lib.lslu_projected.restype = i32
+    lib.lslu_projected_noalloc.argtypes = [i32, vp, i32, f64, i32, f64, i64, vp, vp, vp, vp,
+                                           vp, vp]
+    lib.lslu_projected_noalloc.restype = i32
     lib.lslu_profile.argtypes = [vp, i32]
     lib.lslu_profile.restype = i32
     lib.lslu_timing.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(f64)]
@@ -197,6 +200,19 @@ class Solver:
 
     def __exit__(self, *a):
         self.close()
+
+
+def projected_noalloc(H, beta, rule, lam, m, y=None, sigma=None, c=None, lam_out=None,
+                      resid_out=None, stream=None):
+    """Allocation-free projected solve: H and every output are device tensors
+    (torch, FP64); asynchronous on stream.  Raises LsluError on failure."""
+    lib = load()
+    k = H.shape[1]
+    st = lib.lslu_projected_noalloc(k, _ptr(H), H.stride(1), float(beta), RULES[rule],
+                                    float(lam), int(m), _ptr(y), _ptr(sigma), _ptr(c),
+                                    _ptr(lam_out), _ptr(resid_out), stream)
+    if st != OK:
+        raise LsluError(st, lib.lslu_error_string(None).decode())
 
 
 def from_problem(P, value_type="f32", max_iter=300):
