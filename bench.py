@@ -155,6 +155,48 @@ def cpu_baseline(P, K, sample_s):
                       f"1 thread), {dt:.1f} s"}
 
 
+def precision_study(P, K, rule, dev, x_main, main_vt):
+    """Mixed precision against the FP64 GPU path on the same instance: A's
+    values in FP64 / FP32 / BF16 (FP64 or FP32 basis), throughput of the
+    whole solve and relative error of x_K against x_true and against the FP64
+    GPU result.  'equal_error' is true when the mixed path's error against
+    x_true is within 1% of the FP64 path's."""
+    import torch
+
+    from paper_2409_05239_gb300 import lslu
+
+    res = {}
+    xs = {main_vt: x_main}
+    b_dev = torch.from_numpy(P.b).to(dev)
+    x_dev = torch.empty(P.n, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for vt in ("f64", "f32", "bf16"):
+        s = lslu.Solver(P.m, P.n, P.row_ptr, P.col_idx, P.vals, vt, K, stream=stream.cuda_stream)
+        s.solve_device(b_dev, x_dev, K, rule)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        reps = 3
+        e0.record(stream)
+        for _ in range(reps):
+            s.solve_device(b_dev, x_dev, K, rule)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        xs[vt] = x_dev.cpu().numpy()
+        s.close()
+        res[vt] = {"iter_per_s": K / (ms / 1e3), "ms_per_solve": ms,
+                   "rel_err_x_true": float(np.linalg.norm(xs[vt] - P.x_true) /
+                                           np.linalg.norm(P.x_true))}
+    for vt in ("f32", "bf16"):
+        res[vt]["rel_diff_vs_f64_gpu"] = float(np.linalg.norm(xs[vt] - xs["f64"]) /
+                                               np.linalg.norm(xs["f64"]))
+        res[vt]["equal_error"] = bool(res[vt]["rel_err_x_true"] <=
+                                      1.01 * res["f64"]["rel_err_x_true"])
+        res[vt]["speedup_vs_f64"] = res[vt]["iter_per_s"] / res["f64"]["iter_per_s"]
+    return res
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -318,6 +360,8 @@ def run_gpu(args):
             "clocks": clocks,
         }
     solver.close()
+    if rank == 0 and not args.no_extras and world == 1:
+        out["precision_study"] = precision_study(P, K, rule, dev, x, args.value_type)
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         out["cpu_baseline"] = cpu_baseline(P, K, args.cpu_sample_s)
     if rank == 0:
