@@ -197,6 +197,73 @@ def precision_study(P, K, rule, dev, x_main, main_vt):
     return res
 
 
+def batched_study(dev, K=150, count=64):
+    """Batched solves: `count` independent problems of uneven size (image side
+    64..256, 30..180 angles, 1.41 N rays, own phantom and noise level in
+    [0.5%, 3%]) solved together by one launch sequence (FP32, GCV, K
+    iterations each), against the same problems solved one after another
+    with single-problem handles."""
+    import torch
+
+    from paper_2409_05239_gb300 import lslu
+
+    Ps = tomo.make_uneven_batch(count)
+    stream = torch.cuda.current_stream(dev)
+    b = np.concatenate([P.b for P in Ps])
+    b_dev = torch.from_numpy(b).to(dev)
+    x_dev = torch.empty(sum(P.n for P in Ps), dtype=torch.float64, device=dev)
+    kd_dev = torch.empty(count, dtype=torch.int32, device=dev)
+    bs = lslu.from_problems(Ps, "f32", K, stream=stream.cuda_stream)
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    ms_b = timed(lambda: bs.solve_device(b_dev, x_dev, K, "gcv", k_done=kd_dev), 3)
+    launches = bs.last_launch_count()
+    x = x_dev.cpu().numpy()
+    kd = kd_dev.cpu().numpy()
+    bs.close()
+    singles = [lslu.Solver(P.m, P.n, P.row_ptr, P.col_idx, P.vals, "f32", K,
+                           stream=stream.cuda_stream) for P in Ps]
+    bd = [torch.from_numpy(P.b).to(dev) for P in Ps]
+    xd = [torch.empty(P.n, dtype=torch.float64, device=dev) for P in Ps]
+
+    def seq():
+        for s, bb, xx in zip(singles, bd, xd):
+            s.solve_device(bb, xx, K, "gcv")
+
+    ms_s = timed(seq, 2)
+    same = all(np.array_equal(xd[p].cpu().numpy(), x[off:off + P.n])
+               for p, (P, off) in enumerate(zip(Ps, np.cumsum([0] + [P.n for P in Ps]))))
+    for s in singles:
+        s.close()
+    iters = int(kd.sum())
+    errs = []
+    off = 0
+    for P in Ps:
+        errs.append(np.linalg.norm(x[off:off + P.n] - P.x_true) / np.linalg.norm(P.x_true))
+        off += P.n
+    nbytes = sum(solve_bytes(P, "f32", K) for P in Ps)
+    return {"problems": count, "K": K, "m_total": int(sum(P.m for P in Ps)),
+            "n_total": int(sum(P.n for P in Ps)), "nnz_total": int(sum(P.nnz for P in Ps)),
+            "ms_per_batch_solve": ms_b, "problem_iter_per_s": iters / (ms_b / 1e3),
+            "hbm_gbs_solve": nbytes / (ms_b * 1e-3) / 1e9,
+            "kernel_launches_per_batch_solve": launches,
+            "sequential_single_ms": ms_s, "speedup_vs_sequential": ms_s / ms_b,
+            "identical_to_single_solves": bool(same),
+            "rel_err_x_true_median": float(np.median(errs)),
+            "rel_err_x_true_max": float(np.max(errs))}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -248,7 +315,7 @@ def run_gpu(args):
     cfg = tomo.CONFIGS[args.workload]
     K = args.K or cfg["K"]
     P = tomo.make_problem(cfg["N"], cfg["n_ang"], cfg["p"], cfg["n_ellipses"], cfg["etas"][0],
-                          seed=1000 * cfg["config"] + rank)
+                          seed=cfg["seed_base"] + rank)
     stream = torch.cuda.current_stream(dev)
     solver = lslu.Solver(P.m, P.n, P.row_ptr, P.col_idx, P.vals, args.value_type, K,
                          stream=stream.cuda_stream)
@@ -362,6 +429,8 @@ def run_gpu(args):
     solver.close()
     if rank == 0 and not args.no_extras and world == 1:
         out["precision_study"] = precision_study(P, K, rule, dev, x, args.value_type)
+    if rank == 0 and not args.no_extras and world == 1:
+        out["batched_study"] = batched_study(dev)
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         out["cpu_baseline"] = cpu_baseline(P, K, args.cpu_sample_s)
     if rank == 0:

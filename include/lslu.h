@@ -99,12 +99,52 @@ lslu_status lslu_solve(lslu_handle h, const double* b, const double* x0, int32_t
                        int32_t* col_pivots, int32_t* row_pivots, double* lambda_hist,
                        double* resid_hist, int32_t* k_done);
 
+/* Batched Hybrid LSLU (Algorithm 5 run independently on nprob problems that
+ * share one launch sequence).  Problem p owns rows row_off[p] .. row_off[p+1]-1
+ * and columns col_off[p] .. col_off[p+1]-1 of one block-diagonal CSR matrix
+ * (row_ptr: row_off[nprob]+1 int64 offsets; col_idx: int32; vals: FP64; every
+ * entry of a row of problem p must lie in problem p's column range).  All
+ * arrays are host memory; row_off and col_off have nprob+1 entries, start at
+ * 0 and are strictly increasing.  Values are stored as value_type, which must
+ * be LSLU_F32 or LSLU_BF16 (the basis is FP32).  Internally every problem
+ * starts on a 128-row boundary of the concatenated row and column spaces, so
+ * each tile of the elimination kernels belongs to one problem; the padding
+ * rows are masked out of every pivot search.
+ * Errors: LSLU_ERR_INVALID_ARG (nprob < 1, bad offsets, a problem with no row
+ * or column, an entry outside its block, a non-finite value, FP64 values,
+ * max_iter outside [1, 2048]); LSLU_ERR_OOM; LSLU_ERR_CUDA. */
+lslu_status lslu_create_batched(int32_t nprob, const int64_t* row_off, const int64_t* col_off,
+                                const int64_t* row_ptr, const int32_t* col_idx,
+                                const double* vals, int32_t value_type, int32_t max_iter,
+                                void* cuda_stream, lslu_handle* out);
+
+/* K iterations of Hybrid LSLU on every problem of a batched handle, from
+ * x0 = 0.  b has row_off[nprob] FP64 entries (problem p's data at
+ * row_off[p]); rule and lambda as in lslu_solve (the same rule for every
+ * problem; lambda_k is chosen per problem, and LSLU_LAMBDA_WGCV uses each
+ * problem's own row count).  Outputs (host or device per ptr_location; all
+ * but x_out may be NULL):
+ *   x_out       col_off[nprob]  FP64  x of every problem at its k_done
+ *   col_pivots  nprob x K       int32 g of problem p at p*K, indices local to
+ *                                     the problem, -1 past its k_done
+ *   row_pivots  nprob x (K+1)   int32 t, same layout with stride K+1
+ *   k_done      nprob           int32 completed iterations per problem
+ *   status      nprob           int32 lslu_status of each problem (OK or a
+ *                                     LSLU_BREAKDOWN_* code)
+ * A breakdown stops only its own problem.  The call returns LSLU_OK unless an
+ * argument is invalid or CUDA fails; 1 <= K <= max_iter. */
+lslu_status lslu_solve_batched(lslu_handle h, const double* b, int32_t K, int32_t rule,
+                               double lambda, int32_t ptr_location, double* x_out,
+                               int32_t* col_pivots, int32_t* row_pivots, int32_t* k_done,
+                               int32_t* status);
+
 /* Copy the state of the last lslu_solve (host or device per ptr_location;
  * any pointer may be NULL).  k = *k_done of that solve.
  *   H  (k+1) x k FP64 column-major, W k x k FP64 column-major, beta 1 FP64,
  *   L  n x k basis (FP64 for LSLU_F64, FP32 otherwise), column-major,
  *   D  m x (k+1) basis, column-major.
- * Errors: LSLU_ERR_INVALID_ARG if no solve has run. */
+ * Errors: LSLU_ERR_INVALID_ARG if no lslu_solve has run (batched solves keep
+ * no exportable state). */
 lslu_status lslu_get_state(lslu_handle h, int32_t ptr_location, double* H, double* W,
                            double* beta, void* L, void* D);
 
@@ -112,7 +152,7 @@ lslu_status lslu_get_state(lslu_handle h, int32_t ptr_location, double* H, doubl
  * Algorithm 4 iteration): y = A x (transpose = 0; x length n, y length m) or
  * y = A^T x (transpose = 1; x length m, y length n).  x and y are device
  * pointers of the basis type (FP64 for LSLU_F64, FP32 otherwise).  Launched
- * on the handle's stream without synchronising. */
+ * on the handle's stream without synchronising.  Single-problem handles only. */
 lslu_status lslu_spmv(lslu_handle h, int32_t transpose, const void* x, void* y);
 
 /* Solve the projected problem of Eq. (TSP) for one upper Hessenberg

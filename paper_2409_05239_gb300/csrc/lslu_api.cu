@@ -6,6 +6,8 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <type_traits>
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -60,7 +62,8 @@ void destroy_ctx(lslu_ctx* c) {
                   c->q, c->u, c->r0, c->xin, c->coef, c->xp, c->part_val, c->part_idx, c->st,
                   c->TLi, c->TDi,
                   c->pw_single, c->pw_batched, c->pw_offsets, c->proj_out, c->y, c->sig,
-                  c->cvec, c->xout};
+                  c->cvec, c->xout, c->tile_prob_m, c->tile_prob_n, c->pad_m, c->pad_n,
+                  c->map_m, c->map_n, c->xin_pad, c->xout_user, c->mvec};
   for (void* p : ptrs) cudaFree(p);
   if (c->st_host) cudaFreeHost(c->st_host);
   for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
@@ -71,6 +74,96 @@ void destroy_ctx(lslu_ctx* c) {
   delete c;
 }
 
+
+}  // namespace
+
+namespace {
+
+// Device state of a handle whose padded concatenated CSR (c->m x c->n rows,
+// c->nprob problems) is rp/ci/vv; every per-problem array is strided.
+lslu_status create_common(lslu_ctx* c, const int64_t* rp, const int32_t* ci, const double* vv) {
+  lslu_status st = LSLU_OK;
+  auto fail = [&](lslu_status s2) {
+    lslu::thread_error() = c->err;
+    destroy_ctx(c);
+    return s2;
+  };
+#define CKC(call)                                   \
+  do {                                              \
+    cudaError_t e_ = (call);                        \
+    if (e_ != cudaSuccess) {                        \
+      st = e_ == cudaErrorMemoryAllocation ? LSLU_ERR_OOM : LSLU_ERR_CUDA; \
+      c->err = std::string(#call) + ": " + cudaGetErrorString(e_); \
+      return fail(st);                              \
+    }                                               \
+  } while (0)
+  const int64_t m = c->m, n = c->n;
+  const int P = c->nprob;
+  CKC(cudaGetDevice(&c->device));
+  CKC(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
+  CKC(build_csr_pair(m, n, rp, ci, vv, c->value_type, &c->A, &c->AT, c->stream));
+  const int K = c->kmax;
+  const size_t bb = basis_bytes(c->value_type);
+  c->ldl = round_up(n, 128);  // whole 128-row tiles of the elimination kernel
+  c->ldd = round_up(m, 128);
+  c->ldt = K + 1;
+  c->h_stride = (int64_t)(K + 1) * K;
+  c->w_stride = (int64_t)K * K;
+  c->t_stride = (int64_t)(K + 1) * (K + 1);
+  c->c_stride = K + 2;
+  c->xp_stride = (int64_t)((K + 8) / 8 + 1) * (K + 1);
+  CKC(cudaMalloc(&c->L, (size_t)c->ldl * K * bb));
+  CKC(cudaMalloc(&c->D, (size_t)c->ldd * (K + 1) * bb));
+  CKC(cudaMemset(c->L, 0, (size_t)c->ldl * K * bb));
+  CKC(cudaMemset(c->D, 0, (size_t)c->ldd * (K + 1) * bb));
+  CKC(dmalloc(&c->H, (size_t)P * c->h_stride));
+  CKC(dmalloc(&c->W, (size_t)P * c->w_stride));
+  CKC(cudaMalloc(&c->TLi, (size_t)P * c->t_stride * bb));
+  CKC(cudaMalloc(&c->TDi, (size_t)P * c->t_stride * bb));
+  CKC(dmalloc(&c->gp, (size_t)P * K));
+  CKC(dmalloc(&c->tp, (size_t)P * (K + 1)));
+  CKC(dmalloc(&c->gused, n));
+  CKC(dmalloc(&c->tused, m));
+  CKC(cudaMalloc(&c->q, n * bb));
+  CKC(cudaMalloc(&c->u, m * bb));
+  CKC(dmalloc(&c->r0, m));
+  CKC(dmalloc(&c->xin, m + n));
+  CKC(dmalloc(&c->coef, (size_t)P * c->c_stride));
+  CKC(cudaMalloc(&c->xp, (size_t)P * c->xp_stride * bb));
+  c->part_cap = c->num_sms * 16;
+  CKC(dmalloc(&c->part_val, c->part_cap));
+  CKC(dmalloc(&c->part_idx, c->part_cap));
+  CKC(dmalloc(&c->st, P));
+  CKC(cudaMallocHost((void**)&c->st_host, sizeof(DevState) * P));
+  std::memset(c->st_host, 0, sizeof(DevState) * P);
+  CKC(cudaMemset(c->st, 0, sizeof(DevState) * P));
+  c->pw_cluster = projected_cluster_size();
+  // LSLU_NO_GRAPHS=1: launch every kernel directly instead of replaying
+  // captured graphs (for kernel-level profilers)
+  if (const char* ng = std::getenv("LSLU_NO_GRAPHS")) c->use_graphs = ng[0] == '0';
+  if (std::getenv("LSLU_PROJ_TIMING")) {
+    CKC(cudaMallocManaged(&c->proj_tstamp, 16 * sizeof(unsigned long long)));
+    std::memset(c->proj_tstamp, 0, 16 * sizeof(unsigned long long));
+  }
+  if (std::getenv("LSLU_VERBOSE"))
+    std::fprintf(stderr, "lslu: %d SMs, projected-solve cluster of %d CTAs\n", c->num_sms,
+                 c->pw_cluster);
+  // projected work space: one slot of size K per problem (the histories work
+  // space is allocated on first use)
+  CKC(dmalloc(&c->pw_single, (size_t)P * projected_slot_doubles(K, c->pw_cluster)));
+  c->res_off = K > P ? K : P;
+  CKC(dmalloc(&c->proj_out, 2 * (size_t)c->res_off));
+  CKC(dmalloc(&c->y, (size_t)P * K));
+  CKC(dmalloc(&c->sig, K));
+  CKC(dmalloc(&c->cvec, K + 1));
+  CKC(dmalloc(&c->xout, n));
+  CKC(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+  CKC(cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming));
+  CKC(cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming));
+  CKC(cudaStreamSynchronize(c->stream));
+#undef CKC
+  return LSLU_OK;
+}
 
 }  // namespace
 
@@ -125,88 +218,25 @@ extern "C" lslu_status lslu_create(int64_t m, int64_t n, int64_t nnz, const int6
   }
 
   c = new lslu_ctx();
+  c->nprob = 1;
   c->m = m;
   c->n = n;
+  c->m_user = m;
+  c->n_user = n;
+  c->prob_m = {m};
+  c->prob_n = {n};
+  c->row_base = {0};
+  c->col_base = {0};
   c->nnz = nnz;
   c->value_type = value_type;
   c->kmax = max_iter;
   c->stream = (cudaStream_t)cuda_stream;
-  lslu_status st = LSLU_OK;
-  auto fail = [&](lslu_status s2) {
-    lslu::thread_error() = c->err;
-    destroy_ctx(c);
-    return s2;
-  };
-#define CKC(call)                                   \
-  do {                                              \
-    cudaError_t e_ = (call);                        \
-    if (e_ != cudaSuccess) {                        \
-      st = e_ == cudaErrorMemoryAllocation ? LSLU_ERR_OOM : LSLU_ERR_CUDA; \
-      c->err = std::string(#call) + ": " + cudaGetErrorString(e_); \
-      return fail(st);                              \
-    }                                               \
-  } while (0)
-  CKC(cudaGetDevice(&c->device));
-  CKC(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
-  CKC(build_csr_pair(m, n, rp.data(), ci.data(), vv.data(), value_type, &c->A, &c->AT,
-                     c->stream));
-  const int K = max_iter;
-  const size_t bb = basis_bytes(value_type);
-  c->ldl = round_up(n, 128);  // whole 128-row tiles of the elimination kernel
-  c->ldd = round_up(m, 128);
-  c->ldt = K + 1;
-  CKC(cudaMalloc(&c->L, (size_t)c->ldl * K * bb));
-  CKC(cudaMalloc(&c->D, (size_t)c->ldd * (K + 1) * bb));
-  CKC(cudaMemset(c->L, 0, (size_t)c->ldl * K * bb));
-  CKC(cudaMemset(c->D, 0, (size_t)c->ldd * (K + 1) * bb));
-  CKC(dmalloc(&c->H, (size_t)(K + 1) * K));
-  CKC(dmalloc(&c->W, (size_t)K * K));
-  CKC(cudaMalloc(&c->TLi, (size_t)(K + 1) * (K + 1) * bb));
-  CKC(cudaMalloc(&c->TDi, (size_t)(K + 1) * (K + 1) * bb));
-  CKC(dmalloc(&c->gp, K));
-  CKC(dmalloc(&c->tp, K + 1));
-  CKC(dmalloc(&c->gused, n));
-  CKC(dmalloc(&c->tused, m));
-  CKC(cudaMalloc(&c->q, n * bb));
-  CKC(cudaMalloc(&c->u, m * bb));
-  CKC(dmalloc(&c->r0, m));
-  CKC(dmalloc(&c->xin, m + n));
-  CKC(dmalloc(&c->coef, K + 1));
-  CKC(cudaMalloc(&c->xp, (size_t)((K + 8) / 8 + 1) * (K + 1) * bb));
-  c->part_cap = c->num_sms * 16;
-  CKC(dmalloc(&c->part_val, c->part_cap));
-  CKC(dmalloc(&c->part_idx, c->part_cap));
-  CKC(dmalloc(&c->st, 1));
-  CKC(cudaMallocHost((void**)&c->st_host, sizeof(DevState)));
-  std::memset(c->st_host, 0, sizeof(DevState));
-  CKC(cudaMemset(c->st, 0, sizeof(DevState)));
-  // projected workspace for the single final problem (k <= K); the batched
-  // workspace for histories is allocated on first use
-  c->pw_cluster = projected_cluster_size();
-  // LSLU_NO_GRAPHS=1: launch every kernel directly instead of replaying
-  // captured graphs (for kernel-level profilers)
-  if (const char* ng = std::getenv("LSLU_NO_GRAPHS")) c->use_graphs = ng[0] == '0';
-  if (std::getenv("LSLU_PROJ_TIMING")) {
-    CKC(cudaMallocManaged(&c->proj_tstamp, 16 * sizeof(unsigned long long)));
-    std::memset(c->proj_tstamp, 0, 16 * sizeof(unsigned long long));
-  }
-  if (std::getenv("LSLU_VERBOSE"))
-    std::fprintf(stderr, "lslu: %d SMs, projected-solve cluster of %d CTAs\n", c->num_sms,
-                 c->pw_cluster);
-  CKC(dmalloc(&c->pw_single, (size_t)projected_slot_doubles(K, c->pw_cluster)));
-  CKC(dmalloc(&c->proj_out, 2 * (size_t)K));
-  CKC(dmalloc(&c->y, K));
-  CKC(dmalloc(&c->sig, K));
-  CKC(dmalloc(&c->cvec, K + 1));
-  CKC(dmalloc(&c->xout, n));
-  CKC(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
-  CKC(cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming));
-  CKC(cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming));
-  CKC(cudaStreamSynchronize(c->stream));
-#undef CKC
+  lslu_status st = create_common(c, rp.data(), ci.data(), vv.data());
+  if (st != LSLU_OK) return st;
   *out = c;
   return LSLU_OK;
 }
+
 
 namespace {
 
@@ -258,6 +288,9 @@ int64_t enqueue_solve(Ctx* c, cudaStream_t s, const double* db, const double* dx
   c->ev_used = 0;
   const int64_t m = c->m, n = c->n;
   const int vt = c->value_type;
+  const int P = c->nprob;
+  const int32_t* tpm = c->tile_prob_m;  // nullptr for a single problem
+  const int32_t* tpn = c->tile_prob_n;
   BT* L = (BT*)c->L;
   BT* D = (BT*)c->D;
   CT* q = (CT*)c->q;
@@ -265,11 +298,16 @@ int64_t enqueue_solve(Ctx* c, cudaStream_t s, const double* db, const double* dx
   const int64_t ldh = c->kmax + 1, ldw = c->kmax;
   int64_t launches = 0;
 
-  launch_init_state(c->st, K, s);
-  cudaMemsetAsync(c->gused, 0, n, s);
-  cudaMemsetAsync(c->tused, 0, m, s);
-  cudaMemsetAsync(c->gp, 0xff, sizeof(int32_t) * c->kmax, s);
-  cudaMemsetAsync(c->tp, 0xff, sizeof(int32_t) * (c->kmax + 1), s);
+  launch_init_state(c->st, P, K, s);
+  if (P == 1) {
+    cudaMemsetAsync(c->gused, 0, n, s);
+    cudaMemsetAsync(c->tused, 0, m, s);
+  } else {  // padding rows and columns are never pivots
+    cudaMemcpyAsync(c->gused, c->pad_n, n, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(c->tused, c->pad_m, m, cudaMemcpyDeviceToDevice, s);
+  }
+  cudaMemsetAsync(c->gp, 0xff, sizeof(int32_t) * P * c->kmax, s);
+  cudaMemsetAsync(c->tp, 0xff, sizeof(int32_t) * P * (c->kmax + 1), s);
   launches += 1;
 
   // r0 = b - A x0
@@ -281,55 +319,64 @@ int64_t enqueue_solve(Ctx* c, cudaStream_t s, const double* db, const double* dx
     launch_residual0(db, nullptr, c->r0, m, s);
     launches += 1;
   }
-  // beta = signed max-abs entry of r0, d_1 = r0 / beta, t(1)
+  // beta = signed max-abs entry of r0 (exact, FP64), d_1 = r0 / beta, t(1)
   {
-    PivotArgs pa{c->tp, 0, c->tused, nullptr, c->ldt, LSLU_BREAKDOWN_BETA, 0, 1, c->TDi};
-    launch_eliminate_argmax<double, BT, double>(c->r0, D, c->ldd, 0, c->coef, m, c->r0, pa,
-                                                c->part_val, c->part_idx, c->part_cap, c->st, s,
-                                                c->num_sms);
-    launch_scale<double, BT>(c->r0, D, m, c->st, s, c->num_sms);
-    launches += 2;
+    PivotArgs pa{c->tp, c->kmax + 1, 0, c->tused, nullptr, 0, c->ldt, LSLU_BREAKDOWN_BETA,
+                 0, 1, c->TDi, c->t_stride, c->coef, c->c_stride, P, tpm};
+    launch_init_pivot<BT>(c->r0, m, pa, c->st, s, c->num_sms);
+    launch_scale<double, BT>(c->r0, D, m, c->st, P, tpm, s, c->num_sms);
+    launches += 3;
   }
   for (int k = 0; k < K; ++k) {
     // q = A^T d_k (with the coefficients W(0:k, k) from its pivot rows);
     // eliminate l_0..l_{k-1}; pivot; l_k
     cudaEvent_t e0;
-    PivotCoef pcw{c->gp, k, L, c->ldl, c->coef, c->W + k * ldw, c->xp, c->TLi, c->ldt, c->st, 0};
+    PivotCoef pcw{c->gp,       c->kmax,       k,        L,          c->ldl,
+                  c->coef,     c->c_stride,   c->W + k * ldw,       c->w_stride,
+                  c->xp,       c->xp_stride,  c->TLi,   c->ldt,     c->t_stride,
+                  c->st,       P,             0};
     record_spmv_start(c, s, capturing, &e0);
     launch_spmv_pivots<BT, CT>(c->AT, vt, D + (int64_t)k * c->ldd, q, pcw, s);
     record_spmv_end(c, s, capturing, e0);
-    PivotArgs paw{c->gp, k, c->gused, c->W + k + k * ldw, c->ldt, LSLU_BREAKDOWN_W, k, 0, c->TLi};
-    launch_eliminate_argmax<CT, BT, CT>(q, L, c->ldl, k, c->coef, n, q, paw, c->part_val,
-                                        c->part_idx, c->part_cap, c->st, s, c->num_sms);
-    launch_scale<CT, BT>(q, L + (int64_t)k * c->ldl, n, c->st, s, c->num_sms);
+    PivotArgs paw{c->gp, c->kmax, k, c->gused, c->W + k + k * ldw, c->w_stride, c->ldt,
+                  LSLU_BREAKDOWN_W, k, 0, c->TLi, c->t_stride, c->coef, c->c_stride, P, tpn};
+    launch_eliminate_argmax<CT, BT, CT>(q, L, c->ldl, k, n, q, paw, c->part_val, c->part_idx,
+                                        c->part_cap, c->st, s, c->num_sms);
+    launch_scale<CT, BT>(q, L + (int64_t)k * c->ldl, n, c->st, P, tpn, s, c->num_sms);
     // u = A l_k (with H(0:k+1, k)); eliminate d_0..d_k; pivot; d_{k+1}
-    PivotCoef pch{c->tp, k + 1, D, c->ldd, c->coef, c->H + k * ldh, c->xp, c->TDi, c->ldt, c->st,
-                  0};
+    PivotCoef pch{c->tp,       c->kmax + 1,   k + 1,    D,          c->ldd,
+                  c->coef,     c->c_stride,   c->H + k * ldh,       c->h_stride,
+                  c->xp,       c->xp_stride,  c->TDi,   c->ldt,     c->t_stride,
+                  c->st,       P,             0};
     record_spmv_start(c, s, capturing, &e0);
     launch_spmv_pivots<BT, CT>(c->A, vt, L + (int64_t)k * c->ldl, u, pch, s);
     record_spmv_end(c, s, capturing, e0);
-    PivotArgs pah{c->tp, k + 1, c->tused, c->H + (k + 1) + k * ldh, c->ldt, LSLU_BREAKDOWN_H, k,
-                  0, c->TDi};
-    launch_eliminate_argmax<CT, BT, CT>(u, D, c->ldd, k + 1, c->coef, m, u, pah, c->part_val,
+    PivotArgs pah{c->tp, c->kmax + 1, k + 1, c->tused, c->H + (k + 1) + k * ldh, c->h_stride,
+                  c->ldt, LSLU_BREAKDOWN_H, k, 0, c->TDi, c->t_stride, c->coef, c->c_stride, P,
+                  tpm};
+    launch_eliminate_argmax<CT, BT, CT>(u, D, c->ldd, k + 1, m, u, pah, c->part_val,
                                         c->part_idx, c->part_cap, c->st, s, c->num_sms);
-    launch_scale<CT, BT>(u, D + (int64_t)(k + 1) * c->ldd, m, c->st, s, c->num_sms);
+    launch_scale<CT, BT>(u, D + (int64_t)(k + 1) * c->ldd, m, c->st, P, tpm, s, c->num_sms);
     launches += 6;
   }
-  // projected problems: every k (histories) or only k = k_done
+  // projected problems: every k (histories) or only k = k_done of each problem
   ProjArgs pa;
   std::memset(&pa, 0, sizeof(pa));
   pa.H = c->H;
   pa.ldh = ldh;
-  pa.beta_ptr = &c->st->beta;
   pa.rule = rule;
   pa.lambda = lam;
-  pa.m = m;
+  pa.m = c->prob_m[0];
+  pa.mvec = P > 1 ? c->mvec : nullptr;
   pa.k_first = hist ? 1 : K;
   pa.k_last = K;
   pa.want_y = 1;
   pa.y = c->y;
+  pa.ldy = c->kmax;
+  pa.nbatch = P;
+  pa.strideH = c->h_stride;
   pa.lam_out = c->proj_out;
-  pa.res_out = c->proj_out + c->kmax;
+  pa.res_out = c->proj_out + c->res_off;
   pa.st = c->st;
   pa.tstamp = c->proj_tstamp;
   ProjWork w;
@@ -341,9 +388,11 @@ int64_t enqueue_solve(Ctx* c, cudaStream_t s, const double* db, const double* dx
   } else {
     w.base = c->pw_single;
     w.packed = 0;
+    w.slot_stride = projected_slot_doubles(c->kmax, c->pw_cluster);
   }
   launch_projected(pa, w, s);
-  launch_recombine<BT>(L, c->ldl, c->y, dx0, c->xout, n, c->st, K, s, c->num_sms);
+  launch_recombine<BT>(L, c->ldl, c->y, c->kmax, dx0, c->xout, n, c->st, P, tpn, K, s,
+                       c->num_sms);
   launches += 2;
   return launches;
 }
@@ -412,7 +461,8 @@ lslu_status solve_impl(Ctx* c, const double* db, const double* dx0, int K, int r
     c->launches = ge->launches;
     ev_pairs = ge->ev_pairs;
   }
-  CK(cudaMemcpyAsync(c->st_host, c->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(c->st_host, c->st, sizeof(DevState) * c->nprob, cudaMemcpyDeviceToHost,
+                     s));
   CK(cudaStreamSynchronize(s));
   CK(cudaGetLastError());
   if (c->profile) collect_spmv_times(c, ev_pairs);
@@ -439,6 +489,7 @@ extern "C" lslu_status lslu_solve(lslu_handle h, const double* b, const double* 
                                   double* lambda_hist, double* resid_hist, int32_t* k_done) {
   Ctx* c = h;
   if (!c) return set_err(nullptr, LSLU_ERR_INVALID_ARG, "NULL handle");
+  if (c->map_m) return set_err(c, LSLU_ERR_INVALID_ARG, "batched handle: use lslu_solve_batched");
   if (K < 1 || K > c->kmax) return set_err(c, LSLU_ERR_INVALID_ARG, "K must be in [1, max_iter]");
   if (rule < LSLU_LAMBDA_NONE || rule > LSLU_LAMBDA_WGCV)
     return set_err(c, LSLU_ERR_INVALID_ARG, "unknown lambda rule");
@@ -497,7 +548,7 @@ extern "C" lslu_status lslu_solve(lslu_handle h, const double* b, const double* 
   for (int which = 0; which < 2; ++which) {
     double* dst = which == 0 ? lambda_hist : resid_hist;
     if (!dst) continue;
-    const double* src = c->proj_out + (which == 0 ? 0 : c->kmax);
+    const double* src = c->proj_out + (which == 0 ? 0 : c->res_off);
     CK(cudaMemcpyAsync(dst, src, (size_t)kd * 8, d2o, s));
     if (K > kd) {
       if (host)
@@ -520,6 +571,184 @@ extern "C" lslu_status lslu_solve(lslu_handle h, const double* b, const double* 
                                                         : "non-finite pivot";
     return set_err(c, (lslu_status)ds.status, what);
   }
+  return LSLU_OK;
+}
+
+
+extern "C" lslu_status lslu_create_batched(int32_t nprob, const int64_t* row_off,
+                                           const int64_t* col_off, const int64_t* row_ptr,
+                                           const int32_t* col_idx, const double* vals,
+                                           int32_t value_type, int32_t max_iter,
+                                           void* cuda_stream, lslu_handle* out) {
+  if (!out) return set_err(nullptr, LSLU_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (nprob < 1 || !row_off || !col_off || !row_ptr)
+    return set_err(nullptr, LSLU_ERR_INVALID_ARG, "invalid nprob or NULL offsets");
+  if (value_type != LSLU_F32 && value_type != LSLU_BF16)
+    return set_err(nullptr, LSLU_ERR_INVALID_ARG, "batched solves take FP32 or BF16 values");
+  if (max_iter < 1 || max_iter > kMaxIter)
+    return set_err(nullptr, LSLU_ERR_INVALID_ARG, "max_iter must be in [1, 2048]");
+  if (row_off[0] != 0 || col_off[0] != 0)
+    return set_err(nullptr, LSLU_ERR_INVALID_ARG, "row_off[0] and col_off[0] must be 0");
+  for (int p = 0; p < nprob; ++p)
+    if (row_off[p + 1] <= row_off[p] || col_off[p + 1] <= col_off[p])
+      return set_err(nullptr, LSLU_ERR_INVALID_ARG, "every problem needs m >= 1 and n >= 1");
+  const int64_t mu = row_off[nprob], nu = col_off[nprob];
+  const int64_t nnz = row_ptr[mu];
+  if (nnz < 0 || nnz >= (int64_t)INT32_MAX || row_ptr[0] != 0 || (nnz > 0 && (!col_idx || !vals)))
+    return set_err(nullptr, LSLU_ERR_INVALID_ARG, "invalid CSR (row_ptr[0] != 0 or nnz)");
+  // padded layout: every problem starts on a kTile boundary of both spaces
+  std::vector<int64_t> rb(nprob), cb(nprob);
+  int64_t mp = 0, np = 0;
+  for (int p = 0; p < nprob; ++p) {
+    rb[p] = mp;
+    cb[p] = np;
+    mp = round_up(mp + (row_off[p + 1] - row_off[p]), kTile);
+    np = round_up(np + (col_off[p + 1] - col_off[p]), kTile);
+  }
+  if (mp >= (int64_t)INT32_MAX || np >= (int64_t)INT32_MAX)
+    return set_err(nullptr, LSLU_ERR_INVALID_ARG, "padded sizes must be below 2^31");
+  std::vector<int64_t> rp(mp + 1, 0);
+  std::vector<int32_t> ci;
+  std::vector<double> vv;
+  ci.reserve(nnz);
+  vv.reserve(nnz);
+  std::vector<int32_t> map_m(mu), map_n(nu), tpm(mp / kTile), tpn(np / kTile);
+  std::vector<uint8_t> pad_m(mp, 1), pad_n(np, 1);
+  std::vector<int64_t> mvec(nprob);
+  int64_t prow = 0;
+  for (int p = 0; p < nprob; ++p) {
+    const int64_t m_p = row_off[p + 1] - row_off[p];
+    const int64_t n_p = col_off[p + 1] - col_off[p];
+    mvec[p] = m_p;
+    for (; prow < rb[p]; ++prow) rp[prow + 1] = (int64_t)ci.size();  // padding rows
+    for (int64_t i = 0; i < m_p; ++i, ++prow) {
+      const int64_t r = row_off[p] + i;
+      if (row_ptr[r + 1] < row_ptr[r])
+        return set_err(nullptr, LSLU_ERR_INVALID_ARG, "row_ptr is not monotone");
+      for (int64_t e = row_ptr[r]; e < row_ptr[r + 1]; ++e) {
+        const int64_t cglob = col_idx[e];
+        if (cglob < col_off[p] || cglob >= col_off[p + 1])
+          return set_err(nullptr, LSLU_ERR_INVALID_ARG,
+                         "column index outside its problem's column range");
+        if (!std::isfinite(vals[e]))
+          return set_err(nullptr, LSLU_ERR_INVALID_ARG, "non-finite matrix value");
+        ci.push_back((int32_t)(cb[p] + (cglob - col_off[p])));
+        vv.push_back(vals[e]);
+      }
+      rp[prow + 1] = (int64_t)ci.size();
+      map_m[r] = (int32_t)prow;
+      pad_m[prow] = 0;
+    }
+    for (int64_t j = 0; j < n_p; ++j) {
+      map_n[col_off[p] + j] = (int32_t)(cb[p] + j);
+      pad_n[cb[p] + j] = 0;
+    }
+    const int64_t rend = p + 1 < nprob ? rb[p + 1] : mp;
+    for (int64_t t = rb[p] / kTile; t < rend / kTile; ++t) tpm[t] = p;
+    const int64_t cend = p + 1 < nprob ? cb[p + 1] : np;
+    for (int64_t t = cb[p] / kTile; t < cend / kTile; ++t) tpn[t] = p;
+  }
+  for (; prow < mp; ++prow) rp[prow + 1] = (int64_t)ci.size();
+
+  lslu_ctx* c = new lslu_ctx();
+  c->nprob = nprob;
+  c->m = mp;
+  c->n = np;
+  c->m_user = mu;
+  c->n_user = nu;
+  c->row_base = rb;
+  c->col_base = cb;
+  for (int p = 0; p < nprob; ++p) {
+    c->prob_m.push_back(row_off[p + 1] - row_off[p]);
+    c->prob_n.push_back(col_off[p + 1] - col_off[p]);
+  }
+  c->nnz = nnz;
+  c->value_type = value_type;
+  c->kmax = max_iter;
+  c->stream = (cudaStream_t)cuda_stream;
+  lslu_status st = create_common(c, rp.data(), ci.data(), vv.data());
+  if (st != LSLU_OK) return st;
+  auto up = [&](auto** dst, const auto& v) -> bool {
+    using T = typename std::decay<decltype(v[0])>::type;
+    if (cudaMalloc((void**)dst, std::max<size_t>(v.size(), 1) * sizeof(T)) != cudaSuccess)
+      return false;
+    return cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice) ==
+           cudaSuccess;
+  };
+  if (!up(&c->tile_prob_m, tpm) || !up(&c->tile_prob_n, tpn) || !up(&c->pad_m, pad_m) ||
+      !up(&c->pad_n, pad_n) || !up(&c->map_m, map_m) || !up(&c->map_n, map_n) ||
+      !up(&c->mvec, mvec) || cudaMalloc(&c->xin_pad, mp * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&c->xout_user, nu * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    lslu::thread_error() = "allocating the batch layout failed";
+    destroy_ctx(c);
+    return LSLU_ERR_OOM;
+  }
+  *out = c;
+  return LSLU_OK;
+}
+
+extern "C" lslu_status lslu_solve_batched(lslu_handle h, const double* b, int32_t K,
+                                          int32_t rule, double lambda, int32_t ptr_location,
+                                          double* x_out, int32_t* col_pivots,
+                                          int32_t* row_pivots, int32_t* k_done,
+                                          int32_t* status) {
+  Ctx* c = h;
+  if (!c) return set_err(nullptr, LSLU_ERR_INVALID_ARG, "NULL handle");
+  if (!c->map_m) return set_err(c, LSLU_ERR_INVALID_ARG, "not a batched handle");
+  if (K < 1 || K > c->kmax) return set_err(c, LSLU_ERR_INVALID_ARG, "K must be in [1, max_iter]");
+  if (rule < LSLU_LAMBDA_NONE || rule > LSLU_LAMBDA_WGCV)
+    return set_err(c, LSLU_ERR_INVALID_ARG, "unknown lambda rule");
+  if (rule == LSLU_LAMBDA_FIXED && !(lambda >= 0.0 && std::isfinite(lambda)))
+    return set_err(c, LSLU_ERR_INVALID_ARG, "fixed lambda must be finite and >= 0");
+  if (!b || !x_out) return set_err(c, LSLU_ERR_INVALID_ARG, "b and x_out are required");
+  if (ptr_location != LSLU_HOST && ptr_location != LSLU_DEVICE)
+    return set_err(c, LSLU_ERR_INVALID_ARG, "unknown ptr_location");
+  const bool host = ptr_location == LSLU_HOST;
+  const int P = c->nprob;
+  cudaStream_t s = c->stream;
+  if (host)
+    for (int64_t i = 0; i < c->m_user; ++i)
+      if (!std::isfinite(b[i])) return set_err(c, LSLU_ERR_NONFINITE, "b has a non-finite entry");
+  CK(cudaMemcpyAsync(c->xin, b, c->m_user * 8,
+                     host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemsetAsync(c->xin_pad, 0, c->m * 8, s));
+  launch_scatter(c->xin, c->map_m, c->m_user, c->xin_pad, s);
+  const double lam = rule == LSLU_LAMBDA_FIXED ? lambda : 0.0;
+  lslu_status st = solve_impl<float, float>(c, c->xin_pad, nullptr, K, rule, lam, false);
+  if (st != LSLU_OK) return st;
+  launch_gather(c->xout, c->map_n, c->n_user, c->xout_user, s);
+  const cudaMemcpyKind d2o = host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  CK(cudaMemcpyAsync(x_out, c->xout_user, c->n_user * 8, d2o, s));
+  // pivots in each problem's own index space; -1 past its k_done
+  std::vector<int32_t> g((size_t)P * c->kmax), t((size_t)P * (c->kmax + 1));
+  CK(cudaMemcpyAsync(g.data(), c->gp, g.size() * 4, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(t.data(), c->tp, t.size() * 4, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  std::vector<int32_t> go((size_t)P * K), to((size_t)P * (K + 1)), kd(P), sv(P);
+  for (int p = 0; p < P; ++p) {
+    const DevState& ds = c->st_host[p];
+    const int kdp = ds.k_done < 0 ? 0 : (ds.k_done > K ? K : ds.k_done);
+    kd[p] = kdp;
+    sv[p] = ds.status;
+    const int nt = ds.status == LSLU_BREAKDOWN_BETA ? 0 : kdp + 1;
+    for (int j = 0; j < K; ++j) {
+      const int32_t v = g[(size_t)p * c->kmax + j];
+      go[(size_t)p * K + j] = (j < kdp && v >= 0) ? (int32_t)(v - c->col_base[p]) : -1;
+    }
+    for (int j = 0; j <= K; ++j) {
+      const int32_t v = t[(size_t)p * (c->kmax + 1) + j];
+      to[(size_t)p * (K + 1) + j] = (j < nt && v >= 0) ? (int32_t)(v - c->row_base[p]) : -1;
+    }
+  }
+  const cudaMemcpyKind h2o = host ? cudaMemcpyHostToHost : cudaMemcpyHostToDevice;
+  if (col_pivots) CK(cudaMemcpyAsync(col_pivots, go.data(), go.size() * 4, h2o, s));
+  if (row_pivots) CK(cudaMemcpyAsync(row_pivots, to.data(), to.size() * 4, h2o, s));
+  if (k_done) CK(cudaMemcpyAsync(k_done, kd.data(), kd.size() * 4, h2o, s));
+  if (status) CK(cudaMemcpyAsync(status, sv.data(), sv.size() * 4, h2o, s));
+  CK(cudaStreamSynchronize(s));
+  c->last_k = -1;  // lslu_get_state serves single-problem handles only
   return LSLU_OK;
 }
 
@@ -559,6 +788,7 @@ extern "C" lslu_status lslu_spmv(lslu_handle h, int32_t transpose, const void* x
   Ctx* c = h;
   if (!c) return set_err(nullptr, LSLU_ERR_INVALID_ARG, "NULL handle");
   if (!x || !y) return set_err(c, LSLU_ERR_INVALID_ARG, "NULL vector");
+  if (c->map_m) return set_err(c, LSLU_ERR_INVALID_ARG, "lslu_spmv takes single-problem handles");
   const DevCsr& A = transpose ? c->AT : c->A;
   if (c->value_type == LSLU_F64)
     launch_spmv<double, double>(A, c->value_type, (const double*)x, (double*)y, c->stream,
@@ -609,7 +839,7 @@ extern "C" lslu_status lslu_projected(lslu_handle h, int32_t k, const double* H,
   pa.cvec = c->cvec;
   pa.ldc = c->kmax + 1;
   pa.lam_out = c->proj_out;
-  pa.res_out = c->proj_out + c->kmax;
+  pa.res_out = c->proj_out + c->res_off;
   ProjWork w;
   w.base = c->pw_single;
   w.cluster = c->pw_cluster;
@@ -620,7 +850,7 @@ extern "C" lslu_status lslu_projected(lslu_handle h, int32_t k, const double* H,
   if (sigma) CK(cudaMemcpyAsync(sigma, c->sig, k * 8, kind, s));
   if (cv) CK(cudaMemcpyAsync(cv, c->cvec, (k + 1) * 8, kind, s));
   if (lambda_out) CK(cudaMemcpyAsync(lambda_out, c->proj_out + (k - 1), 8, kind, s));
-  if (resid_out) CK(cudaMemcpyAsync(resid_out, c->proj_out + c->kmax + (k - 1), 8, kind, s));
+  if (resid_out) CK(cudaMemcpyAsync(resid_out, c->proj_out + c->res_off + (k - 1), 8, kind, s));
   CK(cudaStreamSynchronize(s));
   if (stage) cudaFree(stage);
   return LSLU_OK;

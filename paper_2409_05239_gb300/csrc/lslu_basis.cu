@@ -1,18 +1,20 @@
 // Hessenberg step of Algorithm 4 for one new vector x (q = A^T d_k or
 // u = A l_k) against the basis B (L_k or D_{k+1}) with pivot rows piv:
 //
-//   coefficients  c_j = x(piv_j) - sum_{i<j} B_i(piv_j) c_i   (the sequential
-//                 elimination "W(j,k) = q(g(j)); q = q - W(j,k) l_j" read at
-//                 the pivot rows: a forward substitution with the unit lower
-//                 triangular T(j,i) = B_i(piv_j));
+//   coefficients  c = T^-1 x(piv), T(i,j) = b_j(piv_i) unit lower triangular
+//                 (the sequential elimination "W(j,k) = q(g(j)); q = q -
+//                 W(j,k) l_j" read at the pivot rows; computed inside the
+//                 sparse product, lslu_spmv.cu);
 //   elimination   v = x - B c, with v = 0 exactly on pivoted rows;
 //   pivot         i* = argmax |v| over unpivoted rows (ties: lowest index),
-//                 the new Hessenberg entry v(i*), new row of T;
+//                 the new Hessenberg entry v(i*);
 //   scale         b_new = v / v(i*) (1 at i*, 0 on earlier pivots).
 //
-// The argmax is a grid reduction: every block writes its best candidate and
-// the last block to finish (ticket counter) reduces the partials in block
-// order and records the pivot, so the result does not depend on timing.
+// A launch serves every problem of a batch: problem p owns whole kTile-row
+// tiles, its coefficients, pivot list, T^-1 and state sit at base + p * stride.
+// The argmax is a grid reduction that does not depend on timing: FP32 keys
+// combine with an integer atomicMax; FP64 (single problem) candidates are
+// reduced per block and the partials in block order by the last block.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -63,10 +65,6 @@ __device__ void block_argmax(double& v, int& i) {
   __syncthreads();
 }
 
-// Tiles of rows x all basis columns: a tile of 32*VEC consecutive rows is read
-// by every warp of the block as 16-byte vectors (VEC rows per lane); warp w
-// takes the columns j = w, w+8, ...  The eight per-warp partial sums of each
-// row are combined in warp order, then subtracted from x.
 template <typename BT>
 struct Vec16;
 template <>
@@ -86,14 +84,12 @@ struct Vec16<double> {
   }
 };
 
-// Pivot search.  FP32 compute: each candidate becomes the 64-bit key
-// (bits of |v| << 32) | (2^32 - 1 - i), so one unsigned max gives the
-// largest |v| with ties to the lowest index (a NaN has larger bits than any
-// number and wins, so it is reported); blocks combine with one atomicMax.
-// FP64 compute: (|v|, i) pairs are reduced per block and the partials are
-// reduced in block order by the last block.
+// FP32 pivot key: (bits of |v| << 32) | (2^32 - 1 - i).  One unsigned max
+// gives the largest |v| with ties to the lowest index; a NaN has larger bits
+// than any number, wins and is reported.
 __device__ __forceinline__ unsigned long long argkey(float a, int i) {
-  return ((unsigned long long)__float_as_uint(a) << 32) | (unsigned long long)(0xffffffffu - (unsigned)i);
+  return ((unsigned long long)__float_as_uint(a) << 32) |
+         (unsigned long long)(0xffffffffu - (unsigned)i);
 }
 
 __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long k) {
@@ -105,31 +101,69 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long k)
   return k;
 }
 
+__device__ __forceinline__ int tile_problem(const int32_t* tile_prob, int64_t row) {
+  return tile_prob ? tile_prob[row / kTile] : 0;
+}
+
+// Records the pivot of problem p (one thread).
+template <typename CT, typename BT>
+__device__ void record_pivot(const PivotArgs& pa, DevState& s, int p, int besti, double best,
+                             const CT* v) {
+  if (besti < 0 || best == 0.0) {
+    s.status = pa.breakdown_code;
+    s.k_done = pa.k_on_breakdown;
+  } else if (!isfinite(best)) {
+    s.status = LSLU_ERR_NONFINITE;
+    s.k_done = pa.k_on_breakdown;
+  } else {
+    const CT pv = __ldcg(v + besti);
+    s.pivot = (double)pv;
+    s.pivot_f = (float)pv;
+    pa.piv_list[(int64_t)p * pa.piv_stride + pa.piv_slot] = besti;
+    pa.used[besti] = 1;
+    if (pa.hess_entry) pa.hess_entry[(int64_t)p * pa.hess_stride] = (double)pv;
+    if (pa.is_init) s.beta = (double)pv;
+    reinterpret_cast<BT*>(pa.Tinv)[(int64_t)p * pa.tinv_stride +
+                                   (int64_t)pa.piv_slot * pa.ldt + pa.piv_slot] = (BT)1;
+  }
+}
+
+// Tiles of 32*VEC rows x all cnt basis columns: every warp of the block reads
+// the tile as 16-byte vectors (VEC rows per lane) and takes the columns
+// j = w, w+8, ...; the eight per-warp partial sums of a row are combined in
+// warp order and subtracted from x.
 template <typename XT, typename BT, typename CT>
 __global__ void __launch_bounds__(kThreads)
-    k_eliminate_argmax(const XT* x, const BT* __restrict__ B, int64_t ld, int cnt,
-                       const double* __restrict__ coef, int64_t rows, CT* v, PivotArgs pa,
-                       double* __restrict__ part_val, int32_t* __restrict__ part_idx,
-                       DevState* st) {
+    k_eliminate_argmax(const XT* x, const BT* __restrict__ B, int64_t ld, int cnt, int64_t rows,
+                       CT* v, PivotArgs pa, double* __restrict__ part_val,
+                       int32_t* __restrict__ part_idx, DevState* st) {
   constexpr bool kKey = sizeof(CT) == 4;
   constexpr int VEC = Vec16<BT>::N;
   constexpr int TILE = 32 * VEC;
   constexpr int NW = kThreads / 32;
+  static_assert(kTile % TILE == 0, "problem tiles must hold whole elimination tiles");
   extern __shared__ unsigned char smem_raw[];
   CT* c = reinterpret_cast<CT*>(smem_raw);
   __shared__ CT part[NW][TILE];
   __shared__ unsigned long long kred[NW];
   __shared__ bool is_last;
-  if (st->status != LSLU_OK) return;
-  for (int j = threadIdx.x; j < cnt; j += blockDim.x) c[j] = (CT)coef[j];
-  __syncthreads();
+  if (pa.nprob == 1 && st[0].status != LSLU_OK) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t ntiles = (rows + TILE - 1) / TILE;
   double best = 0.0;
   int besti = -1;
   unsigned long long bkey = 0;
+  int cur_p = -1;
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int64_t r0 = t * TILE;
+    const int p = tile_problem(pa.tile_prob, r0);
+    if (p != cur_p) {  // uniform over the block
+      __syncthreads();
+      for (int j = threadIdx.x; j < cnt; j += blockDim.x)
+        c[j] = (CT)pa.coef[(int64_t)p * pa.coef_stride + j];
+      __syncthreads();
+      cur_p = p;
+    }
     CT acc[VEC];
 #pragma unroll
     for (int e = 0; e < VEC; ++e) acc[e] = 0;
@@ -155,6 +189,7 @@ __global__ void __launch_bounds__(kThreads)
 #pragma unroll
     for (int e = 0; e < VEC; ++e) part[warp][lane * VEC + e] = acc[e];
     __syncthreads();
+    unsigned long long tkey = 0;
     if (threadIdx.x < TILE) {
       const int64_t i = r0 + threadIdx.x;
       if (i < rows) {
@@ -165,8 +200,7 @@ __global__ void __launch_bounds__(kThreads)
         if (!pa.used[i]) {
           val = (CT)x[i] - s;
           if constexpr (kKey) {
-            const unsigned long long kk = argkey(fabsf((float)val), (int)i);
-            bkey = kk > bkey ? kk : bkey;
+            tkey = argkey(fabsf((float)val), (int)i);
           } else {
             double a = fabs((double)val);
             if (isnan(a)) a = INFINITY;  // a NaN must win so that it is reported
@@ -179,18 +213,36 @@ __global__ void __launch_bounds__(kThreads)
         v[i] = val;
       }
     }
+    if constexpr (kKey) {
+      if (pa.nprob == 1) {
+        bkey = tkey > bkey ? tkey : bkey;
+      } else {  // batch: one atomicMax per tile on the tile's problem
+        tkey = warp_max_u64(tkey);
+        if (lane == 0) kred[warp] = tkey;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          unsigned long long m = 0;
+          for (int w = 0; w < NW; ++w) m = kred[w] > m ? kred[w] : m;
+          if (m) atomicMax(&st[p].amax, m);
+        }
+      }
+    }
     __syncthreads();
   }
   if constexpr (kKey) {
-    bkey = warp_max_u64(bkey);
-    if (lane == 0) kred[warp] = bkey;
-    __syncthreads();
+    if (pa.nprob == 1) {
+      bkey = warp_max_u64(bkey);
+      if (lane == 0) kred[warp] = bkey;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        unsigned long long m = 0;
+        for (int w = 0; w < NW; ++w) m = kred[w] > m ? kred[w] : m;
+        if (m) atomicMax(&st[0].amax, m);
+      }
+    }
     if (threadIdx.x == 0) {
-      unsigned long long m = 0;
-      for (int w = 0; w < NW; ++w) m = kred[w] > m ? kred[w] : m;
-      if (m) atomicMax(&st->amax, m);
       __threadfence();
-      is_last = (atomicAdd(&st->ticket, 1) == (int)gridDim.x - 1);
+      is_last = (atomicAdd(&st[0].ticket, 1) == (int)gridDim.x - 1);
     }
   } else {
     block_argmax(best, besti);
@@ -198,13 +250,22 @@ __global__ void __launch_bounds__(kThreads)
       part_val[blockIdx.x] = best;
       part_idx[blockIdx.x] = besti;
       __threadfence();
-      is_last = (atomicAdd(&st->ticket, 1) == (int)gridDim.x - 1);
+      is_last = (atomicAdd(&st[0].ticket, 1) == (int)gridDim.x - 1);
     }
   }
   __syncthreads();
   if (!is_last) return;
   __threadfence();
-  if constexpr (!kKey) {
+  if constexpr (kKey) {
+    if (threadIdx.x == 0) st[0].ticket = 0;
+    for (int p = threadIdx.x; p < pa.nprob; p += blockDim.x) {
+      const unsigned long long m = atomicExch(&st[p].amax, 0ull);
+      if (st[p].status != LSLU_OK) continue;
+      const int bi = m ? (int)(0xffffffffu - (unsigned)(m & 0xffffffffull)) : -1;
+      const float a = __uint_as_float((unsigned)(m >> 32));
+      record_pivot<CT, BT>(pa, st[p], p, bi, (a != a) ? INFINITY : (double)a, v);
+    }
+  } else {
     best = 0.0;
     besti = -1;
     for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
@@ -216,53 +277,86 @@ __global__ void __launch_bounds__(kThreads)
       }
     }
     block_argmax(best, besti);
+    if (threadIdx.x == 0) {
+      st[0].ticket = 0;
+      record_pivot<CT, BT>(pa, st[0], 0, besti, best, v);
+    }
   }
+}
+
+// Exact pivot of r0 for every problem, in two passes over FP64 values: the
+// largest |r0| (non-negative doubles order like their bit patterns), then the
+// lowest index attaining it; the last block of the second pass records it.
+__global__ void k_r0_max(const double* __restrict__ r0, int64_t rows, const uint8_t* used,
+                         const int32_t* tile_prob, DevState* st) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < rows;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (used[i]) continue;
+    const double a = fabs(r0[i]);
+    unsigned long long bits = (unsigned long long)__double_as_longlong(a);
+    if (a != a) bits = 0x7ff0000000000001ull;  // NaN above every number
+    if (bits) atomicMax(&st[tile_problem(tile_prob, i)].amax, bits);
+  }
+}
+
+template <typename BT>
+__global__ void k_r0_argmin(const double* __restrict__ r0, int64_t rows, PivotArgs pa,
+                            DevState* st) {
+  __shared__ bool is_last;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < rows;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (pa.used[i]) continue;
+    const int p = tile_problem(pa.tile_prob, i);
+    const double a = fabs(r0[i]);
+    unsigned long long bits = (unsigned long long)__double_as_longlong(a);
+    if (a != a) bits = 0x7ff0000000000001ull;
+    if (bits && bits == __ldcg(&st[p].amax)) atomicMin(&st[p].amin, (int)i);
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
-    st->ticket = 0;
-    if constexpr (kKey) {
-      const unsigned long long m = atomicExch(&st->amax, 0ull);
-      besti = m ? (int)(0xffffffffu - (unsigned)(m & 0xffffffffull)) : -1;
-      const float a = __uint_as_float((unsigned)(m >> 32));
-      best = (a != a) ? INFINITY : (double)a;
-    }
-    if (besti < 0 || best == 0.0) {
-      st->status = pa.breakdown_code;
-      st->k_done = pa.k_on_breakdown;
-    } else if (!isfinite(best)) {
-      st->status = LSLU_ERR_NONFINITE;
-      st->k_done = pa.k_on_breakdown;
-    } else {
-      const CT pv = __ldcg(v + besti);
-      st->pivot = (double)pv;
-      st->pivot_f = (float)pv;
-      pa.piv_list[pa.piv_slot] = besti;
-      pa.used[besti] = 1;
-      if (pa.hess_entry) *pa.hess_entry = (double)pv;
-      if (pa.is_init) st->beta = (double)pv;
-      reinterpret_cast<BT*>(pa.Tinv)[(int64_t)pa.piv_slot * pa.ldt + pa.piv_slot] = (BT)1;
-    }
+    __threadfence();
+    is_last = (atomicAdd(&st[0].ticket, 1) == (int)gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  if (threadIdx.x == 0) st[0].ticket = 0;
+  for (int p = threadIdx.x; p < pa.nprob; p += blockDim.x) {
+    const unsigned long long m = atomicExch(&st[p].amax, 0ull);
+    const int bi = atomicExch(&st[p].amin, 0x7fffffff);
+    if (st[p].status != LSLU_OK) continue;
+    const double best = m == 0x7ff0000000000001ull ? INFINITY
+                                                  : __longlong_as_double((long long)m);
+    record_pivot<double, BT>(pa, st[p], p, (m && bi != 0x7fffffff) ? bi : -1, best, r0);
   }
 }
 
 template <typename CT, typename BT>
 __global__ void k_scale(const CT* __restrict__ v, BT* __restrict__ out, int64_t rows,
-                        const DevState* st) {
-  if (st->status != LSLU_OK) return;
-  const CT p = sizeof(CT) == 8 ? (CT)st->pivot : (CT)st->pivot_f;
+                        const DevState* st, int nprob, const int32_t* tile_prob) {
+  if (nprob == 1 && st[0].status != LSLU_OK) return;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < rows;
-       i += (int64_t)gridDim.x * blockDim.x)
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const DevState& s = st[tile_problem(tile_prob, i)];
+    if (s.status != LSLU_OK) continue;
+    const CT p = sizeof(CT) == 8 ? (CT)s.pivot : (CT)s.pivot_f;
     out[i] = (BT)(v[i] / p);
+  }
 }
 
-__global__ void k_init_state(DevState* st, int K) {
-  st->status = LSLU_OK;
-  st->k_done = K;
-  st->ticket = 0;
-  st->ticket2 = 0;
-  st->beta = 0.0;
-  st->pivot = 0.0;
-  st->pivot_f = 0.0f;
-  st->amax = 0ull;
+__global__ void k_init_state(DevState* st, int nprob, int K) {
+  for (int p = threadIdx.x; p < nprob; p += blockDim.x) {
+    DevState& s = st[p];
+    s.status = LSLU_OK;
+    s.k_done = K;
+    s.ticket = 0;
+    s.ticket2 = 0;
+    s.beta = 0.0;
+    s.pivot = 0.0;
+    s.pivot_f = 0.0f;
+    s.amin = 0x7fffffff;
+    s.amax = 0ull;
+  }
 }
 
 __global__ void k_residual0(const double* b, const double* Ax0, double* r0, int64_t m) {
@@ -271,20 +365,45 @@ __global__ void k_residual0(const double* b, const double* Ax0, double* r0, int6
     r0[i] = Ax0 ? b[i] - Ax0[i] : b[i];
 }
 
+__global__ void k_scatter(const double* __restrict__ src, const int32_t* __restrict__ map,
+                          int64_t count, double* __restrict__ dst) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x)
+    dst[map[i]] = src[i];
+}
+
+__global__ void k_gather(const double* __restrict__ src, const int32_t* __restrict__ map,
+                         int64_t count, double* __restrict__ dst) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = src[map[i]];
+}
+
+// x = x0 + L y for every problem; tiles of kTile rows (one problem each),
+// FP64 accumulation.
 template <typename BT>
-__global__ void __launch_bounds__(kThreads)
-    k_recombine(const BT* __restrict__ L, int64_t ldl, const double* __restrict__ y,
+__global__ void __launch_bounds__(kTile)
+    k_recombine(const BT* __restrict__ L, int64_t ldl, const double* __restrict__ y, int64_t ldy,
                 const double* __restrict__ x0, double* __restrict__ x, int64_t n,
-                const DevState* st, int K) {
+                const DevState* st, int nprob, const int32_t* tile_prob, int K) {
   extern __shared__ double ys[];
-  const int k = st ? min(K, st->k_done) : K;
-  for (int j = threadIdx.x; j < k; j += blockDim.x) ys[j] = y[j];
-  __syncthreads();
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    double acc = 0.0;
-    for (int j = 0; j < k; ++j) acc = fma((double)__ldg(L + i + (int64_t)j * ldl), ys[j], acc);
-    x[i] = (x0 ? x0[i] : 0.0) + acc;
+  const int64_t ntiles = (n + kTile - 1) / kTile;
+  int cur_p = -1, k = 0;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int p = tile_problem(tile_prob, t * kTile);
+    if (p != cur_p) {
+      __syncthreads();
+      k = st ? min(K, st[p].k_done) : K;
+      for (int j = threadIdx.x; j < k; j += blockDim.x) ys[j] = y[(int64_t)p * ldy + j];
+      __syncthreads();
+      cur_p = p;
+    }
+    const int64_t i = t * kTile + threadIdx.x;
+    if (i < n) {
+      double acc = 0.0;
+      for (int j = 0; j < k; ++j) acc = fma((double)__ldg(L + i + (int64_t)j * ldl), ys[j], acc);
+      x[i] = (x0 ? x0[i] : 0.0) + acc;
+    }
   }
 }
 
@@ -299,59 +418,91 @@ int grid_for(int64_t rows, int num_sms, int per_sm) {
 }  // namespace
 
 template <typename XT, typename BT, typename CT>
-void launch_eliminate_argmax(const XT* x, const BT* B, int64_t ld, int cnt, const double* coef,
-                             int64_t rows, CT* v, const PivotArgs& pa, double* part_val,
-                             int32_t* part_idx, int part_cap, DevState* st, cudaStream_t s,
-                             int) {
+void launch_eliminate_argmax(const XT* x, const BT* B, int64_t ld, int cnt, int64_t rows, CT* v,
+                             const PivotArgs& pa, double* part_val, int32_t* part_idx,
+                             int part_cap, DevState* st, cudaStream_t s, int) {
   constexpr int TILE = 32 * Vec16<BT>::N;
   int64_t g = (rows + TILE - 1) / TILE;
   if (g > part_cap) g = part_cap;
   if (g < 1) g = 1;
   const size_t sm = (size_t)(cnt > 0 ? cnt : 1) * sizeof(CT);
-  k_eliminate_argmax<XT, BT, CT><<<(unsigned)g, kThreads, sm, s>>>(x, B, ld, cnt, coef, rows, v,
-                                                                   pa, part_val, part_idx, st);
+  k_eliminate_argmax<XT, BT, CT><<<(unsigned)g, kThreads, sm, s>>>(x, B, ld, cnt, rows, v, pa,
+                                                                   part_val, part_idx, st);
+}
+
+template <typename BT>
+void launch_init_pivot(const double* r0, int64_t rows, const PivotArgs& pa, DevState* st,
+                       cudaStream_t s, int num_sms) {
+  const int g = grid_for(rows, num_sms, 4);
+  k_r0_max<<<g, kThreads, 0, s>>>(r0, rows, pa.used, pa.tile_prob, st);
+  k_r0_argmin<BT><<<g, kThreads, 0, s>>>(r0, rows, pa, st);
 }
 
 template <typename CT, typename BT>
-void launch_scale(const CT* v, BT* out, int64_t rows, DevState* st, cudaStream_t s,
-                  int num_sms) {
-  k_scale<CT, BT><<<grid_for(rows, num_sms, 8), kThreads, 0, s>>>(v, out, rows, st);
+void launch_scale(const CT* v, BT* out, int64_t rows, DevState* st, int nprob,
+                  const int32_t* tile_prob, cudaStream_t s, int num_sms) {
+  k_scale<CT, BT><<<grid_for(rows, num_sms, 8), kThreads, 0, s>>>(v, out, rows, st, nprob,
+                                                                  tile_prob);
 }
 
-void launch_init_state(DevState* st, int K, cudaStream_t s) { k_init_state<<<1, 1, 0, s>>>(st, K); }
+void launch_init_state(DevState* st, int nprob, int K, cudaStream_t s) {
+  k_init_state<<<1, 256, 0, s>>>(st, nprob, K);
+}
 
 void launch_residual0(const double* b, const double* Ax0, double* r0, int64_t m,
                       cudaStream_t s) {
   k_residual0<<<(unsigned)std::min<int64_t>((m + 255) / 256, 4096), 256, 0, s>>>(b, Ax0, r0, m);
 }
 
+void launch_scatter(const double* src, const int32_t* map, int64_t count, double* dst,
+                    cudaStream_t s) {
+  if (count <= 0) return;
+  k_scatter<<<(unsigned)std::min<int64_t>((count + 255) / 256, 4096), 256, 0, s>>>(src, map,
+                                                                                 count, dst);
+}
+
+void launch_gather(const double* src, const int32_t* map, int64_t count, double* dst,
+                   cudaStream_t s) {
+  if (count <= 0) return;
+  k_gather<<<(unsigned)std::min<int64_t>((count + 255) / 256, 4096), 256, 0, s>>>(src, map,
+                                                                                count, dst);
+}
+
 template <typename BT>
-void launch_recombine(const BT* L, int64_t ldl, const double* y, const double* x0, double* x,
-                      int64_t n, const DevState* st, int K, cudaStream_t s, int num_sms) {
-  k_recombine<BT><<<grid_for(n, num_sms, 8), kThreads, (size_t)(K > 0 ? K : 1) * 8, s>>>(
-      L, ldl, y, x0, x, n, st, K);
+void launch_recombine(const BT* L, int64_t ldl, const double* y, int64_t ldy, const double* x0,
+                      double* x, int64_t n, const DevState* st, int nprob,
+                      const int32_t* tile_prob, int K, cudaStream_t s, int num_sms) {
+  int64_t g = (n + kTile - 1) / kTile;
+  if (g > (int64_t)num_sms * 16) g = (int64_t)num_sms * 16;
+  k_recombine<BT><<<(unsigned)g, kTile, (size_t)(K > 0 ? K : 1) * 8, s>>>(
+      L, ldl, y, ldy, x0, x, n, st, nprob, tile_prob, K);
 }
 
 // explicit instantiations: FP64 mode (basis double) and FP32 mode (basis float)
-template void launch_eliminate_argmax<double, double, double>(
-    const double*, const double*, int64_t, int, const double*, int64_t, double*,
-    const PivotArgs&, double*, int32_t*, int, DevState*, cudaStream_t, int);
+template void launch_eliminate_argmax<double, double, double>(const double*, const double*,
+                                                              int64_t, int, int64_t, double*,
+                                                              const PivotArgs&, double*,
+                                                              int32_t*, int, DevState*,
+                                                              cudaStream_t, int);
 template void launch_eliminate_argmax<float, float, float>(const float*, const float*, int64_t,
-                                                           int, const double*, int64_t, float*,
+                                                           int, int64_t, float*,
                                                            const PivotArgs&, double*, int32_t*,
                                                            int, DevState*, cudaStream_t, int);
-template void launch_eliminate_argmax<double, float, double>(
-    const double*, const float*, int64_t, int, const double*, int64_t, double*,
-    const PivotArgs&, double*, int32_t*, int, DevState*, cudaStream_t, int);
-template void launch_scale<double, double>(const double*, double*, int64_t, DevState*,
-                                           cudaStream_t, int);
-template void launch_scale<float, float>(const float*, float*, int64_t, DevState*, cudaStream_t,
-                                         int);
-template void launch_scale<double, float>(const double*, float*, int64_t, DevState*,
-                                          cudaStream_t, int);
-template void launch_recombine<double>(const double*, int64_t, const double*, const double*,
-                                       double*, int64_t, const DevState*, int, cudaStream_t, int);
-template void launch_recombine<float>(const float*, int64_t, const double*, const double*,
-                                      double*, int64_t, const DevState*, int, cudaStream_t, int);
+template void launch_init_pivot<double>(const double*, int64_t, const PivotArgs&, DevState*,
+                                        cudaStream_t, int);
+template void launch_init_pivot<float>(const double*, int64_t, const PivotArgs&, DevState*,
+                                       cudaStream_t, int);
+template void launch_scale<double, double>(const double*, double*, int64_t, DevState*, int,
+                                           const int32_t*, cudaStream_t, int);
+template void launch_scale<float, float>(const float*, float*, int64_t, DevState*, int,
+                                         const int32_t*, cudaStream_t, int);
+template void launch_scale<double, float>(const double*, float*, int64_t, DevState*, int,
+                                          const int32_t*, cudaStream_t, int);
+template void launch_recombine<double>(const double*, int64_t, const double*, int64_t,
+                                       const double*, double*, int64_t, const DevState*, int,
+                                       const int32_t*, int, cudaStream_t, int);
+template void launch_recombine<float>(const float*, int64_t, const double*, int64_t,
+                                      const double*, double*, int64_t, const DevState*, int,
+                                      const int32_t*, int, cudaStream_t, int);
 
 }  // namespace lslu

@@ -20,6 +20,11 @@ constexpr int kRowAlign = 8;
 // Upper bound on max_iter (bounds the projected-problem workspace).
 constexpr int kMaxIter = 2048;
 
+// Rows of one elimination tile.  Problems solved together (a batch) start on
+// multiples of kTile in the concatenated row and column spaces, so every tile
+// belongs to exactly one problem.
+constexpr int kTile = 128;
+
 struct DevCsr {
   int64_t rows = 0, cols = 0;
   int64_t nnz = 0;         // true non-zeros
@@ -30,17 +35,18 @@ struct DevCsr {
   void* val = nullptr;         // nnz_padded, type per value type
 };
 
-// Device-resident state of one solve.  Written by the pivot kernels.
+// Device-resident state of one problem of a solve (one per problem of a
+// batch).  Written by the pivot kernels.
 struct DevState {
-  int32_t status;   // lslu_status of the running solve
+  int32_t status;   // lslu_status of this problem
   int32_t k_done;   // completed iterations when status != OK
-  int32_t ticket;   // block counter of the grid-wide argmax reduction
-  int32_t ticket2;  // block counter of the pivot-row products
+  int32_t ticket;   // block counter of the grid-wide argmax reduction (entry 0 only)
+  int32_t ticket2;  // block counter of this problem's pivot-row products
   double beta;      // signed max-abs entry of r0
   double pivot;     // value of the last pivot (FP64 copy)
   float pivot_f;    // same, FP32 copy for the FP32 scale kernel
-  float pad1;
-  unsigned long long amax;  // running argmax key of the FP32 pivot search
+  int32_t amin;     // lowest index attaining the maximum (exact r0 pivot search)
+  unsigned long long amax;  // running argmax key of the pivot search
 };
 
 // Work space of the projected-problem kernel (global memory): one slot per
@@ -51,12 +57,27 @@ struct ProjWork {
   int packed = 0;
   int cluster = 1;       // CTAs per cluster
   int slab_in_smem = 0;  // set by the launcher
+  int64_t slot_stride = 0;  // doubles per problem of a batch
 };
 
 struct Ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
-  int64_t m = 0, n = 0, nnz = 0;
+  int64_t m = 0, n = 0, nnz = 0;  // padded concatenated sizes (= the problem's for nprob == 1)
+  // batch of problems solved together (nprob == 1 for lslu_create)
+  int nprob = 1;
+  std::vector<int64_t> prob_m, prob_n, row_base, col_base;  // per problem (host)
+  int64_t m_user = 0, n_user = 0;      // unpadded totals (the caller's layout)
+  int32_t* tile_prob_m = nullptr;      // problem of each kTile rows of the m-space
+  int32_t* tile_prob_n = nullptr;      // ... of the n-space
+  uint8_t* pad_m = nullptr;            // 1 on padding rows (never pivots)
+  uint8_t* pad_n = nullptr;
+  int32_t* map_m = nullptr;            // caller row -> padded row
+  int32_t* map_n = nullptr;            // caller column -> padded column
+  double* xin_pad = nullptr;           // padded staging of b (batch)
+  double* xout_user = nullptr;         // x in the caller's layout (batch)
+  int64_t* mvec = nullptr;             // rows of every problem (weighted GCV)
+  int64_t res_off = 0;                 // offset of the residual outputs in proj_out
   int value_type = LSLU_F64;
   int kmax = 0;
   DevCsr A, AT;  // A (m rows) and A^T (n rows)
@@ -73,8 +94,10 @@ struct Ctx {
   void* TLi = nullptr;
   void* TDi = nullptr;
   int64_t ldt = 0;
-  int32_t* gp = nullptr;  // kmax
-  int32_t* tp = nullptr;  // kmax+1
+  int32_t* gp = nullptr;  // kmax per problem (padded-space row indices)
+  int32_t* tp = nullptr;  // kmax+1 per problem
+  // per-problem strides of the arrays above and below
+  int64_t h_stride = 0, w_stride = 0, t_stride = 0, c_stride = 0, xp_stride = 0;
   uint8_t* gused = nullptr;  // n
   uint8_t* tused = nullptr;  // m
   void* q = nullptr;      // n work vector (compute type)
@@ -86,8 +109,8 @@ struct Ctx {
   double* part_val = nullptr;  // argmax partials
   int32_t* part_idx = nullptr;
   int part_cap = 0;
-  DevState* st = nullptr;
-  DevState* st_host = nullptr;  // pinned mirror
+  DevState* st = nullptr;       // nprob entries
+  DevState* st_host = nullptr;  // pinned mirror (nprob entries)
   double* pw_single = nullptr;   // projected work space, one problem of size <= kmax
   double* pw_batched = nullptr;  // all problem sizes 1..kmax (histories), on first use
   int64_t* pw_offsets = nullptr; // device offset table of pw_batched
@@ -134,19 +157,26 @@ template <typename XT, typename YT>
 void launch_spmv(const DevCsr& A, int vt, const XT* x, YT* y, cudaStream_t s, int num_sms);
 
 // Elimination coefficients computed inside the sparse product (see
-// k_spmv_pivots): cnt pivot rows piv, pivot-row matrix T.
+// k_spmv_pivots): cnt pivot rows piv per problem, pivot-row inverse Tinv.
+// Problem p's arrays sit at base + p * stride.
 struct PivotCoef {
   const int32_t* piv;
+  int64_t piv_stride;
   int cnt;
   const void* B;     // the basis (basis type), leading dimension ldb: T(i,j) = B(piv_i, j)
   int64_t ldb;
   double* coef;      // cnt coefficients (FP64 copy)
+  int64_t coef_stride;
   double* hess_col;  // cnt Hessenberg entries of this column (W(:,k) or H(:,k))
+  int64_t hess_stride;
   void* xp;          // partial sums, npiv_blocks x ldi (accumulation type)
+  int64_t xp_stride;
   void* Tinv;        // column-major inverse of T (basis type = accumulation type), ld ldi
   int64_t ldi;
+  int64_t tinv_stride;
   DevState* st;
-  int npiv_blocks;   // set by the launcher
+  int nprob;
+  int npiv_blocks;   // per problem, set by the launcher
 };
 template <typename XT, typename YT>
 void launch_spmv_pivots(const DevCsr& A, int vt, const XT* x, YT* y, PivotCoef pc,
@@ -157,37 +187,59 @@ cudaError_t build_csr_pair(int64_t m, int64_t n, const int64_t* rp, const int32_
                            const double* vv, int vt, DevCsr* A, DevCsr* AT, cudaStream_t s);
 void free_csr(DevCsr* c);
 
-// Basis-step kernels; see lslu_basis.cu.
+// Basis-step kernels; see lslu_basis.cu.  Problem p's arrays sit at
+// base + p * stride; tile_prob maps every kTile rows to their problem
+// (nullptr when nprob == 1).
 struct PivotArgs {
   int32_t* piv_list;     // pivot list (gp or tp)
+  int64_t piv_stride;
   int piv_slot;          // index written in piv_list (== number of earlier vectors)
   uint8_t* used;         // pivoted-row mask
   double* hess_entry;    // where the pivot value goes (W(k,k) or H(k+1,k)); may be null
+  int64_t hess_stride;
   int64_t ldt;           // leading dimension of Tinv
   int breakdown_code;    // status to set when no non-zero candidate is left
   int k_on_breakdown;    // k_done to record on breakdown
   int is_init;           // 1 for the r0 pivot (records beta)
-  void* Tinv;            // inverse of T (basis type, row-major): its diagonal entry is set
+  void* Tinv;            // inverse of T (basis type, column-major): its diagonal entry is set
+  int64_t tinv_stride;
+  const double* coef;    // elimination coefficients (cnt per problem)
+  int64_t coef_stride;
+  int nprob;
+  const int32_t* tile_prob;
 };
 
 template <typename XT, typename BT, typename CT>
-void launch_eliminate_argmax(const XT* x, const BT* B, int64_t ld, int cnt, const double* coef,
-                             int64_t rows, CT* v, const PivotArgs& pa, double* part_val,
-                             int32_t* part_idx, int part_cap, DevState* st, cudaStream_t s,
-                             int num_sms);
+void launch_eliminate_argmax(const XT* x, const BT* B, int64_t ld, int cnt, int64_t rows, CT* v,
+                             const PivotArgs& pa, double* part_val, int32_t* part_idx,
+                             int part_cap, DevState* st, cudaStream_t s, int num_sms);
+
+// Exact pivot of r0 for every problem (largest |r0|, lowest index; FP64):
+// sets beta, the first row pivot, its mask entry and T_D^-1(0,0).
+template <typename BT>
+void launch_init_pivot(const double* r0, int64_t rows, const PivotArgs& pa, DevState* st,
+                       cudaStream_t s, int num_sms);
 
 template <typename CT, typename BT>
-void launch_scale(const CT* v, BT* out, int64_t rows, DevState* st, cudaStream_t s, int num_sms);
+void launch_scale(const CT* v, BT* out, int64_t rows, DevState* st, int nprob,
+                  const int32_t* tile_prob, cudaStream_t s, int num_sms);
 
 void launch_residual0(const double* b, const double* Ax0, double* r0, int64_t m, cudaStream_t s);
-void launch_init_state(DevState* st, int K, cudaStream_t s);
+void launch_init_state(DevState* st, int nprob, int K, cudaStream_t s);
+void launch_scatter(const double* src, const int32_t* map, int64_t count, double* dst,
+                    cudaStream_t s);
+void launch_gather(const double* src, const int32_t* map, int64_t count, double* dst,
+                   cudaStream_t s);
 
 // Projected problem (lslu_projected.cu).
 struct ProjArgs {
   const double* H;  // ld = ldh
   int64_t ldh;
-  double beta_val;          // used when beta_ptr is null
-  const double* beta_ptr;   // device beta (from the solve) or null
+  double beta_val;          // used when st is null (otherwise st[p].beta)
+  const int64_t* mvec;      // rows of each batch entry (weighted GCV), or null: m
+  int nbatch;               // > 1: one final problem per batch entry p (strides below)
+  int64_t strideH;          // batch stride of H
+  int64_t ldy;              // batch stride of y
   int rule;
   double lambda;
   int64_t m;
@@ -201,8 +253,8 @@ struct ProjArgs {
   int64_t ldc;
   double* lam_out;  // per problem (may be null), index k-1
   double* res_out;  // per problem (may be null), index k-1
-  const DevState* st;  // if non-null, problems with k > k_done are skipped and
-                       // the y problem uses k = k_done
+  const DevState* st;  // if non-null (per batch entry), problems with k > k_done
+                       // are skipped and the y problem uses k = k_done
   unsigned long long* tstamp;  // optional phase timestamps (ns) of the last problem
 };
 cudaError_t launch_projected(const ProjArgs& a, ProjWork& w, cudaStream_t s);
@@ -210,8 +262,9 @@ int64_t projected_slot_doubles(int kk, int CL);
 int projected_cluster_size();
 
 template <typename BT>
-void launch_recombine(const BT* L, int64_t ldl, const double* y, const double* x0, double* x,
-                      int64_t n, const DevState* st, int K, cudaStream_t s, int num_sms);
+void launch_recombine(const BT* L, int64_t ldl, const double* y, int64_t ldy, const double* x0,
+                      double* x, int64_t n, const DevState* st, int nprob,
+                      const int32_t* tile_prob, int K, cudaStream_t s, int num_sms);
 
 }  // namespace lslu
 

@@ -280,12 +280,15 @@ __global__ void __launch_bounds__(kT) k_projected(ProjArgs a, ProjWork w) {
   const int CL = (int)cluster.num_blocks();
   const int rank = (int)cluster.block_rank();
   const int prob = blockIdx.x / CL;
-  const int kk = a.k_first + prob;
-  const int kdone = a.st ? a.st->k_done : a.k_last;
+  const bool batch = a.nbatch > 1;   // one final problem per batch entry
+  const int p = batch ? prob : 0;
+  const int kk = batch ? a.k_last : a.k_first + prob;
+  const DevState* sp = a.st ? a.st + p : nullptr;
+  const int kdone = sp ? sp->k_done : a.k_last;
   const bool is_final = (kk == a.k_last);
   const int k = is_final ? min(kk, kdone) : kk;
-  double* lam_o = a.lam_out ? a.lam_out + (kk - 1) : nullptr;
-  double* res_o = a.res_out ? a.res_out + (kk - 1) : nullptr;
+  double* lam_o = a.lam_out ? a.lam_out + (batch ? p : kk - 1) : nullptr;
+  double* res_o = a.res_out ? a.res_out + (batch ? p : kk - 1) : nullptr;
   if (k <= 0 || (!is_final && kk > kdone)) {
     if (rank == 0 && threadIdx.x == 0) {
       if (lam_o) *lam_o = 0.0;
@@ -293,8 +296,10 @@ __global__ void __launch_bounds__(kT) k_projected(ProjArgs a, ProjWork w) {
     }
     return;  // the whole cluster leaves: no barrier is left waiting
   }
-  const double beta = a.beta_ptr ? *a.beta_ptr : a.beta_val;
-  Slots S = carve(w.base + (w.packed ? w.offsets[kk] : 0), kk, CL);
+  const double beta = sp ? sp->beta : a.beta_val;
+  const double* Hp = a.H + (int64_t)p * a.strideH;
+  double* yp = a.y ? a.y + (int64_t)p * a.ldy : nullptr;
+  Slots S = carve(w.base + (w.packed ? w.offsets[kk] : (int64_t)p * w.slot_stride), kk, CL);
   const int64_t ld = k + 1;
   const int kmax = a.k_last;
   // shared layout: [al, be, sig, c2, vls : 5 x (kmax+1)] [t2 : 2 x (kmax+1)]
@@ -318,7 +323,7 @@ __global__ void __launch_bounds__(kT) k_projected(ProjArgs a, ProjWork w) {
 
   for (int c = rank; c < k; c += CL) {
     double* cp = col(c);
-    for (int r = tid; r <= k; r += nt) cp[r] = a.H[r + (int64_t)c * a.ldh];
+    for (int r = tid; r <= k; r += nt) cp[r] = Hp[r + (int64_t)c * a.ldh];
   }
   __syncthreads();
 
@@ -554,7 +559,8 @@ __global__ void __launch_bounds__(kT) k_projected(ProjArgs a, ProjWork w) {
   }
   __syncthreads();
   const bool gcv = (a.rule == LSLU_LAMBDA_GCV || a.rule == LSLU_LAMBDA_WGCV) && sig[0] > 0.0;
-  const double omega = a.rule == LSLU_LAMBDA_WGCV ? (double)(k + 1) / (double)a.m : 1.0;
+  const double mrows = a.mvec ? (double)a.mvec[p] : (double)a.m;
+  const double omega = a.rule == LSLU_LAMBDA_WGCV ? (double)(k + 1) / mrows : 1.0;
   const double s1 = sig[0];
   // ---- 4. lambda: the grid is shared by the cluster, the refinement by CTA 0
   double* Gv = S.gv;
@@ -623,7 +629,7 @@ __global__ void __launch_bounds__(kT) k_projected(ProjArgs a, ProjWork w) {
     for (int i = tid; i < k; i += nt) a.sig[(int64_t)prob * a.ldsig + i] = sig[i];
   if (a.cvec)
     for (int i = tid; i <= k; i += nt) a.cvec[(int64_t)prob * a.ldc + i] = sqrt(c2[i]);
-  if (!(is_final && a.want_y)) return;
+  if (!(is_final && a.want_y && yp)) return;
 
   if (ts) ts[5] = gtimer();
   // ---- 6. y = Q z ----------------------------------------------------------
@@ -666,7 +672,7 @@ __global__ void __launch_bounds__(kT) k_projected(ProjArgs a, ProjWork w) {
     for (int c = j + tid; c < k; c += nt) z[c] = fma(-tr * s, ldg_cg(S.Qs + (int64_t)j * k + c), z[c]);
     __syncthreads();
   }
-  for (int i = tid; i < k; i += nt) a.y[i] = z[i];
+  for (int i = tid; i < k; i += nt) yp[i] = z[i];
   if (ts) ts[7] = gtimer();
 }
 
@@ -708,9 +714,13 @@ int projected_cluster_size() {
 }
 
 cudaError_t launch_projected(const ProjArgs& a, ProjWork& w, cudaStream_t s) {
-  const int nprob = a.k_last - a.k_first + 1;
+  // one cluster per projected problem: every k of k_first..k_last (histories),
+  // or one final problem per batch entry
+  const bool batch = a.nbatch > 1;
+  if (batch && (a.k_first != a.k_last || w.packed)) return cudaErrorInvalidValue;
+  const int nprob = batch ? a.nbatch : a.k_last - a.k_first + 1;
   if (nprob <= 0) return cudaSuccess;
-  if (nprob > 1 && !w.packed) return cudaErrorInvalidValue;
+  if (!batch && nprob > 1 && !w.packed) return cudaErrorInvalidValue;
   const int CL = w.cluster;
   const int kmax = a.k_last;
   const int ncl = (kmax + CL - 1) / CL;

@@ -31,7 +31,7 @@ struct ValTraits<float> {
 };
 template <>
 struct ValTraits<__nv_bfloat16> {
-  static constexpr int kChunk = 8;
+  static constexpr int kChunk = 4;
 };
 
 template <typename AT>
@@ -68,13 +68,13 @@ __device__ __forceinline__ void load_vals_cs(const float* p, AT (&v)[4]) {
   v[0] = (AT)a0; v[1] = (AT)a1; v[2] = (AT)a2; v[3] = (AT)a3;
 }
 template <typename AT>
-__device__ __forceinline__ void load_vals_cs(const __nv_bfloat16* p, AT (&v)[8]) {
-  uint32_t w[4];
-  asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
-               : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3])
+__device__ __forceinline__ void load_vals_cs(const __nv_bfloat16* p, AT (&v)[4]) {
+  uint32_t w[2];
+  asm volatile("ld.global.nc.L1::no_allocate.v2.u32 {%0,%1}, [%2];"
+               : "=r"(w[0]), "=r"(w[1])
                : "l"(p));
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < 2; ++i) {
     v[2 * i] = (AT)__uint_as_float(w[i] << 16);
     v[2 * i + 1] = (AT)__uint_as_float(w[i] & 0xffff0000u);
   }
@@ -147,25 +147,30 @@ __global__ void __launch_bounds__(256) k_spmv_pivots(int64_t rows, const int32_t
   __shared__ int last;
   __shared__ YT xs[8];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if ((int)blockIdx.x < pc.npiv_blocks) {
-    if (pc.st->status != LSLU_OK) return;
-    YT* Tinv = reinterpret_cast<YT*>(pc.Tinv);
-    YT* part = reinterpret_cast<YT*>(pc.xp);
+  const int npiv_all = pc.npiv_blocks * pc.nprob;
+  if ((int)blockIdx.x < npiv_all) {
+    const int p = blockIdx.x / pc.npiv_blocks;  // problem of this pivot block
+    const int bb = blockIdx.x - p * pc.npiv_blocks;
+    DevState& sp = pc.st[p];
+    if (sp.status != LSLU_OK) return;
+    YT* Tinv = reinterpret_cast<YT*>(pc.Tinv) + (int64_t)p * pc.tinv_stride;
+    YT* part = reinterpret_cast<YT*>(pc.xp) + (int64_t)p * pc.xp_stride;
+    const int32_t* piv = pc.piv + (int64_t)p * pc.piv_stride;
     const int cnt = pc.cnt, nr = cnt - 1;
-    const int j0 = blockIdx.x * 8;
+    const int j0 = bb * 8;
     const int j = j0 + warp;
     if (j < cnt) {
       if (j < nr) {
         YT a = 0;
         // T(nr, l) = b_l(piv_nr): the newest pivot row of the earlier basis vectors
-        const YT* brow = reinterpret_cast<const YT*>(pc.B) + pc.piv[nr];
+        const YT* brow = reinterpret_cast<const YT*>(pc.B) + piv[nr];
         const YT* tcol = Tinv + (int64_t)j * pc.ldi;
         for (int l = j + lane; l < nr; l += 32)
           a = fma(__ldcg(brow + (int64_t)l * pc.ldb), __ldcg(tcol + l), a);
         a = warp_sum(a);
         if (lane == 0) __stcg(Tinv + (int64_t)j * pc.ldi + nr, -a);
       }
-      const YT yp = row_dot<VT, XT, YT>(pc.piv[j], rp, rl, col, val, x, lane);
+      const YT yp = row_dot<VT, XT, YT>(piv[j], rp, rl, col, val, x, lane);
       if (lane == 0) xs[warp] = yp;
     } else if (lane == 0) {
       xs[warp] = 0;
@@ -177,25 +182,27 @@ __global__ void __launch_bounds__(256) k_spmv_pivots(int64_t rows, const int32_t
       YT acc = 0;
       for (int w = 0; w < jn; ++w)
         if (i >= j0 + w) acc = fma(__ldcg(Tinv + (int64_t)(j0 + w) * pc.ldi + i), xs[w], acc);
-      __stcg(part + (int64_t)blockIdx.x * pc.ldi + i, acc);
+      __stcg(part + (int64_t)bb * pc.ldi + i, acc);
     }
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) last = (atomicAdd(&pc.st->ticket2, 1) == pc.npiv_blocks - 1);
+    if (threadIdx.x == 0) last = (atomicAdd(&sp.ticket2, 1) == pc.npiv_blocks - 1);
     __syncthreads();
     if (!last) return;
     __threadfence();
-    if (threadIdx.x == 0) pc.st->ticket2 = 0;
+    if (threadIdx.x == 0) sp.ticket2 = 0;
+    double* coef = pc.coef + (int64_t)p * pc.coef_stride;
+    double* hess = pc.hess_col ? pc.hess_col + (int64_t)p * pc.hess_stride : nullptr;
     for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
       YT acc = 0;
       const int bmax = i / 8;  // blocks whose columns start at or before row i
-      for (int bb = 0; bb <= bmax; ++bb) acc += __ldcg(part + (int64_t)bb * pc.ldi + i);
-      pc.coef[i] = (double)acc;
-      if (pc.hess_col) pc.hess_col[i] = (double)acc;
+      for (int b2 = 0; b2 <= bmax; ++b2) acc += __ldcg(part + (int64_t)b2 * pc.ldi + i);
+      coef[i] = (double)acc;
+      if (hess) hess[i] = (double)acc;
     }
     return;
   }
-  const int64_t row = (int64_t)(blockIdx.x - pc.npiv_blocks) * 8 + warp;
+  const int64_t row = (int64_t)(blockIdx.x - npiv_all) * 8 + warp;
   if (row >= rows) return;
   const YT acc = row_dot<VT, XT, YT>(row, rp, rl, col, val, x, lane);
   if (lane == 0) y[row] = acc;
@@ -212,7 +219,7 @@ void spmv_typed(const DevCsr& A, const XT* x, YT* y, cudaStream_t s) {
 
 template <typename VT, typename XT, typename YT>
 void spmv_pivots_typed(const DevCsr& A, const XT* x, YT* y, const PivotCoef& pc, cudaStream_t s) {
-  const int64_t blocks = pc.npiv_blocks + (A.rows + 7) / 8;
+  const int64_t blocks = (int64_t)pc.npiv_blocks * pc.nprob + (A.rows + 7) / 8;
   k_spmv_pivots<VT, XT, YT><<<(unsigned)blocks, 256, 0, s>>>(
       A.rows, A.row_ptr, A.row_len, A.col, reinterpret_cast<const VT*>(A.val), x, y, pc);
 }

@@ -25,7 +25,7 @@ HOST, DEVICE = 0, 1
 
 EXPORTS = ("lslu_create", "lslu_solve", "lslu_get_state", "lslu_spmv", "lslu_projected",
            "lslu_projected_noalloc", "lslu_profile", "lslu_timing", "lslu_last_launch_count",
-           "lslu_error_string", "lslu_destroy")
+           "lslu_error_string", "lslu_destroy", "lslu_create_batched", "lslu_solve_batched")
 
 _lib = None
 
@@ -68,6 +68,11 @@ def load(path: str | None = None):
     lib.lslu_last_launch_count.restype = i64
     lib.lslu_error_string.argtypes = [vp]
     lib.lslu_error_string.restype = ctypes.c_char_p
+    lib.lslu_create_batched.argtypes = [i32, vp, vp, vp, vp, vp, i32, i32, vp,
+                                        ctypes.POINTER(vp)]
+    lib.lslu_create_batched.restype = i32
+    lib.lslu_solve_batched.argtypes = [vp, vp, i32, i32, f64, i32, vp, vp, vp, vp, vp]
+    lib.lslu_solve_batched.restype = i32
     lib.lslu_destroy.argtypes = [vp]
     lib.lslu_destroy.restype = None
     _lib = lib
@@ -213,6 +218,95 @@ def projected_noalloc(H, beta, rule, lam, m, y=None, sigma=None, c=None, lam_out
                                     _ptr(lam_out), _ptr(resid_out), stream)
     if st != OK:
         raise LsluError(st, lib.lslu_error_string(None).decode())
+
+
+class BatchedSolver:
+    """One handle over several independent problems solved by one launch
+    sequence (lslu_create_batched).  csr_list holds (m, n, row_ptr, col_idx,
+    vals) per problem in the problem's own index space; they are stacked into
+    one block-diagonal host CSR here (marshalling only)."""
+
+    def __init__(self, csr_list, value_type="f32", max_iter=150, stream=None):
+        self.lib = load()
+        self.nprob = len(csr_list)
+        self.value_type = value_type
+        self.max_iter = int(max_iter)
+        ms = [int(c[0]) for c in csr_list]
+        ns = [int(c[1]) for c in csr_list]
+        self.row_off = np.concatenate([[0], np.cumsum(ms)]).astype(np.int64)
+        self.col_off = np.concatenate([[0], np.cumsum(ns)]).astype(np.int64)
+        rps, cis, vvs = [np.zeros(1, np.int64)], [], []
+        base = 0
+        for p, (m, n, rp, ci, vv) in enumerate(csr_list):
+            rp = np.asarray(rp, dtype=np.int64)
+            rps.append(rp[1:] + base)
+            base += int(rp[-1])
+            cis.append(np.asarray(ci, dtype=np.int64) + self.col_off[p])
+            vvs.append(np.asarray(vv, dtype=np.float64))
+        row_ptr = np.ascontiguousarray(np.concatenate(rps), dtype=np.int64)
+        col_idx = np.ascontiguousarray(np.concatenate(cis), dtype=np.int32)
+        vals = np.ascontiguousarray(np.concatenate(vvs), dtype=np.float64)
+        h = ctypes.c_void_p()
+        st = self.lib.lslu_create_batched(self.nprob, _ptr(self.row_off), _ptr(self.col_off),
+                                          _ptr(row_ptr), _ptr(col_idx), _ptr(vals),
+                                          VALUE_TYPES[value_type], self.max_iter, stream,
+                                          ctypes.byref(h))
+        if st != OK:
+            raise LsluError(st, self.lib.lslu_error_string(None).decode())
+        self.h = h
+
+    def solve(self, b, K, rule="gcv", lam=0.0):
+        """b: the problems' data concatenated (host).  Returns per-problem lists
+        of x, g, t, k_done and status."""
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        P = self.nprob
+        x = np.zeros(int(self.col_off[-1]))
+        gp = np.zeros((P, K), dtype=np.int32)
+        tp = np.zeros((P, K + 1), dtype=np.int32)
+        kd = np.zeros(P, dtype=np.int32)
+        sv = np.zeros(P, dtype=np.int32)
+        st = self.lib.lslu_solve_batched(self.h, _ptr(b), int(K), RULES[rule], float(lam), HOST,
+                                         _ptr(x), _ptr(gp), _ptr(tp), _ptr(kd), _ptr(sv))
+        if st != OK:
+            raise LsluError(st, self.lib.lslu_error_string(self.h).decode())
+        co = self.col_off
+        return dict(x=[x[co[p]:co[p + 1]] for p in range(P)], gp=gp, tp=tp, k_done=kd,
+                    status=sv)
+
+    def solve_device(self, b, x_out, K, rule="gcv", lam=0.0, gp=None, tp=None, k_done=None,
+                     status=None):
+        """Device buffers (torch tensors) in and out."""
+        st = self.lib.lslu_solve_batched(self.h, _ptr(b), int(K), RULES[rule], float(lam),
+                                         DEVICE, _ptr(x_out), _ptr(gp), _ptr(tp), _ptr(k_done),
+                                         _ptr(status))
+        if st != OK:
+            raise LsluError(st, self.lib.lslu_error_string(self.h).decode())
+
+    def last_launch_count(self):
+        return int(self.lib.lslu_last_launch_count(self.h))
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.lib.lslu_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def from_problems(Ps, value_type="f32", max_iter=150, stream=None):
+    """Batched solver over several tomography problems."""
+    return BatchedSolver([(P.m, P.n, P.row_ptr, P.col_idx, P.vals) for P in Ps],
+                         value_type=value_type, max_iter=max_iter, stream=stream)
 
 
 def from_problem(P, value_type="f32", max_iter=300):

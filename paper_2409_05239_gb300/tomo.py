@@ -188,11 +188,11 @@ def make_problem(N: int, n_ang: int, p: int, n_ellipses: int, eta: float,
 # Workloads: image size N, angles, rays per angle, ellipses, noise levels.
 CONFIGS = {
     # 32x32 image, 45 angles x 46 rays, 5 ellipses, 1% noise, FP64, 50 iterations
-    "ct32": dict(N=32, n_ang=45, p=46, n_ellipses=5, etas=(0.01,), config=1, K=50),
+    "ct32": dict(N=32, n_ang=45, p=46, n_ellipses=5, etas=(0.01,), seed_base=1000, K=50),
     # 256x256 image, 180 angles x 362 rays, 5 ellipses, 1% noise, FP32, 200 iterations
-    "ct256": dict(N=256, n_ang=180, p=362, n_ellipses=5, etas=(0.01,), config=2, K=200),
+    "ct256": dict(N=256, n_ang=180, p=362, n_ellipses=5, etas=(0.01,), seed_base=2000, K=200),
     # 512x512 image, 360 angles x 724 rays, 20 ellipses, 0.5% and 2% noise, 300 iterations
-    "ct512": dict(N=512, n_ang=360, p=724, n_ellipses=20, etas=(0.005, 0.02), config=3, K=300),
+    "ct512": dict(N=512, n_ang=360, p=724, n_ellipses=20, etas=(0.005, 0.02), seed_base=3000, K=300),
 }
 
 
@@ -200,7 +200,7 @@ def make_config(name: str, instance: int = 0, eta: float | None = None) -> TomoP
     c = CONFIGS[name]
     e = c["etas"][0] if eta is None else eta
     return make_problem(c["N"], c["n_ang"], c["p"], c["n_ellipses"], e,
-                        seed=1000 * c["config"] + instance)
+                        seed=c["seed_base"] + instance)
 
 
 def round_values(vals: np.ndarray, value_type: str) -> np.ndarray:
@@ -227,3 +227,41 @@ def bf16_bits(vals: np.ndarray) -> np.ndarray:
     """uint16 bit patterns of round_values(vals, 'bf16')."""
     r = round_values(vals, "bf16").astype(np.float32)
     return (r.view(np.uint32) >> 16).astype(np.uint16)
+
+
+def make_uneven_batch(count: int = 64, seed: int = 4000, N_range=(64, 256),
+                      ang_range=(30, 180), eta_range=(0.005, 0.03),
+                      n_ellipses: int = 5) -> list[TomoProblem]:
+    """Independent problems of uneven size for a batched solve: image side N
+    and angle count drawn uniformly from the inclusive ranges, round(1.41 N)
+    rays per angle, and each problem's own seeded phantom and noise level
+    (uniform in eta_range)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for i in range(count):
+        N = int(rng.integers(N_range[0], N_range[1] + 1))
+        n_ang = int(rng.integers(ang_range[0], ang_range[1] + 1))
+        eta = float(rng.uniform(eta_range[0], eta_range[1]))
+        out.append(make_problem(N, n_ang, int(round(1.41 * N)), n_ellipses, eta,
+                                seed=seed + 10 * (i + 1)))
+    return out
+
+
+def make_shared_rhs(name: str = "ct256", nrhs: int = 16, seed: int = 5000) -> list[TomoProblem]:
+    """nrhs right-hand sides for one projector: the workload's A with a
+    different seeded phantom and noise draw per right-hand side."""
+    c = CONFIGS[name]
+    base = make_problem(c["N"], c["n_ang"], c["p"], c["n_ellipses"], c["etas"][0], seed)
+    out = [base]
+    for r in range(1, nrhs):
+        rng = np.random.Generator(np.random.PCG64(seed + 10 * r))
+        x_true = ellipse_phantom(c["N"], c["n_ellipses"], rng)
+        b_clean = csr_matvec_f64(base.row_ptr, base.col_idx, base.vals, x_true)
+        nrng = np.random.Generator(np.random.PCG64(seed + 10 * r + 1))
+        z = nrng.standard_normal(b_clean.shape[0])
+        e = c["etas"][0] * np.linalg.norm(b_clean) * z / np.linalg.norm(z)
+        out.append(TomoProblem(N=base.N, n_ang=base.n_ang, p=base.p, m=base.m, n=base.n,
+                               row_ptr=base.row_ptr, col_idx=base.col_idx, vals=base.vals,
+                               x_true=x_true, b_clean=b_clean, b=b_clean + e,
+                               eta=base.eta, seed=seed + 10 * r))
+    return out

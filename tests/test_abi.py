@@ -74,6 +74,36 @@ def test_create_rejects_bad_arguments_without_gpu(lib):
     assert st == lslu.ERR_INVALID_ARG and b"non-finite" in lib.lslu_error_string(None)
 
 
+def test_create_batched_rejects_bad_arguments_without_gpu(lib):
+    """Batch layout checks run before any CUDA call."""
+    import numpy as np
+
+    h = ctypes.c_void_p()
+    ro = np.array([0, 1, 2], dtype=np.int64)
+    co = np.array([0, 1, 2], dtype=np.int64)
+    rp = np.array([0, 1, 2], dtype=np.int64)
+    v = np.array([1.0, 2.0])
+
+    def create(ro, co, ci, vt=1, nprob=2, v=v):
+        return lib.lslu_create_batched(nprob, ro.ctypes.data, co.ctypes.data, rp.ctypes.data,
+                                       ci.ctypes.data, v.ctypes.data, vt, 10, None,
+                                       ctypes.byref(h))
+
+    ok_ci = np.array([0, 1], dtype=np.int32)
+    # FP64 values are not batched
+    assert create(ro, co, ok_ci, vt=0) == lslu.ERR_INVALID_ARG and not h.value
+    assert b"FP32 or BF16" in lib.lslu_error_string(None)
+    # problem 1's row referencing problem 0's column
+    assert create(ro, co, np.array([0, 0], dtype=np.int32)) == lslu.ERR_INVALID_ARG
+    assert b"outside its problem" in lib.lslu_error_string(None)
+    # an empty problem
+    assert create(np.array([0, 2, 2], dtype=np.int64), co, ok_ci) == lslu.ERR_INVALID_ARG
+    assert create(ro, co, ok_ci, nprob=0) == lslu.ERR_INVALID_ARG
+    assert create(ro, co, ok_ci, v=np.array([1.0, np.inf])) == lslu.ERR_INVALID_ARG
+    assert lib.lslu_solve_batched(None, None, 1, 2, 0.0, 0, None, None, None, None,
+                                  None) == lslu.ERR_INVALID_ARG
+
+
 def test_null_handle_calls_fail_cleanly(lib):
     assert lib.lslu_solve(None, None, None, 1, 2, 0.0, 0, None, None, None, None, None,
                           None) == lslu.ERR_INVALID_ARG

@@ -1,0 +1,122 @@
+"""Batched Hybrid LSLU (lslu_create_batched / lslu_solve_batched).
+
+Every problem of a batch runs Algorithm 5 on its own: its pivots, lambda
+choice, breakdowns and x must equal those of a single-problem solve of the
+same problem with the same value type, bit for bit (the batched kernels do
+the same arithmetic in the same order per problem), and so must match the
+FP64 oracle to the mixed-precision tolerance of the single-problem path.
+"""
+import numpy as np
+import pytest
+
+import oracle.lslu_oracle as O
+from paper_2409_05239_gb300 import lslu, tomo
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2409_05239_gb300 import build
+
+    build.build()
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+@pytest.fixture(scope="module")
+def small_batch():
+    # uneven, ragged sizes (none a multiple of the 128-row tile)
+    return tomo.make_uneven_batch(count=6, seed=4100, N_range=(12, 40), ang_range=(8, 40))
+
+
+def single(P, vt, K, rule, lam=0.0, b=None):
+    with lslu.from_problem(P, vt, K) as s:
+        return s.solve(P.b if b is None else b, K, rule, lam)
+
+
+@pytest.mark.parametrize("vt", ["f32", "bf16"])
+@pytest.mark.parametrize("rule,lam", [("gcv", 0.0), ("wgcv", 0.0), ("fixed", 1e-2), ("none", 0.0)])
+def test_batched_equals_single(small_batch, vt, rule, lam):
+    K = 30
+    with lslu.from_problems(small_batch, vt, K) as bs:
+        r = bs.solve(np.concatenate([P.b for P in small_batch]), K, rule, lam)
+    for p, P in enumerate(small_batch):
+        s = single(P, vt, K, rule, lam)
+        assert r["status"][p] == s["status"] and r["k_done"][p] == s["k_done"]
+        assert np.array_equal(r["gp"][p], s["gp"]) and np.array_equal(r["tp"][p], s["tp"])
+        assert np.array_equal(r["x"][p], s["x"]), p
+
+
+def test_batched_vs_oracle(small_batch):
+    K = 30
+    with lslu.from_problems(small_batch, "f32", K) as bs:
+        r = bs.solve(np.concatenate([P.b for P in small_batch]), K, "gcv")
+    for p, P in enumerate(small_batch):
+        A = P.scipy(tomo.round_values(P.vals, "f32"))
+        ref = O.hybrid_lslu(A, P.b, None, K, "gcv", histories=False)
+        assert r["k_done"][p] == K
+        assert np.array_equal(r["gp"][p][:5], ref.gp[:5])
+        assert np.array_equal(r["tp"][p][:5], ref.tp[:5])
+        assert rel(r["x"][p], ref.x) <= 2e-4, p
+
+
+def test_breakdowns_stay_local(small_batch):
+    """A zero right-hand side (beta breakdown) and a problem with fewer
+    columns than K (runs out of pivots) stop only themselves."""
+    tiny = tomo.make_problem(4, 6, 6, 3, 0.01, seed=77)  # 16 pixels, 36 rays
+    probs = [small_batch[0], tiny, small_batch[1], small_batch[2]]
+    bs_ = [P.b for P in probs]
+    bs_[2] = np.zeros(probs[2].m)
+    K = 20
+    with lslu.from_problems(probs, "f32", K) as bs:
+        r = bs.solve(np.concatenate(bs_), K, "gcv")
+    for p, P in enumerate(probs):
+        s = single(P, "f32", K, "gcv", b=bs_[p])
+        assert r["status"][p] == s["status"] and r["k_done"][p] == s["k_done"], p
+        assert np.array_equal(r["gp"][p], s["gp"]) and np.array_equal(r["tp"][p], s["tp"])
+        assert np.array_equal(r["x"][p], s["x"]), p
+    assert r["status"][2] == lslu.BREAKDOWN_BETA and r["k_done"][2] == 0
+    assert np.all(r["x"][2] == 0.0) and np.all(r["gp"][2] == -1)
+    assert r["status"][1] in (lslu.BREAKDOWN_W, lslu.BREAKDOWN_H) and r["k_done"][1] <= 16
+    assert r["status"][0] == lslu.OK and r["k_done"][0] == K
+
+
+def test_single_problem_batch(small_batch):
+    P = small_batch[3]
+    with lslu.from_problems([P], "f32", 25) as bs:
+        r = bs.solve(P.b, 25, "gcv")
+    s = single(P, "f32", 25, "gcv")
+    assert np.array_equal(r["x"][0], s["x"]) and np.array_equal(r["gp"][0], s["gp"])
+
+
+def test_replay_and_device_pointers(small_batch):
+    import torch
+
+    K = 25
+    b = np.concatenate([P.b for P in small_batch])
+    with lslu.from_problems(small_batch, "f32", K) as bs:
+        a = bs.solve(b, K, "gcv")
+        c = bs.solve(b, K, "gcv")  # replays the captured graph
+        dev = torch.device("cuda", 0)
+        nP = len(small_batch)
+        bd = torch.tensor(b, dtype=torch.float64, device=dev)
+        xd = torch.zeros(sum(P.n for P in small_batch), dtype=torch.float64, device=dev)
+        gd = torch.zeros((nP, K), dtype=torch.int32, device=dev)
+        kd = torch.zeros(nP, dtype=torch.int32, device=dev)
+        bs.solve_device(bd, xd, K, "gcv", gp=gd, k_done=kd)
+        torch.cuda.synchronize()
+    xa = np.concatenate(a["x"])
+    assert np.array_equal(xa, np.concatenate(c["x"]))
+    assert np.array_equal(xa, xd.cpu().numpy())
+    assert np.array_equal(a["gp"], gd.cpu().numpy()) and np.array_equal(a["k_done"], kd.cpu().numpy())
+
+
+def test_fixed_lambda_validation(small_batch):
+    with lslu.from_problems(small_batch[:2], "f32", 5) as bs:
+        with pytest.raises(lslu.LsluError):
+            bs.solve(np.concatenate([P.b for P in small_batch[:2]]), 5, "fixed", -1.0)
+        with pytest.raises(lslu.LsluError):
+            bs.solve(np.concatenate([P.b for P in small_batch[:2]]), 6, "gcv")
