@@ -289,13 +289,20 @@ __global__ void __launch_bounds__(kThreads)
 // lowest index attaining it; the last block of the second pass records it.
 __global__ void k_r0_max(const double* __restrict__ r0, int64_t rows, const uint8_t* used,
                          const int32_t* tile_prob, DevState* st) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < rows;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    if (used[i]) continue;
-    const double a = fabs(r0[i]);
-    unsigned long long bits = (unsigned long long)__double_as_longlong(a);
-    if (a != a) bits = 0x7ff0000000000001ull;  // NaN above every number
-    if (bits) atomicMax(&st[tile_problem(tile_prob, i)].amax, bits);
+  // warp-uniform trip count: the 32 rows of a warp lie in one kTile tile, so
+  // one problem; the warp's maximum goes to that problem with one atomic
+  const int lane = threadIdx.x & 31;
+  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x - lane); i0 < rows;
+       i0 += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = i0 + lane;
+    unsigned long long bits = 0;
+    if (i < rows && !used[i]) {
+      const double a = fabs(r0[i]);
+      bits = (unsigned long long)__double_as_longlong(a);
+      if (a != a) bits = 0x7ff0000000000001ull;  // NaN above every number
+    }
+    bits = warp_max_u64(bits);
+    if (lane == 0 && bits) atomicMax(&st[tile_problem(tile_prob, i0)].amax, bits);
   }
 }
 

@@ -1,11 +1,13 @@
 // Sparse products of Algorithm 4: u = A l_k and q = A^T d_k.
 //
 // Both run on a row-major CSR: A^T is stored as its own (transposed) CSR, so
-// every output entry is one row dot product and no atomics are needed.  One
-// warp owns one row; lane j reads chunks j, j+32, ... of the row with 16-byte
-// vector loads (rows are padded to a multiple of kRowAlign entries), keeps a
-// private partial sum in chunk order and the warp adds the 32 partials with a
-// fixed butterfly, so results are bitwise reproducible run to run.
+// every output entry is one row dot product and no atomics are needed.  A
+// group of 16 lanes (half a warp) owns one row; lane j of the group reads the
+// 4-entry chunks j, j+16, j+32, ... of the row with vector loads (rows are
+// padded to a multiple of kRowAlign entries), two chunks per step so that
+// more loads are in flight, keeps a private partial sum in chunk order, and
+// the group adds its 16 partials with a fixed butterfly, so results are
+// bitwise reproducible run to run.
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 
@@ -19,25 +21,43 @@ namespace lslu {
 
 namespace {
 
+// Lanes per row and chunks per step; kMinBlocks bounds the registers so that
+// that many 256-thread blocks stay resident per SM.
+constexpr int kGroup = 16;
+constexpr int kRowsPerBlock = 256 / kGroup;
 template <typename VT>
 struct ValTraits;
 template <>
 struct ValTraits<double> {
-  static constexpr int kChunk = 4;  // entries per lane step
+  static constexpr int kChunk = 4;  // entries per chunk
+  static constexpr int kUnroll = 1;
+  static constexpr int kMinBlocks = 6;
 };
 template <>
 struct ValTraits<float> {
   static constexpr int kChunk = 4;
+  static constexpr int kUnroll = 2;
+  static constexpr int kMinBlocks = 6;
 };
 template <>
 struct ValTraits<__nv_bfloat16> {
   static constexpr int kChunk = 4;
+  static constexpr int kUnroll = 2;
+  static constexpr int kMinBlocks = 6;
 };
 
 template <typename AT>
 __device__ __forceinline__ AT warp_sum(AT v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum over each group of kGroup lanes (every lane of the warp must call it).
+template <typename AT>
+__device__ __forceinline__ AT group_sum(AT v) {
+#pragma unroll
+  for (int o = kGroup / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 
@@ -80,46 +100,73 @@ __device__ __forceinline__ void load_vals_cs(const __nv_bfloat16* p, AT (&v)[4])
   }
 }
 
-// Dot product of one CSR row with x, computed by one warp (result in every
-// lane).  Lane l takes chunks l, l+32, ... in order; the 32 partial sums are
-// combined by a fixed butterfly, so a row always gets the same bits.
+// Dot product of one CSR row with x, computed by one group of kGroup lanes
+// (result in every lane of the group; gl = lane index within the group; a
+// lane with len = 0 contributes nothing).  Lane gl takes chunks gl, gl+16,
+// ... in order (kUnroll chunks per step); the 16 partial sums are combined by
+// a fixed butterfly, so a row always gets the same bits.  Every lane of the
+// warp must call it (the butterfly is a full-warp shuffle).
 template <typename VT, typename XT, typename YT>
-__device__ __forceinline__ YT row_dot(int64_t row, const int32_t* __restrict__ rp,
-                                      const int32_t* __restrict__ rl,
-                                      const int32_t* __restrict__ col,
-                                      const VT* __restrict__ val, const XT* __restrict__ x,
-                                      int lane) {
+__device__ __forceinline__ YT row_dot_len(int32_t start, int32_t len,
+                                          const int32_t* __restrict__ col,
+                                          const VT* __restrict__ val, const XT* __restrict__ x,
+                                          int gl) {
   constexpr int C = ValTraits<VT>::kChunk;
-  const int32_t start = __ldg(rp + row);
-  const int32_t len = __ldg(rl + row);
+  constexpr int U = ValTraits<VT>::kUnroll;
+  constexpr int S = kGroup * C;  // entries between a lane's consecutive chunks
   YT acc = 0;
-  for (int32_t e = lane * C; e < len; e += 32 * C) {
-    const int32_t base = start + e;
-    int32_t cidx[C];
+  for (int32_t e = gl * C; e < len; e += U * S) {
+    int32_t cidx[U][C];
+    YT v[U][C];
+    bool has[U];
 #pragma unroll
-    for (int i = 0; i < C; i += 4) {
-      const int4 c4 = ld_stream(col + base + i);
-      cidx[i] = c4.x; cidx[i + 1] = c4.y; cidx[i + 2] = c4.z; cidx[i + 3] = c4.w;
+    for (int u = 0; u < U; ++u) {
+      has[u] = u == 0 || e + u * S < len;
+      if (has[u]) {
+        const int4 c4 = ld_stream(col + start + e + u * S);
+        cidx[u][0] = c4.x; cidx[u][1] = c4.y; cidx[u][2] = c4.z; cidx[u][3] = c4.w;
+        load_vals_cs<YT>(val + start + e + u * S, v[u]);
+      } else {
+#pragma unroll
+        for (int i = 0; i < C; ++i) v[u][i] = 0;
+      }
     }
-    YT v[C];
-    load_vals_cs<YT>(val + base, v);
+    XT xv[U][C];
 #pragma unroll
-    for (int i = 0; i < C; ++i) acc = fma(v[i], (YT)__ldg(x + cidx[i]), acc);
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int i = 0; i < C; ++i) xv[u][i] = has[u] ? __ldg(x + cidx[u][i]) : (XT)0;
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int i = 0; i < C; ++i) acc = fma(v[u][i], (YT)xv[u][i], acc);
   }
-  return warp_sum(acc);
+  return group_sum(acc);
 }
 
 template <typename VT, typename XT, typename YT>
-__global__ void __launch_bounds__(256) k_spmv(int64_t rows, const int32_t* __restrict__ rp,
-                                              const int32_t* __restrict__ rl,
-                                              const int32_t* __restrict__ col,
-                                              const VT* __restrict__ val, const XT* __restrict__ x,
-                                              YT* __restrict__ y) {
-  const int lane = threadIdx.x & 31;
-  const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (row >= rows) return;
-  const YT acc = row_dot<VT, XT, YT>(row, rp, rl, col, val, x, lane);
-  if (lane == 0) y[row] = acc;
+__device__ __forceinline__ YT row_dot(int64_t row, bool valid, const int32_t* __restrict__ rp,
+                                      const int32_t* __restrict__ rl,
+                                      const int32_t* __restrict__ col,
+                                      const VT* __restrict__ val, const XT* __restrict__ x,
+                                      int gl) {
+  const int32_t start = valid ? __ldg(rp + row) : 0;
+  const int32_t len = valid ? __ldg(rl + row) : 0;
+  return row_dot_len<VT, XT, YT>(start, len, col, val, x, gl);
+}
+
+template <typename VT, typename XT, typename YT>
+__global__ void __launch_bounds__(256, ValTraits<VT>::kMinBlocks)
+    k_spmv(int64_t rows, const int32_t* __restrict__ rp, const int32_t* __restrict__ rl,
+           const int32_t* __restrict__ col, const VT* __restrict__ val, const XT* __restrict__ x,
+           YT* __restrict__ y) {
+  const int gl = threadIdx.x & (kGroup - 1);
+  const int64_t row = (int64_t)blockIdx.x * kRowsPerBlock + threadIdx.x / kGroup;
+  if ((int64_t)blockIdx.x * kRowsPerBlock + (threadIdx.x & ~31) / kGroup >= rows)
+    return;  // the whole warp is past the last row
+  const bool valid = row < rows;
+  const YT acc = row_dot<VT, XT, YT>(row, valid, rp, rl, col, val, x, gl);
+  if (valid && gl == 0) y[row] = acc;
 }
 
 // y = A x plus the elimination coefficients of the next Hessenberg step,
@@ -138,7 +185,7 @@ __global__ void __launch_bounds__(256) k_spmv(int64_t rows, const int32_t* __res
 //      vector; the last pivot block to finish adds the partials in block order.
 // The remaining blocks compute the other rows of y meanwhile.
 template <typename VT, typename XT, typename YT>
-__global__ void __launch_bounds__(256) k_spmv_pivots(int64_t rows, const int32_t* __restrict__ rp,
+__global__ void __launch_bounds__(256, ValTraits<VT>::kMinBlocks) k_spmv_pivots(int64_t rows, const int32_t* __restrict__ rp,
                                                      const int32_t* __restrict__ rl,
                                                      const int32_t* __restrict__ col,
                                                      const VT* __restrict__ val,
@@ -170,7 +217,8 @@ __global__ void __launch_bounds__(256) k_spmv_pivots(int64_t rows, const int32_t
         a = warp_sum(a);
         if (lane == 0) __stcg(Tinv + (int64_t)j * pc.ldi + nr, -a);
       }
-      const YT yp = row_dot<VT, XT, YT>(piv[j], rp, rl, col, val, x, lane);
+      // both half-warps compute the pivot row (the same bits as its y entry)
+      const YT yp = row_dot<VT, XT, YT>(piv[j], true, rp, rl, col, val, x, lane & (kGroup - 1));
       if (lane == 0) xs[warp] = yp;
     } else if (lane == 0) {
       xs[warp] = 0;
@@ -202,24 +250,26 @@ __global__ void __launch_bounds__(256) k_spmv_pivots(int64_t rows, const int32_t
     }
     return;
   }
-  const int64_t row = (int64_t)(blockIdx.x - npiv_all) * 8 + warp;
-  if (row >= rows) return;
-  const YT acc = row_dot<VT, XT, YT>(row, rp, rl, col, val, x, lane);
-  if (lane == 0) y[row] = acc;
+  const int64_t b0 = (int64_t)(blockIdx.x - npiv_all) * kRowsPerBlock;
+  if (b0 + (threadIdx.x & ~31) / kGroup >= rows) return;  // whole warp past the end
+  const int64_t row = b0 + threadIdx.x / kGroup;
+  const bool valid = row < rows;
+  const YT acc = row_dot<VT, XT, YT>(row, valid, rp, rl, col, val, x, lane & (kGroup - 1));
+  if (valid && (lane & (kGroup - 1)) == 0) y[row] = acc;
 }
 
 template <typename VT, typename XT, typename YT>
 void spmv_typed(const DevCsr& A, const XT* x, YT* y, cudaStream_t s) {
   if (A.rows == 0) return;
-  const int wpb = 8;
-  const int64_t blocks = (A.rows + wpb - 1) / wpb;
-  k_spmv<VT, XT, YT><<<(unsigned)blocks, wpb * 32, 0, s>>>(
+  const int64_t blocks = (A.rows + kRowsPerBlock - 1) / kRowsPerBlock;
+  k_spmv<VT, XT, YT><<<(unsigned)blocks, 256, 0, s>>>(
       A.rows, A.row_ptr, A.row_len, A.col, reinterpret_cast<const VT*>(A.val), x, y);
 }
 
 template <typename VT, typename XT, typename YT>
 void spmv_pivots_typed(const DevCsr& A, const XT* x, YT* y, const PivotCoef& pc, cudaStream_t s) {
-  const int64_t blocks = (int64_t)pc.npiv_blocks * pc.nprob + (A.rows + 7) / 8;
+  const int64_t blocks =
+      (int64_t)pc.npiv_blocks * pc.nprob + (A.rows + kRowsPerBlock - 1) / kRowsPerBlock;
   k_spmv_pivots<VT, XT, YT><<<(unsigned)blocks, 256, 0, s>>>(
       A.rows, A.row_ptr, A.row_len, A.col, reinterpret_cast<const VT*>(A.val), x, y, pc);
 }

@@ -1,0 +1,71 @@
+"""Run Hybrid LSLU on a synthetic tomography workload and print one JSON line.
+
+    python -m paper_2409_05239_gb300.solve_once --workload ct512 --K 300
+    python -m paper_2409_05239_gb300.solve_once --batch 64 --K 150
+
+The first form builds one seeded problem of the named size (see tomo.CONFIGS)
+and solves it `--repeat` times; the second solves a batch of uneven problems
+(tomo.make_uneven_batch) through the batched entry points.  Meant for kernel
+profilers: with LSLU_NO_GRAPHS=1 in the environment every kernel is launched
+directly instead of from a captured CUDA graph.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="ct512")
+    ap.add_argument("--value-type", default="f32", choices=["f64", "f32", "bf16"])
+    ap.add_argument("--K", type=int, default=None)
+    ap.add_argument("--rule", default="gcv", choices=["none", "fixed", "gcv", "wgcv"])
+    ap.add_argument("--lam", type=float, default=0.0)
+    ap.add_argument("--repeat", type=int, default=1)
+    ap.add_argument("--batch", type=int, default=0, help="solve this many uneven problems")
+    a = ap.parse_args(argv)
+
+    import torch
+
+    from paper_2409_05239_gb300 import lslu, tomo
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev).cuda_stream
+    out = {}
+    if a.batch:
+        K = a.K or 150
+        Ps = tomo.make_uneven_batch(a.batch)
+        b = np.concatenate([P.b for P in Ps])
+        with lslu.from_problems(Ps, a.value_type, K, stream=stream) as s:
+            t0 = time.perf_counter()
+            for _ in range(a.repeat):
+                r = s.solve(b, K, a.rule, a.lam)
+            dt = (time.perf_counter() - t0) / a.repeat
+        errs = [np.linalg.norm(x - P.x_true) / np.linalg.norm(P.x_true)
+                for x, P in zip(r["x"], Ps)]
+        out = {"problems": a.batch, "K": K, "k_done_min": int(r["k_done"].min()),
+               "seconds_per_solve": dt, "rel_err_x_true_median": float(np.median(errs))}
+    else:
+        P = tomo.make_config(a.workload)
+        K = a.K or tomo.CONFIGS[a.workload]["K"]
+        with lslu.from_problem(P, a.value_type, K) as s:
+            t0 = time.perf_counter()
+            for _ in range(a.repeat):
+                r = s.solve(P.b, K, a.rule, a.lam)
+            dt = (time.perf_counter() - t0) / a.repeat
+            launches = s.last_launch_count()
+        out = {"workload": a.workload, "m": P.m, "n": P.n, "nnz": P.nnz, "K": K,
+               "k_done": r["k_done"], "status": r["status"], "launches": launches,
+               "seconds_per_solve": dt,
+               "rel_err_x_true": float(np.linalg.norm(r["x"] - P.x_true) /
+                                       np.linalg.norm(P.x_true))}
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()
