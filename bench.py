@@ -264,6 +264,63 @@ def batched_study(dev, K=150, count=64):
             "rel_err_x_true_max": float(np.max(errs))}
 
 
+def adjoint_study(dev, K=100):
+    """Differentiable solve on the 256x256 workload (FP32, fixed lambda = the
+    GCV choice at K): time of the forward solve and of the reverse-mode
+    derivative (lslu_adjoint) on the device, and the log-lambda derivative
+    against central differences of solves with the pivots replayed."""
+    import torch
+
+    from paper_2409_05239_gb300 import lslu
+
+    P = tomo.make_config("ct256")
+    stream = torch.cuda.current_stream(dev)
+    s = lslu.Solver(P.m, P.n, P.row_ptr, P.col_idx, P.vals, "f32", K, stream=stream.cuda_stream)
+    lam = float(s.solve(P.b, K, "gcv", histories=True)["lam_hist"][-1])
+    b_dev = torch.from_numpy(P.b).to(dev)
+    x_dev = torch.empty(P.n, dtype=torch.float64, device=dev)
+    xt = torch.from_numpy(P.x_true).to(dev)
+    bb = torch.empty(P.m, dtype=torch.float64, device=dev)
+    lb = torch.empty(1, dtype=torch.float64, device=dev)
+
+    def fwd():
+        s.solve_device(b_dev, x_dev, K, "fixed", lam)
+
+    def bwd():
+        s.adjoint_device(2.0 * (x_dev - xt), bb, lb)
+
+    fwd()
+    bwd()
+    torch.cuda.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    reps = 3
+    ms_f = ms_b = 0.0
+    for _ in range(reps):
+        e[0].record(stream)
+        fwd()
+        e[1].record(stream)
+        bwd()
+        e[2].record(stream)
+        torch.cuda.synchronize()
+        ms_f += e[0].elapsed_time(e[1]) / reps
+        ms_b += e[1].elapsed_time(e[2]) / reps
+    r = s.solve(P.b, K, "fixed", lam)
+    adj = s.adjoint(2.0 * (r["x"] - P.x_true))
+
+    def J(lm):
+        o = s.solve_fixed_pivots(P.b, K, r["gp"], r["tp"], "fixed", lm)
+        return float(np.sum((o["x"] - P.x_true) ** 2))
+
+    h = 1e-3
+    fd = (J(lam * np.exp(h)) - J(lam * np.exp(-h))) / (2 * h)
+    g = adj["lambda_bar"] * lam
+    s.close()
+    return {"workload": "ct256 (m=%d, n=%d), FP32, K=%d, lambda=%.4g (GCV at K)" % (P.m, P.n, K, lam),
+            "forward_ms": ms_f, "backward_ms": ms_b, "backward_over_forward": ms_b / ms_f,
+            "dJ_dloglam_adjoint": g, "dJ_dloglam_fd": fd,
+            "dJ_dloglam_rel_err_vs_fd": abs(g - fd) / abs(fd)}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -431,6 +488,7 @@ def run_gpu(args):
         out["precision_study"] = precision_study(P, K, rule, dev, x, args.value_type)
     if rank == 0 and not args.no_extras and world == 1:
         out["batched_study"] = batched_study(dev)
+        out["adjoint_study"] = adjoint_study(dev)
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         out["cpu_baseline"] = cpu_baseline(P, K, args.cpu_sample_s)
     if rank == 0:

@@ -138,6 +138,40 @@ lslu_status lslu_solve_batched(lslu_handle h, const double* b, int32_t K, int32_
                                int32_t* col_pivots, int32_t* row_pivots, int32_t* k_done,
                                int32_t* status);
 
+/* lslu_solve with the pivot lists given instead of searched: iteration k
+ * takes row col_pivots[k] of the L-side vector and row row_pivots[k+1] of the
+ * D-side vector as its pivots (row_pivots[0] for r0), whatever their
+ * magnitude.  With the pivots of an earlier solve this is the map whose
+ * derivative lslu_adjoint computes (finite differences with the pivots held
+ * fixed).  col_pivots: K distinct indices in [0, n); row_pivots: K+1 distinct
+ * indices in [0, m) (host or device per ptr_location, validated on the host).
+ * A zero entry at a given pivot is a breakdown.  Outputs x_out (n) and
+ * k_done (may be NULL) as in lslu_solve; the call leaves the same state for
+ * lslu_get_state and lslu_adjoint. */
+lslu_status lslu_solve_fixed_pivots(lslu_handle h, const double* b, const double* x0, int32_t K,
+                                    int32_t rule, double lambda, int32_t ptr_location,
+                                    const int32_t* col_pivots, const int32_t* row_pivots,
+                                    double* x_out, int32_t* k_done);
+
+/* Reverse-mode derivative of the last lslu_solve with its pivot lists held
+ * fixed (with g and t fixed, Algorithm 5 is a smooth map (b, lambda) -> x_K).
+ * Given x_bar = dJ/dx_K for any scalar loss J (n, FP64), returns
+ *   b_bar       m  FP64  dJ/db = (dx_K/db)^T x_bar
+ *   lambda_bar  1  FP64  dJ/dlambda for the lambda_K the solve used, taken as
+ *                        an independent parameter (may be NULL)
+ *   x0_bar      n  FP64  dJ/dx0 (may be NULL)
+ * all host or device per ptr_location.  The sweep runs the transposed steps
+ * on the device: per iteration two sparse products and passes over the
+ * stored bases (about twice the bytes of the forward solve); the projected
+ * adjoint uses a Cholesky factorisation of H^T H + lambda^2 I.  The first
+ * call allocates a work space of the size of the two bases.
+ * Errors: LSLU_ERR_INVALID_ARG for a batched handle, when the last
+ * lslu_solve did not complete all K iterations (or lslu_projected ran since),
+ * or when H^T H + lambda^2 I is not positive definite (lambda = 0 with a rank
+ * deficient H); LSLU_ERR_OOM; LSLU_ERR_CUDA. */
+lslu_status lslu_adjoint(lslu_handle h, const double* x_bar, int32_t ptr_location,
+                         double* b_bar, double* lambda_bar, double* x0_bar);
+
 /* Copy the state of the last lslu_solve (host or device per ptr_location;
  * any pointer may be NULL).  k = *k_done of that solve.
  *   H  (k+1) x k FP64 column-major, W k x k FP64 column-major, beta 1 FP64,

@@ -63,7 +63,9 @@ void destroy_ctx(lslu_ctx* c) {
                   c->TLi, c->TDi,
                   c->pw_single, c->pw_batched, c->pw_offsets, c->proj_out, c->y, c->sig,
                   c->cvec, c->xout, c->tile_prob_m, c->tile_prob_n, c->pad_m, c->pad_n,
-                  c->map_m, c->map_n, c->xin_pad, c->xout_user, c->mvec};
+                  c->map_m, c->map_n, c->xin_pad, c->xout_user, c->mvec,
+                  c->adj_Vb, c->adj_Zb, c->adj_vec, c->adj_small, c->adj_part,
+                  c->fixed_gp, c->fixed_tp};
   for (void* p : ptrs) cudaFree(p);
   if (c->st_host) cudaFreeHost(c->st_host);
   for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
@@ -122,6 +124,8 @@ lslu_status create_common(lslu_ctx* c, const int64_t* rp, const int32_t* ci, con
   CKC(cudaMalloc(&c->TDi, (size_t)P * c->t_stride * bb));
   CKC(dmalloc(&c->gp, (size_t)P * K));
   CKC(dmalloc(&c->tp, (size_t)P * (K + 1)));
+  CKC(dmalloc(&c->fixed_gp, (size_t)K));
+  CKC(dmalloc(&c->fixed_tp, (size_t)K + 1));
   CKC(dmalloc(&c->gused, n));
   CKC(dmalloc(&c->tused, m));
   CKC(cudaMalloc(&c->q, n * bb));
@@ -284,7 +288,7 @@ void collect_spmv_times(Ctx* c, int pairs) {
 // and x = x0 + L y.  Inputs are read from the handle's staging buffers.
 template <typename BT, typename CT>
 int64_t enqueue_solve(Ctx* c, cudaStream_t s, const double* db, const double* dx0, int K,
-                      int rule, double lam, bool hist, bool capturing) {
+                      int rule, double lam, bool hist, bool capturing, bool fixed) {
   c->ev_used = 0;
   const int64_t m = c->m, n = c->n;
   const int vt = c->value_type;
@@ -322,7 +326,8 @@ int64_t enqueue_solve(Ctx* c, cudaStream_t s, const double* db, const double* dx
   // beta = signed max-abs entry of r0 (exact, FP64), d_1 = r0 / beta, t(1)
   {
     PivotArgs pa{c->tp, c->kmax + 1, 0, c->tused, nullptr, 0, c->ldt, LSLU_BREAKDOWN_BETA,
-                 0, 1, c->TDi, c->t_stride, c->coef, c->c_stride, P, tpm};
+                 0, 1, c->TDi, c->t_stride, c->coef, c->c_stride, P, tpm,
+                 fixed ? c->fixed_tp : nullptr};
     launch_init_pivot<BT>(c->r0, m, pa, c->st, s, c->num_sms);
     launch_scale<double, BT>(c->r0, D, m, c->st, P, tpm, s, c->num_sms);
     launches += 3;
@@ -339,7 +344,8 @@ int64_t enqueue_solve(Ctx* c, cudaStream_t s, const double* db, const double* dx
     launch_spmv_pivots<BT, CT>(c->AT, vt, D + (int64_t)k * c->ldd, q, pcw, s);
     record_spmv_end(c, s, capturing, e0);
     PivotArgs paw{c->gp, c->kmax, k, c->gused, c->W + k + k * ldw, c->w_stride, c->ldt,
-                  LSLU_BREAKDOWN_W, k, 0, c->TLi, c->t_stride, c->coef, c->c_stride, P, tpn};
+                  LSLU_BREAKDOWN_W, k, 0, c->TLi, c->t_stride, c->coef, c->c_stride, P, tpn,
+                  fixed ? c->fixed_gp : nullptr};
     launch_eliminate_argmax<CT, BT, CT>(q, L, c->ldl, k, n, q, paw, c->part_val, c->part_idx,
                                         c->part_cap, c->st, s, c->num_sms);
     launch_scale<CT, BT>(q, L + (int64_t)k * c->ldl, n, c->st, P, tpn, s, c->num_sms);
@@ -353,7 +359,7 @@ int64_t enqueue_solve(Ctx* c, cudaStream_t s, const double* db, const double* dx
     record_spmv_end(c, s, capturing, e0);
     PivotArgs pah{c->tp, c->kmax + 1, k + 1, c->tused, c->H + (k + 1) + k * ldh, c->h_stride,
                   c->ldt, LSLU_BREAKDOWN_H, k, 0, c->TDi, c->t_stride, c->coef, c->c_stride, P,
-                  tpm};
+                  tpm, fixed ? c->fixed_tp : nullptr};
     launch_eliminate_argmax<CT, BT, CT>(u, D, c->ldd, k + 1, m, u, pah, c->part_val,
                                         c->part_idx, c->part_cap, c->st, s, c->num_sms);
     launch_scale<CT, BT>(u, D + (int64_t)(k + 1) * c->ldd, m, c->st, P, tpm, s, c->num_sms);
@@ -410,7 +416,7 @@ lslu_status ensure_batched_workspace(Ctx* c) {
 
 template <typename BT, typename CT>
 lslu_status solve_impl(Ctx* c, const double* db, const double* dx0, int K, int rule, double lam,
-                       bool hist) {
+                       bool hist, bool fixed = false) {
   if (hist) {
     lslu_status st = ensure_batched_workspace(c);
     if (st != LSLU_OK) return st;
@@ -419,7 +425,7 @@ lslu_status solve_impl(Ctx* c, const double* db, const double* dx0, int K, int r
   int ev_pairs = 0;
   if (c->profile) ensure_events(c, 4 * K + 8);
   if (!c->use_graphs) {
-    c->launches = enqueue_solve<BT, CT>(c, s, db, dx0, K, rule, lam, hist, false);
+    c->launches = enqueue_solve<BT, CT>(c, s, db, dx0, K, rule, lam, hist, false, fixed);
     ev_pairs = c->ev_used / 2;
     CK(cudaGetLastError());
   } else {
@@ -428,13 +434,13 @@ lslu_status solve_impl(Ctx* c, const double* db, const double* dx0, int K, int r
     Ctx::GraphEntry* ge = nullptr;
     for (auto& g : c->graphs)
       if (g.K == K && g.rule == rule && g.hist == (int)hist && g.has_x0 == has_x0 &&
-          g.lam == lam && g.prof == prof)
+          g.lam == lam && g.prof == prof && g.fixed == (int)fixed)
         ge = &g;
     if (!ge) {
       cudaGraph_t graph;
       CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
       const int64_t nl =
-          enqueue_solve<BT, CT>(c, c->cap_stream, db, dx0, K, rule, lam, hist, true);
+          enqueue_solve<BT, CT>(c, c->cap_stream, db, dx0, K, rule, lam, hist, true, fixed);
       const int pairs = c->ev_used / 2;
       cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
       if (e != cudaSuccess) {
@@ -450,7 +456,7 @@ lslu_status solve_impl(Ctx* c, const double* db, const double* dx0, int K, int r
         cudaGraphExecDestroy(c->graphs.front().exec);
         c->graphs.erase(c->graphs.begin());
       }
-      c->graphs.push_back({K, rule, (int)hist, has_x0, lam, exec, nl, prof, pairs});
+      c->graphs.push_back({K, rule, (int)hist, has_x0, lam, exec, nl, prof, pairs, (int)fixed});
       ge = &c->graphs.back();
     }
     CK(cudaEventRecord(c->ev_in, s));
@@ -483,11 +489,13 @@ lslu_status solve_impl(Ctx* c, const double* db, const double* dx0, int K, int r
 
 }  // namespace
 
-extern "C" lslu_status lslu_solve(lslu_handle h, const double* b, const double* x0, int32_t K,
-                                  int32_t rule, double lambda, int32_t ptr_location,
-                                  double* x_out, int32_t* col_pivots, int32_t* row_pivots,
-                                  double* lambda_hist, double* resid_hist, int32_t* k_done) {
-  Ctx* c = h;
+namespace {
+
+// lslu_solve, and lslu_solve_fixed_pivots when fix_g / fix_t are given
+lslu_status solve_entry(Ctx* c, const double* b, const double* x0, int32_t K, int32_t rule,
+                        double lambda, int32_t ptr_location, double* x_out, int32_t* col_pivots,
+                        int32_t* row_pivots, double* lambda_hist, double* resid_hist,
+                        int32_t* k_done, const int32_t* fix_g, const int32_t* fix_t) {
   if (!c) return set_err(nullptr, LSLU_ERR_INVALID_ARG, "NULL handle");
   if (c->map_m) return set_err(c, LSLU_ERR_INVALID_ARG, "batched handle: use lslu_solve_batched");
   if (K < 1 || K > c->kmax) return set_err(c, LSLU_ERR_INVALID_ARG, "K must be in [1, max_iter]");
@@ -514,16 +522,42 @@ extern "C" lslu_status lslu_solve(lslu_handle h, const double* b, const double* 
     CK(cudaMemcpyAsync(c->xin + m, x0, n * 8, h2d, s));
     dx0 = c->xin + m;
   }
+  const bool fixed = fix_g != nullptr;
+  if (fixed) {  // replayed pivots: validate on the host (indices in range, distinct)
+    std::vector<int32_t> g(K), t(K + 1);
+    if (host) {
+      std::memcpy(g.data(), fix_g, (size_t)K * 4);
+      std::memcpy(t.data(), fix_t, (size_t)(K + 1) * 4);
+    } else {
+      CK(cudaMemcpy(g.data(), fix_g, (size_t)K * 4, cudaMemcpyDeviceToHost));
+      CK(cudaMemcpy(t.data(), fix_t, (size_t)(K + 1) * 4, cudaMemcpyDeviceToHost));
+    }
+    std::vector<uint8_t> seen_n(n, 0), seen_m(m, 0);
+    for (int i = 0; i < K; ++i) {
+      if (g[i] < 0 || g[i] >= n || seen_n[g[i]])
+        return set_err(c, LSLU_ERR_INVALID_ARG, "col_pivots must be distinct indices in [0, n)");
+      seen_n[g[i]] = 1;
+    }
+    for (int i = 0; i <= K; ++i) {
+      if (t[i] < 0 || t[i] >= m || seen_m[t[i]])
+        return set_err(c, LSLU_ERR_INVALID_ARG, "row_pivots must be distinct indices in [0, m)");
+      seen_m[t[i]] = 1;
+    }
+    CK(cudaMemcpyAsync(c->fixed_gp, g.data(), (size_t)K * 4, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(c->fixed_tp, t.data(), (size_t)(K + 1) * 4, cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));  // the host vectors go out of scope
+  }
   const bool hist = lambda_hist || resid_hist;
   const double lam = rule == LSLU_LAMBDA_FIXED ? lambda : 0.0;
   lslu_status st = c->value_type == LSLU_F64
-                       ? solve_impl<double, double>(c, db, dx0, K, rule, lam, hist)
-                       : solve_impl<float, float>(c, db, dx0, K, rule, lam, hist);
+                       ? solve_impl<double, double>(c, db, dx0, K, rule, lam, hist, fixed)
+                       : solve_impl<float, float>(c, db, dx0, K, rule, lam, hist, fixed);
   if (st != LSLU_OK) return st;
   const DevState ds = *c->st_host;
   const int kd = ds.k_done < 0 ? 0 : (ds.k_done > K ? K : ds.k_done);
   c->last_k = kd;
   c->last_K = K;
+  c->adj_valid = ds.status == LSLU_OK && kd == K;
   const cudaMemcpyKind d2o = host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
   CK(cudaMemcpyAsync(x_out, c->xout, n * 8, d2o, s));
   if (col_pivots) {
@@ -574,6 +608,27 @@ extern "C" lslu_status lslu_solve(lslu_handle h, const double* b, const double* 
   return LSLU_OK;
 }
 
+
+}  // namespace
+
+extern "C" lslu_status lslu_solve(lslu_handle h, const double* b, const double* x0, int32_t K,
+                                  int32_t rule, double lambda, int32_t ptr_location,
+                                  double* x_out, int32_t* col_pivots, int32_t* row_pivots,
+                                  double* lambda_hist, double* resid_hist, int32_t* k_done) {
+  return solve_entry(h, b, x0, K, rule, lambda, ptr_location, x_out, col_pivots, row_pivots,
+                     lambda_hist, resid_hist, k_done, nullptr, nullptr);
+}
+
+extern "C" lslu_status lslu_solve_fixed_pivots(lslu_handle h, const double* b, const double* x0,
+                                               int32_t K, int32_t rule, double lambda,
+                                               int32_t ptr_location, const int32_t* col_pivots,
+                                               const int32_t* row_pivots, double* x_out,
+                                               int32_t* k_done) {
+  if (h && (!col_pivots || !row_pivots))
+    return set_err(h, LSLU_ERR_INVALID_ARG, "col_pivots and row_pivots are required");
+  return solve_entry(h, b, x0, K, rule, lambda, ptr_location, x_out, nullptr, nullptr, nullptr,
+                     nullptr, k_done, col_pivots, row_pivots);
+}
 
 extern "C" lslu_status lslu_create_batched(int32_t nprob, const int64_t* row_off,
                                            const int64_t* col_off, const int64_t* row_ptr,
@@ -806,6 +861,7 @@ extern "C" lslu_status lslu_projected(lslu_handle h, int32_t k, const double* H,
                                       double* lambda_out, double* resid_out) {
   Ctx* c = h;
   if (!c) return set_err(nullptr, LSLU_ERR_INVALID_ARG, "NULL handle");
+  c->adj_valid = false;  // the projected work space and y are reused below
   if (k < 1 || k > c->kmax || ldh < k + 1 || !H)
     return set_err(c, LSLU_ERR_INVALID_ARG, "invalid k, ldh or H");
   if (rule < LSLU_LAMBDA_NONE || rule > LSLU_LAMBDA_WGCV || m < 1)

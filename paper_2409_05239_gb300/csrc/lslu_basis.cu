@@ -109,6 +109,11 @@ __device__ __forceinline__ int tile_problem(const int32_t* tile_prob, int64_t ro
 template <typename CT, typename BT>
 __device__ void record_pivot(const PivotArgs& pa, DevState& s, int p, int besti, double best,
                              const CT* v) {
+  if (pa.fixed) {  // replay: the given row, whatever the search found
+    besti = pa.fixed[(int64_t)p * pa.piv_stride + pa.piv_slot];
+    best = fabs((double)__ldcg(v + besti));
+    if (best != best) best = INFINITY;
+  }
   if (besti < 0 || best == 0.0) {
     s.status = pa.breakdown_code;
     s.k_done = pa.k_on_breakdown;

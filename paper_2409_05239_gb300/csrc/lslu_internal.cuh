@@ -96,6 +96,8 @@ struct Ctx {
   int64_t ldt = 0;
   int32_t* gp = nullptr;  // kmax per problem (padded-space row indices)
   int32_t* tp = nullptr;  // kmax+1 per problem
+  int32_t* fixed_gp = nullptr;  // pivots replayed by lslu_solve_fixed_pivots (kmax)
+  int32_t* fixed_tp = nullptr;  // (kmax + 1)
   // per-problem strides of the arrays above and below
   int64_t h_stride = 0, w_stride = 0, t_stride = 0, c_stride = 0, xp_stride = 0;
   uint8_t* gused = nullptr;  // n
@@ -122,7 +124,7 @@ struct Ctx {
   double* xout = nullptr;      // n, FP64
 
   // captured solves: one instantiated CUDA graph per (K, rule, lambda,
-  // histories, x0) and the stream they are launched on
+  // histories, x0, profiling, replayed pivots) and the stream they are launched on
   struct GraphEntry {
     int K, rule, hist, has_x0;
     double lam;
@@ -130,12 +132,23 @@ struct Ctx {
     int64_t launches;
     int prof;      // 1: event-record nodes around every sparse product
     int ev_pairs;  // number of such event pairs
+    int fixed;     // 1: pivots replayed from fixed_gp / fixed_tp
   };
   std::vector<GraphEntry> graphs;
   cudaStream_t cap_stream = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   bool use_graphs = true;
   unsigned long long* proj_tstamp = nullptr;  // LSLU_PROJ_TIMING diagnostics
+
+  // reverse-mode work space (lslu_adjoint), allocated on first use
+  void* adj_Vb = nullptr;      // adjoints of the L-side eliminated vectors, ldl x kmax
+  void* adj_Zb = nullptr;      // adjoints of the D-side eliminated vectors, ldd x kmax
+  void* adj_vec = nullptr;     // compute-type vectors: 3 of length ldl, 3 of length ldd
+  double* adj_small = nullptr; // FP64 projected adjoint, pivot-row adjoints, scalars
+  double* adj_part = nullptr;  // per-block partial sums
+  int adj_part_rows = 0;       // blocks of the partial-sum array
+  bool adj_valid = false;      // the last lslu_solve completed K iterations and its
+                               // state (bases, H, W, y, lambda) is intact
 
   int last_k = -1;  // k_done of the last solve, -1 if none
   int last_K = 0;
@@ -207,6 +220,7 @@ struct PivotArgs {
   int64_t coef_stride;
   int nprob;
   const int32_t* tile_prob;
+  const int32_t* fixed;  // replayed pivot list (same layout as piv_list), or null: argmax
 };
 
 template <typename XT, typename BT, typename CT>

@@ -25,7 +25,8 @@ HOST, DEVICE = 0, 1
 
 EXPORTS = ("lslu_create", "lslu_solve", "lslu_get_state", "lslu_spmv", "lslu_projected",
            "lslu_projected_noalloc", "lslu_profile", "lslu_timing", "lslu_last_launch_count",
-           "lslu_error_string", "lslu_destroy", "lslu_create_batched", "lslu_solve_batched")
+           "lslu_error_string", "lslu_destroy", "lslu_create_batched", "lslu_solve_batched",
+           "lslu_adjoint", "lslu_solve_fixed_pivots")
 
 _lib = None
 
@@ -73,6 +74,10 @@ def load(path: str | None = None):
     lib.lslu_create_batched.restype = i32
     lib.lslu_solve_batched.argtypes = [vp, vp, i32, i32, f64, i32, vp, vp, vp, vp, vp]
     lib.lslu_solve_batched.restype = i32
+    lib.lslu_solve_fixed_pivots.argtypes = [vp, vp, vp, i32, i32, f64, i32, vp, vp, vp, vp]
+    lib.lslu_solve_fixed_pivots.restype = i32
+    lib.lslu_adjoint.argtypes = [vp, vp, i32, vp, vp, vp]
+    lib.lslu_adjoint.restype = i32
     lib.lslu_destroy.argtypes = [vp]
     lib.lslu_destroy.restype = None
     _lib = lib
@@ -116,6 +121,7 @@ class Solver:
         if st != OK:
             raise LsluError(st, self.lib.lslu_error_string(None).decode())
         self.h = h
+        self.epoch = 0  # bumped by every call that replaces the solve state
 
     def _check(self, st, allow_breakdown=False):
         if st == OK or (allow_breakdown and st in BREAKDOWNS):
@@ -133,6 +139,7 @@ class Solver:
         lh = np.zeros(K) if histories else None
         rh = np.zeros(K) if histories else None
         kd = ctypes.c_int32(0)
+        self.epoch += 1
         st = self.lib.lslu_solve(self.h, _ptr(b), _ptr(x0), int(K), RULES[rule], float(lam), HOST,
                                  _ptr(x), _ptr(gp), _ptr(tp), _ptr(lh), _ptr(rh),
                                  ctypes.addressof(kd))
@@ -142,6 +149,7 @@ class Solver:
     def solve_device(self, b, x_out, K, rule="gcv", lam=0.0, x0=None, gp=None, tp=None,
                      lam_hist=None, res_hist=None, k_done=None):
         """Device buffers (torch tensors) in and out; returns the status."""
+        self.epoch += 1
         st = self.lib.lslu_solve(self.h, _ptr(b), _ptr(x0), int(K), RULES[rule], float(lam),
                                  DEVICE, _ptr(x_out), _ptr(gp), _ptr(tp), _ptr(lam_hist),
                                  _ptr(res_hist), _ptr(k_done))
@@ -158,6 +166,40 @@ class Solver:
         self._check(st)
         return dict(H=H.T.copy(), W=W.T.copy(), beta=float(beta[0]), L=L.T.copy(), D=D.T.copy())
 
+    def solve_fixed_pivots(self, b, K, gp, tp, rule="fixed", lam=0.0, x0=None):
+        """Solve with the pivot lists replayed (host arrays)."""
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        x0 = None if x0 is None else np.ascontiguousarray(x0, dtype=np.float64)
+        gp = np.ascontiguousarray(gp, dtype=np.int32)
+        tp = np.ascontiguousarray(tp, dtype=np.int32)
+        x = np.zeros(self.n)
+        kd = ctypes.c_int32(0)
+        self.epoch += 1
+        st = self.lib.lslu_solve_fixed_pivots(self.h, _ptr(b), _ptr(x0), int(K), RULES[rule],
+                                              float(lam), HOST, _ptr(gp), _ptr(tp), _ptr(x),
+                                              ctypes.addressof(kd))
+        self._check(st, allow_breakdown=True)
+        return dict(x=x, k_done=kd.value, status=st)
+
+    def adjoint(self, x_bar, want_x0=False):
+        """Reverse-mode derivative of the last solve (pivots fixed): host
+        x_bar -> dict(b_bar, lambda_bar[, x0_bar])."""
+        x_bar = np.ascontiguousarray(x_bar, dtype=np.float64)
+        bb = np.zeros(self.m)
+        lb = np.zeros(1)
+        xb = np.zeros(self.n) if want_x0 else None
+        self._check(self.lib.lslu_adjoint(self.h, _ptr(x_bar), HOST, _ptr(bb), _ptr(lb),
+                                          _ptr(xb)))
+        out = dict(b_bar=bb, lambda_bar=float(lb[0]))
+        if want_x0:
+            out["x0_bar"] = xb
+        return out
+
+    def adjoint_device(self, x_bar, b_bar, lambda_bar=None, x0_bar=None):
+        """Device tensors in and out (FP64)."""
+        self._check(self.lib.lslu_adjoint(self.h, _ptr(x_bar), DEVICE, _ptr(b_bar),
+                                          _ptr(lambda_bar), _ptr(x0_bar)))
+
     def spmv(self, transpose, x, y):
         """y = A x or y = A^T x on device tensors of the basis type."""
         self._check(self.lib.lslu_spmv(self.h, int(transpose), _ptr(x), _ptr(y)))
@@ -171,6 +213,7 @@ class Solver:
         c = np.zeros(k + 1)
         lo = np.zeros(1)
         ro = np.zeros(1)
+        self.epoch += 1
         st = self.lib.lslu_projected(self.h, k, _ptr(H), k + 1, float(beta), RULES[rule],
                                      float(lam), int(m or self.m), HOST, _ptr(y), _ptr(sig),
                                      _ptr(c), _ptr(lo), _ptr(ro))
@@ -301,6 +344,53 @@ class BatchedSolver:
 
     def __exit__(self, *a):
         self.close()
+
+
+_autograd_fn = None
+
+
+def _solve_function():
+    """torch.autograd.Function around lslu_solve (forward, FIXED lambda) and
+    lslu_adjoint (backward); built on first use so that importing this module
+    does not import torch."""
+    global _autograd_fn
+    if _autograd_fn is not None:
+        return _autograd_fn
+    import torch
+
+    class HybridLsluFn(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, b, log_lam, solver, K):
+            lam = float(torch.exp(log_lam.detach()).item())
+            x = torch.empty(solver.n, dtype=torch.float64, device=b.device)
+            st = solver.solve_device(b.detach().to(torch.float64).contiguous(), x, K, "fixed", lam)
+            if st != OK:
+                raise LsluError(st, "breakdown in the forward solve: no derivative")
+            ctx.solver, ctx.lam, ctx.epoch = solver, lam, solver.epoch
+            return x
+
+        @staticmethod
+        def backward(ctx, x_bar):
+            solver = ctx.solver
+            if solver.epoch != ctx.epoch:
+                raise RuntimeError("the handle solved again after this forward pass; the "
+                                   "backward pass needs the state of its own solve")
+            b_bar = torch.empty(solver.m, dtype=torch.float64, device=x_bar.device)
+            lam_bar = torch.empty(1, dtype=torch.float64, device=x_bar.device)
+            solver.adjoint_device(x_bar.detach().to(torch.float64).contiguous(), b_bar, lam_bar)
+            # d/dlog(lambda) = lambda d/dlambda
+            return b_bar, (lam_bar[0] * ctx.lam), None, None
+
+    _autograd_fn = HybridLsluFn
+    return HybridLsluFn
+
+
+def hybrid_lslu(solver, b, log_lam, K):
+    """x_K of Hybrid LSLU with fixed lambda = exp(log_lam) as a differentiable
+    torch function of b (length m, CUDA) and log_lam (0-d tensor).  The
+    backward pass is lslu_adjoint: the pivots of the forward solve are held
+    fixed.  One backward per forward, before the handle solves again."""
+    return _solve_function().apply(b, log_lam, solver, int(K))
 
 
 def from_problems(Ps, value_type="f32", max_iter=150, stream=None):
