@@ -60,6 +60,34 @@ def dist_env():
     return rank, world, local
 
 
+# DRAM traffic of one k_spmv_pivots launch on the 512x512 FP32 workload
+# (dram__bytes_read.sum + dram__bytes_write.sum, average of the A^T and A
+# launches) from the ncu capture summarised in profiles/k_spmv_pivots_ct512.md.
+# It is reported only while the kernel's sources are the ones captured.
+SPMV_TRAFFIC = {
+    "bytes_per_launch": 975.35e6,
+    "workload": "ct512", "value_type": "f32",
+    "sources": {
+        "paper_2409_05239_gb300/csrc/lslu_spmv.cu":
+            "fa5e99f64e75d91dc118258531dd67dc8a2918472b7f800b8be4f6e1be9e8528",
+        "paper_2409_05239_gb300/csrc/lslu_internal.cuh":
+            "e3510d8e514cebba25942d52518923031eaceb97d1e47de184ba3a4341ae4df7",
+    },
+}
+
+
+def spmv_traffic(workload, value_type):
+    import hashlib
+
+    if workload != SPMV_TRAFFIC["workload"] or value_type != SPMV_TRAFFIC["value_type"]:
+        return None
+    for rel, digest in SPMV_TRAFFIC["sources"].items():
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest() != digest:
+                return None
+    return SPMV_TRAFFIC["bytes_per_launch"]
+
+
 def spmv_bytes(P, value_type):
     """Algorithmic bytes of one sparse product (either direction, averaged):
     values + column indices + row pointers + output + input vector."""
@@ -475,7 +503,10 @@ def run_gpu(args):
                          "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
                          "timing": "CUDA events around each product, second pass of the timed steps",
                          "algorithmic_bytes_per_launch": sbytes, "launches": n_spmv,
-                         "avg_launch_ms": avg_ms, "traffic": None},
+                         "avg_launch_ms": avg_ms,
+                         "traffic": spmv_traffic(args.workload, args.value_type),
+                         "traffic_source": "profiles/k_spmv_pivots_ct512.md (ncu dram bytes "
+                                           "per launch)"},
             "hbm_gbs_solve": total_bytes * args.steps * world / (ms_max / 1e3) / 1e9,
             "rel_err_x_true": rel_true,
             "e2e": {"value": e2e_value, "unit": "iter/s", "h2d_bytes_per_step": P.m * 8,
