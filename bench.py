@@ -292,6 +292,59 @@ def batched_study(dev, K=150, count=64):
             "rel_err_x_true_max": float(np.max(errs))}
 
 
+def shared_rhs_study(dev, K=150, nrhs=16):
+    """16 right-hand sides for the 256x256 projector (FP32, GCV, K iterations):
+    the shared-matrix handle (A read once per product for all of them) against
+    the same right-hand sides as a block-diagonal batch of 16 copies of A and
+    against 16 single-problem solves one after another."""
+    import torch
+
+    from paper_2409_05239_gb300 import lslu
+
+    Ps = tomo.make_shared_rhs("ct256", nrhs)
+    P0 = Ps[0]
+    stream = torch.cuda.current_stream(dev)
+    b = np.concatenate([P.b for P in Ps])
+    b_dev = torch.from_numpy(b).to(dev)
+    x_dev = torch.empty(nrhs * P0.n, dtype=torch.float64, device=dev)
+
+    def timed(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    sh = lslu.shared_rhs(P0, nrhs, "f32", K, stream=stream.cuda_stream)
+    ms_sh = timed(lambda: sh.solve_device(b_dev, x_dev, K, "gcv"))
+    x_sh = x_dev.cpu().numpy()
+    sh.close()
+    bd = lslu.from_problems(Ps, "f32", K, stream=stream.cuda_stream)
+    ms_bd = timed(lambda: bd.solve_device(b_dev, x_dev, K, "gcv"))
+    same_bd = bool(np.array_equal(x_dev.cpu().numpy(), x_sh))
+    bd.close()
+    single = lslu.Solver(P0.m, P0.n, P0.row_ptr, P0.col_idx, P0.vals, "f32", K,
+                         stream=stream.cuda_stream)
+    bs = [torch.from_numpy(P.b).to(dev) for P in Ps]
+    xs = torch.empty(P0.n, dtype=torch.float64, device=dev)
+    ms_seq = timed(lambda: [single.solve_device(bb, xs, K, "gcv") for bb in bs], reps=2)
+    single.close()
+    return {"workload": "ct256 (m=%d, n=%d, nnz=%d) x %d right-hand sides, FP32, K=%d, GCV"
+                        % (P0.m, P0.n, P0.nnz, nrhs, K),
+            "ms_per_solve_shared_matrix": ms_sh,
+            "ms_per_solve_block_diagonal_copies": ms_bd,
+            "ms_sequential_single_solves": ms_seq,
+            "rhs_iter_per_s_shared": nrhs * K / (ms_sh / 1e3),
+            "speedup_vs_block_diagonal": ms_bd / ms_sh,
+            "speedup_vs_sequential": ms_seq / ms_sh,
+            "identical_to_block_diagonal": same_bd}
+
+
 def adjoint_study(dev, K=100):
     """Differentiable solve on the 256x256 workload (FP32, fixed lambda = the
     GCV choice at K): time of the forward solve and of the reverse-mode
@@ -519,6 +572,7 @@ def run_gpu(args):
         out["precision_study"] = precision_study(P, K, rule, dev, x, args.value_type)
     if rank == 0 and not args.no_extras and world == 1:
         out["batched_study"] = batched_study(dev)
+        out["shared_rhs_study"] = shared_rhs_study(dev)
         out["adjoint_study"] = adjoint_study(dev)
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         out["cpu_baseline"] = cpu_baseline(P, K, args.cpu_sample_s)

@@ -118,6 +118,20 @@ lslu_status lslu_create_batched(int32_t nprob, const int64_t* row_off, const int
                                 const double* vals, int32_t value_type, int32_t max_iter,
                                 void* cuda_stream, lslu_handle* out);
 
+/* A batched handle for nrhs right-hand sides that share one m x n CSR matrix
+ * (row_ptr m+1 int64, col_idx int32 in [0, n), vals FP64; host memory).  The
+ * matrix and its transpose are stored once, and every sparse product reads
+ * them once for all right-hand sides: the nrhs input vectors are interleaved
+ * so that each non-zero fetches its nrhs operands together.  Solved with
+ * lslu_solve_batched (problem r = right-hand side r: b holds nrhs x m values,
+ * x_out nrhs x n); each right-hand side gets the result of a single-problem
+ * solve, bit for bit.  value_type LSLU_F32 or LSLU_BF16; 1 <= nrhs <= 16.
+ * Errors: as lslu_create_batched. */
+lslu_status lslu_create_shared(int64_t m, int64_t n, const int64_t* row_ptr,
+                               const int32_t* col_idx, const double* vals, int32_t nrhs,
+                               int32_t value_type, int32_t max_iter, void* cuda_stream,
+                               lslu_handle* out);
+
 /* K iterations of Hybrid LSLU on every problem of a batched handle, from
  * x0 = 0.  b has row_off[nprob] FP64 entries (problem p's data at
  * row_off[p]); rule and lambda as in lslu_solve (the same rule for every

@@ -65,7 +65,7 @@ void destroy_ctx(lslu_ctx* c) {
                   c->cvec, c->xout, c->tile_prob_m, c->tile_prob_n, c->pad_m, c->pad_n,
                   c->map_m, c->map_n, c->xin_pad, c->xout_user, c->mvec,
                   c->adj_Vb, c->adj_Zb, c->adj_vec, c->adj_small, c->adj_part,
-                  c->fixed_gp, c->fixed_tp};
+                  c->fixed_gp, c->fixed_tp, c->xi};
   for (void* p : ptrs) cudaFree(p);
   if (c->st_host) cudaFreeHost(c->st_host);
   for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
@@ -83,7 +83,8 @@ namespace {
 
 // Device state of a handle whose padded concatenated CSR (c->m x c->n rows,
 // c->nprob problems) is rp/ci/vv; every per-problem array is strided.
-lslu_status create_common(lslu_ctx* c, const int64_t* rp, const int32_t* ci, const double* vv) {
+lslu_status create_common(lslu_ctx* c, const int64_t* rp, const int32_t* ci, const double* vv,
+                          int64_t csr_m = -1, int64_t csr_n = -1) {
   lslu_status st = LSLU_OK;
   auto fail = [&](lslu_status s2) {
     lslu::thread_error() = c->err;
@@ -103,7 +104,10 @@ lslu_status create_common(lslu_ctx* c, const int64_t* rp, const int32_t* ci, con
   const int P = c->nprob;
   CKC(cudaGetDevice(&c->device));
   CKC(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
-  CKC(build_csr_pair(m, n, rp, ci, vv, c->value_type, &c->A, &c->AT, c->stream));
+  CKC(build_csr_pair(csr_m < 0 ? m : csr_m, csr_n < 0 ? n : csr_n, rp, ci, vv, c->value_type,
+                     &c->A, &c->AT, c->stream));
+  if (c->shared_rhs)
+    CKC(dmalloc(&c->xi, (size_t)std::max(c->m1, c->n1) * rhs_stride(c->shared_rhs)));
   const int K = c->kmax;
   const size_t bb = basis_bytes(c->value_type);
   c->ldl = round_up(n, 128);  // whole 128-row tiles of the elimination kernel
@@ -341,7 +345,18 @@ int64_t enqueue_solve(Ctx* c, cudaStream_t s, const double* db, const double* dx
                   c->xp,       c->xp_stride,  c->TLi,   c->ldt,     c->t_stride,
                   c->st,       P,             0};
     record_spmv_start(c, s, capturing, &e0);
-    launch_spmv_pivots<BT, CT>(c->AT, vt, D + (int64_t)k * c->ldd, q, pcw, s);
+    if constexpr (std::is_same<BT, float>::value) {
+      if (c->shared_rhs) {
+        launch_interleave(D + (int64_t)k * c->ldd, c->m1_pad, c->m1, c->shared_rhs, c->xi, s,
+                          c->num_sms);
+        launch_spmm_pivots(c->AT, vt, c->xi, q, c->n1_pad, c->shared_rhs, pcw, s);
+        launches += 1;
+      } else {
+        launch_spmv_pivots<BT, CT>(c->AT, vt, D + (int64_t)k * c->ldd, q, pcw, s);
+      }
+    } else {
+      launch_spmv_pivots<BT, CT>(c->AT, vt, D + (int64_t)k * c->ldd, q, pcw, s);
+    }
     record_spmv_end(c, s, capturing, e0);
     PivotArgs paw{c->gp, c->kmax, k, c->gused, c->W + k + k * ldw, c->w_stride, c->ldt,
                   LSLU_BREAKDOWN_W, k, 0, c->TLi, c->t_stride, c->coef, c->c_stride, P, tpn,
@@ -355,7 +370,18 @@ int64_t enqueue_solve(Ctx* c, cudaStream_t s, const double* db, const double* dx
                   c->xp,       c->xp_stride,  c->TDi,   c->ldt,     c->t_stride,
                   c->st,       P,             0};
     record_spmv_start(c, s, capturing, &e0);
-    launch_spmv_pivots<BT, CT>(c->A, vt, L + (int64_t)k * c->ldl, u, pch, s);
+    if constexpr (std::is_same<BT, float>::value) {
+      if (c->shared_rhs) {
+        launch_interleave(L + (int64_t)k * c->ldl, c->n1_pad, c->n1, c->shared_rhs, c->xi, s,
+                          c->num_sms);
+        launch_spmm_pivots(c->A, vt, c->xi, u, c->m1_pad, c->shared_rhs, pch, s);
+        launches += 1;
+      } else {
+        launch_spmv_pivots<BT, CT>(c->A, vt, L + (int64_t)k * c->ldl, u, pch, s);
+      }
+    } else {
+      launch_spmv_pivots<BT, CT>(c->A, vt, L + (int64_t)k * c->ldl, u, pch, s);
+    }
     record_spmv_end(c, s, capturing, e0);
     PivotArgs pah{c->tp, c->kmax + 1, k + 1, c->tused, c->H + (k + 1) + k * ldh, c->h_stride,
                   c->ldt, LSLU_BREAKDOWN_H, k, 0, c->TDi, c->t_stride, c->coef, c->c_stride, P,
@@ -630,6 +656,38 @@ extern "C" lslu_status lslu_solve_fixed_pivots(lslu_handle h, const double* b, c
                      nullptr, k_done, col_pivots, row_pivots);
 }
 
+namespace {
+
+// Device copies of a batch layout (tile -> problem maps, padding masks,
+// caller <-> padded index maps, rows per problem) and the staging buffers.
+lslu_status upload_batch_layout(lslu_ctx* c, const std::vector<int32_t>& tpm,
+                                const std::vector<int32_t>& tpn,
+                                const std::vector<uint8_t>& pad_m,
+                                const std::vector<uint8_t>& pad_n,
+                                const std::vector<int32_t>& map_m,
+                                const std::vector<int32_t>& map_n,
+                                const std::vector<int64_t>& mvec) {
+  auto up = [&](auto** dst, const auto& v) -> bool {
+    using T = typename std::decay<decltype(v[0])>::type;
+    if (cudaMalloc((void**)dst, std::max<size_t>(v.size(), 1) * sizeof(T)) != cudaSuccess)
+      return false;
+    return cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice) ==
+           cudaSuccess;
+  };
+  if (!up(&c->tile_prob_m, tpm) || !up(&c->tile_prob_n, tpn) || !up(&c->pad_m, pad_m) ||
+      !up(&c->pad_n, pad_n) || !up(&c->map_m, map_m) || !up(&c->map_n, map_n) ||
+      !up(&c->mvec, mvec) || cudaMalloc(&c->xin_pad, c->m * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&c->xout_user, c->n_user * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    lslu::thread_error() = "allocating the batch layout failed";
+    destroy_ctx(c);
+    return LSLU_ERR_OOM;
+  }
+  return LSLU_OK;
+}
+
+}  // namespace
+
 extern "C" lslu_status lslu_create_batched(int32_t nprob, const int64_t* row_off,
                                            const int64_t* col_off, const int64_t* row_ptr,
                                            const int32_t* col_idx, const double* vals,
@@ -724,22 +782,82 @@ extern "C" lslu_status lslu_create_batched(int32_t nprob, const int64_t* row_off
   c->stream = (cudaStream_t)cuda_stream;
   lslu_status st = create_common(c, rp.data(), ci.data(), vv.data());
   if (st != LSLU_OK) return st;
-  auto up = [&](auto** dst, const auto& v) -> bool {
-    using T = typename std::decay<decltype(v[0])>::type;
-    if (cudaMalloc((void**)dst, std::max<size_t>(v.size(), 1) * sizeof(T)) != cudaSuccess)
-      return false;
-    return cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice) ==
-           cudaSuccess;
-  };
-  if (!up(&c->tile_prob_m, tpm) || !up(&c->tile_prob_n, tpn) || !up(&c->pad_m, pad_m) ||
-      !up(&c->pad_n, pad_n) || !up(&c->map_m, map_m) || !up(&c->map_n, map_n) ||
-      !up(&c->mvec, mvec) || cudaMalloc(&c->xin_pad, mp * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&c->xout_user, nu * sizeof(double)) != cudaSuccess) {
-    cudaGetLastError();
-    lslu::thread_error() = "allocating the batch layout failed";
-    destroy_ctx(c);
-    return LSLU_ERR_OOM;
+  st = upload_batch_layout(c, tpm, tpn, pad_m, pad_n, map_m, map_n, mvec);
+  if (st != LSLU_OK) return st;
+  *out = c;
+  return LSLU_OK;
+}
+
+extern "C" lslu_status lslu_create_shared(int64_t m, int64_t n, const int64_t* row_ptr,
+                                          const int32_t* col_idx, const double* vals,
+                                          int32_t nrhs, int32_t value_type, int32_t max_iter,
+                                          void* cuda_stream, lslu_handle* out) {
+  if (!out) return set_err(nullptr, LSLU_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (m < 1 || n < 1 || !row_ptr)
+    return set_err(nullptr, LSLU_ERR_INVALID_ARG, "invalid m, n or row_ptr");
+  if (nrhs < 1 || nrhs > 16)
+    return set_err(nullptr, LSLU_ERR_INVALID_ARG, "nrhs must be in [1, 16]");
+  if (value_type != LSLU_F32 && value_type != LSLU_BF16)
+    return set_err(nullptr, LSLU_ERR_INVALID_ARG, "shared-matrix solves take FP32 or BF16 values");
+  if (max_iter < 1 || max_iter > kMaxIter)
+    return set_err(nullptr, LSLU_ERR_INVALID_ARG, "max_iter must be in [1, 2048]");
+  const int64_t nnz = row_ptr[m];
+  if (row_ptr[0] != 0 || nnz < 0 || nnz >= (int64_t)INT32_MAX || (nnz > 0 && (!col_idx || !vals)))
+    return set_err(nullptr, LSLU_ERR_INVALID_ARG, "invalid CSR (row_ptr[0] != 0 or nnz)");
+  for (int64_t r = 0; r < m; ++r)
+    if (row_ptr[r + 1] < row_ptr[r])
+      return set_err(nullptr, LSLU_ERR_INVALID_ARG, "row_ptr is not monotone");
+  for (int64_t e = 0; e < nnz; ++e) {
+    if (col_idx[e] < 0 || col_idx[e] >= n)
+      return set_err(nullptr, LSLU_ERR_INVALID_ARG, "column index out of range");
+    if (!std::isfinite(vals[e]))
+      return set_err(nullptr, LSLU_ERR_INVALID_ARG, "non-finite matrix value");
   }
+  const int64_t m1p = round_up(m, kTile), n1p = round_up(n, kTile);
+  const int64_t mp = nrhs * m1p, np = nrhs * n1p;
+  if (mp >= (int64_t)INT32_MAX || np >= (int64_t)INT32_MAX)
+    return set_err(nullptr, LSLU_ERR_INVALID_ARG, "padded sizes must be below 2^31");
+  std::vector<int32_t> map_m(nrhs * m), map_n(nrhs * n), tpm(mp / kTile), tpn(np / kTile);
+  std::vector<uint8_t> pad_m(mp, 1), pad_n(np, 1);
+  std::vector<int64_t> mvec(nrhs, m);
+  for (int r = 0; r < nrhs; ++r) {
+    for (int64_t i = 0; i < m; ++i) {
+      map_m[r * m + i] = (int32_t)(r * m1p + i);
+      pad_m[r * m1p + i] = 0;
+    }
+    for (int64_t j = 0; j < n; ++j) {
+      map_n[r * n + j] = (int32_t)(r * n1p + j);
+      pad_n[r * n1p + j] = 0;
+    }
+  }
+  for (int64_t t = 0; t < mp / kTile; ++t) tpm[t] = (int32_t)(t / (m1p / kTile));
+  for (int64_t t = 0; t < np / kTile; ++t) tpn[t] = (int32_t)(t / (n1p / kTile));
+  lslu_ctx* c = new lslu_ctx();
+  c->nprob = nrhs;
+  c->m = mp;
+  c->n = np;
+  c->m_user = nrhs * m;
+  c->n_user = nrhs * n;
+  for (int r = 0; r < nrhs; ++r) {
+    c->row_base.push_back(r * m1p);
+    c->col_base.push_back(r * n1p);
+    c->prob_m.push_back(m);
+    c->prob_n.push_back(n);
+  }
+  c->nnz = nnz;
+  c->value_type = value_type;
+  c->kmax = max_iter;
+  c->stream = (cudaStream_t)cuda_stream;
+  c->shared_rhs = nrhs;
+  c->m1 = m;
+  c->n1 = n;
+  c->m1_pad = m1p;
+  c->n1_pad = n1p;
+  lslu_status st = create_common(c, row_ptr, col_idx, vals, m, n);
+  if (st != LSLU_OK) return st;
+  st = upload_batch_layout(c, tpm, tpn, pad_m, pad_n, map_m, map_n, mvec);
+  if (st != LSLU_OK) return st;
   *out = c;
   return LSLU_OK;
 }

@@ -78,6 +78,12 @@ struct Ctx {
   double* xout_user = nullptr;         // x in the caller's layout (batch)
   int64_t* mvec = nullptr;             // rows of every problem (weighted GCV)
   int64_t res_off = 0;                 // offset of the residual outputs in proj_out
+  // right-hand sides sharing one matrix (lslu_create_shared): A and A^T are
+  // stored once (m1 x n1); problem r's rows start at r * m1_pad, its columns
+  // at r * n1_pad
+  int shared_rhs = 0;
+  int64_t m1 = 0, n1 = 0, m1_pad = 0, n1_pad = 0;
+  float* xi = nullptr;                 // interleaved right-hand sides, max(m1, n1) x RS
   int value_type = LSLU_F64;
   int kmax = 0;
   DevCsr A, AT;  // A (m rows) and A^T (n rows)
@@ -194,6 +200,17 @@ struct PivotCoef {
 template <typename XT, typename YT>
 void launch_spmv_pivots(const DevCsr& A, int vt, const XT* x, YT* y, PivotCoef pc,
                         cudaStream_t s);
+
+// Several right-hand sides sharing one matrix (lslu_create_shared): the R
+// vectors x[r * xstride + j] are interleaved into xi[j * RS + r] (RS = R rounded
+// up to 4, 8 or 16), then one pass over the CSR writes y[r * ystride + row]
+// and the elimination coefficients of every right-hand side (as
+// launch_spmv_pivots, with problem p's output rows at p * ystride + row).
+int rhs_stride(int R);
+void launch_interleave(const float* x, int64_t xstride, int64_t count, int R, float* xi,
+                       cudaStream_t s, int num_sms);
+void launch_spmm_pivots(const DevCsr& A, int vt, const float* xi, float* y, int64_t ystride,
+                        int R, PivotCoef pc, cudaStream_t s);
 
 // Build the padded CSR of A and of A^T (host-side layout, then upload).
 cudaError_t build_csr_pair(int64_t m, int64_t n, const int64_t* rp, const int32_t* ci,

@@ -184,70 +184,79 @@ __global__ void __launch_bounds__(256, ValTraits<VT>::kMinBlocks)
 //   c. the block adds Tinv(i, j) y(piv_j) over its 8 columns into a partial
 //      vector; the last pivot block to finish adds the partials in block order.
 // The remaining blocks compute the other rows of y meanwhile.
-template <typename VT, typename XT, typename YT>
-__global__ void __launch_bounds__(256, ValTraits<VT>::kMinBlocks) k_spmv_pivots(int64_t rows, const int32_t* __restrict__ rp,
-                                                     const int32_t* __restrict__ rl,
-                                                     const int32_t* __restrict__ col,
-                                                     const VT* __restrict__ val,
-                                                     const XT* __restrict__ x, YT* __restrict__ y,
-                                                     PivotCoef pc) {
+// Pivot blocks (steps a-c above) for problem p = blockIdx.x / npiv_blocks;
+// rowdot(p, row, gl) is the product of the output row `row` for problem p,
+// computed exactly as the streaming blocks compute it.
+template <typename YT, typename RowDot>
+__device__ __forceinline__ void pivot_blocks(const PivotCoef& pc, RowDot rowdot) {
   __shared__ int last;
   __shared__ YT xs[8];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int p = blockIdx.x / pc.npiv_blocks;  // problem of this pivot block
+  const int bb = blockIdx.x - p * pc.npiv_blocks;
+  DevState& sp = pc.st[p];
+  if (sp.status != LSLU_OK) return;
+  YT* Tinv = reinterpret_cast<YT*>(pc.Tinv) + (int64_t)p * pc.tinv_stride;
+  YT* part = reinterpret_cast<YT*>(pc.xp) + (int64_t)p * pc.xp_stride;
+  const int32_t* piv = pc.piv + (int64_t)p * pc.piv_stride;
+  const int cnt = pc.cnt, nr = cnt - 1;
+  const int j0 = bb * 8;
+  const int j = j0 + warp;
+  if (j < cnt) {
+    if (j < nr) {
+      YT a = 0;
+      // T(nr, l) = b_l(piv_nr): the newest pivot row of the earlier basis vectors
+      const YT* brow = reinterpret_cast<const YT*>(pc.B) + piv[nr];
+      const YT* tcol = Tinv + (int64_t)j * pc.ldi;
+      for (int l = j + lane; l < nr; l += 32)
+        a = fma(__ldcg(brow + (int64_t)l * pc.ldb), __ldcg(tcol + l), a);
+      a = warp_sum(a);
+      if (lane == 0) __stcg(Tinv + (int64_t)j * pc.ldi + nr, -a);
+    }
+    // both half-warps compute the pivot row (the same bits as its y entry)
+    const YT yp = rowdot(p, piv[j], lane & (kGroup - 1));
+    if (lane == 0) xs[warp] = yp;
+  } else if (lane == 0) {
+    xs[warp] = 0;
+  }
+  __threadfence_block();
+  __syncthreads();
+  const int jn = min(8, cnt - j0);
+  for (int i = j0 + threadIdx.x; i < cnt; i += blockDim.x) {
+    YT acc = 0;
+    for (int w = 0; w < jn; ++w)
+      if (i >= j0 + w) acc = fma(__ldcg(Tinv + (int64_t)(j0 + w) * pc.ldi + i), xs[w], acc);
+    __stcg(part + (int64_t)bb * pc.ldi + i, acc);
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = (atomicAdd(&sp.ticket2, 1) == pc.npiv_blocks - 1);
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  if (threadIdx.x == 0) sp.ticket2 = 0;
+  double* coef = pc.coef + (int64_t)p * pc.coef_stride;
+  double* hess = pc.hess_col ? pc.hess_col + (int64_t)p * pc.hess_stride : nullptr;
+  for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+    YT acc = 0;
+    const int bmax = i / 8;  // blocks whose columns start at or before row i
+    for (int b2 = 0; b2 <= bmax; ++b2) acc += __ldcg(part + (int64_t)b2 * pc.ldi + i);
+    coef[i] = (double)acc;
+    if (hess) hess[i] = (double)acc;
+  }
+}
+
+template <typename VT, typename XT, typename YT>
+__global__ void __launch_bounds__(256, ValTraits<VT>::kMinBlocks)
+    k_spmv_pivots(int64_t rows, const int32_t* __restrict__ rp, const int32_t* __restrict__ rl,
+                  const int32_t* __restrict__ col, const VT* __restrict__ val,
+                  const XT* __restrict__ x, YT* __restrict__ y, PivotCoef pc) {
+  const int lane = threadIdx.x & 31;
   const int npiv_all = pc.npiv_blocks * pc.nprob;
   if ((int)blockIdx.x < npiv_all) {
-    const int p = blockIdx.x / pc.npiv_blocks;  // problem of this pivot block
-    const int bb = blockIdx.x - p * pc.npiv_blocks;
-    DevState& sp = pc.st[p];
-    if (sp.status != LSLU_OK) return;
-    YT* Tinv = reinterpret_cast<YT*>(pc.Tinv) + (int64_t)p * pc.tinv_stride;
-    YT* part = reinterpret_cast<YT*>(pc.xp) + (int64_t)p * pc.xp_stride;
-    const int32_t* piv = pc.piv + (int64_t)p * pc.piv_stride;
-    const int cnt = pc.cnt, nr = cnt - 1;
-    const int j0 = bb * 8;
-    const int j = j0 + warp;
-    if (j < cnt) {
-      if (j < nr) {
-        YT a = 0;
-        // T(nr, l) = b_l(piv_nr): the newest pivot row of the earlier basis vectors
-        const YT* brow = reinterpret_cast<const YT*>(pc.B) + piv[nr];
-        const YT* tcol = Tinv + (int64_t)j * pc.ldi;
-        for (int l = j + lane; l < nr; l += 32)
-          a = fma(__ldcg(brow + (int64_t)l * pc.ldb), __ldcg(tcol + l), a);
-        a = warp_sum(a);
-        if (lane == 0) __stcg(Tinv + (int64_t)j * pc.ldi + nr, -a);
-      }
-      // both half-warps compute the pivot row (the same bits as its y entry)
-      const YT yp = row_dot<VT, XT, YT>(piv[j], true, rp, rl, col, val, x, lane & (kGroup - 1));
-      if (lane == 0) xs[warp] = yp;
-    } else if (lane == 0) {
-      xs[warp] = 0;
-    }
-    __threadfence_block();
-    __syncthreads();
-    const int jn = min(8, cnt - j0);
-    for (int i = j0 + threadIdx.x; i < cnt; i += blockDim.x) {
-      YT acc = 0;
-      for (int w = 0; w < jn; ++w)
-        if (i >= j0 + w) acc = fma(__ldcg(Tinv + (int64_t)(j0 + w) * pc.ldi + i), xs[w], acc);
-      __stcg(part + (int64_t)bb * pc.ldi + i, acc);
-    }
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) last = (atomicAdd(&sp.ticket2, 1) == pc.npiv_blocks - 1);
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    if (threadIdx.x == 0) sp.ticket2 = 0;
-    double* coef = pc.coef + (int64_t)p * pc.coef_stride;
-    double* hess = pc.hess_col ? pc.hess_col + (int64_t)p * pc.hess_stride : nullptr;
-    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
-      YT acc = 0;
-      const int bmax = i / 8;  // blocks whose columns start at or before row i
-      for (int b2 = 0; b2 <= bmax; ++b2) acc += __ldcg(part + (int64_t)b2 * pc.ldi + i);
-      coef[i] = (double)acc;
-      if (hess) hess[i] = (double)acc;
-    }
+    pivot_blocks<YT>(pc, [&](int, int32_t row, int gl) {
+      return row_dot<VT, XT, YT>(row, true, rp, rl, col, val, x, gl);
+    });
     return;
   }
   const int64_t b0 = (int64_t)(blockIdx.x - npiv_all) * kRowsPerBlock;
@@ -256,6 +265,119 @@ __global__ void __launch_bounds__(256, ValTraits<VT>::kMinBlocks) k_spmv_pivots(
   const bool valid = row < rows;
   const YT acc = row_dot<VT, XT, YT>(row, valid, rp, rl, col, val, x, lane & (kGroup - 1));
   if (valid && (lane & (kGroup - 1)) == 0) y[row] = acc;
+}
+
+// ---- several right-hand sides sharing one matrix ---------------------------
+// The R input vectors are first interleaved, xi[j * RS + r] (RS = R rounded
+// up to 4, zero-padded), so each non-zero fetches all R values with RS/4
+// 16-byte loads and the matrix is read once for all R products.  Lane gl of a
+// row's 16-lane group takes the same chunks in the same order as row_dot_len,
+// and each right-hand side keeps its own accumulator, so every output equals
+// the single-vector product bit for bit.
+
+// Product of CSR row `row` with right-hand side r of the interleaved xi.
+template <typename VT, int RS>
+__device__ __forceinline__ float row_dot_rhs(int64_t row, const int32_t* __restrict__ rp,
+                                             const int32_t* __restrict__ rl,
+                                             const int32_t* __restrict__ col,
+                                             const VT* __restrict__ val,
+                                             const float* __restrict__ xi, int r, int gl) {
+  constexpr int C = ValTraits<VT>::kChunk;
+  constexpr int S = kGroup * C;
+  const int32_t start = __ldg(rp + row), len = __ldg(rl + row);
+  float acc = 0.f;
+  for (int32_t e = gl * C; e < len; e += S) {
+    const int4 c4 = ld_stream(col + start + e);
+    float v[C];
+    load_vals_cs<float>(val + start + e, v);
+    acc = fmaf(v[0], __ldg(xi + (int64_t)c4.x * RS + r), acc);
+    acc = fmaf(v[1], __ldg(xi + (int64_t)c4.y * RS + r), acc);
+    acc = fmaf(v[2], __ldg(xi + (int64_t)c4.z * RS + r), acc);
+    acc = fmaf(v[3], __ldg(xi + (int64_t)c4.w * RS + r), acc);
+  }
+  return group_sum(acc);
+}
+
+template <int RS>
+__device__ __forceinline__ void gather_rhs(const float* __restrict__ xi, int32_t c, float (&xv)[RS]) {
+  const float4* p = reinterpret_cast<const float4*>(xi + (int64_t)c * RS);
+#pragma unroll
+  for (int q = 0; q < RS / 4; ++q) {
+    const float4 t = __ldg(p + q);
+    xv[4 * q] = t.x; xv[4 * q + 1] = t.y; xv[4 * q + 2] = t.z; xv[4 * q + 3] = t.w;
+  }
+}
+
+// y[r * ystride + row] = (A xi_r)(row) for r < R, rows of the shared CSR;
+// pivot blocks as in k_spmv_pivots, with output rows of problem p at
+// p * ystride + row.
+template <typename VT, int RS>
+__global__ void __launch_bounds__(256, 4)
+    k_spmm_pivots(int64_t rows, const int32_t* __restrict__ rp, const int32_t* __restrict__ rl,
+                  const int32_t* __restrict__ col, const VT* __restrict__ val,
+                  const float* __restrict__ xi, float* __restrict__ y, int64_t ystride, int R,
+                  PivotCoef pc) {
+  constexpr int C = ValTraits<VT>::kChunk;
+  constexpr int S = kGroup * C;
+  const int lane = threadIdx.x & 31;
+  const int npiv_all = pc.npiv_blocks * pc.nprob;
+  if ((int)blockIdx.x < npiv_all) {
+    pivot_blocks<float>(pc, [&](int p, int32_t row, int gl) {
+      return row_dot_rhs<VT, RS>((int64_t)row - (int64_t)p * ystride, rp, rl, col, val, xi, p,
+                                 gl);
+    });
+    return;
+  }
+  const int64_t b0 = (int64_t)(blockIdx.x - npiv_all) * kRowsPerBlock;
+  if (b0 + (threadIdx.x & ~31) / kGroup >= rows) return;  // whole warp past the end
+  const int64_t row = b0 + threadIdx.x / kGroup;
+  const bool valid = row < rows;
+  const int gl = lane & (kGroup - 1);
+  const int32_t start = valid ? __ldg(rp + row) : 0;
+  const int32_t len = valid ? __ldg(rl + row) : 0;
+  float acc[RS];
+#pragma unroll
+  for (int r = 0; r < RS; ++r) acc[r] = 0.f;
+  for (int32_t e = gl * C; e < len; e += S) {
+    const int4 c4 = ld_stream(col + start + e);
+    float v[C];
+    load_vals_cs<float>(val + start + e, v);
+    const int32_t cs[4] = {c4.x, c4.y, c4.z, c4.w};
+#pragma unroll
+    for (int i = 0; i < C; ++i) {
+      float xv[RS];
+      gather_rhs<RS>(xi, cs[i], xv);
+#pragma unroll
+      for (int r = 0; r < RS; ++r) acc[r] = fmaf(v[i], xv[r], acc[r]);
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < RS; ++r) acc[r] = group_sum(acc[r]);
+  if (valid) {
+#pragma unroll
+    for (int r = 0; r < RS; ++r)
+      if (r == gl && r < R) y[(int64_t)r * ystride + row] = acc[r];
+  }
+}
+
+// xi[j * RS + r] = x[r * xstride + j] (r < R), 0 for R <= r < RS.
+template <int RS>
+__global__ void k_interleave(const float* __restrict__ x, int64_t xstride, int64_t count, int R,
+                             float* __restrict__ xi) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < count;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    float4* o = reinterpret_cast<float4*>(xi + j * RS);
+#pragma unroll
+    for (int q = 0; q < RS / 4; ++q) {
+      float t[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int r = 4 * q + e;
+        t[e] = r < R ? x[(int64_t)r * xstride + j] : 0.f;
+      }
+      o[q] = make_float4(t[0], t[1], t[2], t[3]);
+    }
+  }
 }
 
 template <typename VT, typename XT, typename YT>
@@ -410,6 +532,51 @@ void launch_spmv_pivots(const DevCsr& A, int vt, const XT* x, YT* y, PivotCoef p
     spmv_pivots_typed<float, XT, YT>(A, x, y, pc, s);
   else
     spmv_pivots_typed<__nv_bfloat16, XT, YT>(A, x, y, pc, s);
+}
+
+template <typename VT, int RS>
+void spmm_typed(const DevCsr& A, const float* xi, float* y, int64_t ystride, int R,
+                const PivotCoef& pc, cudaStream_t s) {
+  const int64_t blocks =
+      (int64_t)pc.npiv_blocks * pc.nprob + (A.rows + kRowsPerBlock - 1) / kRowsPerBlock;
+  k_spmm_pivots<VT, RS><<<(unsigned)blocks, 256, 0, s>>>(
+      A.rows, A.row_ptr, A.row_len, A.col, reinterpret_cast<const VT*>(A.val), xi, y, ystride, R,
+      pc);
+}
+
+template <typename VT>
+void spmm_rs(const DevCsr& A, const float* xi, float* y, int64_t ystride, int R, int RS,
+             const PivotCoef& pc, cudaStream_t s) {
+  if (RS == 4)
+    spmm_typed<VT, 4>(A, xi, y, ystride, R, pc, s);
+  else if (RS == 8)
+    spmm_typed<VT, 8>(A, xi, y, ystride, R, pc, s);
+  else
+    spmm_typed<VT, 16>(A, xi, y, ystride, R, pc, s);
+}
+
+int rhs_stride(int R) { return R <= 4 ? 4 : (R <= 8 ? 8 : 16); }
+
+void launch_interleave(const float* x, int64_t xstride, int64_t count, int R, float* xi,
+                       cudaStream_t s, int num_sms) {
+  const int RS = rhs_stride(R);
+  const int g = (int)std::min<int64_t>((count + 255) / 256, (int64_t)num_sms * 8);
+  if (RS == 4)
+    k_interleave<4><<<g, 256, 0, s>>>(x, xstride, count, R, xi);
+  else if (RS == 8)
+    k_interleave<8><<<g, 256, 0, s>>>(x, xstride, count, R, xi);
+  else
+    k_interleave<16><<<g, 256, 0, s>>>(x, xstride, count, R, xi);
+}
+
+void launch_spmm_pivots(const DevCsr& A, int vt, const float* xi, float* y, int64_t ystride,
+                        int R, PivotCoef pc, cudaStream_t s) {
+  pc.npiv_blocks = (pc.cnt + 7) / 8;
+  const int RS = rhs_stride(R);
+  if (vt == LSLU_BF16)
+    spmm_rs<__nv_bfloat16>(A, xi, y, ystride, R, RS, pc, s);
+  else
+    spmm_rs<float>(A, xi, y, ystride, R, RS, pc, s);
 }
 
 template void launch_spmv<double, double>(const DevCsr&, int, const double*, double*,

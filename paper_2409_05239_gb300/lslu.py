@@ -26,7 +26,7 @@ HOST, DEVICE = 0, 1
 EXPORTS = ("lslu_create", "lslu_solve", "lslu_get_state", "lslu_spmv", "lslu_projected",
            "lslu_projected_noalloc", "lslu_profile", "lslu_timing", "lslu_last_launch_count",
            "lslu_error_string", "lslu_destroy", "lslu_create_batched", "lslu_solve_batched",
-           "lslu_adjoint", "lslu_solve_fixed_pivots")
+           "lslu_adjoint", "lslu_solve_fixed_pivots", "lslu_create_shared")
 
 _lib = None
 
@@ -72,6 +72,9 @@ def load(path: str | None = None):
     lib.lslu_create_batched.argtypes = [i32, vp, vp, vp, vp, vp, i32, i32, vp,
                                         ctypes.POINTER(vp)]
     lib.lslu_create_batched.restype = i32
+    lib.lslu_create_shared.argtypes = [i64, i64, vp, vp, vp, i32, i32, i32, vp,
+                                       ctypes.POINTER(vp)]
+    lib.lslu_create_shared.restype = i32
     lib.lslu_solve_batched.argtypes = [vp, vp, i32, i32, f64, i32, vp, vp, vp, vp, vp]
     lib.lslu_solve_batched.restype = i32
     lib.lslu_solve_fixed_pivots.argtypes = [vp, vp, vp, i32, i32, f64, i32, vp, vp, vp, vp]
@@ -269,8 +272,13 @@ class BatchedSolver:
     vals) per problem in the problem's own index space; they are stacked into
     one block-diagonal host CSR here (marshalling only)."""
 
-    def __init__(self, csr_list, value_type="f32", max_iter=150, stream=None):
+    def __init__(self, csr_list, value_type="f32", max_iter=150, stream=None, nrhs=None):
         self.lib = load()
+        if nrhs is not None:  # one matrix shared by nrhs right-hand sides
+            m, n, rp, ci, vv = csr_list
+            self._init_shared(int(m), int(n), rp, ci, vv, int(nrhs), value_type, max_iter,
+                              stream)
+            return
         self.nprob = len(csr_list)
         self.value_type = value_type
         self.max_iter = int(max_iter)
@@ -294,6 +302,23 @@ class BatchedSolver:
                                           _ptr(row_ptr), _ptr(col_idx), _ptr(vals),
                                           VALUE_TYPES[value_type], self.max_iter, stream,
                                           ctypes.byref(h))
+        if st != OK:
+            raise LsluError(st, self.lib.lslu_error_string(None).decode())
+        self.h = h
+
+    def _init_shared(self, m, n, rp, ci, vv, nrhs, value_type, max_iter, stream):
+        self.nprob = nrhs
+        self.value_type = value_type
+        self.max_iter = int(max_iter)
+        self.row_off = (np.arange(nrhs + 1) * m).astype(np.int64)
+        self.col_off = (np.arange(nrhs + 1) * n).astype(np.int64)
+        rp = np.ascontiguousarray(rp, dtype=np.int64)
+        ci = np.ascontiguousarray(ci, dtype=np.int32)
+        vv = np.ascontiguousarray(vv, dtype=np.float64)
+        h = ctypes.c_void_p()
+        st = self.lib.lslu_create_shared(m, n, _ptr(rp), _ptr(ci), _ptr(vv), nrhs,
+                                         VALUE_TYPES[value_type], self.max_iter, stream,
+                                         ctypes.byref(h))
         if st != OK:
             raise LsluError(st, self.lib.lslu_error_string(None).decode())
         self.h = h
@@ -397,6 +422,12 @@ def from_problems(Ps, value_type="f32", max_iter=150, stream=None):
     """Batched solver over several tomography problems."""
     return BatchedSolver([(P.m, P.n, P.row_ptr, P.col_idx, P.vals) for P in Ps],
                          value_type=value_type, max_iter=max_iter, stream=stream)
+
+
+def shared_rhs(P, nrhs, value_type="f32", max_iter=150, stream=None):
+    """Batched solver for nrhs right-hand sides of one tomography matrix."""
+    return BatchedSolver((P.m, P.n, P.row_ptr, P.col_idx, P.vals), value_type=value_type,
+                         max_iter=max_iter, stream=stream, nrhs=nrhs)
 
 
 def from_problem(P, value_type="f32", max_iter=300):

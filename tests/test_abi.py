@@ -102,6 +102,18 @@ def test_create_batched_rejects_bad_arguments_without_gpu(lib):
     assert create(ro, co, ok_ci, v=np.array([1.0, np.inf])) == lslu.ERR_INVALID_ARG
     assert lib.lslu_solve_batched(None, None, 1, 2, 0.0, 0, None, None, None, None,
                                   None) == lslu.ERR_INVALID_ARG
+    # shared-matrix handles: FP32/BF16 only, 1..16 right-hand sides
+    rp2 = np.array([0, 1, 2], dtype=np.int64)
+    st = lib.lslu_create_shared(2, 2, rp2.ctypes.data, ok_ci.ctypes.data, v.ctypes.data, 17, 1,
+                                10, None, ctypes.byref(h))
+    assert st == lslu.ERR_INVALID_ARG and not h.value
+    st = lib.lslu_create_shared(2, 2, rp2.ctypes.data, ok_ci.ctypes.data, v.ctypes.data, 2, 0,
+                                10, None, ctypes.byref(h))
+    assert st == lslu.ERR_INVALID_ARG
+    bad = np.array([0, 3], dtype=np.int32)
+    st = lib.lslu_create_shared(2, 2, rp2.ctypes.data, bad.ctypes.data, v.ctypes.data, 2, 1,
+                                10, None, ctypes.byref(h))
+    assert st == lslu.ERR_INVALID_ARG and b"column index" in lib.lslu_error_string(None)
 
 
 def test_null_handle_calls_fail_cleanly(lib):

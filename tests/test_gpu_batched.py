@@ -120,3 +120,34 @@ def test_fixed_lambda_validation(small_batch):
             bs.solve(np.concatenate([P.b for P in small_batch[:2]]), 5, "fixed", -1.0)
         with pytest.raises(lslu.LsluError):
             bs.solve(np.concatenate([P.b for P in small_batch[:2]]), 6, "gcv")
+
+
+@pytest.mark.parametrize("vt", ["f32", "bf16"])
+@pytest.mark.parametrize("nrhs", [1, 3, 8, 16])
+def test_shared_matrix_rhs_equal_single_solves(vt, nrhs):
+    """Right-hand sides sharing one matrix (one pass over A per product for
+    all of them) give each the single-problem result bit for bit."""
+    Ps = tomo.make_shared_rhs("ct32", nrhs, seed=5100)
+    K = 30
+    b = np.concatenate([P.b for P in Ps])
+    with lslu.shared_rhs(Ps[0], nrhs, vt, K) as bs:
+        r = bs.solve(b, K, "gcv")
+        r2 = bs.solve(b, K, "gcv")  # graph replay
+    for p, P in enumerate(Ps):
+        s = single(P, vt, K, "gcv")
+        assert r["status"][p] == s["status"] and r["k_done"][p] == s["k_done"]
+        assert np.array_equal(r["gp"][p], s["gp"]) and np.array_equal(r["tp"][p], s["tp"])
+        assert np.array_equal(r["x"][p], s["x"]), p
+        assert np.array_equal(r2["x"][p], s["x"])
+
+
+def test_shared_matrix_breakdown_is_local():
+    Ps = tomo.make_shared_rhs("ct32", 4, seed=5200)
+    bs_ = [P.b for P in Ps]
+    bs_[1] = np.zeros(Ps[1].m)
+    with lslu.shared_rhs(Ps[0], 4, "f32", 12) as bs:
+        r = bs.solve(np.concatenate(bs_), 12, "wgcv")
+    assert r["status"][1] == lslu.BREAKDOWN_BETA and np.all(r["x"][1] == 0.0)
+    for p in (0, 2, 3):
+        s = single(Ps[p], "f32", 12, "wgcv")
+        assert np.array_equal(r["x"][p], s["x"])
