@@ -25,6 +25,12 @@ design notes):
       sigma_1 * 10^[-14, 2]; the best grid point (ties -> smaller lambda) is
       refined by 64 bisection steps in log(lambda) on the sign of dG/d(lambda^2)
       inside its two neighbours, kept only if it does not increase G.
+  R12 stopping function (Eq. stop2): its numerator is read as n times the
+      projected residual ||beta e1 - H y_k||^2 (the printed formula has a '+'
+      where the filter factor multiplies [U^T e1]_i; its derivation gives the
+      product), its denominator as ((m - k) + sum_i lam_k^2/(sigma_i^2+lam_k^2))^2
+      with lam_k the parameter chosen at iteration k; the iteration stops at the
+      first k with |G^(k+1) - G^(k)| / G^(1) < tol (Eq. tol) and returns x_k.
 """
 from __future__ import annotations
 
@@ -275,3 +281,47 @@ def hybrid_lslu(A, b, x0=None, K=10, rule="gcv", lam=0.0, histories=True):
     return OracleResult(x=x, gp=hp["gp"], tp=hp["tp"], beta=hp["beta"], H=hp["H"],
                         W=hp["W"], L=hp["L"], D=hp["D"], lam_hist=lam_hist,
                         res_hist=res_hist, status=hp["status"], k_done=k)
+
+
+def stopping_gcv_value(sigma, c, lam, n, m):
+    """G^(k) of Eq. (stop2) for one k (reading R12): sigma (k), c = beta U^T e1
+    (k+1), lam = lam_k, n and m the dimensions of A."""
+    k = sigma.shape[0]
+    L2 = lam * lam
+    f = L2 / (sigma * sigma + L2)
+    num = n * (float(np.sum((f * c[:k]) ** 2)) + float(c[k] ** 2))
+    den = (m - k) + float(np.sum(f))
+    return num / (den * den)
+
+
+def stopping_iteration(G, tol):
+    """First k (1-based) with |G(k+1) - G(k)| / G(1) < tol (Eq. tol), or the
+    last k when the test never passes.  G[i] holds G^(i+1)."""
+    for k in range(1, len(G)):
+        if abs((G[k] - G[k - 1]) / G[0]) < tol:
+            return k
+    return len(G)
+
+
+def hybrid_lslu_stopping(A, b, K_max, rule="wgcv", lam=0.0, tol=1e-6):
+    """Hybrid LSLU with the stopping criterion of Section 3.4: runs up to K_max
+    iterations, evaluates G^(k) for every k with the lambda_k of the rule and
+    returns (x_k at the stopping iteration, k, G history)."""
+    m, n = A.shape
+    hp = hessenberg_rect_pivoted(A, b, None, K_max)
+    kd = hp["k"]
+    G = np.zeros(kd)
+    lams = np.zeros(kd)
+    for kk in range(1, kd + 1):
+        Hk = hp["H"][:kk + 1, :kk]
+        s_, c_, _ = projected_svd(Hk, hp["beta"])
+        lk = _lambda_for(rule, lam, s_, c_, kk, m)
+        lams[kk - 1] = lk
+        G[kk - 1] = stopping_gcv_value(s_, c_, lk, n, m)
+    k = stopping_iteration(G, tol) if kd > 0 else 0
+    x = np.zeros(n)
+    if k > 0:
+        Hk = hp["H"][:k + 1, :k]
+        s_, c_, V = projected_svd(Hk, hp["beta"])
+        x = hp["L"][:, :k] @ tikhonov_y(s_, c_, V, lams[k - 1])
+    return x, k, G
