@@ -186,6 +186,22 @@ lslu_status lslu_solve_fixed_pivots(lslu_handle h, const double* b, const double
 lslu_status lslu_adjoint(lslu_handle h, const double* x_bar, int32_t ptr_location,
                          double* b_bar, double* lambda_bar, double* x0_bar);
 
+/* Hybrid LSLU with the stopping criterion of Section 3.4: runs up to K_max
+ * iterations (2 <= K_max <= max_iter), solves the projected problem of every
+ * k with the lambda rule, evaluates
+ *   G^(k) = n ||beta e1 - H_{k+1,k} y_k||^2 / ((m - k) + sum_i lam_k^2/(sigma_i^2 + lam_k^2))^2
+ * (Eq. stop2, read with the filter factor multiplying [U^T e1]_i as in its
+ * derivation) and stops at the first k with |G^(k+1) - G^(k)| / G^(1) < tol
+ * (Eq. tol), else at the last completed iteration.  Outputs (host or device per
+ * ptr_location): x_out (n) = x_k at that iteration (equal to lslu_solve with
+ * K = k), k_stop (1), g_hist (K_max, may be NULL; zero past k_done).  The
+ * iterations past k_stop are computed (the test needs G^(k+1)); the basis of
+ * the first k is independent of them.  A breakdown ends the sequence at
+ * k_done. */
+lslu_status lslu_solve_stopping(lslu_handle h, const double* b, const double* x0, int32_t K_max,
+                                int32_t rule, double lambda, double tol, int32_t ptr_location,
+                                double* x_out, int32_t* k_stop, double* g_hist);
+
 /* Copy the state of the last lslu_solve (host or device per ptr_location;
  * any pointer may be NULL).  k = *k_done of that solve.
  *   H  (k+1) x k FP64 column-major, W k x k FP64 column-major, beta 1 FP64,

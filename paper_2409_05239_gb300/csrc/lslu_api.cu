@@ -160,7 +160,7 @@ lslu_status create_common(lslu_ctx* c, const int64_t* rp, const int32_t* ci, con
   // space is allocated on first use)
   CKC(dmalloc(&c->pw_single, (size_t)P * projected_slot_doubles(K, c->pw_cluster)));
   c->res_off = K > P ? K : P;
-  CKC(dmalloc(&c->proj_out, 2 * (size_t)c->res_off));
+  CKC(dmalloc(&c->proj_out, 3 * (size_t)c->res_off));  // lambda, residual, trace
   CKC(dmalloc(&c->y, (size_t)P * K));
   CKC(dmalloc(&c->sig, K));
   CKC(dmalloc(&c->cvec, K + 1));
@@ -409,6 +409,7 @@ int64_t enqueue_solve(Ctx* c, cudaStream_t s, const double* db, const double* dx
   pa.strideH = c->h_stride;
   pa.lam_out = c->proj_out;
   pa.res_out = c->proj_out + c->res_off;
+  pa.tr_out = hist ? c->proj_out + 2 * c->res_off : nullptr;
   pa.st = c->st;
   pa.tstamp = c->proj_tstamp;
   ProjWork w;
@@ -922,6 +923,98 @@ extern "C" lslu_status lslu_solve_batched(lslu_handle h, const double* b, int32_
   if (status) CK(cudaMemcpyAsync(status, sv.data(), sv.size() * 4, h2o, s));
   CK(cudaStreamSynchronize(s));
   c->last_k = -1;  // lslu_get_state serves single-problem handles only
+  return LSLU_OK;
+}
+
+extern "C" lslu_status lslu_solve_stopping(lslu_handle h, const double* b, const double* x0,
+                                           int32_t K_max, int32_t rule, double lambda,
+                                           double tol, int32_t ptr_location, double* x_out,
+                                           int32_t* k_stop, double* g_hist) {
+  Ctx* c = h;
+  if (!c) return set_err(nullptr, LSLU_ERR_INVALID_ARG, "NULL handle");
+  if (c->map_m) return set_err(c, LSLU_ERR_INVALID_ARG, "single-problem handles only");
+  if (K_max < 2 || K_max > c->kmax)
+    return set_err(c, LSLU_ERR_INVALID_ARG, "K_max must be in [2, max_iter]");
+  if (rule < LSLU_LAMBDA_NONE || rule > LSLU_LAMBDA_WGCV)
+    return set_err(c, LSLU_ERR_INVALID_ARG, "unknown lambda rule");
+  if (rule == LSLU_LAMBDA_FIXED && !(lambda >= 0.0 && std::isfinite(lambda)))
+    return set_err(c, LSLU_ERR_INVALID_ARG, "fixed lambda must be finite and >= 0");
+  if (!(tol > 0.0) || !std::isfinite(tol))
+    return set_err(c, LSLU_ERR_INVALID_ARG, "tol must be finite and > 0");
+  if (!b || !x_out) return set_err(c, LSLU_ERR_INVALID_ARG, "b and x_out are required");
+  if (ptr_location != LSLU_HOST && ptr_location != LSLU_DEVICE)
+    return set_err(c, LSLU_ERR_INVALID_ARG, "unknown ptr_location");
+  const bool host = ptr_location == LSLU_HOST;
+  const int64_t m = c->m, n = c->n;
+  cudaStream_t s = c->stream;
+  if (host)
+    for (int64_t i = 0; i < m; ++i)
+      if (!std::isfinite(b[i])) return set_err(c, LSLU_ERR_NONFINITE, "b has a non-finite entry");
+  const cudaMemcpyKind h2d = host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  CK(cudaMemcpyAsync(c->xin, b, m * 8, h2d, s));
+  const double* dx0 = nullptr;
+  if (x0) {
+    CK(cudaMemcpyAsync(c->xin + m, x0, n * 8, h2d, s));
+    dx0 = c->xin + m;
+  }
+  const double lam = rule == LSLU_LAMBDA_FIXED ? lambda : 0.0;
+  // the basis for K_max iterations and the projected problem of every k
+  lslu_status st = c->value_type == LSLU_F64
+                       ? solve_impl<double, double>(c, c->xin, dx0, K_max, rule, lam, true)
+                       : solve_impl<float, float>(c, c->xin, dx0, K_max, rule, lam, true);
+  if (st != LSLU_OK) return st;
+  c->adj_valid = false;
+  c->last_k = std::min<int>(std::max(c->st_host[0].k_done, 0), K_max);
+  c->last_K = K_max;
+  // G^(k) for every k and the stopping iteration (Eqs. stop2, tol)
+  double* G = c->proj_out + 2 * c->res_off;  // G overwrites the trace in place
+  int32_t* dk = reinterpret_cast<int32_t*>(c->part_idx);
+  launch_stop_select(c->proj_out + c->res_off, G, K_max, (double)n, (double)m, tol, c->st, dk, s);
+  int32_t ks = 0;
+  CK(cudaMemcpyAsync(&ks, dk, 4, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  CK(cudaGetLastError());
+  if (ks > 0) {  // y_k and x_k at the stopping iteration
+    ProjArgs pa;
+    std::memset(&pa, 0, sizeof(pa));
+    pa.H = c->H;
+    pa.ldh = c->kmax + 1;
+    pa.rule = rule;
+    pa.lambda = lam;
+    pa.m = c->prob_m[0];
+    pa.k_first = ks;
+    pa.k_last = ks;
+    pa.want_y = 1;
+    pa.y = c->y;
+    pa.ldy = c->kmax;
+    pa.nbatch = 1;
+    pa.st = c->st;
+    ProjWork w;
+    w.base = c->pw_single;
+    w.cluster = c->pw_cluster;
+    w.slot_stride = projected_slot_doubles(c->kmax, c->pw_cluster);
+    CK(launch_projected(pa, w, s));
+    if (c->value_type == LSLU_F64)
+      launch_recombine<double>((const double*)c->L, c->ldl, c->y, c->kmax, dx0, c->xout, n,
+                               nullptr, 1, nullptr, ks, s, c->num_sms);
+    else
+      launch_recombine<float>((const float*)c->L, c->ldl, c->y, c->kmax, dx0, c->xout, n,
+                              nullptr, 1, nullptr, ks, s, c->num_sms);
+  } else {
+    CK(cudaMemsetAsync(c->xout, 0, n * 8, s));
+    if (dx0) CK(cudaMemcpyAsync(c->xout, dx0, n * 8, cudaMemcpyDeviceToDevice, s));
+  }
+  const cudaMemcpyKind d2o = host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  CK(cudaMemcpyAsync(x_out, c->xout, n * 8, d2o, s));
+  if (g_hist) CK(cudaMemcpyAsync(g_hist, G, (size_t)K_max * 8, d2o, s));
+  if (k_stop) {
+    if (host)
+      *k_stop = ks;
+    else
+      CK(cudaMemcpyAsync(k_stop, dk, 4, cudaMemcpyDeviceToDevice, s));
+  }
+  CK(cudaStreamSynchronize(s));
+  CK(cudaGetLastError());
   return LSLU_OK;
 }
 

@@ -256,6 +256,10 @@ void launch_scale(const CT* v, BT* out, int64_t rows, DevState* st, int nprob,
                   const int32_t* tile_prob, cudaStream_t s, int num_sms);
 
 void launch_residual0(const double* b, const double* Ax0, double* r0, int64_t m, cudaStream_t s);
+// G^(k) of Eq. (stop2) for k = 1..K from the projected residuals and traces
+// (G may alias tr), and the stopping iteration of Eq. (tol) into *k_stop.
+void launch_stop_select(const double* res, double* G, int K, double n, double m, double tol,
+                        const DevState* st, int32_t* k_stop, cudaStream_t s);
 void launch_init_state(DevState* st, int nprob, int K, cudaStream_t s);
 void launch_scatter(const double* src, const int32_t* map, int64_t count, double* dst,
                     cudaStream_t s);
@@ -284,6 +288,7 @@ struct ProjArgs {
   int64_t ldc;
   double* lam_out;  // per problem (may be null), index k-1
   double* res_out;  // per problem (may be null), index k-1
+  double* tr_out;   // sum_i lam^2/(sigma_i^2+lam^2) per problem (may be null), index k-1
   const DevState* st;  // if non-null (per batch entry), problems with k > k_done
                        // are skipped and the y problem uses k = k_done
   unsigned long long* tstamp;  // optional phase timestamps (ns) of the last problem

@@ -289,10 +289,12 @@ __global__ void __launch_bounds__(kT) k_projected(ProjArgs a, ProjWork w) {
   const int k = is_final ? min(kk, kdone) : kk;
   double* lam_o = a.lam_out ? a.lam_out + (batch ? p : kk - 1) : nullptr;
   double* res_o = a.res_out ? a.res_out + (batch ? p : kk - 1) : nullptr;
+  double* tr_o = a.tr_out ? a.tr_out + (batch ? p : kk - 1) : nullptr;
   if (k <= 0 || (!is_final && kk > kdone)) {
     if (rank == 0 && threadIdx.x == 0) {
       if (lam_o) *lam_o = 0.0;
       if (res_o) *res_o = 0.0;
+      if (tr_o) *tr_o = 0.0;
     }
     return;  // the whole cluster leaves: no barrier is left waiting
   }
@@ -611,19 +613,22 @@ __global__ void __launch_bounds__(kT) k_projected(ProjArgs a, ProjWork w) {
     }
   }
 
-  // ---- 5. projected residual -------------------------------------------------
-  double rs = 0.0;
+  // ---- 5. projected residual (and the filter-factor trace of Eq. stop2) ----
+  double rs = 0.0, tr = 0.0;
   if (lam != 0.0) {
     const double L2 = lam * lam;
     for (int i = tid; i < k; i += nt) {
       const double f = L2 / (sig[i] * sig[i] + L2);
       rs = fma(f * f, c2[i], rs);
+      tr += f;
     }
   }
   rs = block_sum(rs, red);
+  if (tr_o) tr = block_sum(tr, red);
   if (tid == 0) {
     if (lam_o) *lam_o = lam;
     if (res_o) *res_o = sqrt(rs + c2[k]);
+    if (tr_o) *tr_o = tr;
   }
   if (a.sig)
     for (int i = tid; i < k; i += nt) a.sig[(int64_t)prob * a.ldsig + i] = sig[i];

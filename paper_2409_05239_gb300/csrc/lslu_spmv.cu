@@ -254,7 +254,7 @@ __global__ void __launch_bounds__(256, ValTraits<VT>::kMinBlocks)
   const int lane = threadIdx.x & 31;
   const int npiv_all = pc.npiv_blocks * pc.nprob;
   if ((int)blockIdx.x < npiv_all) {
-    pivot_blocks<YT>(pc, [&](int, int32_t row, int gl) {
+    pivot_blocks<YT>(pc, [=](int, int32_t row, int gl) {
       return row_dot<VT, XT, YT>(row, true, rp, rl, col, val, x, gl);
     });
     return;
@@ -322,7 +322,7 @@ __global__ void __launch_bounds__(256, 4)
   const int lane = threadIdx.x & 31;
   const int npiv_all = pc.npiv_blocks * pc.nprob;
   if ((int)blockIdx.x < npiv_all) {
-    pivot_blocks<float>(pc, [&](int p, int32_t row, int gl) {
+    pivot_blocks<float>(pc, [=](int p, int32_t row, int gl) {
       return row_dot_rhs<VT, RS>((int64_t)row - (int64_t)p * ystride, rp, rl, col, val, xi, p,
                                  gl);
     });

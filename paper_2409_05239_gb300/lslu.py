@@ -26,7 +26,8 @@ HOST, DEVICE = 0, 1
 EXPORTS = ("lslu_create", "lslu_solve", "lslu_get_state", "lslu_spmv", "lslu_projected",
            "lslu_projected_noalloc", "lslu_profile", "lslu_timing", "lslu_last_launch_count",
            "lslu_error_string", "lslu_destroy", "lslu_create_batched", "lslu_solve_batched",
-           "lslu_adjoint", "lslu_solve_fixed_pivots", "lslu_create_shared")
+           "lslu_adjoint", "lslu_solve_fixed_pivots", "lslu_create_shared",
+           "lslu_solve_stopping")
 
 _lib = None
 
@@ -79,6 +80,8 @@ def load(path: str | None = None):
     lib.lslu_solve_batched.restype = i32
     lib.lslu_solve_fixed_pivots.argtypes = [vp, vp, vp, i32, i32, f64, i32, vp, vp, vp, vp]
     lib.lslu_solve_fixed_pivots.restype = i32
+    lib.lslu_solve_stopping.argtypes = [vp, vp, vp, i32, i32, f64, f64, i32, vp, vp, vp]
+    lib.lslu_solve_stopping.restype = i32
     lib.lslu_adjoint.argtypes = [vp, vp, i32, vp, vp, vp]
     lib.lslu_adjoint.restype = i32
     lib.lslu_destroy.argtypes = [vp]
@@ -183,6 +186,21 @@ class Solver:
                                               ctypes.addressof(kd))
         self._check(st, allow_breakdown=True)
         return dict(x=x, k_done=kd.value, status=st)
+
+    def solve_stopping(self, b, K_max, rule="wgcv", lam=0.0, tol=1e-6, x0=None):
+        """Solve with the stopping criterion G^(k) (host arrays): returns x at
+        the stopping iteration, k_stop and the G history."""
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        x0 = None if x0 is None else np.ascontiguousarray(x0, dtype=np.float64)
+        x = np.zeros(self.n)
+        g = np.zeros(K_max)
+        ks = ctypes.c_int32(0)
+        self.epoch += 1
+        st = self.lib.lslu_solve_stopping(self.h, _ptr(b), _ptr(x0), int(K_max), RULES[rule],
+                                          float(lam), float(tol), HOST, _ptr(x),
+                                          ctypes.addressof(ks), _ptr(g))
+        self._check(st)
+        return dict(x=x, k_stop=ks.value, G=g)
 
     def adjoint(self, x_bar, want_x0=False):
         """Reverse-mode derivative of the last solve (pivots fixed): host

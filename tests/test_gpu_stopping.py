@@ -1,0 +1,64 @@
+"""Stopping criterion G^(k) on the GPU (lslu_solve_stopping) against the
+oracle (Eqs. stop2, tol)."""
+import numpy as np
+import pytest
+
+import oracle.lslu_oracle as O
+from paper_2409_05239_gb300 import lslu, tomo
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2409_05239_gb300 import build
+
+    build.build()
+
+
+@pytest.fixture(scope="module")
+def ct32():
+    return tomo.make_config("ct32")
+
+
+def margin_ok(G, k, tol, rel=1e-6):
+    """True when no step before k (nor at k) sits within rel of the threshold,
+    so two correct FP64 implementations must stop at the same k."""
+    d = np.abs(np.diff(G)) / abs(G[0])
+    return all(abs(v - tol) > rel * tol for v in d[:k])
+
+
+@pytest.mark.parametrize("rule,lam", [("wgcv", 0.0), ("gcv", 0.0), ("fixed", 1e-2)])
+@pytest.mark.parametrize("tol", [1e-6, 1e-4])
+def test_stopping_f64_vs_oracle(ct32, rule, lam, tol):
+    K = 50
+    x_ref, k_ref, G_ref = O.hybrid_lslu_stopping(ct32.scipy(), ct32.b, K, rule, lam, tol)
+    with lslu.from_problem(ct32, "f64", K) as s:
+        r = s.solve_stopping(ct32.b, K, rule, lam, tol)
+        assert np.allclose(r["G"], G_ref, rtol=1e-8, atol=0)
+        if margin_ok(G_ref, k_ref, tol):
+            assert r["k_stop"] == k_ref
+        ref_k = s.solve(ct32.b, r["k_stop"], rule, lam)
+    # x at the stopping iteration equals the plain solve with K = k_stop
+    assert np.array_equal(r["x"], ref_k["x"])
+    if r["k_stop"] == k_ref:
+        assert np.linalg.norm(r["x"] - x_ref) <= 1e-10 * np.linalg.norm(x_ref)
+
+
+def test_stopping_mixed_and_large():
+    P = tomo.make_config("ct256")
+    with lslu.from_problem(P, "f32", 150) as s:
+        r = s.solve_stopping(P.b, 150, "wgcv", 0.0, 1e-6)
+        k = r["k_stop"]
+        assert 1 <= k <= 150
+        assert np.all(r["G"][:k] > 0)
+        ref = s.solve(P.b, k, "wgcv")
+    assert np.array_equal(r["x"], ref["x"])
+
+
+def test_stopping_argument_checks(ct32):
+    with lslu.from_problem(ct32, "f64", 10) as s:
+        with pytest.raises(lslu.LsluError):
+            s.solve_stopping(ct32.b, 1, "gcv")
+        with pytest.raises(lslu.LsluError):
+            s.solve_stopping(ct32.b, 10, "gcv", tol=0.0)
