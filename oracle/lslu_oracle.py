@@ -31,6 +31,11 @@ design notes):
       product), its denominator as ((m - k) + sum_i lam_k^2/(sigma_i^2+lam_k^2))^2
       with lam_k the parameter chosen at iteration k; the iteration stops at the
       first k with |G^(k+1) - G^(k)| / G^(1) < tol (Eq. tol) and returns x_k.
+  R15 sampled pivots (Section 2.2): pick t (t = 0 for r0, 2k+1 for q and 2k+2
+      for u at iteration k) takes the largest |entry| among the unpivoted
+      indices of row t of a given sample table (ties -> lowest index); when no
+      sampled unpivoted entry is non-zero it falls back to the full search.
+      The random indices are inputs, drawn by the caller.
 """
 from __future__ import annotations
 
@@ -74,14 +79,37 @@ def _argmax_abs_unpivoted(v: np.ndarray, pivoted: np.ndarray):
     return int(np.argmax(a))  # numpy argmax returns the first maximum
 
 
-def hessenberg_rect_pivoted(A, b, x0, K):
+def _sampled_pivot(v, pivoted, sample):
+    """Pivot of Section 2.2's sampled variant (reading R15), or None when no
+    sampled unpivoted entry is non-zero."""
+    best, bi = 0.0, None
+    for i in sorted(set(int(j) for j in sample)):
+        if pivoted[i]:
+            continue
+        a = abs(v[i])
+        if a > best:
+            best, bi = a, i
+    return bi
+
+
+def _pick(v, pivoted, samples, t):
+    if samples is not None:
+        i = _sampled_pivot(v, pivoted, samples[t])
+        if i is not None:
+            return i
+    return _argmax_abs_unpivoted(v, pivoted)
+
+
+def hessenberg_rect_pivoted(A, b, x0, K, samples=None):
     """Hessenberg process with pivoting for rectangular A (Algorithm 4).
 
     A is an m x n scipy sparse matrix (or dense array), b length m, x0 length n
     or None.  Runs up to K iterations.  Returns a dict with L (n x k),
     D (m x (k+1)), H ((k+1) x k), W (k x k), pivots gp (k), tp (k+1), beta,
     status and k (completed iterations).  Relations (Eqs. nhr / nhr2):
-    A L_k = D_{k+1} H_{k+1,k} and A^T D_k = L_k W_k.
+    A L_k = D_{k+1} H_{k+1,k} and A^T D_k = L_k W_k.  samples (optional, one
+    row of indices per pivot pick, 2K+1 rows) selects the sampled pivoting of
+    Section 2.2 (reading R15).
     """
     m, n = A.shape
     r0 = np.array(b, dtype=np.float64, copy=True)
@@ -97,7 +125,7 @@ def hessenberg_rect_pivoted(A, b, x0, K):
     t_used = np.zeros(m, dtype=bool)
 
     # initialisation: beta = signed max-abs entry of r0 (R6), d_1 = r0 / beta
-    i = _argmax_abs_unpivoted(r0, t_used)
+    i = _pick(r0, t_used, samples, 0)
     if i is None or r0[i] == 0.0 or not np.isfinite(r0[i]):
         return dict(L=L[:, :0], D=D[:, :0], H=H[:0, :0], W=W[:0, :0], gp=gp[:0],
                     tp=tp[:0], beta=0.0, status=BREAKDOWN_BETA, k=0)
@@ -114,7 +142,7 @@ def hessenberg_rect_pivoted(A, b, x0, K):
         for j in range(k):
             W[j, k] = q[gp[j]]
             q = q - W[j, k] * L[:, j]
-        i = _argmax_abs_unpivoted(q, g_used)
+        i = _pick(q, g_used, samples, 2 * k + 1)
         if i is None or q[i] == 0.0:
             status = BREAKDOWN_W
             break
@@ -128,7 +156,7 @@ def hessenberg_rect_pivoted(A, b, x0, K):
         for j in range(k + 1):
             H[j, k] = u[tp[j]]
             u = u - H[j, k] * D[:, j]
-        i = _argmax_abs_unpivoted(u, t_used)
+        i = _pick(u, t_used, samples, 2 * k + 2)
         if i is None or u[i] == 0.0:
             status = BREAKDOWN_H
             break
@@ -251,7 +279,7 @@ def _lambda_for(rule, lam_fixed, sigma, c, k, m):
     raise ValueError(rule)
 
 
-def hybrid_lslu(A, b, x0=None, K=10, rule="gcv", lam=0.0, histories=True):
+def hybrid_lslu(A, b, x0=None, K=10, rule="gcv", lam=0.0, histories=True, samples=None):
     """Hybrid LSLU (Algorithm 5); rule 'none' is plain LSLU (lambda = 0).
 
     Returns an OracleResult with x_k for the last completed iteration k,
@@ -261,7 +289,7 @@ def hybrid_lslu(A, b, x0=None, K=10, rule="gcv", lam=0.0, histories=True):
     if rule not in RULES:
         raise ValueError(rule)
     m, n = A.shape
-    hp = hessenberg_rect_pivoted(A, b, x0, K)
+    hp = hessenberg_rect_pivoted(A, b, x0, K, samples)
     k = hp["k"]
     x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
     lam_hist = np.zeros(k)
