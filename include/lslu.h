@@ -152,6 +152,20 @@ lslu_status lslu_solve_batched(lslu_handle h, const double* b, int32_t K, int32_
                                int32_t* col_pivots, int32_t* row_pivots, int32_t* k_done,
                                int32_t* status);
 
+/* lslu_solve with the sampled pivoting of Section 2.2: every pivot is the
+ * largest |entry| among the unpivoted rows of a small sample instead of the
+ * whole vector (ties: lowest index); when no sampled unpivoted entry is
+ * non-zero the full search is used.  samples holds 2K+1 rows of nsamp int32
+ * indices (row-major; host or device per ptr_location): row 0 for r0 and
+ * row 2k+2 for u at iteration k index [0, m), row 2k+1 for q indexes [0, n).
+ * The caller draws the random indices (any generator), so results are
+ * reproducible from the table.  Single-problem handles; 1 <= nsamp <= 65536.
+ * Outputs as lslu_solve. */
+lslu_status lslu_solve_sampled(lslu_handle h, const double* b, const double* x0, int32_t K,
+                               int32_t rule, double lambda, const int32_t* samples,
+                               int32_t nsamp, int32_t ptr_location, double* x_out,
+                               int32_t* col_pivots, int32_t* row_pivots, int32_t* k_done);
+
 /* lslu_solve with the pivot lists given instead of searched: iteration k
  * takes row col_pivots[k] of the L-side vector and row row_pivots[k+1] of the
  * D-side vector as its pivots (row_pivots[0] for r0), whatever their

@@ -65,7 +65,7 @@ void destroy_ctx(lslu_ctx* c) {
                   c->cvec, c->xout, c->tile_prob_m, c->tile_prob_n, c->pad_m, c->pad_n,
                   c->map_m, c->map_n, c->xin_pad, c->xout_user, c->mvec,
                   c->adj_Vb, c->adj_Zb, c->adj_vec, c->adj_small, c->adj_part,
-                  c->fixed_gp, c->fixed_tp, c->xi};
+                  c->fixed_gp, c->fixed_tp, c->xi, c->samples};
   for (void* p : ptrs) cudaFree(p);
   if (c->st_host) cudaFreeHost(c->st_host);
   for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
@@ -292,7 +292,12 @@ void collect_spmv_times(Ctx* c, int pairs) {
 // and x = x0 + L y.  Inputs are read from the handle's staging buffers.
 template <typename BT, typename CT>
 int64_t enqueue_solve(Ctx* c, cudaStream_t s, const double* db, const double* dx0, int K,
-                      int rule, double lam, bool hist, bool capturing, bool fixed) {
+                      int rule, double lam, bool hist, bool capturing, bool fixed, int nsamp) {
+  // sampled pivoting: pick t uses row t of the sample table (t = 0 for r0,
+  // 2k+1 for q and 2k+2 for u at iteration k)
+  auto samp = [&](int t) -> const int32_t* {
+    return nsamp > 0 ? c->samples + (int64_t)t * nsamp : nullptr;
+  };
   c->ev_used = 0;
   const int64_t m = c->m, n = c->n;
   const int vt = c->value_type;
@@ -331,7 +336,7 @@ int64_t enqueue_solve(Ctx* c, cudaStream_t s, const double* db, const double* dx
   {
     PivotArgs pa{c->tp, c->kmax + 1, 0, c->tused, nullptr, 0, c->ldt, LSLU_BREAKDOWN_BETA,
                  0, 1, c->TDi, c->t_stride, c->coef, c->c_stride, P, tpm,
-                 fixed ? c->fixed_tp : nullptr};
+                 fixed ? c->fixed_tp : nullptr, samp(0), nsamp};
     launch_init_pivot<BT>(c->r0, m, pa, c->st, s, c->num_sms);
     launch_scale<double, BT>(c->r0, D, m, c->st, P, tpm, s, c->num_sms);
     launches += 3;
@@ -360,7 +365,7 @@ int64_t enqueue_solve(Ctx* c, cudaStream_t s, const double* db, const double* dx
     record_spmv_end(c, s, capturing, e0);
     PivotArgs paw{c->gp, c->kmax, k, c->gused, c->W + k + k * ldw, c->w_stride, c->ldt,
                   LSLU_BREAKDOWN_W, k, 0, c->TLi, c->t_stride, c->coef, c->c_stride, P, tpn,
-                  fixed ? c->fixed_gp : nullptr};
+                  fixed ? c->fixed_gp : nullptr, samp(2 * k + 1), nsamp};
     launch_eliminate_argmax<CT, BT, CT>(q, L, c->ldl, k, n, q, paw, c->part_val, c->part_idx,
                                         c->part_cap, c->st, s, c->num_sms);
     launch_scale<CT, BT>(q, L + (int64_t)k * c->ldl, n, c->st, P, tpn, s, c->num_sms);
@@ -385,7 +390,7 @@ int64_t enqueue_solve(Ctx* c, cudaStream_t s, const double* db, const double* dx
     record_spmv_end(c, s, capturing, e0);
     PivotArgs pah{c->tp, c->kmax + 1, k + 1, c->tused, c->H + (k + 1) + k * ldh, c->h_stride,
                   c->ldt, LSLU_BREAKDOWN_H, k, 0, c->TDi, c->t_stride, c->coef, c->c_stride, P,
-                  tpm, fixed ? c->fixed_tp : nullptr};
+                  tpm, fixed ? c->fixed_tp : nullptr, samp(2 * k + 2), nsamp};
     launch_eliminate_argmax<CT, BT, CT>(u, D, c->ldd, k + 1, m, u, pah, c->part_val,
                                         c->part_idx, c->part_cap, c->st, s, c->num_sms);
     launch_scale<CT, BT>(u, D + (int64_t)(k + 1) * c->ldd, m, c->st, P, tpm, s, c->num_sms);
@@ -443,7 +448,7 @@ lslu_status ensure_batched_workspace(Ctx* c) {
 
 template <typename BT, typename CT>
 lslu_status solve_impl(Ctx* c, const double* db, const double* dx0, int K, int rule, double lam,
-                       bool hist, bool fixed = false) {
+                       bool hist, bool fixed = false, int nsamp = 0) {
   if (hist) {
     lslu_status st = ensure_batched_workspace(c);
     if (st != LSLU_OK) return st;
@@ -452,7 +457,7 @@ lslu_status solve_impl(Ctx* c, const double* db, const double* dx0, int K, int r
   int ev_pairs = 0;
   if (c->profile) ensure_events(c, 4 * K + 8);
   if (!c->use_graphs) {
-    c->launches = enqueue_solve<BT, CT>(c, s, db, dx0, K, rule, lam, hist, false, fixed);
+    c->launches = enqueue_solve<BT, CT>(c, s, db, dx0, K, rule, lam, hist, false, fixed, nsamp);
     ev_pairs = c->ev_used / 2;
     CK(cudaGetLastError());
   } else {
@@ -461,13 +466,14 @@ lslu_status solve_impl(Ctx* c, const double* db, const double* dx0, int K, int r
     Ctx::GraphEntry* ge = nullptr;
     for (auto& g : c->graphs)
       if (g.K == K && g.rule == rule && g.hist == (int)hist && g.has_x0 == has_x0 &&
-          g.lam == lam && g.prof == prof && g.fixed == (int)fixed)
+          g.lam == lam && g.prof == prof && g.fixed == (int)fixed && g.nsamp == nsamp &&
+          g.samples == (nsamp ? (const void*)c->samples : nullptr))
         ge = &g;
     if (!ge) {
       cudaGraph_t graph;
       CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
       const int64_t nl =
-          enqueue_solve<BT, CT>(c, c->cap_stream, db, dx0, K, rule, lam, hist, true, fixed);
+          enqueue_solve<BT, CT>(c, c->cap_stream, db, dx0, K, rule, lam, hist, true, fixed, nsamp);
       const int pairs = c->ev_used / 2;
       cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
       if (e != cudaSuccess) {
@@ -483,7 +489,8 @@ lslu_status solve_impl(Ctx* c, const double* db, const double* dx0, int K, int r
         cudaGraphExecDestroy(c->graphs.front().exec);
         c->graphs.erase(c->graphs.begin());
       }
-      c->graphs.push_back({K, rule, (int)hist, has_x0, lam, exec, nl, prof, pairs, (int)fixed});
+      c->graphs.push_back({K, rule, (int)hist, has_x0, lam, exec, nl, prof, pairs, (int)fixed,
+                           nsamp ? (const void*)c->samples : nullptr, nsamp});
       ge = &c->graphs.back();
     }
     CK(cudaEventRecord(c->ev_in, s));
@@ -522,7 +529,8 @@ namespace {
 lslu_status solve_entry(Ctx* c, const double* b, const double* x0, int32_t K, int32_t rule,
                         double lambda, int32_t ptr_location, double* x_out, int32_t* col_pivots,
                         int32_t* row_pivots, double* lambda_hist, double* resid_hist,
-                        int32_t* k_done, const int32_t* fix_g, const int32_t* fix_t) {
+                        int32_t* k_done, const int32_t* fix_g, const int32_t* fix_t,
+                        const int32_t* samples = nullptr, int32_t nsamp = 0) {
   if (!c) return set_err(nullptr, LSLU_ERR_INVALID_ARG, "NULL handle");
   if (c->map_m) return set_err(c, LSLU_ERR_INVALID_ARG, "batched handle: use lslu_solve_batched");
   if (K < 1 || K > c->kmax) return set_err(c, LSLU_ERR_INVALID_ARG, "K must be in [1, max_iter]");
@@ -574,11 +582,39 @@ lslu_status solve_entry(Ctx* c, const double* b, const double* x0, int32_t K, in
     CK(cudaMemcpyAsync(c->fixed_tp, t.data(), (size_t)(K + 1) * 4, cudaMemcpyHostToDevice, s));
     CK(cudaStreamSynchronize(s));  // the host vectors go out of scope
   }
+  if (nsamp > 0) {  // sample table: validate on the host, stage on the device
+    const int64_t rows = 2LL * K + 1;
+    std::vector<int32_t> t((size_t)(rows * nsamp));
+    if (host)
+      std::memcpy(t.data(), samples, t.size() * 4);
+    else
+      CK(cudaMemcpy(t.data(), samples, t.size() * 4, cudaMemcpyDeviceToHost));
+    for (int64_t r = 0; r < rows; ++r) {
+      const int64_t lim = (r % 2 == 0) ? m : n;
+      for (int j = 0; j < nsamp; ++j) {
+        const int32_t v = t[(size_t)(r * nsamp + j)];
+        if (v < 0 || v >= lim)
+          return set_err(c, LSLU_ERR_INVALID_ARG,
+                         "sample indices must lie in [0, m) for even rows, [0, n) for odd rows");
+      }
+    }
+    if ((int64_t)(2LL * c->kmax + 1) * nsamp > (int64_t)c->samples_cap) {
+      if (c->samples) cudaFree(c->samples);
+      c->samples = nullptr;
+      c->samples_cap = 0;
+      const int64_t cap = (2LL * c->kmax + 1) * nsamp;
+      CK(cudaMalloc(&c->samples, (size_t)cap * 4));
+      c->samples_cap = (int)cap;
+    }
+    CK(cudaMemcpyAsync(c->samples, t.data(), t.size() * 4, cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));  // the host table goes out of scope
+  }
   const bool hist = lambda_hist || resid_hist;
   const double lam = rule == LSLU_LAMBDA_FIXED ? lambda : 0.0;
-  lslu_status st = c->value_type == LSLU_F64
-                       ? solve_impl<double, double>(c, db, dx0, K, rule, lam, hist, fixed)
-                       : solve_impl<float, float>(c, db, dx0, K, rule, lam, hist, fixed);
+  lslu_status st =
+      c->value_type == LSLU_F64
+          ? solve_impl<double, double>(c, db, dx0, K, rule, lam, hist, fixed, nsamp)
+          : solve_impl<float, float>(c, db, dx0, K, rule, lam, hist, fixed, nsamp);
   if (st != LSLU_OK) return st;
   const DevState ds = *c->st_host;
   const int kd = ds.k_done < 0 ? 0 : (ds.k_done > K ? K : ds.k_done);
@@ -644,6 +680,18 @@ extern "C" lslu_status lslu_solve(lslu_handle h, const double* b, const double* 
                                   double* lambda_hist, double* resid_hist, int32_t* k_done) {
   return solve_entry(h, b, x0, K, rule, lambda, ptr_location, x_out, col_pivots, row_pivots,
                      lambda_hist, resid_hist, k_done, nullptr, nullptr);
+}
+
+extern "C" lslu_status lslu_solve_sampled(lslu_handle h, const double* b, const double* x0,
+                                          int32_t K, int32_t rule, double lambda,
+                                          const int32_t* samples, int32_t nsamp,
+                                          int32_t ptr_location, double* x_out,
+                                          int32_t* col_pivots, int32_t* row_pivots,
+                                          int32_t* k_done) {
+  if (h && (!samples || nsamp < 1 || nsamp > 65536))
+    return set_err(h, LSLU_ERR_INVALID_ARG, "samples required, 1 <= nsamp <= 65536");
+  return solve_entry(h, b, x0, K, rule, lambda, ptr_location, x_out, col_pivots, row_pivots,
+                     nullptr, nullptr, k_done, nullptr, nullptr, samples, nsamp);
 }
 
 extern "C" lslu_status lslu_solve_fixed_pivots(lslu_handle h, const double* b, const double* x0,

@@ -133,6 +133,52 @@ __device__ void record_pivot(const PivotArgs& pa, DevState& s, int p, int besti,
   }
 }
 
+// Sampled pivoting (Section 2.2): the largest |v| among the unpivoted rows of
+// the sample (ties to the lowest index) as an FP32 key (0 when none is
+// non-zero); every thread of the block calls it, the result is valid in all.
+template <typename CT>
+__device__ unsigned long long sampled_key(const PivotArgs& pa, const CT* v) {
+  __shared__ unsigned long long sk[kThreads / 32];
+  unsigned long long k = 0;
+  for (int j = threadIdx.x; j < pa.nsamp; j += blockDim.x) {
+    const int32_t i = pa.samples[j];
+    if (!pa.used[i]) {
+      const float a = fabsf((float)__ldcg(v + i));
+      if (a != 0.0f) {
+        const unsigned long long kk = argkey(a, i);
+        k = kk > k ? kk : k;
+      }
+    }
+  }
+  k = warp_max_u64(k);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sk[threadIdx.x >> 5] = k;
+  __syncthreads();
+  unsigned long long r = 0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = sk[w] > r ? sk[w] : r;
+  __syncthreads();
+  return r;
+}
+
+// The same in FP64 (value, index) form; best = 0 when none is non-zero.
+template <typename CT>
+__device__ void sampled_best(const PivotArgs& pa, const CT* v, double& best, int& besti) {
+  best = 0.0;
+  besti = -1;
+  for (int j = threadIdx.x; j < pa.nsamp; j += blockDim.x) {
+    const int32_t i = pa.samples[j];
+    if (pa.used[i]) continue;
+    double a = fabs((double)__ldcg(v + i));
+    if (isnan(a)) a = INFINITY;
+    if (a != 0.0 && better(a, i, best, besti)) {
+      best = a;
+      besti = i;
+    }
+  }
+  block_argmax(best, besti);
+  if (besti < 0) best = 0.0;
+}
+
 // Tiles of 32*VEC rows x all cnt basis columns: every warp of the block reads
 // the tile as 16-byte vectors (VEC rows per lane) and takes the columns
 // j = w, w+8, ...; the eight per-warp partial sums of a row are combined in
@@ -263,8 +309,10 @@ __global__ void __launch_bounds__(kThreads)
   __threadfence();
   if constexpr (kKey) {
     if (threadIdx.x == 0) st[0].ticket = 0;
+    const unsigned long long skey = pa.samples ? sampled_key<CT>(pa, v) : 0ull;
     for (int p = threadIdx.x; p < pa.nprob; p += blockDim.x) {
-      const unsigned long long m = atomicExch(&st[p].amax, 0ull);
+      unsigned long long m = atomicExch(&st[p].amax, 0ull);
+      if (p == 0 && (skey >> 32) != 0) m = skey;  // sampled pivot (full search as fallback)
       if (st[p].status != LSLU_OK) continue;
       const int bi = m ? (int)(0xffffffffu - (unsigned)(m & 0xffffffffull)) : -1;
       const float a = __uint_as_float((unsigned)(m >> 32));
@@ -282,6 +330,15 @@ __global__ void __launch_bounds__(kThreads)
       }
     }
     block_argmax(best, besti);
+    if (pa.samples) {  // sampled pivot, the full search as fallback
+      double sb;
+      int si;
+      sampled_best<CT>(pa, v, sb, si);
+      if (sb > 0.0) {
+        best = sb;
+        besti = si;
+      }
+    }
     if (threadIdx.x == 0) {
       st[0].ticket = 0;
       record_pivot<CT, BT>(pa, st[0], 0, besti, best, v);
@@ -333,13 +390,20 @@ __global__ void k_r0_argmin(const double* __restrict__ r0, int64_t rows, PivotAr
   if (!is_last) return;
   __threadfence();
   if (threadIdx.x == 0) st[0].ticket = 0;
+  double sb = 0.0;
+  int si = -1;
+  if (pa.samples) sampled_best<double>(pa, r0, sb, si);
   for (int p = threadIdx.x; p < pa.nprob; p += blockDim.x) {
     const unsigned long long m = atomicExch(&st[p].amax, 0ull);
     const int bi = atomicExch(&st[p].amin, 0x7fffffff);
     if (st[p].status != LSLU_OK) continue;
-    const double best = m == 0x7ff0000000000001ull ? INFINITY
-                                                  : __longlong_as_double((long long)m);
-    record_pivot<double, BT>(pa, st[p], p, (m && bi != 0x7fffffff) ? bi : -1, best, r0);
+    double best = m == 0x7ff0000000000001ull ? INFINITY : __longlong_as_double((long long)m);
+    int besti = (m && bi != 0x7fffffff) ? bi : -1;
+    if (p == 0 && sb > 0.0) {  // sampled pivot, the full search as fallback
+      best = sb;
+      besti = si;
+    }
+    record_pivot<double, BT>(pa, st[p], p, besti, best, r0);
   }
 }
 

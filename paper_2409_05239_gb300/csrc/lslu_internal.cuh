@@ -104,6 +104,8 @@ struct Ctx {
   int32_t* tp = nullptr;  // kmax+1 per problem
   int32_t* fixed_gp = nullptr;  // pivots replayed by lslu_solve_fixed_pivots (kmax)
   int32_t* fixed_tp = nullptr;  // (kmax + 1)
+  int32_t* samples = nullptr;   // sampled-pivot table, (2 kmax + 1) x samples_cap
+  int samples_cap = 0;
   // per-problem strides of the arrays above and below
   int64_t h_stride = 0, w_stride = 0, t_stride = 0, c_stride = 0, xp_stride = 0;
   uint8_t* gused = nullptr;  // n
@@ -139,6 +141,8 @@ struct Ctx {
     int prof;      // 1: event-record nodes around every sparse product
     int ev_pairs;  // number of such event pairs
     int fixed;     // 1: pivots replayed from fixed_gp / fixed_tp
+    const void* samples;  // sample table of sampled pivoting (null: full search)
+    int nsamp;
   };
   std::vector<GraphEntry> graphs;
   cudaStream_t cap_stream = nullptr;
@@ -238,6 +242,8 @@ struct PivotArgs {
   int nprob;
   const int32_t* tile_prob;
   const int32_t* fixed;  // replayed pivot list (same layout as piv_list), or null: argmax
+  const int32_t* samples;  // sampled pivoting (single problem): nsamp candidate rows, or null
+  int nsamp;
 };
 
 template <typename XT, typename BT, typename CT>

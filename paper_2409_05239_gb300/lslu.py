@@ -27,7 +27,7 @@ EXPORTS = ("lslu_create", "lslu_solve", "lslu_get_state", "lslu_spmv", "lslu_pro
            "lslu_projected_noalloc", "lslu_profile", "lslu_timing", "lslu_last_launch_count",
            "lslu_error_string", "lslu_destroy", "lslu_create_batched", "lslu_solve_batched",
            "lslu_adjoint", "lslu_solve_fixed_pivots", "lslu_create_shared",
-           "lslu_solve_stopping")
+           "lslu_solve_stopping", "lslu_solve_sampled")
 
 _lib = None
 
@@ -80,6 +80,8 @@ def load(path: str | None = None):
     lib.lslu_solve_batched.restype = i32
     lib.lslu_solve_fixed_pivots.argtypes = [vp, vp, vp, i32, i32, f64, i32, vp, vp, vp, vp]
     lib.lslu_solve_fixed_pivots.restype = i32
+    lib.lslu_solve_sampled.argtypes = [vp, vp, vp, i32, i32, f64, vp, i32, i32, vp, vp, vp, vp]
+    lib.lslu_solve_sampled.restype = i32
     lib.lslu_solve_stopping.argtypes = [vp, vp, vp, i32, i32, f64, f64, i32, vp, vp, vp]
     lib.lslu_solve_stopping.restype = i32
     lib.lslu_adjoint.argtypes = [vp, vp, i32, vp, vp, vp]
@@ -186,6 +188,23 @@ class Solver:
                                               ctypes.addressof(kd))
         self._check(st, allow_breakdown=True)
         return dict(x=x, k_done=kd.value, status=st)
+
+    def solve_sampled(self, b, K, samples, rule="gcv", lam=0.0, x0=None):
+        """Sampled pivoting (Section 2.2) with a host sample table of shape
+        (2K+1, s); returns the same dict as solve (without histories)."""
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        x0 = None if x0 is None else np.ascontiguousarray(x0, dtype=np.float64)
+        S = np.ascontiguousarray(samples, dtype=np.int32)
+        x = np.zeros(self.n)
+        gp = np.zeros(K, dtype=np.int32)
+        tp = np.zeros(K + 1, dtype=np.int32)
+        kd = ctypes.c_int32(0)
+        self.epoch += 1
+        st = self.lib.lslu_solve_sampled(self.h, _ptr(b), _ptr(x0), int(K), RULES[rule],
+                                         float(lam), _ptr(S), int(S.shape[1]), HOST, _ptr(x),
+                                         _ptr(gp), _ptr(tp), ctypes.addressof(kd))
+        self._check(st, allow_breakdown=True)
+        return dict(x=x, gp=gp, tp=tp, k_done=kd.value, status=st)
 
     def solve_stopping(self, b, K_max, rule="wgcv", lam=0.0, tol=1e-6, x0=None):
         """Solve with the stopping criterion G^(k) (host arrays): returns x at
@@ -440,6 +459,14 @@ def from_problems(Ps, value_type="f32", max_iter=150, stream=None):
     """Batched solver over several tomography problems."""
     return BatchedSolver([(P.m, P.n, P.row_ptr, P.col_idx, P.vals) for P in Ps],
                          value_type=value_type, max_iter=max_iter, stream=stream)
+
+
+def sample_table(K, s, m, n, seed):
+    """Random sample indices for lslu_solve_sampled: 2K+1 rows of s indices,
+    rows 0, 2, 4, ... in [0, m) and rows 1, 3, ... in [0, n) (numpy PCG64)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return np.stack([rng.integers(0, m if t % 2 == 0 else n, size=s)
+                     for t in range(2 * K + 1)]).astype(np.int32)
 
 
 def shared_rhs(P, nrhs, value_type="f32", max_iter=150, stream=None):
