@@ -457,6 +457,8 @@ def run_gpu(args):
     stream = torch.cuda.current_stream(dev)
     solver = lslu.Solver(P.m, P.n, P.row_ptr, P.col_idx, P.vals, args.value_type, K,
                          stream=stream.cuda_stream)
+    # autotuner: the fastest row shape of the sparse products for this A and A^T
+    tuned = solver.tune_spmv(reps=5)
     b_dev = torch.from_numpy(P.b).to(dev)
     x_dev = torch.empty(P.n, dtype=torch.float64, device=dev)
     rule = "gcv"
@@ -549,7 +551,11 @@ def run_gpu(args):
                        "A_values": args.value_type, "basis": "f64" if args.value_type == "f64"
                        else "f32", "projected_solve": "f64",
                        "l2": "inputs larger than L2 (CSR of A and A^T ~%.1f GB)" % (
-                           2 * P.nnz * 8 / 1e9)},
+                           2 * P.nnz * 8 / 1e9),
+                       "spmv_shape": {"A": lslu.Solver.SHAPES[tuned["shape_A"]],
+                                      "AT": lslu.Solver.SHAPES[tuned["shape_AT"]],
+                                      "tuning_us_A": tuned["us_A"],
+                                      "tuning_us_AT": tuned["us_AT"]}},
             "roofline": {"bound": "hbm", "kernel": "csr_spmv (A l_k and A^T d_k)",
                          "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm if achieved else None,
@@ -557,7 +563,9 @@ def run_gpu(args):
                          "timing": "CUDA events around each product, second pass of the timed steps",
                          "algorithmic_bytes_per_launch": sbytes, "launches": n_spmv,
                          "avg_launch_ms": avg_ms,
-                         "traffic": spmv_traffic(args.workload, args.value_type),
+                         "traffic": (spmv_traffic(args.workload, args.value_type)
+                                     if tuned["shape_A"] == 0 and tuned["shape_AT"] == 0
+                                     else None),
                          "traffic_source": "profiles/k_spmv_pivots_ct512.md (ncu dram bytes "
                                            "per launch)"},
             "hbm_gbs_solve": total_bytes * args.steps * world / (ms_max / 1e3) / 1e9,

@@ -283,6 +283,22 @@ lslu_status lslu_timing(lslu_handle h, int32_t* spmv_launches, double* spmv_ms);
 /* Number of kernel launches made by the last lslu_solve. */
 int64_t lslu_last_launch_count(lslu_handle h);
 
+/* Row shape of the sparse products: lanes per CSR row x 4-entry chunks in
+ * flight per lane.  0: 16x2 (default for FP32/BF16 values), 1: 32x1,
+ * 2: 16x1 (default for FP64 values), 3: 8x1, 4: 8x2, 5: 4x1.  Every shape
+ * computes the same products with a different summation order, so results
+ * change in rounding only; each is bitwise reproducible.  The shared-matrix
+ * product of lslu_create_shared keeps its own 16-lane shape. */
+lslu_status lslu_set_spmv_shape(lslu_handle h, int32_t shape_A, int32_t shape_AT);
+
+/* Autotuner: times every row shape on the handle's A and A^T (reps launches
+ * each, CUDA events on the handle's stream, after one warm-up launch) and
+ * keeps the fastest for each.  Outputs (host, any may be NULL): the chosen
+ * shapes and the average time of every shape in microseconds (us[0..5] for A,
+ * us[6..11] for A^T).  Drops captured solves (they hold the old kernels). */
+lslu_status lslu_tune_spmv(lslu_handle h, int32_t reps, int32_t* shape_A, int32_t* shape_AT,
+                           double* us);
+
 /* One-line description of the last failure on h (h may be NULL for a failed
  * lslu_create on this thread).  The string stays valid until the next call. */
 const char* lslu_error_string(lslu_handle h);

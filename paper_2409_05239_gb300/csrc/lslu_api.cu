@@ -1066,6 +1066,87 @@ extern "C" lslu_status lslu_solve_stopping(lslu_handle h, const double* b, const
   return LSLU_OK;
 }
 
+namespace {
+
+void drop_graphs(Ctx* c) {
+  for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
+  c->graphs.clear();
+}
+
+}  // namespace
+
+extern "C" lslu_status lslu_set_spmv_shape(lslu_handle h, int32_t shape_A, int32_t shape_AT) {
+  Ctx* c = h;
+  if (!c) return set_err(nullptr, LSLU_ERR_INVALID_ARG, "NULL handle");
+  if (shape_A < 0 || shape_A >= kNumShapes || shape_AT < 0 || shape_AT >= kNumShapes)
+    return set_err(c, LSLU_ERR_INVALID_ARG, "shape must be in [0, 6)");
+  CK(cudaStreamSynchronize(c->stream));
+  c->A.shape = shape_A;
+  c->AT.shape = shape_AT;
+  drop_graphs(c);  // captured solves hold the kernels of the old shapes
+  return LSLU_OK;
+}
+
+extern "C" lslu_status lslu_tune_spmv(lslu_handle h, int32_t reps, int32_t* shape_A,
+                                      int32_t* shape_AT, double* us) {
+  Ctx* c = h;
+  if (!c) return set_err(nullptr, LSLU_ERR_INVALID_ARG, "NULL handle");
+  if (reps < 1 || reps > 1000) return set_err(c, LSLU_ERR_INVALID_ARG, "reps must be in [1, 1000]");
+  cudaStream_t s = c->stream;
+  const size_t bb = basis_bytes(c->value_type);
+  // the products read q (n) or u (m) and write the other; their contents do
+  // not change the time
+  CK(cudaMemsetAsync(c->q, 0, (size_t)c->n * bb, s));
+  CK(cudaMemsetAsync(c->u, 0, (size_t)c->m * bb, s));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  int best[2] = {c->A.shape, c->AT.shape};
+  for (int which = 0; which < 2; ++which) {
+    DevCsr& M = which == 0 ? c->A : c->AT;
+    const void* x = which == 0 ? c->q : c->u;
+    void* y = which == 0 ? c->u : c->q;
+    const int saved = M.shape;
+    float best_ms = 0.f;
+    for (int sh = 0; sh < kNumShapes; ++sh) {
+      M.shape = sh;
+      auto run = [&]() {
+        if (c->value_type == LSLU_F64)
+          launch_spmv<double, double>(M, c->value_type, (const double*)x, (double*)y, s,
+                                      c->num_sms);
+        else
+          launch_spmv<float, float>(M, c->value_type, (const float*)x, (float*)y, s,
+                                    c->num_sms);
+      };
+      run();  // warm-up
+      cudaEventRecord(e0, s);
+      for (int r = 0; r < reps; ++r) run();
+      cudaEventRecord(e1, s);
+      cudaError_t e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e != cudaSuccess) {
+        M.shape = saved;
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return set_err(c, LSLU_ERR_CUDA, std::string("tuning: ") + cudaGetErrorString(e));
+      }
+      if (us) us[which * kNumShapes + sh] = 1e3 * ms / reps;
+      if (sh == 0 || ms < best_ms) {
+        best_ms = ms;
+        best[which] = sh;
+      }
+    }
+    M.shape = best[which];
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  drop_graphs(c);
+  if (shape_A) *shape_A = best[0];
+  if (shape_AT) *shape_AT = best[1];
+  return LSLU_OK;
+}
+
 extern "C" lslu_status lslu_get_state(lslu_handle h, int32_t ptr_location, double* H, double* W,
                                       double* beta, void* L, void* D) {
   Ctx* c = h;

@@ -25,7 +25,22 @@ constexpr int kMaxIter = 2048;
 // belongs to exactly one problem.
 constexpr int kTile = 128;
 
+// Row shapes of the sparse products (lanes per CSR row x 4-entry chunks in
+// flight per lane); each matrix has one, set at create (the default of its
+// value type) or by lslu_tune_spmv / lslu_set_spmv_shape.
+enum {
+  kShapeG16U2 = 0,
+  kShapeG32U1 = 1,
+  kShapeG16U1 = 2,
+  kShapeG8U1 = 3,
+  kShapeG8U2 = 4,
+  kShapeG4U1 = 5,
+  kNumShapes = 6
+};
+int default_shape(int vt);
+
 struct DevCsr {
+  int shape = kShapeG16U2;
   int64_t rows = 0, cols = 0;
   int64_t nnz = 0;         // true non-zeros
   int64_t nnz_padded = 0;  // entries stored, including padding
@@ -215,6 +230,31 @@ void launch_interleave(const float* x, int64_t xstride, int64_t count, int R, fl
                        cudaStream_t s, int num_sms);
 void launch_spmm_pivots(const DevCsr& A, int vt, const float* xi, float* y, int64_t ystride,
                         int R, PivotCoef pc, cudaStream_t s);
+
+// Products in a non-default row shape, native vector type only (FP64 for FP64
+// values, FP32 otherwise): shapes 0-2 in lslu_spmv_shapes_a.cu, 3-5 in _b.cu.
+void launch_spmv_shape_a(int shape, const DevCsr& A, int vt, const void* x, void* y,
+                         cudaStream_t s);
+void launch_spmv_pivots_shape_a(int shape, const DevCsr& A, int vt, const void* x, void* y,
+                                const PivotCoef& pc, cudaStream_t s);
+void launch_spmv_shape_b(int shape, const DevCsr& A, int vt, const void* x, void* y,
+                         cudaStream_t s);
+void launch_spmv_pivots_shape_b(int shape, const DevCsr& A, int vt, const void* x, void* y,
+                                const PivotCoef& pc, cudaStream_t s);
+inline void launch_spmv_shape(int shape, const DevCsr& A, int vt, const void* x, void* y,
+                              cudaStream_t s) {
+  if (shape <= kShapeG16U1)
+    launch_spmv_shape_a(shape, A, vt, x, y, s);
+  else
+    launch_spmv_shape_b(shape, A, vt, x, y, s);
+}
+inline void launch_spmv_pivots_shape(int shape, const DevCsr& A, int vt, const void* x,
+                                     void* y, const PivotCoef& pc, cudaStream_t s) {
+  if (shape <= kShapeG16U1)
+    launch_spmv_pivots_shape_a(shape, A, vt, x, y, pc, s);
+  else
+    launch_spmv_pivots_shape_b(shape, A, vt, x, y, pc, s);
+}
 
 // Build the padded CSR of A and of A^T (host-side layout, then upload).
 cudaError_t build_csr_pair(int64_t m, int64_t n, const int64_t* rp, const int32_t* ci,

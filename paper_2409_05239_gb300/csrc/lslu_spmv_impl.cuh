@@ -1,0 +1,273 @@
+// Device code of the sparse products of Algorithm 4 (u = A l_k, q = A^T d_k),
+// templated on the row shape: G lanes per CSR row (4, 8, 16 or 32) and U
+// 4-entry chunks in flight per lane.  Included by the translation units that
+// instantiate the shapes (lslu_spmv.cu: the default shapes and the shared-
+// matrix products; lslu_spmv_shapes.cu: the others).
+//
+// Both products run on a row-major CSR: A^T is stored as its own (transposed)
+// CSR, so every output entry is one row dot product and no atomics are needed.
+// Lane j of a row's group reads the chunks j, j+G, j+2G, ... of the row with
+// vector loads (rows are padded to a multiple of kRowAlign entries), keeps a
+// private partial sum in chunk order, and the group adds its G partials with
+// a fixed butterfly, so results are bitwise reproducible run to run (for a
+// given shape).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include "lslu_internal.cuh"
+
+namespace lslu {
+namespace {
+
+template <typename VT>
+struct ValTraits {
+  static constexpr int kChunk = 4;  // entries per chunk (16-byte column loads)
+};
+
+// Blocks of 256 threads kept resident per SM: bounds the registers per thread.
+template <typename VT, int U>
+constexpr int min_blocks() {
+  return (U >= 2 || sizeof(VT) == 8) ? 6 : 8;
+}
+
+template <typename AT>
+__device__ __forceinline__ AT warp_sum(AT v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum over each group of G lanes (every lane of the warp must call it).
+template <int G, typename AT>
+__device__ __forceinline__ AT group_sum(AT v) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Matrix stream: 16-byte loads through the non-coherent path without L1
+// allocation (ld.global.nc.L1::no_allocate), so L1 keeps the gathered x.
+__device__ __forceinline__ int4 ld_stream(const int32_t* p) {
+  int4 c;
+  asm volatile("ld.global.nc.L1::no_allocate.v4.s32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(c.x), "=r"(c.y), "=r"(c.z), "=r"(c.w)
+               : "l"(p));
+  return c;
+}
+template <typename AT>
+__device__ __forceinline__ void load_vals_cs(const double* p, AT (&v)[4]) {
+  double a0, a1, a2, a3;
+  asm volatile("ld.global.nc.L1::no_allocate.v2.f64 {%0,%1}, [%2];" : "=d"(a0), "=d"(a1) : "l"(p));
+  asm volatile("ld.global.nc.L1::no_allocate.v2.f64 {%0,%1}, [%2];"
+               : "=d"(a2), "=d"(a3)
+               : "l"(p + 2));
+  v[0] = (AT)a0; v[1] = (AT)a1; v[2] = (AT)a2; v[3] = (AT)a3;
+}
+template <typename AT>
+__device__ __forceinline__ void load_vals_cs(const float* p, AT (&v)[4]) {
+  float a0, a1, a2, a3;
+  asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
+               : "=f"(a0), "=f"(a1), "=f"(a2), "=f"(a3)
+               : "l"(p));
+  v[0] = (AT)a0; v[1] = (AT)a1; v[2] = (AT)a2; v[3] = (AT)a3;
+}
+template <typename AT>
+__device__ __forceinline__ void load_vals_cs(const __nv_bfloat16* p, AT (&v)[4]) {
+  uint32_t w[2];
+  asm volatile("ld.global.nc.L1::no_allocate.v2.u32 {%0,%1}, [%2];"
+               : "=r"(w[0]), "=r"(w[1])
+               : "l"(p));
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    v[2 * i] = (AT)__uint_as_float(w[i] << 16);
+    v[2 * i + 1] = (AT)__uint_as_float(w[i] & 0xffff0000u);
+  }
+}
+
+// Dot product of one CSR row with x, computed by one group of G lanes (result
+// in every lane of the group; gl = lane index within the group; a lane with
+// len = 0 contributes nothing).  Lane gl takes chunks gl, gl+G, ... in order
+// (U chunks per step); the G partial sums are combined by a fixed butterfly,
+// so a row always gets the same bits.  Every lane of the warp must call it.
+template <typename VT, typename XT, typename YT, int G, int U>
+__device__ __forceinline__ YT row_dot_len(int32_t start, int32_t len,
+                                          const int32_t* __restrict__ col,
+                                          const VT* __restrict__ val, const XT* __restrict__ x,
+                                          int gl) {
+  constexpr int C = ValTraits<VT>::kChunk;
+  constexpr int S = G * C;  // entries between a lane's consecutive chunks
+  YT acc = 0;
+  for (int32_t e = gl * C; e < len; e += U * S) {
+    int32_t cidx[U][C];
+    YT v[U][C];
+    bool has[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      has[u] = u == 0 || e + u * S < len;
+      if (has[u]) {
+        const int4 c4 = ld_stream(col + start + e + u * S);
+        cidx[u][0] = c4.x; cidx[u][1] = c4.y; cidx[u][2] = c4.z; cidx[u][3] = c4.w;
+        load_vals_cs<YT>(val + start + e + u * S, v[u]);
+      } else {
+#pragma unroll
+        for (int i = 0; i < C; ++i) v[u][i] = 0;
+      }
+    }
+    XT xv[U][C];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int i = 0; i < C; ++i) xv[u][i] = has[u] ? __ldg(x + cidx[u][i]) : (XT)0;
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int i = 0; i < C; ++i) acc = fma(v[u][i], (YT)xv[u][i], acc);
+  }
+  return group_sum<G>(acc);
+}
+
+template <typename VT, typename XT, typename YT, int G, int U>
+__device__ __forceinline__ YT row_dot(int64_t row, bool valid, const int32_t* __restrict__ rp,
+                                      const int32_t* __restrict__ rl,
+                                      const int32_t* __restrict__ col,
+                                      const VT* __restrict__ val, const XT* __restrict__ x,
+                                      int gl) {
+  const int32_t start = valid ? __ldg(rp + row) : 0;
+  const int32_t len = valid ? __ldg(rl + row) : 0;
+  return row_dot_len<VT, XT, YT, G, U>(start, len, col, val, x, gl);
+}
+
+template <typename VT, typename XT, typename YT, int G, int U>
+__global__ void __launch_bounds__(256, min_blocks<VT, U>())
+    k_spmv(int64_t rows, const int32_t* __restrict__ rp, const int32_t* __restrict__ rl,
+           const int32_t* __restrict__ col, const VT* __restrict__ val, const XT* __restrict__ x,
+           YT* __restrict__ y) {
+  constexpr int RPB = 256 / G;  // rows per block
+  const int gl = threadIdx.x & (G - 1);
+  const int64_t row = (int64_t)blockIdx.x * RPB + threadIdx.x / G;
+  if ((int64_t)blockIdx.x * RPB + (threadIdx.x & ~31) / G >= rows)
+    return;  // the whole warp is past the last row
+  const bool valid = row < rows;
+  const YT acc = row_dot<VT, XT, YT, G, U>(row, valid, rp, rl, col, val, x, gl);
+  if (valid && gl == 0) y[row] = acc;
+}
+
+// y = A x plus the elimination coefficients of the next Hessenberg step,
+// c = T^-1 y(piv), where T(i,j) = b_j(piv_i) is the unit lower triangular
+// pivot-row matrix of the basis b and T^-1 is kept explicitly (column-major,
+// accumulation type).  |T| <= 1 under max-abs pivoting keeps
+// T^-1 small and well conditioned, so every coefficient becomes a plain
+// dot product instead of a step of a sequential forward substitution.
+//
+// The first npiv blocks per problem own the pivot columns, one warp per
+// column j:
+//   a. completes the newest row of T^-1 in its column,
+//      Tinv(nr, j) = -sum_{l=j}^{nr-1} T(nr, l) Tinv(l, j),  nr = cnt-1;
+//   b. computes y(piv_j) with the same row reduction as every other row
+//      (so the two agree bit for bit);
+//   c. the block adds Tinv(i, j) y(piv_j) over its 8 columns into a partial
+//      vector; the last pivot block to finish adds the partials in block order.
+// The remaining blocks compute the other rows of y meanwhile.  rowdot(p, row,
+// gl) is the product of output row `row` for problem p.
+template <typename YT, int G, typename RowDot>
+__device__ __forceinline__ void pivot_blocks(const PivotCoef& pc, RowDot rowdot) {
+  __shared__ int last;
+  __shared__ YT xs[8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int p = blockIdx.x / pc.npiv_blocks;  // problem of this pivot block
+  const int bb = blockIdx.x - p * pc.npiv_blocks;
+  DevState& sp = pc.st[p];
+  if (sp.status != LSLU_OK) return;
+  YT* Tinv = reinterpret_cast<YT*>(pc.Tinv) + (int64_t)p * pc.tinv_stride;
+  YT* part = reinterpret_cast<YT*>(pc.xp) + (int64_t)p * pc.xp_stride;
+  const int32_t* piv = pc.piv + (int64_t)p * pc.piv_stride;
+  const int cnt = pc.cnt, nr = cnt - 1;
+  const int j0 = bb * 8;
+  const int j = j0 + warp;
+  if (j < cnt) {
+    if (j < nr) {
+      YT a = 0;
+      // T(nr, l) = b_l(piv_nr): the newest pivot row of the earlier basis vectors
+      const YT* brow = reinterpret_cast<const YT*>(pc.B) + piv[nr];
+      const YT* tcol = Tinv + (int64_t)j * pc.ldi;
+      for (int l = j + lane; l < nr; l += 32)
+        a = fma(__ldcg(brow + (int64_t)l * pc.ldb), __ldcg(tcol + l), a);
+      a = warp_sum(a);
+      if (lane == 0) __stcg(Tinv + (int64_t)j * pc.ldi + nr, -a);
+    }
+    // every lane group of the warp computes the pivot row (the same bits as
+    // its y entry)
+    const YT yp = rowdot(p, piv[j], lane & (G - 1));
+    if (lane == 0) xs[warp] = yp;
+  } else if (lane == 0) {
+    xs[warp] = 0;
+  }
+  __threadfence_block();
+  __syncthreads();
+  const int jn = min(8, cnt - j0);
+  for (int i = j0 + threadIdx.x; i < cnt; i += blockDim.x) {
+    YT acc = 0;
+    for (int w = 0; w < jn; ++w)
+      if (i >= j0 + w) acc = fma(__ldcg(Tinv + (int64_t)(j0 + w) * pc.ldi + i), xs[w], acc);
+    __stcg(part + (int64_t)bb * pc.ldi + i, acc);
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = (atomicAdd(&sp.ticket2, 1) == pc.npiv_blocks - 1);
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  if (threadIdx.x == 0) sp.ticket2 = 0;
+  double* coef = pc.coef + (int64_t)p * pc.coef_stride;
+  double* hess = pc.hess_col ? pc.hess_col + (int64_t)p * pc.hess_stride : nullptr;
+  for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+    YT acc = 0;
+    const int bmax = i / 8;  // blocks whose columns start at or before row i
+    for (int b2 = 0; b2 <= bmax; ++b2) acc += __ldcg(part + (int64_t)b2 * pc.ldi + i);
+    coef[i] = (double)acc;
+    if (hess) hess[i] = (double)acc;
+  }
+}
+
+template <typename VT, typename XT, typename YT, int G, int U>
+__global__ void __launch_bounds__(256, min_blocks<VT, U>())
+    k_spmv_pivots(int64_t rows, const int32_t* __restrict__ rp, const int32_t* __restrict__ rl,
+                  const int32_t* __restrict__ col, const VT* __restrict__ val,
+                  const XT* __restrict__ x, YT* __restrict__ y, PivotCoef pc) {
+  constexpr int RPB = 256 / G;
+  const int lane = threadIdx.x & 31;
+  const int npiv_all = pc.npiv_blocks * pc.nprob;
+  if ((int)blockIdx.x >= npiv_all) {  // streaming rows (all but the first npiv_all blocks)
+    const int64_t b0 = (int64_t)(blockIdx.x - npiv_all) * RPB;
+    if (b0 + (threadIdx.x & ~31) / G >= rows) return;  // whole warp past the end
+    const int64_t row = b0 + threadIdx.x / G;
+    const bool valid = row < rows;
+    const YT acc = row_dot<VT, XT, YT, G, U>(row, valid, rp, rl, col, val, x, lane & (G - 1));
+    if (valid && (lane & (G - 1)) == 0) y[row] = acc;
+    return;
+  }
+  pivot_blocks<YT, G>(pc, [=](int, int32_t row, int gl) {
+    return row_dot<VT, XT, YT, G, U>(row, true, rp, rl, col, val, x, gl);
+  });
+}
+
+template <typename VT, typename XT, typename YT, int G, int U>
+void spmv_run(const DevCsr& A, const XT* x, YT* y, cudaStream_t s) {
+  if (A.rows == 0) return;
+  const int64_t blocks = (A.rows + 256 / G - 1) / (256 / G);
+  k_spmv<VT, XT, YT, G, U><<<(unsigned)blocks, 256, 0, s>>>(
+      A.rows, A.row_ptr, A.row_len, A.col, reinterpret_cast<const VT*>(A.val), x, y);
+}
+
+template <typename VT, typename XT, typename YT, int G, int U>
+void spmv_pivots_run(const DevCsr& A, const XT* x, YT* y, const PivotCoef& pc, cudaStream_t s) {
+  const int64_t blocks =
+      (int64_t)pc.npiv_blocks * pc.nprob + (A.rows + 256 / G - 1) / (256 / G);
+  k_spmv_pivots<VT, XT, YT, G, U><<<(unsigned)blocks, 256, 0, s>>>(
+      A.rows, A.row_ptr, A.row_len, A.col, reinterpret_cast<const VT*>(A.val), x, y, pc);
+}
+
+}  // namespace
+}  // namespace lslu

@@ -27,7 +27,8 @@ EXPORTS = ("lslu_create", "lslu_solve", "lslu_get_state", "lslu_spmv", "lslu_pro
            "lslu_projected_noalloc", "lslu_profile", "lslu_timing", "lslu_last_launch_count",
            "lslu_error_string", "lslu_destroy", "lslu_create_batched", "lslu_solve_batched",
            "lslu_adjoint", "lslu_solve_fixed_pivots", "lslu_create_shared",
-           "lslu_solve_stopping", "lslu_solve_sampled")
+           "lslu_solve_stopping", "lslu_solve_sampled", "lslu_set_spmv_shape",
+           "lslu_tune_spmv")
 
 _lib = None
 
@@ -80,6 +81,10 @@ def load(path: str | None = None):
     lib.lslu_solve_batched.restype = i32
     lib.lslu_solve_fixed_pivots.argtypes = [vp, vp, vp, i32, i32, f64, i32, vp, vp, vp, vp]
     lib.lslu_solve_fixed_pivots.restype = i32
+    lib.lslu_set_spmv_shape.argtypes = [vp, i32, i32]
+    lib.lslu_set_spmv_shape.restype = i32
+    lib.lslu_tune_spmv.argtypes = [vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32), vp]
+    lib.lslu_tune_spmv.restype = i32
     lib.lslu_solve_sampled.argtypes = [vp, vp, vp, i32, i32, f64, vp, i32, i32, vp, vp, vp, vp]
     lib.lslu_solve_sampled.restype = i32
     lib.lslu_solve_stopping.argtypes = [vp, vp, vp, i32, i32, f64, f64, i32, vp, vp, vp]
@@ -259,6 +264,25 @@ class Solver:
                                      _ptr(c), _ptr(lo), _ptr(ro))
         self._check(st)
         return dict(y=y, sigma=sig, c=c, lam=float(lo[0]), resid=float(ro[0]))
+
+    SHAPES = ("16x2", "32x1", "16x1", "8x1", "8x2", "4x1")
+
+    def set_spmv_shape(self, shape_A, shape_AT=None):
+        """Row shape of the sparse products (index into SHAPES)."""
+        sa = int(shape_A)
+        self._check(self.lib.lslu_set_spmv_shape(self.h, sa, sa if shape_AT is None else int(shape_AT)))
+
+    def tune_spmv(self, reps=5):
+        """Time every row shape on A and A^T and keep the fastest; returns the
+        chosen shapes and the per-shape times (microseconds)."""
+        a = ctypes.c_int32(0)
+        t = ctypes.c_int32(0)
+        us = np.zeros(12)
+        self._check(self.lib.lslu_tune_spmv(self.h, int(reps), ctypes.byref(a), ctypes.byref(t),
+                                            _ptr(us)))
+        return dict(shape_A=a.value, shape_AT=t.value,
+                    us_A=dict(zip(self.SHAPES, us[:6].tolist())),
+                    us_AT=dict(zip(self.SHAPES, us[6:].tolist())))
 
     def profile(self, enable=True):
         self._check(self.lib.lslu_profile(self.h, int(enable)))

@@ -174,3 +174,30 @@ def test_graph_replay_matches_direct_launches(ct32, monkeypatch):
     assert np.array_equal(a["x"], b["x"]) and np.array_equal(a["x"], c["x"])
     assert np.array_equal(a["x"], d["x"]) and np.array_equal(a["gp"], d["gp"])
     assert n == 80 and ms > 0
+
+
+@pytest.mark.parametrize("shape", range(6))
+def test_every_spmv_shape_keeps_f64_parity(ct32, shape):
+    """All row shapes of the sparse products (the autotuner's choices) give the
+    oracle's pivots and x within the FP64 tolerance."""
+    K = 30
+    ref = O.hybrid_lslu(ct32.scipy(), ct32.b, None, K, "gcv", histories=False)
+    with lslu.from_problem(ct32, "f64", K) as s:
+        s.set_spmv_shape(shape, (shape + 1) % 6)
+        r = s.solve(ct32.b, K, "gcv")
+        r2 = s.solve(ct32.b, K, "gcv")
+    assert np.array_equal(r["gp"], ref.gp) and np.array_equal(r["tp"], ref.tp)
+    assert rel(r["x"], ref.x) <= TOL_F64
+    assert np.array_equal(r["x"], r2["x"])
+
+
+def test_autotuner_picks_a_shape(ct32):
+    K = 20
+    A32 = ct32.scipy(tomo.round_values(ct32.vals, "f32"))
+    ref = O.hybrid_lslu(A32, ct32.b, None, K, "gcv", histories=False)
+    with lslu.from_problem(ct32, "f32", K) as s:
+        t = s.tune_spmv(reps=3)
+        assert 0 <= t["shape_A"] < 6 and 0 <= t["shape_AT"] < 6
+        assert t["us_A"][s.SHAPES[t["shape_A"]]] == min(t["us_A"].values())
+        r = s.solve(ct32.b, K, "gcv")
+    assert rel(r["x"], ref.x) <= 2e-4
