@@ -36,6 +36,13 @@ design notes):
       indices of row t of a given sample table (ties -> lowest index); when no
       sampled unpivoted entry is non-zero it falls back to the full search.
       The random indices are inputs, drawn by the caller.
+  R16 uncertainty quantification (Section 5): with lambda = sigma / alpha the
+      posterior covariance is sigma^2 (lambda^2 I + A^T A)^-1, so the low-rank
+      Gamma_k uses lambda^2 where the printed formulas show lambda; D_k, W_k
+      are the first k columns / the k x k block (A^T D_k = L_k W_k, Eq. nhr2).
+      The Woodbury step keeps the factor lambda^-2 on the low-rank term:
+      Gamma_k = sigma^2 lambda^-2 (I - Z Delta Z^T) (the last line of the
+      printed derivation drops the factor its previous line carries).
 """
 from __future__ import annotations
 
@@ -353,3 +360,23 @@ def hybrid_lslu_stopping(A, b, K_max, rule="wgcv", lam=0.0, tol=1e-6):
         s_, c_, V = projected_svd(Hk, hp["beta"])
         x = hp["L"][:, :k] @ tikhonov_y(s_, c_, V, lams[k - 1])
     return x, k, G
+
+
+def uq_lowrank(L, D, W, lam, sigma2):
+    """Low-rank posterior covariance of Section 5 (reading R16).
+
+    A^T A ~ L_k W_k (D_k^T D_k)^-1 W_k^T L_k^T = L_k G^T G L_k^T; with the
+    eigendecomposition G^T G = V diag(s2) V^T and Z = L_k V,
+    Gamma_k = sigma^2 lam^-2 (I - Z Delta Z^T), Delta = (Z^T Z + lam^2 diag(s2)^-1)^-1
+    (Woodbury).  Returns (diag(Gamma_k), 1^T Gamma_k 1)."""
+    n, k = L.shape
+    Dk = D[:, :k]
+    GtG = W @ np.linalg.solve(Dk.T @ Dk, W.T)
+    GtG = 0.5 * (GtG + GtG.T)
+    s2, V = np.linalg.eigh(GtG)
+    Z = L @ V
+    Delta = np.linalg.inv(Z.T @ Z + lam * lam * np.diag(1.0 / s2))
+    diag = sigma2 / (lam * lam) * (1.0 - np.einsum("ij,jk,ik->i", Z, Delta, Z))
+    zs = Z.T @ np.ones(n)
+    total = sigma2 / (lam * lam) * (n - zs @ Delta @ zs)
+    return diag, float(total)
