@@ -283,6 +283,21 @@ lslu_status lslu_timing(lslu_handle h, int32_t* spmv_launches, double* spmv_ms);
 /* Number of kernel launches made by the last lslu_solve. */
 int64_t lslu_last_launch_count(lslu_handle h);
 
+/* Low-rank uncertainty quantification of Section 5 on the state of the last
+ * lslu_solve (k = its k_done): with A^T A ~ L_k W_k (D_k^T D_k)^-1 W_k^T L_k^T
+ * (Eq. nhr2) and lambda = sigma / alpha, the posterior covariance
+ * sigma^2 (lambda^2 I + A^T A)^-1 is approximated by
+ *   Gamma_k = sigma^2 lambda^-2 (I - L_k M L_k^T),
+ *   M = (L_k^T L_k + lambda^2 (G^T G)^-1)^-1,  G^T G = W_k (D_k^T D_k)^-1 W_k^T
+ * (the paper's Woodbury form, with lambda^2 for its lambda).  Outputs (host
+ * or device per ptr_location, either may be NULL): var_diag (n, FP64) the
+ * diagonal of Gamma_k (posterior variances), var_sum (1) = 1^T Gamma_k 1.
+ * sigma2 (noise variance) and lambda must be > 0.  Single-problem handles.
+ * Errors: LSLU_ERR_INVALID_ARG when no solve has completed an iteration or
+ * the k x k system is not positive definite; LSLU_ERR_OOM; LSLU_ERR_CUDA. */
+lslu_status lslu_uq(lslu_handle h, double sigma2, double lambda, int32_t ptr_location,
+                    double* var_diag, double* var_sum);
+
 /* Row shape of the sparse products: lanes per CSR row x 4-entry chunks in
  * flight per lane.  0: 16x2 (default for FP32/BF16 values), 1: 32x1,
  * 2: 16x1 (default for FP64 values), 3: 8x1, 4: 8x2, 5: 4x1.  Every shape

@@ -1,0 +1,437 @@
+// Low-rank uncertainty quantification of Section 5 (lslu_uq).
+//
+// After k iterations, A^T A ~ L_k G^T G L_k^T with G^T G = W_k (D_k^T D_k)^-1 W_k^T
+// (Eq. nhr2).  With lambda = sigma / alpha the posterior covariance
+// sigma^2 (lambda^2 I + A^T A)^-1 is approximated by
+//
+//   Gamma_k = sigma^2 (lambda^2 I + L G^T G L^T)^-1
+//           = sigma^2 lambda^-2 (I - L M L^T),  M = (L^T L + lambda^2 (G^T G)^-1)^-1
+//
+// (Woodbury), and (G^T G)^-1 = X^T (D_k^T D_k) X with X = W_k^-1, so no
+// eigendecomposition is needed.  With S = L^T L + lambda^2 X^T D^T D X = R R^T
+// (Cholesky), l_i^T M l_i = ||R^-1 l_i||^2, hence
+//
+//   diag(Gamma_k)_i = sigma^2 / lambda^2 (1 - ||R^-1 l_i||^2),
+//   1^T Gamma_k 1   = sigma^2 / lambda^2 (n - ||R^-1 L^T 1||^2).
+//
+// Kernels: a tiled Gram pass over the bases (L^T L, D_k^T D_k, L^T 1; basis
+// type products accumulated per row slice, FP64 across slices, reduced in a
+// fixed order), two small FP64 GEMMs, one block for W^-1, the Cholesky factor
+// and R^-1, and a row pass that forms R^-1 l_i for every row and its squared
+// norm.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <string>
+
+#include "lslu_internal.cuh"
+
+namespace lslu {
+std::string& thread_error();  // defined in lslu_api.cu
+
+namespace {
+
+constexpr int kTG = 64;    // Gram output tile (kTG x kTG)
+constexpr int kRC = 32;    // rows staged per step
+constexpr int kSlicesMax = 64;
+
+// Partial Gram tiles: block (pair, slice) adds B1(r, i) B2(r, j) over its rows
+// for the kTG x kTG tile (ti, tj) of the pair list; 256 threads, 4 x 4 outputs
+// each.  B1 / B2 column-major with leading dimension ld; cols1 / cols2 columns.
+template <typename BT>
+__global__ void __launch_bounds__(256)
+    k_gram_tiles(const BT* __restrict__ B1, int cols1, const BT* __restrict__ B2, int cols2,
+                 int64_t ld, int64_t rows, const int2* __restrict__ pairs, int rows_per_slice,
+                 double* __restrict__ part) {
+  using CT = BT;  // accumulate in the basis type within a slice
+  __shared__ BT s1[kRC][kTG + 1];
+  __shared__ BT s2[kRC][kTG + 1];
+  const int2 pr = pairs[blockIdx.x];
+  const int i0 = pr.x * kTG, j0 = pr.y * kTG;
+  const int64_t r_begin = (int64_t)blockIdx.y * rows_per_slice;
+  const int64_t r_end = r_begin + rows_per_slice < rows ? r_begin + rows_per_slice : rows;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // 16 x 16 threads
+  CT acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0;
+  for (int64_t r0 = r_begin; r0 < r_end; r0 += kRC) {
+    // stage kRC rows x kTG columns of each operand (zero outside)
+    for (int e = threadIdx.x; e < kRC * kTG; e += blockDim.x) {
+      const int rr = e % kRC, cc = e / kRC;
+      const int64_t r = r0 + rr;
+      const bool in = r < r_end;
+      s1[rr][cc] = (in && i0 + cc < cols1) ? B1[(int64_t)(i0 + cc) * ld + r] : (BT)0;
+      s2[rr][cc] = (in && j0 + cc < cols2) ? B2[(int64_t)(j0 + cc) * ld + r] : (BT)0;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int rr = 0; rr < kRC; ++rr) {
+      CT a[4], b[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        a[q] = s1[rr][ty + 16 * q];
+        b[q] = s2[rr][tx + 16 * q];
+      }
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[p][q] = fma(a[p], b[q], acc[p][q]);
+    }
+    __syncthreads();
+  }
+  double* out = part + ((int64_t)blockIdx.y * gridDim.x + blockIdx.x) * (kTG * kTG);
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) out[(ty + 16 * p) * kTG + (tx + 16 * q)] = (double)acc[p][q];
+}
+
+// C(i, j) (ld ldc) = sum over slices of the partial tiles, in slice order; for
+// symmetric products (B1 == B2) the mirrored entry is written too.
+__global__ void k_gram_reduce(const double* __restrict__ part, const int2* __restrict__ pairs,
+                              int npairs, int nslices, int cols1, int cols2, int symmetric,
+                              double* __restrict__ C, int64_t ldc) {
+  const int64_t total = (int64_t)npairs * kTG * kTG;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int pi = (int)(e / (kTG * kTG));
+    const int w = (int)(e % (kTG * kTG));
+    const int i = pairs[pi].x * kTG + w / kTG, j = pairs[pi].y * kTG + w % kTG;
+    if (i >= cols1 || j >= cols2) continue;
+    double s = 0.0;
+    for (int sl = 0; sl < nslices; ++sl) s += part[((int64_t)sl * npairs + pi) * (kTG * kTG) + w];
+    C[(int64_t)j * ldc + i] = s;
+    if (symmetric) C[(int64_t)i * ldc + j] = s;
+  }
+}
+
+// C = alpha op(A) B + beta C0 for k x k FP64 matrices (column-major, ld k);
+// op(A) = A or A^T.  16 x 16 tiles.
+__global__ void k_gemm_f64(const double* __restrict__ A, int transA, const double* __restrict__ B,
+                           const double* __restrict__ C0, double alpha, double beta, int k,
+                           double* __restrict__ C) {
+  __shared__ double sa[16][17], sb[16][17];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int row = blockIdx.y * 16 + ty, col = blockIdx.x * 16 + tx;
+  double acc = 0.0;
+  for (int t0 = 0; t0 < k; t0 += 16) {
+    const int ar = blockIdx.y * 16 + ty, ac = t0 + tx;
+    double av = 0.0;
+    if (ar < k && ac < k) av = transA ? A[(int64_t)ar * k + ac] : A[(int64_t)ac * k + ar];
+    sa[ty][tx] = av;
+    const int br = t0 + ty, bc = blockIdx.x * 16 + tx;
+    sb[ty][tx] = (br < k && bc < k) ? B[(int64_t)bc * k + br] : 0.0;
+    __syncthreads();
+#pragma unroll
+    for (int t = 0; t < 16; ++t) acc = fma(sa[ty][t], sb[t][tx], acc);
+    __syncthreads();
+  }
+  if (row < k && col < k) {
+    double v = alpha * acc;
+    if (C0) v += beta * C0[(int64_t)col * k + row];
+    C[(int64_t)col * k + row] = v;
+  }
+}
+
+// One block: X = W^-1 (upper triangular; W with leading dimension ldw).
+__global__ void k_upper_inverse(const double* __restrict__ W, int64_t ldw, int k,
+                                double* __restrict__ X) {
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) X[e] = 0.0;
+  __syncthreads();
+  // column j of X solves W x = e_j: x_i = (delta_ij - sum_{l>i} W(i,l) x_l) / W(i,i)
+  for (int j = threadIdx.x; j < k; j += blockDim.x) {
+    double* x = X + (int64_t)j * k;
+    for (int i = j; i >= 0; --i) {
+      double s = (i == j) ? 1.0 : 0.0;
+      for (int l = i + 1; l <= j; ++l) s -= W[(int64_t)l * ldw + i] * x[l];
+      x[i] = s / W[(int64_t)i * ldw + i];
+    }
+  }
+}
+
+// One block: S = R R^T in place (lower), then Ri = R^-1 (lower), t = R^-1 s and
+// the sum 1^T Gamma 1 = sigma^2 / lambda^2 (n - ||t||^2).  err = 1 when S is
+// not positive definite.
+__global__ void __launch_bounds__(1024)
+    k_uq_factor(double* __restrict__ S, int k, double* __restrict__ Ri,
+                const double* __restrict__ s, double* __restrict__ t, double n, double scale,
+                double* out_sum, double* err) {
+  __shared__ int bad;
+  __shared__ double red[32];
+  const int tid = threadIdx.x;
+  if (tid == 0) bad = 0;
+  __syncthreads();
+  for (int p = 0; p < k; ++p) {
+    if (tid == 0) {
+      const double d = S[(int64_t)p * k + p];
+      if (!(d > 0.0) || !isfinite(d)) bad = 1;
+      S[(int64_t)p * k + p] = sqrt(d > 0.0 ? d : 1.0);
+    }
+    __syncthreads();
+    const double piv = S[(int64_t)p * k + p];
+    for (int i = p + 1 + tid; i < k; i += blockDim.x) S[(int64_t)p * k + i] /= piv;
+    __syncthreads();
+    const int rem = k - p - 1;
+    for (int64_t q = tid; q < (int64_t)rem * rem; q += blockDim.x) {
+      const int i = p + 1 + (int)(q % rem), j = p + 1 + (int)(q / rem);
+      if (i >= j) S[(int64_t)j * k + i] -= S[(int64_t)p * k + i] * S[(int64_t)p * k + j];
+    }
+    __syncthreads();
+  }
+  // R^-1: column j solves R x = e_j (forward substitution)
+  for (int j = tid; j < k; j += blockDim.x) {
+    double* x = Ri + (int64_t)j * k;
+    for (int i = 0; i < j; ++i) x[i] = 0.0;
+    for (int i = j; i < k; ++i) {
+      double v = (i == j) ? 1.0 : 0.0;
+      for (int l = j; l < i; ++l) v -= S[(int64_t)l * k + i] * x[l];
+      x[i] = v / S[(int64_t)i * k + i];
+    }
+  }
+  __syncthreads();
+  double acc = 0.0;
+  for (int i = tid; i < k; i += blockDim.x) {
+    double v = 0.0;
+    for (int l = 0; l <= i; ++l) v += Ri[(int64_t)l * k + i] * s[l];
+    t[i] = v;
+    acc += v * v;
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((tid & 31) == 0) red[tid >> 5] = acc;
+  __syncthreads();
+  if (tid == 0) {
+    double tot = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
+    if (out_sum) *out_sum = scale * (n - tot);
+    *err = bad ? 1.0 : 0.0;
+  }
+}
+
+// Row pass: for rows [blockIdx.x * 64, +64) and output columns a-tile
+// blockIdx.y (64 of them), t_i(a) = sum_{b <= a} Ri(a, b) l_i(b); the block
+// writes sum_a t_i(a)^2 for its tile into part[tile][row].
+template <typename BT>
+__global__ void __launch_bounds__(256)
+    k_uq_rows(const BT* __restrict__ L, int64_t ldl, int64_t n, int k,
+              const BT* __restrict__ Ri, double* __restrict__ part) {
+  using CT = BT;
+  __shared__ BT sl[kRC][kTG + 1];  // L(row, b) for 64 rows x 32 b
+  __shared__ BT sr[kRC][kTG + 1];  // Ri(a, b) for 64 a x 32 b
+  const int64_t r0 = (int64_t)blockIdx.x * kTG;
+  const int a0 = blockIdx.y * kTG;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  CT acc[4][4];
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[p][q] = 0;
+  const int bmax = k < a0 + kTG ? k : a0 + kTG;  // Ri(a, b) = 0 for b > a
+  for (int b0 = 0; b0 < bmax; b0 += kRC) {
+    for (int e = threadIdx.x; e < kRC * kTG; e += blockDim.x) {
+      const int bb = e % kRC, cc = e / kRC;
+      const int b = b0 + bb;
+      const int64_t r = r0 + cc;
+      sl[bb][cc] = (b < k && r < n) ? L[(int64_t)b * ldl + r] : (BT)0;
+      const int a = a0 + cc;
+      sr[bb][cc] = (b < k && a < k) ? Ri[(int64_t)b * k + a] : (BT)0;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int bb = 0; bb < kRC; ++bb) {
+      CT x[4], y[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        x[q] = sl[bb][ty + 16 * q];  // rows
+        y[q] = sr[bb][tx + 16 * q];  // a
+      }
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[p][q] = fma(x[p], y[q], acc[p][q]);
+    }
+    __syncthreads();
+  }
+  // squared norms of this tile's 64 t-entries per row: reduce over tx (16
+  // lanes sharing a row) in a fixed butterfly
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    double s = 0.0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) s += (double)acc[p][q] * (double)acc[p][q];
+    for (int o = 8; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    const int64_t r = r0 + ty + 16 * p;
+    if (tx == 0 && r < n) part[(int64_t)blockIdx.y * n + r] = s;
+  }
+}
+
+__global__ void k_uq_diag(const double* __restrict__ part, int ntiles, int64_t n, double scale,
+                          double* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int t = 0; t < ntiles; ++t) s += part[(int64_t)t * n + i];
+    out[i] = scale * (1.0 - s);
+  }
+}
+
+template <typename T>
+__global__ void k_to_basis(const double* __restrict__ a, T* __restrict__ b, int64_t count) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (T)a[i];
+}
+
+template <typename T>
+__global__ void k_fill(T* __restrict__ p, int64_t count, T v) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = v;
+}
+
+lslu_status fail(Ctx* c, lslu_status st, const std::string& msg) {
+  c->err = msg;
+  return st;
+}
+
+// Gram products B1^T B2 (cols1 x cols2, FP64, ld ldc) on the device.
+template <typename BT>
+cudaError_t gram(const BT* B1, int cols1, const BT* B2, int cols2, int64_t ld, int64_t rows,
+                 bool symmetric, double* C, int64_t ldc, int2* dpairs, double* part,
+                 int64_t part_cap, cudaStream_t s) {
+  const int t1 = (cols1 + kTG - 1) / kTG, t2 = (cols2 + kTG - 1) / kTG;
+  std::vector<int2> pairs;
+  for (int i = 0; i < t1; ++i)
+    for (int j = symmetric ? i : 0; j < t2; ++j) pairs.push_back(make_int2(i, j));
+  const int np = (int)pairs.size();
+  int nsl = std::max(1, std::min(kSlicesMax, (960 + np - 1) / np));
+  while (nsl > 1 && (int64_t)nsl * np * kTG * kTG > part_cap) --nsl;
+  if ((int64_t)nsl * np * kTG * kTG > part_cap) return cudaErrorInvalidValue;
+  int64_t rps = (rows + nsl - 1) / nsl;
+  rps = (rps + kRC - 1) / kRC * kRC;
+  cudaError_t e = cudaMemcpyAsync(dpairs, pairs.data(), np * sizeof(int2), cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return e;
+  k_gram_tiles<BT><<<dim3(np, nsl), 256, 0, s>>>(B1, cols1, B2, cols2, ld, rows, dpairs, (int)rps,
+                                                part);
+  const int64_t tot = (int64_t)np * kTG * kTG;
+  k_gram_reduce<<<(unsigned)std::min<int64_t>((tot + 255) / 256, 4096), 256, 0, s>>>(
+      part, dpairs, np, nsl, cols1, cols2, symmetric ? 1 : 0, C, ldc);
+  e = cudaStreamSynchronize(s);  // the host pair list goes out of scope
+  return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+template <typename BT>
+lslu_status uq_impl(Ctx* c, double sigma2, double lam, double* var_diag, double* var_sum) {
+  const int k = c->last_k;
+  const int64_t n = c->n, m = c->m;
+  cudaStream_t s = c->stream;
+  const BT* L = reinterpret_cast<const BT*>(c->L);
+  const BT* D = reinterpret_cast<const BT*>(c->D);
+  // work space: 5 k x k FP64, 2 k-vectors, pair list, Gram partials, ones
+  // column, row partials
+  const int tiles = (k + kTG - 1) / kTG;
+  const int64_t part_cap = std::max<int64_t>((int64_t)1024 * kTG * kTG,
+                                             (int64_t)tiles * (tiles + 1) / 2 * kTG * kTG);
+  const int64_t rows_part = (int64_t)tiles * n;
+  const int64_t kk = (int64_t)k * k;
+  const size_t bytes = (size_t)(5 * kk + 4 * k + 8) * 8 + (size_t)tiles * tiles * sizeof(int2) +
+                       (size_t)std::max(part_cap, rows_part) * 8 + (size_t)c->ldl * sizeof(BT) +
+                       (size_t)kk * sizeof(BT) + 16 * 256;
+  char* ws = nullptr;
+  cudaError_t e = cudaMalloc(&ws, bytes);
+  if (e != cudaSuccess) return fail(c, LSLU_ERR_OOM, "uq work space");
+  auto take = [&](size_t b) {
+    char* p = ws;
+    ws += (b + 255) / 256 * 256;
+    return p;
+  };
+  char* base = ws;
+  double* GL = (double*)take(kk * 8);
+  double* GD = (double*)take(kk * 8);
+  double* X = (double*)take(kk * 8);
+  double* Y = (double*)take(kk * 8);
+  double* Ri = (double*)take(kk * 8);
+  double* sL = (double*)take(k * 8);
+  double* tv = (double*)take(k * 8);
+  double* scal = (double*)take(64);
+  int2* pairs = (int2*)take((size_t)tiles * tiles * sizeof(int2) + 16);
+  double* part = (double*)take((size_t)std::max(part_cap, rows_part) * 8);
+  BT* ones = (BT*)take((size_t)c->ldl * sizeof(BT));
+  BT* Rib = (BT*)take((size_t)kk * sizeof(BT));
+  const int g = (int)std::min<int64_t>((n + 255) / 256, (int64_t)c->num_sms * 8);
+  k_fill<BT><<<g, 256, 0, s>>>(ones, n, (BT)1);
+  const double scale = sigma2 / (lam * lam);
+  // Gram products
+  if ((e = gram<BT>(L, k, L, k, c->ldl, n, true, GL, k, pairs, part, part_cap, s)) != cudaSuccess ||
+      (e = gram<BT>(D, k, D, k, c->ldd, m, true, GD, k, pairs, part, part_cap, s)) != cudaSuccess ||
+      (e = gram<BT>(L, k, ones, 1, c->ldl, n, false, sL, k, pairs, part, part_cap, s)) !=
+          cudaSuccess) {
+    cudaFree(base);
+    return fail(c, LSLU_ERR_CUDA, std::string("uq gram: ") + cudaGetErrorString(e));
+  }
+  // X = W^-1, Y = G_D X, S = G_L + lambda^2 X^T Y (into GL)
+  k_upper_inverse<<<1, 256, 0, s>>>(c->W, c->kmax, k, X);
+  const dim3 gg((k + 15) / 16, (k + 15) / 16);
+  k_gemm_f64<<<gg, 256, 0, s>>>(GD, 0, X, nullptr, 1.0, 0.0, k, Y);
+  k_gemm_f64<<<gg, 256, 0, s>>>(X, 1, Y, GL, lam * lam, 1.0, k, GD);  // GD <- S
+  k_uq_factor<<<1, 1024, 0, s>>>(GD, k, Ri, sL, tv, (double)n, scale, scal, scal + 1);
+  if (var_diag) {
+    k_to_basis<BT><<<64, 256, 0, s>>>(Ri, Rib, kk);
+    const dim3 gr((unsigned)((n + kTG - 1) / kTG), (unsigned)tiles);
+    k_uq_rows<BT><<<gr, 256, 0, s>>>(L, c->ldl, n, k, Rib, part);
+    k_uq_diag<<<g, 256, 0, s>>>(part, tiles, n, scale, var_diag);
+  }
+  double hs[2] = {0.0, 0.0};
+  e = cudaMemcpyAsync(hs, scal, 16, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  cudaFree(base);
+  if (e != cudaSuccess) return fail(c, LSLU_ERR_CUDA, std::string("uq: ") + cudaGetErrorString(e));
+  if (hs[1] != 0.0)
+    return fail(c, LSLU_ERR_INVALID_ARG, "uq: L^T L + lambda^2 (G^T G)^-1 is not positive definite");
+  if (var_sum) *var_sum = hs[0];
+  return LSLU_OK;
+}
+
+}  // namespace
+}  // namespace lslu
+
+using namespace lslu;
+
+extern "C" lslu_status lslu_uq(lslu_handle h, double sigma2, double lambda, int32_t ptr_location,
+                               double* var_diag, double* var_sum) {
+  Ctx* c = h;
+  if (!c) {
+    thread_error() = "NULL handle";
+    return LSLU_ERR_INVALID_ARG;
+  }
+  if (c->map_m) return fail(c, LSLU_ERR_INVALID_ARG, "lslu_uq takes single-problem handles");
+  if (c->last_k < 1) return fail(c, LSLU_ERR_INVALID_ARG, "lslu_uq needs a completed iteration");
+  if (!(sigma2 > 0.0) || !(lambda > 0.0) || !std::isfinite(sigma2) || !std::isfinite(lambda))
+    return fail(c, LSLU_ERR_INVALID_ARG, "sigma2 and lambda must be finite and > 0");
+  if (ptr_location != LSLU_HOST && ptr_location != LSLU_DEVICE)
+    return fail(c, LSLU_ERR_INVALID_ARG, "unknown ptr_location");
+  double* dd = var_diag;
+  if (var_diag && ptr_location == LSLU_HOST) {
+    if (cudaMalloc(&dd, c->n * sizeof(double)) != cudaSuccess)
+      return fail(c, LSLU_ERR_OOM, "uq output");
+  }
+  double sum = 0.0;
+  lslu_status st = c->value_type == LSLU_F64 ? uq_impl<double>(c, sigma2, lambda, dd, &sum)
+                                             : uq_impl<float>(c, sigma2, lambda, dd, &sum);
+  if (st == LSLU_OK && var_diag && ptr_location == LSLU_HOST) {
+    cudaError_t e = cudaMemcpy(var_diag, dd, c->n * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) st = fail(c, LSLU_ERR_CUDA, cudaGetErrorString(e));
+  }
+  if (var_diag && ptr_location == LSLU_HOST) cudaFree(dd);
+  if (st == LSLU_OK && var_sum) {
+    if (ptr_location == LSLU_HOST) {
+      *var_sum = sum;
+    } else if (cudaMemcpy(var_sum, &sum, 8, cudaMemcpyHostToDevice) != cudaSuccess) {
+      st = fail(c, LSLU_ERR_CUDA, "uq: copying the sum");
+    }
+  }
+  return st;
+}

@@ -28,7 +28,7 @@ EXPORTS = ("lslu_create", "lslu_solve", "lslu_get_state", "lslu_spmv", "lslu_pro
            "lslu_error_string", "lslu_destroy", "lslu_create_batched", "lslu_solve_batched",
            "lslu_adjoint", "lslu_solve_fixed_pivots", "lslu_create_shared",
            "lslu_solve_stopping", "lslu_solve_sampled", "lslu_set_spmv_shape",
-           "lslu_tune_spmv")
+           "lslu_tune_spmv", "lslu_uq")
 
 _lib = None
 
@@ -81,6 +81,8 @@ def load(path: str | None = None):
     lib.lslu_solve_batched.restype = i32
     lib.lslu_solve_fixed_pivots.argtypes = [vp, vp, vp, i32, i32, f64, i32, vp, vp, vp, vp]
     lib.lslu_solve_fixed_pivots.restype = i32
+    lib.lslu_uq.argtypes = [vp, f64, f64, i32, vp, vp]
+    lib.lslu_uq.restype = i32
     lib.lslu_set_spmv_shape.argtypes = [vp, i32, i32]
     lib.lslu_set_spmv_shape.restype = i32
     lib.lslu_tune_spmv.argtypes = [vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32), vp]
@@ -264,6 +266,15 @@ class Solver:
                                      _ptr(c), _ptr(lo), _ptr(ro))
         self._check(st)
         return dict(y=y, sigma=sig, c=c, lam=float(lo[0]), resid=float(ro[0]))
+
+    def uq(self, sigma2, lam, want_diag=True):
+        """Low-rank posterior variances (Section 5) from the last solve:
+        dict(var_diag (n) or None, var_sum)."""
+        d = np.zeros(self.n) if want_diag else None
+        tot = np.zeros(1)
+        self._check(self.lib.lslu_uq(self.h, float(sigma2), float(lam), HOST, _ptr(d),
+                                     _ptr(tot)))
+        return dict(var_diag=d, var_sum=float(tot[0]))
 
     SHAPES = ("16x2", "32x1", "16x1", "8x1", "8x2", "4x1")
 
