@@ -43,6 +43,10 @@ design notes):
       The Woodbury step keeps the factor lambda^-2 on the low-rank term:
       Gamma_k = sigma^2 lambda^-2 (I - Z Delta Z^T) (the last line of the
       printed derivation drops the factor its previous line carries).
+  R17 optimal lambda (Section 4, needs x_true): lam_k minimises
+      E(lam) = ||L_k y_k(lam) - x_true||^2; searched on the grid of R11, then 64
+      golden-section steps in log(lam) between the best point's neighbours
+      (kept only if E does not increase).
 """
 from __future__ import annotations
 
@@ -380,3 +384,48 @@ def uq_lowrank(L, D, W, lam, sigma2):
     zs = Z.T @ np.ones(n)
     total = sigma2 / (lam * lam) * (n - zs @ Delta @ zs)
     return diag, float(total)
+
+
+GOLDEN = (math.sqrt(5.0) - 1.0) / 2.0
+
+
+def optimal_lambda(L, sigma, c, V, x_true):
+    """Optimal Tikhonov parameter of the projected problem (reading R17):
+    argmin_lam ||L y(lam) - x_true||^2 with y from Eq. (4)."""
+    def E(lam):
+        r = L @ tikhonov_y(sigma, c, V, lam) - x_true
+        return float(r @ r)
+
+    if sigma.shape[0] == 0 or sigma[0] == 0.0:
+        return 0.0
+    grid = lambda_grid(sigma[0])
+    Eg = np.array([E(l) for l in grid])
+    i = int(np.argmin(Eg))
+    if i == 0 or i == grid.shape[0] - 1:
+        return float(grid[i])
+    a, b = math.log(grid[i - 1]), math.log(grid[i + 1])
+    cpt = b - GOLDEN * (b - a)
+    dpt = a + GOLDEN * (b - a)
+    ec, ed = E(math.exp(cpt)), E(math.exp(dpt))
+    for _ in range(64):
+        if ec < ed:
+            b, dpt, ed = dpt, cpt, ec
+            cpt = b - GOLDEN * (b - a)
+            ec = E(math.exp(cpt))
+        else:
+            a, cpt, ec = cpt, dpt, ed
+            dpt = a + GOLDEN * (b - a)
+            ed = E(math.exp(dpt))
+    lam = math.exp(0.5 * (a + b))
+    return lam if E(lam) <= Eg[i] else float(grid[i])
+
+
+def hybrid_lslu_optimal(A, b, K, x_true):
+    """Hybrid LSLU at iteration K with the optimal lambda (R17): returns
+    (x_K, lam_K, E)."""
+    hp = hessenberg_rect_pivoted(A, b, None, K)
+    k = hp["k"]
+    s_, c_, V = projected_svd(hp["H"][:k + 1, :k], hp["beta"])
+    lam = optimal_lambda(hp["L"], s_, c_, V, x_true)
+    x = hp["L"] @ tikhonov_y(s_, c_, V, lam)
+    return x, lam, float(np.sum((x - x_true) ** 2))
