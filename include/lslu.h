@@ -283,6 +283,18 @@ lslu_status lslu_timing(lslu_handle h, int32_t* spmv_launches, double* spmv_ms);
 /* Number of kernel launches made by the last lslu_solve. */
 int64_t lslu_last_launch_count(lslu_handle h);
 
+/* K iterations of Hybrid LSLU with the optimal Tikhonov parameter of the
+ * final projected problem, the one that minimises ||L_K y_K(lambda) - x_true||
+ * (Section 4's reference curves; needs the true solution): the error is
+ * evaluated on the 257-point grid sigma_1 10^[-14, 2] and refined by 64
+ * golden-section steps in log(lambda) between the best point's neighbours.
+ * Outputs x_out (n) = x_K for that lambda (equal to lslu_solve with
+ * LSLU_LAMBDA_FIXED and that lambda) and lambda_out (1, may be NULL); host or
+ * device per ptr_location (b: m, x_true: n, FP64).  A breakdown before
+ * iteration K is returned as its status. */
+lslu_status lslu_solve_optimal(lslu_handle h, const double* b, int32_t K, const double* x_true,
+                               int32_t ptr_location, double* x_out, double* lambda_out);
+
 /* Low-rank uncertainty quantification of Section 5 on the state of the last
  * lslu_solve (k = its k_done): with A^T A ~ L_k W_k (D_k^T D_k)^-1 W_k^T L_k^T
  * (Eq. nhr2) and lambda = sigma / alpha, the posterior covariance

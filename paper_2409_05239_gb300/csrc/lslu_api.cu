@@ -1147,6 +1147,94 @@ extern "C" lslu_status lslu_tune_spmv(lslu_handle h, int32_t reps, int32_t* shap
   return LSLU_OK;
 }
 
+extern "C" lslu_status lslu_solve_optimal(lslu_handle h, const double* b, int32_t K,
+                                          const double* x_true, int32_t ptr_location,
+                                          double* x_out, double* lambda_out) {
+  Ctx* c = h;
+  if (!c) return set_err(nullptr, LSLU_ERR_INVALID_ARG, "NULL handle");
+  if (c->map_m) return set_err(c, LSLU_ERR_INVALID_ARG, "single-problem handles only");
+  if (K < 1 || K > c->kmax) return set_err(c, LSLU_ERR_INVALID_ARG, "K must be in [1, max_iter]");
+  if (!b || !x_true || !x_out)
+    return set_err(c, LSLU_ERR_INVALID_ARG, "b, x_true and x_out are required");
+  if (ptr_location != LSLU_HOST && ptr_location != LSLU_DEVICE)
+    return set_err(c, LSLU_ERR_INVALID_ARG, "unknown ptr_location");
+  const bool host = ptr_location == LSLU_HOST;
+  const int64_t m = c->m, n = c->n;
+  cudaStream_t s = c->stream;
+  const cudaMemcpyKind h2d = host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  CK(cudaMemcpyAsync(c->xin, b, m * 8, h2d, s));
+  // x_true is staged behind b (the staging buffer holds m + n doubles)
+  CK(cudaMemcpyAsync(c->xin + m, x_true, n * 8, h2d, s));
+  // the basis and the factorisation of the final projected problem
+  lslu_status st = c->value_type == LSLU_F64
+                       ? solve_impl<double, double>(c, c->xin, nullptr, K, LSLU_LAMBDA_NONE, 0.0, false)
+                       : solve_impl<float, float>(c, c->xin, nullptr, K, LSLU_LAMBDA_NONE, 0.0, false);
+  if (st != LSLU_OK) return st;
+  c->adj_valid = false;
+  if (c->st_host[0].status != LSLU_OK)
+    return set_err(c, (lslu_status)c->st_host[0].status, "breakdown before iteration K");
+  c->last_k = K;
+  c->last_K = K;
+  double* G = nullptr;
+  CK(cudaMalloc(&G, ((size_t)K * K + K + 260) * sizeof(double)));
+  double* g = G + (size_t)K * K;
+  double* Eg = g + K;
+  double* dl = Eg + 257;
+  st = basis_gram_products(c, K, c->xin + m, G, g);
+  if (st == LSLU_OK) {
+    ProjWork w;
+    w.base = c->pw_single;
+    w.cluster = c->pw_cluster;
+    cudaError_t e = launch_optimal_lambda(w, K, c->st, G, g, Eg, dl, s);
+    double lam = 0.0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&lam, dl, 8, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) {
+      // y and x for that lambda: the FIXED-rule projected solve
+      ProjArgs pa;
+      std::memset(&pa, 0, sizeof(pa));
+      pa.H = c->H;
+      pa.ldh = c->kmax + 1;
+      pa.rule = LSLU_LAMBDA_FIXED;
+      pa.lambda = lam;
+      pa.m = c->prob_m[0];
+      pa.k_first = K;
+      pa.k_last = K;
+      pa.want_y = 1;
+      pa.y = c->y;
+      pa.ldy = c->kmax;
+      pa.nbatch = 1;
+      pa.st = c->st;
+      ProjWork w2;
+      w2.base = c->pw_single;
+      w2.cluster = c->pw_cluster;
+      w2.slot_stride = projected_slot_doubles(c->kmax, c->pw_cluster);
+      e = launch_projected(pa, w2, s);
+      if (e == cudaSuccess) {
+        if (c->value_type == LSLU_F64)
+          launch_recombine<double>((const double*)c->L, c->ldl, c->y, c->kmax, nullptr, c->xout,
+                                   n, nullptr, 1, nullptr, K, s, c->num_sms);
+        else
+          launch_recombine<float>((const float*)c->L, c->ldl, c->y, c->kmax, nullptr, c->xout,
+                                  n, nullptr, 1, nullptr, K, s, c->num_sms);
+        const cudaMemcpyKind d2o = host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+        e = cudaMemcpyAsync(x_out, c->xout, n * 8, d2o, s);
+        if (e == cudaSuccess && lambda_out) {
+          if (host)
+            *lambda_out = lam;
+          else
+            e = cudaMemcpyAsync(lambda_out, dl, 8, cudaMemcpyDeviceToDevice, s);
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      }
+    }
+    if (e != cudaSuccess) st = set_err(c, LSLU_ERR_CUDA, std::string("optimal lambda: ") +
+                                                           cudaGetErrorString(e));
+  }
+  cudaFree(G);
+  return st;
+}
+
 extern "C" lslu_status lslu_get_state(lslu_handle h, int32_t ptr_location, double* H, double* W,
                                       double* beta, void* L, void* D) {
   Ctx* c = h;

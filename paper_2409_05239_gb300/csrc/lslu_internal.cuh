@@ -341,6 +341,14 @@ struct ProjArgs {
 };
 cudaError_t launch_projected(const ProjArgs& a, ProjWork& w, cudaStream_t s);
 int64_t projected_slot_doubles(int kk, int CL);
+// Optimal lambda of the last projected problem of size K in slot w (needs
+// G = L^T L and g = L^T x_true, k x k and k, FP64): E on the 257-point grid
+// into Eg, then the refined minimiser into *lam_out (device).
+cudaError_t launch_optimal_lambda(const ProjWork& w, int K, const DevState* st, const double* G,
+                                  const double* g, double* Eg, double* lam_out, cudaStream_t s);
+// G = L_k^T L_k and g = L_k^T v (v: n FP64 on the device) for the bases of a
+// handle (lslu_uq.cu); allocates and frees its own work space.
+lslu_status basis_gram_products(struct Ctx* c, int k, const double* v, double* G, double* g);
 int projected_cluster_size();
 
 template <typename BT>

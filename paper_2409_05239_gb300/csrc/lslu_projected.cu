@@ -681,6 +681,132 @@ __global__ void __launch_bounds__(kT) k_projected(ProjArgs a, ProjWork w) {
   if (ts) ts[7] = gtimer();
 }
 
+// ---- optimal lambda (needs x_true) ----------------------------------------
+// y(lam) = Q z(lam) from the factorisation H = P B Q^T that k_projected leaves
+// in its work slot (alpha, beta of B, the right reflectors), z(lam) by the
+// same Givens sweep as phase 6, and E(lam) - ||x_true||^2 = y^T G y - 2 g^T y
+// with G = L^T L (k x k) and g = L^T x_true.  sm holds 4 (k+1) doubles.
+__device__ double opt_eval(const Slots& S, int k, double beta, double lam,
+                           const double* __restrict__ G, const double* __restrict__ g,
+                           double* sm, double* red) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  double* z = sm;
+  double* rho = z + (k + 1);
+  double* thv = rho + (k + 1);
+  double* ph = thv + (k + 1);
+  if (tid == 0) {
+    double rbar = ldg_cg(S.al), phibar = beta;
+    for (int j = 0; j < k; ++j) {
+      double rhat = rbar, phib = phibar;
+      if (lam != 0.0) {
+        const double r1 = hypot(rbar, lam);
+        phib = (rbar / r1) * phibar;
+        rhat = r1;
+      }
+      const double bj = ldg_cg(S.be + j + 1);
+      const double r = hypot(rhat, bj);
+      const double cs = rhat / r, sn = bj / r;
+      rho[j] = r;
+      ph[j] = cs * phib;
+      phibar = sn * phib;
+      if (j + 1 < k) {
+        const double an = ldg_cg(S.al + j + 1);
+        thv[j] = sn * an;
+        rbar = -cs * an;
+      }
+    }
+    z[k - 1] = ph[k - 1] / rho[k - 1];
+    for (int j = k - 2; j >= 0; --j) z[j] = (ph[j] - thv[j] * z[j + 1]) / rho[j];
+  }
+  __syncthreads();
+  for (int j = k - 1; j >= 0; --j) {  // z <- Q_j z
+    const double tr = ldg_cg(S.taur + j);
+    if (tr == 0.0) continue;
+    double s = 0.0;
+    for (int c = j + tid; c < k; c += nt) s = fma(ldg_cg(S.Qs + (int64_t)j * k + c), z[c], s);
+    s = block_sum(s, red);
+    for (int c = j + tid; c < k; c += nt) z[c] = fma(-tr * s, ldg_cg(S.Qs + (int64_t)j * k + c), z[c]);
+    __syncthreads();
+  }
+  double e = 0.0;
+  for (int i = tid; i < k; i += nt) {
+    double t = 0.0;
+    for (int jj = 0; jj < k; ++jj) t = fma(G[(int64_t)jj * k + i], z[jj], t);
+    e = fma(z[i], t - 2.0 * g[i], e);
+  }
+  return block_sum(e, red);
+}
+
+// One block per point of the lambda grid (the grid of the GCV search).
+__global__ void __launch_bounds__(kT) k_opt_grid(ProjWork w, int K, const DevState* st,
+                                                 const double* G, const double* g, double* Eg) {
+  extern __shared__ double sm[];
+  __shared__ double red[33];
+  const Slots S = carve(w.base, K, w.cluster);
+  const int k = min(K, st->k_done);
+  const double s1 = ldg_cg(S.sig);
+  if (k <= 0 || !(s1 > 0.0)) {
+    if (threadIdx.x == 0) Eg[blockIdx.x] = 0.0;
+    return;
+  }
+  const double lam = s1 * pow(10.0, -14.0 + 0.0625 * (int)blockIdx.x);
+  const double e = opt_eval(S, k, st->beta, lam, G, g, sm, red);
+  if (threadIdx.x == 0) Eg[blockIdx.x] = e;
+}
+
+// The best grid point (ties: the smaller lambda), then 64 golden-section
+// steps in log(lambda) between its neighbours; one block.
+__global__ void __launch_bounds__(kT) k_opt_refine(ProjWork w, int K, const DevState* st,
+                                                   const double* G, const double* g,
+                                                   const double* Eg, double* lam_out) {
+  extern __shared__ double sm[];
+  __shared__ double red[33];
+  __shared__ int ib;
+  const Slots S = carve(w.base, K, w.cluster);
+  const int k = min(K, st->k_done);
+  const double s1 = ldg_cg(S.sig);
+  if (k <= 0 || !(s1 > 0.0)) {
+    if (threadIdx.x == 0) *lam_out = 0.0;
+    return;
+  }
+  if (threadIdx.x == 0) {
+    int b = 0;
+    for (int i = 1; i < kGrid; ++i)
+      if (Eg[i] < Eg[b]) b = i;
+    ib = b;
+  }
+  __syncthreads();
+  const int b = ib;
+  double lam = s1 * pow(10.0, -14.0 + 0.0625 * b);
+  if (b > 0 && b < kGrid - 1) {
+    const double phi = 0.5 * (sqrt(5.0) - 1.0);
+    double lo = log(s1 * pow(10.0, -14.0 + 0.0625 * (b - 1)));
+    double hi = log(s1 * pow(10.0, -14.0 + 0.0625 * (b + 1)));
+    const double beta = st->beta;
+    double c = hi - phi * (hi - lo), d = lo + phi * (hi - lo);
+    double ec = opt_eval(S, k, beta, exp(c), G, g, sm, red);
+    double ed = opt_eval(S, k, beta, exp(d), G, g, sm, red);
+    for (int it = 0; it < 64; ++it) {
+      if (ec < ed) {
+        hi = d;
+        d = c;
+        ed = ec;
+        c = hi - phi * (hi - lo);
+        ec = opt_eval(S, k, beta, exp(c), G, g, sm, red);
+      } else {
+        lo = c;
+        c = d;
+        ec = ed;
+        d = lo + phi * (hi - lo);
+        ed = opt_eval(S, k, beta, exp(d), G, g, sm, red);
+      }
+    }
+    const double lm = exp(0.5 * (lo + hi));
+    if (opt_eval(S, k, beta, lm, G, g, sm, red) <= Eg[b]) lam = lm;
+  }
+  if (threadIdx.x == 0) *lam_out = lam;
+}
+
 }  // namespace
 
 int64_t projected_slot_doubles(int kk, int CL) {
@@ -748,6 +874,26 @@ cudaError_t launch_projected(const ProjArgs& a, ProjWork& w, cudaStream_t s) {
   cfg.attrs = at;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, k_projected, a, w);
+}
+
+}  // namespace lslu
+
+namespace lslu {
+
+cudaError_t launch_optimal_lambda(const ProjWork& w, int K, const DevState* st, const double* G,
+                                  const double* g, double* Eg, double* lam_out, cudaStream_t s) {
+  const size_t smem = (size_t)4 * (K + 1) * sizeof(double);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_opt_grid, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_opt_refine, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_opt_grid<<<kGrid, kT, smem, s>>>(w, K, st, G, g, Eg);
+  k_opt_refine<<<1, kT, smem, s>>>(w, K, st, G, g, Eg, lam_out);
+  return cudaGetLastError();
 }
 
 }  // namespace lslu

@@ -395,7 +395,41 @@ lslu_status uq_impl(Ctx* c, double sigma2, double lam, double* var_diag, double*
   return LSLU_OK;
 }
 
+template <typename BT>
+lslu_status gram_products_impl(Ctx* c, int k, const double* v, double* G, double* g) {
+  cudaStream_t s = c->stream;
+  const int tiles = (k + kTG - 1) / kTG;
+  const int64_t part_cap = std::max<int64_t>((int64_t)1024 * kTG * kTG,
+                                             (int64_t)tiles * (tiles + 1) / 2 * kTG * kTG);
+  int2* pairs = nullptr;
+  double* part = nullptr;
+  BT* vb = nullptr;
+  cudaError_t e = cudaMalloc(&pairs, (size_t)tiles * tiles * sizeof(int2) + 16);
+  if (e == cudaSuccess) e = cudaMalloc(&part, (size_t)part_cap * 8);
+  if (e == cudaSuccess) e = cudaMalloc(&vb, (size_t)c->ldl * sizeof(BT));
+  if (e == cudaSuccess) {
+    k_to_basis<BT><<<64, 256, 0, s>>>(v, vb, c->n);
+    const BT* L = reinterpret_cast<const BT*>(c->L);
+    e = gram<BT>(L, k, L, k, c->ldl, c->n, true, G, k, pairs, part, part_cap, s);
+    if (e == cudaSuccess) e = gram<BT>(L, k, vb, 1, c->ldl, c->n, false, g, k, pairs, part, part_cap, s);
+  }
+  cudaFree(pairs);
+  cudaFree(part);
+  cudaFree(vb);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, LSLU_ERR_CUDA, std::string("gram products: ") + cudaGetErrorString(e));
+  }
+  return LSLU_OK;
+}
+
 }  // namespace
+
+lslu_status basis_gram_products(Ctx* c, int k, const double* v, double* G, double* g) {
+  return c->value_type == LSLU_F64 ? gram_products_impl<double>(c, k, v, G, g)
+                                   : gram_products_impl<float>(c, k, v, G, g);
+}
+
 }  // namespace lslu
 
 using namespace lslu;

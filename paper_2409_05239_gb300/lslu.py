@@ -28,7 +28,7 @@ EXPORTS = ("lslu_create", "lslu_solve", "lslu_get_state", "lslu_spmv", "lslu_pro
            "lslu_error_string", "lslu_destroy", "lslu_create_batched", "lslu_solve_batched",
            "lslu_adjoint", "lslu_solve_fixed_pivots", "lslu_create_shared",
            "lslu_solve_stopping", "lslu_solve_sampled", "lslu_set_spmv_shape",
-           "lslu_tune_spmv", "lslu_uq")
+           "lslu_tune_spmv", "lslu_uq", "lslu_solve_optimal")
 
 _lib = None
 
@@ -81,6 +81,8 @@ def load(path: str | None = None):
     lib.lslu_solve_batched.restype = i32
     lib.lslu_solve_fixed_pivots.argtypes = [vp, vp, vp, i32, i32, f64, i32, vp, vp, vp, vp]
     lib.lslu_solve_fixed_pivots.restype = i32
+    lib.lslu_solve_optimal.argtypes = [vp, vp, i32, vp, i32, vp, vp]
+    lib.lslu_solve_optimal.restype = i32
     lib.lslu_uq.argtypes = [vp, f64, f64, i32, vp, vp]
     lib.lslu_uq.restype = i32
     lib.lslu_set_spmv_shape.argtypes = [vp, i32, i32]
@@ -266,6 +268,17 @@ class Solver:
                                      _ptr(c), _ptr(lo), _ptr(ro))
         self._check(st)
         return dict(y=y, sigma=sig, c=c, lam=float(lo[0]), resid=float(ro[0]))
+
+    def solve_optimal(self, b, K, x_true):
+        """x_K with the optimal lambda (needs x_true): dict(x, lam)."""
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        xt = np.ascontiguousarray(x_true, dtype=np.float64)
+        x = np.zeros(self.n)
+        lam = np.zeros(1)
+        self.epoch += 1
+        self._check(self.lib.lslu_solve_optimal(self.h, _ptr(b), int(K), _ptr(xt), HOST, _ptr(x),
+                                                _ptr(lam)))
+        return dict(x=x, lam=float(lam[0]))
 
     def uq(self, sigma2, lam, want_diag=True):
         """Low-rank posterior variances (Section 5) from the last solve:

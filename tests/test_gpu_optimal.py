@@ -1,0 +1,51 @@
+"""Optimal-lambda rule on the GPU (lslu_solve_optimal) against the oracle."""
+import numpy as np
+import pytest
+
+import oracle.lslu_oracle as O
+from paper_2409_05239_gb300 import lslu, tomo
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2409_05239_gb300 import build
+
+    build.build()
+
+
+@pytest.fixture(scope="module")
+def ct32():
+    return tomo.make_config("ct32")
+
+
+def oracle_err(P, K, lam):
+    hp = O.hessenberg_rect_pivoted(P.scipy(), P.b, None, K)
+    s, c, V = O.projected_svd(hp["H"], hp["beta"])
+    r = hp["L"] @ O.tikhonov_y(s, c, V, lam) - P.x_true
+    return float(r @ r)
+
+
+@pytest.mark.parametrize("K", [10, 20, 40])
+def test_optimal_f64_vs_oracle(ct32, K):
+    x_ref, lam_ref, e_ref = O.hybrid_lslu_optimal(ct32.scipy(), ct32.b, K, ct32.x_true)
+    with lslu.from_problem(ct32, "f64", K) as s:
+        r = s.solve_optimal(ct32.b, K, ct32.x_true)
+        f = s.solve(ct32.b, K, "fixed", r["lam"])
+    assert np.array_equal(r["x"], f["x"])
+    assert abs(r["lam"] - lam_ref) <= 1e-4 * lam_ref
+    e_gpu = oracle_err(ct32, K, r["lam"])
+    assert e_gpu <= e_ref * (1 + 1e-8)
+    assert abs(float(np.sum((r["x"] - ct32.x_true) ** 2)) - e_ref) <= 1e-8 * e_ref
+
+
+def test_optimal_f32_large():
+    P = tomo.make_config("ct256")
+    K = 50
+    with lslu.from_problem(P, "f32", K) as s:
+        r = s.solve_optimal(P.b, K, P.x_true)
+        g = s.solve(P.b, K, "gcv")
+    e_opt = np.linalg.norm(r["x"] - P.x_true)
+    e_gcv = np.linalg.norm(g["x"] - P.x_true)
+    assert r["lam"] > 0 and e_opt <= e_gcv * (1 + 1e-6)
