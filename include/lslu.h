@@ -310,19 +310,30 @@ lslu_status lslu_solve_optimal(lslu_handle h, const double* b, int32_t K, const 
 lslu_status lslu_uq(lslu_handle h, double sigma2, double lambda, int32_t ptr_location,
                     double* var_diag, double* var_sum);
 
-/* Row shape of the sparse products: lanes per CSR row x 4-entry chunks in
- * flight per lane.  0: 16x2 (default for FP32/BF16 values), 1: 32x1,
- * 2: 16x1 (default for FP64 values), 3: 8x1, 4: 8x2, 5: 4x1.  Every shape
- * computes the same products with a different summation order, so results
- * change in rounding only; each is bitwise reproducible.  The shared-matrix
- * product of lslu_create_shared keeps its own 16-lane shape. */
+/* Row shape of the sparse products: lanes per CSR row x chunks in flight per
+ * lane.  Shapes 0-5 read 32-bit column indices in chunks of 4 entries:
+ * 0: 16x2 (default for FP32/BF16 values), 1: 32x1, 2: 16x1 (default for
+ * FP64 values), 3: 8x1, 4: 8x2, 5: 4x1; shapes 6-11 are the same lane shapes
+ * on 16-bit column offsets in chunks of 8 entries (2.5 instead of 4 bytes per
+ * entry; available when every 8-entry unit of the matrix spans fewer than
+ * 2^16 columns, see lslu_spmv_config).  Every shape computes the same
+ * products with a different summation order, so results change in rounding
+ * only; each is bitwise reproducible.  The shared-matrix product of
+ * lslu_create_shared follows the default 16-lane shapes. */
 lslu_status lslu_set_spmv_shape(lslu_handle h, int32_t shape_A, int32_t shape_AT);
 
-/* Autotuner: times every row shape on the handle's A and A^T (reps launches
- * each, CUDA events on the handle's stream, after one warm-up launch) and
- * keeps the fastest for each.  Outputs (host, any may be NULL): the chosen
- * shapes and the average time of every shape in microseconds (us[0..5] for A,
- * us[6..11] for A^T).  Drops captured solves (they hold the old kernels). */
+/* The sparse products' configuration (host outputs, any may be NULL): the
+ * row shape of A and A^T and whether each has 16-bit column offsets. */
+lslu_status lslu_spmv_config(lslu_handle h, int32_t* shape_A, int32_t* shape_AT,
+                             int32_t* compressed_A, int32_t* compressed_AT);
+
+/* Autotuner: times every row shape on the handle's A and A^T (each rep
+ * launches A then A^T, as a solve does, so every launch finds the L2 state
+ * the other matrix leaves; CUDA events on the handle's stream, after one
+ * warm-up pair) and keeps the fastest shape for each.  Outputs (host, any may
+ * be NULL): the chosen shapes and the average time of every shape in
+ * microseconds (us[0..11] for A, us[12..23] for A^T; -1 where unavailable).
+ * Drops captured solves (they hold the old kernels). */
 lslu_status lslu_tune_spmv(lslu_handle h, int32_t reps, int32_t* shape_A, int32_t* shape_AT,
                            double* us);
 

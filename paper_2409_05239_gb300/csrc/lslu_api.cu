@@ -1079,11 +1079,28 @@ extern "C" lslu_status lslu_set_spmv_shape(lslu_handle h, int32_t shape_A, int32
   Ctx* c = h;
   if (!c) return set_err(nullptr, LSLU_ERR_INVALID_ARG, "NULL handle");
   if (shape_A < 0 || shape_A >= kNumShapes || shape_AT < 0 || shape_AT >= kNumShapes)
-    return set_err(c, LSLU_ERR_INVALID_ARG, "shape must be in [0, 6)");
+    return set_err(c, LSLU_ERR_INVALID_ARG, "shape must be in [0, 12)");
+  if ((shape_A >= kShapesPerFormat && !c->A.compressed) ||
+      (shape_AT >= kShapesPerFormat && !c->AT.compressed))
+    return set_err(c, LSLU_ERR_INVALID_ARG,
+                   "16-bit offset shapes need a matrix whose 8-entry units span < 2^16 columns");
   CK(cudaStreamSynchronize(c->stream));
   c->A.shape = shape_A;
   c->AT.shape = shape_AT;
+  c->A.use_cmp = shape_A >= kShapesPerFormat;
+  c->AT.use_cmp = shape_AT >= kShapesPerFormat;
   drop_graphs(c);  // captured solves hold the kernels of the old shapes
+  return LSLU_OK;
+}
+
+extern "C" lslu_status lslu_spmv_config(lslu_handle h, int32_t* shape_A, int32_t* shape_AT,
+                                        int32_t* compressed_A, int32_t* compressed_AT) {
+  Ctx* c = h;
+  if (!c) return set_err(nullptr, LSLU_ERR_INVALID_ARG, "NULL handle");
+  if (shape_A) *shape_A = c->A.shape;
+  if (shape_AT) *shape_AT = c->AT.shape;
+  if (compressed_A) *compressed_A = c->A.compressed;
+  if (compressed_AT) *compressed_AT = c->AT.compressed;
   return LSLU_OK;
 }
 
@@ -1098,49 +1115,73 @@ extern "C" lslu_status lslu_tune_spmv(lslu_handle h, int32_t reps, int32_t* shap
   // not change the time
   CK(cudaMemsetAsync(c->q, 0, (size_t)c->n * bb, s));
   CK(cudaMemsetAsync(c->u, 0, (size_t)c->m * bb, s));
-  cudaEvent_t e0, e1;
-  CK(cudaEventCreate(&e0));
-  CK(cudaEventCreate(&e1));
-  int best[2] = {c->A.shape, c->AT.shape};
-  for (int which = 0; which < 2; ++which) {
-    DevCsr& M = which == 0 ? c->A : c->AT;
-    const void* x = which == 0 ? c->q : c->u;
-    void* y = which == 0 ? c->u : c->q;
-    const int saved = M.shape;
-    float best_ms = 0.f;
-    for (int sh = 0; sh < kNumShapes; ++sh) {
-      M.shape = sh;
-      auto run = [&]() {
-        if (c->value_type == LSLU_F64)
-          launch_spmv<double, double>(M, c->value_type, (const double*)x, (double*)y, s,
-                                      c->num_sms);
-        else
-          launch_spmv<float, float>(M, c->value_type, (const float*)x, (float*)y, s,
-                                    c->num_sms);
-      };
-      run();  // warm-up
-      cudaEventRecord(e0, s);
-      for (int r = 0; r < reps; ++r) run();
-      cudaEventRecord(e1, s);
-      cudaError_t e = cudaEventSynchronize(e1);
-      float ms = 0.f;
-      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-      if (e != cudaSuccess) {
-        M.shape = saved;
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
-        return set_err(c, LSLU_ERR_CUDA, std::string("tuning: ") + cudaGetErrorString(e));
-      }
-      if (us) us[which * kNumShapes + sh] = 1e3 * ms / reps;
-      if (sh == 0 || ms < best_ms) {
-        best_ms = ms;
-        best[which] = sh;
+  std::vector<cudaEvent_t> ev(2 * reps + 1);
+  for (auto& e : ev) CK(cudaEventCreate(&e));
+  const int saved[2] = {c->A.shape, c->AT.shape};
+  const int saved_cmp[2] = {c->A.use_cmp, c->AT.use_cmp};
+  int best[2] = {saved[0], saved[1]};
+  float best_ms[2] = {0.f, 0.f};
+  bool have[2] = {false, false};
+  auto run = [&](DevCsr& M, const void* x, void* y) {
+    if (c->value_type == LSLU_F64)
+      launch_spmv<double, double>(M, c->value_type, (const double*)x, (double*)y, s, c->num_sms);
+    else
+      launch_spmv<float, float>(M, c->value_type, (const float*)x, (float*)y, s, c->num_sms);
+  };
+  lslu_status st = LSLU_OK;
+  for (int sh = 0; sh < kNumShapes && st == LSLU_OK; ++sh) {
+    const bool cmp = sh >= kShapesPerFormat;
+    if (cmp && !(c->A.compressed && c->AT.compressed)) {
+      if (us) us[sh] = us[kNumShapes + sh] = -1.0;  // not available
+      continue;
+    }
+    c->A.shape = c->AT.shape = sh;
+    c->A.use_cmp = c->AT.use_cmp = cmp;
+    // A and A^T alternate, as in a solve, so that each launch finds the L2
+    // state the other matrix leaves behind
+    run(c->A, c->q, c->u);
+    run(c->AT, c->u, c->q);
+    cudaEventRecord(ev[0], s);
+    for (int r = 0; r < reps; ++r) {
+      run(c->A, c->q, c->u);
+      cudaEventRecord(ev[2 * r + 1], s);
+      run(c->AT, c->u, c->q);
+      cudaEventRecord(ev[2 * r + 2], s);
+    }
+    cudaError_t e = cudaEventSynchronize(ev[2 * reps]);
+    float t[2] = {0.f, 0.f};
+    for (int r = 0; r < reps && e == cudaSuccess; ++r) {
+      float a = 0.f, b = 0.f;
+      e = cudaEventElapsedTime(&a, ev[2 * r], ev[2 * r + 1]);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&b, ev[2 * r + 1], ev[2 * r + 2]);
+      t[0] += a;
+      t[1] += b;
+    }
+    if (e != cudaSuccess) {
+      st = set_err(c, LSLU_ERR_CUDA, std::string("tuning: ") + cudaGetErrorString(e));
+      break;
+    }
+    for (int w = 0; w < 2; ++w) {
+      if (us) us[w * kNumShapes + sh] = 1e3 * t[w] / reps;
+      if (!have[w] || t[w] < best_ms[w]) {
+        best_ms[w] = t[w];
+        best[w] = sh;
+        have[w] = true;
       }
     }
-    M.shape = best[which];
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+  for (auto& e : ev) cudaEventDestroy(e);
+  if (st != LSLU_OK) {
+    c->A.shape = saved[0];
+    c->AT.shape = saved[1];
+    c->A.use_cmp = saved_cmp[0];
+    c->AT.use_cmp = saved_cmp[1];
+    return st;
+  }
+  c->A.shape = best[0];
+  c->AT.shape = best[1];
+  c->A.use_cmp = best[0] >= kShapesPerFormat;
+  c->AT.use_cmp = best[1] >= kShapesPerFormat;
   drop_graphs(c);
   if (shape_A) *shape_A = best[0];
   if (shape_AT) *shape_AT = best[1];

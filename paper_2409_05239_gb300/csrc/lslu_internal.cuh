@@ -25,9 +25,11 @@ constexpr int kMaxIter = 2048;
 // belongs to exactly one problem.
 constexpr int kTile = 128;
 
-// Row shapes of the sparse products (lanes per CSR row x 4-entry chunks in
-// flight per lane); each matrix has one, set at create (the default of its
-// value type) or by lslu_tune_spmv / lslu_set_spmv_shape.
+// Row shapes of the sparse products (lanes per CSR row x chunks in flight per
+// lane); each matrix has one, set at create (the default of its value type)
+// or by lslu_tune_spmv / lslu_set_spmv_shape.  Shapes 0-5 read 32-bit column
+// indices (chunks of 4 entries), shapes 6-11 the same lane shapes on 16-bit
+// offsets (chunks of 8 entries; only for matrices that have them).
 enum {
   kShapeG16U2 = 0,
   kShapeG32U1 = 1,
@@ -35,12 +37,17 @@ enum {
   kShapeG8U1 = 3,
   kShapeG8U2 = 4,
   kShapeG4U1 = 5,
-  kNumShapes = 6
+  kShapesPerFormat = 6,
+  kNumShapes = 12
 };
 int default_shape(int vt);
 
 struct DevCsr {
   int shape = kShapeG16U2;
+  int compressed = 0;          // 16-bit column offsets available (off, ubase)
+  int use_cmp = 0;             // the shape reads them (shape >= kShapesPerFormat)
+  uint16_t* off = nullptr;     // nnz_padded: column - first column of its 8-entry unit
+  int32_t* ubase = nullptr;    // nnz_padded / 8: first column of every unit
   int64_t rows = 0, cols = 0;
   int64_t nnz = 0;         // true non-zeros
   int64_t nnz_padded = 0;  // entries stored, including padding
@@ -243,17 +250,19 @@ void launch_spmv_pivots_shape_b(int shape, const DevCsr& A, int vt, const void* 
                                 const PivotCoef& pc, cudaStream_t s);
 inline void launch_spmv_shape(int shape, const DevCsr& A, int vt, const void* x, void* y,
                               cudaStream_t s) {
-  if (shape <= kShapeG16U1)
-    launch_spmv_shape_a(shape, A, vt, x, y, s);
+  const int g = shape % kShapesPerFormat;  // the format follows A.use_cmp
+  if (g <= kShapeG16U1)
+    launch_spmv_shape_a(g, A, vt, x, y, s);
   else
-    launch_spmv_shape_b(shape, A, vt, x, y, s);
+    launch_spmv_shape_b(g, A, vt, x, y, s);
 }
 inline void launch_spmv_pivots_shape(int shape, const DevCsr& A, int vt, const void* x,
                                      void* y, const PivotCoef& pc, cudaStream_t s) {
-  if (shape <= kShapeG16U1)
-    launch_spmv_pivots_shape_a(shape, A, vt, x, y, pc, s);
+  const int g = shape % kShapesPerFormat;
+  if (g <= kShapeG16U1)
+    launch_spmv_pivots_shape_a(g, A, vt, x, y, pc, s);
   else
-    launch_spmv_pivots_shape_b(shape, A, vt, x, y, pc, s);
+    launch_spmv_pivots_shape_b(g, A, vt, x, y, pc, s);
 }
 
 // Build the padded CSR of A and of A^T (host-side layout, then upload).

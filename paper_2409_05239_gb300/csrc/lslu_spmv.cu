@@ -27,27 +27,54 @@ constexpr int kRowsPerBlock = 256 / kGroup;
 // 16-byte loads and the matrix is read once for all R products.  Lane gl of a
 // row's 16-lane group takes the same chunks in the same order as row_dot_len,
 // and each right-hand side keeps its own accumulator, so every output equals
-// the single-vector product bit for bit.
+// the single-vector product of the default 16-lane shapes bit for bit (16x2 on
+// 32-bit columns, 16x1 on 16-bit offsets).
 
-// Product of CSR row `row` with right-hand side r of the interleaved xi.
-template <typename VT, int RS>
+// Columns of the lane's next chunk (C entries at position p of the row
+// storage): 32-bit indices (C = 4) or a unit of 16-bit offsets (C = 8).
+template <bool CMP>
+__device__ __forceinline__ void chunk_cols(const ColIdx& ci, int32_t p, int32_t (&c)[CMP ? 8 : 4]) {
+  if constexpr (CMP) {
+    const uint4 o = ld_stream_off(ci.off + p);
+    const int32_t b = __ldg(ci.ubase + (p >> 3));
+    const uint32_t w[4] = {o.x, o.y, o.z, o.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      c[2 * q] = b + (int32_t)(w[q] & 0xffffu);
+      c[2 * q + 1] = b + (int32_t)(w[q] >> 16);
+    }
+  } else {
+    const int4 c4 = ld_stream(ci.col + p);
+    c[0] = c4.x; c[1] = c4.y; c[2] = c4.z; c[3] = c4.w;
+  }
+}
+
+template <typename VT, bool CMP>
+__device__ __forceinline__ void chunk_vals(const VT* val, int32_t p, float (&v)[CMP ? 8 : 4]) {
+  if constexpr (CMP)
+    load_vals8<float>(val + p, v);
+  else
+    load_vals_cs<float>(val + p, v);
+}
+
+// Product of CSR row `row` with right-hand side r of the interleaved xi, in
+// the chunk order of the single-vector default shape (16 lanes).
+template <typename VT, int RS, bool CMP>
 __device__ __forceinline__ float row_dot_rhs(int64_t row, const int32_t* __restrict__ rp,
-                                             const int32_t* __restrict__ rl,
-                                             const int32_t* __restrict__ col,
+                                             const int32_t* __restrict__ rl, const ColIdx ci,
                                              const VT* __restrict__ val,
                                              const float* __restrict__ xi, int r, int gl) {
-  constexpr int C = ValTraits<VT>::kChunk;
+  constexpr int C = CMP ? 8 : 4;
   constexpr int S = kGroup * C;
   const int32_t start = __ldg(rp + row), len = __ldg(rl + row);
   float acc = 0.f;
   for (int32_t e = gl * C; e < len; e += S) {
-    const int4 c4 = ld_stream(col + start + e);
+    int32_t c[C];
     float v[C];
-    load_vals_cs<float>(val + start + e, v);
-    acc = fmaf(v[0], __ldg(xi + (int64_t)c4.x * RS + r), acc);
-    acc = fmaf(v[1], __ldg(xi + (int64_t)c4.y * RS + r), acc);
-    acc = fmaf(v[2], __ldg(xi + (int64_t)c4.z * RS + r), acc);
-    acc = fmaf(v[3], __ldg(xi + (int64_t)c4.w * RS + r), acc);
+    chunk_cols<CMP>(ci, start + e, c);
+    chunk_vals<VT, CMP>(val, start + e, v);
+#pragma unroll
+    for (int i = 0; i < C; ++i) acc = fmaf(v[i], __ldg(xi + (int64_t)c[i] * RS + r), acc);
   }
   return group_sum<kGroup>(acc);
 }
@@ -65,20 +92,19 @@ __device__ __forceinline__ void gather_rhs(const float* __restrict__ xi, int32_t
 // y[r * ystride + row] = (A xi_r)(row) for r < R, rows of the shared CSR;
 // pivot blocks as in k_spmv_pivots, with output rows of problem p at
 // p * ystride + row.
-template <typename VT, int RS>
+template <typename VT, int RS, bool CMP>
 __global__ void __launch_bounds__(256, 4)
     k_spmm_pivots(int64_t rows, const int32_t* __restrict__ rp, const int32_t* __restrict__ rl,
-                  const int32_t* __restrict__ col, const VT* __restrict__ val,
-                  const float* __restrict__ xi, float* __restrict__ y, int64_t ystride, int R,
-                  PivotCoef pc) {
-  constexpr int C = ValTraits<VT>::kChunk;
+                  const ColIdx ci, const VT* __restrict__ val, const float* __restrict__ xi,
+                  float* __restrict__ y, int64_t ystride, int R, PivotCoef pc) {
+  constexpr int C = CMP ? 8 : 4;
   constexpr int S = kGroup * C;
   const int lane = threadIdx.x & 31;
   const int npiv_all = pc.npiv_blocks * pc.nprob;
   if ((int)blockIdx.x < npiv_all) {
     pivot_blocks<float, kGroup>(pc, [=](int p, int32_t row, int gl) {
-      return row_dot_rhs<VT, RS>((int64_t)row - (int64_t)p * ystride, rp, rl, col, val, xi, p,
-                                 gl);
+      return row_dot_rhs<VT, RS, CMP>((int64_t)row - (int64_t)p * ystride, rp, rl, ci, val, xi,
+                                      p, gl);
     });
     return;
   }
@@ -93,10 +119,10 @@ __global__ void __launch_bounds__(256, 4)
 #pragma unroll
   for (int r = 0; r < RS; ++r) acc[r] = 0.f;
   for (int32_t e = gl * C; e < len; e += S) {
-    const int4 c4 = ld_stream(col + start + e);
+    int32_t cs[C];
     float v[C];
-    load_vals_cs<float>(val + start + e, v);
-    const int32_t cs[4] = {c4.x, c4.y, c4.z, c4.w};
+    chunk_cols<CMP>(ci, start + e, cs);
+    chunk_vals<VT, CMP>(val, start + e, v);
 #pragma unroll
     for (int i = 0; i < C; ++i) {
       float xv[RS];
@@ -196,6 +222,42 @@ cudaError_t upload_padded(int64_t rows, int64_t cols, const std::vector<int64_t>
   if (tot && (e = cudaMemcpyAsync(out->col, pc.data(), tot * sizeof(int32_t),
                                   cudaMemcpyHostToDevice, s)) != cudaSuccess)
     return e;
+  // 16-bit column offsets when every 8-entry unit (rows start and end on unit
+  // boundaries) spans fewer than 2^16 columns: offset = column - unit minimum
+  const int64_t units = tot / kRowAlign;
+  std::vector<uint16_t> po;
+  std::vector<int32_t> pb;
+  bool fits = units > 0;
+  if (fits) {
+    po.resize((size_t)tot);
+    pb.resize((size_t)units);
+    for (int64_t u = 0; u < units && fits; ++u) {
+      const int32_t* c = pc.data() + u * kRowAlign;
+      int32_t lo = c[0], hi = c[0];
+      for (int i = 1; i < kRowAlign; ++i) {
+        lo = std::min(lo, c[i]);
+        hi = std::max(hi, c[i]);
+      }
+      if ((int64_t)hi - lo > 65535) {
+        fits = false;
+        break;
+      }
+      pb[u] = lo;
+      for (int i = 0; i < kRowAlign; ++i) po[u * kRowAlign + i] = (uint16_t)(c[i] - lo);
+    }
+  }
+  if (fits) {
+    if ((e = cudaMalloc(&out->off, tot * sizeof(uint16_t))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&out->ubase, units * sizeof(int32_t))) != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(out->off, po.data(), tot * sizeof(uint16_t), cudaMemcpyHostToDevice,
+                             s)) != cudaSuccess)
+      return e;
+    if ((e = cudaMemcpyAsync(out->ubase, pb.data(), units * sizeof(int32_t),
+                             cudaMemcpyHostToDevice, s)) != cudaSuccess)
+      return e;
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;  // po, pb go out of scope
+    out->compressed = 1;
+  }
   if (tot) {
     if (vt == LSLU_F64) {
       e = cudaMemcpyAsync(out->val, pv.data(), tot * 8, cudaMemcpyHostToDevice, s);
@@ -239,8 +301,9 @@ cudaError_t build_csr_pair(int64_t m, int64_t n, const int64_t* rp, const int32_
       cit[pos] = (int32_t)r;
       vt_[pos] = va[i];
     }
+  const cudaError_t e2 = upload_padded(n, m, rpt, cit, vt_, vt, AT, s);
   A->shape = AT->shape = default_shape(vt);
-  return upload_padded(n, m, rpt, cit, vt_, vt, AT, s);
+  return e2;
 }
 
 void free_csr(DevCsr* c) {
@@ -248,9 +311,13 @@ void free_csr(DevCsr* c) {
   cudaFree(c->row_len);
   cudaFree(c->col);
   cudaFree(c->val);
+  cudaFree(c->off);
+  cudaFree(c->ubase);
   *c = DevCsr();
 }
 
+// 16 lanes per row with 8 entries in flight per lane (two 4-entry chunks of
+// 32-bit columns); FP64 values keep 4 in flight (registers).
 int default_shape(int vt) { return vt == LSLU_F64 ? kShapeG16U1 : kShapeG16U2; }
 
 namespace {
@@ -265,34 +332,37 @@ bool native(int vt) {
 
 }  // namespace
 
+// Native products (FP64 vectors for FP64 values, FP32 otherwise) run in the
+// matrix's shape and column format; the others (FP64 vectors on FP32 / BF16
+// values: r0 with x0, the adjoint's x0 term) in the default shape.
 template <typename XT, typename YT>
 void launch_spmv(const DevCsr& A, int vt, const XT* x, YT* y, cudaStream_t s, int) {
-  if (A.shape != default_shape(vt) && native<XT, YT>(vt)) {
+  if (native<XT, YT>(vt) && A.shape != default_shape(vt)) {
     launch_spmv_shape(A.shape, A, vt, x, y, s);
     return;
   }
   if (vt == LSLU_F64)
-    spmv_run<double, XT, YT, 16, 1>(A, x, y, s);
+    spmv_run<double, XT, YT, 16, 1, false>(A, x, y, s);
   else if (vt == LSLU_F32)
-    spmv_run<float, XT, YT, 16, 2>(A, x, y, s);
+    spmv_run<float, XT, YT, 16, 2, false>(A, x, y, s);
   else
-    spmv_run<__nv_bfloat16, XT, YT, 16, 2>(A, x, y, s);
+    spmv_run<__nv_bfloat16, XT, YT, 16, 2, false>(A, x, y, s);
 }
 
 template <typename XT, typename YT>
 void launch_spmv_pivots(const DevCsr& A, int vt, const XT* x, YT* y, PivotCoef pc,
                         cudaStream_t s) {
   pc.npiv_blocks = (pc.cnt + 7) / 8;
-  if (A.shape != default_shape(vt) && native<XT, YT>(vt)) {
+  if (native<XT, YT>(vt) && A.shape != default_shape(vt)) {
     launch_spmv_pivots_shape(A.shape, A, vt, x, y, pc, s);
     return;
   }
   if (vt == LSLU_F64)
-    spmv_pivots_run<double, XT, YT, 16, 1>(A, x, y, pc, s);
+    spmv_pivots_run<double, XT, YT, 16, 1, false>(A, x, y, pc, s);
   else if (vt == LSLU_F32)
-    spmv_pivots_run<float, XT, YT, 16, 2>(A, x, y, pc, s);
+    spmv_pivots_run<float, XT, YT, 16, 2, false>(A, x, y, pc, s);
   else
-    spmv_pivots_run<__nv_bfloat16, XT, YT, 16, 2>(A, x, y, pc, s);
+    spmv_pivots_run<__nv_bfloat16, XT, YT, 16, 2, false>(A, x, y, pc, s);
 }
 
 template <typename VT, int RS>
@@ -300,9 +370,14 @@ void spmm_typed(const DevCsr& A, const float* xi, float* y, int64_t ystride, int
                 const PivotCoef& pc, cudaStream_t s) {
   const int64_t blocks =
       (int64_t)pc.npiv_blocks * pc.nprob + (A.rows + kRowsPerBlock - 1) / kRowsPerBlock;
-  k_spmm_pivots<VT, RS><<<(unsigned)blocks, 256, 0, s>>>(
-      A.rows, A.row_ptr, A.row_len, A.col, reinterpret_cast<const VT*>(A.val), xi, y, ystride, R,
-      pc);
+  const ColIdx ci{A.col, A.off, A.ubase};
+  const VT* v = reinterpret_cast<const VT*>(A.val);
+  if (A.compressed && A.use_cmp)
+    k_spmm_pivots<VT, RS, true><<<(unsigned)blocks, 256, 0, s>>>(A.rows, A.row_ptr, A.row_len,
+                                                                 ci, v, xi, y, ystride, R, pc);
+  else
+    k_spmm_pivots<VT, RS, false><<<(unsigned)blocks, 256, 0, s>>>(A.rows, A.row_ptr, A.row_len,
+                                                                  ci, v, xi, y, ystride, R, pc);
 }
 
 template <typename VT>

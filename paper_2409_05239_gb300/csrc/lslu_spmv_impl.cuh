@@ -26,10 +26,11 @@ struct ValTraits {
   static constexpr int kChunk = 4;  // entries per chunk (16-byte column loads)
 };
 
-// Blocks of 256 threads kept resident per SM: bounds the registers per thread.
-template <typename VT, int U>
+// Blocks of 256 threads kept resident per SM: bounds the registers per thread
+// (E = 4-entry chunks in flight per lane).
+template <typename VT, int E>
 constexpr int min_blocks() {
-  return (U >= 2 || sizeof(VT) == 8) ? 6 : 8;
+  return (E >= 2 || sizeof(VT) == 8) ? 6 : 8;
 }
 
 template <typename AT>
@@ -86,11 +87,95 @@ __device__ __forceinline__ void load_vals_cs(const __nv_bfloat16* p, AT (&v)[4])
   }
 }
 
+// Compressed columns: 8 16-bit offsets of one 8-entry unit (16 bytes).
+__device__ __forceinline__ uint4 ld_stream_off(const uint16_t* p) {
+  uint4 c;
+  asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(c.x), "=r"(c.y), "=r"(c.z), "=r"(c.w)
+               : "l"(p));
+  return c;
+}
+template <typename AT, typename VT>
+__device__ __forceinline__ void load_vals8(const VT* p, AT (&v)[8]) {
+  AT a[4], b[4];
+  load_vals_cs<AT>(p, a);
+  load_vals_cs<AT>(p + 4, b);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    v[i] = a[i];
+    v[4 + i] = b[i];
+  }
+}
+template <typename AT>
+__device__ __forceinline__ void load_vals8(const __nv_bfloat16* p, AT (&v)[8]) {
+  uint32_t w[4];
+  asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3])
+               : "l"(p));
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    v[2 * i] = (AT)__uint_as_float(w[i] << 16);
+    v[2 * i + 1] = (AT)__uint_as_float(w[i] & 0xffff0000u);
+  }
+}
+
+// The column storage a kernel reads: 32-bit indices (chunks of 4 entries) or,
+// when every 8-entry unit spans fewer than 2^16 columns, 16-bit offsets from
+// the unit's first column (chunks of 8 entries; 2.5 bytes per entry).
+struct ColIdx {
+  const int32_t* col;     // nnz_padded 32-bit columns
+  const uint16_t* off;    // nnz_padded offsets (compressed)
+  const int32_t* ubase;   // nnz_padded / 8 unit bases (compressed)
+};
+
 // Dot product of one CSR row with x, computed by one group of G lanes (result
 // in every lane of the group; gl = lane index within the group; a lane with
 // len = 0 contributes nothing).  Lane gl takes chunks gl, gl+G, ... in order
 // (U chunks per step); the G partial sums are combined by a fixed butterfly,
 // so a row always gets the same bits.  Every lane of the warp must call it.
+template <typename VT, typename XT, typename YT, int G, int U>
+__device__ __forceinline__ YT row_dot_len_c(int32_t start, int32_t len, const ColIdx ci,
+                                            const VT* __restrict__ val,
+                                            const XT* __restrict__ x, int gl) {
+  constexpr int C = 8;
+  constexpr int S = G * C;
+  YT acc = 0;
+  for (int32_t e = gl * C; e < len; e += U * S) {
+    int32_t cidx[U][C];
+    YT v[U][C];
+    bool has[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      has[u] = u == 0 || e + u * S < len;
+      if (has[u]) {
+        const int32_t p = start + e + u * S;
+        const uint4 o = ld_stream_off(ci.off + p);
+        const int32_t b = __ldg(ci.ubase + (p >> 3));
+        const uint32_t w[4] = {o.x, o.y, o.z, o.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          cidx[u][2 * q] = b + (int32_t)(w[q] & 0xffffu);
+          cidx[u][2 * q + 1] = b + (int32_t)(w[q] >> 16);
+        }
+        load_vals8<YT>(val + p, v[u]);
+      } else {
+#pragma unroll
+        for (int i = 0; i < C; ++i) v[u][i] = 0;
+      }
+    }
+    XT xv[U][C];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int i = 0; i < C; ++i) xv[u][i] = has[u] ? __ldg(x + cidx[u][i]) : (XT)0;
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int i = 0; i < C; ++i) acc = fma(v[u][i], (YT)xv[u][i], acc);
+  }
+  return group_sum<G>(acc);
+}
+
 template <typename VT, typename XT, typename YT, int G, int U>
 __device__ __forceinline__ YT row_dot_len(int32_t start, int32_t len,
                                           const int32_t* __restrict__ col,
@@ -128,21 +213,23 @@ __device__ __forceinline__ YT row_dot_len(int32_t start, int32_t len,
   return group_sum<G>(acc);
 }
 
-template <typename VT, typename XT, typename YT, int G, int U>
+template <typename VT, typename XT, typename YT, int G, int U, bool CMP>
 __device__ __forceinline__ YT row_dot(int64_t row, bool valid, const int32_t* __restrict__ rp,
-                                      const int32_t* __restrict__ rl,
-                                      const int32_t* __restrict__ col,
+                                      const int32_t* __restrict__ rl, const ColIdx ci,
                                       const VT* __restrict__ val, const XT* __restrict__ x,
                                       int gl) {
   const int32_t start = valid ? __ldg(rp + row) : 0;
   const int32_t len = valid ? __ldg(rl + row) : 0;
-  return row_dot_len<VT, XT, YT, G, U>(start, len, col, val, x, gl);
+  if constexpr (CMP)
+    return row_dot_len_c<VT, XT, YT, G, U>(start, len, ci, val, x, gl);
+  else
+    return row_dot_len<VT, XT, YT, G, U>(start, len, ci.col, val, x, gl);
 }
 
-template <typename VT, typename XT, typename YT, int G, int U>
-__global__ void __launch_bounds__(256, min_blocks<VT, U>())
+template <typename VT, typename XT, typename YT, int G, int U, bool CMP>
+__global__ void __launch_bounds__(256, min_blocks<VT, CMP ? 2 * U : U>())
     k_spmv(int64_t rows, const int32_t* __restrict__ rp, const int32_t* __restrict__ rl,
-           const int32_t* __restrict__ col, const VT* __restrict__ val, const XT* __restrict__ x,
+           const ColIdx ci, const VT* __restrict__ val, const XT* __restrict__ x,
            YT* __restrict__ y) {
   constexpr int RPB = 256 / G;  // rows per block
   const int gl = threadIdx.x & (G - 1);
@@ -150,7 +237,7 @@ __global__ void __launch_bounds__(256, min_blocks<VT, U>())
   if ((int64_t)blockIdx.x * RPB + (threadIdx.x & ~31) / G >= rows)
     return;  // the whole warp is past the last row
   const bool valid = row < rows;
-  const YT acc = row_dot<VT, XT, YT, G, U>(row, valid, rp, rl, col, val, x, gl);
+  const YT acc = row_dot<VT, XT, YT, G, U, CMP>(row, valid, rp, rl, ci, val, x, gl);
   if (valid && gl == 0) y[row] = acc;
 }
 
@@ -231,11 +318,11 @@ __device__ __forceinline__ void pivot_blocks(const PivotCoef& pc, RowDot rowdot)
   }
 }
 
-template <typename VT, typename XT, typename YT, int G, int U>
-__global__ void __launch_bounds__(256, min_blocks<VT, U>())
+template <typename VT, typename XT, typename YT, int G, int U, bool CMP>
+__global__ void __launch_bounds__(256, min_blocks<VT, CMP ? 2 * U : U>())
     k_spmv_pivots(int64_t rows, const int32_t* __restrict__ rp, const int32_t* __restrict__ rl,
-                  const int32_t* __restrict__ col, const VT* __restrict__ val,
-                  const XT* __restrict__ x, YT* __restrict__ y, PivotCoef pc) {
+                  const ColIdx ci, const VT* __restrict__ val, const XT* __restrict__ x,
+                  YT* __restrict__ y, PivotCoef pc) {
   constexpr int RPB = 256 / G;
   const int lane = threadIdx.x & 31;
   const int npiv_all = pc.npiv_blocks * pc.nprob;
@@ -244,29 +331,50 @@ __global__ void __launch_bounds__(256, min_blocks<VT, U>())
     if (b0 + (threadIdx.x & ~31) / G >= rows) return;  // whole warp past the end
     const int64_t row = b0 + threadIdx.x / G;
     const bool valid = row < rows;
-    const YT acc = row_dot<VT, XT, YT, G, U>(row, valid, rp, rl, col, val, x, lane & (G - 1));
+    const YT acc =
+        row_dot<VT, XT, YT, G, U, CMP>(row, valid, rp, rl, ci, val, x, lane & (G - 1));
     if (valid && (lane & (G - 1)) == 0) y[row] = acc;
     return;
   }
   pivot_blocks<YT, G>(pc, [=](int, int32_t row, int gl) {
-    return row_dot<VT, XT, YT, G, U>(row, true, rp, rl, col, val, x, gl);
+    return row_dot<VT, XT, YT, G, U, CMP>(row, true, rp, rl, ci, val, x, gl);
   });
 }
 
-template <typename VT, typename XT, typename YT, int G, int U>
+// Launch in the matrix's column format: 16-bit offsets when its shape reads
+// them (use_cmp) and MAYCMP (native vector types), else 32-bit columns.
+template <typename VT, typename XT, typename YT, int G, int U, bool MAYCMP = true>
 void spmv_run(const DevCsr& A, const XT* x, YT* y, cudaStream_t s) {
   if (A.rows == 0) return;
   const int64_t blocks = (A.rows + 256 / G - 1) / (256 / G);
-  k_spmv<VT, XT, YT, G, U><<<(unsigned)blocks, 256, 0, s>>>(
-      A.rows, A.row_ptr, A.row_len, A.col, reinterpret_cast<const VT*>(A.val), x, y);
+  const ColIdx ci{A.col, A.off, A.ubase};
+  const VT* v = reinterpret_cast<const VT*>(A.val);
+  if constexpr (MAYCMP) {
+    if (A.compressed && A.use_cmp) {
+      k_spmv<VT, XT, YT, G, U, true><<<(unsigned)blocks, 256, 0, s>>>(A.rows, A.row_ptr,
+                                                                       A.row_len, ci, v, x, y);
+      return;
+    }
+  }
+  k_spmv<VT, XT, YT, G, U, false><<<(unsigned)blocks, 256, 0, s>>>(A.rows, A.row_ptr,
+                                                                    A.row_len, ci, v, x, y);
 }
 
-template <typename VT, typename XT, typename YT, int G, int U>
+template <typename VT, typename XT, typename YT, int G, int U, bool MAYCMP = true>
 void spmv_pivots_run(const DevCsr& A, const XT* x, YT* y, const PivotCoef& pc, cudaStream_t s) {
   const int64_t blocks =
       (int64_t)pc.npiv_blocks * pc.nprob + (A.rows + 256 / G - 1) / (256 / G);
-  k_spmv_pivots<VT, XT, YT, G, U><<<(unsigned)blocks, 256, 0, s>>>(
-      A.rows, A.row_ptr, A.row_len, A.col, reinterpret_cast<const VT*>(A.val), x, y, pc);
+  const ColIdx ci{A.col, A.off, A.ubase};
+  const VT* v = reinterpret_cast<const VT*>(A.val);
+  if constexpr (MAYCMP) {
+    if (A.compressed && A.use_cmp) {
+      k_spmv_pivots<VT, XT, YT, G, U, true><<<(unsigned)blocks, 256, 0, s>>>(
+          A.rows, A.row_ptr, A.row_len, ci, v, x, y, pc);
+      return;
+    }
+  }
+  k_spmv_pivots<VT, XT, YT, G, U, false><<<(unsigned)blocks, 256, 0, s>>>(
+      A.rows, A.row_ptr, A.row_len, ci, v, x, y, pc);
 }
 
 }  // namespace

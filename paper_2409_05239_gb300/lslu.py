@@ -28,7 +28,7 @@ EXPORTS = ("lslu_create", "lslu_solve", "lslu_get_state", "lslu_spmv", "lslu_pro
            "lslu_error_string", "lslu_destroy", "lslu_create_batched", "lslu_solve_batched",
            "lslu_adjoint", "lslu_solve_fixed_pivots", "lslu_create_shared",
            "lslu_solve_stopping", "lslu_solve_sampled", "lslu_set_spmv_shape",
-           "lslu_tune_spmv", "lslu_uq", "lslu_solve_optimal")
+           "lslu_tune_spmv", "lslu_uq", "lslu_solve_optimal", "lslu_spmv_config")
 
 _lib = None
 
@@ -81,6 +81,8 @@ def load(path: str | None = None):
     lib.lslu_solve_batched.restype = i32
     lib.lslu_solve_fixed_pivots.argtypes = [vp, vp, vp, i32, i32, f64, i32, vp, vp, vp, vp]
     lib.lslu_solve_fixed_pivots.restype = i32
+    lib.lslu_spmv_config.argtypes = [vp] + [ctypes.POINTER(i32)] * 4
+    lib.lslu_spmv_config.restype = i32
     lib.lslu_solve_optimal.argtypes = [vp, vp, i32, vp, i32, vp, vp]
     lib.lslu_solve_optimal.restype = i32
     lib.lslu_uq.argtypes = [vp, f64, f64, i32, vp, vp]
@@ -289,24 +291,31 @@ class Solver:
                                      _ptr(tot)))
         return dict(var_diag=d, var_sum=float(tot[0]))
 
-    SHAPES = ("16x2", "32x1", "16x1", "8x1", "8x2", "4x1")
+    SHAPES = ("16x2", "32x1", "16x1", "8x1", "8x2", "4x1",
+              "16x2/16-bit", "32x1/16-bit", "16x1/16-bit", "8x1/16-bit", "8x2/16-bit", "4x1/16-bit")
 
     def set_spmv_shape(self, shape_A, shape_AT=None):
         """Row shape of the sparse products (index into SHAPES)."""
         sa = int(shape_A)
         self._check(self.lib.lslu_set_spmv_shape(self.h, sa, sa if shape_AT is None else int(shape_AT)))
 
+    def spmv_config(self):
+        """Row shapes and column formats of A and A^T."""
+        v = [ctypes.c_int32(0) for _ in range(4)]
+        self._check(self.lib.lslu_spmv_config(self.h, *[ctypes.byref(t) for t in v]))
+        return dict(shape_A=self.SHAPES[v[0].value], shape_AT=self.SHAPES[v[1].value],
+                    compressed_A=bool(v[2].value), compressed_AT=bool(v[3].value))
+
     def tune_spmv(self, reps=5):
         """Time every row shape on A and A^T and keep the fastest; returns the
         chosen shapes and the per-shape times (microseconds)."""
         a = ctypes.c_int32(0)
         t = ctypes.c_int32(0)
-        us = np.zeros(12)
+        us = np.zeros(24)
         self._check(self.lib.lslu_tune_spmv(self.h, int(reps), ctypes.byref(a), ctypes.byref(t),
                                             _ptr(us)))
-        return dict(shape_A=a.value, shape_AT=t.value,
-                    us_A=dict(zip(self.SHAPES, us[:6].tolist())),
-                    us_AT=dict(zip(self.SHAPES, us[6:].tolist())))
+        keep = lambda v: {k: x for k, x in zip(self.SHAPES, v.tolist()) if x >= 0}
+        return dict(shape_A=a.value, shape_AT=t.value, us_A=keep(us[:12]), us_AT=keep(us[12:]))
 
     def profile(self, enable=True):
         self._check(self.lib.lslu_profile(self.h, int(enable)))

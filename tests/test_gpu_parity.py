@@ -176,14 +176,14 @@ def test_graph_replay_matches_direct_launches(ct32, monkeypatch):
     assert n == 80 and ms > 0
 
 
-@pytest.mark.parametrize("shape", range(6))
+@pytest.mark.parametrize("shape", range(12))
 def test_every_spmv_shape_keeps_f64_parity(ct32, shape):
     """All row shapes of the sparse products (the autotuner's choices) give the
     oracle's pivots and x within the FP64 tolerance."""
     K = 30
     ref = O.hybrid_lslu(ct32.scipy(), ct32.b, None, K, "gcv", histories=False)
     with lslu.from_problem(ct32, "f64", K) as s:
-        s.set_spmv_shape(shape, (shape + 1) % 6)
+        s.set_spmv_shape(shape, (shape + 1) % 12)
         r = s.solve(ct32.b, K, "gcv")
         r2 = s.solve(ct32.b, K, "gcv")
     assert np.array_equal(r["gp"], ref.gp) and np.array_equal(r["tp"], ref.tp)
