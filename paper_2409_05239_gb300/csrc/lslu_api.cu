@@ -138,7 +138,8 @@ lslu_status create_common(lslu_ctx* c, const int64_t* rp, const int32_t* ci, con
   CKC(dmalloc(&c->xin, m + n));
   CKC(dmalloc(&c->coef, (size_t)P * c->c_stride));
   CKC(cudaMalloc(&c->xp, (size_t)P * c->xp_stride * bb));
-  c->part_cap = c->num_sms * 16;
+  // one FP64 pivot partial per elimination block (one block per 64-row tile)
+  c->part_cap = (int)std::max<int64_t>((int64_t)c->num_sms * 16, (std::max(m, n) + 63) / 64 + 1);
   CKC(dmalloc(&c->part_val, c->part_cap));
   CKC(dmalloc(&c->part_idx, c->part_cap));
   CKC(dmalloc(&c->st, P));

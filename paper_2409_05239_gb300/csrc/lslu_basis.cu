@@ -179,27 +179,30 @@ __device__ void sampled_best(const PivotArgs& pa, const CT* v, double& best, int
   if (besti < 0) best = 0.0;
 }
 
-// Tiles of 32*VEC rows x all cnt basis columns: every warp of the block reads
-// the tile as 16-byte vectors (VEC rows per lane) and takes the columns
-// j = w, w+8, ...; the eight per-warp partial sums of a row are combined in
-// warp order and subtracted from x.
+// One warp per block and per tile of 32*VEC rows: lane l owns rows
+// r0 + l*VEC .. r0 + l*VEC + VEC-1 and eliminates them against all cnt basis
+// columns in order, v = fma(-c_j, b_j, v) for j = 0 .. cnt-1 (the sequential
+// order of Algorithm 4), reading each column as one 16-byte vector with
+// kUnrollJ columns in flight.  No block-level combination is needed, and the
+// small blocks spread evenly over the SMs.  The pivot search is a grid
+// reduction that does not depend on timing: FP32 keys combine with an
+// integer atomicMax; FP64 (single problem) candidates are reduced per block
+// and the partials in block order by the last block.
 template <typename XT, typename BT, typename CT>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(32)
     k_eliminate_argmax(const XT* x, const BT* __restrict__ B, int64_t ld, int cnt, int64_t rows,
                        CT* v, PivotArgs pa, double* __restrict__ part_val,
                        int32_t* __restrict__ part_idx, DevState* st) {
   constexpr bool kKey = sizeof(CT) == 4;
   constexpr int VEC = Vec16<BT>::N;
   constexpr int TILE = 32 * VEC;
-  constexpr int NW = kThreads / 32;
+  constexpr int UJ = 8;  // basis columns in flight per lane
   static_assert(kTile % TILE == 0, "problem tiles must hold whole elimination tiles");
   extern __shared__ unsigned char smem_raw[];
   CT* c = reinterpret_cast<CT*>(smem_raw);
-  __shared__ CT part[NW][TILE];
-  __shared__ unsigned long long kred[NW];
   __shared__ bool is_last;
   if (pa.nprob == 1 && st[0].status != LSLU_OK) return;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x;
   const int64_t ntiles = (rows + TILE - 1) / TILE;
   double best = 0.0;
   int besti = -1;
@@ -208,109 +211,88 @@ __global__ void __launch_bounds__(kThreads)
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int64_t r0 = t * TILE;
     const int p = tile_problem(pa.tile_prob, r0);
-    if (p != cur_p) {  // uniform over the block
-      __syncthreads();
-      for (int j = threadIdx.x; j < cnt; j += blockDim.x)
-        c[j] = (CT)pa.coef[(int64_t)p * pa.coef_stride + j];
-      __syncthreads();
+    if (p != cur_p) {
+      __syncwarp();
+      for (int j = lane; j < cnt; j += 32) c[j] = (CT)pa.coef[(int64_t)p * pa.coef_stride + j];
+      __syncwarp();
       cur_p = p;
     }
-    CT acc[VEC];
+    const int64_t i0 = r0 + lane * VEC;
+    CT val[VEC];
 #pragma unroll
-    for (int e = 0; e < VEC; ++e) acc[e] = 0;
-    const BT* bp = B + r0 + lane * VEC;
-    int j = warp;
-    for (; j + 7 * NW < cnt; j += 8 * NW) {
-      BT b[8][VEC];
+    for (int e = 0; e < VEC; ++e) val[e] = (i0 + e < rows) ? (CT)x[i0 + e] : (CT)0;
+    const BT* bp = B + i0;  // the basis has whole tiles of rows
+    int j = 0;
+    for (; j + UJ <= cnt; j += UJ) {
+      BT b[UJ][VEC];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) Vec16<BT>::load(bp + (int64_t)(j + u * NW) * ld, b[u]);
+      for (int u = 0; u < UJ; ++u) Vec16<BT>::load(bp + (int64_t)(j + u) * ld, b[u]);
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const CT cu = c[j + u * NW];
+      for (int u = 0; u < UJ; ++u) {
+        const CT cu = c[j + u];
 #pragma unroll
-        for (int e = 0; e < VEC; ++e) acc[e] = fma(cu, (CT)b[u][e], acc[e]);
+        for (int e = 0; e < VEC; ++e) val[e] = fma(-cu, (CT)b[u][e], val[e]);
       }
     }
-    for (; j < cnt; j += NW) {
+    for (; j < cnt; ++j) {
       BT b0[VEC];
       Vec16<BT>::load(bp + (int64_t)j * ld, b0);
 #pragma unroll
-      for (int e = 0; e < VEC; ++e) acc[e] = fma(c[j], (CT)b0[e], acc[e]);
+      for (int e = 0; e < VEC; ++e) val[e] = fma(-c[j], (CT)b0[e], val[e]);
     }
-#pragma unroll
-    for (int e = 0; e < VEC; ++e) part[warp][lane * VEC + e] = acc[e];
-    __syncthreads();
     unsigned long long tkey = 0;
-    if (threadIdx.x < TILE) {
-      const int64_t i = r0 + threadIdx.x;
-      if (i < rows) {
-        CT s = 0;
 #pragma unroll
-        for (int w = 0; w < NW; ++w) s += part[w][threadIdx.x];
-        CT val = 0;
-        if (!pa.used[i]) {
-          val = (CT)x[i] - s;
-          if constexpr (kKey) {
-            tkey = argkey(fabsf((float)val), (int)i);
-          } else {
-            double a = fabs((double)val);
-            if (isnan(a)) a = INFINITY;  // a NaN must win so that it is reported
-            if (better(a, (int)i, best, besti)) {
-              best = a;
-              besti = (int)i;
-            }
+    for (int e = 0; e < VEC; ++e) {
+      const int64_t i = i0 + e;
+      if (i >= rows) continue;
+      CT out = 0;
+      if (!pa.used[i]) {
+        out = val[e];
+        if constexpr (kKey) {
+          const unsigned long long kk = argkey(fabsf((float)out), (int)i);
+          tkey = kk > tkey ? kk : tkey;
+        } else {
+          double a = fabs((double)out);
+          if (isnan(a)) a = INFINITY;  // a NaN must win so that it is reported
+          if (better(a, (int)i, best, besti)) {
+            best = a;
+            besti = (int)i;
           }
         }
-        v[i] = val;
       }
+      v[i] = out;
     }
     if constexpr (kKey) {
+      tkey = warp_max_u64(tkey);
       if (pa.nprob == 1) {
         bkey = tkey > bkey ? tkey : bkey;
-      } else {  // batch: one atomicMax per tile on the tile's problem
-        tkey = warp_max_u64(tkey);
-        if (lane == 0) kred[warp] = tkey;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-          unsigned long long m = 0;
-          for (int w = 0; w < NW; ++w) m = kred[w] > m ? kred[w] : m;
-          if (m) atomicMax(&st[p].amax, m);
-        }
+      } else if (lane == 0 && tkey) {  // batch: one atomicMax per tile on its problem
+        atomicMax(&st[p].amax, tkey);
       }
     }
-    __syncthreads();
   }
   if constexpr (kKey) {
-    if (pa.nprob == 1) {
-      bkey = warp_max_u64(bkey);
-      if (lane == 0) kred[warp] = bkey;
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        unsigned long long m = 0;
-        for (int w = 0; w < NW; ++w) m = kred[w] > m ? kred[w] : m;
-        if (m) atomicMax(&st[0].amax, m);
-      }
-    }
-    if (threadIdx.x == 0) {
+    if (pa.nprob == 1 && lane == 0 && bkey) atomicMax(&st[0].amax, bkey);
+    if (lane == 0) {
       __threadfence();
       is_last = (atomicAdd(&st[0].ticket, 1) == (int)gridDim.x - 1);
     }
   } else {
-    block_argmax(best, besti);
-    if (threadIdx.x == 0) {
+    warp_argmax(best, besti);
+    if (lane == 0) {
       part_val[blockIdx.x] = best;
       part_idx[blockIdx.x] = besti;
       __threadfence();
       is_last = (atomicAdd(&st[0].ticket, 1) == (int)gridDim.x - 1);
     }
   }
-  __syncthreads();
+  __syncwarp();
   if (!is_last) return;
   __threadfence();
   if constexpr (kKey) {
-    if (threadIdx.x == 0) st[0].ticket = 0;
+    if (lane == 0) st[0].ticket = 0;
     const unsigned long long skey = pa.samples ? sampled_key<CT>(pa, v) : 0ull;
-    for (int p = threadIdx.x; p < pa.nprob; p += blockDim.x) {
+    for (int p = lane; p < pa.nprob; p += 32) {
       unsigned long long m = atomicExch(&st[p].amax, 0ull);
       if (p == 0 && (skey >> 32) != 0) m = skey;  // sampled pivot (full search as fallback)
       if (st[p].status != LSLU_OK) continue;
@@ -321,7 +303,7 @@ __global__ void __launch_bounds__(kThreads)
   } else {
     best = 0.0;
     besti = -1;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+    for (int b = lane; b < (int)gridDim.x; b += 32) {
       const double pv = __ldcg(part_val + b);
       const int pi = __ldcg(part_idx + b);
       if (better(pv, pi, best, besti)) {
@@ -329,7 +311,7 @@ __global__ void __launch_bounds__(kThreads)
         besti = pi;
       }
     }
-    block_argmax(best, besti);
+    warp_argmax(best, besti);
     if (pa.samples) {  // sampled pivot, the full search as fallback
       double sb;
       int si;
@@ -339,7 +321,7 @@ __global__ void __launch_bounds__(kThreads)
         besti = si;
       }
     }
-    if (threadIdx.x == 0) {
+    if (lane == 0) {
       st[0].ticket = 0;
       record_pivot<CT, BT>(pa, st[0], 0, besti, best, v);
     }
@@ -522,12 +504,13 @@ void launch_eliminate_argmax(const XT* x, const BT* B, int64_t ld, int cnt, int6
                              const PivotArgs& pa, double* part_val, int32_t* part_idx,
                              int part_cap, DevState* st, cudaStream_t s, int) {
   constexpr int TILE = 32 * Vec16<BT>::N;
-  int64_t g = (rows + TILE - 1) / TILE;
-  if (g > part_cap) g = part_cap;
+  int64_t g = (rows + TILE - 1) / TILE;  // one warp per tile
+  if (sizeof(CT) == 8 && g > part_cap) g = part_cap;  // FP64 partials: one per block
+  if (g > (1LL << 30)) g = 1LL << 30;
   if (g < 1) g = 1;
   const size_t sm = (size_t)(cnt > 0 ? cnt : 1) * sizeof(CT);
-  k_eliminate_argmax<XT, BT, CT><<<(unsigned)g, kThreads, sm, s>>>(x, B, ld, cnt, rows, v, pa,
-                                                                   part_val, part_idx, st);
+  k_eliminate_argmax<XT, BT, CT><<<(unsigned)g, 32, sm, s>>>(x, B, ld, cnt, rows, v, pa,
+                                                             part_val, part_idx, st);
 }
 
 template <typename BT>

@@ -197,7 +197,7 @@ def test_autotuner_picks_a_shape(ct32):
     ref = O.hybrid_lslu(A32, ct32.b, None, K, "gcv", histories=False)
     with lslu.from_problem(ct32, "f32", K) as s:
         t = s.tune_spmv(reps=3)
-        assert 0 <= t["shape_A"] < 6 and 0 <= t["shape_AT"] < 6
+        assert 0 <= t["shape_A"] < 12 and 0 <= t["shape_AT"] < 12
         assert t["us_A"][s.SHAPES[t["shape_A"]]] == min(t["us_A"].values())
         r = s.solve(ct32.b, K, "gcv")
     assert rel(r["x"], ref.x) <= 2e-4
