@@ -218,9 +218,35 @@ __global__ void __launch_bounds__(32)
       cur_p = p;
     }
     const int64_t i0 = r0 + lane * VEC;
+    const bool full = i0 + VEC <= rows;
     CT val[VEC];
+    if constexpr (sizeof(XT) == sizeof(CT) && VEC * sizeof(CT) == 16) {
+      if (full) {  // one 16-byte load of x (x may alias v: a coherent load)
+        if constexpr (sizeof(CT) == 4) {
+          const float4 w = *reinterpret_cast<const float4*>(x + i0);
+          val[0] = w.x; val[1] = w.y; val[2] = w.z; val[3] = w.w;
+        } else {
+          const double2 w = *reinterpret_cast<const double2*>(x + i0);
+          val[0] = w.x; val[1] = w.y;
+        }
+      } else {
 #pragma unroll
-    for (int e = 0; e < VEC; ++e) val[e] = (i0 + e < rows) ? (CT)x[i0 + e] : (CT)0;
+        for (int e = 0; e < VEC; ++e) val[e] = (i0 + e < rows) ? (CT)x[i0 + e] : (CT)0;
+      }
+    } else {
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) val[e] = (i0 + e < rows) ? (CT)x[i0 + e] : (CT)0;
+    }
+    // pivoted-row flags of the lane's rows (one 32-bit load when VEC == 4)
+    uint8_t usedf[VEC];
+    if (VEC == 4 && full) {
+      const uint32_t w = *reinterpret_cast<const uint32_t*>(pa.used + i0);
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) usedf[e] = (uint8_t)((w >> (8 * e)) & 0xffu);
+    } else {
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) usedf[e] = (i0 + e < rows) ? pa.used[i0 + e] : (uint8_t)1;
+    }
     const BT* bp = B + i0;  // the basis has whole tiles of rows
     int j = 0;
     for (; j + UJ <= cnt; j += UJ) {
@@ -241,12 +267,14 @@ __global__ void __launch_bounds__(32)
       for (int e = 0; e < VEC; ++e) val[e] = fma(-c[j], (CT)b0[e], val[e]);
     }
     unsigned long long tkey = 0;
+    CT outv[VEC];
 #pragma unroll
     for (int e = 0; e < VEC; ++e) {
       const int64_t i = i0 + e;
+      outv[e] = 0;
       if (i >= rows) continue;
       CT out = 0;
-      if (!pa.used[i]) {
+      if (!usedf[e]) {
         out = val[e];
         if constexpr (kKey) {
           const unsigned long long kk = argkey(fabsf((float)out), (int)i);
@@ -260,7 +288,17 @@ __global__ void __launch_bounds__(32)
           }
         }
       }
-      v[i] = out;
+      outv[e] = out;
+    }
+    if (full && VEC * sizeof(CT) == 16) {
+      if constexpr (sizeof(CT) == 4)
+        *reinterpret_cast<float4*>(v + i0) = make_float4(outv[0], outv[1], outv[2], outv[3]);
+      else
+        *reinterpret_cast<double2*>(v + i0) = make_double2(outv[0], outv[1]);
+    } else {
+#pragma unroll
+      for (int e = 0; e < VEC; ++e)
+        if (i0 + e < rows) v[i0 + e] = outv[e];
     }
     if constexpr (kKey) {
       tkey = warp_max_u64(tkey);
@@ -392,14 +430,20 @@ __global__ void k_r0_argmin(const double* __restrict__ r0, int64_t rows, PivotAr
 template <typename CT, typename BT>
 __global__ void k_scale(const CT* __restrict__ v, BT* __restrict__ out, int64_t rows,
                         const DevState* st, int nprob, const int32_t* tile_prob) {
-  if (nprob == 1 && st[0].status != LSLU_OK) return;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < rows;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const DevState& s = st[tile_problem(tile_prob, i)];
-    if (s.status != LSLU_OK) continue;
-    const CT p = sizeof(CT) == 8 ? (CT)s.pivot : (CT)s.pivot_f;
-    out[i] = (BT)(v[i] / p);
-  }
+  // four consecutive rows per thread (one problem: kTile is a multiple of 4),
+  // the vector read issued before the dependent pivot read
+  const int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+  if (i0 >= rows) return;
+  const bool full = i0 + 4 <= rows;
+  CT a[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) a[e] = (full || i0 + e < rows) ? v[i0 + e] : (CT)0;
+  const DevState& s = st[tile_problem(tile_prob, i0)];
+  if (s.status != LSLU_OK) return;
+  const CT p = sizeof(CT) == 8 ? (CT)s.pivot : (CT)s.pivot_f;
+#pragma unroll
+  for (int e = 0; e < 4; ++e)
+    if (full || i0 + e < rows) out[i0 + e] = (BT)(a[e] / p);
 }
 
 __global__ void k_init_state(DevState* st, int nprob, int K) {
@@ -524,8 +568,9 @@ void launch_init_pivot(const double* r0, int64_t rows, const PivotArgs& pa, DevS
 template <typename CT, typename BT>
 void launch_scale(const CT* v, BT* out, int64_t rows, DevState* st, int nprob,
                   const int32_t* tile_prob, cudaStream_t s, int num_sms) {
-  k_scale<CT, BT><<<grid_for(rows, num_sms, 8), kThreads, 0, s>>>(v, out, rows, st, nprob,
-                                                                  tile_prob);
+  const int64_t g = (rows + 4 * kThreads - 1) / (4 * kThreads);
+  if (g < 1) return;
+  k_scale<CT, BT><<<(unsigned)g, kThreads, 0, s>>>(v, out, rows, st, nprob, tile_prob);
 }
 
 void launch_init_state(DevState* st, int nprob, int K, cudaStream_t s) {
