@@ -2,12 +2,17 @@
 
     python -m paper_2409_05239_gb300.solve_once --workload ct512 --K 300
     python -m paper_2409_05239_gb300.solve_once --batch 64 --K 150
+    python -m paper_2409_05239_gb300.solve_once --workload ct512 --K 2 --shapes all
 
 The first form builds one seeded problem of the named size (see tomo.CONFIGS)
 and solves it `--repeat` times; the second solves a batch of uneven problems
 (tomo.make_uneven_batch) through the batched entry points.  Meant for kernel
 profilers: with LSLU_NO_GRAPHS=1 in the environment every kernel is launched
-directly instead of from a captured CUDA graph.
+directly instead of from a captured CUDA graph.  `--shapes` repeats the
+single-problem solve once per named sparse-product shape (both directions set
+to it; "all" = every shape in lslu.Solver.SHAPES order), so that a profiler sees
+the products of every shape in one process: each solve launches 2 K products,
+A^T d_k then A l_k for k = 0..K-1.
 """
 from __future__ import annotations
 
@@ -27,6 +32,7 @@ def main(argv=None):
     ap.add_argument("--lam", type=float, default=0.0)
     ap.add_argument("--repeat", type=int, default=1)
     ap.add_argument("--batch", type=int, default=0, help="solve this many uneven problems")
+    ap.add_argument("--shapes", default="", help="comma-separated shape names, or 'all'")
     a = ap.parse_args(argv)
 
     import torch
@@ -53,17 +59,27 @@ def main(argv=None):
     else:
         P = tomo.make_config(a.workload)
         K = a.K or tomo.CONFIGS[a.workload]["K"]
+        names = list(lslu.Solver.SHAPES) if a.shapes == "all" else \
+            [t for t in a.shapes.split(",") if t]
         with lslu.from_problem(P, a.value_type, K) as s:
-            t0 = time.perf_counter()
-            for _ in range(a.repeat):
-                r = s.solve(P.b, K, a.rule, a.lam)
-            dt = (time.perf_counter() - t0) / a.repeat
+            runs = []
+            for name in names or [None]:
+                if name is not None:
+                    code = lslu.Solver.SHAPES.index(name)
+                    s.set_spmv_shape(code, code)
+                t0 = time.perf_counter()
+                for _ in range(a.repeat):
+                    r = s.solve(P.b, K, a.rule, a.lam)
+                runs.append({"shape": name, "status": r["status"],
+                             "seconds_per_solve": (time.perf_counter() - t0) / a.repeat})
             launches = s.last_launch_count()
         out = {"workload": a.workload, "m": P.m, "n": P.n, "nnz": P.nnz, "K": K,
                "k_done": r["k_done"], "status": r["status"], "launches": launches,
-               "seconds_per_solve": dt,
+               "seconds_per_solve": runs[-1]["seconds_per_solve"],
                "rel_err_x_true": float(np.linalg.norm(r["x"] - P.x_true) /
                                        np.linalg.norm(P.x_true))}
+        if names:
+            out["shapes"] = runs
     print(json.dumps(out))
 
 
