@@ -60,34 +60,50 @@ def dist_env():
     return rank, world, local
 
 
-# DRAM traffic of one k_spmv_pivots launch on the 512x512 FP32 workload
-# (dram__bytes_read.sum + dram__bytes_write.sum, average of the A^T and A
-# launches) from the ncu capture summarised in profiles/k_spmv_pivots_ct512.md.
-# It is reported only while the kernel's sources are the ones captured.
+# DRAM traffic of one k_spmv_pivots launch on the 512x512 FP32 workload per row
+# shape, (A l_k, A^T d_k) in bytes (dram__bytes_read.sum + dram__bytes_write.sum)
+# from the ncu capture summarised in profiles/spmv_traffic_by_shape_ct512.md.
+# It is reported only while the sparse-product sources are the ones captured.
 SPMV_TRAFFIC = {
-    "bytes_per_launch": 975.35e6,
-    "workload": "ct512", "value_type": "f32", "shape": "16x2", "compressed": False,
+    "workload": "ct512", "value_type": "f32",
+    "bytes": {
+        "16x2": (972.55e6, 974.04e6), "32x1": (971.90e6, 972.85e6),
+        "16x1": (977.98e6, 972.99e6), "8x1": (1004.50e6, 1019.51e6),
+        "8x2": (997.70e6, 985.02e6), "4x1": (1011.23e6, 1022.83e6),
+        "16x2/16-bit": (799.71e6, 795.76e6), "32x1/16-bit": (791.38e6, 790.75e6),
+        "16x1/16-bit": (803.37e6, 809.58e6), "8x1/16-bit": (851.96e6, 898.61e6),
+        "8x2/16-bit": (831.51e6, 830.30e6), "4x1/16-bit": (916.38e6, 896.30e6),
+    },
     "sources": {
         "paper_2409_05239_gb300/csrc/lslu_spmv.cu":
-            "fa5e99f64e75d91dc118258531dd67dc8a2918472b7f800b8be4f6e1be9e8528",
+            "45444dc1059d9be46caa13078c6aecedac425f47754cdbef4d3e537ff27aeef6",
+        "paper_2409_05239_gb300/csrc/lslu_spmv_impl.cuh":
+            "128cf64e6ba7a86a0d5c397821ed6e96ac6b466442093f6f081128d84dc24976",
+        "paper_2409_05239_gb300/csrc/lslu_spmv_shapes_a.cu":
+            "d1fa497a3a9ce3097928ce60e983850dfdd6c9e000f6e80efd0f6e93dd7e0af9",
+        "paper_2409_05239_gb300/csrc/lslu_spmv_shapes_b.cu":
+            "0e773294834ee47b18af1f88926ceff2d1210b793e4dcb2cf9260028db12f63a",
         "paper_2409_05239_gb300/csrc/lslu_internal.cuh":
-            "e3510d8e514cebba25942d52518923031eaceb97d1e47de184ba3a4341ae4df7",
+            "eedc92517e1eeda413a0b322ffc0558d88f0158039e261dafdf08f4ec871570d",
     },
 }
 
 
-def spmv_traffic(workload, value_type, shapes, compressed):
+def spmv_traffic(workload, value_type, shape_A, shape_AT):
+    """Measured DRAM bytes of one sparse product (average of the two directions)
+    for the tuned shapes, or None when no capture matches the current build."""
     import hashlib
 
     if workload != SPMV_TRAFFIC["workload"] or value_type != SPMV_TRAFFIC["value_type"]:
         return None
-    if set(shapes) != {SPMV_TRAFFIC["shape"]} or compressed != SPMV_TRAFFIC["compressed"]:
+    tab = SPMV_TRAFFIC["bytes"]
+    if shape_A not in tab or shape_AT not in tab:
         return None
     for rel, digest in SPMV_TRAFFIC["sources"].items():
         with open(os.path.join(ROOT, rel), "rb") as f:
             if hashlib.sha256(f.read()).hexdigest() != digest:
                 return None
-    return SPMV_TRAFFIC["bytes_per_launch"]
+    return 0.5 * (tab[shape_A][0] + tab[shape_AT][1])
 
 
 def spmv_bytes(P, value_type, cmp_A=False, cmp_AT=False):
@@ -587,10 +603,9 @@ def run_gpu(args):
                          "algorithmic_bytes_per_launch": sbytes, "launches": n_spmv,
                          "avg_launch_ms": avg_ms,
                          "traffic": spmv_traffic(args.workload, args.value_type,
-                                                 (cfg_sp["shape_A"], cfg_sp["shape_AT"]),
-                                                 cmp_A or cmp_AT),
-                         "traffic_source": "profiles/k_spmv_pivots_ct512.md (ncu dram bytes "
-                                           "per launch)"},
+                                                 cfg_sp["shape_A"], cfg_sp["shape_AT"]),
+                         "traffic_source": "profiles/spmv_traffic_by_shape_ct512.md (ncu dram "
+                                           "bytes per launch for the tuned shapes)"},
             "hbm_gbs_solve": total_bytes * args.steps * world / (ms_max / 1e3) / 1e9,
             "rel_err_x_true": rel_true,
             "e2e": {"value": e2e_value, "unit": "iter/s", "h2d_bytes_per_step": P.m * 8,
