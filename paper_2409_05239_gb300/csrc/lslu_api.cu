@@ -510,14 +510,14 @@ lslu_status solve_impl(Ctx* c, const double* db, const double* dx0, int K, int r
   if (c->proj_tstamp) {
     const unsigned long long* t = c->proj_tstamp;
     std::fprintf(stderr,
-                 "lslu projected k=%d: bidiag %.1f us, sturm grid %.1f us, newton+weights %.1f us, "
-                 "lambda %.1f us, lsqr %.1f us, Q %.1f us\n",
-                 K, (t[1] - t[0]) * 1e-3, (t[2] - t[1]) * 1e-3, (t[3] - t[2]) * 1e-3,
-                 (t[4] - t[3]) * 1e-3, (t[6] - t[5]) * 1e-3, (t[7] - t[6]) * 1e-3);
+                 "lslu projected k=%d: bidiag %.1f us, singular values + GCV grid %.1f us "
+                 "(with launch gaps), lambda %.1f us, lsqr %.1f us, Q %.1f us\n",
+                 K, (t[1] - t[0]) * 1e-3, (t[3] - t[1]) * 1e-3, (t[4] - t[3]) * 1e-3,
+                 (t[6] - t[5]) * 1e-3, (t[7] - t[6]) * 1e-3);
     std::fprintf(stderr,
-                 "  bidiag sections: norms %.1f, cluster syncs %.1f, right house+partials %.1f, "
-                 "right update + left house %.1f, left update %.1f us\n",
-                 t[8] * 1e-3, t[9] * 1e-3, t[10] * 1e-3, t[11] * 1e-3, t[12] * 1e-3);
+                 "  bidiag sections: partial products %.1f, cluster barrier %.1f, "
+                 "exchange + reflectors %.1f, column updates %.1f us\n",
+                 t[8] * 1e-3, t[9] * 1e-3, t[10] * 1e-3, t[11] * 1e-3);
   }
   return LSLU_OK;
 }

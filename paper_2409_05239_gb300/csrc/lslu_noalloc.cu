@@ -29,8 +29,8 @@ namespace {
 
 // Largest projected problem the array serves (columns of H).
 constexpr int kNoAllocMaxK = 256;
-// Work space in doubles: one projected-solve slot for k = 256 with a 16-CTA
-// cluster (about 138.6k doubles) plus lambda and residual outputs; 1.12 MB.
+// Work space in doubles: one projected-solve slot for k = 256 (about 133k
+// doubles) plus lambda and residual outputs; 1.12 MB.
 constexpr int64_t kNoAllocDoubles = 140000;
 
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];

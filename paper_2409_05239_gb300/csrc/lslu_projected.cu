@@ -1,31 +1,41 @@
 // Projected Tikhonov problem of Hybrid LSLU (Eq. TSP, Section 3.3), FP64.
 //
-// One thread-block cluster solves the problem for one (k+1) x k upper
-// Hessenberg H and beta:
-//   1. Householder bidiagonalisation H = P B Q^T with B lower bidiagonal
-//      ((k+1) x k: alpha_j on the diagonal, beta_{j+1} below it) and
-//      P e1 = e1 (each step first reflects row j from the right, then column
-//      j below the diagonal from the left, so no left reflector touches
-//      row 0).  Columns of H are dealt round robin to the CTAs of the cluster
-//      and stay in shared memory; partial sums travel through global memory
-//      between cluster barriers.
-//   2. Singular values of B = positive eigenvalues of the Golub-Kahan
-//      tridiagonal T (order 2k+1, zero diagonal, off-diagonals alpha_0,
-//      beta_1, alpha_1, ..., beta_k): Sturm counts on a geometric grid
-//      bracket each one, then Newton's method on det(T - theta I) with
-//      bisection safeguards refines it; one thread per singular value.
-//   3. c = beta U^T e1 (Eq. gcv2): since P e1 = e1, c_i^2 is 2 beta^2 times the
-//      squared first component of T's eigenvector for sigma_i, read off as
-//      the residue of e1^T (T - theta)^-1 e1 = det(T_{2:,2:} - theta) /
-//      det(T - theta); c_{k+1}^2 = beta^2 / ||u||^2 for the null vector u of B^T.
-//   4. lambda by the rule: none (0), fixed, GCV (Eq. gcv2) or weighted GCV
-//      with omega = (k+1)/m (Eq. wgcv), minimised on a 257-point log grid
-//      sigma_1 * 10^[-14, 2] and refined by 64 bisection steps on the sign of
-//      dG/d(lambda^2) between the neighbours of the best grid point.
-//   5. Projected residual ||beta e1 - H y|| = sqrt(sum f_i^2 c_i^2 +
-//      c_{k+1}^2) with f_i = lambda^2 / (sigma_i^2 + lambda^2).
-//   6. y = Q z with z = argmin ||beta e1 - B z||^2 + lambda^2 ||z||^2, by the
-//      Givens sweep for damped bidiagonal least squares and back substitution.
+// For one (k+1) x k upper Hessenberg H and beta (or one per batch entry, or
+// one per k of a history) four kernels run in sequence:
+//   1. k_bidiag, one thread-block cluster per problem: Householder
+//      bidiagonalisation H = P B Q^T with B lower bidiagonal ((k+1) x k:
+//      alpha_j on the diagonal, beta_{j+1} below it) and P e1 = e1 (each step
+//      first reflects row j from the right, then column j below the diagonal
+//      from the left, so no left reflector touches row 0).  Columns of H are
+//      dealt round robin to the CTAs and stay in shared memory.  The right
+//      reflector's product s = A w is formed before the reflector is known,
+//      s = A(:, j) + scale * A(:, j+1:) A(j, j+1:)^T, so one exchange per step
+//      carries both the row norm and s: every CTA publishes its partial
+//      products (and the owner of column j that column) in its own shared
+//      memory, and after one cluster barrier every CTA reads them all through
+//      distributed shared memory, sums them in a fixed order and computes both
+//      reflectors of the step itself.
+//   2. k_sigma, one warp per singular value over the whole GPU: the singular
+//      values of B are the positive eigenvalues of the Golub-Kahan tridiagonal
+//      T (order 2k+1, zero diagonal, off-diagonals alpha_0, beta_1, alpha_1,
+//      ..., beta_k).  Sturm counts at 32 points per round (one per lane,
+//      geometric spacing while the bracket spans more than an octave) shrink
+//      the bracket of sigma_i 33-fold per round.  c = beta U^T e1 (Eq. gcv2):
+//      since P e1 = e1, c_i^2 is 2 beta^2 times the squared first component of
+//      T's eigenvector for sigma_i, the residue of e1^T (T - theta)^-1 e1 =
+//      det(T_{2:,2:} - theta) / det(T - theta), with the leading and trailing
+//      minors evaluated by two lanes of the warp together; one more warp
+//      forms c_{k+1}^2 = beta^2 / ||u||^2 for the null vector u of B^T.
+//   3. k_gcv_grid (GCV rules only), one warp per point of the 257-point log
+//      grid sigma_1 * 10^[-14, 2] of lambda: the GCV function (Eq. gcv2), or
+//      weighted GCV with omega = (k+1)/m (Eq. wgcv).
+//   4. k_finish, one block per problem: lambda by the rule (none: 0, fixed, or
+//      the best grid point refined by 64 bisection steps on the sign of
+//      dG/d(lambda^2) between its neighbours), the projected residual
+//      ||beta e1 - H y|| = sqrt(sum f_i^2 c_i^2 + c_{k+1}^2) with
+//      f_i = lambda^2 / (sigma_i^2 + lambda^2), and y = Q z with
+//      z = argmin ||beta e1 - B z||^2 + lambda^2 ||z||^2 by the Givens sweep
+//      for damped bidiagonal least squares and back substitution.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
@@ -39,11 +49,20 @@ namespace lslu {
 
 namespace {
 
-constexpr int kT = 256;
-constexpr int kGrid = 257;        // lambda grid points
-constexpr int kSturmGrid = 2048;  // geometric grid that brackets the singular values
+constexpr int kT = 256;   // threads of the one-block-per-problem kernels
+constexpr int kTB = 128;  // threads of a bidiagonalisation CTA: one warp per SM sub-partition,
+                          // whose FP64 pipe is the scarce resource
+constexpr int kWB = 4;    // warps per block of the warp-per-item kernels
+constexpr int kMaxCluster = 16;
+constexpr int kGrid = 257;  // lambda grid points
 constexpr double kEps = 2.220446049250313e-16;
 constexpr size_t kSmemCap = 200 * 1024;
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
 
 __device__ double block_sum(double v, double* red) {
 #pragma unroll
@@ -169,27 +188,43 @@ __device__ int sturm(const double* t2, int n, double theta, double& p, double& d
   return cnt;
 }
 
-// det(T_{2:n,2:n} - theta I) by the trailing-minor recurrence, scaled by 2^-exp2.
-__device__ double trailing_det(const double* t2, int n, double theta, int& exp2) {
-  double r1 = 1.0, r0 = -theta;  // r_{n+1}, r_n
-  int e = 0;
-  int j = n - 1;
-  while (j >= 2) {
-    const int jend = max(2, j - 7);
-    for (; j >= jend; --j) {
-      const double rj = fma(-theta, r0, -t2[j] * r1);
-      r1 = r0;
-      r0 = rj;
+// Leading minors p_j = -theta p_{j-1} - t_{j-1}^2 p_{j-2} of det(T - theta I)
+// with their theta-derivative (trailing = false), or the trailing minors
+// r_j = -theta r_{j+1} - t_j^2 r_{j+2}, j = n-1 .. 2, of det(T_{2:n,2:n} -
+// theta I) (trailing = true; the derivative is then unused).  Both run the
+// same steps on different entries of t2, so two lanes of one warp evaluate
+// them together.  v and dv are scaled by 2^-e.
+__device__ void minors(const double* t2, int n, double theta, bool trailing, double& v,
+                       double& dv, int& e) {
+  double pm1 = 1.0, p0 = -theta, dm1 = 0.0, d0 = -1.0;
+  int ex = 0;
+  const int steps = trailing ? n - 2 : n - 1;
+  int m = 0;
+  while (m < n - 1) {
+    const int mend = min(n - 1, m + 8);
+    for (; m < mend; ++m) {
+      if (m < steps) {
+        const double tt = t2[trailing ? n - 1 - m : m + 1];
+        const double pj = fma(-theta, p0, -tt * pm1);
+        const double dj = fma(-theta, d0, fma(-tt, dm1, -p0));
+        pm1 = p0;
+        p0 = pj;
+        dm1 = d0;
+        d0 = dj;
+      }
     }
     int sc;
-    if (needs_rescale(r0, r1, sc)) {
-      r0 = ldexp(r0, sc);
-      r1 = ldexp(r1, sc);
-      e -= sc;
+    if (needs_rescale(p0, pm1, sc)) {
+      p0 = ldexp(p0, sc);
+      pm1 = ldexp(pm1, sc);
+      d0 = ldexp(d0, sc);
+      dm1 = ldexp(dm1, sc);
+      ex -= sc;
     }
   }
-  exp2 = e;
-  return r0;
+  v = p0;
+  dv = d0;
+  e = ex;
 }
 
 __device__ double gcv_G(const double* sig, const double* c2, int k, double lam, double omega) {
@@ -226,38 +261,26 @@ __device__ double gcv_slope(const double* sig, const double* c2, int k, double l
   return dN * Dn - 2.0 * N * dD;
 }
 
-// Global work space of one problem of size kk (all cross-CTA traffic).
+// Global work space of one problem of size kk.
 struct Slots {
-  double* part_s;  // CL x (kk+1) partial sums
-  double* part_n;  // CL partial norms
-  double* x0;      // leading entry of the current row
-  double* vl;      // kk+1 left reflector
-  double* taul;    // its tau
-  double* al;      // kk+1 alpha
-  double* be;      // kk+1 beta (be[0] unused)
-  double* taur;    // kk+1 right-reflector taus
-  double* sig;     // kk+1 singular values
-  double* c2;      // kk+1 squared weights
-  int* gcnt;       // kSturmGrid Sturm counts
-  double* gv;      // kGrid GCV values
-  double* Qs;      // kk x kk: right reflector j in row j (entries c >= j)
-  double* A;       // (kk+1) x kk slab when shared memory is too small
+  double* al;    // kk+1: alpha_j, the diagonal of B
+  double* be;    // kk+1: beta_j below it (be[0] unused)
+  double* taur;  // kk+1: right-reflector taus
+  double* sig;   // kk+1: singular values, largest first
+  double* c2;    // kk+1: c_i^2, then c_{k+1}^2
+  double* gv;    // kGrid+1: GCV function on the lambda grid
+  double* Qs;    // kk x kk: right reflector j in row j (entries c >= j)
+  double* A;     // (kk+1) x kk column slab when shared memory is too small
 };
 
-__device__ Slots carve(double* base, int kk, int CL) {
+__device__ Slots carve(double* base, int kk, int /*CL*/) {
   Slots s;
   double* p = base;
-  s.part_s = p; p += (int64_t)CL * (kk + 1);
-  s.part_n = p; p += CL;
-  s.x0 = p; p += 2;
-  s.vl = p; p += kk + 1;
-  s.taul = p; p += 2;
   s.al = p; p += kk + 1;
   s.be = p; p += kk + 1;
   s.taur = p; p += kk + 1;
   s.sig = p; p += kk + 1;
   s.c2 = p; p += kk + 1;
-  s.gcnt = reinterpret_cast<int*>(p); p += kSturmGrid / 2;
   s.gv = p; p += kGrid + 1;
   s.Qs = p; p += (int64_t)kk * kk;
   s.A = p;
@@ -272,47 +295,56 @@ __device__ __forceinline__ unsigned long long gtimer() {
   return t;
 }
 
-__global__ void __launch_bounds__(kT) k_projected(ProjArgs a, ProjWork w) {
+// Which problem a block works on, and its size (k = 0: nothing to solve).
+struct ProbInfo {
+  int p;          // batch entry (0 without a batch)
+  int kk;         // problem size before clamping to the iterations done
+  int k;          // columns of H solved
+  bool is_final;  // the problem of size k_last (the one that yields y)
+  double beta;
+};
+
+__device__ ProbInfo prob_info(const ProjArgs& a, int prob) {
+  ProbInfo r;
+  const bool batch = a.nbatch > 1;
+  r.p = batch ? prob : 0;
+  r.kk = batch ? a.k_last : a.k_first + prob;
+  const DevState* sp = a.st ? a.st + r.p : nullptr;
+  const int kdone = sp ? sp->k_done : a.k_last;
+  r.is_final = (r.kk == a.k_last);
+  r.k = r.is_final ? min(r.kk, kdone) : r.kk;
+  if (r.k <= 0 || (!r.is_final && r.kk > kdone)) r.k = 0;
+  r.beta = sp ? sp->beta : a.beta_val;
+  return r;
+}
+
+__device__ Slots slot_of(const ProjWork& w, const ProbInfo& pi) {
+  return carve(w.base + (w.packed ? w.offsets[pi.kk] : (int64_t)pi.p * w.slot_stride), pi.kk,
+               w.cluster);
+}
+
+// ---- 1. bidiagonalisation ---------------------------------------------------
+__global__ void __launch_bounds__(kTB) k_bidiag(ProjArgs a, ProjWork w) {
   extern __shared__ double smem[];
-  __shared__ double red[33];
-  __shared__ double red4[128];
+  __shared__ double red[kTB / 32];
   cg::cluster_group cluster = cg::this_cluster();
   const int CL = (int)cluster.num_blocks();
   const int rank = (int)cluster.block_rank();
   const int prob = blockIdx.x / CL;
-  const bool batch = a.nbatch > 1;   // one final problem per batch entry
-  const int p = batch ? prob : 0;
-  const int kk = batch ? a.k_last : a.k_first + prob;
-  const DevState* sp = a.st ? a.st + p : nullptr;
-  const int kdone = sp ? sp->k_done : a.k_last;
-  const bool is_final = (kk == a.k_last);
-  const int k = is_final ? min(kk, kdone) : kk;
-  double* lam_o = a.lam_out ? a.lam_out + (batch ? p : kk - 1) : nullptr;
-  double* res_o = a.res_out ? a.res_out + (batch ? p : kk - 1) : nullptr;
-  double* tr_o = a.tr_out ? a.tr_out + (batch ? p : kk - 1) : nullptr;
-  if (k <= 0 || (!is_final && kk > kdone)) {
-    if (rank == 0 && threadIdx.x == 0) {
-      if (lam_o) *lam_o = 0.0;
-      if (res_o) *res_o = 0.0;
-      if (tr_o) *tr_o = 0.0;
-    }
-    return;  // the whole cluster leaves: no barrier is left waiting
-  }
-  const double beta = sp ? sp->beta : a.beta_val;
-  const double* Hp = a.H + (int64_t)p * a.strideH;
-  double* yp = a.y ? a.y + (int64_t)p * a.ldy : nullptr;
-  Slots S = carve(w.base + (w.packed ? w.offsets[kk] : (int64_t)p * w.slot_stride), kk, CL);
+  const ProbInfo pi = prob_info(a, prob);
+  const int k = pi.k;
+  if (k == 0) return;  // every CTA of the cluster sees the same k: no barrier is left waiting
+  const Slots S = slot_of(w, pi);
+  const double* Hp = a.H + (int64_t)pi.p * a.strideH;
+  const int K1 = a.k_last + 1;
   const int64_t ld = k + 1;
-  const int kmax = a.k_last;
-  // shared layout: [al, be, sig, c2, vls : 5 x (kmax+1)] [t2 : 2 x (kmax+1)]
-  // [slab or scratch]
-  double* al = smem;
-  double* be = al + (kmax + 1);
-  double* sig = be + (kmax + 1);
-  double* c2 = sig + (kmax + 1);
-  double* vls = c2 + (kmax + 1);
-  double* t2 = vls + (kmax + 1);
-  double* slab = t2 + 2 * (kmax + 1);
+  // shared layout: [Ps, cj, sv : K1 each] [xP, xC : 2 x K1 each] [slab]
+  double* Ps = smem;         // summed partial products, rows j..k
+  double* cj = Ps + K1;      // column j (from its owner), then the left reflector
+  double* sv = cj + K1;      // s = A w, rows j+1..k
+  double* xP = sv + K1;      // this CTA's partial products, by step parity
+  double* xC = xP + 2 * K1;  // the owner's copy of the next column, by step parity
+  double* slab = xC + 2 * K1;
   const bool in_smem = w.slab_in_smem != 0;
   auto col = [&](int c) -> double* {
     return in_smem ? slab + (int64_t)(c / CL) * ld : S.A + (int64_t)c * ld;
@@ -320,7 +352,7 @@ __global__ void __launch_bounds__(kT) k_projected(ProjArgs a, ProjWork w) {
   auto first_own = [&](int x) -> int { return x + ((rank - x) % CL + CL) % CL; };
   const int tid = threadIdx.x, nt = blockDim.x;
   const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
-  unsigned long long* ts = (a.tstamp && is_final && rank == 0 && tid == 0) ? a.tstamp : nullptr;
+  unsigned long long* ts = (a.tstamp && pi.is_final && rank == 0 && tid == 0) ? a.tstamp : nullptr;
   if (ts) ts[0] = gtimer();
 
   for (int c = rank; c < k; c += CL) {
@@ -329,8 +361,30 @@ __global__ void __launch_bounds__(kT) k_projected(ProjArgs a, ProjWork w) {
   }
   __syncthreads();
 
-  // ---- 1. bidiagonalisation ------------------------------------------------
-  unsigned long long tsec[6] = {0, 0, 0, 0, 0, 0}, tprev = ts ? gtimer() : 0;
+  // What step jn needs from this CTA: P_r = sum over own columns c > jn of
+  // A[r, c] A[jn, c] for r = jn..k (r = jn: the partial squared norm of row
+  // jn), and from the owner of column jn a copy of it.
+  auto publish = [&](int jn) {
+    double* P = xP + (jn & 1) * K1;
+    const int c0 = first_own(jn + 1);
+    for (int r = jn + tid; r <= k; r += nt) {
+      double s0 = 0.0, s1 = 0.0;
+      int c = c0;
+      for (; c + CL < k; c += 2 * CL) {
+        s0 = fma(col(c)[r], col(c)[jn], s0);
+        s1 = fma(col(c + CL)[r], col(c + CL)[jn], s1);
+      }
+      if (c < k) s0 = fma(col(c)[r], col(c)[jn], s0);
+      P[r] = s0 + s1;
+    }
+    if (jn % CL == rank) {
+      double* C = xC + (jn & 1) * K1;
+      const double* cp = col(jn);
+      for (int r = jn + tid; r <= k; r += nt) C[r] = cp[r];
+    }
+  };
+
+  unsigned long long tsec[4] = {0, 0, 0, 0}, tprev = ts ? gtimer() : 0;
   auto lap = [&](int q) {
     if (ts) {
       const unsigned long long now = gtimer();
@@ -338,261 +392,299 @@ __global__ void __launch_bounds__(kT) k_projected(ProjArgs a, ProjWork w) {
       tprev = now;
     }
   };
+  publish(0);
   for (int j = 0; j < k; ++j) {
-    // right reflector on row j, columns j..k-1
-    if (tid == 0) {
-      double ss = 0.0;
-      for (int c = first_own(j + 1); c < k; c += CL) {
-        const double x = col(c)[j];
-        ss = fma(x, x, ss);
-      }
-      __stcg(S.part_n + rank, ss);
-      if (j % CL == rank) __stcg(S.x0, col(j)[j]);
-      __threadfence();
-    }
+    const int par = j & 1;
     lap(0);
+    // Step j's partials are complete in every CTA.  The buffers of parity
+    // par are rewritten only in step j+2, after the next barrier, which no
+    // CTA passes before all have finished reading them below.
     cluster.sync();
     lap(1);
-    double tss = 0.0;
     {
-      double pv[16];
+      const double* oc = cluster.map_shared_rank(xC + par * K1, j % CL);
+      for (int r = j + tid; r <= k; r += nt) {
+        double pv[kMaxCluster];
 #pragma unroll
-      for (int q = 0; q < 16; ++q) pv[q] = q < CL ? ldg_cg(S.part_n + q) : 0.0;
-      for (int q = 0; q < CL; ++q) tss += pv[q];
+        for (int q = 0; q < kMaxCluster; ++q)
+          pv[q] = q < CL ? *cluster.map_shared_rank(xP + par * K1 + r, q) : 0.0;
+#pragma unroll
+        for (int h = kMaxCluster / 2; h >= 1; h >>= 1)  // fixed pairwise order
+#pragma unroll
+          for (int q = 0; q < h; ++q) pv[q] += pv[q + h];
+        Ps[r] = pv[0];
+        cj[r] = oc[r];
+      }
     }
-    const double x0r = ldg_cg(S.x0);
+    __syncthreads();
+    // right reflector on row j (w_j = 1, w_c = sc A[j, c] for c > j), computed
+    // by every thread from the same values
     double taur, bh, sc;
-    house(x0r, tss, taur, bh, sc);
-    if (tid == 0) {
-      for (int c = first_own(j); c < k; c += CL) {
-        const double wc = (c == j) ? 1.0 : col(c)[j] * sc;
-        col(c)[j] = wc;
-        __stcg(S.Qs + (int64_t)j * k + c, wc);
-      }
-      if (rank == 0) {
-        S.al[j] = bh;
-        S.taur[j] = taur;
-      }
-    }
-    __syncthreads();
-    // partial s_r = sum_{own c >= j} A[r, c] w_c, r = j+1..k
-    const int c0 = first_own(j);
+    house(cj[j], Ps[j], taur, bh, sc);
+    // s_r = sum_c A[r, c] w_c and column j after the right reflector, rows j+1..k
+    double s2 = 0.0;
     for (int r = j + 1 + tid; r <= k; r += nt) {
-      double s0 = 0.0, s1 = 0.0;
-      int c = c0;
-      for (; c + CL < k; c += 2 * CL) {
-        s0 = fma(col(c)[r], col(c)[j], s0);
-        s1 = fma(col(c + CL)[r], col(c + CL)[j], s1);
-      }
-      if (c < k) s0 = fma(col(c)[r], col(c)[j], s0);
-      __stcg(S.part_s + (int64_t)rank * ld + r, s0 + s1);
+      const double s = fma(sc, Ps[r], cj[r]);
+      sv[r] = s;
+      const double v = fma(-taur, s, cj[r]);
+      cj[r] = v;
+      if (r >= j + 2) s2 = fma(v, v, s2);
     }
-    __threadfence();
+    s2 = warp_sum_d(s2);
+    if (lane == 0) red[warp] = s2;
+    __syncthreads();
+    s2 = 0.0;
+    for (int q = 0; q < nw; ++q) s2 += red[q];
+    // left reflector on column j, rows j+1..k
+    double taul, bl, scl;
+    house(cj[j + 1], s2, taul, bl, scl);
+    __syncthreads();  // cj[j+1] and red are read by all before they change
+    for (int r = j + 1 + tid; r <= k; r += nt) cj[r] = (r == j + 1) ? 1.0 : cj[r] * scl;
+    if (rank == 0 && tid == 0) {
+      S.al[j] = bh;
+      S.be[j + 1] = bl;
+      S.taur[j] = taur;
+      S.Qs[(int64_t)j * k + j] = 1.0;
+    }
+    __syncthreads();
     lap(2);
-    cluster.sync();
-    lap(1);
-    if (taur != 0.0) {
-      for (int r = j + 1 + tid; r <= k; r += nt) {
-        double pv[16];
-#pragma unroll
-        for (int q = 0; q < 16; ++q) pv[q] = q < CL ? ldg_cg(S.part_s + (int64_t)q * ld + r) : 0.0;
-        double s = 0.0;
-        for (int q = 0; q < CL; ++q) s += pv[q];
-        const double ts = taur * s;
-        for (int c = c0; c < k; c += CL) col(c)[r] = fma(-ts, col(c)[j], col(c)[r]);
+    // own columns c > j, one warp per column: the right reflector, then the
+    // left one (t = v^T A[j+1:, c])
+    for (int c = first_own(j + 1) + warp * CL; c < k; c += CL * nw) {
+      double* cp = col(c);
+      const double wc = cp[j] * sc;
+      if (lane == 0) __stcg(S.Qs + (int64_t)j * k + c, wc);
+      const double g = taur * wc;
+      double t = 0.0;
+      for (int r = j + 1 + lane; r <= k; r += 32) {
+        const double v = fma(-g, sv[r], cp[r]);
+        cp[r] = v;
+        t = fma(cj[r], v, t);
       }
+      t = warp_sum_d(t);
+      const double h = taul * t;
+      if (h != 0.0)
+        for (int r = j + 1 + lane; r <= k; r += 32) cp[r] = fma(-h, cj[r], cp[r]);
     }
     __syncthreads();
-    // left reflector on column j, rows j+1..k (owner of column j)
-    if (j % CL == rank) {
-      double* cp = col(j);
-      double s2 = 0.0;
-      for (int r = j + 2 + tid; r <= k; r += nt) s2 = fma(cp[r], cp[r], s2);
-      s2 = block_sum(s2, red);
-      double taul, bl, scl;
-      house(cp[j + 1], s2, taul, bl, scl);
-      for (int r = j + 1 + tid; r <= k; r += nt) __stcg(S.vl + r, (r == j + 1) ? 1.0 : cp[r] * scl);
-      if (tid == 0) {
-        __stcg(S.taul, taul);
-        S.be[j + 1] = bl;
-      }
-      __threadfence();
-    }
     lap(3);
-    cluster.sync();
-    lap(1);
-    const double taul = ldg_cg(S.taul);
-    if (taul != 0.0) {
-      for (int r = j + 1 + tid; r <= k; r += nt) vls[r] = ldg_cg(S.vl + r);
-      __syncthreads();
-      // own columns c > j, one warp per column: t = v^T A[j+1:, c]
-      for (int c = first_own(j + 1) + warp * CL; c < k; c += CL * nw) {
-        double* cp = col(c);
-        double t = 0.0;
-        for (int r = j + 1 + lane; r <= k; r += 32) t = fma(vls[r], cp[r], t);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-        const double tt = taul * t;
-        for (int r = j + 1 + lane; r <= k; r += 32) cp[r] = fma(-tt, vls[r], cp[r]);
-      }
-    }
-    __syncthreads();
-    lap(4);
+    if (j + 1 < k) publish(j + 1);
   }
-  if (ts)
-    for (int q = 0; q < 5; ++q) ts[8 + q] = tsec[q];
-  __threadfence();
+  // no CTA leaves while another may still read its shared memory
   cluster.sync();
+  if (ts) {
+    ts[1] = gtimer();
+    for (int q = 0; q < 4; ++q) ts[8 + q] = tsec[q];
+  }
+}
 
-  if (ts) ts[1] = gtimer();
-  // ---- 2./3. singular values and weights -----------------------------------
-  for (int i = tid; i <= k; i += nt) {
-    al[i] = i < k ? ldg_cg(S.al + i) : 0.0;
-    be[i] = i > 0 ? ldg_cg(S.be + i) : 0.0;
-  }
-  __syncthreads();
+// ---- 2. singular values and weights ----------------------------------------
+// Block (x, prob) serves sigma_i for i = x kWB + warp; warp i = k forms
+// c_{k+1}^2.  Shared: t2 (2 (kmax+1)), alpha and beta (kmax+1 each).
+__global__ void __launch_bounds__(kWB * 32) k_sigma(ProjArgs a, ProjWork w) {
+  extern __shared__ double sh[];
+  __shared__ unsigned long long gmax[kWB];
+  const ProbInfo pi = prob_info(a, blockIdx.y);
+  const int k = pi.k;
+  const int i0 = blockIdx.x * kWB;
+  if (k == 0 || i0 > k) return;
+  const Slots S = slot_of(w, pi);
+  const int K1 = a.k_last + 1;
+  double* t2 = sh;            // t2[j] = t_j^2, j = 1..2k
+  double* alv = t2 + 2 * K1;  // alpha_0..alpha_{k-1}
+  double* bev = alv + K1;     // beta_1..beta_k at 1..k
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int n = 2 * k + 1;
-  for (int i = tid; i < k; i += nt) {
-    t2[2 * i + 1] = al[i] * al[i];
-    t2[2 * i + 2] = be[i + 1] * be[i + 1];
+  // spectral bound of T: 2 max |t_j| (no eigenvalue of a zero-diagonal
+  // tridiagonal reaches it), the maximum taken on the bit patterns
+  unsigned long long mx = 0;
+  for (int i = tid; i < k; i += blockDim.x) {
+    const double al = ldg_cg(S.al + i), be = ldg_cg(S.be + i + 1);
+    alv[i] = al;
+    bev[i + 1] = be;
+    t2[2 * i + 1] = al * al;
+    t2[2 * i + 2] = be * be;
+    const unsigned long long ba = (unsigned long long)__double_as_longlong(al) & 0x7fffffffffffffffull;
+    const unsigned long long bb = (unsigned long long)__double_as_longlong(be) & 0x7fffffffffffffffull;
+    mx = max(mx, max(ba, bb));
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) gmax[warp] = mx;
   __syncthreads();
-  __shared__ double Gsh;
-  if (tid == 0) {  // Gershgorin bound of T
-    double gm = 0.0;
-    for (int i = 0; i < k; ++i) {
-      gm = fmax(gm, fabs(al[i]) + fabs(be[i + 1]));
-      if (i + 1 < k) gm = fmax(gm, fabs(be[i + 1]) + fabs(al[i + 1]));
-    }
-    gm = fmax(gm, fabs(al[0]));
-    gm = fmax(gm, fabs(be[k]));
-    Gsh = gm;
-  }
-  __syncthreads();
-  const double G = Gsh;
-  const int gthreads = CL * nt;
-  const int gid = rank * nt + tid;
-  // grid theta_g = G 2^(-60 + 60 g / (NG - 1)); gcnt = number of sigma below
-  for (int g = gid; g < kSturmGrid; g += gthreads) {
-    const double th = G * exp2(-60.0 + 60.0 * g / (kSturmGrid - 1));
-    double p, dp;
-    int e2;
-    __stcg(S.gcnt + g, sturm<false>(t2, n, th, p, dp, e2) - (k + 1));
-  }
-  __threadfence();
-  cluster.sync();
-  if (ts) ts[2] = gtimer();
-  // sigma_i for i = rank, rank + CL, ... : the FP64 work is spread over the cluster
-  for (int i = rank + CL * tid; i < k; i += CL * nt) {
-    const int target = k - 1 - i;  // sigma_i (i-th largest) has target sigmas below it
-    int glo = 0, ghi = kSturmGrid;  // first grid point with count > target (binary search)
-    while (glo < ghi) {
-      const int mid = (glo + ghi) >> 1;
-      if (__ldcg(S.gcnt + mid) <= target)
-        glo = mid + 1;
-      else
-        ghi = mid;
-    }
-    const int g = glo;
-    double lo = g > 0 ? G * exp2(-60.0 + 60.0 * (g - 1) / (kSturmGrid - 1)) : 0.0;
-    double hi = g < kSturmGrid ? G * exp2(-60.0 + 60.0 * g / (kSturmGrid - 1)) : 2.0 * G + 1.0;
-    int clo = g > 0 ? __ldcg(S.gcnt + g - 1) : 0;
-    int chi = g < kSturmGrid ? __ldcg(S.gcnt + g) : k;
-    double th = lo > 0.0 ? sqrt(lo * hi) : 0.5 * hi;
-    double p = 0.0, dp = 0.0, pth = -1.0;
-    int ep = 0;
-    for (int it = 0; it < 200; ++it) {
-      if (hi - lo <= 4.0 * kEps * hi) break;
-      const int cnt = sturm<true>(t2, n, th, p, dp, ep) - (k + 1);
-      pth = th;
-      if (cnt <= target) {
-        lo = th;
-        clo = cnt;
-      } else {
-        hi = th;
-        chi = cnt;
-      }
-      double nx;
-      if (chi - clo == 1 && dp != 0.0) {
-        nx = th - p / dp;  // Newton step on det(T - theta I)
-        if (fabs(nx - th) <= 4.0 * kEps * th) {  // converged (the step is rounding noise)
-          if (nx > lo && nx < hi) th = nx;
-          break;
+  for (int q = 0; q < kWB; ++q) mx = max(mx, gmax[q]);
+  const double G = 2.0 * __longlong_as_double((long long)mx);
+  const int i = i0 + warp;
+  if (i > k) return;
+  if (i == k) {  // null vector of B^T: u_{i+1} = -alpha_i u_i / beta_{i+1}, u_0 = 1
+    if (lane == 0) {
+      double u = 1.0, nrm2 = 1.0;
+      int e = 0;  // u and nrm2 carry the factors 2^-e/2 and 2^-e
+      for (int q = 0; q < k; ++q) {
+        if (bev[q + 1] == 0.0) break;
+        u = -alv[q] * u / bev[q + 1];
+        nrm2 = fma(u, u, nrm2);
+        if (nrm2 > 0x1p+600) {
+          u = ldexp(u, -300);
+          nrm2 = ldexp(nrm2, -600);
+          e += 600;
         }
-        if (!(nx > lo && nx < hi)) nx = lo > 0.0 ? sqrt(lo * hi) : 0.5 * hi;
-      } else {
-        nx = (lo > 0.0 && hi / lo > 4.0) ? sqrt(lo * hi) : 0.5 * (lo + hi);
       }
-      th = nx;
+      __stcg(S.c2 + k, ldexp(pi.beta * pi.beta / nrm2, -e));
     }
-    // weight: first component^2 of T's eigenvector = -det(T_{2:,2:} - th) / det'(T - th);
-    // the derivative of the last Newton evaluation is reused when it was taken
-    // at (numerically) the same theta
-    if (!(fabs(pth - th) <= 1e-10 * th)) sturm<true>(t2, n, th, p, dp, ep);
-    int eq;
-    const double q = trailing_det(t2, n, th, eq);
-    double wgt = (dp != 0.0) ? ldexp(-q / dp, eq - ep) : 0.0;
+    return;
+  }
+  // sigma_i, the i-th largest, has target = k-1-i singular values below it;
+  // the bracket keeps count(lo) <= target < count(hi), both counts evaluated
+  const int target = k - 1 - i;
+  double lo = 0.0, hi = G;
+  if (G > 0.0) {
+    const double tiny = G * 0x1p-200;  // below this a singular value is zero
+    const double f = (double)(lane + 1) * (1.0 / 33.0);
+    for (int round = 0; round < 64; ++round) {
+      if (hi - lo <= 4.0 * kEps * hi || hi <= tiny) break;
+      double th;
+      if (lo == 0.0)
+        th = hi * exp2(-60.0 * (1.0 - f));  // geometric points down to hi 2^-60
+      else if (hi > 2.0 * lo)
+        th = lo * exp2(log2(hi / lo) * f);
+      else
+        th = fma(hi - lo, f, lo);
+      double p, dp;
+      int e2;
+      const int cnt = sturm<false>(t2, n, th, p, dp, e2) - (k + 1);
+      const unsigned above = __ballot_sync(0xffffffffu, cnt > target);
+      const int fl = above ? __ffs(above) - 1 : 32;  // first point above the target
+      const double nhi = __shfl_sync(0xffffffffu, th, fl < 32 ? fl : 0);
+      const double nlo = __shfl_sync(0xffffffffu, th, fl > 0 ? fl - 1 : 0);
+      const double hi2 = fl < 32 ? nhi : hi, lo2 = fl > 0 ? nlo : lo;
+      if (hi2 == hi && lo2 == lo) break;  // the points no longer split the bracket
+      lo = lo2;
+      hi = hi2;
+    }
+  }
+  const double th = lo > 0.0 ? 0.5 * (lo + hi) : 0.5 * hi;
+  // weight: first component^2 of T's eigenvector = -det(T_{2:,2:} - th) / det'(T - th)
+  double v, dv;
+  int ev;
+  minors(t2, n, th, lane == 1, v, dv, ev);
+  const double q = __shfl_sync(0xffffffffu, v, 1);
+  const int eq = __shfl_sync(0xffffffffu, ev, 1);
+  if (lane == 0) {
+    double wgt = (dv != 0.0) ? ldexp(-q / dv, eq - ev) : 0.0;
     if (!(wgt >= 0.0)) wgt = 0.0;
     __stcg(S.sig + i, th);
-    __stcg(S.c2 + i, 2.0 * beta * beta * wgt);
+    __stcg(S.c2 + i, 2.0 * pi.beta * pi.beta * wgt);
   }
-  if (rank == 0 && tid == 0) {
-    // null vector of B^T: u_{i+1} = -alpha_i u_i / beta_{i+1}, u_0 = 1
-    double u = 1.0, nrm2 = 1.0;
-    int e = 0;  // u and nrm2 carry the factors 2^-e/2 and 2^-e
-    for (int i = 0; i < k; ++i) {
-      if (be[i + 1] == 0.0) break;
-      u = -al[i] * u / be[i + 1];
-      nrm2 = fma(u, u, nrm2);
-      if (nrm2 > 0x1p+600) {
-        u = ldexp(u, -300);
-        nrm2 = ldexp(nrm2, -600);
-        e += 600;
-      }
+}
+
+// ---- 3. GCV function on the lambda grid: one warp per grid point ------------
+__global__ void __launch_bounds__(kWB * 32) k_gcv_grid(ProjArgs a, ProjWork w) {
+  const ProbInfo pi = prob_info(a, blockIdx.y);
+  const int k = pi.k;
+  const int t = blockIdx.x * kWB + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (k == 0 || t >= kGrid) return;
+  const Slots S = slot_of(w, pi);
+  const double s1 = ldg_cg(S.sig);
+  if (!(s1 > 0.0)) return;
+  const double mrows = a.mvec ? (double)a.mvec[pi.p] : (double)a.m;
+  const double omega = a.rule == LSLU_LAMBDA_WGCV ? (double)(k + 1) / mrows : 1.0;
+  const double lam = s1 * pow(10.0, -14.0 + 0.0625 * t);
+  const double L2 = lam * lam;
+  double num = 0.0, den = 0.0;
+  for (int i = lane; i < k; i += 32) {
+    const double s = ldg_cg(S.sig + i), s2 = s * s;
+    const double rw = 1.0 / (s2 + L2);
+    const double f = L2 * rw;
+    num = fma(f * f, ldg_cg(S.c2 + i), num);
+    den = fma(fma(1.0 - omega, s2, L2), rw, den);
+  }
+  num = warp_sum_d(num);
+  den = warp_sum_d(den);
+  if (lane == 0) {
+    num += ldg_cg(S.c2 + k);
+    den += 1.0;
+    __stcg(S.gv + t, (double)k * num / (den * den));
+  }
+}
+
+// ---- 4. lambda, residual and y: one block per problem -----------------------
+// Shared: sigma, c2, alpha, beta and four vectors of the sweep (kmax+1 each).
+__global__ void __launch_bounds__(kT) k_finish(ProjArgs a, ProjWork w) {
+  extern __shared__ double sm[];
+  __shared__ double red[33];
+  __shared__ double red4[128];
+  __shared__ int ibest;
+  const int prob = blockIdx.x;
+  const ProbInfo pi = prob_info(a, prob);
+  const int k = pi.k;
+  const bool batch = a.nbatch > 1;
+  const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, lane = tid & 31;
+  double* lam_o = a.lam_out ? a.lam_out + (batch ? pi.p : pi.kk - 1) : nullptr;
+  double* res_o = a.res_out ? a.res_out + (batch ? pi.p : pi.kk - 1) : nullptr;
+  double* tr_o = a.tr_out ? a.tr_out + (batch ? pi.p : pi.kk - 1) : nullptr;
+  if (k == 0) {
+    if (tid == 0) {
+      if (lam_o) *lam_o = 0.0;
+      if (res_o) *res_o = 0.0;
+      if (tr_o) *tr_o = 0.0;
     }
-    __stcg(S.c2 + k, ldexp(beta * beta / nrm2, -e));
+    return;
   }
-  __threadfence();
-  cluster.sync();
+  const Slots S = slot_of(w, pi);
+  const int K1 = a.k_last + 1;
+  double* sig = sm;
+  double* c2 = sig + K1;
+  double* al = c2 + K1;
+  double* be = al + K1;
+  double* z = be + K1;
+  double* rho = z + K1;
+  double* thv = rho + K1;
+  double* ph = thv + K1;
+  unsigned long long* ts = (a.tstamp && pi.is_final && tid == 0) ? a.tstamp : nullptr;
   if (ts) ts[3] = gtimer();
   for (int i = tid; i <= k; i += nt) {
     sig[i] = i < k ? ldg_cg(S.sig + i) : 0.0;
     c2[i] = ldg_cg(S.c2 + i);
+    al[i] = i < k ? ldg_cg(S.al + i) : 0.0;
+    be[i] = i > 0 ? ldg_cg(S.be + i) : 0.0;
   }
   __syncthreads();
   const bool gcv = (a.rule == LSLU_LAMBDA_GCV || a.rule == LSLU_LAMBDA_WGCV) && sig[0] > 0.0;
-  const double mrows = a.mvec ? (double)a.mvec[p] : (double)a.m;
+  const double mrows = a.mvec ? (double)a.mvec[pi.p] : (double)a.m;
   const double omega = a.rule == LSLU_LAMBDA_WGCV ? (double)(k + 1) / mrows : 1.0;
   const double s1 = sig[0];
-  // ---- 4. lambda: the grid is shared by the cluster, the refinement by CTA 0
-  double* Gv = S.gv;
-  if (gcv) {
-    for (int t = rank + CL * tid; t < kGrid; t += CL * nt)
-      __stcg(Gv + t, gcv_G(sig, c2, k, s1 * pow(10.0, -14.0 + 0.0625 * t), omega));
-  }
-  __threadfence();
-  cluster.sync();
-  if (rank != 0) return;
+  const double beta = pi.beta;
   double lam = 0.0;
-  __shared__ int ibest;
   if (a.rule == LSLU_LAMBDA_FIXED) {
     lam = a.lambda;
   } else if (gcv) {
-    if (tid == 0) {
-      int ib = 0;
-      double gb = __ldcg(Gv);
-      for (int t = 1; t < kGrid; ++t) {
-        const double gt = __ldcg(Gv + t);
-        if (gt < gb) {
-          gb = gt;
-          ib = t;
+    if (warp == 0) {  // best grid point, ties to the smaller lambda (G >= 0: bit order)
+      unsigned long long bk = ~0ull;
+      int bi = 0;
+      for (int t = lane; t < kGrid; t += 32) {
+        const double g = ldg_cg(S.gv + t);
+        const unsigned long long key =
+            (g == g) ? (unsigned long long)__double_as_longlong(g) : ~0ull;
+        if (key < bk) {
+          bk = key;
+          bi = t;
         }
       }
-      ibest = ib;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long ok = __shfl_xor_sync(0xffffffffu, bk, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ok < bk || (ok == bk && oi < bi)) {
+          bk = ok;
+          bi = oi;
+        }
+      }
+      if (lane == 0) ibest = bi;
     }
     __syncthreads();
     const int ib = ibest;
-    const double gib = __ldcg(Gv + ib);
+    const double gib = ldg_cg(S.gv + ib);
     lam = s1 * pow(10.0, -14.0 + 0.0625 * ib);
     if (ib > 0 && ib < kGrid - 1) {
       double lo = log(s1 * pow(10.0, -14.0 + 0.0625 * (ib - 1)));
@@ -612,8 +704,9 @@ __global__ void __launch_bounds__(kT) k_projected(ProjArgs a, ProjWork w) {
       }
     }
   }
+  if (ts) ts[4] = gtimer();
 
-  // ---- 5. projected residual (and the filter-factor trace of Eq. stop2) ----
+  // ---- projected residual (and the filter-factor trace of Eq. stop2) --------
   double rs = 0.0, tr = 0.0;
   if (lam != 0.0) {
     const double L2 = lam * lam;
@@ -634,15 +727,11 @@ __global__ void __launch_bounds__(kT) k_projected(ProjArgs a, ProjWork w) {
     for (int i = tid; i < k; i += nt) a.sig[(int64_t)prob * a.ldsig + i] = sig[i];
   if (a.cvec)
     for (int i = tid; i <= k; i += nt) a.cvec[(int64_t)prob * a.ldc + i] = sqrt(c2[i]);
-  if (!(is_final && a.want_y && yp)) return;
+  double* yp = a.y ? a.y + (int64_t)pi.p * a.ldy : nullptr;
+  if (!(pi.is_final && a.want_y && yp)) return;
 
   if (ts) ts[5] = gtimer();
-  // ---- 6. y = Q z ----------------------------------------------------------
-  // (the slab is no longer needed: its space holds z and the sweep results)
-  double* z = slab;
-  double* rho = z + (k + 1);
-  double* thv = rho + (k + 1);
-  double* ph = thv + (k + 1);
+  // ---- y = Q z ---------------------------------------------------------------
   if (tid == 0) {
     double rbar = al[0], phibar = beta;
     for (int j = 0; j < k; ++j) {
@@ -669,12 +758,13 @@ __global__ void __launch_bounds__(kT) k_projected(ProjArgs a, ProjWork w) {
   __syncthreads();
   if (ts) ts[6] = gtimer();
   for (int j = k - 1; j >= 0; --j) {  // z <- Q_j z, j = k-1 .. 0
-    const double tr = ldg_cg(S.taur + j);
-    if (tr == 0.0) continue;
+    const double trj = ldg_cg(S.taur + j);
+    if (trj == 0.0) continue;
     double s = 0.0;
     for (int c = j + tid; c < k; c += nt) s = fma(ldg_cg(S.Qs + (int64_t)j * k + c), z[c], s);
     s = block_sum(s, red);
-    for (int c = j + tid; c < k; c += nt) z[c] = fma(-tr * s, ldg_cg(S.Qs + (int64_t)j * k + c), z[c]);
+    for (int c = j + tid; c < k; c += nt)
+      z[c] = fma(-trj * s, ldg_cg(S.Qs + (int64_t)j * k + c), z[c]);
     __syncthreads();
   }
   for (int i = tid; i < k; i += nt) yp[i] = z[i];
@@ -682,7 +772,7 @@ __global__ void __launch_bounds__(kT) k_projected(ProjArgs a, ProjWork w) {
 }
 
 // ---- optimal lambda (needs x_true) ----------------------------------------
-// y(lam) = Q z(lam) from the factorisation H = P B Q^T that k_projected leaves
+// y(lam) = Q z(lam) from the factorisation H = P B Q^T that k_bidiag leaves
 // in its work slot (alpha, beta of B, the right reflectors), z(lam) by the
 // same Givens sweep as phase 6, and E(lam) - ||x_true||^2 = y^T G y - 2 g^T y
 // with G = L^T L (k x k) and g = L^T x_true.  sm holds 4 (k+1) doubles.
@@ -809,21 +899,22 @@ __global__ void __launch_bounds__(kT) k_opt_refine(ProjWork w, int K, const DevS
 
 }  // namespace
 
-int64_t projected_slot_doubles(int kk, int CL) {
-  return (int64_t)CL * (kk + 1) + CL + 2 + (kk + 1) + 2 + 6 * (kk + 1) + kSturmGrid / 2 + kGrid + 1 +
-         (int64_t)kk * kk + (int64_t)(kk + 1) * kk + 64;
+int64_t projected_slot_doubles(int kk, int /*CL*/) {
+  return 5 * (int64_t)(kk + 1) + kGrid + 1 + (int64_t)kk * kk + (int64_t)(kk + 1) * kk + 64;
 }
 
 int projected_cluster_size() {
   static int cs = 0;
   if (cs) return cs;
-  cudaFuncSetAttribute(k_projected, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-  cudaFuncSetAttribute(k_projected, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
+  cudaFuncSetAttribute(k_bidiag, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  cudaFuncSetAttribute(k_bidiag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
+  cudaFuncSetAttribute(k_sigma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
+  cudaFuncSetAttribute(k_finish, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
   int best = 1;
-  for (int cand : {16, 8, 4, 2}) {
+  for (int cand : {kMaxCluster, 8, 4, 2}) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(cand, 1, 1);
-    cfg.blockDim = dim3(kT, 1, 1);
+    cfg.blockDim = dim3(kTB, 1, 1);
     cfg.dynamicSmemBytes = kSmemCap;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
@@ -833,7 +924,7 @@ int projected_cluster_size() {
     cfg.attrs = at;
     cfg.numAttrs = 1;
     int nclusters = 0;
-    if (cudaOccupancyMaxActiveClusters(&nclusters, k_projected, &cfg) == cudaSuccess &&
+    if (cudaOccupancyMaxActiveClusters(&nclusters, k_bidiag, &cfg) == cudaSuccess &&
         nclusters > 0) {
       best = cand;
       break;
@@ -845,26 +936,30 @@ int projected_cluster_size() {
 }
 
 cudaError_t launch_projected(const ProjArgs& a, ProjWork& w, cudaStream_t s) {
-  // one cluster per projected problem: every k of k_first..k_last (histories),
-  // or one final problem per batch entry
+  // one problem per k of k_first..k_last (histories), or one final problem
+  // per batch entry
   const bool batch = a.nbatch > 1;
   if (batch && (a.k_first != a.k_last || w.packed)) return cudaErrorInvalidValue;
   const int nprob = batch ? a.nbatch : a.k_last - a.k_first + 1;
   if (nprob <= 0) return cudaSuccess;
   if (!batch && nprob > 1 && !w.packed) return cudaErrorInvalidValue;
   const int CL = w.cluster;
+  if (CL < 1 || CL > kMaxCluster) return cudaErrorInvalidValue;
   const int kmax = a.k_last;
+  const size_t K1 = (size_t)kmax + 1;
   const int ncl = (kmax + CL - 1) / CL;
-  const size_t vecs = (size_t)7 * (kmax + 1) * sizeof(double);
-  const size_t slab = (size_t)ncl * (kmax + 1) * sizeof(double);
-  const size_t scratch = (size_t)4 * (kmax + 1) * sizeof(double);
+  const size_t vecs = 7 * K1 * sizeof(double);
+  const size_t slab = (size_t)ncl * K1 * sizeof(double);
   w.slab_in_smem = (vecs + slab <= kSmemCap) ? 1 : 0;
-  size_t dyn = vecs + (w.slab_in_smem ? (slab > scratch ? slab : scratch) : scratch);
-  if (dyn > kSmemCap) return cudaErrorInvalidValue;
+  const size_t dyn1 = vecs + (w.slab_in_smem ? slab : 0);
+  const size_t dyn2 = 4 * K1 * sizeof(double);
+  const size_t dyn4 = 8 * K1 * sizeof(double);
+  if (dyn1 > kSmemCap || dyn2 > kSmemCap || dyn4 > kSmemCap) return cudaErrorInvalidValue;
+  // 1. bidiagonalisation, one cluster per problem
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(nprob * CL), 1, 1);
-  cfg.blockDim = dim3(kT, 1, 1);
-  cfg.dynamicSmemBytes = dyn;
+  cfg.blockDim = dim3(kTB, 1, 1);
+  cfg.dynamicSmemBytes = dyn1;
   cfg.stream = s;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
@@ -873,7 +968,19 @@ cudaError_t launch_projected(const ProjArgs& a, ProjWork& w, cudaStream_t s) {
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_projected, a, w);
+  cudaError_t e = cudaLaunchKernelEx(&cfg, k_bidiag, a, w);
+  if (e != cudaSuccess) return e;
+  // 2. singular values and weights: k + 1 warps per problem
+  const dim3 g2((unsigned)((K1 + kWB - 1) / kWB), (unsigned)nprob);
+  k_sigma<<<g2, kWB * 32, dyn2, s>>>(a, w);
+  // 3. the GCV function on the lambda grid
+  if (a.rule == LSLU_LAMBDA_GCV || a.rule == LSLU_LAMBDA_WGCV) {
+    const dim3 g3((unsigned)((kGrid + kWB - 1) / kWB), (unsigned)nprob);
+    k_gcv_grid<<<g3, kWB * 32, 0, s>>>(a, w);
+  }
+  // 4. lambda, residual, y
+  k_finish<<<(unsigned)nprob, kT, dyn4, s>>>(a, w);
+  return cudaGetLastError();
 }
 
 }  // namespace lslu
