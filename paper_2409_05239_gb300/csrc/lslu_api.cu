@@ -518,6 +518,9 @@ lslu_status solve_impl(Ctx* c, const double* db, const double* dx0, int K, int r
                  "  bidiag sections: partial products %.1f, cluster barrier %.1f, "
                  "exchange + reflectors %.1f, column updates %.1f us\n",
                  t[8] * 1e-3, t[9] * 1e-3, t[10] * 1e-3, t[11] * 1e-3);
+    std::fprintf(stderr, "  singular values: multisection rounds max %llu, mean %.2f\n", t[13],
+                 K > 0 ? (double)t[14] / K : 0.0);
+    std::memset(c->proj_tstamp, 0, 16 * sizeof(unsigned long long));
   }
   return LSLU_OK;
 }

@@ -201,6 +201,8 @@ __global__ void __launch_bounds__(32)
   extern __shared__ unsigned char smem_raw[];
   CT* c = reinterpret_cast<CT*>(smem_raw);
   __shared__ bool is_last;
+  pdl_wait();  // x, the coefficients and the state come from the kernels before
+  pdl_trigger();
   if (pa.nprob == 1 && st[0].status != LSLU_OK) return;
   const int lane = threadIdx.x;
   const int64_t ntiles = (rows + TILE - 1) / TILE;
@@ -432,6 +434,8 @@ __global__ void k_scale(const CT* __restrict__ v, BT* __restrict__ out, int64_t 
                         const DevState* st, int nprob, const int32_t* tile_prob) {
   // four consecutive rows per thread (one problem: kTile is a multiple of 4),
   // the vector read issued before the dependent pivot read
+  pdl_wait();  // v and the pivot come from the elimination before
+  pdl_trigger();
   const int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
   if (i0 >= rows) return;
   const bool full = i0 + 4 <= rows;
@@ -553,8 +557,8 @@ void launch_eliminate_argmax(const XT* x, const BT* B, int64_t ld, int cnt, int6
   if (g > (1LL << 30)) g = 1LL << 30;
   if (g < 1) g = 1;
   const size_t sm = (size_t)(cnt > 0 ? cnt : 1) * sizeof(CT);
-  k_eliminate_argmax<XT, BT, CT><<<(unsigned)g, 32, sm, s>>>(x, B, ld, cnt, rows, v, pa,
-                                                             part_val, part_idx, st);
+  launch_pdl(k_eliminate_argmax<XT, BT, CT>, dim3((unsigned)g), dim3(32), sm, s, x, B, ld, cnt,
+             rows, v, pa, part_val, part_idx, st);
 }
 
 template <typename BT>
@@ -570,7 +574,8 @@ void launch_scale(const CT* v, BT* out, int64_t rows, DevState* st, int nprob,
                   const int32_t* tile_prob, cudaStream_t s, int num_sms) {
   const int64_t g = (rows + 4 * kThreads - 1) / (4 * kThreads);
   if (g < 1) return;
-  k_scale<CT, BT><<<(unsigned)g, kThreads, 0, s>>>(v, out, rows, st, nprob, tile_prob);
+  launch_pdl(k_scale<CT, BT>, dim3((unsigned)g), dim3(kThreads), 0, s, v, out, rows, st, nprob,
+             tile_prob);
 }
 
 void launch_init_state(DevState* st, int nprob, int K, cudaStream_t s) {

@@ -12,6 +12,33 @@
 
 namespace lslu {
 
+// Programmatic dependent launch.  A kernel started with launch_pdl may begin
+// while the previous kernel of its stream is still draining (this hides the
+// launch latency between the short kernels of the iteration).  Such a kernel
+// calls pdl_wait() before it touches anything an earlier kernel wrote or
+// reads, and pdl_trigger() only after that, so that its own successor cannot
+// start before every kernel ahead of it has completed.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 // Rows of the internal CSR start on a multiple of kRowAlign entries and are
 // padded to that length (pad entries repeat the row's last column with value
 // 0), so every row can be read with 16-byte vector loads.

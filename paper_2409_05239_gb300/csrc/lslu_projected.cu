@@ -53,10 +53,12 @@ constexpr int kT = 256;   // threads of the one-block-per-problem kernels
 constexpr int kTB = 128;  // threads of a bidiagonalisation CTA: one warp per SM sub-partition,
                           // whose FP64 pipe is the scarce resource
 constexpr int kWB = 4;    // warps per block of the warp-per-item kernels
+constexpr int kWS = 2;    // warps per block of the singular-value kernel
 constexpr int kMaxCluster = 16;
 constexpr int kGrid = 257;  // lambda grid points
 constexpr double kEps = 2.220446049250313e-16;
 constexpr size_t kSmemCap = 200 * 1024;
+constexpr size_t kSmemOnePerSm = 120 * 1024;  // more than half of an SM's shared memory
 
 __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
@@ -81,25 +83,35 @@ __device__ double block_sum(double v, double* red) {
   return red[32];
 }
 
-// Four block-wide sums at once (one pair of barriers).
-__device__ void block_sum4(double (&v)[4], double* red4) {
-#pragma unroll
-  for (int q = 0; q < 4; ++q)
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+// Four block-wide sums at once.  Within a warp the four values are first
+// reduce-scattered (lanes 0-15 keep the first two, then lanes with bit 3
+// clear keep one of those, ...), so a warp spends 6 FP64 adds instead of 20;
+// the warps' results meet in red4 (2 x 32 entries, alternating between
+// calls so that one barrier per call suffices).
+__device__ void block_sum4(double (&v)[4], double* red4, int& parity) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const bool up = lane & 16, up8 = lane & 8;
+  double a0 = up ? v[2] : v[0], a1 = up ? v[3] : v[1];
+  const double b0 = up ? v[0] : v[2], b1 = up ? v[1] : v[3];
+  a0 += __shfl_xor_sync(0xffffffffu, b0, 16);
+  a1 += __shfl_xor_sync(0xffffffffu, b1, 16);
+  double c = up8 ? a1 : a0;
+  c += __shfl_xor_sync(0xffffffffu, up8 ? a0 : a1, 8);
+  c += __shfl_xor_sync(0xffffffffu, c, 4);
+  c += __shfl_xor_sync(0xffffffffu, c, 2);
+  c += __shfl_xor_sync(0xffffffffu, c, 1);
+  // lane 8 q holds quantity q of this warp
+  double* r = red4 + parity * 32;
+  parity ^= 1;
+  if ((lane & 7) == 0) r[(lane >> 3) * 8 + warp] = c;
   __syncthreads();
-  if (lane == 0)
+  // lane 8 q + w (w < nw) reads quantity q of warp w; sum over the warps
+  double t = ((lane & 7) < nw) ? r[(lane >> 3) * 8 + (lane & 7)] : 0.0;
+  t += __shfl_xor_sync(0xffffffffu, t, 4);
+  t += __shfl_xor_sync(0xffffffffu, t, 2);
+  t += __shfl_xor_sync(0xffffffffu, t, 1);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) red4[q * 32 + w] = v[q];
-  __syncthreads();
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    double t = lane < nw ? red4[q * 32 + lane] : 0.0;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    v[q] = t;
-  }
+  for (int q = 0; q < 4; ++q) v[q] = __shfl_sync(0xffffffffu, t, 8 * q);
 }
 
 // Reflector I - tau v v^T (v0 = 1, v_rest = rest * scale) mapping
@@ -112,10 +124,19 @@ __device__ __forceinline__ void house(double x0, double ss, double& tau, double&
     scale = 0.0;
     return;
   }
-  const double nrm = sqrt(fma(x0, x0, ss));
-  bh = x0 >= 0.0 ? -nrm : nrm;
-  tau = (bh - x0) / bh;
-  scale = 1.0 / (x0 - bh);
+  // with q = x0^2 + ss and nrm = sqrt(q): bh = -sign(x0) nrm,
+  // tau = (bh - x0) / bh = (|x0| + nrm) / nrm and 1 / (x0 - bh) =
+  // sign(x0) / (|x0| + nrm); one rsqrt and one division (each costs about as
+  // much as seven dependent FP64 FMAs here, a sqrt ten)
+  const double q = fma(x0, x0, ss);
+  const double rn = rsqrt(q);
+  const double nrm = q * rn;
+  const double d = fabs(x0) + nrm;
+  const bool neg = x0 < 0.0;
+  bh = neg ? nrm : -nrm;
+  tau = d * rn;
+  const double id = 1.0 / d;
+  scale = neg ? -id : id;
 }
 
 // Squared off-diagonals t_j^2 of the Golub-Kahan tridiagonal T (1-based j,
@@ -150,41 +171,33 @@ __device__ __forceinline__ bool needs_rescale(double p0, double pm1, int& s) {
 // det(T - theta I), optionally with its theta-derivative.  Returns the number
 // of sign changes of p_0..p_n (= eigenvalues of T below theta); p, dp receive
 // the determinant and derivative scaled by 2^-exp2.
-template <bool kDeriv>
-__device__ int sturm(const double* t2, int n, double theta, double& p, double& dp, int& exp2) {
+// Number of eigenvalues of T below theta: sign changes along the leading
+// minors p_0 = 1, p_1 = -theta, p_j = -theta p_{j-1} - t_{j-1}^2 p_{j-2}.
+// The product -t_j^2 p_{j-1} of the next step does not depend on p_j; it is
+// issued right after p_j's FMA so that in-order issue does not stall on it
+// (t2[n] must be readable; its value is not used).
+__device__ int sturm_count(const double* t2, int n, double theta) {
   double pm1 = 1.0, p0 = -theta;
-  double dm1 = 0.0, d0 = -1.0;
   int cnt = (int)(__double_as_longlong(p0) < 0);
-  int e = 0;
+  double x = -t2[1] * pm1;
   int j = 2;
   while (j <= n) {
     const int jend = min(n, j + 7);
+#pragma unroll 4
     for (; j <= jend; ++j) {
-      const double tt = t2[j - 1];
-      const double pj = fma(-theta, p0, -tt * pm1);
-      if (kDeriv) {
-        const double dj = fma(-theta, d0, fma(-tt, dm1, -p0));
-        dm1 = d0;
-        d0 = dj;
-      }
+      const double pj = fma(-theta, p0, x);
+      x = -t2[j] * p0;
       cnt += sign_change(pj, p0);
       pm1 = p0;
       p0 = pj;
     }
     int sc;
-    if (needs_rescale(p0, pm1, sc)) {
+    if (needs_rescale(p0, pm1, sc)) {  // x is proportional to pm1
       p0 = ldexp(p0, sc);
       pm1 = ldexp(pm1, sc);
-      if (kDeriv) {
-        d0 = ldexp(d0, sc);
-        dm1 = ldexp(dm1, sc);
-      }
-      e -= sc;
+      x = ldexp(x, sc);
     }
   }
-  p = p0;
-  dp = d0;
-  exp2 = e;
   return cnt;
 }
 
@@ -196,69 +209,73 @@ __device__ int sturm(const double* t2, int n, double theta, double& p, double& d
 // them together.  v and dv are scaled by 2^-e.
 __device__ void minors(const double* t2, int n, double theta, bool trailing, double& v,
                        double& dv, int& e) {
+  // step m (m = 0 ..) uses tt_m = t2[m + 1] (leading) or t2[n - 1 - m]
+  // (trailing); the next step's products x = -tt p_{j-1} and
+  // z = -tt d_{j-1} - p_j are formed as soon as their inputs exist
   double pm1 = 1.0, p0 = -theta, dm1 = 0.0, d0 = -1.0;
   int ex = 0;
-  const int steps = trailing ? n - 2 : n - 1;
+  const int stride = trailing ? -1 : 1;
+  const double* tp = t2 + (trailing ? n - 1 : 1);
+  double x = -tp[0] * pm1;
+  double z = fma(-tp[0], dm1, -p0);
+  const int common = n - 2;  // steps both recurrences take
   int m = 0;
-  while (m < n - 1) {
-    const int mend = min(n - 1, m + 8);
+  while (m < common) {
+    const int mend = min(common, m + 8);
+#pragma unroll 2
     for (; m < mend; ++m) {
-      if (m < steps) {
-        const double tt = t2[trailing ? n - 1 - m : m + 1];
-        const double pj = fma(-theta, p0, -tt * pm1);
-        const double dj = fma(-theta, d0, fma(-tt, dm1, -p0));
-        pm1 = p0;
-        p0 = pj;
-        dm1 = d0;
-        d0 = dj;
-      }
+      const double pj = fma(-theta, p0, x);
+      const double dj = fma(-theta, d0, z);
+      const double tn = tp[(m + 1) * stride];
+      x = -tn * p0;
+      z = fma(-tn, d0, -pj);
+      pm1 = p0;
+      p0 = pj;
+      dm1 = d0;
+      d0 = dj;
     }
     int sc;
-    if (needs_rescale(p0, pm1, sc)) {
+    if (needs_rescale(p0, pm1, sc)) {  // x and z scale with the minors
       p0 = ldexp(p0, sc);
       pm1 = ldexp(pm1, sc);
       d0 = ldexp(d0, sc);
       dm1 = ldexp(dm1, sc);
+      x = ldexp(x, sc);
+      z = ldexp(z, sc);
       ex -= sc;
     }
+  }
+  if (!trailing) {  // the leading recurrence has one step more
+    const double pj = fma(-theta, p0, x);
+    d0 = fma(-theta, d0, z);
+    p0 = pj;
   }
   v = p0;
   dv = d0;
   e = ex;
 }
 
-__device__ double gcv_G(const double* sig, const double* c2, int k, double lam, double omega) {
-  const double L2 = lam * lam;
-  double num = 0.0, den = 1.0;
-  for (int i = 0; i < k; ++i) {
-    const double s2 = sig[i] * sig[i];
-    const double rw = 1.0 / (s2 + L2);
-    const double f = L2 * rw;
-    num = fma(f * f, c2[i], num);
-    den = fma(fma(1.0 - omega, s2, L2), rw, den);
-  }
-  num += c2[k];
-  return (double)k * num / (den * den);
-}
-
-// sign-carrying derivative of G with respect to mu = lambda^2: N' D - 2 N D'
-__device__ double gcv_slope(const double* sig, const double* c2, int k, double lam, double omega,
-                            double* red4) {
-  const double L2 = lam * lam;
+// The GCV function (Eqs. gcv2/wgcv) N / D^2 scaled by k and its sign-carrying
+// derivative with respect to mu = lambda^2, N' D - 2 N D', evaluated by the
+// whole block (sig2 = sigma_i^2).
+struct GcvSums {
+  double N, dN, D, dD;
+};
+__device__ GcvSums gcv_sums(const double* sig2, const double* c2, int k, double mu, double omega,
+                            double* red4, int& parity) {
   double v[4] = {0.0, 0.0, 0.0, 0.0};  // N, N', D - 1, D'/omega
   for (int i = threadIdx.x; i < k; i += blockDim.x) {
-    const double s2 = sig[i] * sig[i];
-    const double rw = 1.0 / (s2 + L2);
-    const double f = L2 * rw;
+    const double s2 = sig2[i];
+    const double rw = 1.0 / (s2 + mu);
+    const double f = mu * rw;
     const double dfdmu = s2 * rw * rw;
     v[0] = fma(f * f, c2[i], v[0]);
     v[1] = fma(2.0 * f * dfdmu, c2[i], v[1]);
-    v[2] = fma(fma(1.0 - omega, s2, L2), rw, v[2]);
+    v[2] = fma(fma(1.0 - omega, s2, mu), rw, v[2]);
     v[3] += dfdmu;
   }
-  block_sum4(v, red4);
-  const double N = v[0] + c2[k], dN = v[1], Dn = 1.0 + v[2], dD = omega * v[3];
-  return dN * Dn - 2.0 * N * dD;
+  block_sum4(v, red4, parity);
+  return {v[0] + c2[k], v[1], 1.0 + v[2], omega * v[3]};
 }
 
 // Global work space of one problem of size kk.
@@ -448,23 +465,48 @@ __global__ void __launch_bounds__(kTB) k_bidiag(ProjArgs a, ProjWork w) {
     }
     __syncthreads();
     lap(2);
-    // own columns c > j, one warp per column: the right reflector, then the
-    // left one (t = v^T A[j+1:, c])
-    for (int c = first_own(j + 1) + warp * CL; c < k; c += CL * nw) {
+    // own columns c > j, two per warp at a time: the right reflector, then the
+    // left one (t = v^T A[j+1:, c]); the two dots are reduced together
+    for (int c = first_own(j + 1) + warp * CL; c < k; c += 2 * CL * nw) {
+      const int c2 = c + CL * nw;
+      const bool two = c2 < k;
       double* cp = col(c);
-      const double wc = cp[j] * sc;
-      if (lane == 0) __stcg(S.Qs + (int64_t)j * k + c, wc);
-      const double g = taur * wc;
-      double t = 0.0;
-      for (int r = j + 1 + lane; r <= k; r += 32) {
-        const double v = fma(-g, sv[r], cp[r]);
-        cp[r] = v;
-        t = fma(cj[r], v, t);
+      double* cq = col(two ? c2 : c);
+      const double wc = cp[j] * sc, wq = two ? cq[j] * sc : 0.0;
+      if (lane == 0) {
+        __stcg(S.Qs + (int64_t)j * k + c, wc);
+        if (two) __stcg(S.Qs + (int64_t)j * k + c2, wq);
       }
-      t = warp_sum_d(t);
-      const double h = taul * t;
-      if (h != 0.0)
-        for (int r = j + 1 + lane; r <= k; r += 32) cp[r] = fma(-h, cj[r], cp[r]);
+      const double g = taur * wc, gq = taur * wq;
+      double t = 0.0, tq = 0.0;
+      for (int r = j + 1 + lane; r <= k; r += 32) {
+        const double sr = sv[r], vr = cj[r];
+        const double v = fma(-g, sr, cp[r]);
+        cp[r] = v;
+        t = fma(vr, v, t);
+        if (two) {
+          const double vq = fma(-gq, sr, cq[r]);
+          cq[r] = vq;
+          tq = fma(vr, vq, tq);
+        }
+      }
+      // lanes 0-15 finish t, lanes 16-31 tq
+      const bool hiL = lane & 16;
+      double u = hiL ? tq : t;
+      u += __shfl_xor_sync(0xffffffffu, hiL ? t : tq, 16);
+      u += __shfl_xor_sync(0xffffffffu, u, 8);
+      u += __shfl_xor_sync(0xffffffffu, u, 4);
+      u += __shfl_xor_sync(0xffffffffu, u, 2);
+      u += __shfl_xor_sync(0xffffffffu, u, 1);
+      t = __shfl_sync(0xffffffffu, u, 0);
+      tq = __shfl_sync(0xffffffffu, u, 16);
+      const double h = taul * t, hq = taul * tq;
+      if (h != 0.0 || hq != 0.0)
+        for (int r = j + 1 + lane; r <= k; r += 32) {
+          const double vr = cj[r];
+          cp[r] = fma(-h, vr, cp[r]);
+          if (two) cq[r] = fma(-hq, vr, cq[r]);
+        }
     }
     __syncthreads();
     lap(3);
@@ -479,14 +521,17 @@ __global__ void __launch_bounds__(kTB) k_bidiag(ProjArgs a, ProjWork w) {
 }
 
 // ---- 2. singular values and weights ----------------------------------------
-// Block (x, prob) serves sigma_i for i = x kWB + warp; warp i = k forms
-// c_{k+1}^2.  Shared: t2 (2 (kmax+1)), alpha and beta (kmax+1 each).
-__global__ void __launch_bounds__(kWB * 32) k_sigma(ProjArgs a, ProjWork w) {
+// Block (x, prob) serves sigma_i for i = x kWS + warp; warp i = k forms
+// c_{k+1}^2.  Shared: t2 (2 (kmax+1)), alpha and beta (kmax+1 each).  Each
+// warp is a chain of dependent FP64 operations: when the grid fits on the GPU
+// at once, the launcher asks for enough shared memory that every SM holds one
+// block, so no two warps share an FP64 pipe.
+__global__ void __launch_bounds__(kWS * 32) k_sigma(ProjArgs a, ProjWork w) {
   extern __shared__ double sh[];
-  __shared__ unsigned long long gmax[kWB];
+  __shared__ unsigned long long gmax[kWS];
   const ProbInfo pi = prob_info(a, blockIdx.y);
   const int k = pi.k;
-  const int i0 = blockIdx.x * kWB;
+  const int i0 = blockIdx.x * kWS;
   if (k == 0 || i0 > k) return;
   const Slots S = slot_of(w, pi);
   const int K1 = a.k_last + 1;
@@ -508,11 +553,12 @@ __global__ void __launch_bounds__(kWB * 32) k_sigma(ProjArgs a, ProjWork w) {
     const unsigned long long bb = (unsigned long long)__double_as_longlong(be) & 0x7fffffffffffffffull;
     mx = max(mx, max(ba, bb));
   }
+  if (tid == 0) t2[2 * k + 1] = 0.0;  // read (not used) by the last Sturm step
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   if (lane == 0) gmax[warp] = mx;
   __syncthreads();
-  for (int q = 0; q < kWB; ++q) mx = max(mx, gmax[q]);
+  for (int q = 0; q < kWS; ++q) mx = max(mx, gmax[q]);
   const double G = 2.0 * __longlong_as_double((long long)mx);
   const int i = i0 + warp;
   if (i > k) return;
@@ -538,10 +584,11 @@ __global__ void __launch_bounds__(kWB * 32) k_sigma(ProjArgs a, ProjWork w) {
   // the bracket keeps count(lo) <= target < count(hi), both counts evaluated
   const int target = k - 1 - i;
   double lo = 0.0, hi = G;
+  int rounds = 0;
   if (G > 0.0) {
     const double tiny = G * 0x1p-200;  // below this a singular value is zero
     const double f = (double)(lane + 1) * (1.0 / 33.0);
-    for (int round = 0; round < 64; ++round) {
+    for (; rounds < 64; ++rounds) {
       if (hi - lo <= 4.0 * kEps * hi || hi <= tiny) break;
       double th;
       if (lo == 0.0)
@@ -550,9 +597,7 @@ __global__ void __launch_bounds__(kWB * 32) k_sigma(ProjArgs a, ProjWork w) {
         th = lo * exp2(log2(hi / lo) * f);
       else
         th = fma(hi - lo, f, lo);
-      double p, dp;
-      int e2;
-      const int cnt = sturm<false>(t2, n, th, p, dp, e2) - (k + 1);
+      const int cnt = sturm_count(t2, n, th) - (k + 1);
       const unsigned above = __ballot_sync(0xffffffffu, cnt > target);
       const int fl = above ? __ffs(above) - 1 : 32;  // first point above the target
       const double nhi = __shfl_sync(0xffffffffu, th, fl < 32 ? fl : 0);
@@ -562,6 +607,10 @@ __global__ void __launch_bounds__(kWB * 32) k_sigma(ProjArgs a, ProjWork w) {
       lo = lo2;
       hi = hi2;
     }
+  }
+  if (a.tstamp && pi.is_final && lane == 0) {  // multisection rounds (timing mode)
+    atomicMax(a.tstamp + 13, (unsigned long long)rounds);
+    atomicAdd(a.tstamp + 14, (unsigned long long)rounds);
   }
   const double th = lo > 0.0 ? 0.5 * (lo + hi) : 0.5 * hi;
   // weight: first component^2 of T's eigenvector = -det(T_{2:,2:} - th) / det'(T - th)
@@ -609,11 +658,65 @@ __global__ void __launch_bounds__(kWB * 32) k_gcv_grid(ProjArgs a, ProjWork w) {
 }
 
 // ---- 4. lambda, residual and y: one block per problem -----------------------
-// Shared: sigma, c2, alpha, beta and four vectors of the sweep (kmax+1 each).
-__global__ void __launch_bounds__(kT) k_finish(ProjArgs a, ProjWork w) {
+constexpr int kTF = 128;
+constexpr int kQPer = (kMaxIter + kTF - 1) / kTF;
+
+
+// Shared: sigma^2, c2, alpha, beta and three vectors of the sweep (kmax+1 each).
+// y = Q z with Q = H_0 ... H_{k-1}: z <- (I - tau_j w_j w_j^T) z for
+// j = k-1 .. 0 (w_j in row j of Qs, entries c >= j).  Thread t owns entries
+// c = t + kTF e, e < NP, in registers; the row of step j-1 is loaded during
+// step j.
+template <int NP>
+__device__ void apply_q(const Slots& S, int k, const double* z, double* yp,
+                        double (*qred)[kTF / 32]) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  double zr[NP], qc[NP], qn[NP];
+#pragma unroll
+  for (int e = 0; e < NP; ++e) {
+    const int c = tid + kTF * e;
+    zr[e] = c < k ? z[c] : 0.0;
+    qn[e] = (c < k && c >= k - 1) ? ldg_cg(S.Qs + (int64_t)(k - 1) * k + c) : 0.0;
+  }
+  double taun = ldg_cg(S.taur + (k - 1));
+  for (int j = k - 1; j >= 0; --j) {
+    const double tj = taun;
+#pragma unroll
+    for (int e = 0; e < NP; ++e) qc[e] = qn[e];
+    if (j > 0) {
+      taun = ldg_cg(S.taur + (j - 1));
+#pragma unroll
+      for (int e = 0; e < NP; ++e) {
+        const int c = tid + kTF * e;
+        qn[e] = (c < k && c >= j - 1) ? ldg_cg(S.Qs + (int64_t)(j - 1) * k + c) : 0.0;
+      }
+    }
+    if (tj == 0.0) continue;  // the same for every thread
+    double s = 0.0;
+#pragma unroll
+    for (int e = 0; e < NP; ++e) s = fma(qc[e], zr[e], s);
+    s = warp_sum_d(s);
+    if (lane == 0) qred[j & 1][warp] = s;
+    __syncthreads();
+    s = 0.0;
+#pragma unroll
+    for (int q = 0; q < kTF / 32; ++q) s += qred[j & 1][q];
+    const double h = tj * s;
+#pragma unroll
+    for (int e = 0; e < NP; ++e) zr[e] = fma(-h, qc[e], zr[e]);
+  }
+#pragma unroll
+  for (int e = 0; e < NP; ++e) {
+    const int c = tid + kTF * e;
+    if (c < k) yp[c] = zr[e];
+  }
+}
+
+__global__ void __launch_bounds__(kTF) k_finish(ProjArgs a, ProjWork w) {
   extern __shared__ double sm[];
   __shared__ double red[33];
-  __shared__ double red4[128];
+  __shared__ double red4[64];
+  __shared__ double qred[2][kTF / 32];
   __shared__ int ibest;
   const int prob = blockIdx.x;
   const ProbInfo pi = prob_info(a, prob);
@@ -633,28 +736,32 @@ __global__ void __launch_bounds__(kT) k_finish(ProjArgs a, ProjWork w) {
   }
   const Slots S = slot_of(w, pi);
   const int K1 = a.k_last + 1;
-  double* sig = sm;
-  double* c2 = sig + K1;
+  double* sig2 = sm;
+  double* c2 = sig2 + K1;
   double* al = c2 + K1;
   double* be = al + K1;
-  double* z = be + K1;
-  double* rho = z + K1;
-  double* thv = rho + K1;
+  double* rinv = be + K1;
+  double* thv = rinv + K1;
   double* ph = thv + K1;
   unsigned long long* ts = (a.tstamp && pi.is_final && tid == 0) ? a.tstamp : nullptr;
   if (ts) ts[3] = gtimer();
+  const double s1 = ldg_cg(S.sig);
   for (int i = tid; i <= k; i += nt) {
-    sig[i] = i < k ? ldg_cg(S.sig + i) : 0.0;
+    if (i < k) {
+      const double sg = ldg_cg(S.sig + i);
+      sig2[i] = sg * sg;
+      if (a.sig) a.sig[(int64_t)prob * a.ldsig + i] = sg;
+    }
     c2[i] = ldg_cg(S.c2 + i);
     al[i] = i < k ? ldg_cg(S.al + i) : 0.0;
     be[i] = i > 0 ? ldg_cg(S.be + i) : 0.0;
   }
   __syncthreads();
-  const bool gcv = (a.rule == LSLU_LAMBDA_GCV || a.rule == LSLU_LAMBDA_WGCV) && sig[0] > 0.0;
+  const bool gcv = (a.rule == LSLU_LAMBDA_GCV || a.rule == LSLU_LAMBDA_WGCV) && s1 > 0.0;
   const double mrows = a.mvec ? (double)a.mvec[pi.p] : (double)a.m;
   const double omega = a.rule == LSLU_LAMBDA_WGCV ? (double)(k + 1) / mrows : 1.0;
-  const double s1 = sig[0];
   const double beta = pi.beta;
+  int par = 0;
   double lam = 0.0;
   if (a.rule == LSLU_LAMBDA_FIXED) {
     lam = a.lambda;
@@ -687,20 +794,27 @@ __global__ void __launch_bounds__(kT) k_finish(ProjArgs a, ProjWork w) {
     const double gib = ldg_cg(S.gv + ib);
     lam = s1 * pow(10.0, -14.0 + 0.0625 * ib);
     if (ib > 0 && ib < kGrid - 1) {
-      double lo = log(s1 * pow(10.0, -14.0 + 0.0625 * (ib - 1)));
-      double hi = log(s1 * pow(10.0, -14.0 + 0.0625 * (ib + 1)));
-      const double slo = gcv_slope(sig, c2, k, exp(lo), omega, red4);
-      const double shi = gcv_slope(sig, c2, k, exp(hi), omega, red4);
-      if (slo < 0.0 && shi > 0.0) {
+      // bisection in log(lambda) between the neighbours: the midpoint of
+      // log(lo) and log(hi) is log(sqrt(lo hi)), and mu = lambda^2 = lo hi
+      double lo = s1 * pow(10.0, -14.0 + 0.0625 * (ib - 1));
+      double hi = s1 * pow(10.0, -14.0 + 0.0625 * (ib + 1));
+      auto slope = [&](double mu) {
+        const GcvSums g = gcv_sums(sig2, c2, k, mu, omega, red4, par);
+        return g.dN * g.D - 2.0 * g.N * g.dD;
+      };
+      if (slope(lo * lo) < 0.0 && slope(hi * hi) > 0.0) {
         for (int it = 0; it < 64; ++it) {
-          const double mid = 0.5 * (lo + hi);
-          if (gcv_slope(sig, c2, k, exp(mid), omega, red4) < 0.0)
+          const double mu = lo * hi;
+          const double mid = sqrt(mu);
+          if (!(mid > lo && mid < hi)) break;  // the bracket cannot shrink further
+          if (slope(mu) < 0.0)
             lo = mid;
           else
             hi = mid;
         }
-        const double lb = exp(0.5 * (lo + hi));
-        if (!(gcv_G(sig, c2, k, lb, omega) > gib)) lam = lb;
+        const double mu = lo * hi;
+        const GcvSums g = gcv_sums(sig2, c2, k, mu, omega, red4, par);
+        if (!((double)k * g.N / (g.D * g.D) > gib)) lam = sqrt(mu);
       }
     }
   }
@@ -711,7 +825,7 @@ __global__ void __launch_bounds__(kT) k_finish(ProjArgs a, ProjWork w) {
   if (lam != 0.0) {
     const double L2 = lam * lam;
     for (int i = tid; i < k; i += nt) {
-      const double f = L2 / (sig[i] * sig[i] + L2);
+      const double f = L2 / (sig2[i] + L2);
       rs = fma(f * f, c2[i], rs);
       tr += f;
     }
@@ -723,51 +837,61 @@ __global__ void __launch_bounds__(kT) k_finish(ProjArgs a, ProjWork w) {
     if (res_o) *res_o = sqrt(rs + c2[k]);
     if (tr_o) *tr_o = tr;
   }
-  if (a.sig)
-    for (int i = tid; i < k; i += nt) a.sig[(int64_t)prob * a.ldsig + i] = sig[i];
   if (a.cvec)
     for (int i = tid; i <= k; i += nt) a.cvec[(int64_t)prob * a.ldc + i] = sqrt(c2[i]);
   double* yp = a.y ? a.y + (int64_t)pi.p * a.ldy : nullptr;
   if (!(pi.is_final && a.want_y && yp)) return;
 
   if (ts) ts[5] = gtimer();
-  // ---- y = Q z ---------------------------------------------------------------
+  // ---- z = argmin ||beta e1 - B z||^2 + lambda^2 ||z||^2 ---------------------
+  // Givens sweep on B / sigma_1 (rotations do not depend on the scale; the
+  // scaled entries cannot overflow when squared), one thread.
   if (tid == 0) {
-    double rbar = al[0], phibar = beta;
+    const double sc = s1 > 0.0 ? 1.0 / s1 : 1.0;
+    const double lm = lam * sc;
+    const double L2 = lm * lm;
+    double rbar = al[0] * sc, phibar = beta * sc;
     for (int j = 0; j < k; ++j) {
-      double rhat = rbar, phib = phibar;
-      if (lam != 0.0) {  // rotation that removes lambda-row j
-        const double r1 = hypot(rbar, lam);
-        phib = (rbar / r1) * phibar;
-        rhat = r1;
+      const double bj = be[j + 1] * sc;
+      const double q = fma(rbar, rbar, L2);  // r1^2 after removing lambda-row j
+      const double ir = rsqrt(fma(bj, bj, q));  // 1 / r after removing beta_{j+1}
+      double c1 = 1.0, r1 = rbar;  // lambda = 0: no first rotation
+      if (lm != 0.0) {
+        const double iq = rsqrt(q);
+        c1 = rbar * iq;
+        r1 = q * iq;
       }
-      const double bj = be[j + 1];  // rotation that removes beta_{j+1}
-      const double r = hypot(rhat, bj);
-      const double cs = rhat / r, sn = bj / r;
-      rho[j] = r;
+      const double cs = r1 * ir, sn = bj * ir;
+      const double phib = c1 * phibar;
+      rinv[j] = ir;
       ph[j] = cs * phib;
       phibar = sn * phib;
       if (j + 1 < k) {
-        thv[j] = sn * al[j + 1];
-        rbar = -cs * al[j + 1];
+        const double an = al[j + 1] * sc;
+        thv[j] = sn * an;
+        rbar = -cs * an;
       }
     }
-    z[k - 1] = ph[k - 1] / rho[k - 1];
-    for (int j = k - 2; j >= 0; --j) z[j] = (ph[j] - thv[j] * z[j + 1]) / rho[j];
+    // back substitution; z overwrites ph
+    ph[k - 1] *= rinv[k - 1];
+    for (int j = k - 2; j >= 0; --j) ph[j] = (ph[j] - thv[j] * ph[j + 1]) * rinv[j];
   }
   __syncthreads();
   if (ts) ts[6] = gtimer();
-  for (int j = k - 1; j >= 0; --j) {  // z <- Q_j z, j = k-1 .. 0
-    const double trj = ldg_cg(S.taur + j);
-    if (trj == 0.0) continue;
-    double s = 0.0;
-    for (int c = j + tid; c < k; c += nt) s = fma(ldg_cg(S.Qs + (int64_t)j * k + c), z[c], s);
-    s = block_sum(s, red);
-    for (int c = j + tid; c < k; c += nt)
-      z[c] = fma(-trj * s, ldg_cg(S.Qs + (int64_t)j * k + c), z[c]);
-    __syncthreads();
-  }
-  for (int i = tid; i < k; i += nt) yp[i] = z[i];
+  // ---- y = Q z ----------------------------------------------------------------
+  const int np = (k + kTF - 1) / kTF;
+  if (np <= 1)
+    apply_q<1>(S, k, ph, yp, qred);
+  else if (np <= 2)
+    apply_q<2>(S, k, ph, yp, qred);
+  else if (np <= 3)
+    apply_q<3>(S, k, ph, yp, qred);
+  else if (np <= 4)
+    apply_q<4>(S, k, ph, yp, qred);
+  else if (np <= 8)
+    apply_q<8>(S, k, ph, yp, qred);
+  else
+    apply_q<kQPer>(S, k, ph, yp, qred);
   if (ts) ts[7] = gtimer();
 }
 
@@ -903,9 +1027,16 @@ int64_t projected_slot_doubles(int kk, int /*CL*/) {
   return 5 * (int64_t)(kk + 1) + kGrid + 1 + (int64_t)kk * kk + (int64_t)(kk + 1) * kk + 64;
 }
 
+// SMs of the device the projected kernels were set up on
+static int g_num_sms = 0;
+
 int projected_cluster_size() {
   static int cs = 0;
   if (cs) return cs;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    g_num_sms = 0;
   cudaFuncSetAttribute(k_bidiag, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   cudaFuncSetAttribute(k_bidiag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
   cudaFuncSetAttribute(k_sigma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
@@ -953,7 +1084,7 @@ cudaError_t launch_projected(const ProjArgs& a, ProjWork& w, cudaStream_t s) {
   w.slab_in_smem = (vecs + slab <= kSmemCap) ? 1 : 0;
   const size_t dyn1 = vecs + (w.slab_in_smem ? slab : 0);
   const size_t dyn2 = 4 * K1 * sizeof(double);
-  const size_t dyn4 = 8 * K1 * sizeof(double);
+  const size_t dyn4 = 7 * K1 * sizeof(double);
   if (dyn1 > kSmemCap || dyn2 > kSmemCap || dyn4 > kSmemCap) return cudaErrorInvalidValue;
   // 1. bidiagonalisation, one cluster per problem
   cudaLaunchConfig_t cfg = {};
@@ -971,15 +1102,17 @@ cudaError_t launch_projected(const ProjArgs& a, ProjWork& w, cudaStream_t s) {
   cudaError_t e = cudaLaunchKernelEx(&cfg, k_bidiag, a, w);
   if (e != cudaSuccess) return e;
   // 2. singular values and weights: k + 1 warps per problem
-  const dim3 g2((unsigned)((K1 + kWB - 1) / kWB), (unsigned)nprob);
-  k_sigma<<<g2, kWB * 32, dyn2, s>>>(a, w);
+  const dim3 g2((unsigned)((K1 + kWS - 1) / kWS), (unsigned)nprob);
+  size_t sm2 = dyn2;
+  if ((int64_t)g2.x * g2.y <= g_num_sms && sm2 < kSmemOnePerSm) sm2 = kSmemOnePerSm;
+  k_sigma<<<g2, kWS * 32, sm2, s>>>(a, w);
   // 3. the GCV function on the lambda grid
   if (a.rule == LSLU_LAMBDA_GCV || a.rule == LSLU_LAMBDA_WGCV) {
     const dim3 g3((unsigned)((kGrid + kWB - 1) / kWB), (unsigned)nprob);
     k_gcv_grid<<<g3, kWB * 32, 0, s>>>(a, w);
   }
   // 4. lambda, residual, y
-  k_finish<<<(unsigned)nprob, kT, dyn4, s>>>(a, w);
+  k_finish<<<(unsigned)nprob, kTF, dyn4, s>>>(a, w);
   return cudaGetLastError();
 }
 

@@ -324,6 +324,8 @@ __global__ void __launch_bounds__(256, min_blocks<VT, CMP ? 2 * U : U>())
                   const ColIdx ci, const VT* __restrict__ val, const XT* __restrict__ x,
                   YT* __restrict__ y, PivotCoef pc) {
   constexpr int RPB = 256 / G;
+  pdl_wait();  // x and the pivot rows come from the kernels before
+  pdl_trigger();
   const int lane = threadIdx.x & 31;
   const int npiv_all = pc.npiv_blocks * pc.nprob;
   if ((int)blockIdx.x >= npiv_all) {  // streaming rows (all but the first npiv_all blocks)
@@ -368,13 +370,13 @@ void spmv_pivots_run(const DevCsr& A, const XT* x, YT* y, const PivotCoef& pc, c
   const VT* v = reinterpret_cast<const VT*>(A.val);
   if constexpr (MAYCMP) {
     if (A.compressed && A.use_cmp) {
-      k_spmv_pivots<VT, XT, YT, G, U, true><<<(unsigned)blocks, 256, 0, s>>>(
-          A.rows, A.row_ptr, A.row_len, ci, v, x, y, pc);
+      launch_pdl(k_spmv_pivots<VT, XT, YT, G, U, true>, dim3((unsigned)blocks), dim3(256), 0, s,
+                 A.rows, A.row_ptr, A.row_len, ci, v, x, y, pc);
       return;
     }
   }
-  k_spmv_pivots<VT, XT, YT, G, U, false><<<(unsigned)blocks, 256, 0, s>>>(
-      A.rows, A.row_ptr, A.row_len, ci, v, x, y, pc);
+  launch_pdl(k_spmv_pivots<VT, XT, YT, G, U, false>, dim3((unsigned)blocks), dim3(256), 0, s,
+             A.rows, A.row_ptr, A.row_len, ci, v, x, y, pc);
 }
 
 }  // namespace
