@@ -67,24 +67,31 @@ def dist_env():
 SPMV_TRAFFIC = {
     "workload": "ct512", "value_type": "f32",
     "bytes": {
-        "16x2": (972.55e6, 974.04e6), "32x1": (971.90e6, 972.85e6),
-        "16x1": (977.98e6, 972.99e6), "8x1": (1004.50e6, 1019.51e6),
-        "8x2": (997.70e6, 985.02e6), "4x1": (1011.23e6, 1022.83e6),
-        "16x2/16-bit": (799.71e6, 795.76e6), "32x1/16-bit": (791.38e6, 790.75e6),
-        "16x1/16-bit": (803.37e6, 809.58e6), "8x1/16-bit": (851.96e6, 898.61e6),
-        "8x2/16-bit": (831.51e6, 830.30e6), "4x1/16-bit": (916.38e6, 896.30e6),
+        "16x2": (972.43e6, 973.54e6), "32x1": (971.81e6, 972.33e6),
+        "16x1": (978.12e6, 972.49e6), "8x1": (1004.68e6, 1019.12e6),
+        "8x2": (997.67e6, 984.75e6), "4x1": (1011.22e6, 1022.51e6),
+        "16x2/16-bit": (800.28e6, 795.81e6), "32x1/16-bit": (791.60e6, 790.83e6),
+        "16x1/16-bit": (803.88e6, 809.85e6), "8x1/16-bit": (852.67e6, 899.91e6),
+        "8x2/16-bit": (831.89e6, 830.19e6), "4x1/16-bit": (916.85e6, 896.28e6),
+        "tma": (971.70e6, 972.85e6), "tma/16-bit": (790.32e6, 790.95e6),
+        "32x8e": (971.95e6, 972.31e6), "32x8e/16-bit": (791.27e6, 791.09e6),
+        "32x4e": (971.90e6, 972.31e6), "32x4e/16-bit": (793.77e6, 791.89e6),
     },
     "sources": {
         "paper_2409_05239_gb300/csrc/lslu_spmv.cu":
-            "45444dc1059d9be46caa13078c6aecedac425f47754cdbef4d3e537ff27aeef6",
+            "bbfeeeb759777f039867591502b4554c0625d9ea79b5be2f1cd9a18ff50889b5",
         "paper_2409_05239_gb300/csrc/lslu_spmv_impl.cuh":
-            "128cf64e6ba7a86a0d5c397821ed6e96ac6b466442093f6f081128d84dc24976",
+            "e618d799b704a719641bc6e6dbf0e35760f17eb2954ef42a4f8cba87f46cebba",
         "paper_2409_05239_gb300/csrc/lslu_spmv_shapes_a.cu":
             "d1fa497a3a9ce3097928ce60e983850dfdd6c9e000f6e80efd0f6e93dd7e0af9",
         "paper_2409_05239_gb300/csrc/lslu_spmv_shapes_b.cu":
             "0e773294834ee47b18af1f88926ceff2d1210b793e4dcb2cf9260028db12f63a",
+        "paper_2409_05239_gb300/csrc/lslu_spmv_shapes_c.cu":
+            "96910620ae56de115fcdea59e6c10dfb7408ff7c9610c8323ba713ab471e2a0f",
+        "paper_2409_05239_gb300/csrc/lslu_spmv_tma.cu":
+            "3258c2e4fb82c38ccf340c4f48253dc396e784b74b1ebbdd43ae8083ee84199c",
         "paper_2409_05239_gb300/csrc/lslu_internal.cuh":
-            "eedc92517e1eeda413a0b322ffc0558d88f0158039e261dafdf08f4ec871570d",
+            "cbaa9c90e2686d09dea05f7e8b030cb3d8dfd701abfc5bbdbcbf68a5f8cad44c",
     },
 }
 

@@ -1083,16 +1083,19 @@ extern "C" lslu_status lslu_set_spmv_shape(lslu_handle h, int32_t shape_A, int32
   Ctx* c = h;
   if (!c) return set_err(nullptr, LSLU_ERR_INVALID_ARG, "NULL handle");
   if (shape_A < 0 || shape_A >= kNumShapes || shape_AT < 0 || shape_AT >= kNumShapes)
-    return set_err(c, LSLU_ERR_INVALID_ARG, "shape must be in [0, 12)");
-  if ((shape_A >= kShapesPerFormat && !c->A.compressed) ||
-      (shape_AT >= kShapesPerFormat && !c->AT.compressed))
+    return set_err(c, LSLU_ERR_INVALID_ARG, "shape must be in [0, 18)");
+  if ((shape_cmp(shape_A) && !c->A.compressed) || (shape_cmp(shape_AT) && !c->AT.compressed))
     return set_err(c, LSLU_ERR_INVALID_ARG,
                    "16-bit offset shapes need a matrix whose 8-entry units span < 2^16 columns");
+  if ((shape_staged(shape_A) && !c->A.tma_ok) || (shape_staged(shape_AT) && !c->AT.tma_ok))
+    return set_err(c, LSLU_ERR_INVALID_ARG,
+                   "staged shapes need every row to fit a stage (2048 padded entries, "
+                   "1024 for FP64 values)");
   CK(cudaStreamSynchronize(c->stream));
   c->A.shape = shape_A;
   c->AT.shape = shape_AT;
-  c->A.use_cmp = shape_A >= kShapesPerFormat;
-  c->AT.use_cmp = shape_AT >= kShapesPerFormat;
+  c->A.use_cmp = shape_cmp(shape_A);
+  c->AT.use_cmp = shape_cmp(shape_AT);
   drop_graphs(c);  // captured solves hold the kernels of the old shapes
   return LSLU_OK;
 }
@@ -1119,12 +1122,23 @@ extern "C" lslu_status lslu_tune_spmv(lslu_handle h, int32_t reps, int32_t* shap
   // not change the time
   CK(cudaMemsetAsync(c->q, 0, (size_t)c->n * bb, s));
   CK(cudaMemsetAsync(c->u, 0, (size_t)c->m * bb, s));
-  std::vector<cudaEvent_t> ev(2 * reps + 1);
+  // in a solve every product follows an elimination that streams the basis
+  // through L2; a memset of twice the L2 size before each timed product
+  // leaves the cache in a comparable state
+  int l2 = 0;
+  CK(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, c->device));
+  const size_t flush_bytes = (size_t)std::max(l2, 1 << 20) * 2;
+  void* flush = nullptr;
+  if (cudaMalloc(&flush, flush_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return set_err(c, LSLU_ERR_OOM, "tuning: no room for the L2 flush buffer");
+  }
+  std::vector<cudaEvent_t> ev(4 * reps);
   for (auto& e : ev) CK(cudaEventCreate(&e));
   const int saved[2] = {c->A.shape, c->AT.shape};
   const int saved_cmp[2] = {c->A.use_cmp, c->AT.use_cmp};
   int best[2] = {saved[0], saved[1]};
-  float best_ms[2] = {0.f, 0.f};
+  float best_ms[2] = {0.f, 0.f}, def_ms[2] = {0.f, 0.f};
   bool have[2] = {false, false};
   auto run = [&](DevCsr& M, const void* x, void* y) {
     if (c->value_type == LSLU_F64)
@@ -1134,30 +1148,33 @@ extern "C" lslu_status lslu_tune_spmv(lslu_handle h, int32_t reps, int32_t* shap
   };
   lslu_status st = LSLU_OK;
   for (int sh = 0; sh < kNumShapes && st == LSLU_OK; ++sh) {
-    const bool cmp = sh >= kShapesPerFormat;
-    if (cmp && !(c->A.compressed && c->AT.compressed)) {
+    const bool cmp = shape_cmp(sh);
+    if ((cmp && !(c->A.compressed && c->AT.compressed)) ||
+        (shape_staged(sh) && !(c->A.tma_ok && c->AT.tma_ok))) {
       if (us) us[sh] = us[kNumShapes + sh] = -1.0;  // not available
       continue;
     }
     c->A.shape = c->AT.shape = sh;
     c->A.use_cmp = c->AT.use_cmp = cmp;
-    // A and A^T alternate, as in a solve, so that each launch finds the L2
-    // state the other matrix leaves behind
+    // A and A^T alternate, as in a solve; each timed launch follows an L2 flush
     run(c->A, c->q, c->u);
     run(c->AT, c->u, c->q);
-    cudaEventRecord(ev[0], s);
     for (int r = 0; r < reps; ++r) {
+      cudaMemsetAsync(flush, r & 1, flush_bytes, s);
+      cudaEventRecord(ev[4 * r], s);
       run(c->A, c->q, c->u);
-      cudaEventRecord(ev[2 * r + 1], s);
+      cudaEventRecord(ev[4 * r + 1], s);
+      cudaMemsetAsync(flush, r & 1, flush_bytes, s);
+      cudaEventRecord(ev[4 * r + 2], s);
       run(c->AT, c->u, c->q);
-      cudaEventRecord(ev[2 * r + 2], s);
+      cudaEventRecord(ev[4 * r + 3], s);
     }
-    cudaError_t e = cudaEventSynchronize(ev[2 * reps]);
+    cudaError_t e = cudaEventSynchronize(ev[4 * reps - 1]);
     float t[2] = {0.f, 0.f};
     for (int r = 0; r < reps && e == cudaSuccess; ++r) {
       float a = 0.f, b = 0.f;
-      e = cudaEventElapsedTime(&a, ev[2 * r], ev[2 * r + 1]);
-      if (e == cudaSuccess) e = cudaEventElapsedTime(&b, ev[2 * r + 1], ev[2 * r + 2]);
+      e = cudaEventElapsedTime(&a, ev[4 * r], ev[4 * r + 1]);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&b, ev[4 * r + 2], ev[4 * r + 3]);
       t[0] += a;
       t[1] += b;
     }
@@ -1166,6 +1183,7 @@ extern "C" lslu_status lslu_tune_spmv(lslu_handle h, int32_t reps, int32_t* shap
       break;
     }
     for (int w = 0; w < 2; ++w) {
+      if (sh == default_shape(c->value_type)) def_ms[w] = t[w];
       if (us) us[w * kNumShapes + sh] = 1e3 * t[w] / reps;
       if (!have[w] || t[w] < best_ms[w]) {
         best_ms[w] = t[w];
@@ -1175,6 +1193,17 @@ extern "C" lslu_status lslu_tune_spmv(lslu_handle h, int32_t reps, int32_t* shap
     }
   }
   for (auto& e : ev) cudaEventDestroy(e);
+  cudaFree(flush);
+  if (st == LSLU_OK && c->A.tma_err && c->AT.tma_err) {  // a staged product gave up waiting
+    int32_t bad[2] = {0, 0};
+    cudaError_t e = cudaMemcpy(&bad[0], c->A.tma_err, sizeof(int32_t), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(&bad[1], c->AT.tma_err, sizeof(int32_t), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess)
+      st = set_err(c, LSLU_ERR_CUDA, std::string("tuning: ") + cudaGetErrorString(e));
+    else if (bad[0] || bad[1])
+      st = set_err(c, LSLU_ERR_TIMEOUT, "tuning: a staged sparse product timed out");
+  }
   if (st != LSLU_OK) {
     c->A.shape = saved[0];
     c->AT.shape = saved[1];
@@ -1182,10 +1211,15 @@ extern "C" lslu_status lslu_tune_spmv(lslu_handle h, int32_t reps, int32_t* shap
     c->AT.use_cmp = saved_cmp[1];
     return st;
   }
+  // shapes within a few per cent of each other swap places from run to run:
+  // keep the default unless another is clearly faster
+  const int def = default_shape(c->value_type);
+  for (int w = 0; w < 2; ++w)
+    if (best[w] != def && def_ms[w] > 0.f && best_ms[w] > 0.97f * def_ms[w]) best[w] = def;
   c->A.shape = best[0];
   c->AT.shape = best[1];
-  c->A.use_cmp = best[0] >= kShapesPerFormat;
-  c->AT.use_cmp = best[1] >= kShapesPerFormat;
+  c->A.use_cmp = shape_cmp(best[0]);
+  c->AT.use_cmp = shape_cmp(best[1]);
   drop_graphs(c);
   if (shape_A) *shape_A = best[0];
   if (shape_AT) *shape_AT = best[1];

@@ -205,7 +205,10 @@ cudaError_t upload_padded(int64_t rows, int64_t cols, const std::vector<int64_t>
   out->nnz_padded = tot;
   size_t vbytes = vt == LSLU_F64 ? 8 : (vt == LSLU_F32 ? 4 : 2);
   cudaError_t e;
-  if ((e = cudaMalloc(&out->row_ptr, (rows + 1) * sizeof(int32_t))) != cudaSuccess) return e;
+  // row pointers readable up to a multiple of 4 entries (aligned bulk copies)
+  const int64_t nrp = (rows + 1 + 3) / 4 * 4;
+  prp.resize((size_t)nrp, (int32_t)tot);
+  if ((e = cudaMalloc(&out->row_ptr, nrp * sizeof(int32_t))) != cudaSuccess) return e;
   if ((e = cudaMalloc(&out->row_len, std::max<int64_t>(rows, 1) * sizeof(int32_t))) != cudaSuccess)
     return e;
   if ((e = cudaMalloc(&out->col, std::max<int64_t>(tot, kRowAlign) * sizeof(int32_t))) !=
@@ -213,9 +216,43 @@ cudaError_t upload_padded(int64_t rows, int64_t cols, const std::vector<int64_t>
     return e;
   if ((e = cudaMalloc(&out->val, std::max<int64_t>(tot, kRowAlign) * vbytes)) != cudaSuccess)
     return e;
-  if ((e = cudaMemcpyAsync(out->row_ptr, prp.data(), (rows + 1) * sizeof(int32_t),
+  if ((e = cudaMemcpyAsync(out->row_ptr, prp.data(), nrp * sizeof(int32_t),
                            cudaMemcpyHostToDevice, s)) != cudaSuccess)
     return e;
+  // stages of the staged shapes: whole rows, at most SE entries and
+  // kTmaStageRows rows each (unavailable if a row alone exceeds SE)
+  {
+    const int64_t SE = vt == LSLU_F64 ? kTmaStageEntriesF64 : kTmaStageEntries;
+    std::vector<int32_t> stg;
+    bool ok = rows > 0;
+    int64_t r = 0;
+    while (ok && r < rows) {
+      const int64_t e0 = prp[r];
+      int64_t r1 = r;
+      while (r1 < rows && r1 - r < kTmaStageRows && prp[r1 + 1] - e0 <= SE) ++r1;
+      if (r1 == r) ok = false;
+      stg.push_back((int32_t)r);
+      stg.push_back((int32_t)e0);
+      r = r1;
+    }
+    if (ok) {
+      stg.push_back((int32_t)rows);
+      stg.push_back((int32_t)tot);
+      out->tma_nstages = (int)(stg.size() / 2 - 1);
+      if ((e = cudaMalloc(&out->tma_stage, stg.size() * sizeof(int32_t))) != cudaSuccess) return e;
+      if ((e = cudaMemcpyAsync(out->tma_stage, stg.data(), stg.size() * sizeof(int32_t),
+                               cudaMemcpyHostToDevice, s)) != cudaSuccess)
+        return e;
+      if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;  // stg goes out of scope
+      int dev = 0, sms = 0;
+      if (cudaGetDevice(&dev) == cudaSuccess &&
+          cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+        out->tma_blocks = 2 * sms;  // two streaming blocks per SM
+      out->tma_ok = out->tma_blocks > 0;
+    }
+    if ((e = cudaMalloc(&out->tma_err, sizeof(int32_t))) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(out->tma_err, 0, sizeof(int32_t), s)) != cudaSuccess) return e;
+  }
   if (rows && (e = cudaMemcpyAsync(out->row_len, prl.data(), rows * sizeof(int32_t),
                                    cudaMemcpyHostToDevice, s)) != cudaSuccess)
     return e;
@@ -247,12 +284,15 @@ cudaError_t upload_padded(int64_t rows, int64_t cols, const std::vector<int64_t>
     }
   }
   if (fits) {
+    // unit bases readable up to a multiple of 4 units (aligned bulk copies)
+    const int64_t nub = (units + 3) / 4 * 4;
+    pb.resize((size_t)nub, 0);
     if ((e = cudaMalloc(&out->off, tot * sizeof(uint16_t))) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&out->ubase, units * sizeof(int32_t))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&out->ubase, nub * sizeof(int32_t))) != cudaSuccess) return e;
     if ((e = cudaMemcpyAsync(out->off, po.data(), tot * sizeof(uint16_t), cudaMemcpyHostToDevice,
                              s)) != cudaSuccess)
       return e;
-    if ((e = cudaMemcpyAsync(out->ubase, pb.data(), units * sizeof(int32_t),
+    if ((e = cudaMemcpyAsync(out->ubase, pb.data(), nub * sizeof(int32_t),
                              cudaMemcpyHostToDevice, s)) != cudaSuccess)
       return e;
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;  // po, pb go out of scope
@@ -313,6 +353,8 @@ void free_csr(DevCsr* c) {
   cudaFree(c->val);
   cudaFree(c->off);
   cudaFree(c->ubase);
+  cudaFree(c->tma_stage);
+  cudaFree(c->tma_err);
   *c = DevCsr();
 }
 

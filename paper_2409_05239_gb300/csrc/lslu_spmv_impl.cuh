@@ -213,6 +213,70 @@ __device__ __forceinline__ YT row_dot_len(int32_t start, int32_t len,
   return group_sum<G>(acc);
 }
 
+// Scalar stream loads (one entry per lane) without L1 allocation.
+__device__ __forceinline__ float ld_stream1(const float* p) {
+  float v;
+  asm volatile("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ double ld_stream1(const double* p) {
+  double v;
+  asm volatile("ld.global.nc.L1::no_allocate.f64 %0, [%1];" : "=d"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ float ld_stream1(const __nv_bfloat16* p) {
+  unsigned short h;
+  asm volatile("ld.global.nc.L1::no_allocate.u16 %0, [%1];" : "=h"(h) : "l"(p));
+  return __uint_as_float((uint32_t)h << 16);
+}
+__device__ __forceinline__ int32_t ld_stream1(const int32_t* p) {
+  int32_t v;
+  asm volatile("ld.global.nc.L1::no_allocate.s32 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ int32_t ld_stream1(const uint16_t* p) {
+  unsigned short h;
+  asm volatile("ld.global.nc.L1::no_allocate.u16 %0, [%1];" : "=h"(h) : "l"(p));
+  return (int32_t)h;
+}
+
+// Row dot with the 32 lanes of a warp on consecutive entries: lane l takes
+// entries l, l+32, l+64, ... (U per step), so one gather instruction reads 32
+// neighbouring entries of the row; where those have nearby columns (a ray
+// crossing neighbouring pixels) the gathers of x share sectors.  Each lane
+// sums its entries in order; the warp adds the 32 partials by a fixed
+// butterfly.
+template <typename VT, typename XT, typename YT, int U, bool CMP>
+__device__ __forceinline__ YT row_dot_s1(int32_t start, int32_t len, const ColIdx ci,
+                                         const VT* __restrict__ val, const XT* __restrict__ x,
+                                         int lane) {
+  YT acc = 0;
+  for (int32_t e = lane; e < len; e += 32 * U) {
+    YT v[U];
+    int32_t c[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int32_t q = e + 32 * u;
+      if (q < len) {
+        const int32_t p = start + q;
+        v[u] = (YT)ld_stream1(val + p);
+        c[u] = CMP ? __ldg(ci.ubase + (p >> 3)) + ld_stream1(ci.off + p) : ld_stream1(ci.col + p);
+      } else {
+        v[u] = 0;
+        c[u] = -1;
+      }
+    }
+    XT xv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) xv[u] = c[u] >= 0 ? __ldg(x + c[u]) : (XT)0;
+#pragma unroll
+    for (int u = 0; u < U; ++u) acc = fma(v[u], (YT)xv[u], acc);
+  }
+  return group_sum<32>(acc);
+}
+
+// G = 0 selects the warp-per-row stride-1 form (row_dot_s1) with U entries in
+// flight per lane.
 template <typename VT, typename XT, typename YT, int G, int U, bool CMP>
 __device__ __forceinline__ YT row_dot(int64_t row, bool valid, const int32_t* __restrict__ rp,
                                       const int32_t* __restrict__ rl, const ColIdx ci,
@@ -220,21 +284,24 @@ __device__ __forceinline__ YT row_dot(int64_t row, bool valid, const int32_t* __
                                       int gl) {
   const int32_t start = valid ? __ldg(rp + row) : 0;
   const int32_t len = valid ? __ldg(rl + row) : 0;
-  if constexpr (CMP)
+  if constexpr (G == 0)
+    return row_dot_s1<VT, XT, YT, U, CMP>(start, len, ci, val, x, gl);
+  else if constexpr (CMP)
     return row_dot_len_c<VT, XT, YT, G, U>(start, len, ci, val, x, gl);
   else
     return row_dot_len<VT, XT, YT, G, U>(start, len, ci.col, val, x, gl);
 }
 
 template <typename VT, typename XT, typename YT, int G, int U, bool CMP>
-__global__ void __launch_bounds__(256, min_blocks<VT, CMP ? 2 * U : U>())
+__global__ void __launch_bounds__(256, (G == 0 && sizeof(VT) == 8 && U > 4) ? 4 : min_blocks<VT, G == 0 ? U / 4 : (CMP ? 2 * U : U)>())
     k_spmv(int64_t rows, const int32_t* __restrict__ rp, const int32_t* __restrict__ rl,
            const ColIdx ci, const VT* __restrict__ val, const XT* __restrict__ x,
            YT* __restrict__ y) {
-  constexpr int RPB = 256 / G;  // rows per block
-  const int gl = threadIdx.x & (G - 1);
-  const int64_t row = (int64_t)blockIdx.x * RPB + threadIdx.x / G;
-  if ((int64_t)blockIdx.x * RPB + (threadIdx.x & ~31) / G >= rows)
+  constexpr int GL = G == 0 ? 32 : G;  // lanes per row
+  constexpr int RPB = 256 / GL;        // rows per block
+  const int gl = threadIdx.x & (GL - 1);
+  const int64_t row = (int64_t)blockIdx.x * RPB + threadIdx.x / GL;
+  if ((int64_t)blockIdx.x * RPB + (threadIdx.x & ~31) / GL >= rows)
     return;  // the whole warp is past the last row
   const bool valid = row < rows;
   const YT acc = row_dot<VT, XT, YT, G, U, CMP>(row, valid, rp, rl, ci, val, x, gl);
@@ -319,26 +386,27 @@ __device__ __forceinline__ void pivot_blocks(const PivotCoef& pc, RowDot rowdot)
 }
 
 template <typename VT, typename XT, typename YT, int G, int U, bool CMP>
-__global__ void __launch_bounds__(256, min_blocks<VT, CMP ? 2 * U : U>())
+__global__ void __launch_bounds__(256, (G == 0 && sizeof(VT) == 8 && U > 4) ? 4 : min_blocks<VT, G == 0 ? U / 4 : (CMP ? 2 * U : U)>())
     k_spmv_pivots(int64_t rows, const int32_t* __restrict__ rp, const int32_t* __restrict__ rl,
                   const ColIdx ci, const VT* __restrict__ val, const XT* __restrict__ x,
                   YT* __restrict__ y, PivotCoef pc) {
-  constexpr int RPB = 256 / G;
+  constexpr int GL = G == 0 ? 32 : G;
+  constexpr int RPB = 256 / GL;
   pdl_wait();  // x and the pivot rows come from the kernels before
   pdl_trigger();
   const int lane = threadIdx.x & 31;
   const int npiv_all = pc.npiv_blocks * pc.nprob;
   if ((int)blockIdx.x >= npiv_all) {  // streaming rows (all but the first npiv_all blocks)
     const int64_t b0 = (int64_t)(blockIdx.x - npiv_all) * RPB;
-    if (b0 + (threadIdx.x & ~31) / G >= rows) return;  // whole warp past the end
-    const int64_t row = b0 + threadIdx.x / G;
+    if (b0 + (threadIdx.x & ~31) / GL >= rows) return;  // whole warp past the end
+    const int64_t row = b0 + threadIdx.x / GL;
     const bool valid = row < rows;
     const YT acc =
-        row_dot<VT, XT, YT, G, U, CMP>(row, valid, rp, rl, ci, val, x, lane & (G - 1));
-    if (valid && (lane & (G - 1)) == 0) y[row] = acc;
+        row_dot<VT, XT, YT, G, U, CMP>(row, valid, rp, rl, ci, val, x, lane & (GL - 1));
+    if (valid && (lane & (GL - 1)) == 0) y[row] = acc;
     return;
   }
-  pivot_blocks<YT, G>(pc, [=](int, int32_t row, int gl) {
+  pivot_blocks<YT, GL>(pc, [=](int, int32_t row, int gl) {
     return row_dot<VT, XT, YT, G, U, CMP>(row, true, rp, rl, ci, val, x, gl);
   });
 }
@@ -348,7 +416,8 @@ __global__ void __launch_bounds__(256, min_blocks<VT, CMP ? 2 * U : U>())
 template <typename VT, typename XT, typename YT, int G, int U, bool MAYCMP = true>
 void spmv_run(const DevCsr& A, const XT* x, YT* y, cudaStream_t s) {
   if (A.rows == 0) return;
-  const int64_t blocks = (A.rows + 256 / G - 1) / (256 / G);
+  constexpr int GL = G == 0 ? 32 : G;
+  const int64_t blocks = (A.rows + 256 / GL - 1) / (256 / GL);
   const ColIdx ci{A.col, A.off, A.ubase};
   const VT* v = reinterpret_cast<const VT*>(A.val);
   if constexpr (MAYCMP) {
@@ -364,8 +433,9 @@ void spmv_run(const DevCsr& A, const XT* x, YT* y, cudaStream_t s) {
 
 template <typename VT, typename XT, typename YT, int G, int U, bool MAYCMP = true>
 void spmv_pivots_run(const DevCsr& A, const XT* x, YT* y, const PivotCoef& pc, cudaStream_t s) {
+  constexpr int GL = G == 0 ? 32 : G;
   const int64_t blocks =
-      (int64_t)pc.npiv_blocks * pc.nprob + (A.rows + 256 / G - 1) / (256 / G);
+      (int64_t)pc.npiv_blocks * pc.nprob + (A.rows + 256 / GL - 1) / (256 / GL);
   const ColIdx ci{A.col, A.off, A.ubase};
   const VT* v = reinterpret_cast<const VT*>(A.val);
   if constexpr (MAYCMP) {

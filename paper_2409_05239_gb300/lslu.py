@@ -292,7 +292,8 @@ class Solver:
         return dict(var_diag=d, var_sum=float(tot[0]))
 
     SHAPES = ("16x2", "32x1", "16x1", "8x1", "8x2", "4x1",
-              "16x2/16-bit", "32x1/16-bit", "16x1/16-bit", "8x1/16-bit", "8x2/16-bit", "4x1/16-bit")
+              "16x2/16-bit", "32x1/16-bit", "16x1/16-bit", "8x1/16-bit", "8x2/16-bit", "4x1/16-bit",
+              "tma", "tma/16-bit", "32x8e", "32x8e/16-bit", "32x4e", "32x4e/16-bit")
 
     def set_spmv_shape(self, shape_A, shape_AT=None):
         """Row shape of the sparse products (index into SHAPES)."""
@@ -311,11 +312,12 @@ class Solver:
         chosen shapes and the per-shape times (microseconds)."""
         a = ctypes.c_int32(0)
         t = ctypes.c_int32(0)
-        us = np.zeros(24)
+        ns = len(self.SHAPES)
+        us = np.zeros(2 * ns)
         self._check(self.lib.lslu_tune_spmv(self.h, int(reps), ctypes.byref(a), ctypes.byref(t),
                                             _ptr(us)))
         keep = lambda v: {k: x for k, x in zip(self.SHAPES, v.tolist()) if x >= 0}
-        return dict(shape_A=a.value, shape_AT=t.value, us_A=keep(us[:12]), us_AT=keep(us[12:]))
+        return dict(shape_A=a.value, shape_AT=t.value, us_A=keep(us[:ns]), us_AT=keep(us[ns:]))
 
     def profile(self, enable=True):
         self._check(self.lib.lslu_profile(self.h, int(enable)))
