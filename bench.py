@@ -60,6 +60,26 @@ def dist_env():
     return rank, world, local
 
 
+def replica_seed(seed_base, rank):
+    """Each rank solves its own seeded instance of the workload."""
+    return seed_base + rank
+
+
+def replica_rate(local_time, units_per_rank, world, device=None):
+    """Whole-job throughput of independent replicas: the units of all ranks
+    divided by the slowest rank's time (max over ranks; torch.distributed must
+    be initialised when world > 1).  Returns (rate, max_time)."""
+    import torch
+
+    t = torch.tensor([float(local_time)], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    tmax = float(t.item())
+    return units_per_rank * world / tmax, tmax
+
+
 # DRAM traffic of one k_spmv_pivots launch on the 512x512 FP32 workload per row
 # shape, (A l_k, A^T d_k) in bytes (dram__bytes_read.sum + dram__bytes_write.sum)
 # from the ncu capture summarised in profiles/spmv_traffic_by_shape_ct512.md.
@@ -497,7 +517,7 @@ def run_gpu(args):
     cfg = tomo.CONFIGS[args.workload]
     K = args.K or cfg["K"]
     P = tomo.make_problem(cfg["N"], cfg["n_ang"], cfg["p"], cfg["n_ellipses"], cfg["etas"][0],
-                          seed=cfg["seed_base"] + rank)
+                          seed=replica_seed(cfg["seed_base"], rank))
     stream = torch.cuda.current_stream(dev)
     solver = lslu.Solver(P.m, P.n, P.row_ptr, P.col_idx, P.vals, args.value_type, K,
                          stream=stream.cuda_stream)
@@ -541,12 +561,9 @@ def run_gpu(args):
     clocks = sampler.stop()
     n_spmv, spmv_ms = solver.timing()
     solver.profile(False)
-    ms_t = torch.tensor([ms], device=dev)
-    if world > 1:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
     total_iters = K * args.steps * world
-    value = total_iters / (ms_max / 1e3)
+    value, s_max = replica_rate(ms / 1e3, K * args.steps, world, dev)
+    ms_max = s_max * 1e3
 
     # end to end through the C ABI with host buffers (H2D of b, D2H of x)
     b_host = torch.from_numpy(P.b).pin_memory()
@@ -565,10 +582,7 @@ def run_gpu(args):
     for _ in range(args.steps):
         step_host()
     e2e_s = time.perf_counter() - t0
-    e2e_t = torch.tensor([e2e_s], device=dev)
-    if world > 1:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e_value = total_iters / float(e2e_t.item())
+    e2e_value, _ = replica_rate(e2e_s, K * args.steps, world, dev)
 
     out = None
     if rank == 0:
