@@ -81,9 +81,9 @@ def replica_rate(local_time, units_per_rank, world, device=None):
 
 
 # DRAM traffic of one k_spmv_pivots launch on the 512x512 FP32 workload per row
-# shape, (A l_k, A^T d_k) in bytes (dram__bytes_read.sum + dram__bytes_write.sum)
-# from the ncu capture summarised in profiles/spmv_traffic_by_shape_ct512.md.
-# It is reported only while the sparse-product sources are the ones captured.
+# shape, (A l_k, A^T d_k) in bytes (dram__bytes_read.sum + dram__bytes_write.sum
+# from one ncu capture of every shape, solve_once --shapes all).  It is reported
+# only while the sparse-product sources are the ones captured.
 SPMV_TRAFFIC = {
     "workload": "ct512", "value_type": "f32",
     "bytes": {
