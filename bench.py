@@ -87,19 +87,19 @@ def replica_rate(local_time, units_per_rank, world, device=None):
 SPMV_TRAFFIC = {
     "workload": "ct512", "value_type": "f32",
     "bytes": {
-        "16x2": (972.43e6, 973.54e6), "32x1": (971.81e6, 972.33e6),
-        "16x1": (978.12e6, 972.49e6), "8x1": (1004.68e6, 1019.12e6),
-        "8x2": (997.67e6, 984.75e6), "4x1": (1011.22e6, 1022.51e6),
-        "16x2/16-bit": (800.28e6, 795.81e6), "32x1/16-bit": (791.60e6, 790.83e6),
-        "16x1/16-bit": (803.88e6, 809.85e6), "8x1/16-bit": (852.67e6, 899.91e6),
-        "8x2/16-bit": (831.89e6, 830.19e6), "4x1/16-bit": (916.85e6, 896.28e6),
-        "tma": (971.70e6, 972.85e6), "tma/16-bit": (790.32e6, 790.95e6),
-        "32x8e": (971.95e6, 972.31e6), "32x8e/16-bit": (791.27e6, 791.09e6),
-        "32x4e": (971.90e6, 972.31e6), "32x4e/16-bit": (793.77e6, 791.89e6),
+        "16x2": (972.70e6, 973.45e6), "32x1": (972.07e6, 972.30e6),
+        "16x1": (978.26e6, 972.56e6), "8x1": (1004.54e6, 1019.91e6),
+        "8x2": (997.52e6, 987.51e6), "4x1": (1011.15e6, 1022.54e6),
+        "16x2/16-bit": (800.20e6, 795.82e6), "32x1/16-bit": (791.73e6, 790.82e6),
+        "16x1/16-bit": (804.95e6, 809.92e6), "8x1/16-bit": (854.82e6, 905.99e6),
+        "8x2/16-bit": (831.94e6, 831.80e6), "4x1/16-bit": (919.27e6, 897.39e6),
+        "tma": (971.81e6, 972.55e6), "tma/16-bit": (790.36e6, 790.95e6),
+        "32x8e": (971.91e6, 972.32e6), "32x8e/16-bit": (791.31e6, 791.01e6),
+        "32x4e": (971.91e6, 972.26e6), "32x4e/16-bit": (793.64e6, 791.88e6),
     },
     "sources": {
         "paper_2409_05239_gb300/csrc/lslu_spmv.cu":
-            "bbfeeeb759777f039867591502b4554c0625d9ea79b5be2f1cd9a18ff50889b5",
+            "ace85ce1e4d967e7621818d192c300f9c6191fb0b2881f3339d9a31a4265721a",
         "paper_2409_05239_gb300/csrc/lslu_spmv_impl.cuh":
             "e618d799b704a719641bc6e6dbf0e35760f17eb2954ef42a4f8cba87f46cebba",
         "paper_2409_05239_gb300/csrc/lslu_spmv_shapes_a.cu":
@@ -111,7 +111,7 @@ SPMV_TRAFFIC = {
         "paper_2409_05239_gb300/csrc/lslu_spmv_tma.cu":
             "3258c2e4fb82c38ccf340c4f48253dc396e784b74b1ebbdd43ae8083ee84199c",
         "paper_2409_05239_gb300/csrc/lslu_internal.cuh":
-            "cbaa9c90e2686d09dea05f7e8b030cb3d8dfd701abfc5bbdbcbf68a5f8cad44c",
+            "a91f78e3e75890c8a7992b0171c3bf0057f172a3142c404de587197edeea226e",
     },
 }
 

@@ -338,7 +338,7 @@ lslu_status lslu_spmv_config(lslu_handle h, int32_t* shape_A, int32_t* shape_AT,
                              int32_t* compressed_A, int32_t* compressed_AT);
 
 /* Autotuner: times every row shape on the handle's A and A^T (each rep
- * launches A then A^T, as a solve does, each after a memset of twice the L2
+ * launches A then A^T, as a solve does, each after a read of twice the L2
  * size that stands in for the elimination before every product of a solve;
  * CUDA events on the handle's stream, after one warm-up pair) and keeps the
  * fastest shape for each, or the default shape unless the fastest beats it

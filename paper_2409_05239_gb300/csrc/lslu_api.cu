@@ -1123,16 +1123,18 @@ extern "C" lslu_status lslu_tune_spmv(lslu_handle h, int32_t reps, int32_t* shap
   CK(cudaMemsetAsync(c->q, 0, (size_t)c->n * bb, s));
   CK(cudaMemsetAsync(c->u, 0, (size_t)c->m * bb, s));
   // in a solve every product follows an elimination that streams the basis
-  // through L2; a memset of twice the L2 size before each timed product
-  // leaves the cache in a comparable state
+  // through L2; reading twice the L2 size before each timed product leaves
+  // the cache in a comparable state (clean lines; the buffer's contents do
+  // not matter)
   int l2 = 0;
   CK(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, c->device));
   const size_t flush_bytes = (size_t)std::max(l2, 1 << 20) * 2;
   void* flush = nullptr;
-  if (cudaMalloc(&flush, flush_bytes) != cudaSuccess) {
+  if (cudaMalloc(&flush, flush_bytes + 16) != cudaSuccess) {
     cudaGetLastError();
     return set_err(c, LSLU_ERR_OOM, "tuning: no room for the L2 flush buffer");
   }
+  int* sink = reinterpret_cast<int*>(static_cast<char*>(flush) + flush_bytes);
   std::vector<cudaEvent_t> ev(4 * reps);
   for (auto& e : ev) CK(cudaEventCreate(&e));
   const int saved[2] = {c->A.shape, c->AT.shape};
@@ -1160,11 +1162,11 @@ extern "C" lslu_status lslu_tune_spmv(lslu_handle h, int32_t reps, int32_t* shap
     run(c->A, c->q, c->u);
     run(c->AT, c->u, c->q);
     for (int r = 0; r < reps; ++r) {
-      cudaMemsetAsync(flush, r & 1, flush_bytes, s);
+      launch_l2_flush(flush, flush_bytes, sink, s, c->num_sms);
       cudaEventRecord(ev[4 * r], s);
       run(c->A, c->q, c->u);
       cudaEventRecord(ev[4 * r + 1], s);
-      cudaMemsetAsync(flush, r & 1, flush_bytes, s);
+      launch_l2_flush(flush, flush_bytes, sink, s, c->num_sms);
       cudaEventRecord(ev[4 * r + 2], s);
       run(c->AT, c->u, c->q);
       cudaEventRecord(ev[4 * r + 3], s);

@@ -43,6 +43,13 @@ inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, siz
 // padded to that length (pad entries repeat the row's last column with value
 // 0), so every row can be read with 16-byte vector loads.
 constexpr int kRowAlign = 8;
+// Within every full kPermBlock-entry block of a row the entries are stored
+// transposed (4 x 16: stored position 4 l + i holds entry 16 i + l), so that
+// a 16-lane row group reading one 4-entry chunk per lane gathers 16
+// consecutive entries of the row in each step (neighbouring columns share L1
+// sectors); the last partial block of a row keeps its order.  A sum over a
+// row does not depend on the order, only its rounding does.
+constexpr int kPermBlock = 64;
 
 // Upper bound on max_iter (bounds the projected-problem workspace).
 constexpr int kMaxIter = 2048;
@@ -291,6 +298,9 @@ void launch_spmv_pivots(const DevCsr& A, int vt, const XT* x, YT* y, PivotCoef p
 // and the elimination coefficients of every right-hand side (as
 // launch_spmv_pivots, with problem p's output rows at p * ystride + row).
 int rhs_stride(int R);
+// Streams `bytes` of buf through L2 (reads only), so that a timed product
+// starts with the matrix out of L2 and no dirty lines to write back.
+void launch_l2_flush(const void* buf, size_t bytes, int* sink, cudaStream_t s, int num_sms);
 void launch_interleave(const float* x, int64_t xstride, int64_t count, int R, float* xi,
                        cudaStream_t s, int num_sms);
 void launch_spmm_pivots(const DevCsr& A, int vt, const float* xi, float* y, int64_t ystride,

@@ -198,6 +198,25 @@ cudaError_t upload_padded(int64_t rows, int64_t cols, const std::vector<int64_t>
       dc[e] = len ? ci[a + len - 1] : 0;
       dv[e] = 0.0;
     }
+    // full kPermBlock-entry blocks stored transposed (4 x 16): position 4 l + i
+    // holds entry 16 i + l, so that the 16 lanes of a row group gather 16
+    // consecutive entries of the row in each step; the last partial block
+    // keeps its order
+    const int64_t nfull = prl[r] / kPermBlock;
+    for (int64_t b = 0; b < nfull; ++b) {
+      int32_t tc[kPermBlock];
+      double tv[kPermBlock];
+      const int64_t base = b * kPermBlock;
+      for (int l = 0; l < 16; ++l)
+        for (int i = 0; i < 4; ++i) {
+          tc[4 * l + i] = dc[base + 16 * i + l];
+          tv[4 * l + i] = dv[base + 16 * i + l];
+        }
+      for (int q = 0; q < kPermBlock; ++q) {
+        dc[base + q] = tc[q];
+        dv[base + q] = tv[q];
+      }
+    }
   }
   out->rows = rows;
   out->cols = cols;
@@ -434,6 +453,25 @@ void spmm_rs(const DevCsr& A, const float* xi, float* y, int64_t ystride, int R,
 }
 
 int rhs_stride(int R) { return R <= 4 ? 4 : (R <= 8 ? 8 : 16); }
+
+namespace {
+// Reads n 16-byte words through L2 (clean lines, as the elimination leaves
+// them before a product) and stores one word so the reads are not dropped.
+__global__ void k_l2_flush(const int4* __restrict__ p, int64_t n, int* sink) {
+  int acc = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int4 v = __ldcg(p + i);
+    acc ^= v.x ^ v.y ^ v.z ^ v.w;
+  }
+  if (acc == 0x7fffffff) *sink = acc;  // practically never; keeps the loads
+}
+}  // namespace
+
+void launch_l2_flush(const void* buf, size_t bytes, int* sink, cudaStream_t s, int num_sms) {
+  const int64_t n = (int64_t)(bytes / 16);
+  k_l2_flush<<<num_sms * 8, 256, 0, s>>>(reinterpret_cast<const int4*>(buf), n, sink);
+}
 
 void launch_interleave(const float* x, int64_t xstride, int64_t count, int R, float* xi,
                        cudaStream_t s, int num_sms) {
