@@ -47,6 +47,8 @@ def parse():
     p.add_argument("--workload", default=WORKLOAD, choices=sorted(tomo.CONFIGS))
     p.add_argument("--value-type", default="f32", choices=["f32", "bf16", "f64"])
     p.add_argument("--K", type=int, default=None)
+    p.add_argument("--order", default="tiles", choices=["tiles", "natural"],
+                   help="numbering the handle stores A in (tomo.locality_order)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-extras", action="store_true", help="skip the precision study")
     p.add_argument("--cpu-sample-s", type=float, default=15.0)
@@ -80,22 +82,33 @@ def replica_rate(local_time, units_per_rank, world, device=None):
     return units_per_rank * world / tmax, tmax
 
 
-# DRAM traffic of one k_spmv_pivots launch on the 512x512 FP32 workload per row
-# shape, (A l_k, A^T d_k) in bytes (dram__bytes_read.sum + dram__bytes_write.sum
-# from one ncu capture of every shape, solve_once --shapes all).  It is reported
-# only while the sparse-product sources are the ones captured.
+ORDER_NOTE = {
+    "natural": "A as generated (pixels row by row, rays angle by angle)",
+    "tiles": "A stored renumbered by lslu_create_ordered (tomo.locality_order: pixels in 2x4 "
+             "tiles, rays in tiles of 4 angles x 2 rays); b, x and pivots in the natural "
+             "numbering",
+}
+
+# DRAM traffic of one k_spmv_pivots launch on the 512x512 FP32 workload per
+# numbering and row shape, (A l_k, A^T d_k) in bytes (dram__bytes_read.sum +
+# dram__bytes_write.sum from one ncu capture of every shape, solve_once
+# --shapes all [--order tiles]).  It is reported only while the sparse-product
+# sources are the ones captured.
 SPMV_TRAFFIC = {
     "workload": "ct512", "value_type": "f32",
     "bytes": {
-        "16x2": (972.70e6, 973.45e6), "32x1": (972.07e6, 972.30e6),
-        "16x1": (978.26e6, 972.56e6), "8x1": (1004.54e6, 1019.91e6),
-        "8x2": (997.52e6, 987.51e6), "4x1": (1011.15e6, 1022.54e6),
-        "16x2/16-bit": (800.20e6, 795.82e6), "32x1/16-bit": (791.73e6, 790.82e6),
-        "16x1/16-bit": (804.95e6, 809.92e6), "8x1/16-bit": (854.82e6, 905.99e6),
-        "8x2/16-bit": (831.94e6, 831.80e6), "4x1/16-bit": (919.27e6, 897.39e6),
-        "tma": (971.81e6, 972.55e6), "tma/16-bit": (790.36e6, 790.95e6),
-        "32x8e": (971.91e6, 972.32e6), "32x8e/16-bit": (791.31e6, 791.01e6),
-        "32x4e": (971.91e6, 972.26e6), "32x4e/16-bit": (793.64e6, 791.88e6),
+        "natural": {
+            "16x2": (972.70e6, 973.45e6), "32x1": (972.07e6, 972.30e6),
+            "16x1": (978.26e6, 972.56e6), "8x1": (1004.54e6, 1019.91e6),
+            "8x2": (997.52e6, 987.51e6), "4x1": (1011.15e6, 1022.54e6),
+            "16x2/16-bit": (800.20e6, 795.82e6), "32x1/16-bit": (791.73e6, 790.82e6),
+            "16x1/16-bit": (804.95e6, 809.92e6), "8x1/16-bit": (854.82e6, 905.99e6),
+            "8x2/16-bit": (831.94e6, 831.80e6), "4x1/16-bit": (919.27e6, 897.39e6),
+            "tma": (971.81e6, 972.55e6), "tma/16-bit": (790.36e6, 790.95e6),
+            "32x8e": (971.91e6, 972.32e6), "32x8e/16-bit": (791.31e6, 791.01e6),
+            "32x4e": (971.91e6, 972.26e6), "32x4e/16-bit": (793.64e6, 791.88e6),
+        },
+        "tiles": {},
     },
     "sources": {
         "paper_2409_05239_gb300/csrc/lslu_spmv.cu":
@@ -116,14 +129,15 @@ SPMV_TRAFFIC = {
 }
 
 
-def spmv_traffic(workload, value_type, shape_A, shape_AT):
+def spmv_traffic(workload, value_type, order, shape_A, shape_AT):
     """Measured DRAM bytes of one sparse product (average of the two directions)
-    for the tuned shapes, or None when no capture matches the current build."""
+    for the numbering and the tuned shapes, or None when no capture matches the
+    current build."""
     import hashlib
 
     if workload != SPMV_TRAFFIC["workload"] or value_type != SPMV_TRAFFIC["value_type"]:
         return None
-    tab = SPMV_TRAFFIC["bytes"]
+    tab = SPMV_TRAFFIC["bytes"].get(order, {})
     if shape_A not in tab or shape_AT not in tab:
         return None
     for rel, digest in SPMV_TRAFFIC["sources"].items():
@@ -229,7 +243,7 @@ def cpu_baseline(P, K, sample_s):
                       f"1 thread), {dt:.1f} s"}
 
 
-def precision_study(P, K, rule, dev, x_main, main_vt):
+def precision_study(P, K, rule, dev, x_main, main_vt, order=(None, None)):
     """Mixed precision against the FP64 GPU path on the same instance: A's
     values in FP64 / FP32 / BF16 (FP64 or FP32 basis).  For each: throughput
     of the K-iteration solve (autotuned sparse products), relative error of
@@ -249,7 +263,8 @@ def precision_study(P, K, rule, dev, x_main, main_vt):
     ks = list(range(25, K + 1, 25))
     nx = np.linalg.norm(P.x_true)
     for vt in ("f64", "f32", "bf16"):
-        s = lslu.Solver(P.m, P.n, P.row_ptr, P.col_idx, P.vals, vt, K, stream=stream.cuda_stream)
+        s = lslu.Solver(P.m, P.n, P.row_ptr, P.col_idx, P.vals, vt, K, stream=stream.cuda_stream,
+                        row_order=order[0], col_order=order[1])
         s.tune_spmv(reps=3)
         s.solve_device(b_dev, x_dev, K, rule)
         torch.cuda.synchronize()
@@ -519,8 +534,9 @@ def run_gpu(args):
     P = tomo.make_problem(cfg["N"], cfg["n_ang"], cfg["p"], cfg["n_ellipses"], cfg["etas"][0],
                           seed=replica_seed(cfg["seed_base"], rank))
     stream = torch.cuda.current_stream(dev)
+    ro, co = tomo.locality_order(P) if args.order == "tiles" else (None, None)
     solver = lslu.Solver(P.m, P.n, P.row_ptr, P.col_idx, P.vals, args.value_type, K,
-                         stream=stream.cuda_stream)
+                         stream=stream.cuda_stream, row_order=ro, col_order=co)
     # autotuner: the fastest row shape of the sparse products for this A and A^T
     tuned = solver.tune_spmv(reps=5)
     b_dev = torch.from_numpy(P.b).to(dev)
@@ -608,6 +624,7 @@ def run_gpu(args):
             "config": {"workload": f"{args.workload}: {cfg['N']}x{cfg['N']} image, "
                                    f"{cfg['n_ang']} angles x {cfg['p']} rays",
                        "m": P.m, "n": P.n, "nnz": P.nnz, "K": K, "lambda_rule": rule,
+                       "numbering": ORDER_NOTE[args.order],
                        "A_values": args.value_type, "basis": "f64" if args.value_type == "f64"
                        else "f32", "projected_solve": "f64",
                        "l2": "inputs larger than L2 (CSR of A and A^T ~%.1f GB)" % (
@@ -623,7 +640,7 @@ def run_gpu(args):
                          "timing": "CUDA events around each product, second pass of the timed steps",
                          "algorithmic_bytes_per_launch": sbytes, "launches": n_spmv,
                          "avg_launch_ms": avg_ms,
-                         "traffic": spmv_traffic(args.workload, args.value_type,
+                         "traffic": spmv_traffic(args.workload, args.value_type, args.order,
                                                  cfg_sp["shape_A"], cfg_sp["shape_AT"]),
                          "traffic_source": "profiles/spmv_traffic_by_shape_ct512.md (ncu dram "
                                            "bytes per launch for the tuned shapes)"},
@@ -636,7 +653,7 @@ def run_gpu(args):
         }
     solver.close()
     if rank == 0 and not args.no_extras and world == 1:
-        out["precision_study"] = precision_study(P, K, rule, dev, x, args.value_type)
+        out["precision_study"] = precision_study(P, K, rule, dev, x, args.value_type, (ro, co))
     if rank == 0 and not args.no_extras and world == 1:
         out["batched_study"] = batched_study(dev)
         out["shared_rhs_study"] = shared_rhs_study(dev)

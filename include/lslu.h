@@ -79,6 +79,28 @@ lslu_status lslu_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row_pt
                         int32_t max_iter, int32_t ptr_location, void* cuda_stream,
                         lslu_handle* out);
 
+/* lslu_create with a renumbering of the rows and columns of A, for memory
+ * locality of the sparse products (Algorithm 4 gathers the basis vector
+ * through the column indices of every row).  row_order (m int32) and
+ * col_order (n int32) are permutations: caller row i becomes internal row
+ * row_order[i], caller column j internal column col_order[j]; NULL is the
+ * identity.  Host or device per ptr_location, like the CSR arrays; copied.
+ * The handle stores A_hat = P_r A P_c^T (each row's entries sorted by the new
+ * column) and runs every solve on A_hat and b_hat = P_r b.  Every entry point
+ * takes and returns vectors, bases and pivot indices in the caller's
+ * numbering: the renumbering is applied on entry and undone on exit.  The
+ * method commutes with a renumbering (max-abs pivots pick the same entries),
+ * so results equal lslu_create's up to the rounding order of the products,
+ * except where two candidates of a pivot search tie exactly: a tie goes to
+ * the lower internal index.  lslu_spmv is refused on such a handle.
+ * Errors: those of lslu_create, and LSLU_ERR_INVALID_ARG when an order is not
+ * a permutation of [0, m) or [0, n). */
+lslu_status lslu_create_ordered(int64_t m, int64_t n, int64_t nnz, const int64_t* row_ptr,
+                                const int32_t* col_idx, const double* vals, int32_t value_type,
+                                int32_t max_iter, const int32_t* row_order,
+                                const int32_t* col_order, int32_t ptr_location,
+                                void* cuda_stream, lslu_handle* out);
+
 /* Run K iterations of Hybrid LSLU (Algorithm 5) on data b (length m, FP64)
  * from x0 (length n, FP64; NULL means x0 = 0).  rule is an lslu_lambda_rule;
  * lambda is used by LSLU_LAMBDA_FIXED only.  Outputs (host or device per

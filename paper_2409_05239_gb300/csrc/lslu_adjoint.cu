@@ -786,13 +786,16 @@ extern "C" lslu_status lslu_adjoint(lslu_handle h, const double* x_bar, int32_t 
   double* dx0 = nullptr;
   double* dl = nullptr;
   cudaError_t e = cudaSuccess;
-  if (host) {
+  // host vectors, and every vector of a renumbered handle, go through a
+  // device staging area in the internal numbering
+  const bool stage = host || c->ord_m;
+  if (stage) {
     if ((e = cudaMalloc(&dx, (size_t)(2 * n + m + 1) * sizeof(double))) != cudaSuccess)
       return fail(c, LSLU_ERR_OOM, "adjoint staging");
     db = dx + n;
     dx0 = x0_bar ? db + m : nullptr;
     dl = db + m + n;
-    e = cudaMemcpyAsync(dx, x_bar, n * 8, cudaMemcpyHostToDevice, s);
+    e = vec_in(c, false, x_bar, host, dx);
   } else {
     dx = const_cast<double*>(x_bar);
     db = b_bar;
@@ -805,14 +808,15 @@ extern "C" lslu_status lslu_adjoint(lslu_handle h, const double* x_bar, int32_t 
   } else {
     st = fail(c, LSLU_ERR_CUDA, cudaGetErrorString(e));
   }
-  if (host && st == LSLU_OK) {
-    e = cudaMemcpyAsync(b_bar, db, m * 8, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess && x0_bar) e = cudaMemcpyAsync(x0_bar, dx0, n * 8, cudaMemcpyDeviceToHost, s);
+  if (stage && st == LSLU_OK) {
+    e = vec_out(c, true, db, host, b_bar);
+    if (e == cudaSuccess && x0_bar) e = vec_out(c, false, dx0, host, x0_bar);
     if (e == cudaSuccess && lambda_bar)
-      e = cudaMemcpyAsync(lambda_bar, dl, 8, cudaMemcpyDeviceToHost, s);
+      e = cudaMemcpyAsync(lambda_bar, dl, 8,
+                          host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) st = fail(c, LSLU_ERR_CUDA, cudaGetErrorString(e));
   }
-  if (host) cudaFree(dx);
+  if (stage) cudaFree(dx);
   return st;
 }

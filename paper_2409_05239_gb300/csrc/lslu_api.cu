@@ -23,6 +23,26 @@ namespace lslu {
 // Last failure of a call that has no handle (lslu_create, allocation-free
 // entry points); read by lslu_error_string(NULL).
 std::string& thread_error() { return g_create_err_store; }
+
+cudaError_t vec_in(Ctx* c, bool rows, const double* src, bool host, double* dst) {
+  const int64_t len = rows ? c->m : c->n;
+  const cudaMemcpyKind kind = host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  if (!c->ord_m) return cudaMemcpyAsync(dst, src, len * 8, kind, c->stream);
+  cudaError_t e = cudaMemcpyAsync(c->ord_stage, src, len * 8, kind, c->stream);
+  if (e != cudaSuccess) return e;
+  launch_scatter(c->ord_stage, rows ? c->ord_m : c->ord_n, len, dst, c->stream);
+  return cudaGetLastError();
+}
+
+cudaError_t vec_out(Ctx* c, bool rows, const double* src, bool host, double* dst) {
+  const int64_t len = rows ? c->m : c->n;
+  const cudaMemcpyKind kind = host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  if (!c->ord_m) return cudaMemcpyAsync(dst, src, len * 8, kind, c->stream);
+  launch_gather(src, rows ? c->ord_m : c->ord_n, len, c->ord_stage, c->stream);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return cudaMemcpyAsync(dst, c->ord_stage, len * 8, kind, c->stream);
+}
 }  // namespace lslu
 
 namespace {
@@ -65,7 +85,8 @@ void destroy_ctx(lslu_ctx* c) {
                   c->cvec, c->xout, c->tile_prob_m, c->tile_prob_n, c->pad_m, c->pad_n,
                   c->map_m, c->map_n, c->xin_pad, c->xout_user, c->mvec,
                   c->adj_Vb, c->adj_Zb, c->adj_vec, c->adj_small, c->adj_part,
-                  c->fixed_gp, c->fixed_tp, c->xi, c->samples};
+                  c->fixed_gp, c->fixed_tp, c->xi, c->samples, c->ord_m, c->ord_n,
+                  c->ord_stage};
   for (void* p : ptrs) cudaFree(p);
   if (c->st_host) cudaFreeHost(c->st_host);
   for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
@@ -176,10 +197,40 @@ lslu_status create_common(lslu_ctx* c, const int64_t* rp, const int32_t* ci, con
 
 }  // namespace
 
-extern "C" lslu_status lslu_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row_ptr,
-                                   const int32_t* col_idx, const double* vals,
-                                   int32_t value_type, int32_t max_iter, int32_t ptr_location,
-                                   void* cuda_stream, lslu_handle* out) {
+namespace {
+
+// Caller -> internal renumbering of one index space (row or column orders of
+// lslu_create_ordered): copied to the host, checked to be a permutation of
+// [0, len); inv receives its inverse.  NULL means the identity.
+lslu_status read_order(const int32_t* order, int64_t len, bool device, std::vector<int32_t>& fwd,
+                       std::vector<int32_t>& inv, const char* what) {
+  fwd.resize(len);
+  inv.assign(len, -1);
+  if (!order) {
+    for (int64_t i = 0; i < len; ++i) fwd[i] = inv[i] = (int32_t)i;
+    return LSLU_OK;
+  }
+  if (device) {
+    cudaError_t e = cudaMemcpy(fwd.data(), order, len * 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess)
+      return set_err(nullptr, LSLU_ERR_CUDA, std::string("copying ") + what + ": " +
+                                                 cudaGetErrorString(e));
+  } else {
+    std::memcpy(fwd.data(), order, len * 4);
+  }
+  for (int64_t i = 0; i < len; ++i) {
+    const int32_t v = fwd[i];
+    if (v < 0 || v >= len || inv[v] >= 0)
+      return set_err(nullptr, LSLU_ERR_INVALID_ARG, std::string(what) + " is not a permutation");
+    inv[v] = (int32_t)i;
+  }
+  return LSLU_OK;
+}
+
+lslu_status create_single(int64_t m, int64_t n, int64_t nnz, const int64_t* row_ptr,
+                          const int32_t* col_idx, const double* vals, int32_t value_type,
+                          int32_t max_iter, const int32_t* row_order, const int32_t* col_order,
+                          int32_t ptr_location, void* cuda_stream, lslu_handle* out) {
   lslu_ctx* c = nullptr;
   if (!out) return set_err(nullptr, LSLU_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
@@ -225,6 +276,35 @@ extern "C" lslu_status lslu_create(int64_t m, int64_t n, int64_t nnz, const int6
     if (!std::isfinite(vv[i]))
       return set_err(nullptr, LSLU_ERR_INVALID_ARG, "non-finite matrix value");
   }
+  const bool ordered = row_order || col_order;
+  std::vector<int32_t> om, on, im, in;
+  if (ordered) {
+    lslu_status st = read_order(row_order, m, ptr_location == LSLU_DEVICE, om, im, "row_order");
+    if (st == LSLU_OK)
+      st = read_order(col_order, n, ptr_location == LSLU_DEVICE, on, in, "col_order");
+    if (st != LSLU_OK) return st;
+    // internal row r holds caller row im[r] with its columns renumbered and
+    // sorted ascending
+    std::vector<int64_t> rp2(m + 1, 0);
+    for (int64_t r = 0; r < m; ++r) rp2[r + 1] = rp2[r] + (rp[im[r] + 1] - rp[im[r]]);
+    std::vector<int32_t> ci2(nnz);
+    std::vector<double> vv2(nnz);
+    std::vector<uint64_t> key;
+    for (int64_t r = 0; r < m; ++r) {
+      const int64_t a = rp[im[r]], len = rp[im[r] + 1] - a, o = rp2[r];
+      key.resize(len);
+      for (int64_t i = 0; i < len; ++i)
+        key[i] = ((uint64_t)(uint32_t)on[ci[a + i]] << 32) | (uint64_t)i;
+      std::sort(key.begin(), key.end());
+      for (int64_t i = 0; i < len; ++i) {
+        ci2[o + i] = (int32_t)(key[i] >> 32);
+        vv2[o + i] = vv[a + (int64_t)(key[i] & 0xffffffffull)];
+      }
+    }
+    rp.swap(rp2);
+    ci.swap(ci2);
+    vv.swap(vv2);
+  }
 
   c = new lslu_ctx();
   c->nprob = 1;
@@ -242,8 +322,45 @@ extern "C" lslu_status lslu_create(int64_t m, int64_t n, int64_t nnz, const int6
   c->stream = (cudaStream_t)cuda_stream;
   lslu_status st = create_common(c, rp.data(), ci.data(), vv.data());
   if (st != LSLU_OK) return st;
+  if (ordered) {
+    cudaError_t e = dmalloc(&c->ord_m, m);
+    if (e == cudaSuccess) e = dmalloc(&c->ord_n, n);
+    if (e == cudaSuccess) e = dmalloc(&c->ord_stage, std::max(m, n));
+    if (e == cudaSuccess) e = cudaMemcpy(c->ord_m, om.data(), m * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->ord_n, on.data(), n * 4, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      destroy_ctx(c);
+      return set_err(nullptr, e == cudaErrorMemoryAllocation ? LSLU_ERR_OOM : LSLU_ERR_CUDA,
+                     std::string("renumbering maps: ") + cudaGetErrorString(e));
+    }
+    c->ord_m_h.swap(om);
+    c->ord_n_h.swap(on);
+    c->inv_m_h.swap(im);
+    c->inv_n_h.swap(in);
+  }
   *out = c;
   return LSLU_OK;
+}
+
+}  // namespace
+
+extern "C" lslu_status lslu_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row_ptr,
+                                   const int32_t* col_idx, const double* vals,
+                                   int32_t value_type, int32_t max_iter, int32_t ptr_location,
+                                   void* cuda_stream, lslu_handle* out) {
+  return create_single(m, n, nnz, row_ptr, col_idx, vals, value_type, max_iter, nullptr, nullptr,
+                       ptr_location, cuda_stream, out);
+}
+
+extern "C" lslu_status lslu_create_ordered(int64_t m, int64_t n, int64_t nnz,
+                                           const int64_t* row_ptr, const int32_t* col_idx,
+                                           const double* vals, int32_t value_type,
+                                           int32_t max_iter, const int32_t* row_order,
+                                           const int32_t* col_order, int32_t ptr_location,
+                                           void* cuda_stream, lslu_handle* out) {
+  return create_single(m, n, nnz, row_ptr, col_idx, vals, value_type, max_iter, row_order,
+                       col_order, ptr_location, cuda_stream, out);
 }
 
 
@@ -553,14 +670,14 @@ lslu_status solve_entry(Ctx* c, const double* b, const double* x0, int32_t K, in
   if (host)
     for (int64_t i = 0; i < m; ++i)
       if (!std::isfinite(b[i])) return set_err(c, LSLU_ERR_NONFINITE, "b has a non-finite entry");
-  const cudaMemcpyKind h2d = host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
-  CK(cudaMemcpyAsync(c->xin, b, m * 8, h2d, s));
+  CK(vec_in(c, true, b, host, c->xin));
   const double* db = c->xin;
   const double* dx0 = nullptr;
   if (x0) {
-    CK(cudaMemcpyAsync(c->xin + m, x0, n * 8, h2d, s));
+    CK(vec_in(c, false, x0, host, c->xin + m));
     dx0 = c->xin + m;
   }
+  const bool ord = c->ord_m != nullptr;
   const bool fixed = fix_g != nullptr;
   if (fixed) {  // replayed pivots: validate on the host (indices in range, distinct)
     std::vector<int32_t> g(K), t(K + 1);
@@ -582,6 +699,10 @@ lslu_status solve_entry(Ctx* c, const double* b, const double* x0, int32_t K, in
         return set_err(c, LSLU_ERR_INVALID_ARG, "row_pivots must be distinct indices in [0, m)");
       seen_m[t[i]] = 1;
     }
+    if (ord) {  // to the internal numbering
+      for (int i = 0; i < K; ++i) g[i] = c->ord_n_h[g[i]];
+      for (int i = 0; i <= K; ++i) t[i] = c->ord_m_h[t[i]];
+    }
     CK(cudaMemcpyAsync(c->fixed_gp, g.data(), (size_t)K * 4, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(c->fixed_tp, t.data(), (size_t)(K + 1) * 4, cudaMemcpyHostToDevice, s));
     CK(cudaStreamSynchronize(s));  // the host vectors go out of scope
@@ -600,6 +721,7 @@ lslu_status solve_entry(Ctx* c, const double* b, const double* x0, int32_t K, in
         if (v < 0 || v >= lim)
           return set_err(c, LSLU_ERR_INVALID_ARG,
                          "sample indices must lie in [0, m) for even rows, [0, n) for odd rows");
+        if (ord) t[(size_t)(r * nsamp + j)] = (r % 2 == 0) ? c->ord_m_h[v] : c->ord_n_h[v];
       }
     }
     if ((int64_t)(2LL * c->kmax + 1) * nsamp > (int64_t)c->samples_cap) {
@@ -626,9 +748,22 @@ lslu_status solve_entry(Ctx* c, const double* b, const double* x0, int32_t K, in
   c->last_K = K;
   c->adj_valid = ds.status == LSLU_OK && kd == K;
   const cudaMemcpyKind d2o = host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
-  CK(cudaMemcpyAsync(x_out, c->xout, n * 8, d2o, s));
+  CK(vec_out(c, false, c->xout, host, x_out));
+  // pivot indices of a renumbered handle go back to the caller's numbering
+  auto pivots_out = [&](int32_t* dst, const int32_t* src, int cnt,
+                        const std::vector<int32_t>& inv) -> cudaError_t {
+    if (!ord || cnt <= 0) return cudaMemcpyAsync(dst, src, (size_t)cnt * 4, d2o, s);
+    std::vector<int32_t> v(cnt);
+    cudaError_t e = cudaMemcpyAsync(v.data(), src, (size_t)cnt * 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return e;
+    for (int32_t& x : v) x = inv[x];
+    e = cudaMemcpyAsync(dst, v.data(), (size_t)cnt * 4,
+                        host ? cudaMemcpyHostToHost : cudaMemcpyHostToDevice, s);
+    return e == cudaSuccess ? cudaStreamSynchronize(s) : e;
+  };
   if (col_pivots) {
-    CK(cudaMemcpyAsync(col_pivots, c->gp, (size_t)kd * 4, d2o, s));
+    CK(pivots_out(col_pivots, c->gp, kd, c->inv_n_h));
     if (K > kd) {
       if (host)
         std::memset(col_pivots + kd, 0xff, (size_t)(K - kd) * 4);
@@ -638,7 +773,7 @@ lslu_status solve_entry(Ctx* c, const double* b, const double* x0, int32_t K, in
   }
   if (row_pivots) {
     const int nt = (ds.status == LSLU_BREAKDOWN_BETA) ? 0 : kd + 1;
-    CK(cudaMemcpyAsync(row_pivots, c->tp, (size_t)nt * 4, d2o, s));
+    CK(pivots_out(row_pivots, c->tp, nt, c->inv_m_h));
     if (K + 1 > nt) {
       if (host)
         std::memset(row_pivots + nt, 0xff, (size_t)(K + 1 - nt) * 4);
@@ -1002,11 +1137,10 @@ extern "C" lslu_status lslu_solve_stopping(lslu_handle h, const double* b, const
   if (host)
     for (int64_t i = 0; i < m; ++i)
       if (!std::isfinite(b[i])) return set_err(c, LSLU_ERR_NONFINITE, "b has a non-finite entry");
-  const cudaMemcpyKind h2d = host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
-  CK(cudaMemcpyAsync(c->xin, b, m * 8, h2d, s));
+  CK(vec_in(c, true, b, host, c->xin));
   const double* dx0 = nullptr;
   if (x0) {
-    CK(cudaMemcpyAsync(c->xin + m, x0, n * 8, h2d, s));
+    CK(vec_in(c, false, x0, host, c->xin + m));
     dx0 = c->xin + m;
   }
   const double lam = rule == LSLU_LAMBDA_FIXED ? lambda : 0.0;
@@ -1057,7 +1191,7 @@ extern "C" lslu_status lslu_solve_stopping(lslu_handle h, const double* b, const
     if (dx0) CK(cudaMemcpyAsync(c->xout, dx0, n * 8, cudaMemcpyDeviceToDevice, s));
   }
   const cudaMemcpyKind d2o = host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
-  CK(cudaMemcpyAsync(x_out, c->xout, n * 8, d2o, s));
+  CK(vec_out(c, false, c->xout, host, x_out));
   if (g_hist) CK(cudaMemcpyAsync(g_hist, G, (size_t)K_max * 8, d2o, s));
   if (k_stop) {
     if (host)
@@ -1242,10 +1376,9 @@ extern "C" lslu_status lslu_solve_optimal(lslu_handle h, const double* b, int32_
   const bool host = ptr_location == LSLU_HOST;
   const int64_t m = c->m, n = c->n;
   cudaStream_t s = c->stream;
-  const cudaMemcpyKind h2d = host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
-  CK(cudaMemcpyAsync(c->xin, b, m * 8, h2d, s));
+  CK(vec_in(c, true, b, host, c->xin));
   // x_true is staged behind b (the staging buffer holds m + n doubles)
-  CK(cudaMemcpyAsync(c->xin + m, x_true, n * 8, h2d, s));
+  CK(vec_in(c, false, x_true, host, c->xin + m));
   // the basis and the factorisation of the final projected problem
   lslu_status st = c->value_type == LSLU_F64
                        ? solve_impl<double, double>(c, c->xin, nullptr, K, LSLU_LAMBDA_NONE, 0.0, false)
@@ -1298,8 +1431,7 @@ extern "C" lslu_status lslu_solve_optimal(lslu_handle h, const double* b, int32_
         else
           launch_recombine<float>((const float*)c->L, c->ldl, c->y, c->kmax, nullptr, c->xout,
                                   n, nullptr, 1, nullptr, K, s, c->num_sms);
-        const cudaMemcpyKind d2o = host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
-        e = cudaMemcpyAsync(x_out, c->xout, n * 8, d2o, s);
+        e = vec_out(c, false, c->xout, host, x_out);
         if (e == cudaSuccess && lambda_out) {
           if (host)
             *lambda_out = lam;
@@ -1340,10 +1472,31 @@ extern "C" lslu_status lslu_get_state(lslu_handle h, int32_t ptr_location, doubl
     else
       CK(cudaMemcpyAsync(beta, &c->st->beta, 8, cudaMemcpyDeviceToDevice, s));
   }
-  if (L && k > 0)
-    CK(cudaMemcpy2DAsync(L, c->n * bb, c->L, c->ldl * bb, c->n * bb, k, kind, s));
-  if (D)
-    CK(cudaMemcpy2DAsync(D, c->m * bb, c->D, c->ldd * bb, c->m * bb, k + 1, kind, s));
+  if (c->ord_m) {  // bases back to the caller's numbering: row gathers
+    for (int which = 0; which < 2; ++which) {
+      void* dst = which == 0 ? L : D;
+      const int64_t rows = which == 0 ? c->n : c->m;
+      const int cols = which == 0 ? k : k + 1;
+      if (!dst || cols == 0) continue;
+      void* tmp = dst;
+      if (ptr_location == LSLU_HOST) CK(cudaMalloc(&tmp, (size_t)rows * cols * bb));
+      launch_gather_rows(which == 0 ? c->L : c->D, which == 0 ? c->ldl : c->ldd,
+                         which == 0 ? c->ord_n : c->ord_m, rows, cols, tmp, rows, (int)bb, s);
+      cudaError_t e = cudaGetLastError();
+      if (ptr_location == LSLU_HOST) {
+        if (e == cudaSuccess)
+          e = cudaMemcpyAsync(dst, tmp, (size_t)rows * cols * bb, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        cudaFree(tmp);
+      }
+      CK(e);
+    }
+  } else {
+    if (L && k > 0)
+      CK(cudaMemcpy2DAsync(L, c->n * bb, c->L, c->ldl * bb, c->n * bb, k, kind, s));
+    if (D)
+      CK(cudaMemcpy2DAsync(D, c->m * bb, c->D, c->ldd * bb, c->m * bb, k + 1, kind, s));
+  }
   CK(cudaStreamSynchronize(s));
   return LSLU_OK;
 }
@@ -1353,6 +1506,8 @@ extern "C" lslu_status lslu_spmv(lslu_handle h, int32_t transpose, const void* x
   if (!c) return set_err(nullptr, LSLU_ERR_INVALID_ARG, "NULL handle");
   if (!x || !y) return set_err(c, LSLU_ERR_INVALID_ARG, "NULL vector");
   if (c->map_m) return set_err(c, LSLU_ERR_INVALID_ARG, "lslu_spmv takes single-problem handles");
+  if (c->ord_m)
+    return set_err(c, LSLU_ERR_INVALID_ARG, "lslu_spmv takes handles without a renumbering");
   const DevCsr& A = transpose ? c->AT : c->A;
   if (c->value_type == LSLU_F64)
     launch_spmv<double, double>(A, c->value_type, (const double*)x, (double*)y, c->stream,

@@ -485,6 +485,16 @@ __global__ void k_gather(const double* __restrict__ src, const int32_t* __restri
     dst[i] = src[map[i]];
 }
 
+template <typename T>
+__global__ void k_gather_rows(const T* __restrict__ src, int64_t lds,
+                              const int32_t* __restrict__ map, int64_t rows, int64_t cols,
+                              T* __restrict__ dst, int64_t ldd) {
+  for (int64_t j = blockIdx.y; j < cols; j += gridDim.y)
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < rows;
+         i += (int64_t)gridDim.x * blockDim.x)
+      dst[j * ldd + i] = src[j * lds + map[i]];
+}
+
 // x = x0 + L y for every problem; tiles of kTile rows (one problem each),
 // FP64 accumulation.
 template <typename BT>
@@ -604,6 +614,19 @@ void launch_gather(const double* src, const int32_t* map, int64_t count, double*
   if (count <= 0) return;
   k_gather<<<(unsigned)std::min<int64_t>((count + 255) / 256, 4096), 256, 0, s>>>(src, map,
                                                                                 count, dst);
+}
+
+void launch_gather_rows(const void* src, int64_t lds, const int32_t* map, int64_t rows,
+                        int64_t cols, void* dst, int64_t ldd, int elem_bytes, cudaStream_t s) {
+  if (rows <= 0 || cols <= 0) return;
+  const dim3 grid((unsigned)std::min<int64_t>((rows + 255) / 256, 1024),
+                  (unsigned)std::min<int64_t>(cols, 4096));
+  if (elem_bytes == 8)
+    k_gather_rows<double><<<grid, 256, 0, s>>>((const double*)src, lds, map, rows, cols,
+                                               (double*)dst, ldd);
+  else
+    k_gather_rows<float><<<grid, 256, 0, s>>>((const float*)src, lds, map, rows, cols,
+                                              (float*)dst, ldd);
 }
 
 template <typename BT>

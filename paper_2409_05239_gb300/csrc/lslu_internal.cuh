@@ -247,6 +247,16 @@ struct Ctx {
   bool adj_valid = false;      // the last lslu_solve completed K iterations and its
                                // state (bases, H, W, y, lambda) is intact
 
+  // renumbered handle (lslu_create_ordered): caller row i is internal row
+  // ord_m[i], caller column j internal column ord_n[j]; the matrix, the bases
+  // and every pivot search live in the internal numbering, and vectors and
+  // pivot indices are mapped at the entry points
+  int32_t* ord_m = nullptr;
+  int32_t* ord_n = nullptr;
+  std::vector<int32_t> ord_m_h, ord_n_h;  // caller -> internal (host)
+  std::vector<int32_t> inv_m_h, inv_n_h;  // internal -> caller (host)
+  double* ord_stage = nullptr;            // max(m, n) FP64 staging
+
   int last_k = -1;  // k_done of the last solve, -1 if none
   int last_K = 0;
   int64_t launches = 0;
@@ -414,6 +424,15 @@ void launch_scatter(const double* src, const int32_t* map, int64_t count, double
                     cudaStream_t s);
 void launch_gather(const double* src, const int32_t* map, int64_t count, double* dst,
                    cudaStream_t s);
+// dst(i, j) = src(map[i], j) for i < rows, j < cols (column-major, leading
+// dimensions lds and ldd, elements of elem_bytes = 4 or 8 bytes)
+void launch_gather_rows(const void* src, int64_t lds, const int32_t* map, int64_t rows,
+                        int64_t cols, void* dst, int64_t ldd, int elem_bytes, cudaStream_t s);
+// Vectors across the entry points (lslu_api.cu): a caller vector (rows: m
+// entries, else n; host or device) into a device vector of the internal
+// numbering, and back.  Plain copies on a handle without a renumbering.
+cudaError_t vec_in(Ctx* c, bool rows, const double* src, bool host, double* dst);
+cudaError_t vec_out(Ctx* c, bool rows, const double* src, bool host, double* dst);
 
 // Projected problem (lslu_projected.cu).
 struct ProjArgs {

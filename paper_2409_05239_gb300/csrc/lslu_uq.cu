@@ -447,19 +447,24 @@ extern "C" lslu_status lslu_uq(lslu_handle h, double sigma2, double lambda, int3
     return fail(c, LSLU_ERR_INVALID_ARG, "sigma2 and lambda must be finite and > 0");
   if (ptr_location != LSLU_HOST && ptr_location != LSLU_DEVICE)
     return fail(c, LSLU_ERR_INVALID_ARG, "unknown ptr_location");
+  // host outputs, and the output of a renumbered handle, are staged on the
+  // device in the internal numbering
+  const bool host = ptr_location == LSLU_HOST;
+  const bool stage = var_diag && (host || c->ord_m);
   double* dd = var_diag;
-  if (var_diag && ptr_location == LSLU_HOST) {
+  if (stage) {
     if (cudaMalloc(&dd, c->n * sizeof(double)) != cudaSuccess)
       return fail(c, LSLU_ERR_OOM, "uq output");
   }
   double sum = 0.0;
   lslu_status st = c->value_type == LSLU_F64 ? uq_impl<double>(c, sigma2, lambda, dd, &sum)
                                              : uq_impl<float>(c, sigma2, lambda, dd, &sum);
-  if (st == LSLU_OK && var_diag && ptr_location == LSLU_HOST) {
-    cudaError_t e = cudaMemcpy(var_diag, dd, c->n * sizeof(double), cudaMemcpyDeviceToHost);
+  if (st == LSLU_OK && stage) {
+    cudaError_t e = vec_out(c, false, dd, host, var_diag);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) st = fail(c, LSLU_ERR_CUDA, cudaGetErrorString(e));
   }
-  if (var_diag && ptr_location == LSLU_HOST) cudaFree(dd);
+  if (stage) cudaFree(dd);
   if (st == LSLU_OK && var_sum) {
     if (ptr_location == LSLU_HOST) {
       *var_sum = sum;

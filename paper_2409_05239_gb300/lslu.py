@@ -28,7 +28,8 @@ EXPORTS = ("lslu_create", "lslu_solve", "lslu_get_state", "lslu_spmv", "lslu_pro
            "lslu_error_string", "lslu_destroy", "lslu_create_batched", "lslu_solve_batched",
            "lslu_adjoint", "lslu_solve_fixed_pivots", "lslu_create_shared",
            "lslu_solve_stopping", "lslu_solve_sampled", "lslu_set_spmv_shape",
-           "lslu_tune_spmv", "lslu_uq", "lslu_solve_optimal", "lslu_spmv_config")
+           "lslu_tune_spmv", "lslu_uq", "lslu_solve_optimal", "lslu_spmv_config",
+           "lslu_create_ordered")
 
 _lib = None
 
@@ -52,6 +53,9 @@ def load(path: str | None = None):
     vp, i32, i64, f64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
     lib.lslu_create.argtypes = [i64, i64, i64, vp, vp, vp, i32, i32, i32, vp, ctypes.POINTER(vp)]
     lib.lslu_create.restype = i32
+    lib.lslu_create_ordered.argtypes = [i64, i64, i64, vp, vp, vp, i32, i32, vp, vp, i32, vp,
+                                        ctypes.POINTER(vp)]
+    lib.lslu_create_ordered.restype = i32
     lib.lslu_solve.argtypes = [vp, vp, vp, i32, i32, f64, i32, vp, vp, vp, vp, vp, vp]
     lib.lslu_solve.restype = i32
     lib.lslu_get_state.argtypes = [vp, i32, vp, vp, vp, vp, vp]
@@ -121,7 +125,7 @@ class Solver:
     """
 
     def __init__(self, m, n, row_ptr, col_idx, vals, value_type="f32", max_iter=300,
-                 stream=None):
+                 stream=None, row_order=None, col_order=None):
         self.lib = load()
         self.m, self.n = int(m), int(n)
         self.value_type = value_type
@@ -134,9 +138,23 @@ class Solver:
             vals = np.ascontiguousarray(vals, dtype=np.float64)
         nnz = int(row_ptr[-1]) if not on_dev else int(row_ptr[-1].item())
         h = ctypes.c_void_p()
-        st = self.lib.lslu_create(self.m, self.n, nnz, _ptr(row_ptr), _ptr(col_idx), _ptr(vals),
-                                  VALUE_TYPES[value_type], self.max_iter,
-                                  DEVICE if on_dev else HOST, stream, ctypes.byref(h))
+        self.ordered = row_order is not None or col_order is not None
+        if self.ordered:  # lslu_create_ordered: orders live where the CSR arrays do
+            if not on_dev:
+                row_order = None if row_order is None else np.ascontiguousarray(row_order,
+                                                                                dtype=np.int32)
+                col_order = None if col_order is None else np.ascontiguousarray(col_order,
+                                                                                dtype=np.int32)
+            st = self.lib.lslu_create_ordered(
+                self.m, self.n, nnz, _ptr(row_ptr), _ptr(col_idx), _ptr(vals),
+                VALUE_TYPES[value_type], self.max_iter,
+                None if row_order is None else _ptr(row_order),
+                None if col_order is None else _ptr(col_order),
+                DEVICE if on_dev else HOST, stream, ctypes.byref(h))
+        else:
+            st = self.lib.lslu_create(self.m, self.n, nnz, _ptr(row_ptr), _ptr(col_idx),
+                                      _ptr(vals), VALUE_TYPES[value_type], self.max_iter,
+                                      DEVICE if on_dev else HOST, stream, ctypes.byref(h))
         if st != OK:
             raise LsluError(st, self.lib.lslu_error_string(None).decode())
         self.h = h
@@ -534,7 +552,10 @@ def shared_rhs(P, nrhs, value_type="f32", max_iter=150, stream=None):
                          max_iter=max_iter, stream=stream, nrhs=nrhs)
 
 
-def from_problem(P, value_type="f32", max_iter=300):
-    """Solver for a tomography problem (paper_2409_05239_gb300.tomo.TomoProblem)."""
+def from_problem(P, value_type="f32", max_iter=300, order=None):
+    """Solver for a tomography problem (paper_2409_05239_gb300.tomo.TomoProblem).
+    order: None (the matrix as numbered) or a (row_order, col_order) pair for
+    lslu_create_ordered, e.g. tomo.locality_order(P)."""
+    ro, co = (None, None) if order is None else order
     return Solver(P.m, P.n, P.row_ptr, P.col_idx, P.vals, value_type=value_type,
-                  max_iter=max_iter)
+                  max_iter=max_iter, row_order=ro, col_order=co)

@@ -3,6 +3,7 @@
     python -m paper_2409_05239_gb300.solve_once --workload ct512 --K 300
     python -m paper_2409_05239_gb300.solve_once --batch 64 --K 150
     python -m paper_2409_05239_gb300.solve_once --workload ct512 --K 2 --shapes all
+    python -m paper_2409_05239_gb300.solve_once --workload ct512 --K 300 --order tiles
 
 The first form builds one seeded problem of the named size (see tomo.CONFIGS)
 and solves it `--repeat` times; the second solves a batch of uneven problems
@@ -12,7 +13,8 @@ directly instead of from a captured CUDA graph.  `--shapes` repeats the
 single-problem solve once per named sparse-product shape (both directions set
 to it; "all" = every shape in lslu.Solver.SHAPES order), so that a profiler sees
 the products of every shape in one process: each solve launches 2 K products,
-A^T d_k then A l_k for k = 0..K-1.
+A^T d_k then A l_k for k = 0..K-1.  `--order tiles` builds the handle with
+tomo.locality_order's renumbering (lslu_create_ordered).
 """
 from __future__ import annotations
 
@@ -33,6 +35,7 @@ def main(argv=None):
     ap.add_argument("--repeat", type=int, default=1)
     ap.add_argument("--batch", type=int, default=0, help="solve this many uneven problems")
     ap.add_argument("--shapes", default="", help="comma-separated shape names, or 'all'")
+    ap.add_argument("--order", default="natural", choices=["natural", "tiles"])
     a = ap.parse_args(argv)
 
     import torch
@@ -61,7 +64,8 @@ def main(argv=None):
         K = a.K or tomo.CONFIGS[a.workload]["K"]
         names = list(lslu.Solver.SHAPES) if a.shapes == "all" else \
             [t for t in a.shapes.split(",") if t]
-        with lslu.from_problem(P, a.value_type, K) as s:
+        order = tomo.locality_order(P) if a.order == "tiles" else None
+        with lslu.from_problem(P, a.value_type, K, order=order) as s:
             runs = []
             for name in names or [None]:
                 if name is not None:
@@ -73,7 +77,7 @@ def main(argv=None):
                 runs.append({"shape": name, "status": r["status"],
                              "seconds_per_solve": (time.perf_counter() - t0) / a.repeat})
             launches = s.last_launch_count()
-        out = {"workload": a.workload, "m": P.m, "n": P.n, "nnz": P.nnz, "K": K,
+        out = {"workload": a.workload, "order": a.order, "m": P.m, "n": P.n, "nnz": P.nnz, "K": K,
                "k_done": r["k_done"], "status": r["status"], "launches": launches,
                "seconds_per_solve": runs[-1]["seconds_per_solve"],
                "rel_err_x_true": float(np.linalg.norm(r["x"] - P.x_true) /

@@ -40,6 +40,7 @@ __all__ = [
     "CONFIGS",
     "round_values",
     "csr_matvec_f64",
+    "locality_order",
 ]
 
 
@@ -143,6 +144,31 @@ def siddon_csr(N: int, n_ang: int, p: int):
     row_ptr = np.zeros(n_ang * p + 1, dtype=np.int64)
     np.cumsum(counts, out=row_ptr[1:])
     return row_ptr, np.concatenate(cols_all), np.concatenate(vals_all)
+
+
+def locality_order(P: "TomoProblem", pixel_tile=(2, 4), ray_tile=(4, 2)):
+    """A renumbering of the unknowns and the rays that keeps neighbours close in
+    memory (for lslu_create_ordered): pixels in tiles of pixel_tile = (w, h)
+    pixels (w along x, h along y), the tiles row by row; rays in tiles of
+    ray_tile = (a, r) = a consecutive angles x r neighbouring rays, the tiles
+    of a block of a angles ray by ray.  A ray then meets a few pixels of each
+    tile it crosses, and a pixel a few rays of each tile of the sinogram.
+    Returns (row_order, col_order), int32: caller row i -> internal row
+    row_order[i], caller column j -> internal column col_order[j].  Partial
+    tiles at the edges are kept whole."""
+    tw, th = pixel_tile
+    wa, wr = ray_tile
+    j = np.arange(P.N * P.N)
+    ix, iy = j % P.N, j // P.N
+    cols = np.lexsort((ix % tw, iy % th, ix // tw, iy // th))
+    i = np.arange(P.n_ang * P.p)
+    a, r = i // P.p, i % P.p
+    rows = np.lexsort((r % wr, a % wa, r // wr, a // wa))
+    col_order = np.empty(P.n, dtype=np.int32)
+    col_order[cols] = np.arange(P.n, dtype=np.int32)
+    row_order = np.empty(P.m, dtype=np.int32)
+    row_order[rows] = np.arange(P.m, dtype=np.int32)
+    return row_order, col_order
 
 
 def ellipse_phantom(N: int, n_ellipses: int, rng: np.random.Generator) -> np.ndarray:

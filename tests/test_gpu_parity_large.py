@@ -3,7 +3,8 @@
 * 256x256 workload (m = 65160, n = 65536, ~15M non-zeros) in FP64 against the
   FP64 oracle: identical pivots, x_K within 1e-10.
 * 512x512 workload (m = 260640, n = 262144, ~120M non-zeros, K = 300, FP32
-  values and basis, GCV) in the launch configuration the benchmark times,
+  values and basis, GCV) in the launch configuration the benchmark times
+  (autotuned shapes; natural numbering and the renumbered handle),
   checked through properties that hold at any size and on sampled outputs the
   oracle computes one by one:
     - exact pivot structure of every basis vector (Algorithm 4);
@@ -69,11 +70,17 @@ def test_ct256_f64_parity():
     assert abs(e_gpu - e_ref) <= 0.08 * e_ref
 
 
-@pytest.fixture(scope="module")
-def ct512_run():
+@pytest.fixture(scope="module", params=["natural", "tiles"])
+def ct512_run(request):
+    """The benchmark's solve: autotuned product shapes, the matrix as numbered
+    or renumbered by tomo.locality_order (lslu_create_ordered; vectors, bases
+    and pivots come back in the natural numbering, so every check below reads
+    the same)."""
     P = tomo.make_config("ct512")
     K = 300
-    with lslu.from_problem(P, "f32", K) as s:
+    order = tomo.locality_order(P) if request.param == "tiles" else None
+    with lslu.from_problem(P, "f32", K, order=order) as s:
+        s.tune_spmv(reps=2)
         r = s.solve(P.b, K, "gcv")
         st = s.state(r["k_done"])
     return P, K, r, st
@@ -119,14 +126,23 @@ def test_ct512_projected_and_recombination(ct512_run):
     assert err < 0.2
 
 
-def test_ct512_mixed_vs_oracle_prefix():
-    """The first 12 iterations of the 512x512 FP32 solve against the FP64 oracle
-    on the same FP32-rounded matrix: identical pivots, x within FP32 tolerance."""
+@pytest.fixture(scope="module")
+def ct512_prefix_ref():
     P = tomo.make_config("ct512")
     K = 12
     A = P.scipy(tomo.round_values(P.vals, "f32"))
-    ref = O.hybrid_lslu(A, P.b, None, K, "gcv", histories=False)
-    with lslu.from_problem(P, "f32", K) as s:
+    return P, K, O.hybrid_lslu(A, P.b, None, K, "gcv", histories=False)
+
+
+@pytest.mark.parametrize("order", ["natural", "tiles"])
+def test_ct512_mixed_vs_oracle_prefix(ct512_prefix_ref, order):
+    """The first 12 iterations of the 512x512 FP32 solve against the FP64 oracle
+    on the same FP32-rounded matrix: identical pivots, x within FP32 tolerance
+    (the renumbered handle too: its pivots, mapped back, can differ only
+    where a search ties)."""
+    P, K, ref = ct512_prefix_ref
+    o = tomo.locality_order(P) if order == "tiles" else None
+    with lslu.from_problem(P, "f32", K, order=o) as s:
         r = s.solve(P.b, K, "gcv")
     assert np.array_equal(r["gp"], ref.gp) and np.array_equal(r["tp"], ref.tp)
     assert rel(r["x"], ref.x) <= 1e-4

@@ -172,3 +172,23 @@ def test_reconstruction_quality(ct32):
     r = O.hybrid_lslu(ct32.scipy(), ct32.b, None, 50, "gcv")
     err = np.linalg.norm(r.x - ct32.x_true) / np.linalg.norm(ct32.x_true)
     assert err < 0.3
+
+
+def test_method_commutes_with_a_renumbering():
+    """Max-abs pivoting picks the same entries whatever the numbering of rows
+    and columns (Algorithm 4), so Hybrid LSLU on P_r A P_c^T with P_r b gives
+    the pivots mapped through the renumbering and x = P_c^T x_hat, up to
+    rounding (the renumbered handle of the CUDA path relies on this)."""
+    from paper_2409_05239_gb300 import tomo
+
+    P = tomo.make_config("ct32")
+    rng = np.random.default_rng(21)
+    for ro, co in (tomo.locality_order(P), (rng.permutation(P.m), rng.permutation(P.n))):
+        ir, ic = np.argsort(ro), np.argsort(co)
+        Ah = P.scipy()[ir][:, ic].tocsr()
+        for rule, lam in (("gcv", 0.0), ("fixed", 1e-2)):
+            ref = O.hybrid_lslu(P.scipy(), P.b, None, 40, rule, lam)
+            alt = O.hybrid_lslu(Ah, P.b[ir], None, 40, rule, lam)
+            assert np.array_equal(ic[alt.gp], ref.gp) and np.array_equal(ir[alt.tp], ref.tp)
+            assert np.linalg.norm(alt.x[co] - ref.x) <= 1e-12 * np.linalg.norm(ref.x)
+            assert np.allclose(alt.H, ref.H, rtol=0, atol=1e-12 * np.abs(ref.H).max())

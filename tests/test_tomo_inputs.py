@@ -98,3 +98,30 @@ def test_round_values_bf16_matches_torch():
     ref = torch.tensor(v.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
     assert np.array_equal(mine, ref)
     assert np.array_equal(tomo.round_values(v, "f32"), v.astype(np.float32).astype(np.float64))
+
+
+@pytest.mark.parametrize("N,n_ang,p", [(32, 45, 46), (13, 7, 19)])
+def test_locality_order_tiles(N, n_ang, p):
+    """Both orders are permutations; away from the edges the 2x4 pixels of a
+    tile, and the 4 angles x 2 rays of a sinogram tile, take consecutive
+    internal indices (partial tiles at ragged edges stay whole)."""
+    P = tomo.make_problem(N, n_ang, p, 3, 0.01, seed=1)
+    ro, co = tomo.locality_order(P)
+    assert ro.dtype == np.int32 and co.dtype == np.int32
+    assert np.array_equal(np.sort(ro), np.arange(P.m))
+    assert np.array_equal(np.sort(co), np.arange(P.n))
+    # pixel j = iy*N + ix; tile (tx, ty) covers ix in [2tx, 2tx+2), iy in [4ty, 4ty+4)
+    for ty in range(N // 4):
+        for tx in range(N // 2):
+            idx = [co[(4 * ty + dy) * N + 2 * tx + dx] for dy in range(4) for dx in range(2)]
+            assert idx == list(range(idx[0], idx[0] + 8))
+    for ta in range(n_ang // 4):
+        for tr in range(p // 2):
+            idx = [ro[(4 * ta + da) * p + 2 * tr + dr] for da in range(4) for dr in range(2)]
+            assert idx == list(range(idx[0], idx[0] + 8))
+    # every partial tile is contiguous too
+    cells = {}
+    for j in range(P.n):
+        cells.setdefault(((j // N) // 4, (j % N) // 2), []).append(co[j])
+    for v in cells.values():
+        assert sorted(v) == list(range(min(v), min(v) + len(v)))
