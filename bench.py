@@ -98,17 +98,27 @@ SPMV_TRAFFIC = {
     "workload": "ct512", "value_type": "f32",
     "bytes": {
         "natural": {
-            "16x2": (972.70e6, 973.45e6), "32x1": (972.07e6, 972.30e6),
-            "16x1": (978.26e6, 972.56e6), "8x1": (1004.54e6, 1019.91e6),
-            "8x2": (997.52e6, 987.51e6), "4x1": (1011.15e6, 1022.54e6),
-            "16x2/16-bit": (800.20e6, 795.82e6), "32x1/16-bit": (791.73e6, 790.82e6),
-            "16x1/16-bit": (804.95e6, 809.92e6), "8x1/16-bit": (854.82e6, 905.99e6),
-            "8x2/16-bit": (831.94e6, 831.80e6), "4x1/16-bit": (919.27e6, 897.39e6),
-            "tma": (971.81e6, 972.55e6), "tma/16-bit": (790.36e6, 790.95e6),
-            "32x8e": (971.91e6, 972.32e6), "32x8e/16-bit": (791.31e6, 791.01e6),
-            "32x4e": (971.91e6, 972.26e6), "32x4e/16-bit": (793.64e6, 791.88e6),
+            "16x2": (972.51e6, 973.58e6), "32x1": (971.85e6, 972.36e6),
+            "16x1": (978.17e6, 972.60e6), "8x1": (1004.53e6, 1019.86e6),
+            "8x2": (997.54e6, 987.57e6), "4x1": (1011.43e6, 1022.51e6),
+            "16x2/16-bit": (800.24e6, 795.82e6), "32x1/16-bit": (791.90e6, 790.79e6),
+            "16x1/16-bit": (804.77e6, 809.98e6), "8x1/16-bit": (854.16e6, 904.92e6),
+            "8x2/16-bit": (831.69e6, 831.87e6), "4x1/16-bit": (918.48e6, 896.70e6),
+            "tma": (971.89e6, 972.49e6), "tma/16-bit": (790.35e6, 790.94e6),
+            "32x8e": (971.89e6, 972.31e6), "32x8e/16-bit": (791.28e6, 791.08e6),
+            "32x4e": (971.87e6, 972.48e6), "32x4e/16-bit": (793.57e6, 792.07e6),
         },
-        "tiles": {},
+        "tiles": {
+            "16x2": (972.35e6, 973.46e6), "32x1": (972.03e6, 972.34e6),
+            "16x1": (978.15e6, 972.47e6), "8x1": (1005.36e6, 1020.24e6),
+            "8x2": (998.21e6, 994.45e6), "4x1": (1012.09e6, 1021.81e6),
+            "16x2/16-bit": (799.92e6, 795.88e6), "32x1/16-bit": (791.51e6, 790.75e6),
+            "16x1/16-bit": (804.48e6, 810.03e6), "8x1/16-bit": (855.46e6, 928.89e6),
+            "8x2/16-bit": (832.36e6, 837.88e6), "4x1/16-bit": (930.94e6, 892.59e6),
+            "tma": (971.70e6, 972.70e6), "tma/16-bit": (790.24e6, 791.18e6),
+            "32x8e": (971.88e6, 972.30e6), "32x8e/16-bit": (791.37e6, 790.98e6),
+            "32x4e": (971.91e6, 972.29e6), "32x4e/16-bit": (793.58e6, 791.85e6),
+        },
     },
     "sources": {
         "paper_2409_05239_gb300/csrc/lslu_spmv.cu":
@@ -124,7 +134,7 @@ SPMV_TRAFFIC = {
         "paper_2409_05239_gb300/csrc/lslu_spmv_tma.cu":
             "3258c2e4fb82c38ccf340c4f48253dc396e784b74b1ebbdd43ae8083ee84199c",
         "paper_2409_05239_gb300/csrc/lslu_internal.cuh":
-            "a91f78e3e75890c8a7992b0171c3bf0057f172a3142c404de587197edeea226e",
+            "2275773d234adb9dffd8b8c30374292cdf88b8a70a9ac3da2d50aad2ab8a9759",
     },
 }
 
