@@ -757,7 +757,7 @@ lslu_status solve_entry(Ctx* c, const double* b, const double* x0, int32_t K, in
     cudaError_t e = cudaMemcpyAsync(v.data(), src, (size_t)cnt * 4, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return e;
-    for (int32_t& x : v) x = inv[x];
+    for (int32_t& x : v) x = (x >= 0 && x < (int32_t)inv.size()) ? inv[x] : -1;
     e = cudaMemcpyAsync(dst, v.data(), (size_t)cnt * 4,
                         host ? cudaMemcpyHostToHost : cudaMemcpyHostToDevice, s);
     return e == cudaSuccess ? cudaStreamSynchronize(s) : e;

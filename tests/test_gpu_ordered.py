@@ -206,3 +206,53 @@ def test_ct256_f64_renumbered_matches_natural():
         r1 = s1.solve(P.b, K, "gcv")
     assert np.array_equal(r0["gp"], r1["gp"]) and np.array_equal(r0["tp"], r1["tp"])
     assert rel(r1["x"], r0["x"]) <= 1e-10
+
+
+def test_breakdowns_renumbered(ct32):
+    """b = 0 breaks down before the first iteration; and the hand-worked W-step
+    breakdown of the oracle pins (A = diag(1, 2) padded to 4 x 3, b = ones)
+    with both numberings reversed: the first row pivot is a four-way tie, so
+    it goes to the lowest internal index (caller row 3, a zero row of A), and
+    the solve follows the oracle run on the renumbered problem, not the
+    natural one."""
+    ro, co = orders(ct32, "random", seed=9)
+    with lslu.from_problem(ct32, "f64", 5, order=(ro, co)) as s:
+        r = s.solve(np.zeros(ct32.m), 5, "gcv")
+    assert r["status"] == lslu.BREAKDOWN_BETA and r["k_done"] == 0
+    assert np.all(r["x"] == 0.0) and np.all(r["gp"] == -1) and np.all(r["tp"] == -1)
+    rp = np.array([0, 1, 2, 2, 2], dtype=np.int64)
+    ci = np.array([0, 1], dtype=np.int32)
+    Ad = np.zeros((4, 3))
+    Ad[0, 0], Ad[1, 1] = 1.0, 2.0
+    ro = np.array([3, 2, 1, 0], np.int32)
+    co = np.array([2, 1, 0], np.int32)
+    ir, ic = np.argsort(ro), np.argsort(co)
+    ref = O.hybrid_lslu(Ad[ir][:, ic], np.ones(4), None, 5, "none")
+    with lslu.Solver(4, 3, rp, ci, np.array([1.0, 2.0]), "f64", 5, row_order=ro,
+                     col_order=co) as s:
+        r = s.solve(np.ones(4), 5, "none")
+    assert r["status"] == ref.status == lslu.BREAKDOWN_W and r["k_done"] == ref.k_done == 2
+    assert r["gp"].tolist() == ic[ref.gp].tolist() + [-1] * 3
+    assert r["tp"].tolist() == ir[ref.tp].tolist() + [-1] * 3
+    assert r["tp"][0] == 3
+    assert np.allclose(r["x"], ref.x[co], rtol=0, atol=1e-14)
+
+
+def test_device_csr_and_orders(ct32):
+    """CSR arrays and both orders in device memory (ptr_location = device)."""
+    import torch
+
+    dev = torch.device("cuda", 0)
+    ro, co = orders(ct32, "random", seed=13)
+
+    def t(a, dt):
+        return torch.from_numpy(np.ascontiguousarray(a, dtype=dt)).to(dev)
+
+    with lslu.Solver(ct32.m, ct32.n, t(ct32.row_ptr, np.int64), t(ct32.col_idx, np.int32),
+                     t(ct32.vals, np.float64), "f64", 20, row_order=t(ro, np.int32),
+                     col_order=t(co, np.int32)) as s_dev, \
+            lslu.from_problem(ct32, "f64", 20, order=(ro, co)) as s_host:
+        a = s_dev.solve(ct32.b, 20, "gcv")
+        b = s_host.solve(ct32.b, 20, "gcv")
+    assert np.array_equal(a["x"], b["x"])
+    assert np.array_equal(a["gp"], b["gp"]) and np.array_equal(a["tp"], b["tp"])
