@@ -314,12 +314,14 @@ def precision_study(P, K, rule, dev, x_main, main_vt, order=(None, None)):
     return res
 
 
-def batched_study(dev, K=150, count=64):
+def batched_study(dev, K=150, count=64, order="tiles"):
     """Batched solves: `count` independent problems of uneven size (image side
     64..256, 30..180 angles, 1.41 N rays, own phantom and noise level in
     [0.5%, 3%]) solved together by one launch sequence (FP32, GCV, K
     iterations each), against the same problems solved one after another
-    with single-problem handles."""
+    with single-problem handles; every problem renumbered by
+    tomo.locality_order when order == "tiles" (the batch in the natural
+    numbering is timed beside it)."""
     import torch
 
     from paper_2409_05239_gb300 import lslu
@@ -330,7 +332,8 @@ def batched_study(dev, K=150, count=64):
     b_dev = torch.from_numpy(b).to(dev)
     x_dev = torch.empty(sum(P.n for P in Ps), dtype=torch.float64, device=dev)
     kd_dev = torch.empty(count, dtype=torch.int32, device=dev)
-    bs = lslu.from_problems(Ps, "f32", K, stream=stream.cuda_stream)
+    orders = [tomo.locality_order(P) for P in Ps] if order == "tiles" else None
+    bs = lslu.from_problems(Ps, "f32", K, stream=stream.cuda_stream, orders=orders)
 
     def timed(fn, reps):
         fn()
@@ -349,8 +352,16 @@ def batched_study(dev, K=150, count=64):
     x = x_dev.cpu().numpy()
     kd = kd_dev.cpu().numpy()
     bs.close()
+    ms_nat = None
+    if orders is not None:
+        bn = lslu.from_problems(Ps, "f32", K, stream=stream.cuda_stream)
+        ms_nat = timed(lambda: bn.solve_device(b_dev, x_dev, K, "gcv", k_done=kd_dev), 3)
+        bn.close()
     singles = [lslu.Solver(P.m, P.n, P.row_ptr, P.col_idx, P.vals, "f32", K,
-                           stream=stream.cuda_stream) for P in Ps]
+                           stream=stream.cuda_stream,
+                           row_order=None if orders is None else orders[p][0],
+                           col_order=None if orders is None else orders[p][1])
+               for p, P in enumerate(Ps)]
     bd = [torch.from_numpy(P.b).to(dev) for P in Ps]
     xd = [torch.empty(P.n, dtype=torch.float64, device=dev) for P in Ps]
 
@@ -372,7 +383,9 @@ def batched_study(dev, K=150, count=64):
     nbytes = sum(solve_bytes(P, "f32", K) for P in Ps)
     return {"problems": count, "K": K, "m_total": int(sum(P.m for P in Ps)),
             "n_total": int(sum(P.n for P in Ps)), "nnz_total": int(sum(P.nnz for P in Ps)),
-            "ms_per_batch_solve": ms_b, "problem_iter_per_s": iters / (ms_b / 1e3),
+            "numbering": ORDER_NOTE[order], "ms_per_batch_solve": ms_b,
+            "ms_per_batch_solve_natural_numbering": ms_nat,
+            "problem_iter_per_s": iters / (ms_b / 1e3),
             "hbm_gbs_solve": nbytes / (ms_b * 1e-3) / 1e9,
             "kernel_launches_per_batch_solve": launches,
             "sequential_single_ms": ms_s, "speedup_vs_sequential": ms_s / ms_b,
@@ -665,7 +678,7 @@ def run_gpu(args):
     if rank == 0 and not args.no_extras and world == 1:
         out["precision_study"] = precision_study(P, K, rule, dev, x, args.value_type, (ro, co))
     if rank == 0 and not args.no_extras and world == 1:
-        out["batched_study"] = batched_study(dev)
+        out["batched_study"] = batched_study(dev, order=args.order)
         out["shared_rhs_study"] = shared_rhs_study(dev)
         out["adjoint_study"] = adjoint_study(dev)
     if rank == 0 and not args.no_cpu_baseline and world == 1:

@@ -140,6 +140,22 @@ lslu_status lslu_create_batched(int32_t nprob, const int64_t* row_off, const int
                                 const double* vals, int32_t value_type, int32_t max_iter,
                                 void* cuda_stream, lslu_handle* out);
 
+/* lslu_create_batched with every problem renumbered for memory locality, as
+ * lslu_create_ordered does for one problem.  row_order (row_off[nprob] int32)
+ * and col_order (col_off[nprob] int32), host memory, are permutations of the
+ * concatenated rows and columns that map each problem's range onto itself:
+ * caller row i becomes internal row row_order[i]; NULL is the identity.
+ * lslu_solve_batched takes b and returns x and the pivot indices in the
+ * caller's numbering; a tie of a pivot search goes to the lower internal
+ * index.  Errors: those of lslu_create_batched, and LSLU_ERR_INVALID_ARG when
+ * an order is not a permutation or moves an index out of its problem. */
+lslu_status lslu_create_batched_ordered(int32_t nprob, const int64_t* row_off,
+                                        const int64_t* col_off, const int64_t* row_ptr,
+                                        const int32_t* col_idx, const double* vals,
+                                        int32_t value_type, int32_t max_iter,
+                                        const int32_t* row_order, const int32_t* col_order,
+                                        void* cuda_stream, lslu_handle* out);
+
 /* A batched handle for nrhs right-hand sides that share one m x n CSR matrix
  * (row_ptr m+1 int64, col_idx int32 in [0, n), vals FP64; host memory).  The
  * matrix and its transpose are stored once, and every sparse product reads

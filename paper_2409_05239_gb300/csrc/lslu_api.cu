@@ -876,11 +876,13 @@ lslu_status upload_batch_layout(lslu_ctx* c, const std::vector<int32_t>& tpm,
 
 }  // namespace
 
-extern "C" lslu_status lslu_create_batched(int32_t nprob, const int64_t* row_off,
-                                           const int64_t* col_off, const int64_t* row_ptr,
-                                           const int32_t* col_idx, const double* vals,
-                                           int32_t value_type, int32_t max_iter,
-                                           void* cuda_stream, lslu_handle* out) {
+namespace {
+
+lslu_status create_batched_impl(int32_t nprob, const int64_t* row_off, const int64_t* col_off,
+                                const int64_t* row_ptr, const int32_t* col_idx,
+                                const double* vals, int32_t value_type, int32_t max_iter,
+                                const int32_t* row_order, const int32_t* col_order,
+                                void* cuda_stream, lslu_handle* out) {
   if (!out) return set_err(nullptr, LSLU_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   if (nprob < 1 || !row_off || !col_off || !row_ptr)
@@ -898,6 +900,55 @@ extern "C" lslu_status lslu_create_batched(int32_t nprob, const int64_t* row_off
   const int64_t nnz = row_ptr[mu];
   if (nnz < 0 || nnz >= (int64_t)INT32_MAX || row_ptr[0] != 0 || (nnz > 0 && (!col_idx || !vals)))
     return set_err(nullptr, LSLU_ERR_INVALID_ARG, "invalid CSR (row_ptr[0] != 0 or nnz)");
+  // renumbering: each problem's rows and columns onto themselves; the rest of
+  // the layout is built from the renumbered CSR, and the caller -> padded maps
+  // are composed with the orders below
+  const bool ordered = row_order || col_order;
+  std::vector<int32_t> om, on, im, in;
+  std::vector<int64_t> rp_o;
+  std::vector<int32_t> ci_o;
+  std::vector<double> vv_o;
+  if (ordered) {
+    lslu_status st0 = read_order(row_order, mu, false, om, im, "row_order");
+    if (st0 == LSLU_OK) st0 = read_order(col_order, nu, false, on, in, "col_order");
+    if (st0 != LSLU_OK) return st0;
+    for (int p = 0; p < nprob; ++p) {
+      for (int64_t r = row_off[p]; r < row_off[p + 1]; ++r)
+        if (om[r] < row_off[p] || om[r] >= row_off[p + 1])
+          return set_err(nullptr, LSLU_ERR_INVALID_ARG,
+                         "row_order must map every problem's rows onto themselves");
+      for (int64_t j = col_off[p]; j < col_off[p + 1]; ++j)
+        if (on[j] < col_off[p] || on[j] >= col_off[p + 1])
+          return set_err(nullptr, LSLU_ERR_INVALID_ARG,
+                         "col_order must map every problem's columns onto themselves");
+    }
+    for (int64_t r = 0; r < mu; ++r)
+      if (row_ptr[r + 1] < row_ptr[r])
+        return set_err(nullptr, LSLU_ERR_INVALID_ARG, "row_ptr is not monotone");
+    for (int64_t e = 0; e < nnz; ++e)
+      if (col_idx[e] < 0 || col_idx[e] >= nu)
+        return set_err(nullptr, LSLU_ERR_INVALID_ARG,
+                       "column index outside its problem's column range");
+    rp_o.assign(mu + 1, 0);
+    for (int64_t r = 0; r < mu; ++r) rp_o[r + 1] = rp_o[r] + (row_ptr[im[r] + 1] - row_ptr[im[r]]);
+    ci_o.resize(nnz);
+    vv_o.resize(nnz);
+    std::vector<uint64_t> key;
+    for (int64_t r = 0; r < mu; ++r) {
+      const int64_t a = row_ptr[im[r]], len = row_ptr[im[r] + 1] - a, o = rp_o[r];
+      key.resize(len);
+      for (int64_t i = 0; i < len; ++i)
+        key[i] = ((uint64_t)(uint32_t)on[col_idx[a + i]] << 32) | (uint64_t)i;
+      std::sort(key.begin(), key.end());
+      for (int64_t i = 0; i < len; ++i) {
+        ci_o[o + i] = (int32_t)(key[i] >> 32);
+        vv_o[o + i] = vals[a + (int64_t)(key[i] & 0xffffffffull)];
+      }
+    }
+    row_ptr = rp_o.data();
+    col_idx = ci_o.data();
+    vals = vv_o.data();
+  }
   // padded layout: every problem starts on a kTile boundary of both spaces
   std::vector<int64_t> rb(nprob), cb(nprob);
   int64_t mp = 0, np = 0;
@@ -951,6 +1002,13 @@ extern "C" lslu_status lslu_create_batched(int32_t nprob, const int64_t* row_off
     for (int64_t t = cb[p] / kTile; t < cend / kTile; ++t) tpn[t] = p;
   }
   for (; prow < mp; ++prow) rp[prow + 1] = (int64_t)ci.size();
+  if (ordered) {  // caller index -> internal index -> padded position
+    std::vector<int32_t> mm(mu), mn(nu);
+    for (int64_t r = 0; r < mu; ++r) mm[r] = map_m[om[r]];
+    for (int64_t j = 0; j < nu; ++j) mn[j] = map_n[on[j]];
+    map_m.swap(mm);
+    map_n.swap(mn);
+  }
 
   lslu_ctx* c = new lslu_ctx();
   c->nprob = nprob;
@@ -972,8 +1030,35 @@ extern "C" lslu_status lslu_create_batched(int32_t nprob, const int64_t* row_off
   if (st != LSLU_OK) return st;
   st = upload_batch_layout(c, tpm, tpn, pad_m, pad_n, map_m, map_n, mvec);
   if (st != LSLU_OK) return st;
+  if (ordered) {  // for the pivot indices
+    c->inv_m_h.swap(im);
+    c->inv_n_h.swap(in);
+  }
   *out = c;
   return LSLU_OK;
+}
+
+}  // namespace
+
+extern "C" lslu_status lslu_create_batched(int32_t nprob, const int64_t* row_off,
+                                           const int64_t* col_off, const int64_t* row_ptr,
+                                           const int32_t* col_idx, const double* vals,
+                                           int32_t value_type, int32_t max_iter,
+                                           void* cuda_stream, lslu_handle* out) {
+  return create_batched_impl(nprob, row_off, col_off, row_ptr, col_idx, vals, value_type,
+                             max_iter, nullptr, nullptr, cuda_stream, out);
+}
+
+extern "C" lslu_status lslu_create_batched_ordered(int32_t nprob, const int64_t* row_off,
+                                                   const int64_t* col_off,
+                                                   const int64_t* row_ptr,
+                                                   const int32_t* col_idx, const double* vals,
+                                                   int32_t value_type, int32_t max_iter,
+                                                   const int32_t* row_order,
+                                                   const int32_t* col_order,
+                                                   void* cuda_stream, lslu_handle* out) {
+  return create_batched_impl(nprob, row_off, col_off, row_ptr, col_idx, vals, value_type,
+                             max_iter, row_order, col_order, cuda_stream, out);
 }
 
 extern "C" lslu_status lslu_create_shared(int64_t m, int64_t n, const int64_t* row_ptr,
@@ -1088,6 +1173,9 @@ extern "C" lslu_status lslu_solve_batched(lslu_handle h, const double* b, int32_
   CK(cudaMemcpyAsync(t.data(), c->tp, t.size() * 4, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   std::vector<int32_t> go((size_t)P * K), to((size_t)P * (K + 1)), kd(P), sv(P);
+  // a renumbered batch: internal local index -> caller local index
+  const bool ord = !c->inv_m_h.empty();
+  int64_t uro = 0, uco = 0;  // the problem's offsets in the caller's rows and columns
   for (int p = 0; p < P; ++p) {
     const DevState& ds = c->st_host[p];
     const int kdp = ds.k_done < 0 ? 0 : (ds.k_done > K ? K : ds.k_done);
@@ -1096,12 +1184,18 @@ extern "C" lslu_status lslu_solve_batched(lslu_handle h, const double* b, int32_
     const int nt = ds.status == LSLU_BREAKDOWN_BETA ? 0 : kdp + 1;
     for (int j = 0; j < K; ++j) {
       const int32_t v = g[(size_t)p * c->kmax + j];
-      go[(size_t)p * K + j] = (j < kdp && v >= 0) ? (int32_t)(v - c->col_base[p]) : -1;
+      int32_t l = (j < kdp && v >= 0) ? (int32_t)(v - c->col_base[p]) : -1;
+      if (ord && l >= 0) l = (int32_t)(c->inv_n_h[uco + l] - uco);
+      go[(size_t)p * K + j] = l;
     }
     for (int j = 0; j <= K; ++j) {
       const int32_t v = t[(size_t)p * (c->kmax + 1) + j];
-      to[(size_t)p * (K + 1) + j] = (j < nt && v >= 0) ? (int32_t)(v - c->row_base[p]) : -1;
+      int32_t l = (j < nt && v >= 0) ? (int32_t)(v - c->row_base[p]) : -1;
+      if (ord && l >= 0) l = (int32_t)(c->inv_m_h[uro + l] - uro);
+      to[(size_t)p * (K + 1) + j] = l;
     }
+    uro += c->prob_m[p];
+    uco += c->prob_n[p];
   }
   const cudaMemcpyKind h2o = host ? cudaMemcpyHostToHost : cudaMemcpyHostToDevice;
   if (col_pivots) CK(cudaMemcpyAsync(col_pivots, go.data(), go.size() * 4, h2o, s));

@@ -29,7 +29,7 @@ EXPORTS = ("lslu_create", "lslu_solve", "lslu_get_state", "lslu_spmv", "lslu_pro
            "lslu_adjoint", "lslu_solve_fixed_pivots", "lslu_create_shared",
            "lslu_solve_stopping", "lslu_solve_sampled", "lslu_set_spmv_shape",
            "lslu_tune_spmv", "lslu_uq", "lslu_solve_optimal", "lslu_spmv_config",
-           "lslu_create_ordered")
+           "lslu_create_ordered", "lslu_create_batched_ordered")
 
 _lib = None
 
@@ -56,6 +56,9 @@ def load(path: str | None = None):
     lib.lslu_create_ordered.argtypes = [i64, i64, i64, vp, vp, vp, i32, i32, vp, vp, i32, vp,
                                         ctypes.POINTER(vp)]
     lib.lslu_create_ordered.restype = i32
+    lib.lslu_create_batched_ordered.argtypes = [i32, vp, vp, vp, vp, vp, i32, i32, vp, vp, vp,
+                                                ctypes.POINTER(vp)]
+    lib.lslu_create_batched_ordered.restype = i32
     lib.lslu_solve.argtypes = [vp, vp, vp, i32, i32, f64, i32, vp, vp, vp, vp, vp, vp]
     lib.lslu_solve.restype = i32
     lib.lslu_get_state.argtypes = [vp, i32, vp, vp, vp, vp, vp]
@@ -384,11 +387,16 @@ class BatchedSolver:
     """One handle over several independent problems solved by one launch
     sequence (lslu_create_batched).  csr_list holds (m, n, row_ptr, col_idx,
     vals) per problem in the problem's own index space; they are stacked into
-    one block-diagonal host CSR here (marshalling only)."""
+    one block-diagonal host CSR here (marshalling only).  orders: None, or one
+    (row_order, col_order) pair per problem in its own index space (either may
+    be None), stacked into the global orders of lslu_create_batched_ordered."""
 
-    def __init__(self, csr_list, value_type="f32", max_iter=150, stream=None, nrhs=None):
+    def __init__(self, csr_list, value_type="f32", max_iter=150, stream=None, nrhs=None,
+                 orders=None):
         self.lib = load()
         if nrhs is not None:  # one matrix shared by nrhs right-hand sides
+            if orders is not None:
+                raise ValueError("a shared-matrix batch takes no renumbering")
             m, n, rp, ci, vv = csr_list
             self._init_shared(int(m), int(n), rp, ci, vv, int(nrhs), value_type, max_iter,
                               stream)
@@ -412,10 +420,22 @@ class BatchedSolver:
         col_idx = np.ascontiguousarray(np.concatenate(cis), dtype=np.int32)
         vals = np.ascontiguousarray(np.concatenate(vvs), dtype=np.float64)
         h = ctypes.c_void_p()
-        st = self.lib.lslu_create_batched(self.nprob, _ptr(self.row_off), _ptr(self.col_off),
-                                          _ptr(row_ptr), _ptr(col_idx), _ptr(vals),
-                                          VALUE_TYPES[value_type], self.max_iter, stream,
-                                          ctypes.byref(h))
+        if orders is not None:
+            def stack(k, off):
+                return np.ascontiguousarray(np.concatenate([
+                    (np.arange(off[p + 1] - off[p]) if o[k] is None else np.asarray(o[k]))
+                    + off[p] for p, o in enumerate(orders)]), dtype=np.int32)
+
+            ro, co = stack(0, self.row_off), stack(1, self.col_off)
+            st = self.lib.lslu_create_batched_ordered(
+                self.nprob, _ptr(self.row_off), _ptr(self.col_off), _ptr(row_ptr), _ptr(col_idx),
+                _ptr(vals), VALUE_TYPES[value_type], self.max_iter, _ptr(ro), _ptr(co), stream,
+                ctypes.byref(h))
+        else:
+            st = self.lib.lslu_create_batched(self.nprob, _ptr(self.row_off), _ptr(self.col_off),
+                                              _ptr(row_ptr), _ptr(col_idx), _ptr(vals),
+                                              VALUE_TYPES[value_type], self.max_iter, stream,
+                                              ctypes.byref(h))
         if st != OK:
             raise LsluError(st, self.lib.lslu_error_string(None).decode())
         self.h = h
@@ -532,10 +552,11 @@ def hybrid_lslu(solver, b, log_lam, K):
     return _solve_function().apply(b, log_lam, solver, int(K))
 
 
-def from_problems(Ps, value_type="f32", max_iter=150, stream=None):
-    """Batched solver over several tomography problems."""
+def from_problems(Ps, value_type="f32", max_iter=150, stream=None, orders=None):
+    """Batched solver over several tomography problems; orders as BatchedSolver's
+    (e.g. [tomo.locality_order(P) for P in Ps])."""
     return BatchedSolver([(P.m, P.n, P.row_ptr, P.col_idx, P.vals) for P in Ps],
-                         value_type=value_type, max_iter=max_iter, stream=stream)
+                         value_type=value_type, max_iter=max_iter, stream=stream, orders=orders)
 
 
 def sample_table(K, s, m, n, seed):

@@ -151,3 +151,45 @@ def test_shared_matrix_breakdown_is_local():
     for p in (0, 2, 3):
         s = single(Ps[p], "f32", 12, "wgcv")
         assert np.array_equal(r["x"][p], s["x"])
+
+
+@pytest.mark.parametrize("kind", ["tiles", "random"])
+def test_batched_renumbered_equals_single_renumbered(small_batch, kind):
+    """lslu_create_batched_ordered: every problem renumbered inside its own
+    range gives, bit for bit, the single-problem renumbered handle's solve
+    (same stored rows, same kernels), with x and pivots in the caller's
+    numbering."""
+    K = 30
+    rng = np.random.default_rng(31)
+    orders = [tomo.locality_order(P) if kind == "tiles" else
+              (rng.permutation(P.m), rng.permutation(P.n)) for P in small_batch]
+    b = np.concatenate([P.b for P in small_batch])
+    with lslu.from_problems(small_batch, "f32", K, orders=orders) as bs:
+        r = bs.solve(b, K, "gcv")
+    with lslu.from_problems(small_batch, "f32", K) as bn:
+        r0 = bn.solve(b, K, "gcv")
+    for p, P in enumerate(small_batch):
+        with lslu.from_problem(P, "f32", K, order=orders[p]) as s:
+            q = s.solve(P.b, K, "gcv")
+        assert r["status"][p] == q["status"] and r["k_done"][p] == q["k_done"]
+        assert np.array_equal(r["gp"][p], q["gp"]) and np.array_equal(r["tp"][p], q["tp"])
+        assert np.array_equal(r["x"][p], q["x"]), p
+        # and, with no tied pivot search, the natural batch up to FP32 rounding
+        # (each is within 2e-4 of the FP64 oracle, test_batched_vs_oracle)
+        assert np.array_equal(r["gp"][p][:5], r0["gp"][p][:5])
+        assert rel(r["x"][p], r0["x"][p]) <= 4e-4
+
+
+def test_batched_order_must_stay_in_its_problem(small_batch):
+    """A permutation that swaps row 0 of problem 0 with row 0 of problem 1 is
+    refused; so is a renumbering of a shared-matrix batch."""
+    P0, P1 = small_batch[0], small_batch[1]
+    ro0 = np.arange(P0.m)
+    ro0[0] = P0.m  # stacked with offset 0: global row P0.m (problem 1)
+    ro1 = np.arange(P1.m)
+    ro1[0] = -P0.m  # stacked with offset P0.m: global row 0 (problem 0)
+    with pytest.raises(lslu.LsluError, match="onto themselves"):
+        lslu.from_problems([P0, P1], "f32", 5, orders=[(ro0, None), (ro1, None)])
+    with pytest.raises(ValueError):
+        lslu.BatchedSolver((P0.m, P0.n, P0.row_ptr, P0.col_idx, P0.vals), nrhs=2,
+                           orders=[(None, None)])
