@@ -447,18 +447,21 @@ def shared_rhs_study(dev, K=150, nrhs=16):
             "identical_to_block_diagonal": same_bd}
 
 
-def adjoint_study(dev, K=100):
+def adjoint_study(dev, K=100, order="tiles"):
     """Differentiable solve on the 256x256 workload (FP32, fixed lambda = the
-    GCV choice at K): time of the forward solve and of the reverse-mode
-    derivative (lslu_adjoint) on the device, and the log-lambda derivative
-    against central differences of solves with the pivots replayed."""
+    GCV choice at K; renumbered by tomo.locality_order when order == "tiles"):
+    time of the forward solve and of the reverse-mode derivative
+    (lslu_adjoint) on the device, and the log-lambda derivative against
+    central differences of solves with the pivots replayed."""
     import torch
 
     from paper_2409_05239_gb300 import lslu
 
     P = tomo.make_config("ct256")
     stream = torch.cuda.current_stream(dev)
-    s = lslu.Solver(P.m, P.n, P.row_ptr, P.col_idx, P.vals, "f32", K, stream=stream.cuda_stream)
+    ro, co = tomo.locality_order(P) if order == "tiles" else (None, None)
+    s = lslu.Solver(P.m, P.n, P.row_ptr, P.col_idx, P.vals, "f32", K, stream=stream.cuda_stream,
+                    row_order=ro, col_order=co)
     lam = float(s.solve(P.b, K, "gcv", histories=True)["lam_hist"][-1])
     b_dev = torch.from_numpy(P.b).to(dev)
     x_dev = torch.empty(P.n, dtype=torch.float64, device=dev)
@@ -499,6 +502,7 @@ def adjoint_study(dev, K=100):
     g = adj["lambda_bar"] * lam
     s.close()
     return {"workload": "ct256 (m=%d, n=%d), FP32, K=%d, lambda=%.4g (GCV at K)" % (P.m, P.n, K, lam),
+            "numbering": ORDER_NOTE[order],
             "forward_ms": ms_f, "backward_ms": ms_b, "backward_over_forward": ms_b / ms_f,
             "dJ_dloglam_adjoint": g, "dJ_dloglam_fd": fd,
             "dJ_dloglam_rel_err_vs_fd": abs(g - fd) / abs(fd)}
@@ -680,7 +684,7 @@ def run_gpu(args):
     if rank == 0 and not args.no_extras and world == 1:
         out["batched_study"] = batched_study(dev, order=args.order)
         out["shared_rhs_study"] = shared_rhs_study(dev)
-        out["adjoint_study"] = adjoint_study(dev)
+        out["adjoint_study"] = adjoint_study(dev, order=args.order)
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         out["cpu_baseline"] = cpu_baseline(P, K, args.cpu_sample_s)
     if rank == 0:
