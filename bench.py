@@ -98,26 +98,26 @@ SPMV_TRAFFIC = {
     "workload": "ct512", "value_type": "f32",
     "bytes": {
         "natural": {
-            "16x2": (972.51e6, 973.58e6), "32x1": (971.85e6, 972.36e6),
-            "16x1": (978.17e6, 972.60e6), "8x1": (1004.53e6, 1019.86e6),
-            "8x2": (997.54e6, 987.57e6), "4x1": (1011.43e6, 1022.51e6),
-            "16x2/16-bit": (800.24e6, 795.82e6), "32x1/16-bit": (791.90e6, 790.79e6),
-            "16x1/16-bit": (804.77e6, 809.98e6), "8x1/16-bit": (854.16e6, 904.92e6),
-            "8x2/16-bit": (831.69e6, 831.87e6), "4x1/16-bit": (918.48e6, 896.70e6),
-            "tma": (971.89e6, 972.49e6), "tma/16-bit": (790.35e6, 790.94e6),
-            "32x8e": (971.89e6, 972.31e6), "32x8e/16-bit": (791.28e6, 791.08e6),
-            "32x4e": (971.87e6, 972.48e6), "32x4e/16-bit": (793.57e6, 792.07e6),
+            "16x2": (972.47e6, 973.35e6), "32x1": (971.81e6, 972.33e6),
+            "16x1": (978.16e6, 972.46e6), "8x1": (1004.37e6, 1019.95e6),
+            "8x2": (997.49e6, 987.54e6), "4x1": (1011.21e6, 1022.64e6),
+            "16x2/16-bit": (800.09e6, 796.17e6), "32x1/16-bit": (791.64e6, 790.90e6),
+            "16x1/16-bit": (804.80e6, 809.89e6), "8x1/16-bit": (854.40e6, 906.59e6),
+            "8x2/16-bit": (832.11e6, 831.46e6), "4x1/16-bit": (918.24e6, 897.54e6),
+            "tma": (971.92e6, 972.59e6), "tma/16-bit": (790.21e6, 791.06e6),
+            "32x8e": (971.87e6, 972.27e6), "32x8e/16-bit": (791.25e6, 791.03e6),
+            "32x4e": (971.84e6, 972.46e6), "32x4e/16-bit": (793.61e6, 791.96e6),
         },
         "tiles": {
-            "16x2": (972.35e6, 973.46e6), "32x1": (972.03e6, 972.34e6),
-            "16x1": (978.15e6, 972.47e6), "8x1": (1005.36e6, 1020.24e6),
-            "8x2": (998.21e6, 994.45e6), "4x1": (1012.09e6, 1021.81e6),
-            "16x2/16-bit": (799.92e6, 795.88e6), "32x1/16-bit": (791.51e6, 790.75e6),
-            "16x1/16-bit": (804.48e6, 810.03e6), "8x1/16-bit": (855.46e6, 928.89e6),
-            "8x2/16-bit": (832.36e6, 837.88e6), "4x1/16-bit": (930.94e6, 892.59e6),
-            "tma": (971.70e6, 972.70e6), "tma/16-bit": (790.24e6, 791.18e6),
-            "32x8e": (971.88e6, 972.30e6), "32x8e/16-bit": (791.37e6, 790.98e6),
-            "32x4e": (971.91e6, 972.29e6), "32x4e/16-bit": (793.58e6, 791.85e6),
+            "16x2": (972.59e6, 973.41e6), "32x1": (971.96e6, 972.22e6),
+            "16x1": (978.25e6, 972.46e6), "8x1": (1005.26e6, 1020.23e6),
+            "8x2": (998.13e6, 993.24e6), "4x1": (1012.13e6, 1021.67e6),
+            "16x2/16-bit": (799.75e6, 796.06e6), "32x1/16-bit": (791.53e6, 790.91e6),
+            "16x1/16-bit": (804.78e6, 810.25e6), "8x1/16-bit": (855.61e6, 932.44e6),
+            "8x2/16-bit": (832.43e6, 837.37e6), "4x1/16-bit": (931.75e6, 893.35e6),
+            "tma": (971.69e6, 972.67e6), "tma/16-bit": (790.25e6, 791.12e6),
+            "32x8e": (971.88e6, 972.27e6), "32x8e/16-bit": (791.30e6, 791.00e6),
+            "32x4e": (972.05e6, 972.28e6), "32x4e/16-bit": (793.53e6, 791.89e6),
         },
     },
     "sources": {
@@ -134,7 +134,7 @@ SPMV_TRAFFIC = {
         "paper_2409_05239_gb300/csrc/lslu_spmv_tma.cu":
             "3258c2e4fb82c38ccf340c4f48253dc396e784b74b1ebbdd43ae8083ee84199c",
         "paper_2409_05239_gb300/csrc/lslu_internal.cuh":
-            "2275773d234adb9dffd8b8c30374292cdf88b8a70a9ac3da2d50aad2ab8a9759",
+            "d306ddcf7e4c4a5b57d4d76e5550e0d08625a3ae32182b984aaea553fc8e4063",
     },
 }
 

@@ -88,11 +88,11 @@ lslu_status lslu_create(int64_t m, int64_t n, int64_t nnz, const int64_t* row_pt
  * The handle stores A_hat = P_r A P_c^T (each row's entries sorted by the new
  * column) and runs every solve on A_hat and b_hat = P_r b.  Every entry point
  * takes and returns vectors, bases and pivot indices in the caller's
- * numbering: the renumbering is applied on entry and undone on exit.  The
- * method commutes with a renumbering (max-abs pivots pick the same entries),
- * so results equal lslu_create's up to the rounding order of the products,
- * except where two candidates of a pivot search tie exactly: a tie goes to
- * the lower internal index.  lslu_spmv is refused on such a handle.
+ * numbering: the renumbering is applied on entry and undone on exit.  Max-abs
+ * pivots pick the same entries in any numbering, and every pivot search
+ * breaks ties by the caller's index (Algorithm 4's lowest index), so the
+ * pivots are lslu_create's and the results equal up to the rounding order of
+ * the products.  lslu_spmv is refused on such a handle.
  * Errors: those of lslu_create, and LSLU_ERR_INVALID_ARG when an order is not
  * a permutation of [0, m) or [0, n). */
 lslu_status lslu_create_ordered(int64_t m, int64_t n, int64_t nnz, const int64_t* row_ptr,
@@ -146,8 +146,8 @@ lslu_status lslu_create_batched(int32_t nprob, const int64_t* row_off, const int
  * concatenated rows and columns that map each problem's range onto itself:
  * caller row i becomes internal row row_order[i]; NULL is the identity.
  * lslu_solve_batched takes b and returns x and the pivot indices in the
- * caller's numbering; a tie of a pivot search goes to the lower internal
- * index.  Errors: those of lslu_create_batched, and LSLU_ERR_INVALID_ARG when
+ * caller's numbering; pivot searches break ties by the caller's index, as
+ * without a renumbering.  Errors: those of lslu_create_batched, and LSLU_ERR_INVALID_ARG when
  * an order is not a permutation or moves an index out of its problem. */
 lslu_status lslu_create_batched_ordered(int32_t nprob, const int64_t* row_off,
                                         const int64_t* col_off, const int64_t* row_ptr,

@@ -86,7 +86,7 @@ void destroy_ctx(lslu_ctx* c) {
                   c->map_m, c->map_n, c->xin_pad, c->xout_user, c->mvec,
                   c->adj_Vb, c->adj_Zb, c->adj_vec, c->adj_small, c->adj_part,
                   c->fixed_gp, c->fixed_tp, c->xi, c->samples, c->ord_m, c->ord_n,
-                  c->ord_stage};
+                  c->ord_stage, c->rank_m, c->rank_n};
   for (void* p : ptrs) cudaFree(p);
   if (c->st_host) cudaFreeHost(c->st_host);
   for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
@@ -325,15 +325,21 @@ lslu_status create_single(int64_t m, int64_t n, int64_t nnz, const int64_t* row_
   if (ordered) {
     cudaError_t e = dmalloc(&c->ord_m, m);
     if (e == cudaSuccess) e = dmalloc(&c->ord_n, n);
+    if (e == cudaSuccess) e = dmalloc(&c->rank_m, m);
+    if (e == cudaSuccess) e = dmalloc(&c->rank_n, n);
     if (e == cudaSuccess) e = dmalloc(&c->ord_stage, std::max(m, n));
     if (e == cudaSuccess) e = cudaMemcpy(c->ord_m, om.data(), m * 4, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(c->ord_n, on.data(), n * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->rank_m, im.data(), m * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->rank_n, in.data(), n * 4, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
       cudaGetLastError();
       destroy_ctx(c);
       return set_err(nullptr, e == cudaErrorMemoryAllocation ? LSLU_ERR_OOM : LSLU_ERR_CUDA,
                      std::string("renumbering maps: ") + cudaGetErrorString(e));
     }
+    c->unrank_m = c->ord_m;
+    c->unrank_n = c->ord_n;
     c->ord_m_h.swap(om);
     c->ord_n_h.swap(on);
     c->inv_m_h.swap(im);
@@ -454,7 +460,7 @@ int64_t enqueue_solve(Ctx* c, cudaStream_t s, const double* db, const double* dx
   {
     PivotArgs pa{c->tp, c->kmax + 1, 0, c->tused, nullptr, 0, c->ldt, LSLU_BREAKDOWN_BETA,
                  0, 1, c->TDi, c->t_stride, c->coef, c->c_stride, P, tpm,
-                 fixed ? c->fixed_tp : nullptr, samp(0), nsamp};
+                 fixed ? c->fixed_tp : nullptr, samp(0), nsamp, c->rank_m, c->unrank_m};
     launch_init_pivot<BT>(c->r0, m, pa, c->st, s, c->num_sms);
     launch_scale<double, BT>(c->r0, D, m, c->st, P, tpm, s, c->num_sms);
     launches += 3;
@@ -483,7 +489,8 @@ int64_t enqueue_solve(Ctx* c, cudaStream_t s, const double* db, const double* dx
     record_spmv_end(c, s, capturing, e0);
     PivotArgs paw{c->gp, c->kmax, k, c->gused, c->W + k + k * ldw, c->w_stride, c->ldt,
                   LSLU_BREAKDOWN_W, k, 0, c->TLi, c->t_stride, c->coef, c->c_stride, P, tpn,
-                  fixed ? c->fixed_gp : nullptr, samp(2 * k + 1), nsamp};
+                  fixed ? c->fixed_gp : nullptr, samp(2 * k + 1), nsamp, c->rank_n,
+                  c->unrank_n};
     launch_eliminate_argmax<CT, BT, CT>(q, L, c->ldl, k, n, q, paw, c->part_val, c->part_idx,
                                         c->part_cap, c->st, s, c->num_sms);
     launch_scale<CT, BT>(q, L + (int64_t)k * c->ldl, n, c->st, P, tpn, s, c->num_sms);
@@ -508,7 +515,8 @@ int64_t enqueue_solve(Ctx* c, cudaStream_t s, const double* db, const double* dx
     record_spmv_end(c, s, capturing, e0);
     PivotArgs pah{c->tp, c->kmax + 1, k + 1, c->tused, c->H + (k + 1) + k * ldh, c->h_stride,
                   c->ldt, LSLU_BREAKDOWN_H, k, 0, c->TDi, c->t_stride, c->coef, c->c_stride, P,
-                  tpm, fixed ? c->fixed_tp : nullptr, samp(2 * k + 2), nsamp};
+                  tpm, fixed ? c->fixed_tp : nullptr, samp(2 * k + 2), nsamp, c->rank_m,
+                  c->unrank_m};
     launch_eliminate_argmax<CT, BT, CT>(u, D, c->ldd, k + 1, m, u, pah, c->part_val,
                                         c->part_idx, c->part_cap, c->st, s, c->num_sms);
     launch_scale<CT, BT>(u, D + (int64_t)(k + 1) * c->ldd, m, c->st, P, tpm, s, c->num_sms);
@@ -1030,7 +1038,22 @@ lslu_status create_batched_impl(int32_t nprob, const int64_t* row_off, const int
   if (st != LSLU_OK) return st;
   st = upload_batch_layout(c, tpm, tpn, pad_m, pad_n, map_m, map_n, mvec);
   if (st != LSLU_OK) return st;
-  if (ordered) {  // for the pivot indices
+  if (ordered) {  // pivot ties by the caller's index; pivot indices back to it
+    std::vector<int32_t> rm(mp, INT32_MAX), rn(np, INT32_MAX);
+    for (int64_t r = 0; r < mu; ++r) rm[map_m[r]] = (int32_t)r;
+    for (int64_t j = 0; j < nu; ++j) rn[map_n[j]] = (int32_t)j;
+    cudaError_t e = dmalloc(&c->rank_m, mp);
+    if (e == cudaSuccess) e = dmalloc(&c->rank_n, np);
+    if (e == cudaSuccess) e = cudaMemcpy(c->rank_m, rm.data(), mp * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->rank_n, rn.data(), np * 4, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      destroy_ctx(c);
+      return set_err(nullptr, e == cudaErrorMemoryAllocation ? LSLU_ERR_OOM : LSLU_ERR_CUDA,
+                     std::string("renumbering ranks: ") + cudaGetErrorString(e));
+    }
+    c->unrank_m = c->map_m;
+    c->unrank_n = c->map_n;
     c->inv_m_h.swap(im);
     c->inv_n_h.swap(in);
   }

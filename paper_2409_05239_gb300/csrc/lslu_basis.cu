@@ -105,6 +105,16 @@ __device__ __forceinline__ int tile_problem(const int32_t* tile_prob, int64_t ro
   return tile_prob ? tile_prob[row / kTile] : 0;
 }
 
+// The index a pivot search compares on ties (Algorithm 4, lowest index): the
+// caller's index of a row on a renumbered handle, the row itself otherwise;
+// unrank_of maps the winner back to its stored row.
+__device__ __forceinline__ int rank_of(const PivotArgs& pa, int64_t i) {
+  return pa.rank ? __ldg(pa.rank + i) : (int)i;
+}
+__device__ __forceinline__ int unrank_of(const PivotArgs& pa, int r) {
+  return (pa.unrank && r >= 0) ? __ldg(pa.unrank + r) : r;
+}
+
 // Records the pivot of problem p (one thread).
 template <typename CT, typename BT>
 __device__ void record_pivot(const PivotArgs& pa, DevState& s, int p, int besti, double best,
@@ -145,7 +155,7 @@ __device__ unsigned long long sampled_key(const PivotArgs& pa, const CT* v) {
     if (!pa.used[i]) {
       const float a = fabsf((float)__ldcg(v + i));
       if (a != 0.0f) {
-        const unsigned long long kk = argkey(a, i);
+        const unsigned long long kk = argkey(a, rank_of(pa, i));
         k = kk > k ? kk : k;
       }
     }
@@ -161,6 +171,7 @@ __device__ unsigned long long sampled_key(const PivotArgs& pa, const CT* v) {
 }
 
 // The same in FP64 (value, index) form; best = 0 when none is non-zero.
+// besti is the winner's rank (rank_of).
 template <typename CT>
 __device__ void sampled_best(const PivotArgs& pa, const CT* v, double& best, int& besti) {
   best = 0.0;
@@ -170,9 +181,10 @@ __device__ void sampled_best(const PivotArgs& pa, const CT* v, double& best, int
     if (pa.used[i]) continue;
     double a = fabs((double)__ldcg(v + i));
     if (isnan(a)) a = INFINITY;
-    if (a != 0.0 && better(a, i, best, besti)) {
+    const int ri = rank_of(pa, i);
+    if (a != 0.0 && better(a, ri, best, besti)) {
       best = a;
-      besti = i;
+      besti = ri;
     }
   }
   block_argmax(best, besti);
@@ -268,6 +280,25 @@ __global__ void __launch_bounds__(32)
 #pragma unroll
       for (int e = 0; e < VEC; ++e) val[e] = fma(-c[j], (CT)b0[e], val[e]);
     }
+    // tie-breaking index of the lane's rows (rank_of, one vector load)
+    int rk[VEC];
+    if (pa.rank) {
+      if constexpr (VEC == 4) {
+        if (full) {
+          const int4 w = __ldg(reinterpret_cast<const int4*>(pa.rank + i0));
+          rk[0] = w.x; rk[1] = w.y; rk[2] = w.z; rk[3] = w.w;
+        } else {
+#pragma unroll
+          for (int e = 0; e < VEC; ++e) rk[e] = (i0 + e < rows) ? __ldg(pa.rank + i0 + e) : 0;
+        }
+      } else {
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) rk[e] = (i0 + e < rows) ? __ldg(pa.rank + i0 + e) : 0;
+      }
+    } else {
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) rk[e] = (int)(i0 + e);
+    }
     unsigned long long tkey = 0;
     CT outv[VEC];
 #pragma unroll
@@ -279,14 +310,14 @@ __global__ void __launch_bounds__(32)
       if (!usedf[e]) {
         out = val[e];
         if constexpr (kKey) {
-          const unsigned long long kk = argkey(fabsf((float)out), (int)i);
+          const unsigned long long kk = argkey(fabsf((float)out), rk[e]);
           tkey = kk > tkey ? kk : tkey;
         } else {
           double a = fabs((double)out);
           if (isnan(a)) a = INFINITY;  // a NaN must win so that it is reported
-          if (better(a, (int)i, best, besti)) {
+          if (better(a, rk[e], best, besti)) {
             best = a;
-            besti = (int)i;
+            besti = rk[e];
           }
         }
       }
@@ -336,7 +367,7 @@ __global__ void __launch_bounds__(32)
       unsigned long long m = atomicExch(&st[p].amax, 0ull);
       if (p == 0 && (skey >> 32) != 0) m = skey;  // sampled pivot (full search as fallback)
       if (st[p].status != LSLU_OK) continue;
-      const int bi = m ? (int)(0xffffffffu - (unsigned)(m & 0xffffffffull)) : -1;
+      const int bi = m ? unrank_of(pa, (int)(0xffffffffu - (unsigned)(m & 0xffffffffull))) : -1;
       const float a = __uint_as_float((unsigned)(m >> 32));
       record_pivot<CT, BT>(pa, st[p], p, bi, (a != a) ? INFINITY : (double)a, v);
     }
@@ -363,7 +394,7 @@ __global__ void __launch_bounds__(32)
     }
     if (lane == 0) {
       st[0].ticket = 0;
-      record_pivot<CT, BT>(pa, st[0], 0, besti, best, v);
+      record_pivot<CT, BT>(pa, st[0], 0, unrank_of(pa, besti), best, v);
     }
   }
 }
@@ -401,7 +432,7 @@ __global__ void k_r0_argmin(const double* __restrict__ r0, int64_t rows, PivotAr
     const double a = fabs(r0[i]);
     unsigned long long bits = (unsigned long long)__double_as_longlong(a);
     if (a != a) bits = 0x7ff0000000000001ull;
-    if (bits && bits == __ldcg(&st[p].amax)) atomicMin(&st[p].amin, (int)i);
+    if (bits && bits == __ldcg(&st[p].amax)) atomicMin(&st[p].amin, rank_of(pa, i));
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -420,10 +451,10 @@ __global__ void k_r0_argmin(const double* __restrict__ r0, int64_t rows, PivotAr
     const int bi = atomicExch(&st[p].amin, 0x7fffffff);
     if (st[p].status != LSLU_OK) continue;
     double best = m == 0x7ff0000000000001ull ? INFINITY : __longlong_as_double((long long)m);
-    int besti = (m && bi != 0x7fffffff) ? bi : -1;
+    int besti = (m && bi != 0x7fffffff) ? unrank_of(pa, bi) : -1;
     if (p == 0 && sb > 0.0) {  // sampled pivot, the full search as fallback
       best = sb;
-      besti = si;
+      besti = unrank_of(pa, si);
     }
     record_pivot<double, BT>(pa, st[p], p, besti, best, r0);
   }

@@ -256,6 +256,13 @@ struct Ctx {
   std::vector<int32_t> ord_m_h, ord_n_h;  // caller -> internal (host)
   std::vector<int32_t> inv_m_h, inv_n_h;  // internal -> caller (host)
   double* ord_stage = nullptr;            // max(m, n) FP64 staging
+  // pivot tie-breaking by the caller's index: stored row -> caller index
+  // (owned; padding rows of a batch get INT32_MAX) and caller index -> stored
+  // row (ord_m / ord_n, or the composed batch maps map_m / map_n)
+  int32_t* rank_m = nullptr;
+  int32_t* rank_n = nullptr;
+  const int32_t* unrank_m = nullptr;
+  const int32_t* unrank_n = nullptr;
 
   int last_k = -1;  // k_done of the last solve, -1 if none
   int last_K = 0;
@@ -397,6 +404,11 @@ struct PivotArgs {
   const int32_t* fixed;  // replayed pivot list (same layout as piv_list), or null: argmax
   const int32_t* samples;  // sampled pivoting (single problem): nsamp candidate rows, or null
   int nsamp;
+  // renumbered handles: rank[i] = the caller's index of row i, unrank its
+  // inverse; a tie of a pivot search goes to the lowest caller index (both
+  // null: the row index itself)
+  const int32_t* rank;
+  const int32_t* unrank;
 };
 
 template <typename XT, typename BT, typename CT>

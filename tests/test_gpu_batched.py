@@ -193,3 +193,25 @@ def test_batched_order_must_stay_in_its_problem(small_batch):
     with pytest.raises(ValueError):
         lslu.BatchedSolver((P0.m, P0.n, P0.row_ptr, P0.col_idx, P0.vals), nrhs=2,
                            orders=[(None, None)])
+
+
+def test_batched_renumbered_ties_follow_the_caller_numbering():
+    """Two copies of the hand-worked W-step breakdown (A = diag(1, 2) padded to
+    4 x 3, b = ones: the first row pivot is a four-way tie), renumbered in
+    reverse: every pivot, tie included, is the natural batch's."""
+    rp = np.array([0, 1, 2, 2, 2], dtype=np.int64)
+    ci = np.array([0, 1], dtype=np.int32)
+    v = np.array([1.0, 2.0])
+    csr = [(4, 3, rp, ci, v), (4, 3, rp, ci, 2.0 * v)]
+    rev = (np.array([3, 2, 1, 0]), np.array([2, 1, 0]))
+    b = np.ones(8)
+    with lslu.BatchedSolver(csr, "f32", 5) as bn, \
+            lslu.BatchedSolver(csr, "f32", 5, orders=[rev, rev]) as bo:
+        r0 = bn.solve(b, 5, "none")
+        r1 = bo.solve(b, 5, "none")
+    assert np.array_equal(r0["status"], r1["status"]) and np.array_equal(r0["k_done"],
+                                                                          r1["k_done"])
+    assert np.array_equal(r0["gp"], r1["gp"]) and np.array_equal(r0["tp"], r1["tp"])
+    assert r1["tp"][0][0] == 0 and r1["tp"][1][0] == 0
+    for p in range(2):
+        assert np.allclose(r0["x"][p], r1["x"][p], rtol=1e-6, atol=0)

@@ -2,11 +2,12 @@
 
 A handle made with a row order and a column order stores A_hat = P_r A P_c^T,
 solves with b_hat = P_r b, and maps vectors, bases and pivot indices back to
-the caller's numbering.  Checked against the FP64 oracle run on A_hat (the
-definition, with ties of a pivot search going to the lower internal index)
-and against a handle without a renumbering: on these inputs no pivot search
-ties (the oracle gives the same pivots in both numberings), so every entry
-point that takes or returns a vector must agree up to rounding.
+the caller's numbering; a pivot search still breaks ties by the caller's
+index, so the pivots are those of a handle without a renumbering.  Checked
+against the FP64 oracle run on A_hat (inputs with no tied search, where the
+two definitions agree), against a handle without a renumbering at every entry
+point that takes or returns a vector (equal up to rounding), and on a
+hand-worked case whose first pivot is a four-way tie.
 """
 import numpy as np
 import pytest
@@ -211,10 +212,9 @@ def test_ct256_f64_renumbered_matches_natural():
 def test_breakdowns_renumbered(ct32):
     """b = 0 breaks down before the first iteration; and the hand-worked W-step
     breakdown of the oracle pins (A = diag(1, 2) padded to 4 x 3, b = ones)
-    with both numberings reversed: the first row pivot is a four-way tie, so
-    it goes to the lowest internal index (caller row 3, a zero row of A), and
-    the solve follows the oracle run on the renumbered problem, not the
-    natural one."""
+    with both numberings reversed: the first row pivot is a four-way tie,
+    which goes to the lowest caller index (row 0, not internal row 0 = caller
+    row 3), so the solve is the natural one."""
     ro, co = orders(ct32, "random", seed=9)
     with lslu.from_problem(ct32, "f64", 5, order=(ro, co)) as s:
         r = s.solve(np.zeros(ct32.m), 5, "gcv")
@@ -224,18 +224,27 @@ def test_breakdowns_renumbered(ct32):
     ci = np.array([0, 1], dtype=np.int32)
     Ad = np.zeros((4, 3))
     Ad[0, 0], Ad[1, 1] = 1.0, 2.0
+    ref = O.hybrid_lslu(Ad, np.ones(4), None, 5, "none")
     ro = np.array([3, 2, 1, 0], np.int32)
     co = np.array([2, 1, 0], np.int32)
-    ir, ic = np.argsort(ro), np.argsort(co)
-    ref = O.hybrid_lslu(Ad[ir][:, ic], np.ones(4), None, 5, "none")
     with lslu.Solver(4, 3, rp, ci, np.array([1.0, 2.0]), "f64", 5, row_order=ro,
                      col_order=co) as s:
         r = s.solve(np.ones(4), 5, "none")
     assert r["status"] == ref.status == lslu.BREAKDOWN_W and r["k_done"] == ref.k_done == 2
-    assert r["gp"].tolist() == ic[ref.gp].tolist() + [-1] * 3
-    assert r["tp"].tolist() == ir[ref.tp].tolist() + [-1] * 3
-    assert r["tp"][0] == 3
-    assert np.allclose(r["x"], ref.x[co], rtol=0, atol=1e-14)
+    assert r["gp"].tolist() == [1, 0, -1, -1, -1]
+    assert r["tp"].tolist() == [0, 1, 2, -1, -1, -1]
+    assert rel(r["x"], ref.x) <= TOL_F64
+    # the sampled search breaks ties the same way: a sample of all four rows
+    S = np.tile(np.array([3, 2, 1, 0], np.int32), (11, 1))
+    S[1::2] = np.array([2, 1, 0, 2], np.int32)
+    with lslu.Solver(4, 3, rp, ci, np.array([1.0, 2.0]), "f64", 5, row_order=ro,
+                     col_order=co) as s, lslu.Solver(4, 3, rp, ci, np.array([1.0, 2.0]), "f64",
+                                                     5) as s0:
+        a = s.solve_sampled(np.ones(4), 5, S, "none")
+        b = s0.solve_sampled(np.ones(4), 5, S, "none")
+    assert a["status"] == b["status"] and a["k_done"] == b["k_done"]
+    assert np.array_equal(a["gp"], b["gp"]) and np.array_equal(a["tp"], b["tp"])
+    assert a["tp"][0] == 0
 
 
 def test_device_csr_and_orders(ct32):
