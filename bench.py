@@ -394,11 +394,12 @@ def batched_study(dev, K=150, count=64, order="tiles"):
             "rel_err_x_true_max": float(np.max(errs))}
 
 
-def shared_rhs_study(dev, K=150, nrhs=16):
+def shared_rhs_study(dev, K=150, nrhs=16, order="tiles"):
     """16 right-hand sides for the 256x256 projector (FP32, GCV, K iterations):
     the shared-matrix handle (A read once per product for all of them) against
     the same right-hand sides as a block-diagonal batch of 16 copies of A and
-    against 16 single-problem solves one after another."""
+    against 16 single-problem solves one after another; all three renumbered
+    by tomo.locality_order when order == "tiles"."""
     import torch
 
     from paper_2409_05239_gb300 import lslu
@@ -422,22 +423,26 @@ def shared_rhs_study(dev, K=150, nrhs=16):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / reps
 
-    sh = lslu.shared_rhs(P0, nrhs, "f32", K, stream=stream.cuda_stream)
+    o = tomo.locality_order(P0) if order == "tiles" else None
+    sh = lslu.shared_rhs(P0, nrhs, "f32", K, stream=stream.cuda_stream, order=o)
     ms_sh = timed(lambda: sh.solve_device(b_dev, x_dev, K, "gcv"))
     x_sh = x_dev.cpu().numpy()
     sh.close()
-    bd = lslu.from_problems(Ps, "f32", K, stream=stream.cuda_stream)
+    bd = lslu.from_problems(Ps, "f32", K, stream=stream.cuda_stream,
+                            orders=None if o is None else [o] * nrhs)
     ms_bd = timed(lambda: bd.solve_device(b_dev, x_dev, K, "gcv"))
     same_bd = bool(np.array_equal(x_dev.cpu().numpy(), x_sh))
     bd.close()
     single = lslu.Solver(P0.m, P0.n, P0.row_ptr, P0.col_idx, P0.vals, "f32", K,
-                         stream=stream.cuda_stream)
+                         stream=stream.cuda_stream, row_order=None if o is None else o[0],
+                         col_order=None if o is None else o[1])
     bs = [torch.from_numpy(P.b).to(dev) for P in Ps]
     xs = torch.empty(P0.n, dtype=torch.float64, device=dev)
     ms_seq = timed(lambda: [single.solve_device(bb, xs, K, "gcv") for bb in bs], reps=2)
     single.close()
     return {"workload": "ct256 (m=%d, n=%d, nnz=%d) x %d right-hand sides, FP32, K=%d, GCV"
                         % (P0.m, P0.n, P0.nnz, nrhs, K),
+            "numbering": ORDER_NOTE[order],
             "ms_per_solve_shared_matrix": ms_sh,
             "ms_per_solve_block_diagonal_copies": ms_bd,
             "ms_sequential_single_solves": ms_seq,
@@ -683,7 +688,7 @@ def run_gpu(args):
         out["precision_study"] = precision_study(P, K, rule, dev, x, args.value_type, (ro, co))
     if rank == 0 and not args.no_extras and world == 1:
         out["batched_study"] = batched_study(dev, order=args.order)
-        out["shared_rhs_study"] = shared_rhs_study(dev)
+        out["shared_rhs_study"] = shared_rhs_study(dev, order=args.order)
         out["adjoint_study"] = adjoint_study(dev, order=args.order)
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         out["cpu_baseline"] = cpu_baseline(P, K, args.cpu_sample_s)

@@ -170,6 +170,19 @@ lslu_status lslu_create_shared(int64_t m, int64_t n, const int64_t* row_ptr,
                                int32_t value_type, int32_t max_iter, void* cuda_stream,
                                lslu_handle* out);
 
+/* lslu_create_shared with the matrix renumbered for memory locality, as
+ * lslu_create_ordered does: row_order (m int32) and col_order (n int32), host
+ * memory, are permutations (NULL: the identity) applied to the one stored
+ * matrix and so to every right-hand side.  lslu_solve_batched takes b and
+ * returns x and the pivot indices in the caller's numbering; pivot searches
+ * break ties by the caller's index.  Errors: those of lslu_create_shared, and
+ * LSLU_ERR_INVALID_ARG when an order is not a permutation. */
+lslu_status lslu_create_shared_ordered(int64_t m, int64_t n, const int64_t* row_ptr,
+                                       const int32_t* col_idx, const double* vals, int32_t nrhs,
+                                       int32_t value_type, int32_t max_iter,
+                                       const int32_t* row_order, const int32_t* col_order,
+                                       void* cuda_stream, lslu_handle* out);
+
 /* K iterations of Hybrid LSLU on every problem of a batched handle, from
  * x0 = 0.  b has row_off[nprob] FP64 entries (problem p's data at
  * row_off[p]); rule and lambda as in lslu_solve (the same rule for every

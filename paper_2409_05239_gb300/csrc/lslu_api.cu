@@ -227,6 +227,31 @@ lslu_status read_order(const int32_t* order, int64_t len, bool device, std::vect
   return LSLU_OK;
 }
 
+// A host CSR renumbered: stored row r holds caller row inv_row[r], with its
+// columns mapped through col_new and sorted ascending (stable for repeats).
+void renumber_csr(int64_t rows, const int64_t* rp, const int32_t* ci, const double* vv,
+                  const std::vector<int32_t>& inv_row, const std::vector<int32_t>& col_new,
+                  std::vector<int64_t>& rp_o, std::vector<int32_t>& ci_o,
+                  std::vector<double>& vv_o) {
+  rp_o.assign(rows + 1, 0);
+  for (int64_t r = 0; r < rows; ++r)
+    rp_o[r + 1] = rp_o[r] + (rp[inv_row[r] + 1] - rp[inv_row[r]]);
+  ci_o.resize(rp_o[rows]);
+  vv_o.resize(rp_o[rows]);
+  std::vector<uint64_t> key;
+  for (int64_t r = 0; r < rows; ++r) {
+    const int64_t a = rp[inv_row[r]], len = rp[inv_row[r] + 1] - a, o = rp_o[r];
+    key.resize(len);
+    for (int64_t i = 0; i < len; ++i)
+      key[i] = ((uint64_t)(uint32_t)col_new[ci[a + i]] << 32) | (uint64_t)i;
+    std::sort(key.begin(), key.end());
+    for (int64_t i = 0; i < len; ++i) {
+      ci_o[o + i] = (int32_t)(key[i] >> 32);
+      vv_o[o + i] = vv[a + (int64_t)(key[i] & 0xffffffffull)];
+    }
+  }
+}
+
 lslu_status create_single(int64_t m, int64_t n, int64_t nnz, const int64_t* row_ptr,
                           const int32_t* col_idx, const double* vals, int32_t value_type,
                           int32_t max_iter, const int32_t* row_order, const int32_t* col_order,
@@ -283,24 +308,10 @@ lslu_status create_single(int64_t m, int64_t n, int64_t nnz, const int64_t* row_
     if (st == LSLU_OK)
       st = read_order(col_order, n, ptr_location == LSLU_DEVICE, on, in, "col_order");
     if (st != LSLU_OK) return st;
-    // internal row r holds caller row im[r] with its columns renumbered and
-    // sorted ascending
-    std::vector<int64_t> rp2(m + 1, 0);
-    for (int64_t r = 0; r < m; ++r) rp2[r + 1] = rp2[r] + (rp[im[r] + 1] - rp[im[r]]);
-    std::vector<int32_t> ci2(nnz);
-    std::vector<double> vv2(nnz);
-    std::vector<uint64_t> key;
-    for (int64_t r = 0; r < m; ++r) {
-      const int64_t a = rp[im[r]], len = rp[im[r] + 1] - a, o = rp2[r];
-      key.resize(len);
-      for (int64_t i = 0; i < len; ++i)
-        key[i] = ((uint64_t)(uint32_t)on[ci[a + i]] << 32) | (uint64_t)i;
-      std::sort(key.begin(), key.end());
-      for (int64_t i = 0; i < len; ++i) {
-        ci2[o + i] = (int32_t)(key[i] >> 32);
-        vv2[o + i] = vv[a + (int64_t)(key[i] & 0xffffffffull)];
-      }
-    }
+    std::vector<int64_t> rp2;
+    std::vector<int32_t> ci2;
+    std::vector<double> vv2;
+    renumber_csr(m, rp.data(), ci.data(), vv.data(), im, on, rp2, ci2, vv2);
     rp.swap(rp2);
     ci.swap(ci2);
     vv.swap(vv2);
@@ -937,22 +948,7 @@ lslu_status create_batched_impl(int32_t nprob, const int64_t* row_off, const int
       if (col_idx[e] < 0 || col_idx[e] >= nu)
         return set_err(nullptr, LSLU_ERR_INVALID_ARG,
                        "column index outside its problem's column range");
-    rp_o.assign(mu + 1, 0);
-    for (int64_t r = 0; r < mu; ++r) rp_o[r + 1] = rp_o[r] + (row_ptr[im[r] + 1] - row_ptr[im[r]]);
-    ci_o.resize(nnz);
-    vv_o.resize(nnz);
-    std::vector<uint64_t> key;
-    for (int64_t r = 0; r < mu; ++r) {
-      const int64_t a = row_ptr[im[r]], len = row_ptr[im[r] + 1] - a, o = rp_o[r];
-      key.resize(len);
-      for (int64_t i = 0; i < len; ++i)
-        key[i] = ((uint64_t)(uint32_t)on[col_idx[a + i]] << 32) | (uint64_t)i;
-      std::sort(key.begin(), key.end());
-      for (int64_t i = 0; i < len; ++i) {
-        ci_o[o + i] = (int32_t)(key[i] >> 32);
-        vv_o[o + i] = vals[a + (int64_t)(key[i] & 0xffffffffull)];
-      }
-    }
+    renumber_csr(mu, row_ptr, col_idx, vals, im, on, rp_o, ci_o, vv_o);
     row_ptr = rp_o.data();
     col_idx = ci_o.data();
     vals = vv_o.data();
@@ -1084,10 +1080,12 @@ extern "C" lslu_status lslu_create_batched_ordered(int32_t nprob, const int64_t*
                              max_iter, row_order, col_order, cuda_stream, out);
 }
 
-extern "C" lslu_status lslu_create_shared(int64_t m, int64_t n, const int64_t* row_ptr,
-                                          const int32_t* col_idx, const double* vals,
-                                          int32_t nrhs, int32_t value_type, int32_t max_iter,
-                                          void* cuda_stream, lslu_handle* out) {
+namespace {
+
+lslu_status create_shared_impl(int64_t m, int64_t n, const int64_t* row_ptr,
+                               const int32_t* col_idx, const double* vals, int32_t nrhs,
+                               int32_t value_type, int32_t max_iter, const int32_t* row_order,
+                               const int32_t* col_order, void* cuda_stream, lslu_handle* out) {
   if (!out) return set_err(nullptr, LSLU_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   if (m < 1 || n < 1 || !row_ptr)
@@ -1114,16 +1112,31 @@ extern "C" lslu_status lslu_create_shared(int64_t m, int64_t n, const int64_t* r
   const int64_t mp = nrhs * m1p, np = nrhs * n1p;
   if (mp >= (int64_t)INT32_MAX || np >= (int64_t)INT32_MAX)
     return set_err(nullptr, LSLU_ERR_INVALID_ARG, "padded sizes must be below 2^31");
+  // renumbering of the one matrix, the same for every right-hand side
+  const bool ordered = row_order || col_order;
+  std::vector<int32_t> om, on, im, in;
+  std::vector<int64_t> rp_o;
+  std::vector<int32_t> ci_o;
+  std::vector<double> vv_o;
+  if (ordered) {
+    lslu_status st0 = read_order(row_order, m, false, om, im, "row_order");
+    if (st0 == LSLU_OK) st0 = read_order(col_order, n, false, on, in, "col_order");
+    if (st0 != LSLU_OK) return st0;
+    renumber_csr(m, row_ptr, col_idx, vals, im, on, rp_o, ci_o, vv_o);
+    row_ptr = rp_o.data();
+    col_idx = ci_o.data();
+    vals = vv_o.data();
+  }
   std::vector<int32_t> map_m(nrhs * m), map_n(nrhs * n), tpm(mp / kTile), tpn(np / kTile);
   std::vector<uint8_t> pad_m(mp, 1), pad_n(np, 1);
   std::vector<int64_t> mvec(nrhs, m);
   for (int r = 0; r < nrhs; ++r) {
     for (int64_t i = 0; i < m; ++i) {
-      map_m[r * m + i] = (int32_t)(r * m1p + i);
+      map_m[r * m + i] = (int32_t)(r * m1p + (ordered ? om[i] : i));
       pad_m[r * m1p + i] = 0;
     }
     for (int64_t j = 0; j < n; ++j) {
-      map_n[r * n + j] = (int32_t)(r * n1p + j);
+      map_n[r * n + j] = (int32_t)(r * n1p + (ordered ? on[j] : j));
       pad_n[r * n1p + j] = 0;
     }
   }
@@ -1154,8 +1167,51 @@ extern "C" lslu_status lslu_create_shared(int64_t m, int64_t n, const int64_t* r
   if (st != LSLU_OK) return st;
   st = upload_batch_layout(c, tpm, tpn, pad_m, pad_n, map_m, map_n, mvec);
   if (st != LSLU_OK) return st;
+  if (ordered) {  // pivot ties by the caller's index; pivot indices back to it
+    std::vector<int32_t> rm(mp, INT32_MAX), rn(np, INT32_MAX), gm(nrhs * m), gn(nrhs * n);
+    for (int64_t r = 0; r < nrhs * m; ++r) rm[map_m[r]] = (int32_t)r;
+    for (int64_t j = 0; j < nrhs * n; ++j) rn[map_n[j]] = (int32_t)j;
+    for (int q = 0; q < nrhs; ++q) {  // caller-global index of internal-global index
+      for (int64_t i = 0; i < m; ++i) gm[q * m + i] = (int32_t)(q * m + im[i]);
+      for (int64_t j = 0; j < n; ++j) gn[q * n + j] = (int32_t)(q * n + in[j]);
+    }
+    cudaError_t e = dmalloc(&c->rank_m, mp);
+    if (e == cudaSuccess) e = dmalloc(&c->rank_n, np);
+    if (e == cudaSuccess) e = cudaMemcpy(c->rank_m, rm.data(), mp * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->rank_n, rn.data(), np * 4, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      destroy_ctx(c);
+      return set_err(nullptr, e == cudaErrorMemoryAllocation ? LSLU_ERR_OOM : LSLU_ERR_CUDA,
+                     std::string("renumbering ranks: ") + cudaGetErrorString(e));
+    }
+    c->unrank_m = c->map_m;
+    c->unrank_n = c->map_n;
+    c->inv_m_h.swap(gm);
+    c->inv_n_h.swap(gn);
+  }
   *out = c;
   return LSLU_OK;
+}
+
+}  // namespace
+
+extern "C" lslu_status lslu_create_shared(int64_t m, int64_t n, const int64_t* row_ptr,
+                                          const int32_t* col_idx, const double* vals,
+                                          int32_t nrhs, int32_t value_type, int32_t max_iter,
+                                          void* cuda_stream, lslu_handle* out) {
+  return create_shared_impl(m, n, row_ptr, col_idx, vals, nrhs, value_type, max_iter, nullptr,
+                            nullptr, cuda_stream, out);
+}
+
+extern "C" lslu_status lslu_create_shared_ordered(int64_t m, int64_t n, const int64_t* row_ptr,
+                                                  const int32_t* col_idx, const double* vals,
+                                                  int32_t nrhs, int32_t value_type,
+                                                  int32_t max_iter, const int32_t* row_order,
+                                                  const int32_t* col_order, void* cuda_stream,
+                                                  lslu_handle* out) {
+  return create_shared_impl(m, n, row_ptr, col_idx, vals, nrhs, value_type, max_iter, row_order,
+                            col_order, cuda_stream, out);
 }
 
 extern "C" lslu_status lslu_solve_batched(lslu_handle h, const double* b, int32_t K,

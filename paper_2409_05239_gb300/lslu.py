@@ -29,7 +29,7 @@ EXPORTS = ("lslu_create", "lslu_solve", "lslu_get_state", "lslu_spmv", "lslu_pro
            "lslu_adjoint", "lslu_solve_fixed_pivots", "lslu_create_shared",
            "lslu_solve_stopping", "lslu_solve_sampled", "lslu_set_spmv_shape",
            "lslu_tune_spmv", "lslu_uq", "lslu_solve_optimal", "lslu_spmv_config",
-           "lslu_create_ordered", "lslu_create_batched_ordered")
+           "lslu_create_ordered", "lslu_create_batched_ordered", "lslu_create_shared_ordered")
 
 _lib = None
 
@@ -59,6 +59,9 @@ def load(path: str | None = None):
     lib.lslu_create_batched_ordered.argtypes = [i32, vp, vp, vp, vp, vp, i32, i32, vp, vp, vp,
                                                 ctypes.POINTER(vp)]
     lib.lslu_create_batched_ordered.restype = i32
+    lib.lslu_create_shared_ordered.argtypes = [i64, i64, vp, vp, vp, i32, i32, i32, vp, vp, vp,
+                                               ctypes.POINTER(vp)]
+    lib.lslu_create_shared_ordered.restype = i32
     lib.lslu_solve.argtypes = [vp, vp, vp, i32, i32, f64, i32, vp, vp, vp, vp, vp, vp]
     lib.lslu_solve.restype = i32
     lib.lslu_get_state.argtypes = [vp, i32, vp, vp, vp, vp, vp]
@@ -389,17 +392,17 @@ class BatchedSolver:
     vals) per problem in the problem's own index space; they are stacked into
     one block-diagonal host CSR here (marshalling only).  orders: None, or one
     (row_order, col_order) pair per problem in its own index space (either may
-    be None), stacked into the global orders of lslu_create_batched_ordered."""
+    be None), stacked into the global orders of lslu_create_batched_ordered;
+    with nrhs, one (row_order, col_order) pair for the shared matrix
+    (lslu_create_shared_ordered)."""
 
     def __init__(self, csr_list, value_type="f32", max_iter=150, stream=None, nrhs=None,
                  orders=None):
         self.lib = load()
         if nrhs is not None:  # one matrix shared by nrhs right-hand sides
-            if orders is not None:
-                raise ValueError("a shared-matrix batch takes no renumbering")
             m, n, rp, ci, vv = csr_list
             self._init_shared(int(m), int(n), rp, ci, vv, int(nrhs), value_type, max_iter,
-                              stream)
+                              stream, orders)
             return
         self.nprob = len(csr_list)
         self.value_type = value_type
@@ -440,7 +443,7 @@ class BatchedSolver:
             raise LsluError(st, self.lib.lslu_error_string(None).decode())
         self.h = h
 
-    def _init_shared(self, m, n, rp, ci, vv, nrhs, value_type, max_iter, stream):
+    def _init_shared(self, m, n, rp, ci, vv, nrhs, value_type, max_iter, stream, order=None):
         self.nprob = nrhs
         self.value_type = value_type
         self.max_iter = int(max_iter)
@@ -450,9 +453,17 @@ class BatchedSolver:
         ci = np.ascontiguousarray(ci, dtype=np.int32)
         vv = np.ascontiguousarray(vv, dtype=np.float64)
         h = ctypes.c_void_p()
-        st = self.lib.lslu_create_shared(m, n, _ptr(rp), _ptr(ci), _ptr(vv), nrhs,
-                                         VALUE_TYPES[value_type], self.max_iter, stream,
-                                         ctypes.byref(h))
+        if order is not None:
+            ro, co = (None if o is None else np.ascontiguousarray(o, dtype=np.int32)
+                      for o in order)
+            st = self.lib.lslu_create_shared_ordered(m, n, _ptr(rp), _ptr(ci), _ptr(vv), nrhs,
+                                                     VALUE_TYPES[value_type], self.max_iter,
+                                                     _ptr(ro), _ptr(co), stream,
+                                                     ctypes.byref(h))
+        else:
+            st = self.lib.lslu_create_shared(m, n, _ptr(rp), _ptr(ci), _ptr(vv), nrhs,
+                                             VALUE_TYPES[value_type], self.max_iter, stream,
+                                             ctypes.byref(h))
         if st != OK:
             raise LsluError(st, self.lib.lslu_error_string(None).decode())
         self.h = h
@@ -567,10 +578,11 @@ def sample_table(K, s, m, n, seed):
                      for t in range(2 * K + 1)]).astype(np.int32)
 
 
-def shared_rhs(P, nrhs, value_type="f32", max_iter=150, stream=None):
-    """Batched solver for nrhs right-hand sides of one tomography matrix."""
+def shared_rhs(P, nrhs, value_type="f32", max_iter=150, stream=None, order=None):
+    """Batched solver for nrhs right-hand sides of one tomography matrix; order:
+    None or a (row_order, col_order) pair, e.g. tomo.locality_order(P)."""
     return BatchedSolver((P.m, P.n, P.row_ptr, P.col_idx, P.vals), value_type=value_type,
-                         max_iter=max_iter, stream=stream, nrhs=nrhs)
+                         max_iter=max_iter, stream=stream, nrhs=nrhs, orders=order)
 
 
 def from_problem(P, value_type="f32", max_iter=300, order=None):

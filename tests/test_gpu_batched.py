@@ -182,7 +182,7 @@ def test_batched_renumbered_equals_single_renumbered(small_batch, kind):
 
 def test_batched_order_must_stay_in_its_problem(small_batch):
     """A permutation that swaps row 0 of problem 0 with row 0 of problem 1 is
-    refused; so is a renumbering of a shared-matrix batch."""
+    refused; so is a shared-matrix order that is not a permutation."""
     P0, P1 = small_batch[0], small_batch[1]
     ro0 = np.arange(P0.m)
     ro0[0] = P0.m  # stacked with offset 0: global row P0.m (problem 1)
@@ -190,9 +190,9 @@ def test_batched_order_must_stay_in_its_problem(small_batch):
     ro1[0] = -P0.m  # stacked with offset P0.m: global row 0 (problem 0)
     with pytest.raises(lslu.LsluError, match="onto themselves"):
         lslu.from_problems([P0, P1], "f32", 5, orders=[(ro0, None), (ro1, None)])
-    with pytest.raises(ValueError):
-        lslu.BatchedSolver((P0.m, P0.n, P0.row_ptr, P0.col_idx, P0.vals), nrhs=2,
-                           orders=[(None, None)])
+    bad = np.zeros(P0.m, np.int32)
+    with pytest.raises(lslu.LsluError, match="permutation"):
+        lslu.shared_rhs(P0, 2, "f32", 5, order=(bad, None))
 
 
 def test_batched_renumbered_ties_follow_the_caller_numbering():
@@ -215,3 +215,22 @@ def test_batched_renumbered_ties_follow_the_caller_numbering():
     assert r1["tp"][0][0] == 0 and r1["tp"][1][0] == 0
     for p in range(2):
         assert np.allclose(r0["x"][p], r1["x"][p], rtol=1e-6, atol=0)
+
+
+@pytest.mark.parametrize("nrhs", [3, 16])
+def test_shared_matrix_renumbered_equals_single_renumbered(nrhs):
+    """lslu_create_shared_ordered: the one matrix renumbered for every
+    right-hand side gives each the renumbered single-problem result bit for
+    bit, x and pivots in the caller's numbering."""
+    Ps = tomo.make_shared_rhs("ct32", nrhs, seed=5300)
+    K = 30
+    order = tomo.locality_order(Ps[0])
+    b = np.concatenate([P.b for P in Ps])
+    with lslu.shared_rhs(Ps[0], nrhs, "f32", K, order=order) as bs:
+        r = bs.solve(b, K, "gcv")
+    for p, P in enumerate(Ps):
+        with lslu.from_problem(P, "f32", K, order=order) as s:
+            q = s.solve(P.b, K, "gcv")
+        assert r["status"][p] == q["status"] and r["k_done"][p] == q["k_done"]
+        assert np.array_equal(r["gp"][p], q["gp"]) and np.array_equal(r["tp"][p], q["tp"])
+        assert np.array_equal(r["x"][p], q["x"]), p
