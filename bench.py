@@ -6,7 +6,10 @@ seeded synthetic problem that stands in for a tomography test problem:
 512x512 image (n = 262144), 360 angles x 724 rays (m = 260640), Siddon
 ray-pixel lengths (~120M non-zeros), 20-ellipse phantom, 0.5% noise.
 A's values are stored in FP32 (default) with FP32 accumulation and FP32 basis
-vectors; H, W, the projected solve, lambda and x are FP64.
+vectors; H, W, the projected solve, lambda and x are FP64.  The handle stores
+A renumbered for gather locality (`--order tiles`, the default:
+tomo.locality_order through lslu_create_ordered); b, x and the pivots stay in
+the natural numbering, and pivot ties are broken by the natural index.
 
 Contract: `python bench.py --gpus N --steps K --warmup W` prints ONE JSON line.
 Under torchrun (N > 1) every rank runs an independent replica (the solve of
