@@ -280,9 +280,11 @@ __global__ void __launch_bounds__(32)
 #pragma unroll
       for (int e = 0; e < VEC; ++e) val[e] = fma(-c[j], (CT)b0[e], val[e]);
     }
-    // tie-breaking index of the lane's rows (rank_of, one vector load)
+    // tie-breaking index of the lane's rows: the row itself, or (renumbered
+    // handle, FP64 comparisons) its rank in one vector load; FP32 keys read
+    // the ranks of the few rows that can win after the warp's maximum below
     int rk[VEC];
-    if (pa.rank) {
+    if (!kKey && pa.rank) {
       if constexpr (VEC == 4) {
         if (full) {
           const int4 w = __ldg(reinterpret_cast<const int4*>(pa.rank + i0));
@@ -334,6 +336,24 @@ __global__ void __launch_bounds__(32)
         if (i0 + e < rows) v[i0 + e] = outv[e];
     }
     if constexpr (kKey) {
+      if (pa.rank) {
+        // only rows holding the warp's largest |v| can win here: their keys
+        // are rebuilt on the rank, the rest drop out (same maximum key as
+        // keying every row on its rank)
+        const unsigned wb = __reduce_max_sync(0xffffffffu, (unsigned)(tkey >> 32));
+        unsigned long long rkey = 0;
+        if (wb != 0u && (unsigned)(tkey >> 32) == wb) {
+#pragma unroll
+          for (int e = 0; e < VEC; ++e) {
+            const float a = fabsf((float)outv[e]);
+            if (i0 + e < rows && !usedf[e] && __float_as_uint(a) == wb) {
+              const unsigned long long kk = argkey(a, __ldg(pa.rank + i0 + e));
+              rkey = kk > rkey ? kk : rkey;
+            }
+          }
+        }
+        tkey = rkey;
+      }
       tkey = warp_max_u64(tkey);
       if (pa.nprob == 1) {
         bkey = tkey > bkey ? tkey : bkey;
