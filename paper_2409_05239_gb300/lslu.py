@@ -386,6 +386,15 @@ def projected_noalloc(H, beta, rule, lam, m, y=None, sigma=None, c=None, lam_out
         raise LsluError(st, lib.lslu_error_string(None).decode())
 
 
+def stack_orders(orders, k, off):
+    """Global order of a batch from per-problem orders (entry k of each pair,
+    None = identity) in the problems' own index spaces: problem p's index i
+    goes to off[p] + order_p[i]."""
+    return np.ascontiguousarray(np.concatenate([
+        (np.arange(off[p + 1] - off[p]) if o[k] is None else np.asarray(o[k])) + off[p]
+        for p, o in enumerate(orders)]), dtype=np.int32)
+
+
 class BatchedSolver:
     """One handle over several independent problems solved by one launch
     sequence (lslu_create_batched).  csr_list holds (m, n, row_ptr, col_idx,
@@ -424,12 +433,7 @@ class BatchedSolver:
         vals = np.ascontiguousarray(np.concatenate(vvs), dtype=np.float64)
         h = ctypes.c_void_p()
         if orders is not None:
-            def stack(k, off):
-                return np.ascontiguousarray(np.concatenate([
-                    (np.arange(off[p + 1] - off[p]) if o[k] is None else np.asarray(o[k]))
-                    + off[p] for p, o in enumerate(orders)]), dtype=np.int32)
-
-            ro, co = stack(0, self.row_off), stack(1, self.col_off)
+            ro, co = stack_orders(orders, 0, self.row_off), stack_orders(orders, 1, self.col_off)
             st = self.lib.lslu_create_batched_ordered(
                 self.nprob, _ptr(self.row_off), _ptr(self.col_off), _ptr(row_ptr), _ptr(col_idx),
                 _ptr(vals), VALUE_TYPES[value_type], self.max_iter, _ptr(ro), _ptr(co), stream,

@@ -131,3 +131,47 @@ def test_binding_fails_loudly_without_library(tmp_path):
             lslu.load(str(tmp_path / "missing.so"))
         finally:
             lslu._lib = saved
+
+
+def test_create_ordered_rejects_bad_orders_without_gpu(lib):
+    """The renumbering checks of the three ordered creates run before any CUDA
+    call: an order that is not a permutation, and a batch order that moves
+    an index into another problem, are refused."""
+    import numpy as np
+
+    h = ctypes.c_void_p()
+    rp = np.array([0, 1, 2], dtype=np.int64)
+    ci = np.array([0, 1], dtype=np.int32)
+    v = np.array([1.0, 2.0])
+    ok = np.array([1, 0], dtype=np.int32)
+    for ro, co in ((np.array([0, 0], np.int32), ok), (ok, np.array([0, 2], np.int32)),
+                   (np.array([-1, 0], np.int32), None)):
+        st = lib.lslu_create_ordered(2, 2, 2, rp.ctypes.data, ci.ctypes.data, v.ctypes.data, 1,
+                                     10, ro.ctypes.data,
+                                     None if co is None else co.ctypes.data, 0, None,
+                                     ctypes.byref(h))
+        assert st == lslu.ERR_INVALID_ARG and not h.value
+        assert b"permutation" in lib.lslu_error_string(None)
+    off = np.array([0, 1, 2], dtype=np.int64)
+    swap = np.array([1, 0], dtype=np.int32)  # row 0 of problem 0 <-> row 0 of problem 1
+    st = lib.lslu_create_batched_ordered(2, off.ctypes.data, off.ctypes.data, rp.ctypes.data,
+                                         ci.ctypes.data, v.ctypes.data, 1, 10, swap.ctypes.data,
+                                         None, None, ctypes.byref(h))
+    assert st == lslu.ERR_INVALID_ARG and b"onto themselves" in lib.lslu_error_string(None)
+    st = lib.lslu_create_shared_ordered(2, 2, rp.ctypes.data, ci.ctypes.data, v.ctypes.data, 2,
+                                        1, 10, None, np.array([1, 1], np.int32).ctypes.data,
+                                        None, ctypes.byref(h))
+    assert st == lslu.ERR_INVALID_ARG and b"permutation" in lib.lslu_error_string(None)
+
+
+def test_stack_orders():
+    """Per-problem orders become one global order of the batch: problem p's
+    index i goes to off[p] + order_p[i]; None is the identity."""
+    import numpy as np
+
+    off = np.array([0, 3, 5, 9])
+    g = lslu.stack_orders([(np.array([2, 0, 1]), None), (None, None),
+                           (np.array([3, 2, 1, 0]), None)], 0, off)
+    assert g.dtype == np.int32
+    assert g.tolist() == [2, 0, 1, 3, 4, 8, 7, 6, 5]
+    assert sorted(g.tolist()) == list(range(9))
