@@ -54,7 +54,7 @@ typedef enum {
  * Hessenberg entries (H, W), the projected solve, lambda and x stay FP64. */
 typedef enum { LSLU_F64 = 0, LSLU_F32 = 1, LSLU_BF16 = 2 } lslu_value_type;
 
-/* Choice of lambda_k in Algorithm 5 (Section 3.3). */
+/* Choice of lambda_k in Algorithm 5 (Section 3.2.1). */
 typedef enum {
   LSLU_LAMBDA_NONE = 0,  /* LSLU: lambda = 0                                  */
   LSLU_LAMBDA_FIXED = 1, /* the lambda argument for every k                   */
@@ -251,7 +251,7 @@ lslu_status lslu_solve_fixed_pivots(lslu_handle h, const double* b, const double
 lslu_status lslu_adjoint(lslu_handle h, const double* x_bar, int32_t ptr_location,
                          double* b_bar, double* lambda_bar, double* x0_bar);
 
-/* Hybrid LSLU with the stopping criterion of Section 3.4: runs up to K_max
+/* Hybrid LSLU with the stopping criterion of Section 3.2.2: runs up to K_max
  * iterations (2 <= K_max <= max_iter), solves the projected problem of every
  * k with the lambda rule, evaluates
  *   G^(k) = n ||beta e1 - H_{k+1,k} y_k||^2 / ((m - k) + sum_i lam_k^2/(sigma_i^2 + lam_k^2))^2
@@ -336,7 +336,8 @@ int64_t lslu_last_launch_count(lslu_handle h);
 
 /* K iterations of Hybrid LSLU with the optimal Tikhonov parameter of the
  * final projected problem, the one that minimises ||L_K y_K(lambda) - x_true||
- * (Section 4's reference curves; needs the true solution): the error is
+ * (Eq. lambda of Section 3.2.1, the reference curves of Section 4.1; needs the
+ * true solution): the error is
  * evaluated on the 257-point grid sigma_1 10^[-14, 2] and refined by 64
  * golden-section steps in log(lambda) between the best point's neighbours.
  * Outputs x_out (n) = x_K for that lambda (equal to lslu_solve with
@@ -346,7 +347,7 @@ int64_t lslu_last_launch_count(lslu_handle h);
 lslu_status lslu_solve_optimal(lslu_handle h, const double* b, int32_t K, const double* x_true,
                                int32_t ptr_location, double* x_out, double* lambda_out);
 
-/* Low-rank uncertainty quantification of Section 5 on the state of the last
+/* Low-rank uncertainty quantification of Section 4.2 on the state of the last
  * lslu_solve (k = its k_done): with A^T A ~ L_k W_k (D_k^T D_k)^-1 W_k^T L_k^T
  * (Eq. nhr2) and lambda = sigma / alpha, the posterior covariance
  * sigma^2 (lambda^2 I + A^T A)^-1 is approximated by

@@ -1,10 +1,17 @@
 """Plain FP64 oracle of LSLU and Hybrid LSLU (arXiv 2409.05239).
 
 TEST INFRASTRUCTURE ONLY.  Only tests, the smoke check and the CPU-baseline leg
-of the benchmark may import this module.  It is deliberately slow and literal:
-every step follows the paper in its order, in FP64 numpy / scipy, with library
-primitives (sparse mat-vec, dense SVD) as single steps.  Indices are 0-based
-(the paper is 1-based).
+of the benchmark may import this module.  It is deliberately slow and plain,
+FP64 numpy / scipy with library primitives (sparse mat-vec, dense SVD) as
+single steps, and computes what the method defines:
+  - the two bases of Section 2.2 (Eqs. nhr, nhr2): each new vector is A^T d_k
+    or A l_k with the earlier basis vectors of its side removed, one at a
+    time, by its own entries at their pivot rows, then divided by its largest
+    unpivoted entry, whose row becomes the next pivot;
+  - the projected Tikhonov problem of Section 3 (Eq. TSP) through the SVD of
+    H_{k+1,k} (Eqs. 3-4), with lambda_k from Eqs. (gcv2) / (wgcv_projected1);
+  - x_k = x_0 + L_k y_k.
+Indices are 0-based (the paper is 1-based).
 
 Parity pins (tests/test_oracle_pins.py) tie each function to something other
 than itself; every function below is pinned.
@@ -36,14 +43,14 @@ design notes):
       indices of row t of a given sample table (ties -> lowest index); when no
       sampled unpivoted entry is non-zero it falls back to the full search.
       The random indices are inputs, drawn by the caller.
-  R16 uncertainty quantification (Section 5): with lambda = sigma / alpha the
+  R16 uncertainty quantification (Section 4.2): with lambda = sigma / alpha the
       posterior covariance is sigma^2 (lambda^2 I + A^T A)^-1, so the low-rank
       Gamma_k uses lambda^2 where the printed formulas show lambda; D_k, W_k
       are the first k columns / the k x k block (A^T D_k = L_k W_k, Eq. nhr2).
       The Woodbury step keeps the factor lambda^-2 on the low-rank term:
       Gamma_k = sigma^2 lambda^-2 (I - Z Delta Z^T) (the last line of the
       printed derivation drops the factor its previous line carries).
-  R17 optimal lambda (Section 4, needs x_true): lam_k minimises
+  R17 optimal lambda (Section 3.2.1, Eq. lambda; needs x_true): lam_k minimises
       E(lam) = ||L_k y_k(lam) - x_true||^2; searched on the grid of R11, then 64
       golden-section steps in log(lam) between the best point's neighbours
       (kept only if E does not increase).
@@ -183,7 +190,7 @@ def hessenberg_rect_pivoted(A, b, x0, K, samples=None):
 
 
 def projected_svd(H: np.ndarray, beta: float):
-    """SVD quantities of the projected problem (Section 3.3, Eqs. 3-4, gcv2).
+    """SVD quantities of the projected problem (Section 3.2.1, Eqs. 3-4, gcv2).
 
     H = U Sigma V^T with U (k+1) x (k+1).  Returns sigma (k), c = beta U^T e1
     (length k+1) and V (k x k).
@@ -343,7 +350,7 @@ def stopping_iteration(G, tol):
 
 
 def hybrid_lslu_stopping(A, b, K_max, rule="wgcv", lam=0.0, tol=1e-6):
-    """Hybrid LSLU with the stopping criterion of Section 3.4: runs up to K_max
+    """Hybrid LSLU with the stopping criterion of Section 3.2.2: runs up to K_max
     iterations, evaluates G^(k) for every k with the lambda_k of the rule and
     returns (x_k at the stopping iteration, k, G history)."""
     m, n = A.shape
@@ -367,7 +374,7 @@ def hybrid_lslu_stopping(A, b, K_max, rule="wgcv", lam=0.0, tol=1e-6):
 
 
 def uq_lowrank(L, D, W, lam, sigma2):
-    """Low-rank posterior covariance of Section 5 (reading R16).
+    """Low-rank posterior covariance of Section 4.2 (reading R16).
 
     A^T A ~ L_k W_k (D_k^T D_k)^-1 W_k^T L_k^T = L_k G^T G L_k^T; with the
     eigendecomposition G^T G = V diag(s2) V^T and Z = L_k V,

@@ -1,4 +1,4 @@
-// Projected Tikhonov problem of Hybrid LSLU (Eq. TSP, Section 3.3), FP64.
+// Projected Tikhonov problem of Hybrid LSLU (Eq. TSP, Section 3.2.1), FP64.
 //
 // For one (k+1) x k upper Hessenberg H and beta (or one per batch entry, or
 // one per k of a history) four kernels run in sequence:

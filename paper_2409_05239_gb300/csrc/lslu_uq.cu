@@ -1,4 +1,4 @@
-// Low-rank uncertainty quantification of Section 5 (lslu_uq).
+// Low-rank uncertainty quantification of Section 4.2 (lslu_uq).
 //
 // After k iterations, A^T A ~ L_k G^T G L_k^T with G^T G = W_k (D_k^T D_k)^-1 W_k^T
 // (Eq. nhr2).  With lambda = sigma / alpha the posterior covariance

@@ -307,7 +307,7 @@ class Solver:
         return dict(x=x, lam=float(lam[0]))
 
     def uq(self, sigma2, lam, want_diag=True):
-        """Low-rank posterior variances (Section 5) from the last solve:
+        """Low-rank posterior variances (Section 4.2) from the last solve:
         dict(var_diag (n) or None, var_sum)."""
         d = np.zeros(self.n) if want_diag else None
         tot = np.zeros(1)

@@ -190,6 +190,59 @@ def check_lambda_is_minimiser(O, H, beta, omega=1.0):
         assert abs(np.log(lam) - res.x) < 1e-3, f"lambda {lam} vs scipy {np.exp(res.x)}"
 
 
+def wgcv_from_definition(H, beta, lam, omega):
+    """G(omega, lambda) of Eq. (wgcv_projected1) from its definition, without
+    an SVD: y_lambda from a QR of the stacked matrix [H; lambda I], the
+    residual (I - H H_lambda^+) beta e1 = beta e1 - H y_lambda, and
+    trace(H H_lambda^+) = ||Q_1||_F^2 with Q_1 the first k+1 rows of Q
+    (H = Q_1 R and H_lambda^+ = R^-1 Q_1^T), so the denominator is
+    ((k+1) - omega ||Q_1||_F^2)^2."""
+    kp1, k = H.shape
+    Q, R = np.linalg.qr(np.vstack([H, lam * np.eye(k)]))
+    rhs = np.zeros(kp1 + k)
+    rhs[0] = beta
+    y = np.linalg.solve(R, Q.T @ rhs)
+    r = rhs[:kp1] - H @ y
+    tr = float(np.sum(Q[:kp1] ** 2))
+    return k * float(r @ r) / (kp1 - omega * tr) ** 2
+
+
+def check_wgcv_rule(O, A, b, K, npts=801):
+    """The weighted-GCV rule (Section 3.2.1): at every iteration k, lambda_k
+    minimises G(omega, lambda) with omega = (k+1)/m, m the row count of A.
+    G comes from wgcv_from_definition and omega is computed here from k and
+    m, so neither the oracle's SVD form nor its omega is reused.  lambda_k
+    must reach the minimum of an npts-point log grid over
+    sigma_1 10^[-14, 2] and, when that minimum is interior, agree with a
+    bounded scalar minimiser (scipy) between its neighbours to 1e-3 in
+    log(lambda)."""
+    from scipy.optimize import minimize_scalar
+
+    m = A.shape[0]
+    res = O.hybrid_lslu(A, b, None, K, "wgcv")
+    assert res.k_done == K, f"wgcv run stopped at {res.k_done}"
+    for k in range(1, K + 1):
+        H = res.H[:k + 1, :k]
+        omega = (k + 1) / m
+        lam = float(res.lam_hist[k - 1])
+
+        def G(t):
+            return wgcv_from_definition(H, res.beta, t, omega)
+
+        s1 = np.linalg.norm(H, 2)
+        grid = s1 * 10.0 ** np.linspace(-14.0, 2.0, npts)
+        Gg = np.array([G(t) for t in grid])
+        j = int(np.argmin(Gg))
+        assert lam > 0.0 and G(lam) <= Gg[j] * (1 + 1e-9), \
+            f"k={k}: G(lambda_k)={G(lam)} above the grid minimum {Gg[j]}"
+        if 0 < j < npts - 1:
+            r = minimize_scalar(lambda t: G(np.exp(t)), method="bounded",
+                                bounds=(np.log(grid[j - 1]), np.log(grid[j + 1])),
+                                options={"xatol": 1e-10})
+            assert abs(np.log(lam) - r.x) < 1e-3, \
+                f"k={k}: lambda_k={lam} but the minimiser is {np.exp(r.x)}"
+
+
 # ----------------------------------------------------------------------------
 # whole-iterate pins (Eq. quasi, Eq. TP, Theorems 1 and 2)
 # ----------------------------------------------------------------------------

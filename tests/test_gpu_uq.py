@@ -1,4 +1,4 @@
-"""Low-rank uncertainty quantification (Section 5) on the GPU (lslu_uq)
+"""Low-rank uncertainty quantification (Section 4.2) on the GPU (lslu_uq)
 against the oracle's eigendecomposition/Woodbury form on the same basis."""
 import numpy as np
 import pytest

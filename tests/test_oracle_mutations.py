@@ -26,6 +26,10 @@ MUTATIONS = {
                     "den = 1.0 + np.sum(((1.0 - omega) * L2 + s2) / (s2 + L2))"),
     "slope_sign": ("return float(dN * Dn - 2.0 * N * dD)", "return float(dN * Dn + 2.0 * N * dD)"),
     "recombination_basis": ("x = x + hp[\"L\"] @ y", "x = x + hp[\"L\"][:, ::-1] @ y"),
+    "wgcv_omega_k_over_m": ("return select_lambda(sigma, c, (k + 1) / m)",
+                            "return select_lambda(sigma, c, k / m)"),
+    "wgcv_omega_columns": ("lk = _lambda_for(rule, lam, s, c, kk, m)",
+                           "lk = _lambda_for(rule, lam, s, c, kk, n)"),
 }
 
 
@@ -74,6 +78,8 @@ def run_all_pins(M, P):
     attempt("lambda_min", lambda: pins.check_lambda_is_minimiser(M, H, hp["beta"], 1.0))
     attempt("oblique", lambda: pins.check_oblique_bruteforce(M, A, P.b, 10, 1e-2, "fixed"))
     attempt("oblique_gcv", lambda: pins.check_oblique_bruteforce(M, A, P.b, 10, 0.0, "gcv"))
+    Aw, _, bw = pins.random_problem(40, 25, seed=5, decay=0.8)
+    attempt("wgcv_rule", lambda: pins.check_wgcv_rule(M, Aw, bw, 14, npts=401))
     return failures
 
 

@@ -80,6 +80,22 @@ def test_lambda_is_minimiser(ct32_run, k, omega):
     pins.check_lambda_is_minimiser(O, H, ct32_run["beta"], omega)
 
 
+@pytest.mark.parametrize("m,n,seed,decay", [(40, 25, 5, 0.8), (40, 25, 7, 0.7), (60, 30, 3, 0.85),
+                                             (25, 40, 9, 0.8)])
+def test_wgcv_rule_minimises_definition(m, n, seed, decay):
+    """Weighted GCV with omega = (k+1)/m (Section 3.2.1): the oracle's
+    lambda_k minimises Eq. (wgcv_projected1) built from its definition, at
+    every k, on problems where m != n and m is small enough that omega moves
+    the minimiser."""
+    A, _, b = pins.random_problem(m, n, seed=seed, decay=decay)
+    pins.check_wgcv_rule(O, A, b, 14)
+
+
+def test_wgcv_rule_ct32(ct32):
+    """The same on the 32x32 tomography workload (m = 2070 rows, n = 1024)."""
+    pins.check_wgcv_rule(O, ct32.scipy(), ct32.b, 20, npts=401)
+
+
 def test_gcv_k1_closed_form():
     """For k = 1 the GCV minimiser has the closed form f* = c2^2 / c1^2 with
     f = lam^2 / (sigma^2 + lam^2) (set dG/df = 0 in Eq. gcv2)."""

@@ -1,4 +1,4 @@
-"""Pins of the low-rank uncertainty quantification (Section 5) in the oracle.
+"""Pins of the low-rank uncertainty quantification (Section 4.2) in the oracle.
 
 The oracle follows the paper's steps (G^T G, its eigendecomposition, Z, the
 Woodbury form).  The pins form the same covariance densely from its
