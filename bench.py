@@ -107,7 +107,6 @@ SPMV_TRAFFIC = {
             "16x2/16-bit": (800.09e6, 796.17e6), "32x1/16-bit": (791.64e6, 790.90e6),
             "16x1/16-bit": (804.80e6, 809.89e6), "8x1/16-bit": (854.40e6, 906.59e6),
             "8x2/16-bit": (832.11e6, 831.46e6), "4x1/16-bit": (918.24e6, 897.54e6),
-            "tma": (971.92e6, 972.59e6), "tma/16-bit": (790.21e6, 791.06e6),
             "32x8e": (971.87e6, 972.27e6), "32x8e/16-bit": (791.25e6, 791.03e6),
             "32x4e": (971.84e6, 972.46e6), "32x4e/16-bit": (793.61e6, 791.96e6),
         },
@@ -118,7 +117,6 @@ SPMV_TRAFFIC = {
             "16x2/16-bit": (799.75e6, 796.06e6), "32x1/16-bit": (791.53e6, 790.91e6),
             "16x1/16-bit": (804.78e6, 810.25e6), "8x1/16-bit": (855.61e6, 932.44e6),
             "8x2/16-bit": (832.43e6, 837.37e6), "4x1/16-bit": (931.75e6, 893.35e6),
-            "tma": (971.69e6, 972.67e6), "tma/16-bit": (790.25e6, 791.12e6),
             "32x8e": (971.88e6, 972.27e6), "32x8e/16-bit": (791.30e6, 791.00e6),
             "32x4e": (972.05e6, 972.28e6), "32x4e/16-bit": (793.53e6, 791.89e6),
         },
@@ -134,8 +132,6 @@ SPMV_TRAFFIC = {
             "0e773294834ee47b18af1f88926ceff2d1210b793e4dcb2cf9260028db12f63a",
         "paper_2409_05239_gb300/csrc/lslu_spmv_shapes_c.cu":
             "96910620ae56de115fcdea59e6c10dfb7408ff7c9610c8323ba713ab471e2a0f",
-        "paper_2409_05239_gb300/csrc/lslu_spmv_tma.cu":
-            "3258c2e4fb82c38ccf340c4f48253dc396e784b74b1ebbdd43ae8083ee84199c",
         "paper_2409_05239_gb300/csrc/lslu_internal.cuh":
             "d306ddcf7e4c4a5b57d4d76e5550e0d08625a3ae32182b984aaea553fc8e4063",
     },

@@ -368,20 +368,15 @@ lslu_status lslu_uq(lslu_handle h, double sigma2, double lambda, int32_t ptr_loc
  * FP64 values), 3: 8x1, 4: 8x2, 5: 4x1; shapes 6-11 are the same lane shapes
  * on 16-bit column offsets in chunks of 8 entries (2.5 instead of 4 bytes per
  * entry; available when every 8-entry unit of the matrix spans fewer than
- * 2^16 columns, see lslu_spmv_config).  Shapes 12 ("tma", 32-bit columns)
- * and 13 ("tma/16-bit", 16-bit offsets) stream the matrix through shared
- * memory with bulk copies in stages of whole rows and let every thread take
- * 8-entry units; available when every padded row holds at most 2048 entries
- * (1024 for FP64 values).  Shapes 14 ("32x8e") and 16 ("32x4e") put the
- * 32 lanes of a warp on consecutive entries of one row (8 or 4 entries in
- * flight per lane), so neighbouring columns share the sectors of their x
- * gathers; 15 and 17 are the same on 16-bit offsets.  Every shape computes the same
- * products with a different summation order, so results change in rounding
- * only; each is bitwise reproducible.  A staged product whose copies never
- * arrive gives up after a bounded wait and the solve returns
- * LSLU_ERR_TIMEOUT.  The shared-matrix product of lslu_create_shared follows
- * the default 16-lane shapes.  Errors: LSLU_ERR_INVALID_ARG for a shape
- * outside [0, 18) or one the matrix does not support. */
+ * 2^16 columns, see lslu_spmv_config).  Shapes 12 ("32x8e") and 14
+ * ("32x4e") put the 32 lanes of a warp on consecutive entries of one row (8
+ * or 4 entries in flight per lane), so neighbouring columns share the sectors
+ * of their x gathers; 13 and 15 are the same on 16-bit offsets.  Every shape
+ * computes the same products with a different summation order, so results
+ * change in rounding only; each is bitwise reproducible.  The shared-matrix
+ * product of lslu_create_shared follows the default 16-lane shapes.
+ * Errors: LSLU_ERR_INVALID_ARG for a shape outside [0, 16) or one the matrix
+ * does not support. */
 lslu_status lslu_set_spmv_shape(lslu_handle h, int32_t shape_A, int32_t shape_AT);
 
 /* The sparse products' configuration (host outputs, any may be NULL): the
@@ -397,9 +392,8 @@ lslu_status lslu_spmv_config(lslu_handle h, int32_t* shape_A, int32_t* shape_AT,
  * by more than 3% (closer times swap places from run to run).  Allocates
  * and frees the flush buffer (LSLU_ERR_OOM if it cannot).  Outputs (host, any may
  * be NULL): the chosen shapes and the average time of every shape in
- * microseconds (us[0..17] for A, us[18..35] for A^T; -1 where unavailable).
- * Drops captured solves (they hold the old kernels).  LSLU_ERR_TIMEOUT if a
- * staged product gave up waiting for its copies. */
+ * microseconds (us[0..15] for A, us[16..31] for A^T; -1 where unavailable).
+ * Drops captured solves (they hold the old kernels). */
 lslu_status lslu_tune_spmv(lslu_handle h, int32_t reps, int32_t* shape_A, int32_t* shape_AT,
                            double* us);
 

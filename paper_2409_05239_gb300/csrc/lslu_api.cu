@@ -1390,14 +1390,10 @@ extern "C" lslu_status lslu_set_spmv_shape(lslu_handle h, int32_t shape_A, int32
   Ctx* c = h;
   if (!c) return set_err(nullptr, LSLU_ERR_INVALID_ARG, "NULL handle");
   if (shape_A < 0 || shape_A >= kNumShapes || shape_AT < 0 || shape_AT >= kNumShapes)
-    return set_err(c, LSLU_ERR_INVALID_ARG, "shape must be in [0, 18)");
+    return set_err(c, LSLU_ERR_INVALID_ARG, "shape must be in [0, 16)");
   if ((shape_cmp(shape_A) && !c->A.compressed) || (shape_cmp(shape_AT) && !c->AT.compressed))
     return set_err(c, LSLU_ERR_INVALID_ARG,
                    "16-bit offset shapes need a matrix whose 8-entry units span < 2^16 columns");
-  if ((shape_staged(shape_A) && !c->A.tma_ok) || (shape_staged(shape_AT) && !c->AT.tma_ok))
-    return set_err(c, LSLU_ERR_INVALID_ARG,
-                   "staged shapes need every row to fit a stage (2048 padded entries, "
-                   "1024 for FP64 values)");
   CK(cudaStreamSynchronize(c->stream));
   c->A.shape = shape_A;
   c->AT.shape = shape_AT;
@@ -1458,8 +1454,7 @@ extern "C" lslu_status lslu_tune_spmv(lslu_handle h, int32_t reps, int32_t* shap
   lslu_status st = LSLU_OK;
   for (int sh = 0; sh < kNumShapes && st == LSLU_OK; ++sh) {
     const bool cmp = shape_cmp(sh);
-    if ((cmp && !(c->A.compressed && c->AT.compressed)) ||
-        (shape_staged(sh) && !(c->A.tma_ok && c->AT.tma_ok))) {
+    if (cmp && !(c->A.compressed && c->AT.compressed)) {
       if (us) us[sh] = us[kNumShapes + sh] = -1.0;  // not available
       continue;
     }
@@ -1503,16 +1498,6 @@ extern "C" lslu_status lslu_tune_spmv(lslu_handle h, int32_t reps, int32_t* shap
   }
   for (auto& e : ev) cudaEventDestroy(e);
   cudaFree(flush);
-  if (st == LSLU_OK && c->A.tma_err && c->AT.tma_err) {  // a staged product gave up waiting
-    int32_t bad[2] = {0, 0};
-    cudaError_t e = cudaMemcpy(&bad[0], c->A.tma_err, sizeof(int32_t), cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess)
-      e = cudaMemcpy(&bad[1], c->AT.tma_err, sizeof(int32_t), cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess)
-      st = set_err(c, LSLU_ERR_CUDA, std::string("tuning: ") + cudaGetErrorString(e));
-    else if (bad[0] || bad[1])
-      st = set_err(c, LSLU_ERR_TIMEOUT, "tuning: a staged sparse product timed out");
-  }
   if (st != LSLU_OK) {
     c->A.shape = saved[0];
     c->AT.shape = saved[1];
@@ -1707,12 +1692,19 @@ extern "C" lslu_status lslu_projected(lslu_handle h, int32_t k, const double* H,
     return set_err(c, LSLU_ERR_INVALID_ARG, "unknown ptr_location");
   cudaStream_t s = c->stream;
   const double* dH = H;
-  double* stage = nullptr;
+  // staging copy of a host H, freed on every exit (cudaFree waits for the
+  // work queued on it)
+  struct StageGuard {
+    double* p = nullptr;
+    ~StageGuard() {
+      if (p) cudaFree(p);
+    }
+  } stage;
   if (ptr_location == LSLU_HOST) {
-    CK(dmalloc(&stage, (size_t)(k + 1) * k));
-    CK(cudaMemcpy2DAsync(stage, (k + 1) * 8, H, (size_t)ldh * 8, (k + 1) * 8, k,
+    CK(dmalloc(&stage.p, (size_t)(k + 1) * k));
+    CK(cudaMemcpy2DAsync(stage.p, (k + 1) * 8, H, (size_t)ldh * 8, (k + 1) * 8, k,
                          cudaMemcpyHostToDevice, s));
-    dH = stage;
+    dH = stage.p;
     ldh = k + 1;
   }
   ProjArgs pa;
@@ -1745,7 +1737,6 @@ extern "C" lslu_status lslu_projected(lslu_handle h, int32_t k, const double* H,
   if (lambda_out) CK(cudaMemcpyAsync(lambda_out, c->proj_out + (k - 1), 8, kind, s));
   if (resid_out) CK(cudaMemcpyAsync(resid_out, c->proj_out + c->res_off + (k - 1), 8, kind, s));
   CK(cudaStreamSynchronize(s));
-  if (stage) cudaFree(stage);
   return LSLU_OK;
 }
 

@@ -64,11 +64,8 @@ constexpr int kTile = 128;
 // or by lslu_tune_spmv / lslu_set_spmv_shape.  Shapes 0-5 read 32-bit column
 // indices (chunks of 4 entries), shapes 6-11 the same lane shapes on 16-bit
 // offsets (chunks of 8 entries; only for matrices that have them).
-// Shapes 12 and 13 stream the matrix through shared memory with bulk copies
-// (lslu_spmv_tma.cu; 32-bit columns and 16-bit offsets), for matrices whose
-// rows fit a stage.  Shapes 14-17 put the 32 lanes of a warp on consecutive
-// entries of one row (8 or 4 entries in flight per lane; 32-bit columns and
-// 16-bit offsets).
+// Shapes 12-15 put the 32 lanes of a warp on consecutive entries of one row
+// (8 or 4 entries in flight per lane; 32-bit columns and 16-bit offsets).
 enum {
   kShapeG16U2 = 0,
   kShapeG32U1 = 1,
@@ -77,27 +74,17 @@ enum {
   kShapeG8U2 = 4,
   kShapeG4U1 = 5,
   kShapesPerFormat = 6,
-  kShapeTma = 12,
-  kShapeTmaCmp = 13,
-  kShapeE8 = 14,
-  kShapeE8Cmp = 15,
-  kShapeE4 = 16,
-  kShapeE4Cmp = 17,
-  kNumShapes = 18
+  kShapeE8 = 12,
+  kShapeE8Cmp = 13,
+  kShapeE4 = 14,
+  kShapeE4Cmp = 15,
+  kNumShapes = 16
 };
 int default_shape(int vt);
 // the shape reads 16-bit column offsets
 inline bool shape_cmp(int sh) {
-  return (sh >= kShapesPerFormat && sh < kShapeTma) || (sh >= kShapeTma && (sh & 1));
+  return (sh >= kShapesPerFormat && sh < kShapeE8) || (sh >= kShapeE8 && (sh & 1));
 }
-// the shape streams through shared memory (needs every row to fit a stage)
-inline bool shape_staged(int sh) { return sh == kShapeTma || sh == kShapeTmaCmp; }
-
-// Stages of the staged shapes: whole rows, at most this many padded entries
-// (FP64 values: the smaller figure) and rows each.
-constexpr int kTmaStageEntries = 2048;
-constexpr int kTmaStageEntriesF64 = 1024;
-constexpr int kTmaStageRows = 256;
 
 struct DevCsr {
   int shape = kShapeG16U2;
@@ -112,14 +99,6 @@ struct DevCsr {
   int32_t* row_len = nullptr;  // rows (padded length, multiple of kRowAlign)
   int32_t* col = nullptr;      // nnz_padded
   void* val = nullptr;         // nnz_padded, type per value type
-  // staged shapes: 2 (tma_nstages + 1) ints (first row, first entry of every
-  // stage), the number of streaming blocks, whether every row fits a stage,
-  // and a device word a timed-out wait sets
-  int32_t* tma_stage = nullptr;
-  int tma_nstages = 0;
-  int tma_blocks = 0;
-  int tma_ok = 0;
-  int32_t* tma_err = nullptr;
 };
 
 // Device-resident state of one problem of a solve (one per problem of a
@@ -333,12 +312,6 @@ void launch_spmv_shape_b(int shape, const DevCsr& A, int vt, const void* x, void
                          cudaStream_t s);
 void launch_spmv_pivots_shape_b(int shape, const DevCsr& A, int vt, const void* x, void* y,
                                 const PivotCoef& pc, cudaStream_t s);
-// Staged shapes (lslu_spmv_tma.cu): plain product, or with the pivot-row
-// coefficients (the format follows A.use_cmp); shared memory per block.
-void launch_spmv_tma(const DevCsr& A, int vt, const void* x, void* y, cudaStream_t s);
-void launch_spmv_pivots_tma(const DevCsr& A, int vt, const void* x, void* y, const PivotCoef& pc,
-                            cudaStream_t s);
-size_t tma_smem_need(int vt, int cmp);
 void launch_spmv_shape_c(int shape, const DevCsr& A, int vt, const void* x, void* y,
                          cudaStream_t s);
 void launch_spmv_pivots_shape_c(int shape, const DevCsr& A, int vt, const void* x, void* y,
@@ -347,10 +320,6 @@ inline void launch_spmv_shape(int shape, const DevCsr& A, int vt, const void* x,
                               cudaStream_t s) {
   if (shape >= kShapeE8) {
     launch_spmv_shape_c(shape, A, vt, x, y, s);
-    return;
-  }
-  if (shape >= kShapeTma) {
-    launch_spmv_tma(A, vt, x, y, s);
     return;
   }
   const int g = shape % kShapesPerFormat;  // the format follows A.use_cmp
@@ -363,10 +332,6 @@ inline void launch_spmv_pivots_shape(int shape, const DevCsr& A, int vt, const v
                                      void* y, const PivotCoef& pc, cudaStream_t s) {
   if (shape >= kShapeE8) {
     launch_spmv_pivots_shape_c(shape, A, vt, x, y, pc, s);
-    return;
-  }
-  if (shape >= kShapeTma) {
-    launch_spmv_pivots_tma(A, vt, x, y, pc, s);
     return;
   }
   const int g = shape % kShapesPerFormat;

@@ -39,6 +39,8 @@
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include <cmath>
 
 #include "lslu_internal.cuh"
@@ -1027,16 +1029,31 @@ int64_t projected_slot_doubles(int kk, int /*CL*/) {
   return 5 * (int64_t)(kk + 1) + kGrid + 1 + (int64_t)kk * kk + (int64_t)(kk + 1) * kk + 64;
 }
 
-// SMs of the device the projected kernels were set up on
-static int g_num_sms = 0;
+// Per-device set-up of the projected kernels: their attributes (cluster size
+// above 8, dynamic shared memory above 48 KB) are properties of the device
+// they are set on, so they are set once for every device the process uses,
+// with the cluster size found there and the device's SM count.  A mutex
+// guards the first call on each device.
+namespace {
+constexpr int kProjMaxDevices = 64;
+struct ProjDeviceSetup {
+  int cluster = 0;  // 0: not set up yet
+  int num_sms = 0;
+};
+ProjDeviceSetup g_proj_setup[kProjMaxDevices];
+std::mutex g_proj_setup_mutex;
 
-int projected_cluster_size() {
-  static int cs = 0;
-  if (cs) return cs;
+ProjDeviceSetup setup_current_device() {
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess ||
-      cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-    g_num_sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kProjMaxDevices) {
+    cudaGetLastError();
+    return ProjDeviceSetup{1, 0};
+  }
+  std::lock_guard<std::mutex> lock(g_proj_setup_mutex);
+  ProjDeviceSetup& d = g_proj_setup[dev];
+  if (d.cluster) return d;
+  if (cudaDeviceGetAttribute(&d.num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    d.num_sms = 0;
   cudaFuncSetAttribute(k_bidiag, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   cudaFuncSetAttribute(k_bidiag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
   cudaFuncSetAttribute(k_sigma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
@@ -1062,9 +1079,12 @@ int projected_cluster_size() {
     }
     cudaGetLastError();
   }
-  cs = best;
-  return cs;
+  d.cluster = best;
+  return d;
 }
+}  // namespace
+
+int projected_cluster_size() { return setup_current_device().cluster; }
 
 cudaError_t launch_projected(const ProjArgs& a, ProjWork& w, cudaStream_t s) {
   // one problem per k of k_first..k_last (histories), or one final problem
@@ -1076,6 +1096,7 @@ cudaError_t launch_projected(const ProjArgs& a, ProjWork& w, cudaStream_t s) {
   if (!batch && nprob > 1 && !w.packed) return cudaErrorInvalidValue;
   const int CL = w.cluster;
   if (CL < 1 || CL > kMaxCluster) return cudaErrorInvalidValue;
+  const ProjDeviceSetup dev_setup = setup_current_device();
   const int kmax = a.k_last;
   const size_t K1 = (size_t)kmax + 1;
   const int ncl = (kmax + CL - 1) / CL;
@@ -1104,7 +1125,7 @@ cudaError_t launch_projected(const ProjArgs& a, ProjWork& w, cudaStream_t s) {
   // 2. singular values and weights: k + 1 warps per problem
   const dim3 g2((unsigned)((K1 + kWS - 1) / kWS), (unsigned)nprob);
   size_t sm2 = dyn2;
-  if ((int64_t)g2.x * g2.y <= g_num_sms && sm2 < kSmemOnePerSm) sm2 = kSmemOnePerSm;
+  if ((int64_t)g2.x * g2.y <= dev_setup.num_sms && sm2 < kSmemOnePerSm) sm2 = kSmemOnePerSm;
   k_sigma<<<g2, kWS * 32, sm2, s>>>(a, w);
   // 3. the GCV function on the lambda grid
   if (a.rule == LSLU_LAMBDA_GCV || a.rule == LSLU_LAMBDA_WGCV) {

@@ -224,7 +224,7 @@ cudaError_t upload_padded(int64_t rows, int64_t cols, const std::vector<int64_t>
   out->nnz_padded = tot;
   size_t vbytes = vt == LSLU_F64 ? 8 : (vt == LSLU_F32 ? 4 : 2);
   cudaError_t e;
-  // row pointers readable up to a multiple of 4 entries (aligned bulk copies)
+  // row pointers padded to a multiple of 4 entries
   const int64_t nrp = (rows + 1 + 3) / 4 * 4;
   prp.resize((size_t)nrp, (int32_t)tot);
   if ((e = cudaMalloc(&out->row_ptr, nrp * sizeof(int32_t))) != cudaSuccess) return e;
@@ -238,40 +238,6 @@ cudaError_t upload_padded(int64_t rows, int64_t cols, const std::vector<int64_t>
   if ((e = cudaMemcpyAsync(out->row_ptr, prp.data(), nrp * sizeof(int32_t),
                            cudaMemcpyHostToDevice, s)) != cudaSuccess)
     return e;
-  // stages of the staged shapes: whole rows, at most SE entries and
-  // kTmaStageRows rows each (unavailable if a row alone exceeds SE)
-  {
-    const int64_t SE = vt == LSLU_F64 ? kTmaStageEntriesF64 : kTmaStageEntries;
-    std::vector<int32_t> stg;
-    bool ok = rows > 0;
-    int64_t r = 0;
-    while (ok && r < rows) {
-      const int64_t e0 = prp[r];
-      int64_t r1 = r;
-      while (r1 < rows && r1 - r < kTmaStageRows && prp[r1 + 1] - e0 <= SE) ++r1;
-      if (r1 == r) ok = false;
-      stg.push_back((int32_t)r);
-      stg.push_back((int32_t)e0);
-      r = r1;
-    }
-    if (ok) {
-      stg.push_back((int32_t)rows);
-      stg.push_back((int32_t)tot);
-      out->tma_nstages = (int)(stg.size() / 2 - 1);
-      if ((e = cudaMalloc(&out->tma_stage, stg.size() * sizeof(int32_t))) != cudaSuccess) return e;
-      if ((e = cudaMemcpyAsync(out->tma_stage, stg.data(), stg.size() * sizeof(int32_t),
-                               cudaMemcpyHostToDevice, s)) != cudaSuccess)
-        return e;
-      if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;  // stg goes out of scope
-      int dev = 0, sms = 0;
-      if (cudaGetDevice(&dev) == cudaSuccess &&
-          cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
-        out->tma_blocks = 2 * sms;  // two streaming blocks per SM
-      out->tma_ok = out->tma_blocks > 0;
-    }
-    if ((e = cudaMalloc(&out->tma_err, sizeof(int32_t))) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(out->tma_err, 0, sizeof(int32_t), s)) != cudaSuccess) return e;
-  }
   if (rows && (e = cudaMemcpyAsync(out->row_len, prl.data(), rows * sizeof(int32_t),
                                    cudaMemcpyHostToDevice, s)) != cudaSuccess)
     return e;
@@ -372,8 +338,6 @@ void free_csr(DevCsr* c) {
   cudaFree(c->val);
   cudaFree(c->off);
   cudaFree(c->ubase);
-  cudaFree(c->tma_stage);
-  cudaFree(c->tma_err);
   *c = DevCsr();
 }
 

@@ -317,7 +317,7 @@ class Solver:
 
     SHAPES = ("16x2", "32x1", "16x1", "8x1", "8x2", "4x1",
               "16x2/16-bit", "32x1/16-bit", "16x1/16-bit", "8x1/16-bit", "8x2/16-bit", "4x1/16-bit",
-              "tma", "tma/16-bit", "32x8e", "32x8e/16-bit", "32x4e", "32x4e/16-bit")
+              "32x8e", "32x8e/16-bit", "32x4e", "32x4e/16-bit")
 
     def set_spmv_shape(self, shape_A, shape_AT=None):
         """Row shape of the sparse products (index into SHAPES)."""
@@ -373,12 +373,30 @@ class Solver:
         self.close()
 
 
+def torch_f64():
+    import torch
+
+    return torch.float64
+
+
 def projected_noalloc(H, beta, rule, lam, m, y=None, sigma=None, c=None, lam_out=None,
                       resid_out=None, stream=None):
     """Allocation-free projected solve: H and every output are device tensors
     (torch, FP64); asynchronous on stream.  Raises LsluError on failure."""
     lib = load()
     k = H.shape[1]
+    # the library sees raw pointers only: check the layouts it assumes here
+    if H.dtype != torch_f64() or not H.is_cuda or H.dim() != 2 or H.stride(0) != 1 \
+            or H.shape[0] < k + 1:
+        raise ValueError("H must be a (k+1) x k column-major float64 CUDA tensor")
+    for name, t, need in (("y", y, k), ("sigma", sigma, k), ("c", c, k + 1),
+                          ("lam_out", lam_out, 1), ("resid_out", resid_out, 1)):
+        if t is None:
+            continue
+        if t.dtype != torch_f64() or t.device != H.device or not t.is_contiguous() \
+                or t.numel() < need:
+            raise ValueError(f"{name} must be a contiguous float64 tensor on {H.device} "
+                             f"with at least {need} entries")
     st = lib.lslu_projected_noalloc(k, _ptr(H), H.stride(1), float(beta), RULES[rule],
                                     float(lam), int(m), _ptr(y), _ptr(sigma), _ptr(c),
                                     _ptr(lam_out), _ptr(resid_out), stream)

@@ -14,7 +14,8 @@ single-problem solve once per named sparse-product shape (both directions set
 to it; "all" = every shape in lslu.Solver.SHAPES order), so that a profiler sees
 the products of every shape in one process: each solve launches 2 K products,
 A^T d_k then A l_k for k = 0..K-1.  `--order tiles` builds the handle with
-tomo.locality_order's renumbering (lslu_create_ordered).
+tomo.locality_order's renumbering (lslu_create_ordered); `--tune` runs the
+sparse-product autotuner first, as the benchmark does.
 """
 from __future__ import annotations
 
@@ -36,6 +37,8 @@ def main(argv=None):
     ap.add_argument("--batch", type=int, default=0, help="solve this many uneven problems")
     ap.add_argument("--shapes", default="", help="comma-separated shape names, or 'all'")
     ap.add_argument("--order", default="natural", choices=["natural", "tiles"])
+    ap.add_argument("--tune", action="store_true",
+                    help="run the sparse-product autotuner before the solves (as bench.py does)")
     a = ap.parse_args(argv)
 
     import torch
@@ -66,6 +69,8 @@ def main(argv=None):
             [t for t in a.shapes.split(",") if t]
         order = tomo.locality_order(P) if a.order == "tiles" else None
         with lslu.from_problem(P, a.value_type, K, order=order) as s:
+            if a.tune:
+                s.tune_spmv(reps=3)
             runs = []
             for name in names or [None]:
                 if name is not None:
@@ -77,8 +82,10 @@ def main(argv=None):
                 runs.append({"shape": name, "status": r["status"],
                              "seconds_per_solve": (time.perf_counter() - t0) / a.repeat})
             launches = s.last_launch_count()
+            cfg = s.spmv_config()
         out = {"workload": a.workload, "order": a.order, "m": P.m, "n": P.n, "nnz": P.nnz, "K": K,
                "k_done": r["k_done"], "status": r["status"], "launches": launches,
+               "spmv_config": cfg,
                "seconds_per_solve": runs[-1]["seconds_per_solve"],
                "rel_err_x_true": float(np.linalg.norm(r["x"] - P.x_true) /
                                        np.linalg.norm(P.x_true))}

@@ -176,14 +176,14 @@ def test_graph_replay_matches_direct_launches(ct32, monkeypatch):
     assert n == 80 and ms > 0
 
 
-@pytest.mark.parametrize("shape", range(18))
+@pytest.mark.parametrize("shape", range(16))
 def test_every_spmv_shape_keeps_f64_parity(ct32, shape):
     """All row shapes of the sparse products (the autotuner's choices) give the
     oracle's pivots and x within the FP64 tolerance."""
     K = 30
     ref = O.hybrid_lslu(ct32.scipy(), ct32.b, None, K, "gcv", histories=False)
     with lslu.from_problem(ct32, "f64", K) as s:
-        s.set_spmv_shape(shape, (shape + 1) % 18)
+        s.set_spmv_shape(shape, (shape + 1) % 16)
         r = s.solve(ct32.b, K, "gcv")
         r2 = s.solve(ct32.b, K, "gcv")
     assert np.array_equal(r["gp"], ref.gp) and np.array_equal(r["tp"], ref.tp)
@@ -197,7 +197,7 @@ def test_autotuner_picks_a_shape(ct32):
     ref = O.hybrid_lslu(A32, ct32.b, None, K, "gcv", histories=False)
     with lslu.from_problem(ct32, "f32", K) as s:
         t = s.tune_spmv(reps=3)
-        assert 0 <= t["shape_A"] < 18 and 0 <= t["shape_AT"] < 18
+        assert 0 <= t["shape_A"] < 16 and 0 <= t["shape_AT"] < 16
         for key, shp in (("us_A", t["shape_A"]), ("us_AT", t["shape_AT"])):
             best = min(t[key].values())
             chosen = t[key][s.SHAPES[shp]]

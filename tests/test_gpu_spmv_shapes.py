@@ -1,9 +1,9 @@
-"""The staged sparse products (row shapes "tma" and "tma/16-bit": the matrix
-streamed through shared memory by bulk copies in stages of whole rows)
-through the C ABI (lslu_set_spmv_shape, lslu_spmv) against the FP64 product
-of scipy, on matrices that exercise the stage boundaries: empty rows, stages
-cut by the 256-row limit, a row that fills a whole stage, and a matrix whose
-longest row does not fit a stage (the shapes are then refused)."""
+"""Every row shape of the sparse products (lanes per row x chunks in flight,
+32-bit columns or 16-bit offsets) through the C ABI (lslu_set_spmv_shape,
+lslu_spmv) against the FP64 product of scipy within the rounding bound of the
+accumulation type, on matrices with empty rows, rows of mixed length (ragged
+ends of the 8-entry units and of the 64-entry transposed blocks), one long
+row and many one-entry rows; and the refusal of an out-of-range shape."""
 import numpy as np
 import pytest
 import scipy.sparse as sp
@@ -12,7 +12,7 @@ from paper_2409_05239_gb300 import lslu
 
 pytestmark = pytest.mark.gpu
 
-TMA, TMA_CMP = 12, 13
+NSHAPES = len(lslu.Solver.SHAPES)
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -88,8 +88,8 @@ def check(A, vt, shape, seed=0, transpose=False):
 
 
 @pytest.mark.parametrize("vt", ["f64", "f32", "bf16"])
-@pytest.mark.parametrize("shape", [TMA, TMA_CMP])
-def test_staged_rows_of_mixed_length_and_empty_rows(vt, shape):
+@pytest.mark.parametrize("shape", range(NSHAPES))
+def test_rows_of_mixed_length_and_empty_rows(vt, shape):
     rng = np.random.default_rng(1)
     lens = rng.integers(0, 300, size=3000)
     lens[rng.random(3000) < 0.1] = 0
@@ -100,32 +100,33 @@ def test_staged_rows_of_mixed_length_and_empty_rows(vt, shape):
     check(A, vt, shape, seed=4, transpose=True)
 
 
-@pytest.mark.parametrize("shape", [TMA, TMA_CMP])
-def test_staged_many_short_rows(shape):
-    """Every stage is cut by the 256-row limit (rows of one entry)."""
+@pytest.mark.parametrize("shape", range(NSHAPES))
+def test_many_one_entry_rows(shape):
     n = 20000
     A = sp.diags(np.linspace(1.0, 2.0, n)).tocsr() + sp.eye(n, k=7, format="csr")
     check(A.tocsr(), "f32", shape, seed=5)
 
 
-def test_staged_row_that_fills_a_stage():
-    """One row of exactly 2048 entries (a whole FP32 stage) among short rows."""
+@pytest.mark.parametrize("shape", [0, 6, 12, 13])
+def test_one_long_row(shape):
+    """One row of 4099 entries (many 64-entry blocks and a ragged tail) among
+    short rows."""
     lens = np.full(600, 5)
-    lens[300] = 2048
-    A = random_csr(600, 4096, lens, seed=6)
-    check(A, "f32", TMA, seed=7)
+    lens[300] = 4099
+    A = random_csr(600, 8192, lens, seed=6)
+    check(A, "f32", shape, seed=7)
+    check(A, "f64", shape, seed=8, transpose=True)
 
 
-def test_staged_shape_refused_when_a_row_exceeds_a_stage():
+def test_shape_out_of_range_refused():
     lens = np.full(100, 3)
-    lens[50] = 2049  # padded to 2056 > 2048
-    A = random_csr(100, 4096, lens, seed=8)
-    s = lslu.Solver(100, 4096, A.indptr.astype(np.int64), A.indices.astype(np.int32), A.data,
+    A = random_csr(100, 400, lens, seed=8)
+    s = lslu.Solver(100, 400, A.indptr.astype(np.int64), A.indices.astype(np.int32), A.data,
                     "f32", 8)
     try:
-        with pytest.raises(lslu.LsluError, match="stage"):
-            s.set_spmv_shape(TMA, 0)
-        t = s.tune_spmv(reps=1)  # the tuner skips the staged shapes for A
-        assert "tma" not in t["us_A"] and t["shape_A"] not in (TMA, TMA_CMP)
+        with pytest.raises(lslu.LsluError, match=r"\[0, 16\)"):
+            s.set_spmv_shape(NSHAPES, 0)
+        t = s.tune_spmv(reps=1)
+        assert set(t["us_A"]) <= set(lslu.Solver.SHAPES) and 0 <= t["shape_A"] < NSHAPES
     finally:
         s.close()
