@@ -234,9 +234,24 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(P, K, sample_s):
-    """The FP64 oracle as it stands on a bounded sample of the workload: the
-    first k_s iterations of the same solve, k_s chosen to take ~sample_s."""
+def cpu_baseline(P, K, sample_s, oracle_runs=None):
+    """The FP64 oracle as it stands: the full K-iteration GCV solve of the
+    benchmark instance timed in its own process (one thread) when the
+    precision study's oracle runs are available, else the first k_s
+    iterations of the same solve, k_s chosen to take ~sample_s."""
+    nproc = os.cpu_count()
+    if oracle_runs is not None:
+        try:
+            for r in oracle_runs.get():
+                if r["value_type"] == "f64" and r["eta"] == P.eta:
+                    return {"value": r["k_done"] / r["seconds"], "unit": "iter/s", "cores": 1,
+                            "kind": "oracle", "host_cores": nproc,
+                            "sample": f"the full {r['k_done']}-iteration solve of the same "
+                                      f"instance (FP64 numpy/scipy, 1 thread), "
+                                      f"{r['seconds']:.1f} s, while the precision study's "
+                                      f"other oracle solves ran on other cores"}
+        except Exception as e:  # noqa: BLE001 - fall back to the bounded sample
+            print(f"oracle runs failed: {e}", file=sys.stderr)
     import oracle.lslu_oracle as O
 
     A = P.scipy()
@@ -247,69 +262,152 @@ def cpu_baseline(P, K, sample_s):
     t0 = time.perf_counter()
     O.hybrid_lslu(A, P.b, None, ks, "gcv", histories=False)
     dt = time.perf_counter() - t0
-    return {"value": ks / dt, "unit": "iter/s", "cores": 1, "kind": "oracle",
+    return {"value": ks / dt, "unit": "iter/s", "cores": 1, "kind": "oracle", "host_cores": nproc,
             "sample": f"first {ks} of {K} iterations of the same solve (FP64 numpy/scipy, "
                       f"1 thread), {dt:.1f} s"}
 
 
-def precision_study(P, K, rule, dev, x_main, main_vt, order=(None, None)):
-    """Mixed precision against the FP64 GPU path on the same instance: A's
-    values in FP64 / FP32 / BF16 (FP64 or FP32 basis).  For each: throughput
-    of the K-iteration solve (autotuned sparse products), relative error of
-    x_k against x_true at k = 25, 50, ..., K (x_k of a k-iteration solve is
-    the k-th iterate) and its minimum; for the mixed paths, whether the error
-    at K is within 1% of the FP64 path's ('equal_error') and the first k of
-    the curve that reaches it."""
+ORACLE_ETAS = (0.005, 0.02)
+VALUE_TYPES_STUDY = ("f64", "f32", "bf16")
+
+
+def _oracle_job(job):
+    """Worker process: the FP64 oracle's K-iteration GCV solve of a workload
+    instance with A's values rounded to a value type (one thread)."""
+    workload, vt, eta, K = job
+    import oracle.lslu_oracle as O
+
+    P = tomo.make_config(workload, eta=eta)
+    A = P.scipy(tomo.round_values(P.vals, vt))
+    t0 = time.perf_counter()
+    r = O.hybrid_lslu(A, P.b, None, K, "gcv", histories=False)
+    dt = time.perf_counter() - t0
+    return {"value_type": vt, "eta": eta, "K": K, "x": r.x, "gp": r.gp, "tp": r.tp,
+            "k_done": r.k_done, "seconds": dt}
+
+
+def start_oracle_runs(workload, K):
+    """The oracle at the full workload, one spawned process per (value type,
+    noise level) of the precision study; started before the first GPU call and
+    collected at the end (multiprocessing AsyncResult)."""
+    import multiprocessing as mp
+
+    jobs = [(workload, vt, eta, K) for eta in ORACLE_ETAS for vt in VALUE_TYPES_STUDY]
+    pool = mp.get_context("spawn").Pool(processes=len(jobs))
+    return pool, pool.map_async(_oracle_job, jobs), len(jobs)
+
+
+def precision_study(P, K, dev, order=(None, None), oracle=None, n_phantoms=3, k_step=10,
+                    stop_tol=1e-6):
+    """Mixed precision against the FP64 GPU path: A's values in FP64 / FP32 /
+    BF16 (FP64 or FP32 basis), GCV lambda, on n_phantoms seeded phantoms at
+    each noise level of ORACLE_ETAS (instance 0 at the first level is P).
+    For every value type: iterations/s of the K-iteration solve; for every
+    instance the relative error against x_true at the iterate the stopping
+    rule of Eqs. (stop2)/(tol) picks (GCV lambda, tol = stop_tol), at the
+    best iterate of a k_step grid and at K.  For the mixed paths: the mean and
+    worst difference to the FP64 path's error at each of the three points, and
+    on how many instances the error is within 1% of the FP64 path's.  With
+    oracle (the AsyncResult of start_oracle_runs): x_K of instance 0 at each
+    noise level against the FP64 oracle run on the same rounded values."""
     import torch
 
     from paper_2409_05239_gb300 import lslu
 
-    res = {}
-    xs = {}
-    b_dev = torch.from_numpy(P.b).to(dev)
-    x_dev = torch.empty(P.n, dtype=torch.float64, device=dev)
+    c = tomo.CONFIGS[WORKLOAD]
+    insts = []
+    for eta in ORACLE_ETAS:
+        for i in range(n_phantoms):
+            Q = P if (i == 0 and eta == P.eta) else tomo.same_matrix(
+                P, c["seed_base"] + i, eta, c["n_ellipses"])
+            insts.append((eta, c["seed_base"] + i, Q))
     stream = torch.cuda.current_stream(dev)
-    ks = list(range(25, K + 1, 25))
-    nx = np.linalg.norm(P.x_true)
-    for vt in ("f64", "f32", "bf16"):
+    b_dev = [torch.from_numpy(Q.b).to(dev) for _, _, Q in insts]
+    x_dev = torch.empty(P.n, dtype=torch.float64, device=dev)
+    ks = list(range(k_step, K + 1, k_step))
+    res = {}
+    x_K, gp_K = {}, {}
+    for vt in VALUE_TYPES_STUDY:
         s = lslu.Solver(P.m, P.n, P.row_ptr, P.col_idx, P.vals, vt, K, stream=stream.cuda_stream,
                         row_order=order[0], col_order=order[1])
         s.tune_spmv(reps=3)
-        s.solve_device(b_dev, x_dev, K, rule)
+        s.solve_device(b_dev[0], x_dev, K, "gcv")
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         reps = 3
         e0.record(stream)
         for _ in range(reps):
-            s.solve_device(b_dev, x_dev, K, rule)
+            s.solve_device(b_dev[0], x_dev, K, "gcv")
         e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / reps
-        xs[vt] = x_dev.cpu().numpy()
-        curve = []
-        for k in ks:
-            s.solve_device(b_dev, x_dev, k, rule)
-            torch.cuda.synchronize()
-            curve.append(float(np.linalg.norm(x_dev.cpu().numpy() - P.x_true) / nx))
+        errs = np.zeros((len(insts), len(ks)))
+        for j, k in enumerate(ks):  # one captured graph per k, replayed per instance
+            for i, (_, _, Q) in enumerate(insts):
+                s.solve_device(b_dev[i], x_dev, k, "gcv")
+                x = x_dev.cpu().numpy()
+                errs[i, j] = np.linalg.norm(x - Q.x_true) / np.linalg.norm(Q.x_true)
+                if k == K:
+                    x_K[(vt, i)] = x
+        for i, (eta, seed, Q) in enumerate(insts):
+            if seed == c["seed_base"]:  # the instances the oracle solves: pivots too
+                r = s.solve(Q.b, K, "gcv")
+                x_K[(vt, i)] = r["x"]
+                gp_K[(vt, i)] = r["gp"]
+        rows = []
+        for i, (eta, seed, Q) in enumerate(insts):
+            st = s.solve_stopping(Q.b, K, "gcv", 0.0, stop_tol)
+            e_stop = float(np.linalg.norm(st["x"] - Q.x_true) / np.linalg.norm(Q.x_true))
+            jb = int(np.argmin(errs[i]))
+            rows.append({"eta": eta, "phantom_seed": seed, "k_stop": int(st["k_stop"]),
+                         "err_at_stop": e_stop, "k_min": ks[jb], "err_min": float(errs[i, jb]),
+                         "err_at_K": float(errs[i, -1])})
         s.close()
-        res[vt] = {"iter_per_s": K / (ms / 1e3), "ms_per_solve": ms,
-                   "rel_err_x_true": curve[-1], "rel_err_x_true_at_k": dict(zip(ks, curve))}
-    for vt in res:
-        c = res[vt]["rel_err_x_true_at_k"]
-        kb = min(c, key=c.get)
-        res[vt]["min_rel_err"] = {"k": kb, "rel_err_x_true": c[kb]}
-    target = res["f64"]["rel_err_x_true"]
+        res[vt] = {"iter_per_s": K / (ms / 1e3), "ms_per_solve": ms, "instances": rows}
     for vt in ("f32", "bf16"):
-        res[vt]["rel_diff_vs_f64_gpu"] = float(np.linalg.norm(xs[vt] - xs["f64"]) /
-                                               np.linalg.norm(xs["f64"]))
-        # the iterates are semi-convergent, so the comparison is made at the
-        # same iteration K; the first k reaching the FP64 path's error at K is
-        # reported as well
-        res[vt]["equal_error"] = bool(res[vt]["rel_err_x_true"] <= 1.01 * target)
-        hit = [k for k, e in res[vt]["rel_err_x_true_at_k"].items() if e <= 1.01 * target]
-        res[vt]["first_k_within_1pct_of_f64_at_K"] = hit[0] if hit else None
+        cmp = {}
+        for point in ("err_at_stop", "err_min", "err_at_K"):
+            d = np.array([a[point] - b[point] for a, b in
+                          zip(res[vt]["instances"], res["f64"]["instances"])])
+            within = sum(a[point] <= 1.01 * b[point] for a, b in
+                         zip(res[vt]["instances"], res["f64"]["instances"]))
+            cmp[point] = {"mean_diff": float(d.mean()), "worst_diff": float(d.max()),
+                          "within_1pct_of_f64": f"{within}/{len(insts)}"}
+        res[vt]["vs_f64"] = cmp
         res[vt]["speedup_vs_f64"] = res[vt]["iter_per_s"] / res["f64"]["iter_per_s"]
+        res[vt]["rel_diff_x_K_vs_f64_gpu"] = [
+            float(np.linalg.norm(x_K[(vt, i)] - x_K[("f64", i)]) / np.linalg.norm(x_K[("f64", i)]))
+            for i in range(len(insts))]
+    res["setup"] = (f"{len(insts)} instances: phantoms seeds {c['seed_base']}.."
+                    f"{c['seed_base'] + n_phantoms - 1} x noise {list(ORACLE_ETAS)}; GCV lambda; "
+                    f"errors on a {k_step}-iteration grid; stopping rule tol {stop_tol}; "
+                    f"differences are mixed minus FP64 (relative error, absolute)")
+    if oracle is not None:
+        from oracle.perturb import first_difference
+
+        out = []
+        try:
+            oracle_results = oracle.get()
+        except Exception as e:  # noqa: BLE001 - reported, the study stands without it
+            res["vs_oracle"] = f"oracle runs failed: {e}"
+            return res
+        for r in oracle_results:
+            i = next(j for j, (eta, seed, _) in enumerate(insts)
+                     if eta == r["eta"] and seed == c["seed_base"])
+            Q = insts[i][2]
+            xg = x_K[(r["value_type"], i)]
+            out.append({"value_type": r["value_type"], "eta": r["eta"], "K": r["K"],
+                        "first_pivot_difference": first_difference(gp_K[(r["value_type"], i)],
+                                                                   r["gp"]),
+                        "rel_diff_x_K_vs_oracle": float(np.linalg.norm(xg - r["x"]) /
+                                                        np.linalg.norm(r["x"])),
+                        "oracle_rel_err_x_true": float(np.linalg.norm(r["x"] - Q.x_true) /
+                                                       np.linalg.norm(Q.x_true)),
+                        "gpu_rel_err_x_true": float(np.linalg.norm(xg - Q.x_true) /
+                                                    np.linalg.norm(Q.x_true)),
+                        "oracle_seconds": r["seconds"]})
+        res["vs_oracle"] = out
     return res
 
 
@@ -512,6 +610,80 @@ def adjoint_study(dev, K=100, order="tiles"):
             "dJ_dloglam_rel_err_vs_fd": abs(g - fd) / abs(fd)}
 
 
+def persistent_study(dev, batch_count=64, K_batch=150, order="tiles"):
+    """Launch-bound workloads with the basis loop as six kernels per iteration
+    replayed from a CUDA graph against one persistent cooperative launch
+    (lslu_set_loop): the 32x32 workload in FP64 (K = 50, GCV), and the
+    64-problem uneven batch (FP32, K = 150, GCV; renumbered like
+    batched_study)."""
+    import torch
+
+    from paper_2409_05239_gb300 import lslu
+
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    out = {}
+    P = tomo.make_config("ct32")
+    K = tomo.CONFIGS["ct32"]["K"]
+    b = torch.from_numpy(P.b).to(dev)
+    x = torch.empty(P.n, dtype=torch.float64, device=dev)
+    xs = {}
+    for vt in ("f64", "f32"):
+        s = lslu.Solver(P.m, P.n, P.row_ptr, P.col_idx, P.vals, vt, K, stream=stream.cuda_stream)
+        ms_g = timed(lambda: s.solve_device(b, x, K, "gcv"), 200)
+        launches_g = s.last_launch_count()
+        xg = x.cpu().numpy()
+        s.set_loop("persistent")
+        blocks = s.loop_config()["blocks"]
+        ms_p = timed(lambda: s.solve_device(b, x, K, "gcv"), 200)
+        launches_p = s.last_launch_count()
+        xs[vt] = x.cpu().numpy()
+        s.close()
+        out[f"ct32_{vt}"] = {
+            "workload": f"ct32 (m={P.m}, n={P.n}, nnz={P.nnz}), {vt.upper()}, K={K}, GCV",
+            "graph_ms_per_solve": ms_g, "graph_iter_per_s": K / (ms_g / 1e3),
+            "graph_launches_per_solve": launches_g,
+            "persistent_ms_per_solve": ms_p, "persistent_iter_per_s": K / (ms_p / 1e3),
+            "persistent_launches_per_solve": launches_p, "persistent_blocks": blocks,
+            "speedup": ms_g / ms_p,
+            "rel_diff_x_persistent_vs_graph": float(np.linalg.norm(xs[vt] - xg) /
+                                                    np.linalg.norm(xg))}
+    Ps = tomo.make_uneven_batch(batch_count)
+    bb = torch.from_numpy(np.concatenate([Q.b for Q in Ps])).to(dev)
+    xb = torch.empty(sum(Q.n for Q in Ps), dtype=torch.float64, device=dev)
+    kd = torch.empty(batch_count, dtype=torch.int32, device=dev)
+    orders = [tomo.locality_order(Q) for Q in Ps] if order == "tiles" else None
+    bs = lslu.from_problems(Ps, "f32", K_batch, stream=stream.cuda_stream, orders=orders)
+    ms_g = timed(lambda: bs.solve_device(bb, xb, K_batch, "gcv", k_done=kd), 3)
+    xg = xb.cpu().numpy()
+    bs.set_loop("persistent")
+    ms_p = timed(lambda: bs.solve_device(bb, xb, K_batch, "gcv", k_done=kd), 3)
+    iters = int(kd.sum().item())
+    out["batch64_f32"] = {
+        "workload": f"{batch_count} uneven problems, FP32, K={K_batch}, GCV",
+        "numbering": ORDER_NOTE[order],
+        "graph_ms_per_batch_solve": ms_g, "persistent_ms_per_batch_solve": ms_p,
+        "persistent_blocks": bs.loop_config()["blocks"],
+        "graph_problem_iter_per_s": iters / (ms_g / 1e3),
+        "persistent_problem_iter_per_s": iters / (ms_p / 1e3), "speedup": ms_g / ms_p,
+        "rel_diff_x_persistent_vs_graph": float(np.linalg.norm(xb.cpu().numpy() - xg) /
+                                                np.linalg.norm(xg))}
+    bs.close()
+    return out
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -555,13 +727,18 @@ def run_gpu(args):
     from paper_2409_05239_gb300 import build, lslu
 
     rank, world, local = dist_env()
+    cfg = tomo.CONFIGS[args.workload]
+    K = args.K or cfg["K"]
+    # the FP64 oracle at the full workload for the precision study and the CPU
+    # baseline, in spawned processes that run while the GPU is measured
+    oracle_pool = oracle_runs = None
+    if rank == 0 and world == 1 and not args.no_extras and args.workload == WORKLOAD:
+        oracle_pool, oracle_runs, _ = start_oracle_runs(args.workload, K)
     if world > 1:
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     build.build()
-    cfg = tomo.CONFIGS[args.workload]
-    K = args.K or cfg["K"]
     P = tomo.make_problem(cfg["N"], cfg["n_ang"], cfg["p"], cfg["n_ellipses"], cfg["etas"][0],
                           seed=replica_seed(cfg["seed_base"], rank))
     stream = torch.cuda.current_stream(dev)
@@ -684,13 +861,17 @@ def run_gpu(args):
         }
     solver.close()
     if rank == 0 and not args.no_extras and world == 1:
-        out["precision_study"] = precision_study(P, K, rule, dev, x, args.value_type, (ro, co))
+        out["precision_study"] = precision_study(P, K, dev, (ro, co), oracle=oracle_runs)
     if rank == 0 and not args.no_extras and world == 1:
         out["batched_study"] = batched_study(dev, order=args.order)
         out["shared_rhs_study"] = shared_rhs_study(dev, order=args.order)
         out["adjoint_study"] = adjoint_study(dev, order=args.order)
+        out["persistent_study"] = persistent_study(dev, order=args.order)
     if rank == 0 and not args.no_cpu_baseline and world == 1:
-        out["cpu_baseline"] = cpu_baseline(P, K, args.cpu_sample_s)
+        out["cpu_baseline"] = cpu_baseline(P, K, args.cpu_sample_s, oracle_runs)
+    if oracle_pool is not None:
+        oracle_pool.close()
+        oracle_pool.join()
     if rank == 0:
         print(json.dumps(out))
     if world > 1:

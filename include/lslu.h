@@ -397,6 +397,40 @@ lslu_status lslu_spmv_config(lslu_handle h, int32_t* shape_A, int32_t* shape_AT,
 lslu_status lslu_tune_spmv(lslu_handle h, int32_t reps, int32_t* shape_A, int32_t* shape_AT,
                            double* us);
 
+/* How later solves on the handle run the basis loop of Algorithm 4:
+ *   LSLU_LOOP_GRAPH       each step is its own kernel (six per iteration),
+ *                         replayed from a captured CUDA graph (default);
+ *   LSLU_LOOP_PERSISTENT  one cooperative launch runs the pivot of r0 and all
+ *                         K iterations, with grid-wide barriers between the
+ *                         dependent steps (four per iteration).  For
+ *                         workloads whose steps are too short to fill the
+ *                         GPU (small problems, small batches).
+ * The projected solve and x = L y follow as in the graph mode.  A persistent
+ * handle serves lslu_solve, lslu_solve_batched, lslu_solve_stopping and
+ * lslu_solve_optimal with x0 = NULL and searched pivots; x0, replayed or
+ * sampled pivots return LSLU_ERR_INVALID_ARG (set the graph mode for them).
+ * Results equal the graph mode's up to the rounding order of the products
+ * (identical pivots wherever no near-tie separates them).
+ *   blocks          blocks of the launch; 0 = one per SM, or fewer for small
+ *                   problems; at most the co-resident count (lslu_loop_config).
+ *   wait_limit_ns   every barrier wait gives up after this many nanoseconds
+ *                   (0 = one second); the solve then returns LSLU_ERR_TIMEOUT
+ *                   with no completed iteration and the handle stays usable.
+ *   stall_first_barrier  testing only: != 0 makes the first barrier wait on
+ *                   a word nothing writes, so it runs out after wait_limit_ns
+ *                   (which must then be given); use 0 otherwise.
+ * Errors: LSLU_ERR_INVALID_ARG (unknown mode, shared-matrix handles, more than
+ * 1024 problems, blocks or wait_limit_ns out of range), LSLU_ERR_CUDA (no
+ * cooperative launch on the device), LSLU_ERR_OOM.  Drops captured solves. */
+enum { LSLU_LOOP_GRAPH = 0, LSLU_LOOP_PERSISTENT = 1 };
+lslu_status lslu_set_loop(lslu_handle h, int32_t mode, int32_t blocks, int64_t wait_limit_ns,
+                          int32_t stall_first_barrier);
+
+/* The loop configuration (host outputs, any may be NULL): mode, blocks of the
+ * persistent launch (0 in graph mode) and the largest co-resident block count
+ * of that launch on the handle's device (0 where the mode is unavailable). */
+lslu_status lslu_loop_config(lslu_handle h, int32_t* mode, int32_t* blocks, int32_t* max_blocks);
+
 /* One-line description of the last failure on h (h may be NULL for a failed
  * lslu_create on this thread).  The string stays valid until the next call. */
 const char* lslu_error_string(lslu_handle h);

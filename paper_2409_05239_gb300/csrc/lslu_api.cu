@@ -86,7 +86,9 @@ void destroy_ctx(lslu_ctx* c) {
                   c->map_m, c->map_n, c->xin_pad, c->xout_user, c->mvec,
                   c->adj_Vb, c->adj_Zb, c->adj_vec, c->adj_small, c->adj_part,
                   c->fixed_gp, c->fixed_tp, c->xi, c->samples, c->ord_m, c->ord_n,
-                  c->ord_stage, c->rank_m, c->rank_n};
+                  c->ord_stage, c->rank_m, c->rank_n, c->pq_v, c->pq_w, c->pq_row0,
+                  c->pq_col0, c->pq_keys, c->pq_slot_val, c->pq_slot_idx, c->pq_bar,
+                  c->pq_err};
   for (void* p : ptrs) cudaFree(p);
   if (c->st_host) cudaFreeHost(c->st_host);
   for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
@@ -458,6 +460,14 @@ int64_t enqueue_solve(Ctx* c, cudaStream_t s, const double* db, const double* dx
   cudaMemsetAsync(c->tp, 0xff, sizeof(int32_t) * P * (c->kmax + 1), s);
   launches += 1;
 
+  if (c->loop_mode == LSLU_LOOP_PERSISTENT) {
+    // r0 = b (x0 = 0), then the whole basis loop in one cooperative launch
+    launch_residual0(db, nullptr, c->r0, m, s);
+    cudaMemsetAsync(c->pq_bar, 0, 3 * sizeof(unsigned), s);
+    cudaMemsetAsync(c->pq_err, 0, sizeof(int), s);
+    launch_persistent_basis(c, c->r0, K, c->loop_blocks, c->loop_wait_ns, c->loop_stall, s);
+    launches += 2;
+  } else {
   // r0 = b - A x0
   if (dx0) {
     launch_spmv<double, double>(c->A, vt, dx0, c->r0, s, c->num_sms);
@@ -533,6 +543,7 @@ int64_t enqueue_solve(Ctx* c, cudaStream_t s, const double* db, const double* dx
     launch_scale<CT, BT>(u, D + (int64_t)(k + 1) * c->ldd, m, c->st, P, tpm, s, c->num_sms);
     launches += 6;
   }
+  }  // graph-mode basis loop
   // projected problems: every k (histories) or only k = k_done of each problem
   ProjArgs pa;
   std::memset(&pa, 0, sizeof(pa));
@@ -593,7 +604,7 @@ lslu_status solve_impl(Ctx* c, const double* db, const double* dx0, int K, int r
   cudaStream_t s = c->stream;
   int ev_pairs = 0;
   if (c->profile) ensure_events(c, 4 * K + 8);
-  if (!c->use_graphs) {
+  if (!c->use_graphs || (c->loop_mode == LSLU_LOOP_PERSISTENT && c->pq_no_graph)) {
     c->launches = enqueue_solve<BT, CT>(c, s, db, dx0, K, rule, lam, hist, false, fixed, nsamp);
     ev_pairs = c->ev_used / 2;
     CK(cudaGetLastError());
@@ -613,15 +624,21 @@ lslu_status solve_impl(Ctx* c, const double* db, const double* dx0, int K, int r
           enqueue_solve<BT, CT>(c, c->cap_stream, db, dx0, K, rule, lam, hist, true, fixed, nsamp);
       const int pairs = c->ev_used / 2;
       cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
+      cudaGraphExec_t exec = nullptr;
+      if (e == cudaSuccess) {
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+      }
+      if (e != cudaSuccess && c->loop_mode == LSLU_LOOP_PERSISTENT) {
+        // the cooperative launch was not captured: launch this mode directly
+        cudaGetLastError();
+        c->pq_no_graph = true;
+        return solve_impl<BT, CT>(c, db, dx0, K, rule, lam, hist, fixed, nsamp);
+      }
       if (e != cudaSuccess) {
         cudaGetLastError();
         return set_err(c, LSLU_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
       }
-      cudaGraphExec_t exec;
-      e = cudaGraphInstantiate(&exec, graph, 0);
-      cudaGraphDestroy(graph);
-      if (e != cudaSuccess)
-        return set_err(c, LSLU_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
       if (c->graphs.size() >= 8) {
         cudaGraphExecDestroy(c->graphs.front().exec);
         c->graphs.erase(c->graphs.begin());
@@ -698,6 +715,10 @@ lslu_status solve_entry(Ctx* c, const double* b, const double* x0, int32_t K, in
   }
   const bool ord = c->ord_m != nullptr;
   const bool fixed = fix_g != nullptr;
+  if (c->loop_mode == LSLU_LOOP_PERSISTENT && (x0 || fixed || nsamp > 0))
+    return set_err(c, LSLU_ERR_INVALID_ARG,
+                   "the persistent basis loop serves x0 = 0 with searched pivots; "
+                   "lslu_set_loop(h, LSLU_LOOP_GRAPH, ...) for x0, replayed or sampled pivots");
   if (fixed) {  // replayed pivots: validate on the host (indices in range, distinct)
     std::vector<int32_t> g(K), t(K + 1);
     if (host) {
@@ -823,7 +844,9 @@ lslu_status solve_entry(Ctx* c, const double* b, const double* x0, int32_t K, in
     const char* what = ds.status == LSLU_BREAKDOWN_BETA ? "breakdown: r0 = 0"
                        : ds.status == LSLU_BREAKDOWN_W  ? "breakdown in the W step"
                        : ds.status == LSLU_BREAKDOWN_H  ? "breakdown in the H step"
-                                                        : "non-finite pivot";
+                       : ds.status == LSLU_ERR_TIMEOUT
+                           ? "a grid barrier of the persistent basis loop timed out"
+                           : "non-finite pivot";
     return set_err(c, (lslu_status)ds.status, what);
   }
   return LSLU_OK;
@@ -1283,6 +1306,99 @@ extern "C" lslu_status lslu_solve_batched(lslu_handle h, const double* b, int32_
   if (status) CK(cudaMemcpyAsync(status, sv.data(), sv.size() * 4, h2o, s));
   CK(cudaStreamSynchronize(s));
   c->last_k = -1;  // lslu_get_state serves single-problem handles only
+  for (int p = 0; p < P; ++p)
+    if (sv[p] == LSLU_ERR_TIMEOUT)
+      return set_err(c, LSLU_ERR_TIMEOUT, "a grid barrier of the persistent basis loop timed out");
+  return LSLU_OK;
+}
+
+namespace {
+void drop_graphs(Ctx* c);
+}
+
+extern "C" lslu_status lslu_set_loop(lslu_handle h, int32_t mode, int32_t blocks,
+                                     int64_t wait_limit_ns, int32_t stall_first_barrier) {
+  Ctx* c = h;
+  if (!c) return set_err(nullptr, LSLU_ERR_INVALID_ARG, "NULL handle");
+  if (mode == LSLU_LOOP_GRAPH) {
+    CK(cudaStreamSynchronize(c->stream));
+    c->loop_mode = LSLU_LOOP_GRAPH;
+    c->loop_stall = 0;
+    drop_graphs(c);
+    return LSLU_OK;
+  }
+  if (mode != LSLU_LOOP_PERSISTENT) return set_err(c, LSLU_ERR_INVALID_ARG, "unknown loop mode");
+  if (c->shared_rhs)
+    return set_err(c, LSLU_ERR_INVALID_ARG,
+                   "the persistent basis loop does not serve shared-matrix handles");
+  if (c->nprob > kMaxPersistProblems)
+    return set_err(c, LSLU_ERR_INVALID_ARG, "the persistent basis loop serves at most " +
+                                                std::to_string(kMaxPersistProblems) + " problems");
+  if (wait_limit_ns < 0 || wait_limit_ns > 60000000000LL)
+    return set_err(c, LSLU_ERR_INVALID_ARG, "wait_limit_ns must be in [0, 6e10]");
+  if (stall_first_barrier && wait_limit_ns == 0)
+    return set_err(c, LSLU_ERR_INVALID_ARG, "a stalled barrier needs an explicit wait limit");
+  int coop = 0;
+  CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c->device));
+  if (!coop) return set_err(c, LSLU_ERR_CUDA, "the device has no cooperative launch");
+  const int maxb = persistent_max_blocks(c->value_type, c->kmax, c->nprob, c->num_sms);
+  if (maxb < 1)
+    return set_err(c, LSLU_ERR_INVALID_ARG,
+                   "the persistent kernel cannot be resident for this max_iter and problem count");
+  if (blocks < 0 || blocks > maxb)
+    return set_err(c, LSLU_ERR_INVALID_ARG, "blocks must be in [0, " + std::to_string(maxb) +
+                                                "] (0: automatic)");
+  if (blocks == 0) {
+    // one block per SM, or fewer when the rows (two per warp in the products)
+    // do not fill them
+    const int64_t need = (std::max(c->m, c->n) + 15) / 16;
+    blocks = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)maxb, (int64_t)c->num_sms,
+                                                          need}));
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  const size_t bb = basis_bytes(c->value_type);
+  if (!c->pq_v) {
+    CK(cudaMalloc(&c->pq_v, (size_t)c->n * bb));
+    CK(cudaMalloc(&c->pq_w, (size_t)c->m * bb));
+    CK(dmalloc(&c->pq_keys, 2 * (size_t)c->nprob));
+    CK(dmalloc(&c->pq_bar, 4));
+    CK(dmalloc(&c->pq_err, 1));
+    CK(cudaMemset(c->pq_bar, 0, 4 * sizeof(unsigned)));
+    CK(cudaMemset(c->pq_err, 0, sizeof(int)));
+    if (c->nprob > 1) {
+      CK(dmalloc(&c->pq_row0, (size_t)c->nprob));
+      CK(dmalloc(&c->pq_col0, (size_t)c->nprob));
+      CK(cudaMemcpy(c->pq_row0, c->row_base.data(), c->nprob * 8, cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(c->pq_col0, c->col_base.data(), c->nprob * 8, cudaMemcpyHostToDevice));
+    }
+  }
+  if (c->pq_slot_val) {
+    cudaFree(c->pq_slot_val);
+    cudaFree(c->pq_slot_idx);
+    c->pq_slot_val = nullptr;
+    c->pq_slot_idx = nullptr;
+  }
+  CK(dmalloc(&c->pq_slot_val, (size_t)blocks));
+  CK(dmalloc(&c->pq_slot_idx, (size_t)blocks));
+  c->loop_mode = LSLU_LOOP_PERSISTENT;
+  c->loop_blocks = blocks;
+  c->loop_wait_ns = wait_limit_ns ? (unsigned long long)wait_limit_ns : 1000000000ull;
+  c->loop_stall = stall_first_barrier ? 1 : 0;
+  drop_graphs(c);  // captured solves hold the launch sequence of the old mode
+  return LSLU_OK;
+}
+
+extern "C" lslu_status lslu_loop_config(lslu_handle h, int32_t* mode, int32_t* blocks,
+                                        int32_t* max_blocks) {
+  Ctx* c = h;
+  if (!c) return set_err(nullptr, LSLU_ERR_INVALID_ARG, "NULL handle");
+  if (mode) *mode = c->loop_mode;
+  if (blocks) *blocks = c->loop_mode == LSLU_LOOP_PERSISTENT ? c->loop_blocks : 0;
+  if (max_blocks) {
+    *max_blocks = c->shared_rhs ? 0
+                                : persistent_max_blocks(c->value_type, c->kmax, c->nprob,
+                                                        c->num_sms);
+  }
   return LSLU_OK;
 }
 

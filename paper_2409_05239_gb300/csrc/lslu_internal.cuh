@@ -53,6 +53,9 @@ constexpr int kPermBlock = 64;
 
 // Upper bound on max_iter (bounds the projected-problem workspace).
 constexpr int kMaxIter = 2048;
+// Problems one persistent basis loop serves (per-problem tables in shared
+// memory).
+constexpr int kMaxPersistProblems = 1024;
 
 // Rows of one elimination tile.  Problems solved together (a batch) start on
 // multiples of kTile in the concatenated row and column spaces, so every tile
@@ -242,6 +245,23 @@ struct Ctx {
   int32_t* rank_n = nullptr;
   const int32_t* unrank_m = nullptr;
   const int32_t* unrank_n = nullptr;
+
+  // persistent basis loop (lslu_set_loop): one cooperative launch runs the
+  // whole basis generation of a solve, with bounded grid barriers
+  int loop_mode = 0;            // LSLU_LOOP_GRAPH or LSLU_LOOP_PERSISTENT
+  int loop_blocks = 0;          // blocks of the persistent launch
+  unsigned long long loop_wait_ns = 1000000000ull;  // limit of one barrier wait
+  int loop_stall = 0;           // test only: the first barrier waits on a word nothing writes
+  void* pq_v = nullptr;         // n eliminated q (compute type)
+  void* pq_w = nullptr;         // m eliminated u
+  int64_t* pq_row0 = nullptr;   // first m-space row of every problem (batches)
+  int64_t* pq_col0 = nullptr;   // first n-space row of every problem
+  unsigned long long* pq_keys = nullptr;  // 2 nprob pivot keys
+  double* pq_slot_val = nullptr;          // one partial per block (FP64)
+  int32_t* pq_slot_idx = nullptr;
+  unsigned* pq_bar = nullptr;   // barrier counter, generation, stall word
+  bool pq_no_graph = false;     // the persistent launch could not be captured
+  int* pq_err = nullptr;        // 0 or LSLU_ERR_TIMEOUT
 
   int last_k = -1;  // k_done of the last solve, -1 if none
   int last_K = 0;
@@ -449,6 +469,18 @@ cudaError_t launch_optimal_lambda(const ProjWork& w, int K, const DevState* st, 
 // handle (lslu_uq.cu); allocates and frees its own work space.
 lslu_status basis_gram_products(struct Ctx* c, int k, const double* v, double* G, double* g);
 int projected_cluster_size();
+
+// Persistent basis loop (lslu_persistent.cu): the r0 pivot and K iterations
+// of the basis steps of every problem of c in one cooperative launch of
+// `blocks` blocks, from r0 (FP64, m; x0 = 0) into the handle's bases, H, W,
+// pivot lists and state.  Barrier waits give up after wait_ns (stall != 0:
+// the first barrier waits on a word nothing writes, for testing) and the
+// problems then end with LSLU_ERR_TIMEOUT.  persistent_max_blocks sets the
+// kernel up on the current device and returns its co-resident block count
+// (0: the launch cannot be resident); call it before the first launch.
+cudaError_t launch_persistent_basis(Ctx* c, const double* r0, int K, int blocks,
+                                    unsigned long long wait_ns, int stall, cudaStream_t s);
+int persistent_max_blocks(int vt, int K, int nprob, int num_sms);
 
 template <typename BT>
 void launch_recombine(const BT* L, int64_t ldl, const double* y, int64_t ldy, const double* x0,

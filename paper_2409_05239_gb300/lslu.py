@@ -29,7 +29,8 @@ EXPORTS = ("lslu_create", "lslu_solve", "lslu_get_state", "lslu_spmv", "lslu_pro
            "lslu_adjoint", "lslu_solve_fixed_pivots", "lslu_create_shared",
            "lslu_solve_stopping", "lslu_solve_sampled", "lslu_set_spmv_shape",
            "lslu_tune_spmv", "lslu_uq", "lslu_solve_optimal", "lslu_spmv_config",
-           "lslu_create_ordered", "lslu_create_batched_ordered", "lslu_create_shared_ordered")
+           "lslu_create_ordered", "lslu_create_batched_ordered", "lslu_create_shared_ordered",
+           "lslu_set_loop", "lslu_loop_config")
 
 _lib = None
 
@@ -107,6 +108,10 @@ def load(path: str | None = None):
     lib.lslu_solve_stopping.restype = i32
     lib.lslu_adjoint.argtypes = [vp, vp, i32, vp, vp, vp]
     lib.lslu_adjoint.restype = i32
+    lib.lslu_set_loop.argtypes = [vp, i32, i32, i64, i32]
+    lib.lslu_set_loop.restype = i32
+    lib.lslu_loop_config.argtypes = [vp] + [ctypes.POINTER(i32)] * 3
+    lib.lslu_loop_config.restype = i32
     lib.lslu_destroy.argtypes = [vp]
     lib.lslu_destroy.restype = None
     _lib = lib
@@ -123,7 +128,28 @@ def _ptr(a):
     return a.data_ptr()  # torch tensor
 
 
-class Solver:
+LOOPS = {"graph": 0, "persistent": 1}
+
+
+class _LoopControl:
+    """Basis-loop execution of a handle (lslu_set_loop / lslu_loop_config)."""
+
+    def set_loop(self, mode="persistent", blocks=0, wait_limit_ns=0, stall_first_barrier=False):
+        st = self.lib.lslu_set_loop(self.h, LOOPS[mode], int(blocks), int(wait_limit_ns),
+                                    int(bool(stall_first_barrier)))
+        if st != OK:
+            raise LsluError(st, self.lib.lslu_error_string(self.h).decode())
+
+    def loop_config(self):
+        v = [ctypes.c_int32(0) for _ in range(3)]
+        st = self.lib.lslu_loop_config(self.h, *[ctypes.byref(t) for t in v])
+        if st != OK:
+            raise LsluError(st, self.lib.lslu_error_string(self.h).decode())
+        return dict(mode=[k for k, c in LOOPS.items() if c == v[0].value][0],
+                    blocks=v[1].value, max_blocks=v[2].value)
+
+
+class Solver(_LoopControl):
     """One LSLU handle on the current CUDA device.
 
     value_type: 'f64' (FP64 basis and accumulation), 'f32' or 'bf16' (A's
@@ -397,7 +423,10 @@ def projected_noalloc(H, beta, rule, lam, m, y=None, sigma=None, c=None, lam_out
                 or t.numel() < need:
             raise ValueError(f"{name} must be a contiguous float64 tensor on {H.device} "
                              f"with at least {need} entries")
-    st = lib.lslu_projected_noalloc(k, _ptr(H), H.stride(1), float(beta), RULES[rule],
+    # a one-column H has no meaningful column stride: its leading dimension is
+    # its row count
+    ldh = H.stride(1) if k > 1 else H.shape[0]
+    st = lib.lslu_projected_noalloc(k, _ptr(H), ldh, float(beta), RULES[rule],
                                     float(lam), int(m), _ptr(y), _ptr(sigma), _ptr(c),
                                     _ptr(lam_out), _ptr(resid_out), stream)
     if st != OK:
@@ -413,7 +442,7 @@ def stack_orders(orders, k, off):
         for p, o in enumerate(orders)]), dtype=np.int32)
 
 
-class BatchedSolver:
+class BatchedSolver(_LoopControl):
     """One handle over several independent problems solved by one launch
     sequence (lslu_create_batched).  csr_list holds (m, n, row_ptr, col_idx,
     vals) per problem in the problem's own index space; they are stacked into

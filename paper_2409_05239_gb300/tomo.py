@@ -37,6 +37,7 @@ __all__ = [
     "siddon_csr",
     "ellipse_phantom",
     "make_problem",
+    "same_matrix",
     "CONFIGS",
     "round_values",
     "csr_matvec_f64",
@@ -227,6 +228,22 @@ def make_config(name: str, instance: int = 0, eta: float | None = None) -> TomoP
     e = c["etas"][0] if eta is None else eta
     return make_problem(c["N"], c["n_ang"], c["p"], c["n_ellipses"], e,
                         seed=c["seed_base"] + instance)
+
+
+def same_matrix(P: TomoProblem, seed: int, eta: float, n_ellipses: int) -> TomoProblem:
+    """Another seeded instance on P's projector: a phantom of n_ellipses drawn
+    from PCG64(seed) and noise at level eta from PCG64(seed + 1), as
+    make_problem draws them (so same_matrix(P, s, eta, E) equals
+    make_problem(P.N, P.n_ang, P.p, E, eta, s) without rebuilding A)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    x_true = ellipse_phantom(P.N, n_ellipses, rng)
+    b_clean = csr_matvec_f64(P.row_ptr, P.col_idx, P.vals, x_true)
+    nrng = np.random.Generator(np.random.PCG64(seed + 1))
+    z = nrng.standard_normal(b_clean.shape[0])
+    e = eta * np.linalg.norm(b_clean) * z / np.linalg.norm(z)
+    return TomoProblem(N=P.N, n_ang=P.n_ang, p=P.p, m=P.m, n=P.n, row_ptr=P.row_ptr,
+                       col_idx=P.col_idx, vals=P.vals, x_true=x_true, b_clean=b_clean,
+                       b=b_clean + e, eta=eta, seed=seed)
 
 
 def round_values(vals: np.ndarray, value_type: str) -> np.ndarray:

@@ -123,6 +123,11 @@ def test_null_handle_calls_fail_cleanly(lib):
     lib.lslu_destroy(None)
 
 
+def test_loop_control_rejects_bad_arguments_without_gpu(lib):
+    assert lib.lslu_set_loop(None, 1, 0, 0, 0) == lslu.ERR_INVALID_ARG
+    assert lib.lslu_loop_config(None, None, None, None) == lslu.ERR_INVALID_ARG
+
+
 def test_binding_fails_loudly_without_library(tmp_path):
     with pytest.raises(RuntimeError, match="not built"):
         saved = lslu._lib

@@ -125,3 +125,13 @@ def test_locality_order_tiles(N, n_ang, p):
         cells.setdefault(((j // N) // 4, (j % N) // 2), []).append(co[j])
     for v in cells.values():
         assert sorted(v) == list(range(min(v), min(v) + len(v)))
+
+
+def test_same_matrix_equals_make_problem():
+    """Another instance on the same projector draws phantom and noise exactly
+    as make_problem does with that seed and noise level."""
+    P = tomo.make_problem(20, 12, 28, 3, 0.01, seed=9)
+    Q = tomo.same_matrix(P, seed=17, eta=0.02, n_ellipses=4)
+    R = tomo.make_problem(20, 12, 28, 4, 0.02, seed=17)
+    assert np.array_equal(Q.x_true, R.x_true) and np.array_equal(Q.b, R.b)
+    assert Q.row_ptr is P.row_ptr and Q.eta == 0.02 and Q.seed == 17

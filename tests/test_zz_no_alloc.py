@@ -17,6 +17,13 @@ from tests import pins
 pytestmark = pytest.mark.gpu
 
 
+def _colmajor(torch, H, dev):
+    """H as a column-major FP64 device tensor with leading dimension rows."""
+    out = torch.empty_strided(H.shape, (1, H.shape[0]), dtype=torch.float64, device=dev)
+    out.copy_(torch.from_numpy(np.ascontiguousarray(H)))
+    return out
+
+
 def _outputs(torch, k, dev):
     return dict(y=torch.zeros(k, dtype=torch.float64, device=dev),
                 sigma=torch.zeros(k, dtype=torch.float64, device=dev),
@@ -39,7 +46,7 @@ def test_noalloc_matches_projected(rule, lam):
         for k in (37, 60):  # two calls in a row on the shared work space
             H = hp["H"][:k + 1, :k]
             ref = s.projected(H, hp["beta"], rule, lam)
-            Hd = torch.from_numpy(np.asfortranarray(H)).to(dev).t().contiguous().t()
+            Hd = _colmajor(torch, H, dev)
             out = _outputs(torch, k, dev)
             lslu.projected_noalloc(Hd, hp["beta"], rule, lam, P.m, **out)
             torch.cuda.synchronize()
@@ -88,9 +95,8 @@ def test_noalloc_at_the_edges(k, rule, lam):
     P = tomo.make_config("ct32")
     with lslu.from_problem(P, "f64", 256) as s:
         ref_h = s.projected(H, beta, rule, lam, m=m)
-    Hd = torch.from_numpy(np.asfortranarray(H)).to(dev).t().contiguous().t()
-    H40 = O.hessenberg_rect_pivoted(A, b, None, 40)["H"]
-    other = torch.from_numpy(np.asfortranarray(H40)).to(dev).t().contiguous().t()
+    Hd = _colmajor(torch, H, dev)
+    other = _colmajor(torch, O.hessenberg_rect_pivoted(A, b, None, 40)["H"], dev)
     lslu.projected_noalloc(other, 1.0, "gcv", 0.0, 500, **_outputs(torch, 40, dev))
     # effective condition of the regularised projected problem: a backward
     # stable solve gets y to about eps * sigma_1 / max(lambda, sigma_k)
@@ -125,7 +131,7 @@ def test_noalloc_checks_tensor_layouts():
     H = torch.from_numpy(_hessenberg(k, 3)).to(dev)  # row-major
     with pytest.raises(ValueError, match="column-major"):
         lslu.projected_noalloc(H, 1.0, "gcv", 0.0, 100)
-    Hc = H.t().contiguous().t()
+    Hc = _colmajor(torch, _hessenberg(k, 3), dev)
     with pytest.raises(ValueError, match="at least 6"):
         lslu.projected_noalloc(Hc, 1.0, "gcv", 0.0, 100,
                                c=torch.zeros(k, dtype=torch.float64, device=dev))
@@ -136,6 +142,6 @@ def test_noalloc_rejects_k_beyond_limit():
 
     dev = torch.device("cuda", 0)
     k = 257
-    H = torch.zeros((k + 1, k), dtype=torch.float64, device=dev).t().contiguous().t()
+    H = _colmajor(torch, np.zeros((k + 1, k)), dev)
     with pytest.raises(lslu.LsluError, match=r"k must be in \[1, 256\]"):
         lslu.projected_noalloc(H, 1.0, "gcv", 0.0, 1000)
