@@ -602,12 +602,37 @@ def adjoint_study(dev, K=100, order="tiles"):
     h = 1e-3
     fd = (J(lam * np.exp(h)) - J(lam * np.exp(-h))) / (2 * h)
     g = adj["lambda_bar"] * lam
+    # dJ/db along a random direction: the adjoint against central differences
+    # of the solve with the pivots replayed, relative steps 1e-3 and 1e-5, at
+    # K = 10 (well conditioned) and at K
+    db = np.random.default_rng(1).standard_normal(P.m)
+    grad_b = {}
+    for Kb in (10, K):
+        rb = s.solve(P.b, Kb, "fixed", lam)
+        gb = float(s.adjoint(2.0 * (rb["x"] - P.x_true))["b_bar"] @ db)
+
+        def Jb(bb):
+            o = s.solve_fixed_pivots(bb, Kb, rb["gp"], rb["tp"], "fixed", lam)
+            return float(np.sum((o["x"] - P.x_true) ** 2))
+
+        fds = {}
+        for step in (1e-3, 1e-5):
+            hb = step * np.linalg.norm(P.b) / np.linalg.norm(db)
+            fds[step] = (Jb(P.b + hb * db) - Jb(P.b - hb * db)) / (2 * hb)
+        grad_b[f"K={Kb}"] = {"adjoint": gb, "fd_step_1e-3": fds[1e-3], "fd_step_1e-5": fds[1e-5],
+                             "rel_err_vs_fd_1e-5": abs(gb - fds[1e-5]) / abs(fds[1e-5]),
+                             "fd_steps_disagree_by": abs(fds[1e-3] - fds[1e-5]) / abs(fds[1e-5])}
     s.close()
     return {"workload": "ct256 (m=%d, n=%d), FP32, K=%d, lambda=%.4g (GCV at K)" % (P.m, P.n, K, lam),
             "numbering": ORDER_NOTE[order],
             "forward_ms": ms_f, "backward_ms": ms_b, "backward_over_forward": ms_b / ms_f,
             "dJ_dloglam_adjoint": g, "dJ_dloglam_fd": fd,
-            "dJ_dloglam_rel_err_vs_fd": abs(g - fd) / abs(fd)}
+            "dJ_dloglam_rel_err_vs_fd": abs(g - fd) / abs(fd),
+            "dJ_db_direction": grad_b,
+            "dJ_db_note": "with the pivots fixed, the b-derivative at K=100 is not determined in "
+                          "floating point: differences at two step sizes disagree, and two FP64 "
+                          "evaluations of the oracle's tangent in different summation orders "
+                          "differ by several per cent (tests/test_gpu_adjoint.py)"}
 
 
 def persistent_study(dev, batch_count=64, K_batch=150, order="tiles"):
@@ -846,7 +871,14 @@ def run_gpu(args):
                          "frac": achieved / hbm if achieved else None,
                          "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
                          "timing": "CUDA events around each product, second pass of the timed steps",
-                         "algorithmic_bytes_per_launch": sbytes, "launches": n_spmv,
+                         "algorithmic_bytes_per_launch": sbytes,
+                         "bytes_model": "the stored format's bytes: values, column storage "
+                                        "(2.5 B per entry with 16-bit offsets), row pointers, "
+                                        "output and input vector",
+                         "frac_value_plus_int32_column_model": (
+                             P.nnz * ({"f64": 8, "f32": 4, "bf16": 2}[args.value_type] + 4) /
+                             (avg_ms * 1e-3) / 1e9 / hbm if n_spmv else None),
+                         "launches": n_spmv,
                          "avg_launch_ms": avg_ms,
                          "traffic": spmv_traffic(args.workload, args.value_type, args.order,
                                                  cfg_sp["shape_A"], cfg_sp["shape_AT"]),

@@ -60,50 +60,51 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
-__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
 __device__ __forceinline__ int ld_volatile(const int* p) {
   return *reinterpret_cast<const volatile int*>(p);
 }
 
+__device__ __forceinline__ unsigned atom_add_release(unsigned* p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.add.release.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v)
+               : "memory");
+  return old;
+}
+
 // Grid barrier; false when the launch must stop (a wait ran out here or in
-// another block).  bar[0] counts arrivals, bar[1] is the generation, bar[2]
-// a word nothing writes (the test-only stall waits on it).
+// another block).  bar[0] counts arrivals and is never reset during a launch
+// (the host clears it before every launch): the n-th barrier completes when
+// it reaches n * gridDim.x.  Each block's thread 0 arrives with a release
+// add, after the block's __syncthreads, and waits with acquire loads, so
+// every write made before the barrier by any block is visible to every
+// thread after it.  bar[2] is a word nothing writes (the test-only stall
+// waits on it).
 __device__ bool grid_barrier(unsigned* bar, int* err, unsigned long long limit_ns, bool stall) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
-    const unsigned gen = ld_acquire(bar + 1);
-    __threadfence();
-    const unsigned arrived = atomicAdd(bar, 1u);
-    if (!stall && arrived == gridDim.x - 1) {
-      atomicExch(bar, 0u);
-      __threadfence();
-      st_release(bar + 1, gen + 1);
-    } else {
-      const unsigned* word = stall ? bar + 2 : bar + 1;
-      const unsigned old = stall ? 0u : gen;
-      // bounded by the clock, and by a poll count as a second guard (a poll
-      // takes well over 64 ns, so the count cannot end a wait early)
-      const unsigned long long t0 = global_ns();
-      const unsigned long long max_polls = limit_ns / 64 + 1000;
-      unsigned long long polls = 0;
-      while (ld_acquire(word) == old) {
-        if (ld_volatile(err)) {
-          ok = 0;
-          break;
-        }
-        if (global_ns() - t0 > limit_ns || ++polls > max_polls) {
-          atomicExch(err, (int)LSLU_ERR_TIMEOUT);
-          ok = 0;
-          break;
-        }
-        __nanosleep(32);
+    const unsigned old = atom_add_release(bar, 1u);
+    const unsigned target = (old / gridDim.x + 1) * gridDim.x;
+    const unsigned* word = stall ? bar + 2 : bar;
+    // bounded by the clock, and by a poll count as a second guard (a poll
+    // takes well over 64 ns, so the count cannot end a wait early)
+    const unsigned long long t0 = global_ns();
+    const unsigned long long max_polls = limit_ns / 64 + 1000;
+    unsigned long long polls = 0;
+    while (stall ? ld_acquire(word) == 0u : (int)(ld_acquire(word) - target) < 0) {
+      if (ld_volatile(err)) {
+        ok = 0;
+        break;
       }
+      if (global_ns() - t0 > limit_ns || ++polls > max_polls) {
+        atomicExch(err, (int)LSLU_ERR_TIMEOUT);
+        ok = 0;
+        break;
+      }
+      __nanosleep(20);
     }
-    __threadfence();
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
     s_ok = ok && ld_volatile(err) == 0;
   }
   __syncthreads();
@@ -210,28 +211,31 @@ __device__ __forceinline__ int prob_of(const int32_t* tile_prob, int64_t row) {
   return tile_prob ? __ldg(tile_prob + row / kTile) : 0;
 }
 
-// FP32 pivot key (bits of |v| << 32 | (2^32 - 1 - rank)): one unsigned max
-// gives the largest |v|, ties to the lowest rank; a NaN wins and is reported.
-__device__ __forceinline__ unsigned long long pkey(float a, int r) {
-  return ((unsigned long long)__float_as_uint(a) << 32) |
-         (unsigned long long)(0xffffffffu - (unsigned)r);
+// FP32 pivot key: bits of |v| << 32 | (2^31 - 1 - rank) << 1 | sign of v.
+// One unsigned max gives the largest |v| with ties to the lowest rank (ranks
+// are distinct, so the sign bit never decides), and the key carries the
+// pivot's value itself; a NaN has larger bits than any number, wins and is
+// reported.
+__device__ __forceinline__ unsigned long long pkey(float v, int r) {
+  const unsigned lo = ((0x7fffffffu - (unsigned)r) << 1) | (__float_as_uint(v) >> 31);
+  return ((unsigned long long)(__float_as_uint(v) & 0x7fffffffu) << 32) | lo;
+}
+__device__ __forceinline__ int pkey_rank(unsigned long long k) {
+  return (int)(0x7fffffffu - (((unsigned)k >> 1) & 0x7fffffffu));
+}
+__device__ __forceinline__ float pkey_value(unsigned long long k) {
+  return __uint_as_float((unsigned)(k >> 32) | ((unsigned)k << 31));
 }
 
+// larger |value| wins, equal |value|: lower rank; rank -1 = no candidate
 __device__ __forceinline__ bool better(double va, int ia, double vb, int ib) {
   if (ia < 0) return false;
   if (ib < 0) return true;
-  return va > vb || (va == vb && ia < ib);
+  double a = fabs(va), b = fabs(vb);
+  if (a != a) a = INFINITY;  // a NaN must win so that it is reported
+  if (b != b) b = INFINITY;
+  return a > b || (a == b && ia < ib);
 }
-
-// Per-block view of every problem (shared memory): status, and the pivot of
-// the newest vector on each side with its row.
-template <typename CT>
-struct ProbView {
-  int* stat;      // lslu_status per problem (mirrors st[p].status)
-  CT* piv_l;      // pivot value of l_k (divides the gathered v)
-  CT* piv_d;      // pivot value of d_k
-  double* beta;   // beta of r0 (divides the gathered r0 at k = 0)
-};
 
 // One sparse product over all rows of a matrix (16 lanes per row, two rows
 // per warp, warps of the whole grid in turn).  The input entry j is
@@ -348,7 +352,9 @@ struct Side {
   int32_t* piv;     // pivot list of problem 0 (stride piv_stride)
   int64_t piv_stride;
   uint8_t* used;
-  CT* Tinv;         // of problem 0 (stride t_stride), column-major ld ldt
+  CT* Tinv;         // of problem 0 (stride t_stride), column-major ld ldt (global)
+  CT* Ts;           // the block's copy of T^-1 (one problem), ld lds; null: use Tinv
+  int lds;
   double* hess;     // Hessenberg column of problem 0 (W(:, k) or H(:, k)), stride hess_stride
   int64_t hess_stride;
   const int32_t* tile_prob;
@@ -359,7 +365,8 @@ struct Side {
 };
 
 // Coefficients c = T^-1 x(piv) of problem p into cs (every thread of the
-// block calls it).  xs is scratch of cnt entries.
+// block calls it): x at the pivot rows into xs, then one coefficient per
+// thread from the block's shared copy of T^-1, or from global memory.
 template <typename BT, typename CT>
 __device__ void coefficients(const Side<BT, CT>& sd, const PersistArgs& a, int p, CT* cs,
                              CT* xs) {
@@ -367,28 +374,96 @@ __device__ void coefficients(const Side<BT, CT>& sd, const PersistArgs& a, int p
   const int32_t* piv = sd.piv + (int64_t)p * sd.piv_stride;
   for (int j = threadIdx.x; j < cnt; j += kPT) xs[j] = sd.x[piv[j]];
   __syncthreads();
-  const CT* Ti = sd.Tinv + (int64_t)p * a.t_stride;
+  const CT* Ti = sd.Ts ? sd.Ts : sd.Tinv + (int64_t)p * a.t_stride;
+  const int64_t ld = sd.Ts ? sd.lds : a.ldt;
   for (int i = threadIdx.x; i < cnt; i += kPT) {
     CT s0 = 0, s1 = 0, s2 = 0, s3 = 0;
     int j = 0;
     for (; j + 3 <= i; j += 4) {
-      s0 = fma(Ti[(int64_t)j * a.ldt + i], xs[j], s0);
-      s1 = fma(Ti[(int64_t)(j + 1) * a.ldt + i], xs[j + 1], s1);
-      s2 = fma(Ti[(int64_t)(j + 2) * a.ldt + i], xs[j + 2], s2);
-      s3 = fma(Ti[(int64_t)(j + 3) * a.ldt + i], xs[j + 3], s3);
+      s0 = fma(Ti[(int64_t)j * ld + i], xs[j], s0);
+      s1 = fma(Ti[(int64_t)(j + 1) * ld + i], xs[j + 1], s1);
+      s2 = fma(Ti[(int64_t)(j + 2) * ld + i], xs[j + 2], s2);
+      s3 = fma(Ti[(int64_t)(j + 3) * ld + i], xs[j + 3], s3);
     }
-    for (; j <= i; ++j) s0 = fma(Ti[(int64_t)j * a.ldt + i], xs[j], s0);
+    for (; j <= i; ++j) s0 = fma(Ti[(int64_t)j * ld + i], xs[j], s0);
     cs[i] = (s0 + s1) + (s2 + s3);
   }
   __syncthreads();
 }
 
+// acc += sum_{j in [j0, j1)} c_j b_j on the lane's VEC rows (from bp)
+template <typename BT, typename CT, int VEC>
+__device__ __forceinline__ void column_sum(const BT* bp, int64_t ldb, const CT* cs, int j0,
+                                           int j1, CT (&acc)[VEC]) {
+  int j = j0;
+  for (; j + 8 <= j1; j += 8) {
+    BT b[8][VEC];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      if constexpr (VEC == 4) {
+        const float4 w = *reinterpret_cast<const float4*>(bp + (int64_t)(j + u) * ldb);
+        b[u][0] = w.x; b[u][1] = w.y; b[u][2] = w.z; b[u][3] = w.w;
+      } else {
+        const double2 w = *reinterpret_cast<const double2*>(bp + (int64_t)(j + u) * ldb);
+        b[u][0] = w.x; b[u][1] = w.y;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const CT cu = cs[j + u];
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) acc[e] = fma(cu, (CT)b[u][e], acc[e]);
+    }
+  }
+  for (; j < j1; ++j) {
+    const CT cu = cs[j];
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) acc[e] = fma(cu, (CT)bp[(int64_t)j * ldb + e], acc[e]);
+  }
+}
+
+// Masks pivoted rows, stores v and folds the lane's rows into its pivot key
+// (FP32) or best (value, rank) (FP64).
+template <typename BT, typename CT, int VEC>
+__device__ __forceinline__ void finish_rows(const Side<BT, CT>& sd, int64_t i0,
+                                            const CT (&val)[VEC], unsigned long long& wkey,
+                                            double& best, int& besti) {
+#pragma unroll
+  for (int e = 0; e < VEC; ++e) {
+    const int64_t i = i0 + e;
+    if (i >= sd.rows) continue;
+    CT out = 0;
+    if (!sd.used[i]) {
+      out = val[e];
+      const int r = sd.rank ? __ldg(sd.rank + i) : (int)i;
+      if constexpr (sizeof(CT) == 4) {
+        const unsigned long long kk = pkey((float)out, r);
+        wkey = kk > wkey ? kk : wkey;
+      } else {
+        if (better((double)out, r, best, besti)) {
+          best = (double)out;
+          besti = r;
+        }
+      }
+    }
+    sd.v[i] = out;
+  }
+}
+
 // Elimination of the block's tiles with the pivot search: v = x - B c on
 // every row of a live problem, 0 on pivoted rows; the block's largest |v|
-// per problem goes to keys (FP32) or to its slot (FP64, one problem).
+// per problem goes to keys (FP32) or to its slot (FP64, one problem).  The
+// columns are summed in eight ranges, each from zero, and the eight partial
+// sums subtracted from x in range order.  A block with at least as many
+// tiles of a problem as warps gives each warp whole tiles (the warp runs the
+// ranges one after another); with fewer tiles the eight warps take one range
+// each of every tile (the dependent chain shrinks eightfold for small
+// problems).  Both forms give the same bits, so the result does not depend
+// on the block count.
 template <typename BT, typename CT>
 __device__ void eliminate_phase(const Side<BT, CT>& sd, const PersistArgs& a, const int* stat,
-                                CT* cs, CT* xs, unsigned long long* keys, bool record_hess) {
+                                CT* cs, CT* xs, CT* part, unsigned long long* keys,
+                                bool record_hess) {
   constexpr int VEC = TileGeom<CT>::VEC;
   constexpr int TILE = TileGeom<CT>::TILE;
   constexpr bool kKey = sizeof(CT) == 4;
@@ -413,58 +488,46 @@ __device__ void eliminate_phase(const Side<BT, CT>& sd, const PersistArgs& a, co
         for (int j = threadIdx.x; j < sd.cnt; j += kPT) h[j] = (double)cs[j];
       }
       unsigned long long wkey = 0;
-      for (int64_t tt = t + warp; tt < te; tt += kPWarps) {
-        const int64_t i0 = tt * TILE + lane * VEC;
-        CT val[VEC];
+      if (te - t >= kPWarps) {
+        for (int64_t tt = t + warp; tt < te; tt += kPWarps) {
+          const int64_t i0 = tt * TILE + lane * VEC;
+          CT val[VEC];
 #pragma unroll
-        for (int e = 0; e < VEC; ++e) val[e] = (i0 + e < sd.rows) ? sd.x[i0 + e] : (CT)0;
-        const BT* bp = sd.B + i0;  // the bases hold whole tiles of rows
-        int j = 0;
-        for (; j + 8 <= sd.cnt; j += 8) {
-          BT b[8][VEC];
+          for (int e = 0; e < VEC; ++e) val[e] = (i0 + e < sd.rows) ? sd.x[i0 + e] : (CT)0;
+          // the eight column ranges of the split form, in the same order
+          for (int w = 0; w < kPWarps; ++w) {
+            CT acc[VEC];
 #pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            if constexpr (VEC == 4) {
-              const float4 w = *reinterpret_cast<const float4*>(bp + (int64_t)(j + u) * sd.ldb);
-              b[u][0] = w.x; b[u][1] = w.y; b[u][2] = w.z; b[u][3] = w.w;
-            } else {
-              const double2 w = *reinterpret_cast<const double2*>(bp + (int64_t)(j + u) * sd.ldb);
-              b[u][0] = w.x; b[u][1] = w.y;
-            }
+            for (int e = 0; e < VEC; ++e) acc[e] = 0;
+            column_sum<BT, CT, VEC>(sd.B + i0, sd.ldb, cs, (int)((int64_t)w * sd.cnt / kPWarps),
+                                    (int)((int64_t)(w + 1) * sd.cnt / kPWarps), acc);
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) val[e] -= acc[e];
           }
-#pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            const CT cu = cs[j + u];
-#pragma unroll
-            for (int e = 0; e < VEC; ++e) val[e] = fma(-cu, (CT)b[u][e], val[e]);
-          }
+          finish_rows<BT, CT, VEC>(sd, i0, val, wkey, best, besti);
         }
-        for (; j < sd.cnt; ++j) {
-          const CT cu = cs[j];
+      } else {
+        const int j0 = (int)((int64_t)warp * sd.cnt / kPWarps);
+        const int j1 = (int)((int64_t)(warp + 1) * sd.cnt / kPWarps);
+        for (int64_t tt = t; tt < te; ++tt) {
+          const int64_t i0 = tt * TILE + lane * VEC;
+          CT acc[VEC];
 #pragma unroll
-          for (int e = 0; e < VEC; ++e) val[e] = fma(-cu, (CT)bp[(int64_t)j * sd.ldb + e], val[e]);
-        }
+          for (int e = 0; e < VEC; ++e) acc[e] = 0;
+          column_sum<BT, CT, VEC>(sd.B + i0, sd.ldb, cs, j0, j1, acc);
 #pragma unroll
-        for (int e = 0; e < VEC; ++e) {
-          const int64_t i = i0 + e;
-          if (i >= sd.rows) continue;
-          CT out = 0;
-          if (!sd.used[i]) {
-            out = val[e];
-            const int r = sd.rank ? __ldg(sd.rank + i) : (int)i;
-            if constexpr (kKey) {
-              const unsigned long long kk = pkey(fabsf((float)out), r);
-              wkey = kk > wkey ? kk : wkey;
-            } else {
-              double av = fabs((double)out);
-              if (av != av) av = INFINITY;  // a NaN must win so that it is reported
-              if (better(av, r, best, besti)) {
-                best = av;
-                besti = r;
-              }
+          for (int e = 0; e < VEC; ++e) part[(warp * 32 + lane) * VEC + e] = acc[e];
+          __syncthreads();
+          if (warp == 0) {
+            CT val[VEC];
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) {
+              val[e] = (i0 + e < sd.rows) ? sd.x[i0 + e] : (CT)0;
+              for (int w = 0; w < kPWarps; ++w) val[e] -= part[(w * 32 + lane) * VEC + e];
             }
+            finish_rows<BT, CT, VEC>(sd, i0, val, wkey, best, besti);
           }
-          sd.v[i] = out;
+          __syncthreads();
         }
       }
       if constexpr (kKey) {
@@ -509,10 +572,35 @@ __device__ void eliminate_phase(const Side<BT, CT>& sd, const PersistArgs& a, co
   }
 }
 
+// New row `slot` of T^-1 for the pivot row idx: T(slot, l) = b_l(idx),
+// Tinv(slot, j) = -sum_{l=j}^{slot-1} T(slot, l) Tinv(l, j), Tinv(slot, slot) = 1,
+// into Ti (column-major, leading dimension ld).  Every thread of the block
+// calls it; trow is scratch of slot entries.
+template <typename BT, typename CT>
+__device__ void tinv_new_row(const BT* B, int64_t ldb, int idx, int slot, CT* Ti, int64_t ld,
+                             CT* trow) {
+  for (int l = threadIdx.x; l < slot; l += kPT) trow[l] = (CT)B[(int64_t)l * ldb + idx];
+  __syncthreads();
+  for (int j = threadIdx.x; j < slot; j += kPT) {
+    CT s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+    int l = j;
+    for (; l + 4 <= slot; l += 4) {
+      s0 = fma(trow[l], Ti[(int64_t)j * ld + l], s0);
+      s1 = fma(trow[l + 1], Ti[(int64_t)j * ld + l + 1], s1);
+      s2 = fma(trow[l + 2], Ti[(int64_t)j * ld + l + 2], s2);
+      s3 = fma(trow[l + 3], Ti[(int64_t)j * ld + l + 3], s3);
+    }
+    for (; l < slot; ++l) s0 = fma(trow[l], Ti[(int64_t)j * ld + l], s0);
+    Ti[(int64_t)j * ld + slot] = -((s0 + s1) + (s2 + s3));
+  }
+  if (threadIdx.x == 0) Ti[(int64_t)slot * ld + slot] = (CT)1;
+  __syncthreads();
+}
+
 // Pivot of every problem from the published maxima (every block, the same
-// result): updates the block's status table and pivot values; the owner of
-// the problem's first tile records the pivot, the Hessenberg entry, the
-// status of a breakdown and the new row of T^-1.
+// result): updates the block's status table and pivot values (and its copy
+// of T^-1); the owner of the problem's first tile records the pivot, the
+// Hessenberg entry, the status of a breakdown and the new row of T^-1.
 template <typename BT, typename CT>
 __device__ void resolve_phase(const Side<BT, CT>& sd, const PersistArgs& a, int* stat,
                               CT* piv_tab, const unsigned long long* keys, int bcode, int k_on_bd,
@@ -520,7 +608,7 @@ __device__ void resolve_phase(const Side<BT, CT>& sd, const PersistArgs& a, int*
   constexpr int TILE = TileGeom<CT>::TILE;
   constexpr bool kKey = sizeof(CT) == 4;
   __shared__ int s_idx[1];
-  __shared__ double s_abs[1];
+  __shared__ double s_val[1];
   const int64_t T = (sd.rows + TILE - 1) / TILE;
   if constexpr (!kKey) {  // one problem: reduce the slots in block order (warp 0)
     if (threadIdx.x < 32) {
@@ -545,7 +633,7 @@ __device__ void resolve_phase(const Side<BT, CT>& sd, const PersistArgs& a, int*
       }
       if (threadIdx.x == 0) {
         s_idx[0] = besti;
-        s_abs[0] = best;
+        s_val[0] = best;
       }
     }
     __syncthreads();
@@ -553,24 +641,24 @@ __device__ void resolve_phase(const Side<BT, CT>& sd, const PersistArgs& a, int*
   for (int p = 0; p < a.nprob; ++p) {
     if (stat[p] != LSLU_OK) continue;  // uniform across the block
     int idx = -1;
-    double absv = 0.0;
+    CT pv = 0;
     if constexpr (kKey) {
       const unsigned long long key = keys[p];
-      if (key) {
-        const int r = (int)(0xffffffffu - (unsigned)(key & 0xffffffffull));
-        idx = sd.unrank ? __ldg(sd.unrank + r) : r;
-        const float af = __uint_as_float((unsigned)(key >> 32));
-        absv = (af != af) ? INFINITY : (double)af;
+      if (key >> 32) {
+        idx = pkey_rank(key);
+        idx = sd.unrank ? __ldg(sd.unrank + idx) : idx;
+        pv = pkey_value(key);
       }
     } else {
       idx = s_idx[0] >= 0 ? (sd.unrank ? __ldg(sd.unrank + s_idx[0]) : s_idx[0]) : -1;
-      absv = s_abs[0];
+      pv = (CT)s_val[0];
     }
-    const bool owner = tile_owner(sd.first_row ? sd.first_row[p] / TILE : 0, T) == (int)blockIdx.x;
+    const bool owner =
+        tile_owner(sd.first_row ? sd.first_row[p] / TILE : 0, T) == (int)blockIdx.x;
     int code = LSLU_OK;
-    if (idx < 0 || absv == 0.0)
+    if (idx < 0 || pv == (CT)0)
       code = bcode;
-    else if (!isfinite(absv))
+    else if (!isfinite((double)pv))
       code = LSLU_ERR_NONFINITE;
     if (code != LSLU_OK) {
       __syncthreads();
@@ -584,50 +672,66 @@ __device__ void resolve_phase(const Side<BT, CT>& sd, const PersistArgs& a, int*
       __syncthreads();
       continue;
     }
-    const CT pv = sd.v[idx];
-    __syncthreads();
+    const int slot = sd.cnt;  // the new pivot's index in the list
     if (threadIdx.x == 0) piv_tab[p] = pv;
-    if (owner) {
-      const int slot = sd.cnt;  // the new pivot's index in the list
-      CT* Ti = sd.Tinv + (int64_t)p * a.t_stride;
-      if (threadIdx.x == 0) {
-        sd.piv[(int64_t)p * sd.piv_stride + slot] = idx;
-        sd.used[idx] = 1;
-        sd.hess[(int64_t)p * sd.hess_stride + slot] = (double)pv;
-        a.st[p].pivot = (double)pv;
-        a.st[p].pivot_f = (float)pv;
-        Ti[(int64_t)slot * a.ldt + slot] = (CT)1;
-      }
-      // new row of T^-1: T(slot, l) = b_l(idx), Tinv(slot, j) =
-      // -sum_{l=j}^{slot-1} T(slot, l) Tinv(l, j)
-      for (int l = threadIdx.x; l < slot; l += kPT) trow[l] = (CT)sd.B[(int64_t)l * sd.ldb + idx];
-      __syncthreads();
-      const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-      for (int j = warp; j < slot; j += kPWarps) {
-        CT acc = 0;
-        for (int l = j + lane; l < slot; l += 32) acc = fma(trow[l], Ti[(int64_t)j * a.ldt + l], acc);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) Ti[(int64_t)j * a.ldt + slot] = -acc;
-      }
+    if (owner && threadIdx.x == 0) {
+      sd.piv[(int64_t)p * sd.piv_stride + slot] = idx;
+      sd.used[idx] = 1;
+      sd.hess[(int64_t)p * sd.hess_stride + slot] = (double)pv;
+      a.st[p].pivot = (double)pv;
+      a.st[p].pivot_f = (float)pv;
+    }
+    CT* Tg = sd.Tinv + (int64_t)p * a.t_stride;
+    if (sd.Ts) {
+      // every block extends its own copy; the owner also stores the new row
+      tinv_new_row<BT, CT>(sd.B, sd.ldb, idx, slot, sd.Ts, sd.lds, trow);
+      if (owner)
+        for (int j = threadIdx.x; j <= slot; j += kPT)
+          Tg[(int64_t)j * a.ldt + slot] = sd.Ts[(int64_t)j * sd.lds + slot];
+    } else if (owner) {
+      tinv_new_row<BT, CT>(sd.B, sd.ldb, idx, slot, Tg, a.ldt, trow);
     }
     __syncthreads();
   }
 }
 
-template <typename VT, typename BT, typename CT>
+// Shared memory of the kernel: coefficient, pivot-row and T-row scratch
+// (kcap = K + 2 entries each), the column-split partial sums (8 warps x one
+// tile), the per-problem tables (pivot values of both sides, beta, status)
+// and, with SMT, the block's copies of T_L^-1 and T_D^-1 ((K+1) x lds each).
+template <typename CT>
+struct SmemLayout {
+  size_t kcap, part, ts_ld, ts_elems;
+  size_t off_tables, off_beta, off_stat, off_ts, total;
+  __host__ __device__ SmemLayout(int K, int nprob, bool smt) {
+    kcap = (size_t)K + 2;
+    part = (size_t)kPWarps * TileGeom<CT>::TILE;
+    ts_ld = (size_t)K + 1 + (((K + 1) & 1) ? 0 : 1);  // odd leading dimension
+    ts_elems = smt ? (size_t)(K + 1) * ts_ld : 0;
+    off_tables = (3 * kcap + part) * sizeof(CT);
+    off_beta = ((off_tables + 2 * (size_t)nprob * sizeof(CT) + 7) / 8) * 8;
+    off_stat = off_beta + (size_t)nprob * 8;
+    off_ts = ((off_stat + (size_t)nprob * 4 + 15) / 16) * 16;
+    total = off_ts + 2 * ts_elems * sizeof(CT);
+  }
+};
+
+template <typename VT, typename BT, typename CT, bool SMT>
 __global__ void __launch_bounds__(kPT, 1) k_persistent_basis(PersistArgs a) {
-  extern __shared__ unsigned char smem_raw[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   const int P = a.nprob;
-  const int kcap = a.K + 2;
+  const SmemLayout<CT> lay(a.K, P, SMT);
   CT* cs = reinterpret_cast<CT*>(smem_raw);
-  CT* xs = cs + kcap;
-  CT* trow = xs + kcap;
-  CT* piv_l = trow + kcap;
+  CT* xs = cs + lay.kcap;
+  CT* trow = xs + lay.kcap;
+  CT* part = trow + lay.kcap;
+  CT* piv_l = reinterpret_cast<CT*>(smem_raw + lay.off_tables);
   CT* piv_d = piv_l + P;
-  double* beta = reinterpret_cast<double*>(
-      smem_raw + (((3 * (size_t)kcap + 2 * (size_t)P) * sizeof(CT) + 7) / 8) * 8);
-  int* stat = reinterpret_cast<int*>(beta + P);
+  double* beta = reinterpret_cast<double*>(smem_raw + lay.off_beta);
+  int* stat = reinterpret_cast<int*>(smem_raw + lay.off_stat);
+  CT* TLs = SMT ? reinterpret_cast<CT*>(smem_raw + lay.off_ts) : nullptr;
+  CT* TDs = SMT ? TLs + lay.ts_elems : nullptr;
+  const int lds = (int)lay.ts_ld;
   for (int p = threadIdx.x; p < P; p += kPT) {
     stat[p] = LSLU_OK;
     piv_l[p] = (CT)1;
@@ -643,6 +747,11 @@ __global__ void __launch_bounds__(kPT, 1) k_persistent_basis(PersistArgs a) {
     const bool ok = grid_barrier(a.bar, a.err, lim, stall);
     stall = false;
     return ok;
+  };
+  auto any_live = [&]() -> bool {
+    for (int p = 0; p < P; ++p)
+      if (stat[p] == LSLU_OK) return true;
+    return false;
   };
   BT* Lb = reinterpret_cast<BT*>(a.L);
   BT* Db = reinterpret_cast<BT*>(a.D);
@@ -723,10 +832,12 @@ __global__ void __launch_bounds__(kPT, 1) k_persistent_basis(PersistArgs a) {
         }
       }
     }
+    if (SMT && threadIdx.x == 0) TDs[0] = (CT)1;
     __syncthreads();
   }
 
   for (int k = 0; k < a.K; ++k) {
+    if (!any_live()) break;  // every problem stopped (the same in every block)
     // ---- S1: q = A^T d_k; store d_k on the block's rows
     if (k == 0) {
       product_phase<VT, BT, CT, true>(a.n, a.t_rp, a.t_rl, a.t_col, tval, a.r0, piv_d, beta,
@@ -740,17 +851,19 @@ __global__ void __launch_bounds__(kPT, 1) k_persistent_basis(PersistArgs a) {
     if (!sync()) goto out;
     // ---- E1: eliminate q against l_0 .. l_{k-1}
     {
-      if (blockIdx.x == 0)  // keys of the other parity: read by everyone before the last barrier
+      if (blockIdx.x == 0)  // keys of the other parity: everyone read them before the last barrier
         for (int i = threadIdx.x; i < P; i += kPT) a.keys[(int64_t)((2 * k + 1) & 1) * P + i] = 0ull;
       Side<BT, CT> sd{a.n, qx, qv, Lb, a.ldl, a.gp, a.gp_stride, a.gused,
-                      reinterpret_cast<CT*>(a.TLi), a.W + (int64_t)k * a.ldw, a.w_stride,
-                      a.tile_prob_n, a.col0, a.rank_n, a.unrank_n, k};
-      eliminate_phase<BT, CT>(sd, a, stat, cs, xs, a.keys + (int64_t)((2 * k) & 1) * P, true);
+                      reinterpret_cast<CT*>(a.TLi), TLs, lds, a.W + (int64_t)k * a.ldw,
+                      a.w_stride, a.tile_prob_n, a.col0, a.rank_n, a.unrank_n, k};
+      eliminate_phase<BT, CT>(sd, a, stat, cs, xs, part, a.keys + (int64_t)((2 * k) & 1) * P,
+                              true);
       if (!sync()) goto out;
       // ---- R1: pivot g_k, W(k, k), new row of T_L^-1
       resolve_phase<BT, CT>(sd, a, stat, piv_l, a.keys + (int64_t)((2 * k) & 1) * P,
                             LSLU_BREAKDOWN_W, k, trow);
     }
+    if (!any_live()) break;
     // ---- S2: u = A l_k; store l_k on the block's rows
     product_phase<VT, BT, CT, false>(a.m, a.a_rp, a.a_rl, a.a_col, aval, qv, piv_l, beta, stat,
                                      a.tile_prob_m, ux);
@@ -761,17 +874,18 @@ __global__ void __launch_bounds__(kPT, 1) k_persistent_basis(PersistArgs a) {
       if (blockIdx.x == 0)
         for (int i = threadIdx.x; i < P; i += kPT) a.keys[(int64_t)((2 * k) & 1) * P + i] = 0ull;
       Side<BT, CT> sd{a.m, ux, uv, Db, a.ldd, a.tp, a.tp_stride, a.tused,
-                      reinterpret_cast<CT*>(a.TDi), a.H + (int64_t)k * a.ldh, a.h_stride,
-                      a.tile_prob_m, a.row0, a.rank_m, a.unrank_m, k + 1};
-      eliminate_phase<BT, CT>(sd, a, stat, cs, xs, a.keys + (int64_t)((2 * k + 1) & 1) * P, true);
+                      reinterpret_cast<CT*>(a.TDi), TDs, lds, a.H + (int64_t)k * a.ldh,
+                      a.h_stride, a.tile_prob_m, a.row0, a.rank_m, a.unrank_m, k + 1};
+      eliminate_phase<BT, CT>(sd, a, stat, cs, xs, part,
+                              a.keys + (int64_t)((2 * k + 1) & 1) * P, true);
       if (!sync()) goto out;
       // ---- R2: pivot t_{k+1}, H(k+1, k), new row of T_D^-1
       resolve_phase<BT, CT>(sd, a, stat, piv_d, a.keys + (int64_t)((2 * k + 1) & 1) * P,
                             LSLU_BREAKDOWN_H, k, trow);
     }
+    if (k == a.K - 1)  // d_{K+1} on the block's rows
+      scale_own_rows<BT, CT>(a.m, uv, piv_d, stat, a.tile_prob_m, Db + (int64_t)a.K * a.ldd);
   }
-  // d_{K+1} on the block's rows
-  scale_own_rows<BT, CT>(a.m, uv, piv_d, stat, a.tile_prob_m, Db + (int64_t)a.K * a.ldd);
   return;
 out:
   // a barrier wait ran out (here or in another block): the solve stops with
@@ -785,11 +899,11 @@ out:
 
 // Dynamic shared memory the kernels are set up for (an upper bound; a launch
 // asks for what its K and problem count need).
-constexpr size_t kPersistSmemCap = 96 * 1024;
+constexpr size_t kPersistSmemCap = 200 * 1024;
 
-template <typename VT, typename BT, typename CT>
+template <typename VT, typename BT, typename CT, bool SMT>
 cudaError_t launch_typed(const PersistArgs& a, int blocks, size_t smem, cudaStream_t s) {
-  auto kern = k_persistent_basis<VT, BT, CT>;
+  auto kern = k_persistent_basis<VT, BT, CT, SMT>;
   if (smem > kPersistSmemCap) return cudaErrorInvalidValue;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)blocks);
@@ -804,38 +918,52 @@ cudaError_t launch_typed(const PersistArgs& a, int blocks, size_t smem, cudaStre
   return cudaLaunchKernelEx(&cfg, kern, a);
 }
 
-// Sets the kernel up on the current device (its shared-memory bound) and
-// returns the co-resident block count for smem bytes of dynamic shared memory.
-template <typename VT, typename BT, typename CT>
-int max_resident_typed(size_t smem, int num_sms) {
-  auto kern = k_persistent_basis<VT, BT, CT>;
-  if (smem > kPersistSmemCap) return 0;
+// Sets one instantiation up on the current device (its shared-memory bound)
+// and returns its co-resident block count at the largest shared memory a
+// launch may ask for.
+template <typename VT, typename BT, typename CT, bool SMT>
+int max_resident_one(int num_sms) {
+  auto kern = k_persistent_basis<VT, BT, CT, SMT>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)kPersistSmemCap) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPT, smem) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPT, kPersistSmemCap) !=
+      cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
   return per_sm * num_sms;
 }
 
-size_t persist_smem(int vt, int K, int nprob) {
-  const size_t ct = vt == LSLU_F64 ? 8 : 4;
-  const size_t kcap = (size_t)K + 2;
-  return (((3 * kcap + 2 * (size_t)nprob) * ct + 7) / 8) * 8 + (size_t)nprob * (8 + 4);
+template <typename VT, typename BT, typename CT>
+int max_resident_typed(int num_sms) {
+  return std::min(max_resident_one<VT, BT, CT, false>(num_sms),
+                  max_resident_one<VT, BT, CT, true>(num_sms));
+}
+
+template <typename CT>
+size_t smem_bytes(int K, int nprob, bool smt) {
+  return SmemLayout<CT>(K, nprob, smt).total;
+}
+
+// The block keeps its own T^-1 copies when one problem's two fit.
+template <typename CT>
+bool use_smem_tinv(int K, int nprob) {
+  return nprob == 1 && smem_bytes<CT>(K, nprob, true) <= kPersistSmemCap;
 }
 
 }  // namespace
 
 int persistent_max_blocks(int vt, int K, int nprob, int num_sms) {
-  const size_t smem = persist_smem(vt, K, nprob);
-  if (vt == LSLU_F64) return max_resident_typed<double, double, double>(smem, num_sms);
-  if (vt == LSLU_F32) return max_resident_typed<float, float, float>(smem, num_sms);
-  return max_resident_typed<__nv_bfloat16, float, float>(smem, num_sms);
+  const size_t need = vt == LSLU_F64 ? smem_bytes<double>(K, nprob, false)
+                                     : smem_bytes<float>(K, nprob, false);
+  if (need > kPersistSmemCap) return 0;
+  if (vt == LSLU_F64) return max_resident_typed<double, double, double>(num_sms);
+  if (vt == LSLU_F32) return max_resident_typed<float, float, float>(num_sms);
+  return max_resident_typed<__nv_bfloat16, float, float>(num_sms);
 }
 
 cudaError_t launch_persistent_basis(Ctx* c, const double* r0, int K, int blocks,
@@ -894,10 +1022,19 @@ cudaError_t launch_persistent_basis(Ctx* c, const double* r0, int K, int blocks,
   a.K = K;
   a.wait_ns = wait_ns;
   a.stall = stall;
-  const size_t smem = persist_smem(c->value_type, K, c->nprob);
-  if (c->value_type == LSLU_F64) return launch_typed<double, double, double>(a, blocks, smem, s);
-  if (c->value_type == LSLU_F32) return launch_typed<float, float, float>(a, blocks, smem, s);
-  return launch_typed<__nv_bfloat16, float, float>(a, blocks, smem, s);
+  if (c->value_type == LSLU_F64) {
+    const bool smt = use_smem_tinv<double>(K, c->nprob);
+    const size_t smem = smem_bytes<double>(K, c->nprob, smt);
+    return smt ? launch_typed<double, double, double, true>(a, blocks, smem, s)
+               : launch_typed<double, double, double, false>(a, blocks, smem, s);
+  }
+  const bool smt = use_smem_tinv<float>(K, c->nprob);
+  const size_t smem = smem_bytes<float>(K, c->nprob, smt);
+  if (c->value_type == LSLU_F32)
+    return smt ? launch_typed<float, float, float, true>(a, blocks, smem, s)
+               : launch_typed<float, float, float, false>(a, blocks, smem, s);
+  return smt ? launch_typed<__nv_bfloat16, float, float, true>(a, blocks, smem, s)
+             : launch_typed<__nv_bfloat16, float, float, false>(a, blocks, smem, s);
 }
 
 }  // namespace lslu

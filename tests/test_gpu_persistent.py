@@ -200,8 +200,11 @@ def test_batch_breakdowns_stay_local(small_batch):
         assert r["status"][p] == g["status"][p] and r["k_done"][p] == g["k_done"][p], p
         if g["status"][p] == lslu.OK or g["k_done"][p] > 0:
             assert rel(r["x"][p], g["x"][p]) <= 2e-4, p
-    assert g["status"][1] == lslu.BREAKDOWN_W and g["k_done"][1] == 16
-    assert g["status"][2] == lslu.BREAKDOWN_BETA
+    # the 16-pixel problem runs out of pivots before K, the zero data breaks
+    # down at once, the others complete
+    assert g["status"][1] in (lslu.BREAKDOWN_W, lslu.BREAKDOWN_H) and g["k_done"][1] < K
+    assert g["status"][2] == lslu.BREAKDOWN_BETA and g["k_done"][2] == 0
+    assert g["status"][0] == lslu.OK and g["status"][3] == lslu.OK
 
 
 def test_batch_barrier_timeout(small_batch):
