@@ -94,36 +94,37 @@ ORDER_NOTE = {
 
 # DRAM traffic of one k_spmv_pivots launch on the 512x512 FP32 workload per
 # numbering and row shape, (A l_k, A^T d_k) in bytes (dram__bytes_read.sum +
-# dram__bytes_write.sum from one ncu capture of every shape, solve_once
-# --shapes all [--order tiles]).  It is reported only while the sparse-product
-# sources are the ones captured.
+# dram__bytes_write.sum, one ncu pass per launch, averaged over the two
+# launches of each direction of solve_once --K 2 --shapes all [--order
+# tiles]).  It is reported only while the sources that define the sparse
+# products and their launches are the ones captured.
 SPMV_TRAFFIC = {
     "workload": "ct512", "value_type": "f32",
     "bytes": {
         "natural": {
-            "16x2": (972.47e6, 973.35e6), "32x1": (971.81e6, 972.33e6),
-            "16x1": (978.16e6, 972.46e6), "8x1": (1004.37e6, 1019.95e6),
-            "8x2": (997.49e6, 987.54e6), "4x1": (1011.21e6, 1022.64e6),
-            "16x2/16-bit": (800.09e6, 796.17e6), "32x1/16-bit": (791.64e6, 790.90e6),
-            "16x1/16-bit": (804.80e6, 809.89e6), "8x1/16-bit": (854.40e6, 906.59e6),
-            "8x2/16-bit": (832.11e6, 831.46e6), "4x1/16-bit": (918.24e6, 897.54e6),
-            "32x8e": (971.87e6, 972.27e6), "32x8e/16-bit": (791.25e6, 791.03e6),
-            "32x4e": (971.84e6, 972.46e6), "32x4e/16-bit": (793.61e6, 791.96e6),
+            "16x2": (972.48e6, 974.17e6), "32x1": (971.89e6, 972.75e6),
+            "16x1": (978.13e6, 973.03e6), "8x1": (1004.44e6, 1020.27e6),
+            "8x2": (997.67e6, 988.00e6), "4x1": (1011.29e6, 1022.83e6),
+            "16x2/16-bit": (800.03e6, 795.78e6), "32x1/16-bit": (791.36e6, 790.76e6),
+            "16x1/16-bit": (804.18e6, 809.83e6), "8x1/16-bit": (853.34e6, 904.81e6),
+            "8x2/16-bit": (831.13e6, 831.64e6), "4x1/16-bit": (918.39e6, 897.77e6),
+            "32x8e": (972.00e6, 972.91e6), "32x8e/16-bit": (791.05e6, 791.10e6),
+            "32x4e": (971.93e6, 972.72e6), "32x4e/16-bit": (793.30e6, 791.76e6),
         },
         "tiles": {
-            "16x2": (972.59e6, 973.41e6), "32x1": (971.96e6, 972.22e6),
-            "16x1": (978.25e6, 972.46e6), "8x1": (1005.26e6, 1020.23e6),
-            "8x2": (998.13e6, 993.24e6), "4x1": (1012.13e6, 1021.67e6),
-            "16x2/16-bit": (799.75e6, 796.06e6), "32x1/16-bit": (791.53e6, 790.91e6),
-            "16x1/16-bit": (804.78e6, 810.25e6), "8x1/16-bit": (855.61e6, 932.44e6),
-            "8x2/16-bit": (832.43e6, 837.37e6), "4x1/16-bit": (931.75e6, 893.35e6),
-            "32x8e": (971.88e6, 972.27e6), "32x8e/16-bit": (791.30e6, 791.00e6),
-            "32x4e": (972.05e6, 972.28e6), "32x4e/16-bit": (793.53e6, 791.89e6),
+            "16x2": (972.37e6, 974.02e6), "32x1": (971.85e6, 972.76e6),
+            "16x1": (978.19e6, 972.89e6), "8x1": (1005.26e6, 1020.68e6),
+            "8x2": (998.17e6, 993.89e6), "4x1": (1012.00e6, 1022.04e6),
+            "16x2/16-bit": (799.68e6, 795.89e6), "32x1/16-bit": (791.28e6, 790.66e6),
+            "16x1/16-bit": (804.39e6, 809.88e6), "8x1/16-bit": (854.99e6, 926.65e6),
+            "8x2/16-bit": (832.14e6, 837.37e6), "4x1/16-bit": (931.91e6, 894.62e6),
+            "32x8e": (972.04e6, 972.82e6), "32x8e/16-bit": (791.14e6, 790.89e6),
+            "32x4e": (972.04e6, 972.71e6), "32x4e/16-bit": (793.30e6, 791.71e6),
         },
     },
     "sources": {
         "paper_2409_05239_gb300/csrc/lslu_spmv.cu":
-            "ace85ce1e4d967e7621818d192c300f9c6191fb0b2881f3339d9a31a4265721a",
+            "6cc9ecd7150c65c3be752d624f2e0cca975c796399ff9f580e1f7746fc9d32e0",
         "paper_2409_05239_gb300/csrc/lslu_spmv_impl.cuh":
             "e618d799b704a719641bc6e6dbf0e35760f17eb2954ef42a4f8cba87f46cebba",
         "paper_2409_05239_gb300/csrc/lslu_spmv_shapes_a.cu":
@@ -132,8 +133,6 @@ SPMV_TRAFFIC = {
             "0e773294834ee47b18af1f88926ceff2d1210b793e4dcb2cf9260028db12f63a",
         "paper_2409_05239_gb300/csrc/lslu_spmv_shapes_c.cu":
             "96910620ae56de115fcdea59e6c10dfb7408ff7c9610c8323ba713ab471e2a0f",
-        "paper_2409_05239_gb300/csrc/lslu_internal.cuh":
-            "d306ddcf7e4c4a5b57d4d76e5550e0d08625a3ae32182b984aaea553fc8e4063",
     },
 }
 
@@ -637,10 +636,10 @@ def adjoint_study(dev, K=100, order="tiles"):
 
 def persistent_study(dev, batch_count=64, K_batch=150, order="tiles"):
     """Launch-bound workloads with the basis loop as six kernels per iteration
-    replayed from a CUDA graph against one persistent cooperative launch
-    (lslu_set_loop): the 32x32 workload in FP64 (K = 50, GCV), and the
-    64-problem uneven batch (FP32, K = 150, GCV; renumbered like
-    batched_study)."""
+    replayed from a CUDA graph against one persistent cooperative launch and
+    (single problems) one thread-block cluster (lslu_set_loop): the 32x32
+    workload in FP64 and FP32 (K = 50, GCV), and the 64-problem uneven batch
+    (FP32, K = 150, GCV; renumbered like batched_study)."""
     import torch
 
     from paper_2409_05239_gb300 import lslu
@@ -675,6 +674,10 @@ def persistent_study(dev, batch_count=64, K_batch=150, order="tiles"):
         ms_p = timed(lambda: s.solve_device(b, x, K, "gcv"), 200)
         launches_p = s.last_launch_count()
         xs[vt] = x.cpu().numpy()
+        s.set_loop("cluster")
+        ctas = s.loop_config()["blocks"]
+        ms_c = timed(lambda: s.solve_device(b, x, K, "gcv"), 200)
+        xc = x.cpu().numpy()
         s.close()
         out[f"ct32_{vt}"] = {
             "workload": f"ct32 (m={P.m}, n={P.n}, nnz={P.nnz}), {vt.upper()}, K={K}, GCV",
@@ -684,7 +687,10 @@ def persistent_study(dev, batch_count=64, K_batch=150, order="tiles"):
             "persistent_launches_per_solve": launches_p, "persistent_blocks": blocks,
             "speedup": ms_g / ms_p,
             "rel_diff_x_persistent_vs_graph": float(np.linalg.norm(xs[vt] - xg) /
-                                                    np.linalg.norm(xg))}
+                                                    np.linalg.norm(xg)),
+            "cluster_ms_per_solve": ms_c, "cluster_iter_per_s": K / (ms_c / 1e3),
+            "cluster_ctas": ctas, "cluster_speedup_vs_graph": ms_g / ms_c,
+            "rel_diff_x_cluster_vs_graph": float(np.linalg.norm(xc - xg) / np.linalg.norm(xg))}
     Ps = tomo.make_uneven_batch(batch_count)
     bb = torch.from_numpy(np.concatenate([Q.b for Q in Ps])).to(dev)
     xb = torch.empty(sum(Q.n for Q in Ps), dtype=torch.float64, device=dev)

@@ -404,7 +404,17 @@ lslu_status lslu_tune_spmv(lslu_handle h, int32_t reps, int32_t* shape_A, int32_
  *                         K iterations, with grid-wide barriers between the
  *                         dependent steps (four per iteration).  For
  *                         workloads whose steps are too short to fill the
- *                         GPU (small problems, small batches).
+ *                         GPU (small problems, small batches);
+ *   LSLU_LOOP_CLUSTER     one thread-block cluster (16 CTAs where the device
+ *                         allows, else 8) runs the same steps for one small
+ *                         problem, keeping the current basis vector, T^-1 and
+ *                         its rows of every vector in shared memory and
+ *                         synchronising with hardware cluster barriers; single
+ *                         problems whose vectors and T^-1 fit a CTA's shared
+ *                         memory: about max(m, n) + 2 (max_iter+1)^2 entries
+ *                         of the compute type (8 bytes with FP64 values, 4
+ *                         otherwise), at most 200 KB (refused otherwise).
+ *                         blocks and stall_first_barrier must be 0.
  * The projected solve and x = L y follow as in the graph mode.  A persistent
  * handle serves lslu_solve, lslu_solve_batched, lslu_solve_stopping and
  * lslu_solve_optimal with x0 = NULL and searched pivots; x0, replayed or
@@ -420,15 +430,17 @@ lslu_status lslu_tune_spmv(lslu_handle h, int32_t reps, int32_t* shape_A, int32_
  *                   a word nothing writes, so it runs out after wait_limit_ns
  *                   (which must then be given); use 0 otherwise.
  * Errors: LSLU_ERR_INVALID_ARG (unknown mode, shared-matrix handles, more than
- * 1024 problems, blocks or wait_limit_ns out of range), LSLU_ERR_CUDA (no
- * cooperative launch on the device), LSLU_ERR_OOM.  Drops captured solves. */
-enum { LSLU_LOOP_GRAPH = 0, LSLU_LOOP_PERSISTENT = 1 };
+ * 1024 problems, blocks or wait_limit_ns out of range; for the cluster mode a
+ * batch or a problem that does not fit), LSLU_ERR_CUDA (no cooperative or
+ * cluster launch on the device), LSLU_ERR_OOM.  Drops captured solves. */
+enum { LSLU_LOOP_GRAPH = 0, LSLU_LOOP_PERSISTENT = 1, LSLU_LOOP_CLUSTER = 2 };
 lslu_status lslu_set_loop(lslu_handle h, int32_t mode, int32_t blocks, int64_t wait_limit_ns,
                           int32_t stall_first_barrier);
 
 /* The loop configuration (host outputs, any may be NULL): mode, blocks of the
- * persistent launch (0 in graph mode) and the largest co-resident block count
- * of that launch on the handle's device (0 where the mode is unavailable). */
+ * persistent launch or CTAs of the cluster (0 in graph mode) and the largest
+ * co-resident block count of the persistent launch on the handle's device (0
+ * where that mode is unavailable). */
 lslu_status lslu_loop_config(lslu_handle h, int32_t* mode, int32_t* blocks, int32_t* max_blocks);
 
 /* One-line description of the last failure on h (h may be NULL for a failed

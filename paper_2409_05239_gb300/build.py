@@ -20,7 +20,7 @@ LIB = os.path.join(LIBDIR, "liblslu.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["lslu_api.cu", "lslu_spmv.cu", "lslu_basis.cu", "lslu_projected.cu", "lslu_noalloc.cu",
            "lslu_adjoint.cu", "lslu_spmv_shapes_a.cu", "lslu_spmv_shapes_b.cu", "lslu_spmv_shapes_c.cu",
-           "lslu_uq.cu", "lslu_persistent.cu"]
+           "lslu_uq.cu", "lslu_persistent.cu", "lslu_cluster.cu"]
 
 
 def nvcc_path() -> str:

@@ -460,7 +460,12 @@ int64_t enqueue_solve(Ctx* c, cudaStream_t s, const double* db, const double* dx
   cudaMemsetAsync(c->tp, 0xff, sizeof(int32_t) * P * (c->kmax + 1), s);
   launches += 1;
 
-  if (c->loop_mode == LSLU_LOOP_PERSISTENT) {
+  if (c->loop_mode == LSLU_LOOP_CLUSTER) {
+    // r0 = b (x0 = 0), then the whole basis loop on one thread-block cluster
+    launch_residual0(db, nullptr, c->r0, m, s);
+    launch_cluster_basis(c, c->r0, K, c->loop_blocks, s);
+    launches += 2;
+  } else if (c->loop_mode == LSLU_LOOP_PERSISTENT) {
     // r0 = b (x0 = 0), then the whole basis loop in one cooperative launch
     launch_residual0(db, nullptr, c->r0, m, s);
     cudaMemsetAsync(c->pq_bar, 0, 3 * sizeof(unsigned), s);
@@ -715,9 +720,9 @@ lslu_status solve_entry(Ctx* c, const double* b, const double* x0, int32_t K, in
   }
   const bool ord = c->ord_m != nullptr;
   const bool fixed = fix_g != nullptr;
-  if (c->loop_mode == LSLU_LOOP_PERSISTENT && (x0 || fixed || nsamp > 0))
+  if (c->loop_mode != LSLU_LOOP_GRAPH && (x0 || fixed || nsamp > 0))
     return set_err(c, LSLU_ERR_INVALID_ARG,
-                   "the persistent basis loop serves x0 = 0 with searched pivots; "
+                   "the persistent and cluster basis loops serve x0 = 0 with searched pivots; "
                    "lslu_set_loop(h, LSLU_LOOP_GRAPH, ...) for x0, replayed or sampled pivots");
   if (fixed) {  // replayed pivots: validate on the host (indices in range, distinct)
     std::vector<int32_t> g(K), t(K + 1);
@@ -1327,6 +1332,25 @@ extern "C" lslu_status lslu_set_loop(lslu_handle h, int32_t mode, int32_t blocks
     drop_graphs(c);
     return LSLU_OK;
   }
+  if (mode == LSLU_LOOP_CLUSTER) {
+    if (c->nprob != 1 || c->shared_rhs)
+      return set_err(c, LSLU_ERR_INVALID_ARG, "the cluster basis loop serves single problems");
+    if (blocks != 0 || stall_first_barrier)
+      return set_err(c, LSLU_ERR_INVALID_ARG,
+                     "the cluster basis loop takes no block count and no stalled barrier");
+    const int C = cluster_loop_setup(c->value_type);
+    if (C < 1) return set_err(c, LSLU_ERR_CUDA, "no thread-block cluster can be resident");
+    if (!cluster_loop_fits(c->value_type, c->m, c->n, c->kmax, C))
+      return set_err(c, LSLU_ERR_INVALID_ARG,
+                     "the problem does not fit one cluster's shared memory "
+                     "(use LSLU_LOOP_PERSISTENT or LSLU_LOOP_GRAPH)");
+    CK(cudaStreamSynchronize(c->stream));
+    c->loop_mode = LSLU_LOOP_CLUSTER;
+    c->loop_blocks = C;
+    c->loop_stall = 0;
+    drop_graphs(c);
+    return LSLU_OK;
+  }
   if (mode != LSLU_LOOP_PERSISTENT) return set_err(c, LSLU_ERR_INVALID_ARG, "unknown loop mode");
   if (c->shared_rhs)
     return set_err(c, LSLU_ERR_INVALID_ARG,
@@ -1393,7 +1417,7 @@ extern "C" lslu_status lslu_loop_config(lslu_handle h, int32_t* mode, int32_t* b
   Ctx* c = h;
   if (!c) return set_err(nullptr, LSLU_ERR_INVALID_ARG, "NULL handle");
   if (mode) *mode = c->loop_mode;
-  if (blocks) *blocks = c->loop_mode == LSLU_LOOP_PERSISTENT ? c->loop_blocks : 0;
+  if (blocks) *blocks = c->loop_mode != LSLU_LOOP_GRAPH ? c->loop_blocks : 0;
   if (max_blocks) {
     *max_blocks = c->shared_rhs ? 0
                                 : persistent_max_blocks(c->value_type, c->kmax, c->nprob,

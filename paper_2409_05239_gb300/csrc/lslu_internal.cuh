@@ -248,8 +248,8 @@ struct Ctx {
 
   // persistent basis loop (lslu_set_loop): one cooperative launch runs the
   // whole basis generation of a solve, with bounded grid barriers
-  int loop_mode = 0;            // LSLU_LOOP_GRAPH or LSLU_LOOP_PERSISTENT
-  int loop_blocks = 0;          // blocks of the persistent launch
+  int loop_mode = 0;            // LSLU_LOOP_GRAPH, _PERSISTENT or _CLUSTER
+  int loop_blocks = 0;          // blocks of the persistent launch, CTAs of the cluster
   unsigned long long loop_wait_ns = 1000000000ull;  // limit of one barrier wait
   int loop_stall = 0;           // test only: the first barrier waits on a word nothing writes
   void* pq_v = nullptr;         // n eliminated q (compute type)
@@ -481,6 +481,16 @@ int projected_cluster_size();
 cudaError_t launch_persistent_basis(Ctx* c, const double* r0, int K, int blocks,
                                     unsigned long long wait_ns, int stall, cudaStream_t s);
 int persistent_max_blocks(int vt, int K, int nprob, int num_sms);
+
+// Basis loop of one small problem on one thread-block cluster
+// (lslu_cluster.cu).  cluster_loop_setup sets the kernels up on the current
+// device and returns the cluster size they run with (0: unavailable);
+// cluster_loop_fits tells whether an m x n problem with K iterations fits the
+// CTAs' shared memory; launch_cluster_basis runs the r0 pivot and K
+// iterations (x0 = 0) into the handle's bases, H, W, pivot lists and state.
+int cluster_loop_setup(int vt);
+bool cluster_loop_fits(int vt, int64_t m, int64_t n, int K, int C);
+cudaError_t launch_cluster_basis(Ctx* c, const double* r0, int K, int C, cudaStream_t s);
 
 template <typename BT>
 void launch_recombine(const BT* L, int64_t ldl, const double* y, int64_t ldy, const double* x0,

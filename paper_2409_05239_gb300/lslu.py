@@ -128,7 +128,7 @@ def _ptr(a):
     return a.data_ptr()  # torch tensor
 
 
-LOOPS = {"graph": 0, "persistent": 1}
+LOOPS = {"graph": 0, "persistent": 1, "cluster": 2}
 
 
 class _LoopControl:
