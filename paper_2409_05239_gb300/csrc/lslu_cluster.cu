@@ -5,7 +5,9 @@
 // ranges of the rows of A (m-space) and of A^T (n-space).  Every CTA keeps in
 // shared memory a copy of the whole current basis vector (the input of the
 // next sparse product), its own rows of the product and of the eliminated
-// vector, its own row pointers, and its own copies of T_L^-1 and T_D^-1.
+// vector, its own rows of both bases (row-major, so the elimination reads
+// them without touching global memory), its own row pointers, and its own
+// copies of T_L^-1 and T_D^-1.
 // Cross-CTA data moves through distributed shared memory, and the three
 // synchronisation points of a half iteration are hardware cluster barriers
 // (release / acquire):
@@ -20,7 +22,8 @@
 //       and writes them into every CTA's copy of the input vector;
 //                                                               cluster barrier
 //
-// Matrices and bases stay in global memory (L2-resident at these sizes).  The
+// The matrix stays in global memory (L2-resident at these sizes); the bases
+// are also written there, for the projected solve and lslu_get_state.  The
 // cluster's CTAs are co-scheduled by the hardware, so no barrier can wait on a
 // CTA that is not running.  Summation orders are fixed (lane groups and
 // shuffle trees), so results are bitwise reproducible.
@@ -41,7 +44,7 @@ namespace cg = cooperative_groups;
 
 constexpr int kCT = 512;             // threads per CTA
 constexpr int kCW = kCT / 32;        // warps per CTA
-constexpr int kLanesPerRow = 8;      // lanes of one row of a sparse product
+constexpr int kLanesPerRow = 4;      // lanes of one row of a product or an elimination
 constexpr int kRowsPerPass = kCT / kLanesPerRow;
 constexpr int kMaxClusterCTAs = 16;
 
@@ -79,13 +82,51 @@ struct ClusterArgs {
   int K;
 };
 
-__device__ __forceinline__ bool better(double va, int ia, double vb, int ib) {
-  if (ia < 0) return false;
-  if (ib < 0) return true;
-  double a = fabs(va), b = fabs(vb);
-  if (a != a) a = INFINITY;  // a NaN must win so that it is reported
-  if (b != b) b = INFINITY;
-  return a > b || (a == b && ia < ib);
+// Pivot candidate as an integer key: hi = bits of |v| (a NaN has larger bits
+// than any number, wins and is reported), lo = (2^31 - 1 - rank) << 1 | sign
+// of v.  The larger (hi, lo) is the larger |v|, ties to the lowest rank (ranks
+// are distinct, so the sign never decides); (0, 0) is no candidate.  Integer
+// comparisons keep the reductions off the FP64 pipe.
+struct PKey {
+  unsigned long long hi;
+  unsigned lo;
+};
+__device__ __forceinline__ bool key_less(const PKey& x, const PKey& y) {
+  return x.hi < y.hi || (x.hi == y.hi && x.lo < y.lo);
+}
+template <typename CT>
+__device__ __forceinline__ PKey make_key(CT v, int rank) {
+  PKey k;
+  if constexpr (sizeof(CT) == 8) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong((double)v);
+    k.hi = b & 0x7fffffffffffffffull;
+    k.lo = ((0x7fffffffu - (unsigned)rank) << 1) | (unsigned)(b >> 63);
+  } else {
+    const unsigned b = __float_as_uint((float)v);
+    k.hi = b & 0x7fffffffu;
+    k.lo = ((0x7fffffffu - (unsigned)rank) << 1) | (b >> 31);
+  }
+  return k;
+}
+template <typename CT>
+__device__ __forceinline__ CT key_value(const PKey& k) {
+  if constexpr (sizeof(CT) == 8)
+    return (CT)__longlong_as_double((long long)(k.hi | ((unsigned long long)(k.lo & 1u) << 63)));
+  else
+    return (CT)__uint_as_float((unsigned)k.hi | ((k.lo & 1u) << 31));
+}
+__device__ __forceinline__ int key_rank(const PKey& k) {
+  return (int)(0x7fffffffu - (k.lo >> 1));
+}
+__device__ __forceinline__ PKey warp_max_key(PKey k, unsigned mask = 0xffffffffu) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    PKey x;
+    x.hi = __shfl_xor_sync(mask, k.hi, o);
+    x.lo = __shfl_xor_sync(mask, k.lo, o);
+    if (key_less(k, x)) k = x;
+  }
+  return k;
 }
 
 template <typename VT>
@@ -116,8 +157,9 @@ __device__ __forceinline__ int owner_of(int64_t row, int64_t rows, int C) {
 // Shared-memory layout of one CTA (offsets in bytes).
 template <typename CT>
 struct CLayout {
-  size_t xv, rows_max, yown, vown, rp, rl, used, cs, xs, trow, slots_v, slots_i, gps, tps, tl, td,
-      total;
+  size_t xv, rows_max, yown, vown, rp, rl, used, cs, xs, trow, slots_h, slots_l, gps, tps, tl, td,
+      lrows, drows, total;
+  int ldr;  // leading dimension of the own basis rows (row-major, columns 0..K)
   int lds;
   __host__ __device__ CLayout(int64_t m, int64_t n, int K, int C) {
     const size_t nmax = (size_t)(m > n ? m : n);
@@ -139,12 +181,15 @@ struct CLayout {
     cs = take(kc * sizeof(CT));
     xs = take(kc * sizeof(CT));
     trow = take(kc * sizeof(CT));
-    slots_v = take(kMaxClusterCTAs * sizeof(double));
-    slots_i = take(kMaxClusterCTAs * sizeof(int));
+    slots_h = take(kMaxClusterCTAs * sizeof(unsigned long long));
+    slots_l = take(kMaxClusterCTAs * sizeof(unsigned));
     gps = take(kc * sizeof(int32_t));
     tps = take(kc * sizeof(int32_t));
     tl = take((size_t)(K + 1) * lds * sizeof(CT));
     td = take((size_t)(K + 1) * lds * sizeof(CT));
+    ldr = K + 1 + (((K + 1) & 1) ? 0 : 1);
+    lrows = take(rows_max * ldr * sizeof(CT));  // own rows of L (columns 0..K-1)
+    drows = take(rows_max * ldr * sizeof(CT));  // own rows of D (columns 0..K)
     total = o;
   }
 };
@@ -165,8 +210,11 @@ __global__ void __launch_bounds__(kCT, 1) k_cluster_basis(ClusterArgs a) {
   CT* cs = reinterpret_cast<CT*>(smem + lay.cs);
   CT* xs = reinterpret_cast<CT*>(smem + lay.xs);
   CT* trow = reinterpret_cast<CT*>(smem + lay.trow);
-  double* slot_v = reinterpret_cast<double*>(smem + lay.slots_v);
-  int* slot_i = reinterpret_cast<int*>(smem + lay.slots_i);
+  unsigned long long* slot_h = reinterpret_cast<unsigned long long*>(smem + lay.slots_h);
+  unsigned* slot_l = reinterpret_cast<unsigned*>(smem + lay.slots_l);
+  CT* lrows = reinterpret_cast<CT*>(smem + lay.lrows);  // own rows of the bases, kept in
+  CT* drows = reinterpret_cast<CT*>(smem + lay.drows);  // shared memory (row-major)
+  const int ldr = lay.ldr;
   int32_t* gps = reinterpret_cast<int32_t*>(smem + lay.gps);  // pivot lists, the same in
   int32_t* tps = reinterpret_cast<int32_t*>(smem + lay.tps);  // every CTA
   CT* TLs = reinterpret_cast<CT*>(smem + lay.tl);
@@ -174,7 +222,7 @@ __global__ void __launch_bounds__(kCT, 1) k_cluster_basis(ClusterArgs a) {
   const int lds = lay.lds;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   __shared__ int s_idx;
-  __shared__ double s_piv;
+  __shared__ CT s_piv;
 
   // own rows: m-space [m0, m1), n-space [n0, n1)
   const int64_t m0 = range_lo(a.m, me, C), m1 = range_lo(a.m, me + 1, C);
@@ -197,75 +245,73 @@ __global__ void __launch_bounds__(kCT, 1) k_cluster_basis(ClusterArgs a) {
   const VT* tval = reinterpret_cast<const VT*>(a.t_val);
   __syncthreads();
 
-  // the CTA's largest |value| (ties: lowest rank) over the pairs every thread
-  // holds, written into slot `me` of every CTA of the cluster
-  __shared__ double w_best[kCW];
-  __shared__ int w_bi[kCW];
-  auto publish_best = [&](double best, int besti) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const double ov = __shfl_xor_sync(0xffffffffu, best, o);
-      const int oi = __shfl_xor_sync(0xffffffffu, besti, o);
-      if (better(ov, oi, best, besti)) {
-        best = ov;
-        besti = oi;
-      }
-    }
+  // the CTA's largest key over the keys every thread holds, written into
+  // slot `me` of every CTA of the cluster
+  __shared__ unsigned long long w_hi[kCW];
+  __shared__ unsigned w_lo[kCW];
+  auto publish_key = [&](PKey k) {
+    k = warp_max_key(k);
     if (lane == 0) {
-      w_best[warp] = best;
-      w_bi[warp] = besti;
+      w_hi[warp] = k.hi;
+      w_lo[warp] = k.lo;
     }
     __syncthreads();
-    if (tid < C) {  // thread q sends the CTA's best to CTA q
-      double bb = 0.0;
-      int bi = -1;
-      for (int w = 0; w < kCW; ++w)
-        if (better(w_best[w], w_bi[w], bb, bi)) {
-          bb = w_best[w];
-          bi = w_bi[w];
-        }
-      *cluster.map_shared_rank(slot_v + me, tid) = bb;
-      *cluster.map_shared_rank(slot_i + me, tid) = bi;
+    if (warp == 0) {
+      PKey b;
+      b.hi = lane < kCW ? w_hi[lane] : 0ull;
+      b.lo = lane < kCW ? w_lo[lane] : 0u;
+      b = warp_max_key(b);
+      if (lane < C) {  // lane q sends the CTA's best to CTA q
+        *cluster.map_shared_rank(slot_h + me, lane) = b.hi;
+        *cluster.map_shared_rank(slot_l + me, lane) = b.lo;
+      }
     }
   };
-  // the cluster-wide pivot from the C slots (after a cluster barrier), in
-  // CTA order: rank into s_idx (-1: none), signed value into s_piv
+  // the cluster-wide pivot from the C slots (after a cluster barrier), the
+  // same in every CTA: rank into s_idx (-1: none), value into s_piv
   auto resolve_slots = [&]() {
-    if (tid == 0) {
-      double bb = 0.0;
-      int bi = -1;
-      for (int q = 0; q < C; ++q)
-        if (better(slot_v[q], slot_i[q], bb, bi)) {
-          bb = slot_v[q];
-          bi = slot_i[q];
-        }
-      s_idx = bi;
-      s_piv = bb;
+    if (warp == 0) {
+      PKey b;
+      b.hi = lane < C ? slot_h[lane] : 0ull;
+      b.lo = lane < C ? slot_l[lane] : 0u;
+      b = warp_max_key(b);
+      if (lane == 0) {
+        s_idx = (b.hi | b.lo) ? key_rank(b) : -1;
+        s_piv = key_value<CT>(b);
+      }
     }
     __syncthreads();
   };
 
   // ---- pivot of r0 (exact, FP64) and d_1 = r0 / beta
   {
-    double best = 0.0;
-    int besti = -1;
+    PKey best = {0ull, 0u};
     for (int i = tid; i < nm; i += kCT) {
       if (__ldg(a.tused + m0 + i)) {  // (single problem: nothing is pivoted yet)
         used_s[i] = 1;
         continue;
       }
       const int r = a.rank_m ? __ldg(a.rank_m + m0 + i) : (int)(m0 + i);
-      const double v = __ldg(a.r0 + m0 + i);
-      if (better(v, r, best, besti)) {
-        best = v;
-        besti = r;
+      const PKey kk = make_key<double>(__ldg(a.r0 + m0 + i), r);
+      if (key_less(best, kk)) best = kk;
+    }
+    publish_key(best);
+    cluster.sync();
+    // the exact FP64 pivot of r0 (resolve_slots gives the compute type)
+    __shared__ double s_beta;
+    if (warp == 0) {
+      PKey b;
+      b.hi = lane < C ? slot_h[lane] : 0ull;
+      b.lo = lane < C ? slot_l[lane] : 0u;
+      b = warp_max_key(b);
+      if (lane == 0) {
+        s_idx = (b.hi | b.lo) ? key_rank(b) : -1;
+        s_beta = key_value<double>(b);
       }
     }
-    publish_best(best, besti);
-    cluster.sync();
-    resolve_slots();
+    __syncthreads();
     const int rk = s_idx;
-    const double beta = s_piv;
+    const double beta = s_beta;
     const int idx = rk >= 0 ? (a.unrank_m ? __ldg(a.unrank_m + rk) : rk) : -1;
     if (idx < 0 || beta == 0.0 || !isfinite(beta)) {
       if (me == 0 && tid == 0) {
@@ -288,10 +334,12 @@ __global__ void __launch_bounds__(kCT, 1) k_cluster_basis(ClusterArgs a) {
         a.tused[idx] = 1;
       }
     }
-    // d_1 on the own rows, into the global basis and every CTA's input copy
+    // d_1 on the own rows: the global basis, the own rows of D and every
+    // CTA's input copy
     for (int i = tid; i < nm; i += kCT) {
       const BT d = (BT)(__ldg(a.r0 + m0 + i) / beta);
       Db[m0 + i] = d;
+      drows[(size_t)i * ldr] = (CT)d;
       for (int q = 0; q < C; ++q) *cluster.map_shared_rank(xv + m0 + i, q) = (CT)d;
     }
     cluster.sync();
@@ -312,31 +360,33 @@ __global__ void __launch_bounds__(kCT, 1) k_cluster_basis(ClusterArgs a) {
       const VT* val = Ls ? tval : aval;
       const int cnt = Ls ? k : k + 1;  // earlier basis vectors of this side
       const int32_t* piv = Ls ? gps : tps;
-      const BT* B = Ls ? Lb : Db;
-      const int64_t ldb = Ls ? a.ldl : a.ldd;
+      CT* brows = Ls ? lrows : drows;  // own rows of this side's basis
       CT* Ts = Ls ? TLs : TDs;
       // ---- P1: own rows of the product, gathering from the input copy
       for (int base = 0; base < nr; base += kRowsPerPass) {
         const int rr = base + tid / kLanesPerRow;
         const int gl = tid & (kLanesPerRow - 1);
-        CT acc = 0;
+        CT acc = 0, acc2 = 0;
         if (rr < nr) {
           const int32_t st = rps[rr], len = rls[rr];
-          // four entries per lane in flight: loads first, then the gathers
-          for (int32_t e = gl; e < len; e += 4 * kLanesPerRow) {
-            int32_t cc[4];
-            CT vv[4];
+          // eight entries per lane in flight: loads first, then the gathers
+          for (int32_t e = gl; e < len; e += 8 * kLanesPerRow) {
+            int32_t cc[8];
+            CT vv[8];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < 8; ++u) {
               const int32_t q = e + u * kLanesPerRow;
               cc[u] = q < len ? __ldg(col + st + q) : -1;
               vv[u] = q < len ? (CT)val_at<VT>(val, st + q) : (CT)0;
             }
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
+            for (int u = 0; u < 8; u += 2) {
               if (cc[u] >= 0) acc = fma(vv[u], xv[cc[u]], acc);
+              if (cc[u + 1] >= 0) acc2 = fma(vv[u + 1], xv[cc[u + 1]], acc2);
+            }
           }
         }
+        acc += acc2;
 #pragma unroll
         for (int o = kLanesPerRow / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         if (rr < nr && gl == 0) yown[rr] = acc;
@@ -368,26 +418,21 @@ __global__ void __launch_bounds__(kCT, 1) k_cluster_basis(ClusterArgs a) {
       }
       // ---- P3: eliminate the own rows (lane group per row, columns split
       // over the group's lanes in a fixed order), then the CTA's best
-      double best = 0.0;
-      int besti = -1;
+      PKey best = {0ull, 0u};
       for (int base = 0; base < nr; base += kRowsPerPass) {
         const int rr = base + tid / kLanesPerRow;
         const int gl = tid & (kLanesPerRow - 1);
-        CT acc = 0;
+        CT acc = 0, acc2 = 0;
         if (rr < nr) {
-          const BT* bp = B + r0 + rr;
-          for (int j = gl; j < cnt; j += 4 * kLanesPerRow) {
-            CT bv[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              const int q = j + u * kLanesPerRow;
-              bv[u] = q < cnt ? (CT)bp[(int64_t)q * ldb] : (CT)0;
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-              if (j + u * kLanesPerRow < cnt) acc = fma(cs[j + u * kLanesPerRow], bv[u], acc);
+          const CT* bp = brows + (size_t)rr * ldr;
+          int j = gl;
+          for (; j + kLanesPerRow < cnt; j += 2 * kLanesPerRow) {
+            acc = fma(cs[j], bp[j], acc);
+            acc2 = fma(cs[j + kLanesPerRow], bp[j + kLanesPerRow], acc2);
           }
+          if (j < cnt) acc = fma(cs[j], bp[j], acc);
         }
+        acc += acc2;
 #pragma unroll
         for (int o = kLanesPerRow / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         if (rr < nr && gl == 0) {
@@ -397,21 +442,19 @@ __global__ void __launch_bounds__(kCT, 1) k_cluster_basis(ClusterArgs a) {
             const int64_t row = r0 + rr;
             const int rk = Ls ? (a.rank_n ? __ldg(a.rank_n + row) : (int)row)
                               : (a.rank_m ? __ldg(a.rank_m + row) : (int)row);
-            if (better((double)v, rk, best, besti)) {
-              best = (double)v;
-              besti = rk;
-            }
+            const PKey kk = make_key<CT>(v, rk);
+            if (key_less(best, kk)) best = kk;
           }
         }
       }
-      publish_best(best, besti);
+      publish_key(best);
       cluster.sync();
       // ---- P4: the pivot, T^-1, the new basis vector
       resolve_slots();
       const int rk = s_idx;
       const int32_t* unrank = Ls ? a.unrank_n : a.unrank_m;
       const int idx = rk >= 0 ? (unrank ? __ldg(unrank + rk) : rk) : -1;
-      const CT pv = (CT)s_piv;
+      const CT pv = s_piv;
       const int slot = cnt;
       if (idx < 0 || pv == (CT)0 || !isfinite((double)pv)) {
         if (me == 0 && tid == 0) {
@@ -439,20 +482,25 @@ __global__ void __launch_bounds__(kCT, 1) k_cluster_basis(ClusterArgs a) {
           (Ls ? a.gused : a.tused)[idx] = 1;
         }
       }
-      // new row `slot` of T^-1: T(slot, l) = b_l(idx)
-      for (int l = tid; l < slot; l += kCT) trow[l] = (CT)B[(int64_t)l * ldb + idx];
+      // new row `slot` of T^-1: T(slot, l) = b_l(idx), from the owner's rows
+      {
+        const int o = owner_of(idx, rows, C);
+        const CT* orow =
+            cluster.map_shared_rank(brows, o) + (size_t)(idx - range_lo(rows, o, C)) * ldr;
+        for (int l = tid; l < slot; l += kCT) trow[l] = orow[l];
+      }
       __syncthreads();
+      // (threads step through l together, so a warp's reads of Ts hit
+      // distinct banks; the terms l < j are zero)
       for (int j = tid; j < slot; j += kCT) {
-        CT s0 = 0, s1 = 0, s2 = 0, s3 = 0;
-        int l = j;
-        for (; l + 4 <= slot; l += 4) {
-          s0 = fma(trow[l], Ts[j * lds + l], s0);
-          s1 = fma(trow[l + 1], Ts[j * lds + l + 1], s1);
-          s2 = fma(trow[l + 2], Ts[j * lds + l + 2], s2);
-          s3 = fma(trow[l + 3], Ts[j * lds + l + 3], s3);
+        CT s[4] = {0, 0, 0, 0};
+        const int l0 = j & ~3;
+        for (int l = l0; l < slot; l += 4) {
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (l + u >= j && l + u < slot) s[u] = fma(trow[l + u], Ts[j * lds + l + u], s[u]);
         }
-        for (; l < slot; ++l) s0 = fma(trow[l], Ts[j * lds + l], s0);
-        Ts[j * lds + slot] = -((s0 + s1) + (s2 + s3));
+        Ts[j * lds + slot] = -((s[0] + s[1]) + (s[2] + s[3]));
       }
       if (tid == 0) Ts[slot * lds + slot] = (CT)1;
       __syncthreads();
@@ -463,9 +511,11 @@ __global__ void __launch_bounds__(kCT, 1) k_cluster_basis(ClusterArgs a) {
       // b_new = v / pivot on the own rows: the global basis (column k of L, or
       // k+1 of D) and every CTA's input copy for the next product
       BT* out = Ls ? Lb + (int64_t)k * a.ldl : Db + (int64_t)(k + 1) * a.ldd;
+      const int ocol = Ls ? k : k + 1;
       for (int i = tid; i < nr; i += kCT) {
         const BT b = (BT)(vown[i] / pv);
         out[r0 + i] = b;
+        brows[(size_t)i * ldr + ocol] = (CT)b;
         for (int q = 0; q < C; ++q) *cluster.map_shared_rank(xv + r0 + i, q) = (CT)b;
       }
       cluster.sync();

@@ -30,8 +30,8 @@
 //      grid sigma_1 * 10^[-14, 2] of lambda: the GCV function (Eq. gcv2), or
 //      weighted GCV with omega = (k+1)/m (Eq. wgcv).
 //   4. k_finish, one block per problem: lambda by the rule (none: 0, fixed, or
-//      the best grid point refined by 64 bisection steps on the sign of
-//      dG/d(lambda^2) between its neighbours), the projected residual
+//      the best grid point refined between its neighbours to the root of
+//      dG/d(lambda^2) by safeguarded Newton steps), the projected residual
 //      ||beta e1 - H y|| = sqrt(sum f_i^2 c_i^2 + c_{k+1}^2) with
 //      f_i = lambda^2 / (sigma_i^2 + lambda^2), and y = Q z with
 //      z = argmin ||beta e1 - B z||^2 + lambda^2 ||z||^2 by the Givens sweep
@@ -278,6 +278,39 @@ __device__ GcvSums gcv_sums(const double* sig2, const double* c2, int k, double 
   }
   block_sum4(v, red4, parity);
   return {v[0] + c2[k], v[1], 1.0 + v[2], omega * v[3]};
+}
+
+// The slope s(mu) = N' D - 2 N D' of G = N / D^2 (same sign as dG/dlambda)
+// and its derivative s'(mu) = N'' D - N' D' - 2 N D'' for the safeguarded
+// Newton refinement of lambda; f = mu / (s2 + mu), f' = s2 / (s2 + mu)^2,
+// f'' = -2 s2 / (s2 + mu)^3, N = sum f^2 c2 + c2_{k+1}, D = 1 + sum
+// ((1 - omega) s2 + mu) / (s2 + mu), D' = omega sum f', D'' = omega sum f''.
+struct SlopeAndDerivative {
+  double s, ds, N, D;
+};
+__device__ SlopeAndDerivative gcv_slope2(const double* sig2, const double* c2, int k, double mu,
+                                         double omega, double* red4, int& parity) {
+  double v[4] = {0.0, 0.0, 0.0, 0.0};  // N, N', N'', D - 1
+  double w[4] = {0.0, 0.0, 0.0, 0.0};  // sum f', sum f'', unused
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    const double s2 = sig2[i];
+    const double rw = 1.0 / (s2 + mu);
+    const double f = mu * rw;
+    const double fp = s2 * rw * rw;
+    const double fpp = -2.0 * fp * rw;
+    const double c = c2[i];
+    v[0] = fma(f * f, c, v[0]);
+    v[1] = fma(2.0 * f * fp, c, v[1]);
+    v[2] = fma(2.0 * fma(fp, fp, f * fpp), c, v[2]);
+    v[3] = fma(fma(1.0 - omega, s2, mu), rw, v[3]);
+    w[0] += fp;
+    w[1] += fpp;
+  }
+  block_sum4(v, red4, parity);
+  block_sum4(w, red4, parity);
+  const double N = v[0] + c2[k], dN = v[1], ddN = v[2], D = 1.0 + v[3];
+  const double dD = omega * w[0], ddD = omega * w[1];
+  return {dN * D - 2.0 * N * dD, ddN * D - dN * dD - 2.0 * N * ddD, N, D};
 }
 
 // Global work space of one problem of size kk.
@@ -805,16 +838,25 @@ __global__ void __launch_bounds__(kTF) k_finish(ProjArgs a, ProjWork w) {
         return g.dN * g.D - 2.0 * g.N * g.dD;
       };
       if (slope(lo * lo) < 0.0 && slope(hi * hi) > 0.0) {
-        for (int it = 0; it < 64; ++it) {
-          const double mu = lo * hi;
-          const double mid = sqrt(mu);
-          if (!(mid > lo && mid < hi)) break;  // the bracket cannot shrink further
-          if (slope(mu) < 0.0)
-            lo = mid;
+        // the root of the slope inside the bracket [a, b] (in mu = lambda^2):
+        // Newton steps, kept only while they stay inside the bracket (else
+        // the geometric midpoint), the bracket narrowed by the slope's sign;
+        // it ends when a step cannot move mu (the root to working precision)
+        double a2 = lo * lo, b2 = hi * hi, mu = lo * hi;
+        for (int it = 0; it < 60; ++it) {
+          const SlopeAndDerivative sd = gcv_slope2(sig2, c2, k, mu, omega, red4, par);
+          if (sd.s == 0.0) break;
+          if (sd.s < 0.0)
+            a2 = mu;
           else
-            hi = mid;
+            b2 = mu;
+          double nx = (sd.ds > 0.0) ? mu - sd.s / sd.ds : -1.0;
+          if (!(nx > a2 && nx < b2)) nx = sqrt(a2) * sqrt(b2);
+          if (!(nx > a2 && nx < b2) || nx == mu) break;
+          const bool done = fabs(nx - mu) <= 4.0 * kEps * mu;
+          mu = nx;
+          if (done) break;
         }
-        const double mu = lo * hi;
         const GcvSums g = gcv_sums(sig2, c2, k, mu, omega, red4, par);
         if (!((double)k * g.N / (g.D * g.D) > gib)) lam = sqrt(mu);
       }

@@ -15,7 +15,8 @@ to it; "all" = every shape in lslu.Solver.SHAPES order), so that a profiler sees
 the products of every shape in one process: each solve launches 2 K products,
 A^T d_k then A l_k for k = 0..K-1.  `--order tiles` builds the handle with
 tomo.locality_order's renumbering (lslu_create_ordered); `--tune` runs the
-sparse-product autotuner first, as the benchmark does.
+sparse-product autotuner first, as the benchmark does; `--loop persistent` or
+`--loop cluster` runs the basis loop as one launch (lslu_set_loop).
 """
 from __future__ import annotations
 
@@ -39,6 +40,8 @@ def main(argv=None):
     ap.add_argument("--order", default="natural", choices=["natural", "tiles"])
     ap.add_argument("--tune", action="store_true",
                     help="run the sparse-product autotuner before the solves (as bench.py does)")
+    ap.add_argument("--loop", default="graph", choices=["graph", "persistent", "cluster"],
+                    help="basis-loop execution (lslu_set_loop)")
     a = ap.parse_args(argv)
 
     import torch
@@ -54,6 +57,8 @@ def main(argv=None):
         Ps = tomo.make_uneven_batch(a.batch)
         b = np.concatenate([P.b for P in Ps])
         with lslu.from_problems(Ps, a.value_type, K, stream=stream) as s:
+            if a.loop != "graph":
+                s.set_loop(a.loop)
             t0 = time.perf_counter()
             for _ in range(a.repeat):
                 r = s.solve(b, K, a.rule, a.lam)
@@ -71,6 +76,8 @@ def main(argv=None):
         with lslu.from_problem(P, a.value_type, K, order=order) as s:
             if a.tune:
                 s.tune_spmv(reps=3)
+            if a.loop != "graph":
+                s.set_loop(a.loop)
             runs = []
             for name in names or [None]:
                 if name is not None:
