@@ -84,12 +84,21 @@ struct Vec16<double> {
   }
 };
 
-// FP32 pivot key: (bits of |v| << 32) | (2^32 - 1 - i).  One unsigned max
-// gives the largest |v| with ties to the lowest index; a NaN has larger bits
-// than any number, wins and is reported.
-__device__ __forceinline__ unsigned long long argkey(float a, int i) {
+// FP32 pivot key: (bits of |v| << 32) | ((2^31 - 1 - i) << 1) | sign of v.
+// One unsigned max gives the largest |v| with ties to the lowest index i
+// (0 <= i < 2^31; the sign bit never decides, as i is unique); a NaN has
+// larger bits than any number, wins and is reported.  The key holds the
+// pivot's value exactly, so the pivot is recorded without reading v again.
+__device__ __forceinline__ unsigned long long argkey(float a, int i, bool neg) {
   return ((unsigned long long)__float_as_uint(a) << 32) |
-         (unsigned long long)(0xffffffffu - (unsigned)i);
+         ((unsigned long long)(0x7fffffffu - (unsigned)i) << 1) | (neg ? 1ull : 0ull);
+}
+__device__ __forceinline__ int key_index(unsigned long long m) {
+  return (int)(0x7fffffffu - (unsigned)((m & 0xffffffffull) >> 1));
+}
+__device__ __forceinline__ float key_value(unsigned long long m) {
+  const float a = __uint_as_float((unsigned)(m >> 32));
+  return (m & 1ull) ? -a : a;
 }
 
 __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long k) {
@@ -116,13 +125,15 @@ __device__ __forceinline__ int unrank_of(const PivotArgs& pa, int r) {
 }
 
 // Records the pivot of problem p (one thread).
+// have_val: pv_known is v(besti) (from an FP32 key), so v is not read again.
 template <typename CT, typename BT>
 __device__ void record_pivot(const PivotArgs& pa, DevState& s, int p, int besti, double best,
-                             const CT* v) {
+                             const CT* v, bool have_val = false, CT pv_known = 0) {
   if (pa.fixed) {  // replay: the given row, whatever the search found
     besti = pa.fixed[(int64_t)p * pa.piv_stride + pa.piv_slot];
     best = fabs((double)__ldcg(v + besti));
     if (best != best) best = INFINITY;
+    have_val = false;
   }
   if (besti < 0 || best == 0.0) {
     s.status = pa.breakdown_code;
@@ -131,7 +142,7 @@ __device__ void record_pivot(const PivotArgs& pa, DevState& s, int p, int besti,
     s.status = LSLU_ERR_NONFINITE;
     s.k_done = pa.k_on_breakdown;
   } else {
-    const CT pv = __ldcg(v + besti);
+    const CT pv = have_val ? pv_known : __ldcg(v + besti);
     s.pivot = (double)pv;
     s.pivot_f = (float)pv;
     pa.piv_list[(int64_t)p * pa.piv_stride + pa.piv_slot] = besti;
@@ -153,9 +164,10 @@ __device__ unsigned long long sampled_key(const PivotArgs& pa, const CT* v) {
   for (int j = threadIdx.x; j < pa.nsamp; j += blockDim.x) {
     const int32_t i = pa.samples[j];
     if (!pa.used[i]) {
-      const float a = fabsf((float)__ldcg(v + i));
+      const float vi = (float)__ldcg(v + i);
+      const float a = fabsf(vi);
       if (a != 0.0f) {
-        const unsigned long long kk = argkey(a, rank_of(pa, i));
+        const unsigned long long kk = argkey(a, rank_of(pa, i), vi < 0.0f);
         k = kk > k ? kk : k;
       }
     }
@@ -215,7 +227,10 @@ __global__ void __launch_bounds__(32)
   __shared__ bool is_last;
   pdl_wait();  // x, the coefficients and the state come from the kernels before
   pdl_trigger();
-  if (pa.nprob == 1 && st[0].status != LSLU_OK) return;
+  // A single problem that has broken down writes nothing.  Its status is only
+  // needed at the first store, so its read overlaps the tile's first reads
+  // (x, the pivot flags, the coefficients, the basis).
+  const int status0 = pa.nprob == 1 ? st[0].status : (int)LSLU_OK;
   const int lane = threadIdx.x;
   const int64_t ntiles = (rows + TILE - 1) / TILE;
   double best = 0.0;
@@ -225,12 +240,6 @@ __global__ void __launch_bounds__(32)
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int64_t r0 = t * TILE;
     const int p = tile_problem(pa.tile_prob, r0);
-    if (p != cur_p) {
-      __syncwarp();
-      for (int j = lane; j < cnt; j += 32) c[j] = (CT)pa.coef[(int64_t)p * pa.coef_stride + j];
-      __syncwarp();
-      cur_p = p;
-    }
     const int64_t i0 = r0 + lane * VEC;
     const bool full = i0 + VEC <= rows;
     CT val[VEC];
@@ -260,6 +269,12 @@ __global__ void __launch_bounds__(32)
     } else {
 #pragma unroll
       for (int e = 0; e < VEC; ++e) usedf[e] = (i0 + e < rows) ? pa.used[i0 + e] : (uint8_t)1;
+    }
+    if (p != cur_p) {  // the problem's coefficients (x and the flags are in flight meanwhile)
+      __syncwarp();
+      for (int j = lane; j < cnt; j += 32) c[j] = (CT)pa.coef[(int64_t)p * pa.coef_stride + j];
+      __syncwarp();
+      cur_p = p;
     }
     const BT* bp = B + i0;  // the basis has whole tiles of rows
     int j = 0;
@@ -301,6 +316,7 @@ __global__ void __launch_bounds__(32)
 #pragma unroll
       for (int e = 0; e < VEC; ++e) rk[e] = (int)(i0 + e);
     }
+    if (status0 != LSLU_OK) return;
     unsigned long long tkey = 0;
     CT outv[VEC];
 #pragma unroll
@@ -312,7 +328,7 @@ __global__ void __launch_bounds__(32)
       if (!usedf[e]) {
         out = val[e];
         if constexpr (kKey) {
-          const unsigned long long kk = argkey(fabsf((float)out), rk[e]);
+          const unsigned long long kk = argkey(fabsf((float)out), rk[e], (float)out < 0.0f);
           tkey = kk > tkey ? kk : tkey;
         } else {
           double a = fabs((double)out);
@@ -347,7 +363,8 @@ __global__ void __launch_bounds__(32)
           for (int e = 0; e < VEC; ++e) {
             const float a = fabsf((float)outv[e]);
             if (i0 + e < rows && !usedf[e] && __float_as_uint(a) == wb) {
-              const unsigned long long kk = argkey(a, __ldg(pa.rank + i0 + e));
+              const unsigned long long kk =
+                  argkey(a, __ldg(pa.rank + i0 + e), (float)outv[e] < 0.0f);
               rkey = kk > rkey ? kk : rkey;
             }
           }
@@ -387,9 +404,10 @@ __global__ void __launch_bounds__(32)
       unsigned long long m = atomicExch(&st[p].amax, 0ull);
       if (p == 0 && (skey >> 32) != 0) m = skey;  // sampled pivot (full search as fallback)
       if (st[p].status != LSLU_OK) continue;
-      const int bi = m ? unrank_of(pa, (int)(0xffffffffu - (unsigned)(m & 0xffffffffull))) : -1;
+      const int bi = m ? unrank_of(pa, key_index(m)) : -1;
       const float a = __uint_as_float((unsigned)(m >> 32));
-      record_pivot<CT, BT>(pa, st[p], p, bi, (a != a) ? INFINITY : (double)a, v);
+      record_pivot<CT, BT>(pa, st[p], p, bi, (a != a) ? INFINITY : (double)a, v, true,
+                           (CT)key_value(m));
     }
   } else {
     best = 0.0;
