@@ -86,3 +86,32 @@ def test_every_numbering_has_a_note_and_a_table():
     for order in ("tiles", "natural"):
         assert order in bench.ORDER_NOTE
         assert set(bench.SPMV_TRAFFIC["bytes"][order]) >= {"16x2", "16x2/16-bit"}
+
+
+def test_cpu_baseline_from_concurrent_oracle_runs():
+    """cpu_baseline takes the FP64 run of the benchmark's noise level as the
+    one-thread figure and the span of all concurrent runs as the multi-core
+    one (runs are supplied by a stand-in for the process pool's result)."""
+
+    class Done:
+        def __init__(self, runs):
+            self.runs = runs
+
+        def get(self):
+            return self.runs
+
+    runs = [
+        {"value_type": vt, "eta": eta, "k_done": 300, "seconds": sec,
+         "wall_start": 100.0 + i, "wall_end": 100.0 + i + sec}
+        for i, (vt, eta, sec) in enumerate([("f64", 0.005, 200.0), ("f32", 0.005, 190.0),
+                                            ("f64", 0.02, 210.0)])]
+
+    @dataclasses.dataclass
+    class P:
+        eta: float = 0.005
+
+    cb = bench.cpu_baseline(P(), 300, 15.0, oracle_runs=Done(runs))
+    assert cb["cores"] == 1 and cb["value"] == pytest.approx(300 / 200.0)
+    mc = cb["multi_core"]
+    # earliest start 100, latest end 102 + 210 = 312
+    assert mc["cores"] == 3 and mc["value"] == pytest.approx(900 / 212.0)
