@@ -727,6 +727,60 @@ def persistent_study(dev, batch_count=64, K_batch=150, order="tiles"):
     return out
 
 
+def variants_study(solver, P, K, reps=3):
+    """The method's variants on the benchmark handle (same workload, numbering
+    and tuned products), each through the public host API (b in, x out):
+    the plain GCV solve for reference; the stopping rule of Eqs. (stop2)/(tol)
+    (the basis to K, the projected solve of every k, the stopping k, x there);
+    sampled pivots (Section 2.2) with 25, 50 and 100 samples per step; the
+    optimal-lambda reference rule; the low-rank posterior variances of Section
+    4.2 after a solve.  Times are per call (the host copies included)."""
+    from paper_2409_05239_gb300 import lslu
+
+    def timed(fn):
+        out = fn()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            out = fn()
+        return (time.perf_counter() - t0) / reps * 1e3, out
+
+    def err(x):
+        return float(np.linalg.norm(x - P.x_true) / np.linalg.norm(P.x_true))
+
+    res = {"workload": f"ct512, K={K}, FP32 values, GCV, the benchmark's handle", "reps": reps}
+    ms, r = timed(lambda: solver.solve(P.b, K, "gcv"))
+    res["plain_solve"] = {"ms": ms, "iter_per_s": K / (ms / 1e3), "rel_err_x_true": err(r["x"])}
+    ms, r = timed(lambda: solver.solve(P.b, K, "gcv", histories=True))
+    lam = float(r["lam_hist"][r["k_done"] - 1])
+    res["solve_with_histories"] = {
+        "ms": ms, "lambda": lam,
+        "note": "lambda_k and the projected residual of every k: a projected solve per k"}
+    ms, r = timed(lambda: solver.solve_stopping(P.b, K, "gcv", 0.0, 1e-6))
+    ne = int(np.count_nonzero(r["G"]))
+    res["stopping_rule"] = {"ms": ms, "tol": 1e-6, "k_stop": int(r["k_stop"]),
+                            "iterations_evaluated": ne,
+                            "rel_err_x_true_at_k_stop": err(r["x"]),
+                            "over_plain_solve": ms / res["plain_solve"]["ms"],
+                            "note": "online: the basis in chunks of 8 iterations, the criterion "
+                                    "after each chunk"}
+    res["sampled_pivots"] = {}
+    for ns in (25, 50, 100):
+        table = lslu.sample_table(K, ns, P.m, P.n, seed=5000 + ns)
+        ms, r = timed(lambda: solver.solve_sampled(P.b, K, table, "gcv"))
+        res["sampled_pivots"][str(ns)] = {"ms": ms, "iter_per_s": r["k_done"] / (ms / 1e3),
+                                          "k_done": int(r["k_done"]),
+                                          "rel_err_x_true": err(r["x"])}
+    ms, r = timed(lambda: solver.solve_optimal(P.b, K, P.x_true))
+    res["optimal_lambda"] = {"ms": ms, "lambda": r["lam"], "rel_err_x_true": err(r["x"])}
+    solver.solve(P.b, K, "gcv")
+    sigma2 = float((P.eta * np.linalg.norm(P.b)) ** 2 / P.m)
+    ms, u = timed(lambda: solver.uq(sigma2, lam, want_diag=True))
+    res["uq_after_solve"] = {"ms": ms, "k": K, "sigma2": sigma2, "var_sum": u["var_sum"],
+                             "note": "diag(Gamma_K) (n entries) and 1^T Gamma_K 1 from the "
+                                     "solve's bases"}
+    return res
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -917,6 +971,7 @@ def run_gpu(args):
         out["shared_rhs_study"] = shared_rhs_study(dev, order=args.order)
         out["adjoint_study"] = adjoint_study(dev, order=args.order)
         out["persistent_study"] = persistent_study(dev, order=args.order)
+        out["variants_study"] = variants_study(solver, P, K)
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         out["cpu_baseline"] = cpu_baseline(P, K, args.cpu_sample_s, oracle_runs)
     if oracle_pool is not None:

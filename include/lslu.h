@@ -259,10 +259,17 @@ lslu_status lslu_adjoint(lslu_handle h, const double* x_bar, int32_t ptr_locatio
  * derivation) and stops at the first k with |G^(k+1) - G^(k)| / G^(1) < tol
  * (Eq. tol), else at the last completed iteration.  Outputs (host or device per
  * ptr_location): x_out (n) = x_k at that iteration (equal to lslu_solve with
- * K = k), k_stop (1), g_hist (K_max, may be NULL; zero past k_done).  The
- * iterations past k_stop are computed (the test needs G^(k+1)); the basis of
- * the first k is independent of them.  A breakdown ends the sequence at
- * k_done. */
+ * K = k), k_stop (1), g_hist (K_max, may be NULL).  The graph loop mode
+ * (the default) stops online: it runs the basis in chunks of 8 iterations,
+ * solves the projected problems of each chunk's sizes and evaluates the
+ * criterion after each chunk, so it computes at most 8 iterations past
+ * k_stop + 1 (the test needs G^(k+1)); g_hist then holds G^(k) for the
+ * iterations evaluated (at least through k_stop + 1, whole chunks or K_max)
+ * and zero past them.  With the persistent or cluster loop (lslu_set_loop) it
+ * runs all K_max iterations, g_hist holds every G^(k) (zero past k_done), and
+ * x0 must be NULL.  Either way the basis of the first k iterations does not
+ * depend on the later ones, so x and each G^(k) are those of the full run.
+ * A breakdown ends the sequence at k_done. */
 lslu_status lslu_solve_stopping(lslu_handle h, const double* b, const double* x0, int32_t K_max,
                                 int32_t rule, double lambda, double tol, int32_t ptr_location,
                                 double* x_out, int32_t* k_stop, double* g_hist);

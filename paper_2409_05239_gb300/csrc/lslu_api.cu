@@ -79,7 +79,7 @@ void destroy_ctx(lslu_ctx* c) {
   free_csr(&c->AT);
   if (c->proj_tstamp) cudaFree(c->proj_tstamp);
   void* ptrs[] = {c->L, c->D, c->H, c->W, c->gp, c->tp, c->gused, c->tused,
-                  c->q, c->u, c->r0, c->xin, c->coef, c->xp, c->part_val, c->part_idx, c->st,
+                  c->q, c->u, c->r0, c->xin, c->coef, c->xp, c->part_val, c->part_idx, c->gstop, c->st,
                   c->TLi, c->TDi,
                   c->pw_single, c->pw_batched, c->pw_offsets, c->proj_out, c->y, c->sig,
                   c->cvec, c->xout, c->tile_prob_m, c->tile_prob_n, c->pad_m, c->pad_n,
@@ -427,9 +427,13 @@ void collect_spmv_times(Ctx* c, int pairs) {
 // Enqueues one whole solve on stream s (no host synchronisation, capturable):
 // state reset, r0 and its pivot, K basis iterations, the projected problems
 // and x = x0 + L y.  Inputs are read from the handle's staging buffers.
+// A part of it (graph loop mode only): iterations k_begin .. k_end-1, with the
+// reset and r0 when k_begin == 0 and the projected problems and x when finish.
 template <typename BT, typename CT>
 int64_t enqueue_solve(Ctx* c, cudaStream_t s, const double* db, const double* dx0, int K,
-                      int rule, double lam, bool hist, bool capturing, bool fixed, int nsamp) {
+                      int rule, double lam, bool hist, bool capturing, bool fixed, int nsamp,
+                      int k_begin = 0, int k_end = -1, bool finish = true) {
+  if (k_end < 0) k_end = K;
   // sampled pivoting: pick t uses row t of the sample table (t = 0 for r0,
   // 2k+1 for q and 2k+2 for u at iteration k)
   auto samp = [&](int t) -> const int32_t* {
@@ -448,6 +452,7 @@ int64_t enqueue_solve(Ctx* c, cudaStream_t s, const double* db, const double* dx
   const int64_t ldh = c->kmax + 1, ldw = c->kmax;
   int64_t launches = 0;
 
+  if (k_begin == 0) {
   launch_init_state(c->st, P, K, s);
   if (P == 1) {
     cudaMemsetAsync(c->gused, 0, n, s);
@@ -459,6 +464,7 @@ int64_t enqueue_solve(Ctx* c, cudaStream_t s, const double* db, const double* dx
   cudaMemsetAsync(c->gp, 0xff, sizeof(int32_t) * P * c->kmax, s);
   cudaMemsetAsync(c->tp, 0xff, sizeof(int32_t) * P * (c->kmax + 1), s);
   launches += 1;
+  }
 
   if (c->loop_mode == LSLU_LOOP_CLUSTER) {
     // r0 = b (x0 = 0), then the whole basis loop on one thread-block cluster
@@ -473,6 +479,7 @@ int64_t enqueue_solve(Ctx* c, cudaStream_t s, const double* db, const double* dx
     launch_persistent_basis(c, c->r0, K, c->loop_blocks, c->loop_wait_ns, c->loop_stall, s);
     launches += 2;
   } else {
+  if (k_begin == 0) {
   // r0 = b - A x0
   if (dx0) {
     launch_spmv<double, double>(c->A, vt, dx0, c->r0, s, c->num_sms);
@@ -491,7 +498,8 @@ int64_t enqueue_solve(Ctx* c, cudaStream_t s, const double* db, const double* dx
     launch_scale<double, BT>(c->r0, D, m, c->st, P, tpm, s, c->num_sms);
     launches += 3;
   }
-  for (int k = 0; k < K; ++k) {
+  }
+  for (int k = k_begin; k < k_end; ++k) {
     // q = A^T d_k (with the coefficients W(0:k, k) from its pivot rows);
     // eliminate l_0..l_{k-1}; pivot; l_k
     cudaEvent_t e0;
@@ -549,6 +557,7 @@ int64_t enqueue_solve(Ctx* c, cudaStream_t s, const double* db, const double* dx
     launches += 6;
   }
   }  // graph-mode basis loop
+  if (!finish) return launches;
   // projected problems: every k (histories) or only k = k_done of each problem
   ProjArgs pa;
   std::memset(&pa, 0, sizeof(pa));
@@ -1426,6 +1435,72 @@ extern "C" lslu_status lslu_loop_config(lslu_handle h, int32_t* mode, int32_t* b
   return LSLU_OK;
 }
 
+// The stopping rule online (graph loop mode): the basis in chunks of
+// kStopChunk iterations launched directly; after each chunk the projected
+// problems of its sizes (one batched launch: residual and trace of each),
+// G^(k) for every k so far and the first k that meets Eq. (tol); the host
+// reads it and stops as soon as the criterion, a breakdown or K_max decides.
+// Each G^(k) and the basis are those of the whole run to K_max, bit for bit.
+constexpr int kStopChunk = 8;
+
+template <typename BT, typename CT>
+lslu_status stopping_online(Ctx* c, const double* db, const double* dx0, int K_max, int rule,
+                            double lam, double tol, double* G, int32_t* dk, int* ks_out) {
+  lslu_status st = ensure_batched_workspace(c);
+  if (st != LSLU_OK) return st;
+  cudaStream_t s = c->stream;
+  const int64_t m = c->m, n = c->n;
+  CK(cudaMemsetAsync(G, 0, (size_t)K_max * 8, s));
+  int64_t launches = 1;
+  int ks = 0;
+  for (int k0 = 0; k0 < K_max;) {
+    const int k1 = std::min(K_max, k0 + kStopChunk);
+    launches += enqueue_solve<BT, CT>(c, s, db, dx0, K_max, rule, lam, false, false, false, 0,
+                                      k0, k1, false);
+    ProjArgs pa;
+    std::memset(&pa, 0, sizeof(pa));
+    pa.H = c->H;
+    pa.ldh = c->kmax + 1;
+    pa.rule = rule;
+    pa.lambda = lam;
+    pa.m = c->prob_m[0];
+    pa.k_first = k0 + 1;
+    pa.k_last = k1;
+    pa.want_y = 0;
+    pa.y = c->y;
+    pa.ldy = c->kmax;
+    pa.nbatch = 1;
+    pa.strideH = c->h_stride;
+    pa.lam_out = c->proj_out;
+    pa.res_out = c->proj_out + c->res_off;
+    pa.tr_out = c->proj_out + 2 * c->res_off;
+    pa.st = c->st;
+    ProjWork w;
+    w.cluster = c->pw_cluster;
+    w.base = c->pw_batched;
+    w.offsets = c->pw_offsets;
+    w.packed = 1;
+    CK(launch_projected(pa, w, s));
+    launch_stop_select(pa.res_out, pa.tr_out, G, k1, (double)n, (double)m, tol, c->st, dk, s);
+    launches += 5;  // projected kernels and the selection
+    int32_t r = 0;
+    CK(cudaMemcpyAsync(&r, dk, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(c->st_host, c->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    CK(cudaGetLastError());
+    // r < k1: the criterion (or a breakdown at k_done = r) decided; a breakdown
+    // at k_done = k1 or the last chunk ends the run with r = min(k1, k_done)
+    if (r < k1 || c->st_host[0].status != LSLU_OK || k1 == K_max) {
+      ks = r;
+      break;
+    }
+    k0 = k1;
+  }
+  c->launches = launches;
+  *ks_out = ks;
+  return LSLU_OK;
+}
+
 extern "C" lslu_status lslu_solve_stopping(lslu_handle h, const double* b, const double* x0,
                                            int32_t K_max, int32_t rule, double lambda,
                                            double tol, int32_t ptr_location, double* x_out,
@@ -1444,6 +1519,9 @@ extern "C" lslu_status lslu_solve_stopping(lslu_handle h, const double* b, const
   if (!b || !x_out) return set_err(c, LSLU_ERR_INVALID_ARG, "b and x_out are required");
   if (ptr_location != LSLU_HOST && ptr_location != LSLU_DEVICE)
     return set_err(c, LSLU_ERR_INVALID_ARG, "unknown ptr_location");
+  if (x0 && c->loop_mode != LSLU_LOOP_GRAPH)
+    return set_err(c, LSLU_ERR_INVALID_ARG,
+                   "the persistent and cluster basis loops serve x0 = 0 only");
   const bool host = ptr_location == LSLU_HOST;
   const int64_t m = c->m, n = c->n;
   cudaStream_t s = c->stream;
@@ -1457,22 +1535,37 @@ extern "C" lslu_status lslu_solve_stopping(lslu_handle h, const double* b, const
     dx0 = c->xin + m;
   }
   const double lam = rule == LSLU_LAMBDA_FIXED ? lambda : 0.0;
-  // the basis for K_max iterations and the projected problem of every k
-  lslu_status st = c->value_type == LSLU_F64
-                       ? solve_impl<double, double>(c, c->xin, dx0, K_max, rule, lam, true)
-                       : solve_impl<float, float>(c, c->xin, dx0, K_max, rule, lam, true);
-  if (st != LSLU_OK) return st;
+  int32_t* dk = reinterpret_cast<int32_t*>(c->part_idx);
+  double* G = nullptr;
+  int32_t ks = 0;
+  if (c->loop_mode == LSLU_LOOP_GRAPH) {
+    // online: the basis in chunks, stopped once k_stop is known
+    if (!c->gstop) CK(dmalloc(&c->gstop, (size_t)c->kmax + 1));
+    G = c->gstop;
+    int ksi = 0;
+    lslu_status st =
+        c->value_type == LSLU_F64
+            ? stopping_online<double, double>(c, c->xin, dx0, K_max, rule, lam, tol, G, dk, &ksi)
+            : stopping_online<float, float>(c, c->xin, dx0, K_max, rule, lam, tol, G, dk, &ksi);
+    if (st != LSLU_OK) return st;
+    ks = ksi;
+  } else {
+    // the basis for K_max iterations and the projected problem of every k
+    lslu_status st = c->value_type == LSLU_F64
+                         ? solve_impl<double, double>(c, c->xin, dx0, K_max, rule, lam, true)
+                         : solve_impl<float, float>(c, c->xin, dx0, K_max, rule, lam, true);
+    if (st != LSLU_OK) return st;
+    // G^(k) for every k and the stopping iteration (Eqs. stop2, tol)
+    G = c->proj_out + 2 * c->res_off;  // G overwrites the trace in place
+    launch_stop_select(c->proj_out + c->res_off, G, G, K_max, (double)n, (double)m, tol, c->st,
+                       dk, s);
+    CK(cudaMemcpyAsync(&ks, dk, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    CK(cudaGetLastError());
+  }
   c->adj_valid = false;
   c->last_k = std::min<int>(std::max(c->st_host[0].k_done, 0), K_max);
   c->last_K = K_max;
-  // G^(k) for every k and the stopping iteration (Eqs. stop2, tol)
-  double* G = c->proj_out + 2 * c->res_off;  // G overwrites the trace in place
-  int32_t* dk = reinterpret_cast<int32_t*>(c->part_idx);
-  launch_stop_select(c->proj_out + c->res_off, G, K_max, (double)n, (double)m, tol, c->st, dk, s);
-  int32_t ks = 0;
-  CK(cudaMemcpyAsync(&ks, dk, 4, cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
-  CK(cudaGetLastError());
   if (ks > 0) {  // y_k and x_k at the stopping iteration
     ProjArgs pa;
     std::memset(&pa, 0, sizeof(pa));

@@ -592,18 +592,19 @@ __global__ void __launch_bounds__(kTile)
   }
 }
 
-// G^(k) = n res_k^2 / ((m - k) + tr_k)^2 for k = 1..k_done (Eq. stop2; G holds
-// tr_k on entry), zero past k_done, and the first k with
-// |G(k+1) - G(k)| / G(1) < tol (Eq. tol), else k_done.  One block.
-__global__ void k_stop_select(const double* __restrict__ res, double* G, int K, double n,
-                              double m, double tol, const DevState* st, int32_t* k_stop) {
+// G^(k) = n res_k^2 / ((m - k) + tr_k)^2 for k = 1..k_done (Eq. stop2; tr may
+// be G itself), zero past k_done, and the first k with
+// |G(k+1) - G(k)| / G(1) < tol (Eq. tol), else min(K, k_done).  One block.
+__global__ void k_stop_select(const double* __restrict__ res, const double* tr, double* G, int K,
+                              double n, double m, double tol, const DevState* st,
+                              int32_t* k_stop) {
   __shared__ int first;
   const int kd = min(K, max(st->k_done, 0));
   if (threadIdx.x == 0) first = kd;
   for (int k = 1 + threadIdx.x; k <= K; k += blockDim.x) {
     double g = 0.0;
     if (k <= kd) {
-      const double den = (m - k) + G[k - 1];
+      const double den = (m - k) + tr[k - 1];
       g = n * res[k - 1] * res[k - 1] / (den * den);
     }
     G[k - 1] = g;
@@ -661,9 +662,10 @@ void launch_init_state(DevState* st, int nprob, int K, cudaStream_t s) {
   k_init_state<<<1, 256, 0, s>>>(st, nprob, K);
 }
 
-void launch_stop_select(const double* res, double* G, int K, double n, double m, double tol,
-                        const DevState* st, int32_t* k_stop, cudaStream_t s) {
-  k_stop_select<<<1, 256, 0, s>>>(res, G, K, n, m, tol, st, k_stop);
+void launch_stop_select(const double* res, const double* tr, double* G, int K, double n,
+                        double m, double tol, const DevState* st, int32_t* k_stop,
+                        cudaStream_t s) {
+  k_stop_select<<<1, 256, 0, s>>>(res, tr, G, K, n, m, tol, st, k_stop);
 }
 
 void launch_residual0(const double* b, const double* Ax0, double* r0, int64_t m,

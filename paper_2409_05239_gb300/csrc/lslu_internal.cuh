@@ -187,6 +187,7 @@ struct Ctx {
   void* xp = nullptr;     // partial coefficient sums: ceil((kmax+1)/8) x ldt
   double* part_val = nullptr;  // argmax partials
   int32_t* part_idx = nullptr;
+  double* gstop = nullptr;  // G^(k) of the online stopping rule (max_iter entries)
   int part_cap = 0;
   DevState* st = nullptr;       // nprob entries
   DevState* st_host = nullptr;  // pinned mirror (nprob entries)
@@ -414,8 +415,9 @@ void launch_scale(const CT* v, BT* out, int64_t rows, DevState* st, int nprob,
 void launch_residual0(const double* b, const double* Ax0, double* r0, int64_t m, cudaStream_t s);
 // G^(k) of Eq. (stop2) for k = 1..K from the projected residuals and traces
 // (G may alias tr), and the stopping iteration of Eq. (tol) into *k_stop.
-void launch_stop_select(const double* res, double* G, int K, double n, double m, double tol,
-                        const DevState* st, int32_t* k_stop, cudaStream_t s);
+void launch_stop_select(const double* res, const double* tr, double* G, int K, double n,
+                        double m, double tol, const DevState* st, int32_t* k_stop,
+                        cudaStream_t s);
 void launch_init_state(DevState* st, int nprob, int K, cudaStream_t s);
 void launch_scatter(const double* src, const int32_t* map, int64_t count, double* dst,
                     cudaStream_t s);

@@ -1,5 +1,7 @@
 """Stopping criterion G^(k) on the GPU (lslu_solve_stopping) against the
-oracle (Eqs. stop2, tol)."""
+oracle (Eqs. stop2, tol).  The graph loop mode stops online: the basis runs
+in chunks of 8 iterations and G^(k) is returned for the iterations evaluated
+(at least through k_stop + 1), zero past them."""
 import numpy as np
 import pytest
 
@@ -21,6 +23,25 @@ def ct32():
     return tomo.make_config("ct32")
 
 
+CHUNK = 8
+
+
+def evaluated(G):
+    """Number of leading entries of a returned G history that were evaluated."""
+    nz = np.flatnonzero(G)
+    return 0 if nz.size == 0 else int(nz[-1]) + 1
+
+
+def check_online_history(G, G_ref, k_stop, K):
+    """The evaluated prefix equals the oracle's; it covers k_stop + 1 (or K)
+    and ends on a chunk boundary or at K; zeros after it."""
+    ne = evaluated(G)
+    assert ne >= min(k_stop + 1, K)
+    assert ne == K or ne % CHUNK == 0
+    assert np.allclose(G[:ne], G_ref[:ne], rtol=1e-8, atol=0)
+    assert np.all(G[ne:] == 0.0)
+
+
 def margin_ok(G, k, tol, rel=1e-6):
     """True when no step before k (nor at k) sits within rel of the threshold,
     so two correct FP64 implementations must stop at the same k."""
@@ -35,9 +56,9 @@ def test_stopping_f64_vs_oracle(ct32, rule, lam, tol):
     x_ref, k_ref, G_ref = O.hybrid_lslu_stopping(ct32.scipy(), ct32.b, K, rule, lam, tol)
     with lslu.from_problem(ct32, "f64", K) as s:
         r = s.solve_stopping(ct32.b, K, rule, lam, tol)
-        assert np.allclose(r["G"], G_ref, rtol=1e-8, atol=0)
         if margin_ok(G_ref, k_ref, tol):
             assert r["k_stop"] == k_ref
+        check_online_history(r["G"], G_ref, r["k_stop"], K)
         ref_k = s.solve(ct32.b, r["k_stop"], rule, lam)
     # x at the stopping iteration equals the plain solve with K = k_stop
     assert np.array_equal(r["x"], ref_k["x"])
@@ -62,3 +83,32 @@ def test_stopping_argument_checks(ct32):
             s.solve_stopping(ct32.b, 1, "gcv")
         with pytest.raises(lslu.LsluError):
             s.solve_stopping(ct32.b, 10, "gcv", tol=0.0)
+
+
+@pytest.mark.parametrize("tol", [1e-6, 1e-3])
+def test_online_stop_equals_the_full_run(ct32, tol):
+    """The online stop (graph loop mode) against the run to K_max (a persistent
+    loop handle takes that path: every projected problem, then the
+    selection): the same stopping k, G^(k) on the evaluated prefix and x."""
+    K = 50
+    with lslu.from_problem(ct32, "f64", K) as s:
+        r = s.solve_stopping(ct32.b, K, "gcv", 0.0, tol)
+    with lslu.from_problem(ct32, "f64", K) as s:
+        s.set_loop("persistent")
+        full = s.solve_stopping(ct32.b, K, "gcv", 0.0, tol)
+    assert evaluated(full["G"]) == K
+    if margin_ok(full["G"], full["k_stop"], tol):
+        assert r["k_stop"] == full["k_stop"]
+    ne = evaluated(r["G"])
+    assert np.allclose(r["G"][:ne], full["G"][:ne], rtol=1e-10, atol=0)
+    if r["k_stop"] == full["k_stop"]:
+        assert np.linalg.norm(r["x"] - full["x"]) <= 1e-10 * np.linalg.norm(full["x"])
+
+
+def test_online_stop_runs_to_k_max_when_the_criterion_never_holds(ct32):
+    K = 20
+    with lslu.from_problem(ct32, "f64", K) as s:
+        r = s.solve_stopping(ct32.b, K, "gcv", 0.0, 1e-300)
+        ref = s.solve(ct32.b, K, "gcv")
+    assert r["k_stop"] == K and evaluated(r["G"]) == K
+    assert np.array_equal(r["x"], ref["x"])
