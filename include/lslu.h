@@ -345,8 +345,9 @@ int64_t lslu_last_launch_count(lslu_handle h);
  * final projected problem, the one that minimises ||L_K y_K(lambda) - x_true||
  * (Eq. lambda of Section 3.2.1, the reference curves of Section 4.1; needs the
  * true solution): the error is
- * evaluated on the 257-point grid sigma_1 10^[-14, 2] and refined by 64
- * golden-section steps in log(lambda) between the best point's neighbours.
+ * evaluated on the 257-point grid sigma_1 10^[-14, 2] and refined between the
+ * best point's neighbours by 5 rounds of 63-point multisection in log(lambda)
+ * (each round keeps its best point and that point's neighbours).
  * Outputs x_out (n) = x_K for that lambda (equal to lslu_solve with
  * LSLU_LAMBDA_FIXED and that lambda) and lambda_out (1, may be NULL); host or
  * device per ptr_location (b: m, x_true: n, FP64).  A breakdown before

@@ -1781,16 +1781,17 @@ extern "C" lslu_status lslu_solve_optimal(lslu_handle h, const double* b, int32_
   c->last_k = K;
   c->last_K = K;
   double* G = nullptr;
-  CK(cudaMalloc(&G, ((size_t)K * K + K + 260) * sizeof(double)));
+  CK(cudaMalloc(&G, ((size_t)K * K + K + 260 + optimal_lambda_work_doubles()) * sizeof(double)));
   double* g = G + (size_t)K * K;
   double* Eg = g + K;
   double* dl = Eg + 257;
+  double* Er = dl + 3;
   st = basis_gram_products(c, K, c->xin + m, G, g);
   if (st == LSLU_OK) {
     ProjWork w;
     w.base = c->pw_single;
     w.cluster = c->pw_cluster;
-    cudaError_t e = launch_optimal_lambda(w, K, c->st, G, g, Eg, dl, s);
+    cudaError_t e = launch_optimal_lambda(w, K, c->st, G, g, Eg, Er, dl, s);
     double lam = 0.0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&lam, dl, 8, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);

@@ -465,8 +465,10 @@ int64_t projected_slot_doubles(int kk, int CL);
 // Optimal lambda of the last projected problem of size K in slot w (needs
 // G = L^T L and g = L^T x_true, k x k and k, FP64): E on the 257-point grid
 // into Eg, then the refined minimiser into *lam_out (device).
+int optimal_lambda_work_doubles();  // round values of the refinement (Er below)
 cudaError_t launch_optimal_lambda(const ProjWork& w, int K, const DevState* st, const double* G,
-                                  const double* g, double* Eg, double* lam_out, cudaStream_t s);
+                                  const double* g, double* Eg, double* Er, double* lam_out,
+                                  cudaStream_t s);
 // G = L_k^T L_k and g = L_k^T v (v: n FP64 on the device) for the bases of a
 // handle (lslu_uq.cu); allocates and frees its own work space.
 lslu_status basis_gram_products(struct Ctx* c, int k, const double* v, double* G, double* g);

@@ -1012,57 +1012,87 @@ __global__ void __launch_bounds__(kT) k_opt_grid(ProjWork w, int K, const DevSta
   if (threadIdx.x == 0) Eg[blockIdx.x] = e;
 }
 
-// The best grid point (ties: the smaller lambda), then 64 golden-section
-// steps in log(lambda) between its neighbours; one block.
-__global__ void __launch_bounds__(kT) k_opt_refine(ProjWork w, int K, const DevState* st,
-                                                   const double* G, const double* g,
-                                                   const double* Eg, double* lam_out) {
+// Refinement of the best grid point (ties: the smaller lambda) by
+// multisection in log(lambda): round r evaluates kOptPts points spaced evenly
+// inside its bracket, one block each, all at once (each evaluation is a chain
+// of dependent FP64 operations, so rounds of parallel points take far less
+// time than one point after another); the next bracket is the best point
+// (ties: the smaller) and its two neighbours.  The bracket holds its centre
+// as a point (kOptPts is odd), so the best value never increases; it shrinks
+// by (kOptPts + 1) / 2 per round, to about 1e-8 of the grid's log spacing
+// after kOptRounds rounds, below the resolution to which the minimiser of an
+// error that is quadratic at its minimum is defined (~sqrt(eps)).
+constexpr int kOptPts = 63;
+constexpr int kOptRounds = 5;
+
+// The bracket [lo, hi] (log lambda) that round r samples; false when the
+// grid's best point is at an end of the grid (no refinement), with lo the
+// log of that grid point.  One thread.
+__device__ bool opt_bracket(int r, double s1, const double* Eg, const double* Er, double& lo,
+                            double& hi) {
+  int b = 0;
+  for (int i = 1; i < kGrid; ++i)
+    if (Eg[i] < Eg[b]) b = i;
+  if (b == 0 || b == kGrid - 1) {
+    lo = hi = log(s1 * pow(10.0, -14.0 + 0.0625 * b));
+    return false;
+  }
+  lo = log(s1 * pow(10.0, -14.0 + 0.0625 * (b - 1)));
+  hi = log(s1 * pow(10.0, -14.0 + 0.0625 * (b + 1)));
+  for (int q = 0; q < r; ++q) {
+    const double h = (hi - lo) / (kOptPts + 1);
+    int j = 0;
+    for (int i = 1; i < kOptPts; ++i)
+      if (Er[q * kOptPts + i] < Er[q * kOptPts + j]) j = i;
+    const double t = lo + (j + 1) * h;
+    lo = t - h;
+    hi = t + h;
+  }
+  return true;
+}
+
+// Round r of the refinement: block i evaluates point i of the round's bracket.
+__global__ void __launch_bounds__(kT) k_opt_round(ProjWork w, int K, const DevState* st,
+                                                  const double* G, const double* g,
+                                                  const double* Eg, double* Er, int r) {
   extern __shared__ double sm[];
   __shared__ double red[33];
-  __shared__ int ib;
+  __shared__ double br[2];
+  __shared__ bool go;
+  const Slots S = carve(w.base, K, w.cluster);
+  const int k = min(K, st->k_done);
+  const double s1 = ldg_cg(S.sig);
+  if (k <= 0 || !(s1 > 0.0)) return;
+  if (threadIdx.x == 0) {
+    double lo, hi;
+    go = opt_bracket(r, s1, Eg, Er, lo, hi);
+    br[0] = lo;
+    br[1] = hi;
+  }
+  __syncthreads();
+  if (!go) return;
+  const double lam = exp(br[0] + (blockIdx.x + 1) * ((br[1] - br[0]) / (kOptPts + 1)));
+  const double e = opt_eval(S, k, st->beta, lam, G, g, sm, red);
+  if (threadIdx.x == 0) Er[r * kOptPts + blockIdx.x] = e;
+}
+
+// The refined lambda: the best point of the last round (or the grid point
+// when it lies at an end of the grid).  One thread.
+__global__ void k_opt_pick(ProjWork w, int K, const DevState* st, const double* Eg,
+                           const double* Er, double* lam_out) {
   const Slots S = carve(w.base, K, w.cluster);
   const int k = min(K, st->k_done);
   const double s1 = ldg_cg(S.sig);
   if (k <= 0 || !(s1 > 0.0)) {
-    if (threadIdx.x == 0) *lam_out = 0.0;
+    *lam_out = 0.0;
     return;
   }
-  if (threadIdx.x == 0) {
-    int b = 0;
-    for (int i = 1; i < kGrid; ++i)
-      if (Eg[i] < Eg[b]) b = i;
-    ib = b;
+  double lo, hi;
+  if (!opt_bracket(kOptRounds, s1, Eg, Er, lo, hi)) {
+    *lam_out = exp(lo);
+    return;
   }
-  __syncthreads();
-  const int b = ib;
-  double lam = s1 * pow(10.0, -14.0 + 0.0625 * b);
-  if (b > 0 && b < kGrid - 1) {
-    const double phi = 0.5 * (sqrt(5.0) - 1.0);
-    double lo = log(s1 * pow(10.0, -14.0 + 0.0625 * (b - 1)));
-    double hi = log(s1 * pow(10.0, -14.0 + 0.0625 * (b + 1)));
-    const double beta = st->beta;
-    double c = hi - phi * (hi - lo), d = lo + phi * (hi - lo);
-    double ec = opt_eval(S, k, beta, exp(c), G, g, sm, red);
-    double ed = opt_eval(S, k, beta, exp(d), G, g, sm, red);
-    for (int it = 0; it < 64; ++it) {
-      if (ec < ed) {
-        hi = d;
-        d = c;
-        ed = ec;
-        c = hi - phi * (hi - lo);
-        ec = opt_eval(S, k, beta, exp(c), G, g, sm, red);
-      } else {
-        lo = c;
-        c = d;
-        ec = ed;
-        d = lo + phi * (hi - lo);
-        ed = opt_eval(S, k, beta, exp(d), G, g, sm, red);
-      }
-    }
-    const double lm = exp(0.5 * (lo + hi));
-    if (opt_eval(S, k, beta, lm, G, g, sm, red) <= Eg[b]) lam = lm;
-  }
-  if (threadIdx.x == 0) *lam_out = lam;
+  *lam_out = exp(0.5 * (lo + hi));  // the last round's best point
 }
 
 }  // namespace
@@ -1183,19 +1213,24 @@ cudaError_t launch_projected(const ProjArgs& a, ProjWork& w, cudaStream_t s) {
 
 namespace lslu {
 
+int optimal_lambda_work_doubles() { return kOptRounds * kOptPts; }
+
 cudaError_t launch_optimal_lambda(const ProjWork& w, int K, const DevState* st, const double* G,
-                                  const double* g, double* Eg, double* lam_out, cudaStream_t s) {
+                                  const double* g, double* Eg, double* Er, double* lam_out,
+                                  cudaStream_t s) {
   const size_t smem = (size_t)4 * (K + 1) * sizeof(double);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_opt_grid, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_opt_refine, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      e = cudaFuncSetAttribute(k_opt_round, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)smem);
     if (e != cudaSuccess) return e;
   }
   k_opt_grid<<<kGrid, kT, smem, s>>>(w, K, st, G, g, Eg);
-  k_opt_refine<<<1, kT, smem, s>>>(w, K, st, G, g, Eg, lam_out);
+  for (int r = 0; r < kOptRounds; ++r)
+    k_opt_round<<<kOptPts, kT, smem, s>>>(w, K, st, G, g, Eg, Er, r);
+  k_opt_pick<<<1, 1, 0, s>>>(w, K, st, Eg, Er, lam_out);
   return cudaGetLastError();
 }
 
