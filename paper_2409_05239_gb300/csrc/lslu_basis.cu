@@ -207,7 +207,7 @@ __device__ void sampled_best(const PivotArgs& pa, const CT* v, double& best, int
 // r0 + l*VEC .. r0 + l*VEC + VEC-1 and eliminates them against all cnt basis
 // columns in order, v = fma(-c_j, b_j, v) for j = 0 .. cnt-1 (the sequential
 // order of Algorithm 4), reading each column as one 16-byte vector with
-// kUnrollJ columns in flight.  No block-level combination is needed, and the
+// UJ = 8 columns in flight.  No block-level combination is needed, and the
 // small blocks spread evenly over the SMs.  The pivot search is a grid
 // reduction that does not depend on timing: FP32 keys combine with an
 // integer atomicMax; FP64 (single problem) candidates are reduced per block
