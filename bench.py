@@ -299,8 +299,9 @@ def _oracle_job(job):
 
 def start_oracle_runs(workload, K):
     """The oracle at the full workload, one spawned process per (value type,
-    noise level) of the precision study; started before the first GPU call and
-    collected at the end (multiprocessing AsyncResult)."""
+    noise level) of the precision study, started with "spawn" (the parent
+    already holds a CUDA context) and collected at the end (multiprocessing
+    AsyncResult)."""
     import multiprocessing as mp
 
     jobs = [(workload, vt, eta, K) for eta in ORACLE_ETAS for vt in VALUE_TYPES_STUDY]
@@ -308,8 +309,7 @@ def start_oracle_runs(workload, K):
     return pool, pool.map_async(_oracle_job, jobs), len(jobs)
 
 
-def precision_study(P, K, dev, order=(None, None), oracle=None, n_phantoms=3, k_step=10,
-                    stop_tol=1e-6):
+def precision_study(P, K, dev, order=(None, None), n_phantoms=3, k_step=10, stop_tol=1e-6):
     """Mixed precision against the FP64 GPU path: A's values in FP64 / FP32 /
     BF16 (FP64 or FP32 basis), GCV lambda, on n_phantoms seeded phantoms at
     each noise level of ORACLE_ETAS (instance 0 at the first level is P).
@@ -318,9 +318,9 @@ def precision_study(P, K, dev, order=(None, None), oracle=None, n_phantoms=3, k_
     rule of Eqs. (stop2)/(tol) picks (GCV lambda, tol = stop_tol), at the
     best iterate of a k_step grid and at K.  For the mixed paths: the mean and
     worst difference to the FP64 path's error at each of the three points, and
-    on how many instances the error is within 1% of the FP64 path's.  With
-    oracle (the AsyncResult of start_oracle_runs): x_K of instance 0 at each
-    noise level against the FP64 oracle run on the same rounded values."""
+    on how many instances the error is within 1% of the FP64 path's.  Returns
+    the study and what oracle_comparison needs to add x_K of instance 0 at
+    each noise level against the FP64 oracle run on the same rounded values."""
     import torch
 
     from paper_2409_05239_gb300 import lslu
@@ -394,32 +394,38 @@ def precision_study(P, K, dev, order=(None, None), oracle=None, n_phantoms=3, k_
                     f"{c['seed_base'] + n_phantoms - 1} x noise {list(ORACLE_ETAS)}; GCV lambda; "
                     f"errors on a {k_step}-iteration grid; stopping rule tol {stop_tol}; "
                     f"differences are mixed minus FP64 (relative error, absolute)")
-    if oracle is not None:
-        from oracle.perturb import first_difference
+    return res, (insts, x_K, gp_K, c)
 
-        out = []
-        try:
-            oracle_results = oracle.get()
-        except Exception as e:  # noqa: BLE001 - reported, the study stands without it
-            res["vs_oracle"] = f"oracle runs failed: {e}"
-            return res
-        for r in oracle_results:
-            i = next(j for j, (eta, seed, _) in enumerate(insts)
-                     if eta == r["eta"] and seed == c["seed_base"])
-            Q = insts[i][2]
-            xg = x_K[(r["value_type"], i)]
-            out.append({"value_type": r["value_type"], "eta": r["eta"], "K": r["K"],
-                        "first_pivot_difference": first_difference(gp_K[(r["value_type"], i)],
-                                                                   r["gp"]),
-                        "rel_diff_x_K_vs_oracle": float(np.linalg.norm(xg - r["x"]) /
-                                                        np.linalg.norm(r["x"])),
-                        "oracle_rel_err_x_true": float(np.linalg.norm(r["x"] - Q.x_true) /
-                                                       np.linalg.norm(Q.x_true)),
-                        "gpu_rel_err_x_true": float(np.linalg.norm(xg - Q.x_true) /
-                                                    np.linalg.norm(Q.x_true)),
-                        "oracle_seconds": r["seconds"]})
-        res["vs_oracle"] = out
-    return res
+
+def oracle_comparison(res, data, oracle):
+    """res["vs_oracle"]: the GPU's x_K of the precision study's instance 0 at
+    each noise level against the oracle runs (the AsyncResult of
+    start_oracle_runs; waits for them)."""
+    from oracle.perturb import first_difference
+
+    insts, x_K, gp_K, c = data
+    try:
+        oracle_results = oracle.get()
+    except Exception as e:  # noqa: BLE001 - reported, the study stands without it
+        res["vs_oracle"] = f"oracle runs failed: {e}"
+        return
+    out = []
+    for r in oracle_results:
+        i = next(j for j, (eta, seed, _) in enumerate(insts)
+                 if eta == r["eta"] and seed == c["seed_base"])
+        Q = insts[i][2]
+        xg = x_K[(r["value_type"], i)]
+        out.append({"value_type": r["value_type"], "eta": r["eta"], "K": r["K"],
+                    "first_pivot_difference": first_difference(gp_K[(r["value_type"], i)],
+                                                               r["gp"]),
+                    "rel_diff_x_K_vs_oracle": float(np.linalg.norm(xg - r["x"]) /
+                                                    np.linalg.norm(r["x"])),
+                    "oracle_rel_err_x_true": float(np.linalg.norm(r["x"] - Q.x_true) /
+                                                   np.linalg.norm(Q.x_true)),
+                    "gpu_rel_err_x_true": float(np.linalg.norm(xg - Q.x_true) /
+                                                np.linalg.norm(Q.x_true)),
+                    "oracle_seconds": r["seconds"]})
+    res["vs_oracle"] = out
 
 
 def batched_study(dev, K=150, count=64, order="tiles"):
@@ -826,11 +832,7 @@ def run_gpu(args):
     rank, world, local = dist_env()
     cfg = tomo.CONFIGS[args.workload]
     K = args.K or cfg["K"]
-    # the FP64 oracle at the full workload for the precision study and the CPU
-    # baseline, in spawned processes that run while the GPU is measured
     oracle_pool = oracle_runs = None
-    if rank == 0 and world == 1 and not args.no_extras and args.workload == WORKLOAD:
-        oracle_pool, oracle_runs, _ = start_oracle_runs(args.workload, K)
     if world > 1:
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
@@ -963,15 +965,40 @@ def run_gpu(args):
             "gpu_launches": launches,
             "clocks": clocks,
         }
+    def study(name, fn):
+        # a study that fails reports its error in its own field; the line stands
+        try:
+            out[name] = fn()
+        except Exception as e:  # noqa: BLE001
+            out[name] = {"error": f"{type(e).__name__}: {e}"}
+            print(f"{name} failed: {e}", file=sys.stderr)
+
+    extras = rank == 0 and not args.no_extras and world == 1
+    if extras:
+        study("variants_study", lambda: variants_study(solver, P, K))
     solver.close()
-    if rank == 0 and not args.no_extras and world == 1:
-        out["precision_study"] = precision_study(P, K, dev, (ro, co), oracle=oracle_runs)
-    if rank == 0 and not args.no_extras and world == 1:
-        out["batched_study"] = batched_study(dev, order=args.order)
-        out["shared_rhs_study"] = shared_rhs_study(dev, order=args.order)
-        out["adjoint_study"] = adjoint_study(dev, order=args.order)
-        out["persistent_study"] = persistent_study(dev, order=args.order)
-        out["variants_study"] = variants_study(solver, P, K)
+    # the FP64 oracle at the full workload for the precision study and the CPU
+    # baseline, in spawned processes that run beside the studies (after the
+    # host-timed measurements above, which they would disturb)
+    if extras and args.workload == WORKLOAD:
+        oracle_pool, oracle_runs, _ = start_oracle_runs(args.workload, K)
+    prec_data = None
+    if extras:
+        def prec():
+            nonlocal prec_data
+            res, prec_data = precision_study(P, K, dev, (ro, co))
+            return res
+
+        study("precision_study", prec)
+        study("batched_study", lambda: batched_study(dev, order=args.order))
+        study("shared_rhs_study", lambda: shared_rhs_study(dev, order=args.order))
+        study("adjoint_study", lambda: adjoint_study(dev, order=args.order))
+        study("persistent_study", lambda: persistent_study(dev, order=args.order))
+        if oracle_runs is not None and prec_data is not None:
+            try:
+                oracle_comparison(out["precision_study"], prec_data, oracle_runs)
+            except Exception as e:  # noqa: BLE001
+                out["precision_study"]["vs_oracle"] = f"{type(e).__name__}: {e}"
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         out["cpu_baseline"] = cpu_baseline(P, K, args.cpu_sample_s, oracle_runs)
     if oracle_pool is not None:
