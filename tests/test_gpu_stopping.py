@@ -112,3 +112,32 @@ def test_online_stop_runs_to_k_max_when_the_criterion_never_holds(ct32):
         ref = s.solve(ct32.b, K, "gcv")
     assert r["k_stop"] == K and evaluated(r["G"]) == K
     assert np.array_equal(r["x"], ref["x"])
+
+
+def test_online_stop_at_a_breakdown_in_a_later_chunk():
+    """A = diag(1..12), b generic: the process breaks down at k_done = 11, in
+    the second chunk; with a criterion that never holds the run stops there,
+    G^(k) for k <= 11 against the oracle and zero after."""
+    n, K = 12, 16
+    A = np.diag(np.arange(1.0, n + 1))
+    b = np.linspace(1.0, 2.0, n)
+    x_ref, k_ref, G_ref = O.hybrid_lslu_stopping(A, b, K, "gcv", 0.0, 1e-300)
+    assert k_ref == 11
+    rp = np.arange(n + 1, dtype=np.int64)
+    ci = np.arange(n, dtype=np.int32)
+    with lslu.Solver(n, n, rp, ci, np.arange(1.0, n + 1), "f64", K) as s:
+        r = s.solve_stopping(b, K, "gcv", 0.0, 1e-300)
+    assert r["k_stop"] == k_ref
+    assert np.allclose(r["G"][:k_ref], G_ref[:k_ref], rtol=1e-8, atol=0)
+    assert np.all(r["G"][k_ref:] == 0.0)
+    assert np.linalg.norm(r["x"] - x_ref) <= 1e-10 * np.linalg.norm(x_ref)
+
+
+def test_online_stop_with_x0(ct32):
+    K = 30
+    x0 = 0.1 * np.sin(np.arange(ct32.n))
+    with lslu.from_problem(ct32, "f64", K) as s:
+        r = s.solve_stopping(ct32.b, K, "gcv", 0.0, 1e-4, x0=x0)
+        ref = s.solve(ct32.b, r["k_stop"], "gcv", x0=x0)
+    assert 1 <= r["k_stop"] <= K
+    assert np.array_equal(r["x"], ref["x"])
