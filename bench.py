@@ -733,6 +733,47 @@ def persistent_study(dev, batch_count=64, K_batch=150, order="tiles"):
     return out
 
 
+def ct256_study(dev, K=200, order="tiles", reps=20):
+    """The 256x256 workload as its configuration states it: Hybrid LSLU, FP32
+    values and accumulation, K = 200, GCV lambda (renumbered like the
+    benchmark when order == "tiles", products autotuned): iterations/s of the
+    device-resident solve (CUDA events on the launch stream over `reps`
+    replays) and the error against x_true; parity against the oracle at this
+    size is tests/test_gpu_parity_large.py::test_ct256_f32_k200_against_oracle."""
+    import torch
+
+    from paper_2409_05239_gb300 import lslu
+
+    P = tomo.make_config("ct256")
+    stream = torch.cuda.current_stream(dev)
+    ro, co = tomo.locality_order(P) if order == "tiles" else (None, None)
+    s = lslu.Solver(P.m, P.n, P.row_ptr, P.col_idx, P.vals, "f32", K, stream=stream.cuda_stream,
+                    row_order=ro, col_order=co)
+    try:
+        s.tune_spmv(reps=5)
+        tuned = {k: v for k, v in s.spmv_config().items() if k.startswith("shape")}
+        b = torch.from_numpy(P.b).to(dev)
+        x = torch.empty(P.n, dtype=torch.float64, device=dev)
+        for _ in range(3):
+            s.solve_device(b, x, K, "gcv")
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            s.solve_device(b, x, K, "gcv")
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        xh = x.cpu().numpy()
+        return {"workload": f"ct256 (m={P.m}, n={P.n}, nnz={P.nnz}), FP32, K={K}, GCV",
+                "numbering": ORDER_NOTE[order], "spmv_shape": tuned, "ms_per_solve": ms,
+                "iter_per_s": K / (ms / 1e3),
+                "rel_err_x_true": float(np.linalg.norm(xh - P.x_true) / np.linalg.norm(P.x_true))}
+    finally:
+        s.close()
+
+
 def variants_study(solver, P, K, reps=3):
     """The method's variants on the benchmark handle (same workload, numbering
     and tuned products), each through the public host API (b in, x out):
@@ -994,6 +1035,7 @@ def run_gpu(args):
         study("shared_rhs_study", lambda: shared_rhs_study(dev, order=args.order))
         study("adjoint_study", lambda: adjoint_study(dev, order=args.order))
         study("persistent_study", lambda: persistent_study(dev, order=args.order))
+        study("ct256_study", lambda: ct256_study(dev, order=args.order))
         if oracle_runs is not None and prec_data is not None:
             try:
                 oracle_comparison(out["precision_study"], prec_data, oracle_runs)
