@@ -841,7 +841,9 @@ __global__ void __launch_bounds__(kTF) k_finish(ProjArgs a, ProjWork w) {
         // the root of the slope inside the bracket [a, b] (in mu = lambda^2):
         // Newton steps, kept only while they stay inside the bracket (else
         // the geometric midpoint), the bracket narrowed by the slope's sign;
-        // it ends when a step cannot move mu (the root to working precision)
+        // it ends when a step moves mu by less than 1e-13 relative (near the
+        // root the slope is rounding noise, and steps below that only wander
+        // inside it) or cannot move it at all
         double a2 = lo * lo, b2 = hi * hi, mu = lo * hi;
         for (int it = 0; it < 60; ++it) {
           const SlopeAndDerivative sd = gcv_slope2(sig2, c2, k, mu, omega, red4, par);
@@ -853,7 +855,7 @@ __global__ void __launch_bounds__(kTF) k_finish(ProjArgs a, ProjWork w) {
           double nx = (sd.ds > 0.0) ? mu - sd.s / sd.ds : -1.0;
           if (!(nx > a2 && nx < b2)) nx = sqrt(a2) * sqrt(b2);
           if (!(nx > a2 && nx < b2) || nx == mu) break;
-          const bool done = fabs(nx - mu) <= 4.0 * kEps * mu;
+          const bool done = fabs(nx - mu) <= 1e-13 * mu;
           mu = nx;
           if (done) break;
         }
