@@ -45,6 +45,7 @@ namespace cg = cooperative_groups;
 constexpr int kCT = 512;             // threads per CTA
 constexpr int kCW = kCT / 32;        // warps per CTA
 constexpr int kLanesPerRow = 4;      // lanes of one row of a product or an elimination
+constexpr int kSumLanes = 8;         // lanes of one coefficient or one new T^-1 entry
 constexpr int kRowsPerPass = kCT / kLanesPerRow;
 constexpr int kMaxClusterCTAs = 16;
 
@@ -399,17 +400,17 @@ __global__ void __launch_bounds__(kCT, 1) k_cluster_basis(ClusterArgs a) {
         xs[j] = *cluster.map_shared_rank(yown + (pr - range_lo(rows, o, C)), o);
       }
       __syncthreads();
-      for (int i = tid; i < cnt; i += kCT) {
-        CT s0 = 0, s1 = 0, s2 = 0, s3 = 0;
-        int j = 0;
-        for (; j + 3 <= i; j += 4) {
-          s0 = fma(Ts[j * lds + i], xs[j], s0);
-          s1 = fma(Ts[(j + 1) * lds + i], xs[j + 1], s1);
-          s2 = fma(Ts[(j + 2) * lds + i], xs[j + 2], s2);
-          s3 = fma(Ts[(j + 3) * lds + i], xs[j + 3], s3);
-        }
-        for (; j <= i; ++j) s0 = fma(Ts[j * lds + i], xs[j], s0);
-        cs[i] = (s0 + s1) + (s2 + s3);
+      // (kSumLanes lanes per coefficient, each a strided part of its sum, then
+      // a fixed shuffle tree: the dependent FP64 chains are kSumLanes times
+      // shorter and spread over the CTA's warps)
+      for (int b0 = 0; b0 < cnt; b0 += kCT / kSumLanes) {
+        const int i = b0 + tid / kSumLanes, part = tid & (kSumLanes - 1);
+        CT sum = 0;
+        if (i < cnt)
+          for (int j = part; j <= i; j += kSumLanes) sum = fma(Ts[j * lds + i], xs[j], sum);
+#pragma unroll
+        for (int o = kSumLanes / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        if (i < cnt && part == 0) cs[i] = sum;
       }
       __syncthreads();
       if (me == 0) {
@@ -490,17 +491,16 @@ __global__ void __launch_bounds__(kCT, 1) k_cluster_basis(ClusterArgs a) {
         for (int l = tid; l < slot; l += kCT) trow[l] = orow[l];
       }
       __syncthreads();
-      // (threads step through l together, so a warp's reads of Ts hit
-      // distinct banks; the terms l < j are zero)
-      for (int j = tid; j < slot; j += kCT) {
-        CT s[4] = {0, 0, 0, 0};
-        const int l0 = j & ~3;
-        for (int l = l0; l < slot; l += 4) {
+      // (kSumLanes lanes per entry j, each a strided part of the sum over
+      // l = j .. slot-1, then a fixed shuffle tree; the terms l < j are zero)
+      for (int b0 = 0; b0 < slot; b0 += kCT / kSumLanes) {
+        const int j = b0 + tid / kSumLanes, part = tid & (kSumLanes - 1);
+        CT sum = 0;
+        if (j < slot)
+          for (int l = j + part; l < slot; l += kSumLanes) sum = fma(trow[l], Ts[j * lds + l], sum);
 #pragma unroll
-          for (int u = 0; u < 4; ++u)
-            if (l + u >= j && l + u < slot) s[u] = fma(trow[l + u], Ts[j * lds + l + u], s[u]);
-        }
-        Ts[j * lds + slot] = -((s[0] + s[1]) + (s[2] + s[3]));
+        for (int o = kSumLanes / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        if (j < slot && part == 0) Ts[j * lds + slot] = -sum;
       }
       if (tid == 0) Ts[slot * lds + slot] = (CT)1;
       __syncthreads();
