@@ -48,6 +48,7 @@ namespace lslu {
 namespace {
 
 constexpr int kPT = 256;           // threads per block
+constexpr int kSumLanes = 8;       // lanes of one coefficient or one new T^-1 entry
 constexpr int kPWarps = kPT / 32;  // warps per block
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -376,17 +377,16 @@ __device__ void coefficients(const Side<BT, CT>& sd, const PersistArgs& a, int p
   __syncthreads();
   const CT* Ti = sd.Ts ? sd.Ts : sd.Tinv + (int64_t)p * a.t_stride;
   const int64_t ld = sd.Ts ? sd.lds : a.ldt;
-  for (int i = threadIdx.x; i < cnt; i += kPT) {
-    CT s0 = 0, s1 = 0, s2 = 0, s3 = 0;
-    int j = 0;
-    for (; j + 3 <= i; j += 4) {
-      s0 = fma(Ti[(int64_t)j * ld + i], xs[j], s0);
-      s1 = fma(Ti[(int64_t)(j + 1) * ld + i], xs[j + 1], s1);
-      s2 = fma(Ti[(int64_t)(j + 2) * ld + i], xs[j + 2], s2);
-      s3 = fma(Ti[(int64_t)(j + 3) * ld + i], xs[j + 3], s3);
-    }
-    for (; j <= i; ++j) s0 = fma(Ti[(int64_t)j * ld + i], xs[j], s0);
-    cs[i] = (s0 + s1) + (s2 + s3);
+  // kSumLanes lanes per coefficient, each a strided part of its sum, then a
+  // fixed shuffle tree (short FP64 chains spread over the block's warps)
+  for (int b0 = 0; b0 < cnt; b0 += kPT / kSumLanes) {
+    const int i = b0 + (int)threadIdx.x / kSumLanes, part = threadIdx.x & (kSumLanes - 1);
+    CT sum = 0;
+    if (i < cnt)
+      for (int j = part; j <= i; j += kSumLanes) sum = fma(Ti[(int64_t)j * ld + i], xs[j], sum);
+#pragma unroll
+    for (int o = kSumLanes / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (i < cnt && part == 0) cs[i] = sum;
   }
   __syncthreads();
 }
@@ -581,17 +581,16 @@ __device__ void tinv_new_row(const BT* B, int64_t ldb, int idx, int slot, CT* Ti
                              CT* trow) {
   for (int l = threadIdx.x; l < slot; l += kPT) trow[l] = (CT)B[(int64_t)l * ldb + idx];
   __syncthreads();
-  for (int j = threadIdx.x; j < slot; j += kPT) {
-    CT s0 = 0, s1 = 0, s2 = 0, s3 = 0;
-    int l = j;
-    for (; l + 4 <= slot; l += 4) {
-      s0 = fma(trow[l], Ti[(int64_t)j * ld + l], s0);
-      s1 = fma(trow[l + 1], Ti[(int64_t)j * ld + l + 1], s1);
-      s2 = fma(trow[l + 2], Ti[(int64_t)j * ld + l + 2], s2);
-      s3 = fma(trow[l + 3], Ti[(int64_t)j * ld + l + 3], s3);
-    }
-    for (; l < slot; ++l) s0 = fma(trow[l], Ti[(int64_t)j * ld + l], s0);
-    Ti[(int64_t)j * ld + slot] = -((s0 + s1) + (s2 + s3));
+  // kSumLanes lanes per entry, as in coefficients()
+  for (int b0 = 0; b0 < slot; b0 += kPT / kSumLanes) {
+    const int j = b0 + (int)threadIdx.x / kSumLanes, part = threadIdx.x & (kSumLanes - 1);
+    CT sum = 0;
+    if (j < slot)
+      for (int l = j + part; l < slot; l += kSumLanes)
+        sum = fma(trow[l], Ti[(int64_t)j * ld + l], sum);
+#pragma unroll
+    for (int o = kSumLanes / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (j < slot && part == 0) Ti[(int64_t)j * ld + slot] = -sum;
   }
   if (threadIdx.x == 0) Ti[(int64_t)slot * ld + slot] = (CT)1;
   __syncthreads();
