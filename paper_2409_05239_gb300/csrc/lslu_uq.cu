@@ -16,9 +16,9 @@
 //
 // Kernels: a tiled Gram pass over the bases (L^T L, D_k^T D_k, L^T 1; basis
 // type products accumulated per row slice, FP64 across slices, reduced in a
-// fixed order), two small FP64 GEMMs, one block for W^-1, the Cholesky factor
-// and R^-1, and a row pass that forms R^-1 l_i for every row and its squared
-// norm.
+// fixed order), two small FP64 GEMMs, one block for the Cholesky factor R,
+// the triangular inverses W^-1 and R^-1 with one warp per column over the GPU,
+// and a row pass that forms R^-1 l_i for every row and its squared norm.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -136,31 +136,77 @@ __global__ void k_gemm_f64(const double* __restrict__ A, int transA, const doubl
   }
 }
 
-// One block: X = W^-1 (upper triangular; W with leading dimension ldw).
-__global__ void k_upper_inverse(const double* __restrict__ W, int64_t ldw, int k,
-                                double* __restrict__ X) {
-  for (int e = threadIdx.x; e < k * k; e += blockDim.x) X[e] = 0.0;
+// X = T^-1 for a triangular T (k x k, leading dimension ldt, column-major;
+// upper: T(i, l) for i <= l, else lower), one warp per column j of X,
+// column-oriented substitution: b = e_j, then for each l from j towards the
+// far end, x_l = b_l * (1 / T(l, l)) and b_i -= T(i, l) x_l for the entries
+// still ahead, which the warp's lanes update in parallel (b in shared memory).
+// Each step is a short chain (a multiply and one FMA per lane entry) instead
+// of one thread's dot product, and all columns run at once over the GPU.
+constexpr int kTriWarps = 4;
+__global__ void __launch_bounds__(kTriWarps * 32)
+    k_tri_inverse(const double* __restrict__ T, int64_t ldt, int k, int upper,
+                  double* __restrict__ X) {
+  extern __shared__ double tsm[];
+  double* rd = tsm;                                          // 1 / T(l, l)
+  double* b = tsm + k + (int64_t)(threadIdx.x >> 5) * k;     // this warp's b
+  const int lane = threadIdx.x & 31;
+  for (int l = threadIdx.x; l < k; l += blockDim.x) rd[l] = 1.0 / T[(int64_t)l * ldt + l];
   __syncthreads();
-  // column j of X solves W x = e_j: x_i = (delta_ij - sum_{l>i} W(i,l) x_l) / W(i,i)
-  for (int j = threadIdx.x; j < k; j += blockDim.x) {
-    double* x = X + (int64_t)j * k;
-    for (int i = j; i >= 0; --i) {
-      double s = (i == j) ? 1.0 : 0.0;
-      for (int l = i + 1; l <= j; ++l) s -= W[(int64_t)l * ldw + i] * x[l];
-      x[i] = s / W[(int64_t)i * ldw + i];
+  const int j = blockIdx.x * kTriWarps + (threadIdx.x >> 5);
+  if (j >= k) return;
+  double* x = X + (int64_t)j * k;
+  for (int i = lane; i < k; i += 32) {
+    b[i] = (i == j) ? 1.0 : 0.0;
+    if (upper ? i > j : i < j) x[i] = 0.0;
+  }
+  __syncwarp();
+  if (upper) {
+    for (int l = j; l >= 0; --l) {
+      const double xl = b[l] * rd[l];
+      if (lane == 0) x[l] = xl;
+      const double* tc = T + (int64_t)l * ldt;
+      for (int i = lane; i < l; i += 32) b[i] = fma(-tc[i], xl, b[i]);
+      __syncwarp();
+    }
+  } else {
+    for (int l = j; l < k; ++l) {
+      const double xl = b[l] * rd[l];
+      if (lane == 0) x[l] = xl;
+      const double* tc = T + (int64_t)l * ldt;
+      for (int i = l + 1 + lane; i < k; i += 32) b[i] = fma(-tc[i], xl, b[i]);
+      __syncwarp();
     }
   }
 }
 
-// One block: S = R R^T in place (lower), then Ri = R^-1 (lower), t = R^-1 s and
-// the sum 1^T Gamma 1 = sigma^2 / lambda^2 (n - ||t||^2).  err = 1 when S is
-// not positive definite.
-__global__ void __launch_bounds__(1024)
-    k_uq_factor(double* __restrict__ S, int k, double* __restrict__ Ri,
-                const double* __restrict__ s, double* __restrict__ t, double n, double scale,
-                double* out_sum, double* err) {
-  __shared__ int bad;
+size_t tri_inverse_smem(int k) { return (size_t)(1 + kTriWarps) * k * sizeof(double); }
+
+// t = R^-1 s (R^-1 lower) and 1^T Gamma 1 = scale (n - ||t||^2); one block.
+__global__ void k_uq_tsum(const double* __restrict__ Ri, int k, const double* __restrict__ s,
+                          double* __restrict__ t, double n, double scale, double* out_sum) {
   __shared__ double red[32];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    double v = 0.0;
+    for (int l = 0; l <= i; ++l) v = fma(Ri[(int64_t)l * k + i], s[l], v);
+    t[i] = v;
+    acc = fma(v, v, acc);
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
+    if (out_sum) *out_sum = scale * (n - tot);
+  }
+}
+
+// One block: S = R R^T in place (lower); err = 1 when S is not positive
+// definite.
+__global__ void __launch_bounds__(1024) k_uq_factor(double* __restrict__ S, int k, double* err) {
+  __shared__ int bad;
   const int tid = threadIdx.x;
   if (tid == 0) bad = 0;
   __syncthreads();
@@ -181,33 +227,7 @@ __global__ void __launch_bounds__(1024)
     }
     __syncthreads();
   }
-  // R^-1: column j solves R x = e_j (forward substitution)
-  for (int j = tid; j < k; j += blockDim.x) {
-    double* x = Ri + (int64_t)j * k;
-    for (int i = 0; i < j; ++i) x[i] = 0.0;
-    for (int i = j; i < k; ++i) {
-      double v = (i == j) ? 1.0 : 0.0;
-      for (int l = j; l < i; ++l) v -= S[(int64_t)l * k + i] * x[l];
-      x[i] = v / S[(int64_t)i * k + i];
-    }
-  }
-  __syncthreads();
-  double acc = 0.0;
-  for (int i = tid; i < k; i += blockDim.x) {
-    double v = 0.0;
-    for (int l = 0; l <= i; ++l) v += Ri[(int64_t)l * k + i] * s[l];
-    t[i] = v;
-    acc += v * v;
-  }
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if ((tid & 31) == 0) red[tid >> 5] = acc;
-  __syncthreads();
-  if (tid == 0) {
-    double tot = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
-    if (out_sum) *out_sum = scale * (n - tot);
-    *err = bad ? 1.0 : 0.0;
-  }
+  if (tid == 0) *err = bad ? 1.0 : 0.0;
 }
 
 // Row pass: for rows [blockIdx.x * 64, +64) and output columns a-tile
@@ -372,11 +392,17 @@ lslu_status uq_impl(Ctx* c, double sigma2, double lam, double* var_diag, double*
     return fail(c, LSLU_ERR_CUDA, std::string("uq gram: ") + cudaGetErrorString(e));
   }
   // X = W^-1, Y = G_D X, S = G_L + lambda^2 X^T Y (into GL)
-  k_upper_inverse<<<1, 256, 0, s>>>(c->W, c->kmax, k, X);
+  const unsigned gt = (unsigned)((k + kTriWarps - 1) / kTriWarps);
+  const size_t smt = tri_inverse_smem(k);
+  if (smt > 48 * 1024)
+    cudaFuncSetAttribute(k_tri_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smt);
+  k_tri_inverse<<<gt, kTriWarps * 32, smt, s>>>(c->W, c->kmax, k, 1, X);
   const dim3 gg((k + 15) / 16, (k + 15) / 16);
   k_gemm_f64<<<gg, 256, 0, s>>>(GD, 0, X, nullptr, 1.0, 0.0, k, Y);
   k_gemm_f64<<<gg, 256, 0, s>>>(X, 1, Y, GL, lam * lam, 1.0, k, GD);  // GD <- S
-  k_uq_factor<<<1, 1024, 0, s>>>(GD, k, Ri, sL, tv, (double)n, scale, scal, scal + 1);
+  k_uq_factor<<<1, 1024, 0, s>>>(GD, k, scal + 1);
+  k_tri_inverse<<<gt, kTriWarps * 32, smt, s>>>(GD, k, k, 0, Ri);
+  k_uq_tsum<<<1, 256, 0, s>>>(Ri, k, sL, tv, (double)n, scale, scal);
   if (var_diag) {
     k_to_basis<BT><<<64, 256, 0, s>>>(Ri, Rib, kk);
     const dim3 gr((unsigned)((n + kTG - 1) / kTG), (unsigned)tiles);
