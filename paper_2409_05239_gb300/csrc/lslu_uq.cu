@@ -251,7 +251,9 @@ __global__ void __launch_bounds__(256)
   const int bmax = k < a0 + kTG ? k : a0 + kTG;  // Ri(a, b) = 0 for b > a
   for (int b0 = 0; b0 < bmax; b0 += kRC) {
     for (int e = threadIdx.x; e < kRC * kTG; e += blockDim.x) {
-      const int bb = e % kRC, cc = e / kRC;
+      // consecutive threads on consecutive rows of L (and entries a of Ri):
+      // coalesced reads of the column-major operands
+      const int cc = e % kTG, bb = e / kTG;
       const int b = b0 + bb;
       const int64_t r = r0 + cc;
       sl[bb][cc] = (b < k && r < n) ? L[(int64_t)b * ldl + r] : (BT)0;
