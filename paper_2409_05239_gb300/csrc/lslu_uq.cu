@@ -57,16 +57,31 @@ __global__ void __launch_bounds__(256)
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int b = 0; b < 4; ++b) acc[a][b] = 0;
-  for (int64_t r0 = r_begin; r0 < r_end; r0 += kRC) {
-    // stage kRC rows x kTG columns of each operand (zero outside)
-    for (int e = threadIdx.x; e < kRC * kTG; e += blockDim.x) {
+  // stage kRC rows x kTG columns of each operand (zero outside); the next
+  // slab's loads are issued into registers before the current one is used
+  constexpr int kPer = kRC * kTG / 256;
+  BT p1[kPer], p2[kPer];
+  auto fetch = [&](int64_t r0) {
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+      const int e = (int)threadIdx.x + 256 * u;
       const int rr = e % kRC, cc = e / kRC;
       const int64_t r = r0 + rr;
       const bool in = r < r_end;
-      s1[rr][cc] = (in && i0 + cc < cols1) ? B1[(int64_t)(i0 + cc) * ld + r] : (BT)0;
-      s2[rr][cc] = (in && j0 + cc < cols2) ? B2[(int64_t)(j0 + cc) * ld + r] : (BT)0;
+      p1[u] = (in && i0 + cc < cols1) ? B1[(int64_t)(i0 + cc) * ld + r] : (BT)0;
+      p2[u] = (in && j0 + cc < cols2) ? B2[(int64_t)(j0 + cc) * ld + r] : (BT)0;
+    }
+  };
+  if (r_begin < r_end) fetch(r_begin);
+  for (int64_t r0 = r_begin; r0 < r_end; r0 += kRC) {
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+      const int e = (int)threadIdx.x + 256 * u;
+      s1[e % kRC][e / kRC] = p1[u];
+      s2[e % kRC][e / kRC] = p2[u];
     }
     __syncthreads();
+    if (r0 + kRC < r_end) fetch(r0 + kRC);
 #pragma unroll 4
     for (int rr = 0; rr < kRC; ++rr) {
       CT a[4], b[4];
@@ -220,10 +235,14 @@ __global__ void __launch_bounds__(1024) k_uq_factor(double* __restrict__ S, int 
     const double piv = S[(int64_t)p * k + p];
     for (int i = p + 1 + tid; i < k; i += blockDim.x) S[(int64_t)p * k + i] /= piv;
     __syncthreads();
-    const int rem = k - p - 1;
-    for (int64_t q = tid; q < (int64_t)rem * rem; q += blockDim.x) {
-      const int i = p + 1 + (int)(q % rem), j = p + 1 + (int)(q / rem);
-      if (i >= j) S[(int64_t)j * k + i] -= S[(int64_t)p * k + i] * S[(int64_t)p * k + j];
+    // trailing update of the lower triangle: warp w takes columns j, its
+    // lanes the rows i >= j
+    const int lane = tid & 31, nw = (int)(blockDim.x >> 5);
+    const double* cp = S + (int64_t)p * k;
+    for (int j = p + 1 + (tid >> 5); j < k; j += nw) {
+      const double sj = cp[j];
+      double* col = S + (int64_t)j * k;
+      for (int i = j + lane; i < k; i += 32) col[i] -= cp[i] * sj;
     }
     __syncthreads();
   }
