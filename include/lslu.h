@@ -365,8 +365,12 @@ lslu_status lslu_solve_optimal(lslu_handle h, const double* b, int32_t K, const 
  * or device per ptr_location, either may be NULL): var_diag (n, FP64) the
  * diagonal of Gamma_k (posterior variances), var_sum (1) = 1^T Gamma_k 1.
  * sigma2 (noise variance) and lambda must be > 0.  Single-problem handles.
- * Errors: LSLU_ERR_INVALID_ARG when no solve has completed an iteration or
- * the k x k system is not positive definite; LSLU_ERR_OOM; LSLU_ERR_CUDA. */
+ * The k x k Cholesky factor runs on one thread-block cluster that keeps its
+ * columns in shared memory: k up to about 640 with 16 CTAs (beyond that W_k is
+ * numerically singular in FP64 for this method).
+ * Errors: LSLU_ERR_INVALID_ARG when no solve has completed an iteration, the
+ * k x k system is not positive definite, or k is above that limit;
+ * LSLU_ERR_OOM; LSLU_ERR_CUDA. */
 lslu_status lslu_uq(lslu_handle h, double sigma2, double lambda, int32_t ptr_location,
                     double* var_diag, double* var_sum);
 

@@ -19,10 +19,12 @@
 // fixed order), two small FP64 GEMMs, one block for the Cholesky factor R,
 // the triangular inverses W^-1 and R^-1 with one warp per column over the GPU,
 // and a row pass that forms R^-1 l_i for every row and its squared norm.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <string>
 
 #include "lslu_internal.cuh"
@@ -218,35 +220,71 @@ __global__ void k_uq_tsum(const double* __restrict__ Ri, int k, const double* __
   }
 }
 
-// One block: S = R R^T in place (lower); err = 1 when S is not positive
-// definite.
-__global__ void __launch_bounds__(1024) k_uq_factor(double* __restrict__ S, int k, double* err) {
+// S = R R^T in place (lower; err = 1 when S is not positive definite) on one
+// thread-block cluster: CTA r of C keeps the
+// columns j = r (mod C) of S in shared memory.  Step p: the owner of column p
+// takes its square root, scales it and writes it into every CTA's buffer of
+// parity p & 1; one cluster barrier; every CTA subtracts its outer product
+// from its own columns j > p.  A buffer is rewritten two steps later, after
+// the barrier that every reader of it has passed.  The FP64 updates spread
+// over C SMs, and a step costs one barrier instead of three.
+constexpr int kCholThreads = 512;
+__global__ void __launch_bounds__(kCholThreads)
+    k_chol_cluster(double* __restrict__ S, int k, double* err) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  extern __shared__ double csm[];
+  const int C = (int)cluster.num_blocks(), me = (int)cluster.block_rank();
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = kCholThreads / 32;
+  const int nown = (k - me + C - 1) / C;  // columns me, me + C, ...
+  double* own = csm;                       // nown x k, column c/C at (c / C) * k
+  double* colp = own + (int64_t)((k + C - 1) / C) * k;  // 2 x k
   __shared__ int bad;
-  const int tid = threadIdx.x;
   if (tid == 0) bad = 0;
-  __syncthreads();
+  for (int q = 0; q < nown; ++q)
+    for (int i = tid; i < k; i += kCholThreads)
+      own[(int64_t)q * k + i] = S[(int64_t)(me + q * C) * k + i];
+  cluster.sync();
   for (int p = 0; p < k; ++p) {
-    if (tid == 0) {
-      const double d = S[(int64_t)p * k + p];
-      if (!(d > 0.0) || !isfinite(d)) bad = 1;
-      S[(int64_t)p * k + p] = sqrt(d > 0.0 ? d : 1.0);
+    double* buf = colp + (p & 1) * k;
+    if (p % C == me) {
+      double* cp = own + (int64_t)(p / C) * k;
+      __shared__ double piv;
+      if (tid == 0) {
+        const double d = cp[p];
+        if (!(d > 0.0) || !isfinite(d)) bad = 1;
+        piv = sqrt(d > 0.0 ? d : 1.0);
+        cp[p] = piv;
+      }
+      __syncthreads();
+      const double pv = piv;
+      for (int i = p + tid; i < k; i += kCholThreads) {
+        const double v = i == p ? pv : cp[i] / pv;
+        cp[i] = v;
+        for (int r = 0; r < C; ++r) *cluster.map_shared_rank(buf + i, r) = v;
+      }
     }
-    __syncthreads();
-    const double piv = S[(int64_t)p * k + p];
-    for (int i = p + 1 + tid; i < k; i += blockDim.x) S[(int64_t)p * k + i] /= piv;
-    __syncthreads();
-    // trailing update of the lower triangle: warp w takes columns j, its
-    // lanes the rows i >= j
-    const int lane = tid & 31, nw = (int)(blockDim.x >> 5);
-    const double* cp = S + (int64_t)p * k;
-    for (int j = p + 1 + (tid >> 5); j < k; j += nw) {
-      const double sj = cp[j];
-      double* col = S + (int64_t)j * k;
-      for (int i = j + lane; i < k; i += 32) col[i] -= cp[i] * sj;
+    cluster.sync();
+    // own columns j > p: S(i, j) -= L(i, p) L(j, p), i >= j
+    for (int q = (p + 1 - me + C - 1) / C + warp; q < nown; q += nw) {
+      const int j = me + q * C;
+      if (j <= p) continue;
+      const double lj = buf[j];
+      double* col = own + (int64_t)q * k;
+      for (int i = j + lane; i < k; i += 32) col[i] -= buf[i] * lj;
     }
     __syncthreads();
   }
-  if (tid == 0) *err = bad ? 1.0 : 0.0;
+  for (int q = 0; q < nown; ++q)
+    for (int i = tid; i < k; i += kCholThreads)
+      S[(int64_t)(me + q * C) * k + i] = own[(int64_t)q * k + i];
+  if (tid == 0 && bad) *err = 1.0;
+  cluster.sync();  // no CTA leaves while another may still write its buffer
+}
+
+constexpr size_t kCholSmemCap = 200 * 1024;
+size_t chol_cluster_smem(int k, int C) {
+  return ((size_t)((k + C - 1) / C) * k + 2 * (size_t)k) * sizeof(double);
 }
 
 // Row pass: for rows [blockIdx.x * 64, +64) and output columns a-tile
@@ -368,6 +406,22 @@ lslu_status uq_impl(Ctx* c, double sigma2, double lam, double* var_diag, double*
   const int k = c->last_k;
   const int64_t n = c->n, m = c->m;
   cudaStream_t s = c->stream;
+  // the k x k Cholesky factor runs on one thread-block cluster whose CTAs hold
+  // its columns in shared memory (k up to about 640 with 16 CTAs; beyond that
+  // W_k is numerically singular in FP64 for this method anyway)
+  const int ccl = projected_cluster_size();
+  const size_t smc = ccl > 0 ? chol_cluster_smem(k, ccl) : 0;
+  if (ccl <= 0 || smc > kCholSmemCap)
+    return fail(c, LSLU_ERR_INVALID_ARG,
+                "uq: k = " + std::to_string(k) +
+                    " is above what the cluster Cholesky factor holds in shared memory");
+  if (cudaFuncSetAttribute(k_chol_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(k_chol_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smc) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, LSLU_ERR_CUDA, "uq: cluster Cholesky set-up");
+  }
   const BT* L = reinterpret_cast<const BT*>(c->L);
   const BT* D = reinterpret_cast<const BT*>(c->D);
   // work space: 5 k x k FP64, 2 k-vectors, pair list, Gram partials, ones
@@ -421,7 +475,29 @@ lslu_status uq_impl(Ctx* c, double sigma2, double lam, double* var_diag, double*
   const dim3 gg((k + 15) / 16, (k + 15) / 16);
   k_gemm_f64<<<gg, 256, 0, s>>>(GD, 0, X, nullptr, 1.0, 0.0, k, Y);
   k_gemm_f64<<<gg, 256, 0, s>>>(X, 1, Y, GL, lam * lam, 1.0, k, GD);  // GD <- S
-  k_uq_factor<<<1, 1024, 0, s>>>(GD, k, scal + 1);
+  // the Cholesky factor on a thread-block cluster (checked to fit above)
+  {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)ccl);
+    cfg.blockDim = dim3(kCholThreads);
+    cfg.dynamicSmemBytes = smc;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)ccl;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    e = cudaMemsetAsync(scal + 1, 0, sizeof(double), s);
+    if (e == cudaSuccess) e = cudaLaunchKernelEx(&cfg, k_chol_cluster, GD, k, scal + 1);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      cudaStreamSynchronize(s);
+      cudaFree(base);
+      return fail(c, LSLU_ERR_CUDA, std::string("uq: cluster Cholesky: ") + cudaGetErrorString(e));
+    }
+  }
   k_tri_inverse<<<gt, kTriWarps * 32, smt, s>>>(GD, k, k, 0, Ri);
   k_uq_tsum<<<1, 256, 0, s>>>(Ri, k, sL, tv, (double)n, scale, scal);
   if (var_diag) {

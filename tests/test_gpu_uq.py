@@ -73,3 +73,16 @@ def test_uq_argument_checks(ct32):
         s.solve(ct32.b, 5, "gcv")
         with pytest.raises(lslu.LsluError):
             s.uq(1.0, 0.0)
+
+
+def test_uq_refuses_k_beyond_the_cluster_factor(ct32):
+    """The k x k Cholesky factor runs on one cluster that holds its columns in
+    shared memory; at k = 660 it does not fit, and (as the oracle shows on
+    this problem: cond(W) ~ 1e18) W_k is numerically singular there anyway.
+    lslu_uq refuses instead of computing a meaningless covariance."""
+    K = 660
+    with lslu.from_problem(ct32, "f64", K) as s:
+        r = s.solve(ct32.b, K, "gcv")
+        assert r["k_done"] == K
+        with pytest.raises(lslu.LsluError, match="cluster Cholesky"):
+            s.uq(noise_var(ct32), 0.05)
