@@ -126,6 +126,11 @@ struct ProjWork {
   int packed = 0;
   int cluster = 1;       // CTAs per cluster
   int slab_in_smem = 0;  // set by the launcher
+  // set by the launcher for each launch that serves part of the problems:
+  int prob0 = 0;  // problem index (k - k_first) of the launch's first problem
+  int kcap = 0;   // largest k of a bidiagonalisation launch (sizes its shared
+                  // memory; 0: k_last)
+  int desc = 0;   // 1: bidiagonalisation clusters take the problems largest k first
   int64_t slot_stride = 0;  // doubles per problem of a batch
 };
 

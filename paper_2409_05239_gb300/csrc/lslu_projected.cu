@@ -57,6 +57,7 @@ constexpr int kTB = 128;  // threads of a bidiagonalisation CTA: one warp per SM
 constexpr int kWB = 4;    // warps per block of the warp-per-item kernels
 constexpr int kWS = 2;    // warps per block of the singular-value kernel
 constexpr int kMaxCluster = 16;
+constexpr int kHistoryCluster = 8;  // CTAs per problem of a history's bidiagonalisation
 constexpr int kGrid = 257;  // lambda grid points
 constexpr double kEps = 2.220446049250313e-16;
 constexpr size_t kSmemCap = 200 * 1024;
@@ -382,20 +383,26 @@ __global__ void __launch_bounds__(kTB) k_bidiag(ProjArgs a, ProjWork w) {
   cg::cluster_group cluster = cg::this_cluster();
   const int CL = (int)cluster.num_blocks();
   const int rank = (int)cluster.block_rank();
-  const int prob = blockIdx.x / CL;
+  const int local = blockIdx.x / CL, nlocal = gridDim.x / CL;
+  const int prob = w.prob0 + (w.desc ? nlocal - 1 - local : local);
   const ProbInfo pi = prob_info(a, prob);
   const int k = pi.k;
   if (k == 0) return;  // every CTA of the cluster sees the same k: no barrier is left waiting
   const Slots S = slot_of(w, pi);
   const double* Hp = a.H + (int64_t)pi.p * a.strideH;
-  const int K1 = a.k_last + 1;
+  const int K1 = (w.kcap > 0 ? w.kcap : a.k_last) + 1;
   const int64_t ld = k + 1;
-  // shared layout: [Ps, cj, sv : K1 each] [xP, xC : 2 x K1 each] [slab]
-  double* Ps = smem;         // summed partial products, rows j..k
-  double* cj = Ps + K1;      // column j (from its owner), then the left reflector
-  double* sv = cj + K1;      // s = A w, rows j+1..k
-  double* xP = sv + K1;      // this CTA's partial products, by step parity
-  double* xC = xP + 2 * K1;  // the owner's copy of the next column, by step parity
+  // The partial products are summed over kMaxCluster virtual ranks (columns
+  // c = v mod kMaxCluster) in one fixed order whatever the cluster size; a
+  // CTA holds the V = kMaxCluster / CL virtual ranks rank + t CL, so results
+  // do not depend on CL.
+  const int V = kMaxCluster / CL;
+  // shared layout: [Ps, cj, sv : K1 each] [xP : 2 V x K1] [xC : 2 x K1] [slab]
+  double* Ps = smem;             // summed partial products, rows j..k
+  double* cj = Ps + K1;          // column j (from its owner), then the left reflector
+  double* sv = cj + K1;          // s = A w, rows j+1..k
+  double* xP = sv + K1;          // this CTA's partial products, by step parity and virtual rank
+  double* xC = xP + 2 * V * K1;  // the owner's copy of the next column, by step parity
   double* slab = xC + 2 * K1;
   const bool in_smem = w.slab_in_smem != 0;
   auto col = [&](int c) -> double* {
@@ -417,17 +424,20 @@ __global__ void __launch_bounds__(kTB) k_bidiag(ProjArgs a, ProjWork w) {
   // A[r, c] A[jn, c] for r = jn..k (r = jn: the partial squared norm of row
   // jn), and from the owner of column jn a copy of it.
   auto publish = [&](int jn) {
-    double* P = xP + (jn & 1) * K1;
-    const int c0 = first_own(jn + 1);
-    for (int r = jn + tid; r <= k; r += nt) {
-      double s0 = 0.0, s1 = 0.0;
-      int c = c0;
-      for (; c + CL < k; c += 2 * CL) {
-        s0 = fma(col(c)[r], col(c)[jn], s0);
-        s1 = fma(col(c + CL)[r], col(c + CL)[jn], s1);
+    for (int t = 0; t < V; ++t) {
+      double* P = xP + ((jn & 1) * V + t) * K1;
+      const int v = rank + t * CL;
+      const int c0 = jn + 1 + ((v - jn - 1) % kMaxCluster + kMaxCluster) % kMaxCluster;
+      for (int r = jn + tid; r <= k; r += nt) {
+        double s0 = 0.0, s1 = 0.0;
+        int c = c0;
+        for (; c + kMaxCluster < k; c += 2 * kMaxCluster) {
+          s0 = fma(col(c)[r], col(c)[jn], s0);
+          s1 = fma(col(c + kMaxCluster)[r], col(c + kMaxCluster)[jn], s1);
+        }
+        if (c < k) s0 = fma(col(c)[r], col(c)[jn], s0);
+        P[r] = s0 + s1;
       }
-      if (c < k) s0 = fma(col(c)[r], col(c)[jn], s0);
-      P[r] = s0 + s1;
     }
     if (jn % CL == rank) {
       double* C = xC + (jn & 1) * K1;
@@ -459,7 +469,7 @@ __global__ void __launch_bounds__(kTB) k_bidiag(ProjArgs a, ProjWork w) {
         double pv[kMaxCluster];
 #pragma unroll
         for (int q = 0; q < kMaxCluster; ++q)
-          pv[q] = q < CL ? *cluster.map_shared_rank(xP + par * K1 + r, q) : 0.0;
+          pv[q] = *cluster.map_shared_rank(xP + (par * V + q / CL) * K1 + r, q % CL);
 #pragma unroll
         for (int h = kMaxCluster / 2; h >= 1; h >>= 1)  // fixed pairwise order
 #pragma unroll
@@ -564,7 +574,7 @@ __global__ void __launch_bounds__(kTB) k_bidiag(ProjArgs a, ProjWork w) {
 __global__ void __launch_bounds__(kWS * 32) k_sigma(ProjArgs a, ProjWork w) {
   extern __shared__ double sh[];
   __shared__ unsigned long long gmax[kWS];
-  const ProbInfo pi = prob_info(a, blockIdx.y);
+  const ProbInfo pi = prob_info(a, w.prob0 + blockIdx.y);
   const int k = pi.k;
   const int i0 = blockIdx.x * kWS;
   if (k == 0 || i0 > k) return;
@@ -660,6 +670,136 @@ __global__ void __launch_bounds__(kWS * 32) k_sigma(ProjArgs a, ProjWork w) {
     __stcg(S.sig + i, th);
     __stcg(S.c2 + i, 2.0 * pi.beta * pi.beta * wgt);
   }
+}
+
+// ---- 2'. the same, one lane per singular value ------------------------------
+// For the many problems of a history (every k of 1..K).  An FP64 warp
+// instruction holds its sub-partition's FP64 pipe for the same time whatever
+// its lanes do, so 32 lanes spent on one singular value (33-fold bracket
+// shrink per round) buy about 5 bits per round where 32 lanes bisecting 32
+// singular values buy 32 (k = 1..300: 15 ms against 47).  Each lane bisects
+// its own sigma_i: through the exponent (halving the number of octaves) while
+// the bracket spans at least two, then linearly, to the same final width as
+// k_sigma.  A warp serves 32 consecutive i of one problem, so its lanes read
+// the same t2 entries; blocks take the problems largest k first.  Shared: as
+// k_sigma.
+constexpr int kWL = 4;           // warps per block
+constexpr int kMaxBisect = 160;  // rounds (the bracket needs ~13 + 52 at most)
+
+__device__ __forceinline__ int biased_exponent(double x) {
+  return (int)((__double_as_longlong(x) >> 52) & 0x7ff);
+}
+
+__global__ void __launch_bounds__(kWL * 32) k_sigma_lanes(ProjArgs a, ProjWork w) {
+  extern __shared__ double sh[];
+  __shared__ unsigned long long gmax[kWL];
+  const ProbInfo pi = prob_info(a, w.prob0 + (int)(gridDim.y - 1 - blockIdx.y));
+  const int k = pi.k;
+  const int i0 = blockIdx.x * kWL * 32;
+  if (k == 0 || i0 > k) return;
+  const Slots S = slot_of(w, pi);
+  const int K1 = a.k_last + 1;
+  double* t2 = sh;            // t2[j] = t_j^2, j = 1..2k
+  double* alv = t2 + 2 * K1;  // alpha_0..alpha_{k-1}
+  double* bev = alv + K1;     // beta_1..beta_k at 1..k
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int n = 2 * k + 1;
+  unsigned long long mx = 0;
+  for (int q = tid; q < k; q += blockDim.x) {
+    const double al = ldg_cg(S.al + q), be = ldg_cg(S.be + q + 1);
+    alv[q] = al;
+    bev[q + 1] = be;
+    t2[2 * q + 1] = al * al;
+    t2[2 * q + 2] = be * be;
+    const unsigned long long ba = (unsigned long long)__double_as_longlong(al) & 0x7fffffffffffffffull;
+    const unsigned long long bb = (unsigned long long)__double_as_longlong(be) & 0x7fffffffffffffffull;
+    mx = max(mx, max(ba, bb));
+  }
+  if (tid == 0) t2[2 * k + 1] = 0.0;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) gmax[warp] = mx;
+  __syncthreads();
+  for (int q = 0; q < kWL; ++q) mx = max(mx, gmax[q]);
+  const double G = 2.0 * __longlong_as_double((long long)mx);
+  const int wbase = i0 + warp * 32;
+  if (wbase > k) return;  // whole warp past the problem (warp-uniform)
+  const int i = wbase + lane;
+  // lanes with i >= k run the rounds on a settled bracket and store nothing
+  const bool mine = i < k;
+  const int target = k - 1 - i;
+  double lo = 0.0, hi = G;
+  if (G > 0.0) {
+    const double tiny = G * 0x1p-200;  // below this a singular value is zero
+    for (int r = 0; r < kMaxBisect; ++r) {
+      const bool settled = !mine || hi - lo <= 4.0 * kEps * hi || hi <= tiny;
+      if (__all_sync(0xffffffffu, settled)) break;
+      // the trial point: 2^-16 hi while lo = 0; lo 2^(d/2) while hi spans
+      // d >= 2 octaves above lo (exact scalings); else the midpoint
+      const int d = biased_exponent(hi) - biased_exponent(lo);
+      double th;
+      if (lo == 0.0)
+        th = hi * 0x1p-16;
+      else if (d >= 2 && biased_exponent(lo) > 0)
+        th = lo * __longlong_as_double((long long)(1023 + d / 2) << 52);
+      else
+        th = fma(0.5, hi - lo, lo);
+      const int cnt = sturm_count(t2, n, th) - (k + 1);
+      if (!settled) {
+        if (cnt > target)
+          hi = th;
+        else
+          lo = th;
+      }
+    }
+  }
+  if (mine) {
+    const double th = lo > 0.0 ? 0.5 * (lo + hi) : 0.5 * hi;
+    // weight as in k_sigma, both minors on this lane
+    double v, dv, q, dq;
+    int ev, eq;
+    minors(t2, n, th, false, v, dv, ev);
+    minors(t2, n, th, true, q, dq, eq);
+    double wgt = (dv != 0.0) ? ldexp(-q / dv, eq - ev) : 0.0;
+    if (!(wgt >= 0.0)) wgt = 0.0;
+    __stcg(S.sig + i, th);
+    __stcg(S.c2 + i, 2.0 * pi.beta * pi.beta * wgt);
+  }
+  if (i == k) {  // null vector of B^T, as in k_sigma
+    double u = 1.0, nrm2 = 1.0;
+    int e = 0;
+    for (int q = 0; q < k; ++q) {
+      if (bev[q + 1] == 0.0) break;
+      u = -alv[q] * u / bev[q + 1];
+      nrm2 = fma(u, u, nrm2);
+      if (nrm2 > 0x1p+600) {
+        u = ldexp(u, -300);
+        nrm2 = ldexp(nrm2, -600);
+        e += 600;
+      }
+    }
+    __stcg(S.c2 + k, ldexp(pi.beta * pi.beta / nrm2, -e));
+  }
+}
+
+// Which of the two singular-value kernels finishes first: per warp, rounds
+// times the Sturm length 2k+1, either along the longest warp's chain or
+// spread over the GPU's sub-partitions (rounds: ~11 for k_sigma, measured at
+// k = 300; ~60 for bisection).
+bool sigma_by_lanes(const ProjArgs& a, int nprob, int num_sms) {
+  if (num_sms <= 0) return false;
+  double multi = 0.0, lanes = 0.0;
+  int kmax = 0;
+  for (int p = 0; p < nprob; ++p) {  // problems k_first .. k_first + nprob - 1
+    const int k = a.k_first + p;
+    kmax = k > kmax ? k : kmax;
+    multi += (double)(k + 1) * (2 * k + 1);
+    lanes += (double)((k + 32) / 32) * (2 * k + 1);
+  }
+  const double spread = 4.0 * num_sms;
+  const double c_multi = 11.0 * fmax(2 * kmax + 1, multi / spread);
+  const double c_lanes = 60.0 * fmax(2 * kmax + 1, lanes / spread);
+  return c_lanes < c_multi;
 }
 
 // ---- 3. GCV function on the lambda grid: one warp per grid point ------------
@@ -1131,6 +1271,7 @@ ProjDeviceSetup setup_current_device() {
   cudaFuncSetAttribute(k_bidiag, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   cudaFuncSetAttribute(k_bidiag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
   cudaFuncSetAttribute(k_sigma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
+  cudaFuncSetAttribute(k_sigma_lanes, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
   cudaFuncSetAttribute(k_finish, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
   int best = 1;
   for (int cand : {kMaxCluster, 8, 4, 2}) {
@@ -1168,14 +1309,28 @@ cudaError_t launch_projected(const ProjArgs& a, ProjWork& w, cudaStream_t s) {
   const int nprob = batch ? a.nbatch : a.k_last - a.k_first + 1;
   if (nprob <= 0) return cudaSuccess;
   if (!batch && nprob > 1 && !w.packed) return cudaErrorInvalidValue;
-  const int CL = w.cluster;
-  if (CL < 1 || CL > kMaxCluster) return cudaErrorInvalidValue;
+  if (w.cluster < 1 || w.cluster > kMaxCluster) return cudaErrorInvalidValue;
   const ProjDeviceSetup dev_setup = setup_current_device();
   const int kmax = a.k_last;
   const size_t K1 = (size_t)kmax + 1;
-  const int ncl = (kmax + CL - 1) / CL;
-  const size_t vecs = 7 * K1 * sizeof(double);
-  const size_t slab = (size_t)ncl * K1 * sizeof(double);
+  // shared memory of k_bidiag: 5 + 2 kMaxCluster / cl vectors, and the slab
+  // of the CTA's columns when it fits beside them
+  auto vec_bytes = [&](int cl) { return (size_t)(5 + 2 * (kMaxCluster / cl)) * K1 * sizeof(double); };
+  auto slab_bytes = [&](int cl) { return (size_t)((kmax + cl - 1) / cl) * K1 * sizeof(double); };
+  // A history (problems of every size up to kmax) with more CTAs than two
+  // per SM keeps the GPU busy with many clusters at once: there 8 CTAs per
+  // problem, largest k first, do the whole batch in about 0.56 of the time 16
+  // take (k = 1..300), although one problem alone is fastest on 16.
+  int CL = w.cluster;
+  w.desc = 0;
+  if (!batch && nprob * CL > 2 * dev_setup.num_sms && CL > kHistoryCluster &&
+      vec_bytes(kHistoryCluster) + slab_bytes(kHistoryCluster) <= kSmemCap) {
+    CL = kHistoryCluster;
+    w.desc = 1;
+  }
+  w.prob0 = 0;
+  w.kcap = 0;
+  const size_t vecs = vec_bytes(CL), slab = slab_bytes(CL);
   w.slab_in_smem = (vecs + slab <= kSmemCap) ? 1 : 0;
   const size_t dyn1 = vecs + (w.slab_in_smem ? slab : 0);
   const size_t dyn2 = 4 * K1 * sizeof(double);
@@ -1196,11 +1351,26 @@ cudaError_t launch_projected(const ProjArgs& a, ProjWork& w, cudaStream_t s) {
   cfg.numAttrs = 1;
   cudaError_t e = cudaLaunchKernelEx(&cfg, k_bidiag, a, w);
   if (e != cudaSuccess) return e;
-  // 2. singular values and weights: k + 1 warps per problem
-  const dim3 g2((unsigned)((K1 + kWS - 1) / kWS), (unsigned)nprob);
-  size_t sm2 = dyn2;
-  if ((int64_t)g2.x * g2.y <= dev_setup.num_sms && sm2 < kSmemOnePerSm) sm2 = kSmemOnePerSm;
-  k_sigma<<<g2, kWS * 32, sm2, s>>>(a, w);
+  // 2. singular values and weights.  Final problems (the one of size k_last,
+  // every batch entry) always take k_sigma, so that x does not depend on
+  // whether histories were asked for or on the batch a problem was solved
+  // in; the other problems of a history take k_sigma_lanes where that
+  // finishes first.
+  const int nlanes =
+      (!batch && nprob > 1 && sigma_by_lanes(a, nprob - 1, dev_setup.num_sms)) ? nprob - 1 : 0;
+  if (nlanes > 0) {
+    w.prob0 = 0;
+    const dim3 gl((unsigned)((K1 + kWL * 32 - 1) / (kWL * 32)), (unsigned)nlanes);
+    k_sigma_lanes<<<gl, kWL * 32, dyn2, s>>>(a, w);
+  }
+  {
+    w.prob0 = nlanes;
+    const dim3 g2((unsigned)((K1 + kWS - 1) / kWS), (unsigned)(nprob - nlanes));
+    size_t sm2 = dyn2;
+    if ((int64_t)g2.x * g2.y <= dev_setup.num_sms && sm2 < kSmemOnePerSm) sm2 = kSmemOnePerSm;
+    k_sigma<<<g2, kWS * 32, sm2, s>>>(a, w);
+    w.prob0 = 0;
+  }
   // 3. the GCV function on the lambda grid
   if (a.rule == LSLU_LAMBDA_GCV || a.rule == LSLU_LAMBDA_WGCV) {
     const dim3 g3((unsigned)((kGrid + kWB - 1) / kWB), (unsigned)nprob);

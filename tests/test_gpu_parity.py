@@ -73,6 +73,33 @@ def test_ct32_final_only_equals_histories(ct32):
     assert np.array_equal(a["x"], b["x"]) and np.array_equal(b["x"], c["x"])
 
 
+@pytest.mark.parametrize("rule", ["gcv", "wgcv"])
+def test_long_history_against_the_oracle_rule(ct32, rule):
+    """A history of K = 200 projected problems is solved as a throughput batch
+    (8-CTA bidiagonalisations, largest k first; one lane per singular value
+    for every problem but the last), the final one as in a final-only solve.
+    Each lambda_k must minimise the oracle's (w)GCV function of the GPU's own
+    H_{k+1,k} as well as the oracle's choice does, each residual must be the
+    oracle's at that lambda_k, and x must be bit for bit the final-only x."""
+    K = 200
+    with lslu.from_problem(ct32, "f64", K) as s:
+        a = s.solve(ct32.b, K, rule, histories=True)
+        st = s.state(a["k_done"])
+        b = s.solve(ct32.b, K, rule, histories=False)
+    assert a["status"] == lslu.OK and a["k_done"] == K
+    assert np.array_equal(a["x"], b["x"])
+    H, beta = st["H"], st["beta"]
+    for k in list(range(1, K + 1, 9)) + [K - 1, K]:
+        sig, c, _ = O.projected_svd(H[:k + 1, :k], beta)
+        omega = 1.0 if rule == "gcv" else (k + 1) / ct32.m
+        lam_ref = O.select_lambda(sig, c, omega)
+        lam = a["lam_hist"][k - 1]
+        G_ref = O.gcv_value(sig, c, lam_ref, omega)
+        assert O.gcv_value(sig, c, lam, omega) <= G_ref * (1 + 1e-9), k
+        res = O.projected_residual(sig, c, lam)
+        assert abs(a["res_hist"][k - 1] - res) <= 1e-9 * res, k
+
+
 @pytest.mark.parametrize("k", [1, 2, 5, 20, 50])
 @pytest.mark.parametrize("rule,lam", [("none", 0.0), ("fixed", 0.05), ("gcv", 0.0), ("wgcv", 0.0)])
 def test_projected_solve_parity(ct32, k, rule, lam):
