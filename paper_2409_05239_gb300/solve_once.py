@@ -4,6 +4,7 @@
     python -m paper_2409_05239_gb300.solve_once --batch 64 --K 150
     python -m paper_2409_05239_gb300.solve_once --workload ct512 --K 2 --shapes all
     python -m paper_2409_05239_gb300.solve_once --workload ct512 --K 300 --order tiles
+    python -m paper_2409_05239_gb300.solve_once --workload ct512 --K 300 --histories
 
 The first form builds one seeded problem of the named size (see tomo.CONFIGS)
 and solves it `--repeat` times; the second solves a batch of uneven problems
@@ -16,7 +17,9 @@ the products of every shape in one process: each solve launches 2 K products,
 A^T d_k then A l_k for k = 0..K-1.  `--order tiles` builds the handle with
 tomo.locality_order's renumbering (lslu_create_ordered); `--tune` runs the
 sparse-product autotuner first, as the benchmark does; `--loop persistent` or
-`--loop cluster` runs the basis loop as one launch (lslu_set_loop).
+`--loop cluster` runs the basis loop as one launch (lslu_set_loop);
+`--histories` asks for the lambda and residual histories (a projected problem
+for every k).
 """
 from __future__ import annotations
 
@@ -42,6 +45,8 @@ def main(argv=None):
                     help="run the sparse-product autotuner before the solves (as bench.py does)")
     ap.add_argument("--loop", default="graph", choices=["graph", "persistent", "cluster"],
                     help="basis-loop execution (lslu_set_loop)")
+    ap.add_argument("--histories", action="store_true",
+                    help="also solve the projected problem of every k (lambda and residual histories)")
     a = ap.parse_args(argv)
 
     import torch
@@ -85,7 +90,7 @@ def main(argv=None):
                     s.set_spmv_shape(code, code)
                 t0 = time.perf_counter()
                 for _ in range(a.repeat):
-                    r = s.solve(P.b, K, a.rule, a.lam)
+                    r = s.solve(P.b, K, a.rule, a.lam, histories=a.histories)
                 runs.append({"shape": name, "status": r["status"],
                              "seconds_per_solve": (time.perf_counter() - t0) / a.repeat})
             launches = s.last_launch_count()
