@@ -428,14 +428,17 @@ def oracle_comparison(res, data, oracle):
     res["vs_oracle"] = out
 
 
-def batched_study(dev, K=150, count=64, order="tiles"):
+def batched_study(dev, K=150, count=64, order="tiles", shape=None):
     """Batched solves: `count` independent problems of uneven size (image side
     64..256, 30..180 angles, 1.41 N rays, own phantom and noise level in
     [0.5%, 3%]) solved together by one launch sequence (FP32, GCV, K
     iterations each), against the same problems solved one after another
     with single-problem handles; every problem renumbered by
     tomo.locality_order when order == "tiles" (the batch in the natural
-    numbering is timed beside it)."""
+    numbering is timed beside it).  Every handle runs its sparse products
+    with the row shape `shape` where its matrices allow it (None: the
+    default), the batch and the single-problem handles alike, so that each
+    problem's x can be compared bit for bit."""
     import torch
 
     from paper_2409_05239_gb300 import lslu
@@ -447,7 +450,19 @@ def batched_study(dev, K=150, count=64, order="tiles"):
     x_dev = torch.empty(sum(P.n for P in Ps), dtype=torch.float64, device=dev)
     kd_dev = torch.empty(count, dtype=torch.int32, device=dev)
     orders = [tomo.locality_order(P) for P in Ps] if order == "tiles" else None
-    bs = lslu.from_problems(Ps, "f32", K, stream=stream.cuda_stream, orders=orders)
+    code = None if shape is None else lslu.Solver.SHAPES.index(shape)
+    shaped = []
+
+    def use_shape(s):
+        cfg = s.spmv_config()
+        ok = code is not None and (cfg["compressed_A"] or "16-bit" not in shape) and \
+            (cfg["compressed_AT"] or "16-bit" not in shape)
+        if ok:
+            s.set_spmv_shape(code, code)
+        shaped.append(ok)
+        return s
+
+    bs = use_shape(lslu.from_problems(Ps, "f32", K, stream=stream.cuda_stream, orders=orders))
 
     def timed(fn, reps):
         fn()
@@ -468,13 +483,13 @@ def batched_study(dev, K=150, count=64, order="tiles"):
     bs.close()
     ms_nat = None
     if orders is not None:
-        bn = lslu.from_problems(Ps, "f32", K, stream=stream.cuda_stream)
+        bn = use_shape(lslu.from_problems(Ps, "f32", K, stream=stream.cuda_stream))
         ms_nat = timed(lambda: bn.solve_device(b_dev, x_dev, K, "gcv", k_done=kd_dev), 3)
         bn.close()
-    singles = [lslu.Solver(P.m, P.n, P.row_ptr, P.col_idx, P.vals, "f32", K,
-                           stream=stream.cuda_stream,
-                           row_order=None if orders is None else orders[p][0],
-                           col_order=None if orders is None else orders[p][1])
+    singles = [use_shape(lslu.Solver(P.m, P.n, P.row_ptr, P.col_idx, P.vals, "f32", K,
+                                     stream=stream.cuda_stream,
+                                     row_order=None if orders is None else orders[p][0],
+                                     col_order=None if orders is None else orders[p][1]))
                for p, P in enumerate(Ps)]
     bd = [torch.from_numpy(P.b).to(dev) for P in Ps]
     xd = [torch.empty(P.n, dtype=torch.float64, device=dev) for P in Ps]
@@ -497,7 +512,10 @@ def batched_study(dev, K=150, count=64, order="tiles"):
     nbytes = sum(solve_bytes(P, "f32", K) for P in Ps)
     return {"problems": count, "K": K, "m_total": int(sum(P.m for P in Ps)),
             "n_total": int(sum(P.n for P in Ps)), "nnz_total": int(sum(P.nnz for P in Ps)),
-            "numbering": ORDER_NOTE[order], "ms_per_batch_solve": ms_b,
+            "numbering": ORDER_NOTE[order],
+            "spmv_shape": "default" if shape is None else shape if all(shaped) else
+            {"shape": shape, "handles_with_it": int(sum(shaped)), "handles": len(shaped)},
+            "ms_per_batch_solve": ms_b,
             "ms_per_batch_solve_natural_numbering": ms_nat,
             "problem_iter_per_s": iters / (ms_b / 1e3),
             "hbm_gbs_solve": nbytes / (ms_b * 1e-3) / 1e9,

@@ -131,25 +131,62 @@ def _ptr(a):
 LOOPS = {"graph": 0, "persistent": 1, "cluster": 2}
 
 
+def _raise_unless_ok(handle, st):
+    if st != OK:
+        raise LsluError(st, handle.lib.lslu_error_string(handle.h).decode())
+    return st
+
+
 class _LoopControl:
     """Basis-loop execution of a handle (lslu_set_loop / lslu_loop_config)."""
 
     def set_loop(self, mode="persistent", blocks=0, wait_limit_ns=0, stall_first_barrier=False):
-        st = self.lib.lslu_set_loop(self.h, LOOPS[mode], int(blocks), int(wait_limit_ns),
-                                    int(bool(stall_first_barrier)))
-        if st != OK:
-            raise LsluError(st, self.lib.lslu_error_string(self.h).decode())
+        _raise_unless_ok(self, self.lib.lslu_set_loop(self.h, LOOPS[mode], int(blocks),
+                                                      int(wait_limit_ns),
+                                                      int(bool(stall_first_barrier))))
 
     def loop_config(self):
         v = [ctypes.c_int32(0) for _ in range(3)]
-        st = self.lib.lslu_loop_config(self.h, *[ctypes.byref(t) for t in v])
-        if st != OK:
-            raise LsluError(st, self.lib.lslu_error_string(self.h).decode())
+        _raise_unless_ok(self, self.lib.lslu_loop_config(self.h, *[ctypes.byref(t) for t in v]))
         return dict(mode=[k for k, c in LOOPS.items() if c == v[0].value][0],
                     blocks=v[1].value, max_blocks=v[2].value)
 
 
-class Solver(_LoopControl):
+class _SpmvControl:
+    """Row shapes of a handle's sparse products (lslu_set_spmv_shape,
+    lslu_spmv_config, lslu_tune_spmv); a batched handle has them too."""
+
+    SHAPES = ("16x2", "32x1", "16x1", "8x1", "8x2", "4x1",
+              "16x2/16-bit", "32x1/16-bit", "16x1/16-bit", "8x1/16-bit", "8x2/16-bit", "4x1/16-bit",
+              "32x8e", "32x8e/16-bit", "32x4e", "32x4e/16-bit")
+
+    def set_spmv_shape(self, shape_A, shape_AT=None):
+        """Row shape of the sparse products (index into SHAPES)."""
+        sa = int(shape_A)
+        st = sa if shape_AT is None else int(shape_AT)
+        _raise_unless_ok(self, self.lib.lslu_set_spmv_shape(self.h, sa, st))
+
+    def spmv_config(self):
+        """Row shapes and column formats of A and A^T."""
+        v = [ctypes.c_int32(0) for _ in range(4)]
+        _raise_unless_ok(self, self.lib.lslu_spmv_config(self.h, *[ctypes.byref(t) for t in v]))
+        return dict(shape_A=self.SHAPES[v[0].value], shape_AT=self.SHAPES[v[1].value],
+                    compressed_A=bool(v[2].value), compressed_AT=bool(v[3].value))
+
+    def tune_spmv(self, reps=5):
+        """Time every row shape on A and A^T and keep the fastest; returns the
+        chosen shapes and the per-shape times (microseconds)."""
+        a = ctypes.c_int32(0)
+        t = ctypes.c_int32(0)
+        ns = len(self.SHAPES)
+        us = np.zeros(2 * ns)
+        _raise_unless_ok(self, self.lib.lslu_tune_spmv(self.h, int(reps), ctypes.byref(a),
+                                                       ctypes.byref(t), _ptr(us)))
+        keep = lambda v: {k: x for k, x in zip(self.SHAPES, v.tolist()) if x >= 0}
+        return dict(shape_A=a.value, shape_AT=t.value, us_A=keep(us[:ns]), us_AT=keep(us[ns:]))
+
+
+class Solver(_LoopControl, _SpmvControl):
     """One LSLU handle on the current CUDA device.
 
     value_type: 'f64' (FP64 basis and accumulation), 'f32' or 'bf16' (A's
@@ -341,34 +378,6 @@ class Solver(_LoopControl):
                                      _ptr(tot)))
         return dict(var_diag=d, var_sum=float(tot[0]))
 
-    SHAPES = ("16x2", "32x1", "16x1", "8x1", "8x2", "4x1",
-              "16x2/16-bit", "32x1/16-bit", "16x1/16-bit", "8x1/16-bit", "8x2/16-bit", "4x1/16-bit",
-              "32x8e", "32x8e/16-bit", "32x4e", "32x4e/16-bit")
-
-    def set_spmv_shape(self, shape_A, shape_AT=None):
-        """Row shape of the sparse products (index into SHAPES)."""
-        sa = int(shape_A)
-        self._check(self.lib.lslu_set_spmv_shape(self.h, sa, sa if shape_AT is None else int(shape_AT)))
-
-    def spmv_config(self):
-        """Row shapes and column formats of A and A^T."""
-        v = [ctypes.c_int32(0) for _ in range(4)]
-        self._check(self.lib.lslu_spmv_config(self.h, *[ctypes.byref(t) for t in v]))
-        return dict(shape_A=self.SHAPES[v[0].value], shape_AT=self.SHAPES[v[1].value],
-                    compressed_A=bool(v[2].value), compressed_AT=bool(v[3].value))
-
-    def tune_spmv(self, reps=5):
-        """Time every row shape on A and A^T and keep the fastest; returns the
-        chosen shapes and the per-shape times (microseconds)."""
-        a = ctypes.c_int32(0)
-        t = ctypes.c_int32(0)
-        ns = len(self.SHAPES)
-        us = np.zeros(2 * ns)
-        self._check(self.lib.lslu_tune_spmv(self.h, int(reps), ctypes.byref(a), ctypes.byref(t),
-                                            _ptr(us)))
-        keep = lambda v: {k: x for k, x in zip(self.SHAPES, v.tolist()) if x >= 0}
-        return dict(shape_A=a.value, shape_AT=t.value, us_A=keep(us[:ns]), us_AT=keep(us[ns:]))
-
     def profile(self, enable=True):
         self._check(self.lib.lslu_profile(self.h, int(enable)))
 
@@ -442,7 +451,7 @@ def stack_orders(orders, k, off):
         for p, o in enumerate(orders)]), dtype=np.int32)
 
 
-class BatchedSolver(_LoopControl):
+class BatchedSolver(_LoopControl, _SpmvControl):
     """One handle over several independent problems solved by one launch
     sequence (lslu_create_batched).  csr_list holds (m, n, row_ptr, col_idx,
     vals) per problem in the problem's own index space; they are stacked into
