@@ -115,7 +115,8 @@ lslu_status lslu_create_ordered(int64_t m, int64_t n, int64_t nnz, const int64_t
  * for every j (all at once after the basis loop, since the basis never
  * depends on lambda); otherwise only for j = k_done.  x_out is the same bit
  * for bit either way.  A breakdown is not a failure of the call: it returns
- * LSLU_BREAKDOWN_* with x of the last completed iteration (x0 if none).  K must satisfy 1 <= K <= max_iter. */
+ * LSLU_BREAKDOWN_* with x of the last completed iteration (x0 if none).  K
+ * must satisfy 1 <= K <= max_iter. */
 lslu_status lslu_solve(lslu_handle h, const double* b, const double* x0, int32_t K,
                        int32_t rule, double lambda, int32_t ptr_location, double* x_out,
                        int32_t* col_pivots, int32_t* row_pivots, double* lambda_hist,
