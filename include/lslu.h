@@ -304,6 +304,22 @@ lslu_status lslu_projected(lslu_handle h, int32_t k, const double* H, int32_t ld
                            double* y, double* sigma, double* c, double* lambda_out,
                            double* resid_out);
 
+/* The projected problems of a whole history (Algorithm 5 solves Eq. TSP at
+ * every iteration): for every leading block H_{k+1,k}, k = 1..K, of one
+ * H ((K+1) x K, FP64, column-major, ldh >= K+1; H_{k+1,k} is rows 0..k and
+ * columns 0..k-1) with the same beta, lambda_k by the rule of lslu_solve and
+ * the residual ||beta e1 - H_{k+1,k} y_k||.  The same launches as the
+ * histories of lslu_solve, so a history can be recomputed under another rule
+ * from lslu_get_state's H without running the basis again; lambda_hist[K-1]
+ * equals lslu_projected's lambda_out for k = K bit for bit.  H, lambda_hist
+ * (K) and resid_hist (K; either may be NULL) are host or device per
+ * ptr_location.  Uses the handle's workspace; 1 <= K <= max_iter of the
+ * handle.  Errors: LSLU_ERR_INVALID_ARG (K, ldh, H, rule, m, a negative
+ * fixed lambda, ptr_location), LSLU_ERR_OOM, LSLU_ERR_CUDA. */
+lslu_status lslu_projected_history(lslu_handle h, int32_t K, const double* H, int32_t ldh,
+                                   double beta, int32_t rule, double lambda, int64_t m,
+                                   int32_t ptr_location, double* lambda_hist, double* resid_hist);
+
 /* Allocation-free variant of lslu_projected, for callers that cannot call
  * cudaMalloc (for example code that runs under a framework whose memory pool
  * must own every device allocation, or a time-critical loop that cannot

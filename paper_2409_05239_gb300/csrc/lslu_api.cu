@@ -590,10 +590,11 @@ int64_t enqueue_solve(Ctx* c, cudaStream_t s, const double* db, const double* dx
     w.packed = 0;
     w.slot_stride = projected_slot_doubles(c->kmax, c->pw_cluster);
   }
-  launch_projected(pa, w, s);
+  int nproj = 0;
+  launch_projected(pa, w, s, &nproj);
   launch_recombine<BT>(L, c->ldl, c->y, c->kmax, dx0, c->xout, n, c->st, P, tpn, K, s,
                        c->num_sms);
-  launches += 2;
+  launches += nproj + 1;
   return launches;
 }
 
@@ -1480,9 +1481,10 @@ lslu_status stopping_online(Ctx* c, const double* db, const double* dx0, int K_m
     w.base = c->pw_batched;
     w.offsets = c->pw_offsets;
     w.packed = 1;
-    CK(launch_projected(pa, w, s));
+    int nproj = 0;
+    CK(launch_projected(pa, w, s, &nproj));
     launch_stop_select(pa.res_out, pa.tr_out, G, k1, (double)n, (double)m, tol, c->st, dk, s);
-    launches += 5;  // projected kernels and the selection
+    launches += nproj + 1;  // projected kernels and the selection
     int32_t r = 0;
     CK(cudaMemcpyAsync(&r, dk, 4, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(c->st_host, c->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
@@ -1585,7 +1587,9 @@ extern "C" lslu_status lslu_solve_stopping(lslu_handle h, const double* b, const
     w.base = c->pw_single;
     w.cluster = c->pw_cluster;
     w.slot_stride = projected_slot_doubles(c->kmax, c->pw_cluster);
-    CK(launch_projected(pa, w, s));
+    int nproj = 0;
+    CK(launch_projected(pa, w, s, &nproj));
+    c->launches += nproj + 1;
     if (c->value_type == LSLU_F64)
       launch_recombine<double>((const double*)c->L, c->ldl, c->y, c->kmax, dx0, c->xout, n,
                                nullptr, 1, nullptr, ks, s, c->num_sms);
@@ -1970,6 +1974,67 @@ extern "C" lslu_status lslu_projected(lslu_handle h, int32_t k, const double* H,
   if (cv) CK(cudaMemcpyAsync(cv, c->cvec, (k + 1) * 8, kind, s));
   if (lambda_out) CK(cudaMemcpyAsync(lambda_out, c->proj_out + (k - 1), 8, kind, s));
   if (resid_out) CK(cudaMemcpyAsync(resid_out, c->proj_out + c->res_off + (k - 1), 8, kind, s));
+  CK(cudaStreamSynchronize(s));
+  return LSLU_OK;
+}
+
+extern "C" lslu_status lslu_projected_history(lslu_handle h, int32_t K, const double* H,
+                                              int32_t ldh, double beta, int32_t rule,
+                                              double lambda, int64_t m, int32_t ptr_location,
+                                              double* lambda_hist, double* resid_hist) {
+  Ctx* c = h;
+  if (!c) return set_err(nullptr, LSLU_ERR_INVALID_ARG, "NULL handle");
+  if (K < 1 || K > c->kmax || ldh < K + 1 || !H)
+    return set_err(c, LSLU_ERR_INVALID_ARG, "invalid K, ldh or H");
+  if (rule < LSLU_LAMBDA_NONE || rule > LSLU_LAMBDA_WGCV || m < 1)
+    return set_err(c, LSLU_ERR_INVALID_ARG, "invalid rule or m");
+  if (rule == LSLU_LAMBDA_FIXED && !(lambda >= 0.0))
+    return set_err(c, LSLU_ERR_INVALID_ARG, "fixed lambda must be >= 0");
+  if (ptr_location != LSLU_HOST && ptr_location != LSLU_DEVICE)
+    return set_err(c, LSLU_ERR_INVALID_ARG, "unknown ptr_location");
+  c->adj_valid = false;  // the projected work space is reused below
+  lslu_status st = ensure_batched_workspace(c);
+  if (st != LSLU_OK) return st;
+  cudaStream_t s = c->stream;
+  const double* dH = H;
+  struct StageGuard {  // staging copy of a host H, freed on every exit
+    double* p = nullptr;
+    ~StageGuard() {
+      if (p) cudaFree(p);
+    }
+  } stage;
+  if (ptr_location == LSLU_HOST) {
+    CK(dmalloc(&stage.p, (size_t)(K + 1) * K));
+    CK(cudaMemcpy2DAsync(stage.p, (K + 1) * 8, H, (size_t)ldh * 8, (K + 1) * 8, K,
+                         cudaMemcpyHostToDevice, s));
+    dH = stage.p;
+    ldh = K + 1;
+  }
+  ProjArgs pa;
+  std::memset(&pa, 0, sizeof(pa));
+  pa.H = dH;
+  pa.ldh = ldh;
+  pa.beta_val = beta;
+  pa.rule = rule;
+  pa.lambda = rule == LSLU_LAMBDA_FIXED ? lambda : 0.0;
+  pa.m = m;
+  pa.nbatch = 1;
+  pa.k_first = 1;
+  pa.k_last = K;
+  pa.want_y = 0;
+  pa.lam_out = c->proj_out;
+  pa.res_out = c->proj_out + c->res_off;
+  ProjWork w;
+  w.base = c->pw_batched;
+  w.offsets = c->pw_offsets;
+  w.packed = 1;
+  w.cluster = c->pw_cluster;
+  CK(launch_projected(pa, w, s));
+  const cudaMemcpyKind kind =
+      ptr_location == LSLU_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  if (lambda_hist) CK(cudaMemcpyAsync(lambda_hist, c->proj_out, (size_t)K * 8, kind, s));
+  if (resid_hist)
+    CK(cudaMemcpyAsync(resid_hist, c->proj_out + c->res_off, (size_t)K * 8, kind, s));
   CK(cudaStreamSynchronize(s));
   return LSLU_OK;
 }

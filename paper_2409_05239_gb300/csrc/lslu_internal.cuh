@@ -465,7 +465,9 @@ struct ProjArgs {
                        // are skipped and the y problem uses k = k_done
   unsigned long long* tstamp;  // optional phase timestamps (ns) of the last problem
 };
-cudaError_t launch_projected(const ProjArgs& a, ProjWork& w, cudaStream_t s);
+// nlaunch (may be null) receives the number of kernels launched.
+cudaError_t launch_projected(const ProjArgs& a, ProjWork& w, cudaStream_t s,
+                             int* nlaunch = nullptr);
 int64_t projected_slot_doubles(int kk, int CL);
 // Optimal lambda of the last projected problem of size K in slot w (needs
 // G = L^T L and g = L^T x_true, k x k and k, FP64): E on the 257-point grid

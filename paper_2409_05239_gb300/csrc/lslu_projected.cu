@@ -832,6 +832,46 @@ __global__ void __launch_bounds__(kWL * 32) k_sigma_lanes(ProjArgs a, ProjWork w
   }
 }
 
+// ---- 2''. weights of numerically zero singular values ----------------------
+// U is orthogonal, so sum_i c_i^2 + c_{k+1}^2 = beta^2.  The residue formula
+// keeps that to rounding for every separated singular value, tiny ones
+// included, but at an exactly or numerically zero one (a rank-deficient H;
+// never an unreduced Hessenberg H of the basis loop) it degenerates at the
+// near-triple eigenvalue 0 of T and the sum is off.  Such a sigma_i (<= (k+1)
+// eps sigma_1) has its left singular vector, and c_i, fixed only up to the
+// null space of H^T; only the sum of those c_i^2 and c_{k+1}^2 enters G, the
+// residual and y (f_i = 1 for them, sigma_i c_i / (sigma_i^2 + lambda^2)
+// vanishes with sigma_i, and lambda = 0 drops them).  So where the sum misses
+// beta^2 by more than rounding (64 k eps beta^2), those c_i^2 share equally
+// what is left of beta^2.  One block per problem.
+__global__ void __launch_bounds__(kT) k_weights(ProjArgs a, ProjWork w) {
+  __shared__ double red[33];  // block_sum's scratch
+  const ProbInfo pi = prob_info(a, blockIdx.x);
+  const int k = pi.k;
+  if (k == 0) return;  // block-uniform
+  const Slots S = slot_of(w, pi);
+  const double thr = (double)(k + 1) * kEps * ldg_cg(S.sig);
+  double rest = 0.0, zero = 0.0, nzero = 0.0;
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    const double c2 = ldg_cg(S.c2 + i);
+    if (ldg_cg(S.sig + i) <= thr) {
+      nzero += 1.0;
+      zero += c2;
+    } else {
+      rest += c2;
+    }
+  }
+  nzero = block_sum(nzero, red);  // exact: a count below 2^53
+  if (nzero == 0.0) return;       // block-uniform
+  rest = block_sum(rest, red) + ldg_cg(S.c2 + k);
+  zero = block_sum(zero, red);
+  const double b2 = pi.beta * pi.beta;
+  if (fabs(b2 - rest - zero) <= 64.0 * k * kEps * b2) return;  // consistent
+  const double each = fmax(0.0, b2 - rest) / nzero;
+  for (int i = threadIdx.x; i < k; i += blockDim.x)
+    if (ldg_cg(S.sig + i) <= thr) __stcg(S.c2 + i, each);
+}
+
 // Which of the two singular-value kernels finishes first: per warp, rounds
 // times the Sturm length 2k+1, either along the longest warp's chain or
 // spread over the GPU's sub-partitions (rounds: ~11 for k_sigma, measured at
@@ -1352,7 +1392,8 @@ ProjDeviceSetup setup_current_device() {
 
 int projected_cluster_size() { return setup_current_device().cluster; }
 
-cudaError_t launch_projected(const ProjArgs& a, ProjWork& w, cudaStream_t s) {
+cudaError_t launch_projected(const ProjArgs& a, ProjWork& w, cudaStream_t s, int* nlaunch) {
+  if (nlaunch) *nlaunch = 0;
   // one problem per k of k_first..k_last (histories), or one final problem
   // per batch entry
   const bool batch = a.nbatch > 1;
@@ -1422,13 +1463,16 @@ cudaError_t launch_projected(const ProjArgs& a, ProjWork& w, cudaStream_t s) {
     k_sigma<<<g2, kWS * 32, sm2, s>>>(a, w);
     w.prob0 = 0;
   }
+  k_weights<<<(unsigned)nprob, kT, 0, s>>>(a, w);
   // 3. the GCV function on the lambda grid
-  if (a.rule == LSLU_LAMBDA_GCV || a.rule == LSLU_LAMBDA_WGCV) {
+  const bool grid = a.rule == LSLU_LAMBDA_GCV || a.rule == LSLU_LAMBDA_WGCV;
+  if (grid) {
     const dim3 g3((unsigned)((kGrid + kWB - 1) / kWB), (unsigned)nprob);
     k_gcv_grid<<<g3, kWB * 32, 0, s>>>(a, w);
   }
   // 4. lambda, residual, y
   k_finish<<<(unsigned)nprob, kTF, dyn4, s>>>(a, w);
+  if (nlaunch) *nlaunch = 4 + (nlanes > 0 ? 1 : 0) + (grid ? 1 : 0);
   return cudaGetLastError();
 }
 

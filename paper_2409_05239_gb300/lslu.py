@@ -30,7 +30,7 @@ EXPORTS = ("lslu_create", "lslu_solve", "lslu_get_state", "lslu_spmv", "lslu_pro
            "lslu_solve_stopping", "lslu_solve_sampled", "lslu_set_spmv_shape",
            "lslu_tune_spmv", "lslu_uq", "lslu_solve_optimal", "lslu_spmv_config",
            "lslu_create_ordered", "lslu_create_batched_ordered", "lslu_create_shared_ordered",
-           "lslu_set_loop", "lslu_loop_config")
+           "lslu_set_loop", "lslu_loop_config", "lslu_projected_history")
 
 _lib = None
 
@@ -71,6 +71,8 @@ def load(path: str | None = None):
     lib.lslu_spmv.restype = i32
     lib.lslu_projected.argtypes = [vp, i32, vp, i32, f64, i32, f64, i64, i32, vp, vp, vp, vp, vp]
     lib.lslu_projected.restype = i32
+    lib.lslu_projected_history.argtypes = [vp, i32, vp, i32, f64, i32, f64, i64, i32, vp, vp]
+    lib.lslu_projected_history.restype = i32
     lib.lslu_projected_noalloc.argtypes = [i32, vp, i32, f64, i32, f64, i64, vp, vp, vp, vp,
                                            vp, vp]
     lib.lslu_projected_noalloc.restype = i32
@@ -357,6 +359,20 @@ class Solver(_LoopControl, _SpmvControl):
                                      _ptr(c), _ptr(lo), _ptr(ro))
         self._check(st)
         return dict(y=y, sigma=sig, c=c, lam=float(lo[0]), resid=float(ro[0]))
+
+    def projected_history(self, H, beta, rule="gcv", lam=0.0, m=None):
+        """lambda_k and the residual of the projected problem of every leading
+        block H[:k+1, :k], k = 1..K, of a host H ((K+1) x K):
+        dict(lam_hist, res_hist)."""
+        H = np.asfortranarray(H, dtype=np.float64)
+        K = H.shape[1]
+        lh = np.zeros(K)
+        rh = np.zeros(K)
+        self.epoch += 1
+        self._check(self.lib.lslu_projected_history(self.h, K, _ptr(H), K + 1, float(beta),
+                                                    RULES[rule], float(lam), int(m or self.m),
+                                                    HOST, _ptr(lh), _ptr(rh)))
+        return dict(lam_hist=lh, res_hist=rh)
 
     def solve_optimal(self, b, K, x_true):
         """x_K with the optimal lambda (needs x_true): dict(x, lam)."""
