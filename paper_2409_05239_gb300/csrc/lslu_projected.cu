@@ -1,8 +1,9 @@
 // Projected Tikhonov problem of Hybrid LSLU (Eq. TSP, Section 3.2.1), FP64.
 //
 // For one (k+1) x k upper Hessenberg H and beta (or one per batch entry, or
-// one per k of a history) four kernels run in sequence:
-//   1. k_bidiag, one thread-block cluster per problem: Householder
+// one per k of a history) these kernels run in sequence:
+//   1. k_bidiag, one thread-block cluster per problem (16 CTAs; 8 for the
+//      many problems of a history, largest k first): Householder
 //      bidiagonalisation H = P B Q^T with B lower bidiagonal ((k+1) x k:
 //      alpha_j on the diagonal, beta_{j+1} below it) and P e1 = e1 (each step
 //      first reflects row j from the right, then column j below the diagonal
@@ -14,7 +15,8 @@
 //      products (and the owner of column j that column) in its own shared
 //      memory, and after one cluster barrier every CTA reads them all through
 //      distributed shared memory, sums them in a fixed order and computes both
-//      reflectors of the step itself.
+//      reflectors of the step itself.  The partial sums run over 16 virtual
+//      ranks in one fixed order whatever the cluster size.
 //   2. k_sigma, one warp per singular value over the whole GPU: the singular
 //      values of B are the positive eigenvalues of the Golub-Kahan tridiagonal
 //      T (order 2k+1, zero diagonal, off-diagonals alpha_0, beta_1, alpha_1,
@@ -26,6 +28,10 @@
 //      det(T_{2:,2:} - theta) / det(T - theta), with the leading and trailing
 //      minors evaluated by two lanes of the warp together; one more warp
 //      forms c_{k+1}^2 = beta^2 / ||u||^2 for the null vector u of B^T.
+//      k_sigma_lanes does the same for the non-final problems of a history,
+//      one lane per singular value, where that finishes first.  k_weights
+//      then keeps sum c_i^2 + c_{k+1}^2 = beta^2 where a numerically zero
+//      singular value breaks the residue formula.
 //   3. k_gcv_grid (GCV rules only), one warp per point of the 257-point log
 //      grid sigma_1 * 10^[-14, 2] of lambda: the GCV function (Eq. gcv2), or
 //      weighted GCV with omega = (k+1)/m (Eq. wgcv).
