@@ -208,3 +208,37 @@ def test_method_commutes_with_a_renumbering():
             assert np.array_equal(ic[alt.gp], ref.gp) and np.array_equal(ir[alt.tp], ref.tp)
             assert np.linalg.norm(alt.x[co] - ref.x) <= 1e-12 * np.linalg.norm(ref.x)
             assert np.allclose(alt.H, ref.H, rtol=0, atol=1e-12 * np.abs(ref.H).max())
+
+
+def test_zero_singular_value_weight_enters_only_as_a_sum():
+    """For a rank-deficient block (a zero column) the weight c_i of its zero
+    singular value is fixed only up to the null space of H^T: G (Eqs. gcv2,
+    wgcv) and the projected residual see it only through c_i^2 + c_{k+1}^2,
+    y (Eq. 4) only through sigma_i c_i / (sigma_i^2 + lambda^2), which
+    vanishes with sigma_i, and sum c^2 = beta^2 since U is orthogonal.  This
+    is why the GPU may place that weight differently (a reading of the
+    paper's formulas at a singular H, which the paper does not discuss)."""
+    rng = np.random.default_rng(8)
+    k = 12
+    H = rng.standard_normal((k + 1, k))
+    H[:, 5] = 0.0
+    beta = 1.7
+    sig, c, V = O.projected_svd(H, beta)
+    assert abs(np.sum(c ** 2) - beta ** 2) <= 1e-13 * beta ** 2
+    z = sig <= (k + 1) * np.finfo(float).eps * sig[0]
+    assert z.sum() == 1 and z[-1]
+    assert np.linalg.norm(H @ V[:, -1]) <= 1e-13 * sig[0]
+    moved = c.copy()
+    moved[k] = np.hypot(c[k], c[k - 1])
+    moved[k - 1] = 0.0
+    for lam in [0.0] + [f * sig[0] for f in (1e-6, 1e-3, 0.3, 5.0)]:
+        if lam > 0.0:
+            for omega in (1.0, 0.2):
+                assert np.isclose(O.gcv_value(sig, moved, lam, omega),
+                                  O.gcv_value(sig, c, lam, omega), rtol=1e-12, atol=0)
+        assert np.isclose(O.projected_residual(sig, moved, lam),
+                          O.projected_residual(sig, c, lam), rtol=1e-12, atol=0)
+        y0 = O.tikhonov_y(sig, c, V, lam)
+        term = 0.0 if lam == 0.0 else sig[-1] * abs(c[k - 1]) / (sig[-1] ** 2 + lam ** 2)
+        dy = np.linalg.norm(O.tikhonov_y(sig, moved, V, lam) - y0)
+        assert dy <= term * (1 + 1e-9) + 1e-12 * np.linalg.norm(y0)
