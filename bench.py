@@ -856,12 +856,23 @@ def run_reference(args):
     import oracle.lslu_oracle as O
 
     A = P.scipy()
-    t0 = time.perf_counter()
-    O.hybrid_lslu(A, P.b, None, 2, "gcv", histories=False)
-    t_probe = time.perf_counter() - t0
-    # each step: a bounded sample of the same solve, sized so the whole run
-    # stays within a few minutes
-    ks = int(max(2, min(K, (120.0 / max(1, args.steps + args.warmup)) / max(t_probe / 2, 1e-3))))
+
+    def solve_seconds(k):
+        t0 = time.perf_counter()
+        O.hybrid_lslu(A, P.b, None, k, "gcv", histories=False)
+        return time.perf_counter() - t0
+
+    # each step: a bounded sample of the same solve (its first ks iterations),
+    # sized so the whole run stays within a few minutes.  Iteration j
+    # eliminates against j earlier basis vectors, so k iterations cost about
+    # a k + b k^2; two probes fix a and b.
+    t2, t10 = solve_seconds(2), solve_seconds(10)
+    b = max((t10 - 5.0 * t2) / 80.0, 0.0)
+    a = max((t2 - 4.0 * b) / 2.0, 1e-4)
+    per_solve = 120.0 / max(1, args.steps + args.warmup)
+    ks = 2
+    while ks < K and a * (ks + 1) + b * (ks + 1) ** 2 <= per_solve:
+        ks += 1
     for _ in range(args.warmup):
         O.hybrid_lslu(A, P.b, None, ks, "gcv", histories=False)
     t0 = time.perf_counter()
